@@ -1,0 +1,886 @@
+/*
+ * qs_oracle.c -- plain, slow FP64 CPU oracle of the QuadSwarm forward-dynamics
+ * step (Huang et al., "QuadSwarm: A Modular Multi-Quadrotor Simulator for Deep
+ * Reinforcement Learning with Direct Thrust Control", arXiv 2306.09537).
+ *
+ * TEST INFRASTRUCTURE. Only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this library. The product path (the CUDA
+ * library) never calls it, and the two share no source, header, table or
+ * constant generator.
+ *
+ * Scope and order of one control step (paper Sec. III-A .. III-E, IV):
+ *   for each substep s (physics at 200 Hz, two per 100 Hz control step, Sec. IV):
+ *     per drone: S1 motor command + lag (Sec. III-A "Motor Lag"),
+ *                S2 motor noise + thrust (Sec. III-A "Motor Noise"),
+ *                S3 wrench from the rotor layout (Sec. III-A dynamics block),
+ *                S4 linear dynamics with floor friction (Sec. III-A, III-B "Ground"),
+ *                S5 angular (Euler) dynamics (Sec. III-A dynamics block),
+ *                S6 semi-implicit Euler + re-orthonormalisation,
+ *                S7 floor hit (Sec. III-B "Ground"),
+ *                S8 wall / ceiling contact (Sec. III-B "Wall or Ceiling")
+ *   S9  pair pass: which pairs of an environment collide (Sec. III-B "Quad-Quad")
+ *   S10 collision response (Sec. III-B "Quad-Quad" equation block)
+ *   S11 K nearest neighbours (Sec. II-B, III-C)
+ *   S12 observation with sensor noise (Sec. III-C)
+ *   S13 reward (Sec. III-E) and done (15 s episodes, Sec. IV)
+ *
+ * Where the paper is silent or garbled this file takes the readings listed in
+ * the repository's design notes; each is restated at the point of use.
+ *
+ * Floating point: everything is double, except the canonical pair key (S9,
+ * S11), which is evaluated in binary32 on binary32-rounded positions so that
+ * neighbour indices and collision sets are well defined decisions. Build with
+ * -ffp-contract=off and without -ffast-math.
+ *
+ * Parity unpinned (no closed form or printed value constrains them): the
+ * reward weights' semantics, the friction constant mu, the collision constants
+ * and the sensor-noise reading; the tests only check them for self-consistency
+ * and against hand-derived single cases.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "qs_oracle.h"
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as    */
+/* easy as 1, 2, 3", SC'11): a 4x32-bit counter, a 2x32-bit key, ten rounds   */
+/* of two 32x32->64 multiplies with the Weyl key schedule between rounds.     */
+/* ------------------------------------------------------------------------- */
+static const uint32_t PH_MUL0 = 0xD2511F53u, PH_MUL1 = 0xCD9E8D57u;
+static const uint32_t PH_WEYL0 = 0x9E3779B9u, PH_WEYL1 = 0xBB67AE85u;
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += PH_WEYL0; k1 += PH_WEYL1; }
+        uint64_t prod0 = (uint64_t)PH_MUL0 * (uint64_t)x0;
+        uint64_t prod1 = (uint64_t)PH_MUL1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* u = (2k+1) / 2^24 with k = the top 23 bits of r: strictly inside (0,1) and
+ * exactly representable in binary32 and binary64 alike. */
+double or_uniform(uint32_t r) { return ((double)(r >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+/* Box-Muller (1958): two independent N(0,1) from two uniforms. */
+static void box_muller(double u0, double u1, double* n0, double* n1) {
+    double rho = sqrt(-2.0 * log(u0));
+    double ang = 2.0 * M_PI * u1;
+    *n0 = rho * cos(ang);
+    *n1 = rho * sin(ang);
+}
+
+/* One Philox block at counter (tick, id, tag<<16 | sub<<8 | blk, 0). */
+static void draw_block(const or_env* h, uint32_t tick, uint32_t id, uint32_t tag, uint32_t sub,
+                       uint32_t blk, double u[4]) {
+    uint32_t ctr[4] = {tick, id, (tag << 16) | (sub << 8) | blk, 0u};
+    uint32_t key[2] = {h->key[0], h->key[1]};
+    uint32_t r[4];
+    or_philox4x32_10(ctr, key, r);
+    for (int i = 0; i < 4; ++i) u[i] = or_uniform(r[i]);
+}
+
+static void draw_block_key(const uint32_t key_in[2], uint32_t tick, uint32_t id, uint32_t tag,
+                           uint32_t sub, uint32_t blk, double u[4]) {
+    uint32_t ctr[4] = {tick, id, (tag << 16) | (sub << 8) | blk, 0u};
+    uint32_t key[2] = {key_in[0], key_in[1]};
+    uint32_t r[4];
+    or_philox4x32_10(ctr, key, r);
+    for (int i = 0; i < 4; ++i) u[i] = or_uniform(r[i]);
+}
+
+/* Six N(0,1) draws (collision / wall perturbation): blocks 0 and 1. */
+static void draw_six_normals(const or_env* h, uint32_t tick, uint32_t id, uint32_t tag,
+                             uint32_t sub, double n[6]) {
+    double u[4], w[4], spare;
+    draw_block(h, tick, id, tag, sub, 0, u);
+    draw_block(h, tick, id, tag, sub, 1, w);
+    box_muller(u[0], u[1], &n[0], &n[1]);
+    box_muller(u[2], u[3], &n[2], &n[3]);
+    box_muller(w[0], w[1], &n[4], &n[5]);
+    (void)spare;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Small 3x3 helpers (row-major).                                             */
+/* ------------------------------------------------------------------------- */
+static double det3(const double m[9]) {
+    return m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+           m[2] * (m[3] * m[7] - m[4] * m[6]);
+}
+
+/* inverse-transpose: (M^{-1})^T = cofactor(M) / det(M) */
+static void inv_transpose3(const double m[9], double out[9]) {
+    double d = det3(m);
+    out[0] = (m[4] * m[8] - m[5] * m[7]) / d;
+    out[1] = -(m[3] * m[8] - m[5] * m[6]) / d;
+    out[2] = (m[3] * m[7] - m[4] * m[6]) / d;
+    out[3] = -(m[1] * m[8] - m[2] * m[7]) / d;
+    out[4] = (m[0] * m[8] - m[2] * m[6]) / d;
+    out[5] = -(m[0] * m[7] - m[1] * m[6]) / d;
+    out[6] = (m[1] * m[5] - m[2] * m[4]) / d;
+    out[7] = -(m[0] * m[5] - m[2] * m[3]) / d;
+    out[8] = (m[0] * m[4] - m[1] * m[3]) / d;
+}
+
+/* Orthogonal polar factor of a nonsingular M with det M > 0: the unique
+ * rotation R with M = R H, H symmetric positive definite. Computed by Newton's
+ * polar iteration X <- (X + X^{-T}) / 2 (Higham 1986), run until it stops
+ * moving in binary64. This is the "nearest rotation" that the re-
+ * orthonormalisation of the integrated rotation matrix asks for. */
+void or_polar(const double m[9], double r[9]) {
+    double x[9], it[9];
+    memcpy(x, m, sizeof x);
+    for (int iter = 0; iter < 60; ++iter) {
+        inv_transpose3(x, it);
+        double change = 0.0;
+        for (int k = 0; k < 9; ++k) {
+            double nx = 0.5 * (x[k] + it[k]);
+            double dd = fabs(nx - x[k]);
+            if (dd > change) change = dd;
+            x[k] = nx;
+        }
+        if (change < 1e-15) break;
+    }
+    memcpy(r, x, sizeof x);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Canonical binary32 pair key (S9, S11): with dx = fl32(x_j - x_i) etc.,     */
+/* key = fl32(fl32(fl32(dx*dx) + fl32(dy*dy)) + fl32(dz*dz)). No contraction. */
+/* ------------------------------------------------------------------------- */
+float or_pair_key(const float xi[3], const float xj[3]) {
+    volatile float dx = xj[0] - xi[0];
+    volatile float dy = xj[1] - xi[1];
+    volatile float dz = xj[2] - xi[2];
+    volatile float sx = dx * dx;
+    volatile float sy = dy * dy;
+    volatile float sz = dz * dz;
+    volatile float s = sx + sy;
+    volatile float k = s + sz;
+    return k;
+}
+
+/* Collision threshold fl32(fl32(l_i + l_j)^2) for binary32 arm lengths. */
+static float pair_threshold(float li, float lj) {
+    volatile float r = li + lj;
+    volatile float t = r * r;
+    return t;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Environment creation and defaults.                                         */
+/* ------------------------------------------------------------------------- */
+void or_default_config(or_config* c) {
+    memset(c, 0, sizeof *c);
+    c->n_envs = 1;
+    c->k_neighbors = 6;
+    c->substeps = 2;           /* 200 Hz physics under 100 Hz control (Sec. IV) */
+    c->dt = 0.005;
+    c->episode_steps = 1500;   /* 15 s at 100 Hz (Sec. IV) */
+    c->seed = 1;
+    c->flags = OR_F_DR | OR_F_MOTOR_NOISE | OR_F_OBS_NOISE | OR_F_COLLISIONS | OR_F_FLOOR |
+               OR_F_WALLS;
+    /* Crazyflie 2.x nominal values; the paper states none (proposed readings). */
+    c->mass = 0.028;
+    c->arm = 0.046;
+    c->ixx = 1.657e-5;
+    c->iyy = 1.666e-5;
+    c->izz = 2.926e-5;
+    c->t2w = 2.0;
+    c->kappa = 0.006;
+    c->tau_m = 0.04;
+    c->gravity = 9.81;
+    c->mu = 0.3;
+    c->alpha_nd = 0.9;
+    c->alpha_ns_frac = 0.02;
+    c->alpha_c = 0.8;
+    c->coll_sigma_v = 0.2;
+    c->coll_sigma_w = 0.5;
+    c->obs_sigma_x = 5e-3;    /* Sec. III-C */
+    c->obs_sigma_v = 1e-2;    /* Sec. III-C */
+    c->obs_sigma_w = 1.75e-4; /* Sec. III-C */
+    c->room_hx = 5.0;
+    c->room_hy = 5.0;
+    c->room_h = 10.0;
+    c->dr_lo = 0.8;
+    c->dr_hi = 1.2;
+    c->smooth_beta = 200.0;
+    c->smooth_kc = 20.0;
+    c->prox_factor = 4.0;
+    /* goal-reaching weights: position, spin, and each collision indicator */
+    c->w[OR_W_POS] = -1.0;
+    c->w[OR_W_SPIN] = -0.1;
+    c->w[OR_W_HIT_FLOOR] = -1.0;
+    c->w[OR_W_HIT_WALL] = -1.0;
+    c->w[OR_W_HIT_CEIL] = -1.0;
+    c->w[OR_W_HIT_QUAD] = -1.0;
+}
+
+or_env* or_create(const or_config* cfg, const int32_t* swarm_sizes) {
+    if (!cfg || cfg->n_envs <= 0 || cfg->substeps <= 0 || cfg->substeps > 255) return NULL;
+    or_env* h = (or_env*)calloc(1, sizeof(or_env));
+    h->cfg = *cfg;
+    int E = cfg->n_envs;
+    h->env_off = (int32_t*)calloc((size_t)E + 1, sizeof(int32_t));
+    for (int e = 0; e < E; ++e) {
+        int n = swarm_sizes ? swarm_sizes[e] : 1;
+        if (n <= 0) { free(h->env_off); free(h); return NULL; }
+        h->env_off[e + 1] = h->env_off[e] + n;
+    }
+    int D = h->env_off[E];
+    h->n_drones = D;
+    h->prm = (double*)calloc((size_t)E * OR_NPRM, sizeof(double));
+    h->goal = (double*)calloc((size_t)E * 3, sizeof(double));
+    h->st = (double*)calloc((size_t)D * OR_NST, sizeof(double));
+    h->ep_t = (int32_t*)calloc((size_t)E, sizeof(int32_t));
+    h->ev = (uint32_t*)calloc((size_t)D, sizeof(uint32_t));
+    int K = cfg->k_neighbors > 0 ? cfg->k_neighbors : 1;
+    h->knn = (int32_t*)calloc((size_t)D * K, sizeof(int32_t));
+    h->margin = (double*)calloc((size_t)D, sizeof(double));
+    h->key[0] = (uint32_t)(cfg->seed & 0xffffffffu);
+    h->key[1] = (uint32_t)(cfg->seed >> 32);
+    for (int d = 0; d < D; ++d) h->margin[d] = INFINITY;
+    return h;
+}
+
+void or_destroy(or_env* h) {
+    if (!h) return;
+    free(h->env_off); free(h->prm); free(h->goal); free(h->st); free(h->ep_t);
+    free(h->ev); free(h->knn); free(h->margin); free(h);
+}
+
+int or_n_drones(const or_env* h) { return h->n_drones; }
+
+static double hover_command(const double* prm) { return 1.0 / prm[OR_P_T2W]; }
+
+/* S0: per-environment domain randomisation and goal. Independent U(lo,hi)
+ * scale factors on m, Ixx, Iyy, Izz, t2w, tau_m and l (one draw per env, all
+ * drones of the env share them); goal uniform in the room. */
+static void reset_env_params(or_env* h, const uint32_t key[2], uint32_t tick, uint32_t tag, int e) {
+    const or_config* c = &h->cfg;
+    double u[12];
+    draw_block_key(key, tick, (uint32_t)e, tag, 0, 0, u);
+    draw_block_key(key, tick, (uint32_t)e, tag, 0, 1, u + 4);
+    draw_block_key(key, tick, (uint32_t)e, tag, 0, 2, u + 8);
+    double nominal[OR_NPRM] = {c->mass, c->ixx, c->iyy, c->izz, c->t2w, c->tau_m, c->arm};
+    double* p = h->prm + (size_t)e * OR_NPRM;
+    for (int k = 0; k < OR_NPRM; ++k) {
+        double scale = (c->flags & OR_F_DR) ? c->dr_lo + (c->dr_hi - c->dr_lo) * u[k] : 1.0;
+        p[k] = nominal[k] * scale;
+    }
+    double* g = h->goal + (size_t)e * 3;
+    g[0] = -c->room_hx + 2.0 * c->room_hx * u[7];
+    g[1] = -c->room_hy + 2.0 * c->room_hy * u[8];
+    g[2] = c->room_h * u[9];
+}
+
+/* S0: per-drone initial state. Position uniform in the room, velocity and
+ * body rates uniform in [-1,1], orientation from a uniformly random unit
+ * quaternion (Shoemake, "Uniform random rotations", Graphics Gems III, 1992),
+ * filtered rotor speed at hover, motor noise zero, previous command = hover. */
+static void reset_drone(or_env* h, const uint32_t key[2], uint32_t tick, uint32_t tag, int e, int d) {
+    const or_config* c = &h->cfg;
+    double u[12];
+    draw_block_key(key, tick, (uint32_t)d, tag, 0, 0, u);
+    draw_block_key(key, tick, (uint32_t)d, tag, 0, 1, u + 4);
+    draw_block_key(key, tick, (uint32_t)d, tag, 0, 2, u + 8);
+    double* s = h->st + (size_t)d * OR_NST;
+    const double* p = h->prm + (size_t)e * OR_NPRM;
+    s[OR_S_X + 0] = -c->room_hx + 2.0 * c->room_hx * u[0];
+    s[OR_S_X + 1] = -c->room_hy + 2.0 * c->room_hy * u[1];
+    s[OR_S_X + 2] = c->room_h * u[2];
+    s[OR_S_V + 0] = -1.0 + 2.0 * u[3];
+    s[OR_S_V + 1] = -1.0 + 2.0 * u[4];
+    s[OR_S_V + 2] = -1.0 + 2.0 * u[5];
+    double a = sqrt(1.0 - u[6]), b = sqrt(u[6]);
+    double qx = a * sin(2.0 * M_PI * u[7]);
+    double qy = a * cos(2.0 * M_PI * u[7]);
+    double qz = b * sin(2.0 * M_PI * u[8]);
+    double qw = b * cos(2.0 * M_PI * u[8]);
+    double* R = s + OR_S_R;
+    R[0] = 1.0 - 2.0 * (qy * qy + qz * qz);
+    R[1] = 2.0 * (qx * qy - qz * qw);
+    R[2] = 2.0 * (qx * qz + qy * qw);
+    R[3] = 2.0 * (qx * qy + qz * qw);
+    R[4] = 1.0 - 2.0 * (qx * qx + qz * qz);
+    R[5] = 2.0 * (qy * qz - qx * qw);
+    R[6] = 2.0 * (qx * qz - qy * qw);
+    R[7] = 2.0 * (qy * qz + qx * qw);
+    R[8] = 1.0 - 2.0 * (qx * qx + qy * qy);
+    s[OR_S_W + 0] = -1.0 + 2.0 * u[9];
+    s[OR_S_W + 1] = -1.0 + 2.0 * u[10];
+    s[OR_S_W + 2] = -1.0 + 2.0 * u[11];
+    double hov = hover_command(p);
+    for (int r = 0; r < 4; ++r) {
+        s[OR_S_UF + r] = sqrt(hov);
+        s[OR_S_EPS + r] = 0.0;
+        s[OR_S_FPREV + r] = hov;
+    }
+}
+
+static void reset_env_all(or_env* h, const uint32_t key[2], uint32_t tick, uint32_t tag_env,
+                          uint32_t tag_drone, int e) {
+    reset_env_params(h, key, tick, tag_env, e);
+    for (int d = h->env_off[e]; d < h->env_off[e + 1]; ++d) reset_drone(h, key, tick, tag_drone, e, d);
+    h->ep_t[e] = 0;
+}
+
+/* Full reset (mask == NULL): new key from seed, tick 0, every env redrawn at
+ * counter 0. Partial reset: the masked envs are redrawn from key = seed at
+ * the current tick; the handle's noise key is unchanged. */
+void or_reset(or_env* h, uint64_t seed, const uint8_t* mask) {
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    if (!mask) {
+        h->key[0] = key[0]; h->key[1] = key[1];
+        h->tick = 0;
+        for (int e = 0; e < h->cfg.n_envs; ++e) reset_env_all(h, key, 0, OR_TAG_RESET_ENV, OR_TAG_RESET_DRONE, e);
+    } else {
+        for (int e = 0; e < h->cfg.n_envs; ++e)
+            if (mask[e]) reset_env_all(h, key, h->tick, OR_TAG_RESET_ENV, OR_TAG_RESET_DRONE, e);
+    }
+    for (int d = 0; d < h->n_drones; ++d) { h->ev[d] = 0; h->margin[d] = INFINITY; }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Decision margins: every branch on a continuous quantity records how far    */
+/* that quantity was from its threshold (normalised). A binary32 run can take */
+/* the other branch only where this margin is at the level of its rounding.   */
+/* ------------------------------------------------------------------------- */
+static void note_margin(or_env* h, int d, double m) {
+    m = fabs(m);
+    if (m < h->margin[d]) h->margin[d] = m;
+}
+
+/* Same, but an exact zero is not a near-decision: it arises only from values
+ * both implementations set exactly (a drone parked at z = 0, clamped onto a
+ * wall, or at rest). */
+static void note_margin_nz(or_env* h, int d, double m) {
+    if (m != 0.0) note_margin(h, d, m);
+}
+
+/* softplus_beta(u) = log(1 + exp(beta u)) / beta, evaluated without overflow */
+static double softplus_b(double u, double beta) {
+    double z = beta * u;
+    return (fmax(z, 0.0) + log1p(exp(-fabs(z)))) / beta;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One physics substep of one drone (S1 .. S8).                               */
+/* pair_acc: smooth-contact pair acceleration (NULL when not in smooth mode). */
+/* ------------------------------------------------------------------------- */
+static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4],
+                          const double pair_acc[3], double fhat_out[4]) {
+    const or_config* c = &h->cfg;
+    const double* p = h->prm + (size_t)e * OR_NPRM;
+    double* s = h->st + (size_t)d * OR_NST;
+    const double dt = c->dt, g = c->gravity;
+    const double m = p[OR_P_M], ixx = p[OR_P_IXX], iyy = p[OR_P_IYY], izz = p[OR_P_IZZ];
+    const double t2w = p[OR_P_T2W], tau_m = p[OR_P_TAU], arm = p[OR_P_ARM];
+    const double fmax = 0.25 * m * g * t2w;                /* per-rotor max thrust */
+    const double alpha_lag = 1.0 - exp(-dt / tau_m);       /* 2% settling = tau_m ln 50 */
+    const double alpha_ns = c->alpha_ns_frac * m * g / 4.0;
+    const int smooth = (c->flags & OR_F_SMOOTH) != 0;
+
+    double* x = s + OR_S_X; double* v = s + OR_S_V; double* R = s + OR_S_R; double* w = s + OR_S_W;
+    double* uf = s + OR_S_UF; double* eps = s + OR_S_EPS;
+
+    /* S1: normalised command f^ in [0,1], rotor speed u^ = sqrt(f^), first-order lag. */
+    double f[4];
+    for (int r = 0; r < 4; ++r) {
+        double fh;
+        if (c->flags & OR_F_ACTION_SYMMETRIC) {
+            double a = a_in[r] < -1.0 ? -1.0 : (a_in[r] > 1.0 ? 1.0 : a_in[r]);
+            fh = 0.5 * (a + 1.0);
+        } else {
+            fh = a_in[r] < 0.0 ? 0.0 : (a_in[r] > 1.0 ? 1.0 : a_in[r]);
+        }
+        fhat_out[r] = fh;
+        double u = sqrt(fh);
+        uf[r] = alpha_lag * (u - uf[r]) + uf[r];
+    }
+    /* S2: AR(1) motor noise, eps <- a_nd eps + a_ns N(0,1); per-rotor thrust. */
+    if (c->flags & OR_F_MOTOR_NOISE) {
+        double u[4], n[4];
+        draw_block(h, h->tick, (uint32_t)d, OR_TAG_MOTOR, (uint32_t)sub, 0, u);
+        box_muller(u[0], u[1], &n[0], &n[1]);
+        box_muller(u[2], u[3], &n[2], &n[3]);
+        for (int r = 0; r < 4; ++r) eps[r] = c->alpha_nd * eps[r] + alpha_ns * n[r];
+    }
+    for (int r = 0; r < 4; ++r) f[r] = fmax * uf[r] * uf[r] + eps[r];
+
+    /* S3: X layout, rotor r at arm*(cos t_r, sin t_r, 0), t_r = 45,135,225,315 deg;
+     * thrust along body +z; tau_th = sum p_r x (0,0,f_r); tau_p = (0,0,kappa sum s_r f_r)
+     * with spin signs s = (-1,+1,-1,+1). */
+    double T = f[0] + f[1] + f[2] + f[3];
+    double tau[3] = {0.0, 0.0, 0.0};
+    {
+        /* cos / sin of 45, 135, 225, 315 degrees are exactly +-1/sqrt(2) */
+        const double sx[4] = {1.0, -1.0, -1.0, 1.0}, sy[4] = {1.0, 1.0, -1.0, -1.0};
+        const double s = arm * M_SQRT1_2;
+        for (int r = 0; r < 4; ++r) {
+            double px = s * sx[r], py = s * sy[r];
+            tau[0] += py * f[r];
+            tau[1] += -px * f[r];
+        }
+    }
+    {
+        const double spin[4] = {-1.0, 1.0, -1.0, 1.0};
+        for (int r = 0; r < 4; ++r) tau[2] += c->kappa * spin[r] * f[r];
+    }
+
+    /* S4: world thrust F = R (0,0,T); acceleration g + F/m. */
+    double F[3] = {R[2] * T, R[5] * T, R[8] * T};
+    double acc[3] = {F[0] / m, F[1] / m, F[2] / m - g};
+    int on_floor = 0, moving = 0;
+    if (smooth) {
+        double kc = c->smooth_kc * g; /* k_c / m, with k_c = smooth_kc * m g per metre */
+        double beta = c->smooth_beta;
+        acc[2] += kc * softplus_b(-x[2], beta);                 /* floor */
+        acc[2] -= kc * softplus_b(x[2] - c->room_h, beta);      /* ceiling */
+        acc[0] -= kc * softplus_b(x[0] - c->room_hx, beta);     /* walls */
+        acc[0] += kc * softplus_b(-c->room_hx - x[0], beta);
+        acc[1] -= kc * softplus_b(x[1] - c->room_hy, beta);
+        acc[1] += kc * softplus_b(-c->room_hy - x[1], beta);
+        if (pair_acc) { acc[0] += pair_acc[0]; acc[1] += pair_acc[1]; acc[2] += pair_acc[2]; }
+    } else if (c->flags & OR_F_FLOOR) {
+        /* Ground, "on the floor": thrust too weak to lift off -> friction arrests the
+         * horizontal motion; no vertical motion. */
+        if (x[2] <= 0.0) {
+            note_margin(h, d, (F[2] - m * g) / (m * g));
+            if (F[2] < m * g) {
+                on_floor = 1;
+                h->ev[d] |= OR_EV_ON_FLOOR;
+                double ffric = c->mu * (m * g - F[2]);
+                double fx = F[0], fy = F[1];
+                if (v[0] == 0.0 && v[1] == 0.0) {
+                    /* at rest: friction opposes the horizontal thrust, up to its size */
+                    double nf = sqrt(fx * fx + fy * fy);
+                    note_margin(h, d, (nf - ffric) / (m * g));
+                    double keep = nf > ffric ? (nf - ffric) / nf : 0.0;
+                    fx *= keep; fy *= keep;
+                } else {
+                    /* sliding: friction of size mu (m g - F_z) against the velocity */
+                    double nv = sqrt(v[0] * v[0] + v[1] * v[1]);
+                    fx -= ffric * v[0] / nv;
+                    fy -= ffric * v[1] / nv;
+                    moving = 1;
+                }
+                acc[0] = fx / m; acc[1] = fy / m; acc[2] = 0.0;
+                v[2] = 0.0;
+            }
+        }
+    }
+
+    /* S5: Euler's equation in the body frame, diagonal inertia. */
+    double Iw[3] = {ixx * w[0], iyy * w[1], izz * w[2]};
+    double gyro[3] = {w[1] * Iw[2] - w[2] * Iw[1], w[2] * Iw[0] - w[0] * Iw[2], w[0] * Iw[1] - w[1] * Iw[0]};
+    double wdot[3] = {(tau[0] - gyro[0]) / ixx, (tau[1] - gyro[1]) / iyy, (tau[2] - gyro[2]) / izz};
+
+    /* S6: semi-implicit Euler: velocities first, then positions with the new
+     * velocities; dR/dt = R [w]x with body-frame w; polar re-orthonormalisation. */
+    double vold[2] = {v[0], v[1]};
+    for (int k = 0; k < 3; ++k) v[k] += acc[k] * dt;
+    if (on_floor && moving) {
+        /* friction never reverses the sliding direction within one substep */
+        double dot = v[0] * vold[0] + v[1] * vold[1];
+        note_margin(h, d, dot / (vold[0] * vold[0] + vold[1] * vold[1]));
+        if (dot < 0.0) { v[0] = 0.0; v[1] = 0.0; }
+    }
+    for (int k = 0; k < 3; ++k) x[k] += v[k] * dt;
+    for (int k = 0; k < 3; ++k) w[k] += wdot[k] * dt;
+    double M[9];
+    for (int i = 0; i < 3; ++i) {
+        /* row_i(R [w]x) = row_i(R) x w */
+        double r0 = R[3 * i + 0], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
+        M[3 * i + 0] = r0 + dt * (r1 * w[2] - r2 * w[1]);
+        M[3 * i + 1] = r1 + dt * (r2 * w[0] - r0 * w[2]);
+        M[3 * i + 2] = r2 + dt * (r0 * w[1] - r1 * w[0]);
+    }
+    or_polar(M, R);
+
+    if (smooth) {
+        if (x[2] < 0.0) h->ev[d] |= OR_EV_HIT_FLOOR;
+        if (x[2] > c->room_h) h->ev[d] |= OR_EV_HIT_CEIL;
+        if (fabs(x[0]) > c->room_hx || fabs(x[1]) > c->room_hy) h->ev[d] |= OR_EV_HIT_WALL;
+        return;
+    }
+
+    /* S7: ground hit: velocities and momenta to zero, body z-axis set upright
+     * keeping the heading (yaw) of the first body axis. */
+    if (c->flags & OR_F_FLOOR) {
+        note_margin_nz(h, d, x[2]);
+        if (x[2] <= 0.0) note_margin_nz(h, d, v[2]);
+        if (x[2] <= 0.0 && v[2] < 0.0) {
+            h->ev[d] |= OR_EV_HIT_FLOOR;
+            x[2] = 0.0;
+            for (int k = 0; k < 3; ++k) { v[k] = 0.0; w[k] = 0.0; }
+            double cs, sn, hyp = sqrt(R[0] * R[0] + R[3] * R[3]);
+            if (hyp >= 1e-6) { cs = R[0] / hyp; sn = R[3] / hyp; }
+            else { double h2 = sqrt(R[1] * R[1] + R[4] * R[4]); cs = R[4] / h2; sn = -R[1] / h2; }
+            double Rz[9] = {cs, -sn, 0.0, sn, cs, 0.0, 0.0, 0.0, 1.0};
+            memcpy(R, Rz, sizeof Rz);
+        }
+    }
+
+    /* S8: walls x = +-hx, y = +-hy and ceiling z = H. The quad-quad rule with a
+     * static partner: the normal velocity component is removed (not
+     * reflected), then v <- alpha_c (v + eps_v), w <- w + eps_w; the position is
+     * clamped back onto the boundary. */
+    if (c->flags & OR_F_WALLS) {
+        int hit_wall = 0, hit_ceil = 0;
+        const double lim[2] = {c->room_hx, c->room_hy};
+        for (int k = 0; k < 2; ++k) {
+            note_margin_nz(h, d, x[k] - lim[k]);
+            note_margin_nz(h, d, x[k] + lim[k]);
+            if (x[k] > lim[k] && v[k] > 0.0) { v[k] = 0.0; x[k] = lim[k]; hit_wall = 1; }
+            else if (x[k] < -lim[k] && v[k] < 0.0) { v[k] = 0.0; x[k] = -lim[k]; hit_wall = 1; }
+        }
+        note_margin_nz(h, d, x[2] - c->room_h);
+        if (x[2] > c->room_h && v[2] > 0.0) { v[2] = 0.0; x[2] = c->room_h; hit_ceil = 1; }
+        if (hit_wall || hit_ceil) {
+            double n[6];
+            draw_six_normals(h, h->tick, (uint32_t)d, OR_TAG_WALL, (uint32_t)sub, n);
+            for (int k = 0; k < 3; ++k) {
+                v[k] = c->alpha_c * (v[k] + c->coll_sigma_v * n[k]);
+                w[k] = w[k] + c->coll_sigma_w * n[3 + k];
+            }
+            if (hit_wall) h->ev[d] |= OR_EV_HIT_WALL;
+            if (hit_ceil) h->ev[d] |= OR_EV_HIT_CEIL;
+        }
+    }
+}
+
+/* Smooth-contact pair acceleration on drone i: sum over j != i of
+ * k_c/m * softplus_beta(2l - d_ij) * n_ij, n_ij = (x_i - x_j)/d_ij. */
+static void smooth_pair_acc(const or_env* h, int e, int i, double out[3]) {
+    const or_config* c = &h->cfg;
+    const double* p = h->prm + (size_t)e * OR_NPRM;
+    const double* xi = h->st + (size_t)i * OR_NST + OR_S_X;
+    double kc = c->smooth_kc * c->gravity;
+    out[0] = out[1] = out[2] = 0.0;
+    for (int j = h->env_off[e]; j < h->env_off[e + 1]; ++j) {
+        if (j == i) continue;
+        const double* xj = h->st + (size_t)j * OR_NST + OR_S_X;
+        double dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
+        double dist = sqrt(dx * dx + dy * dy + dz * dz);
+        if (dist == 0.0) continue; /* direction undefined: no push */
+        double mag = kc * softplus_b(2.0 * p[OR_P_ARM] - dist, c->smooth_beta);
+        out[0] += mag * dx / dist; out[1] += mag * dy / dist; out[2] += mag * dz / dist;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* One control step of one environment (S1 .. S13).                           */
+/* ------------------------------------------------------------------------- */
+typedef struct { uint32_t key; int32_t j; } knn_item;
+
+static int knn_cmp(const void* a, const void* b) {
+    const knn_item* x = (const knn_item*)a; const knn_item* y = (const knn_item*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->j < y->j ? -1 : (x->j > y->j ? 1 : 0);
+}
+
+static uint32_t f32_bits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+static void step_env(or_env* h, int e, const double* actions, double* obs, double* rew, uint8_t* done,
+                     double* loss) {
+    const or_config* c = &h->cfg;
+    const int d0 = h->env_off[e], d1 = h->env_off[e + 1], N = d1 - d0;
+    const int K = c->k_neighbors;
+    const int keff = K < N - 1 ? K : N - 1;
+    const int od = 18 + 6 * K;
+    const double* p = h->prm + (size_t)e * OR_NPRM;
+    const double* goal = h->goal + (size_t)e * 3;
+    const int smooth = (c->flags & OR_F_SMOOTH) != 0;
+
+    double* fhat = (double*)malloc(sizeof(double) * 4 * (size_t)N);
+    double* pacc = smooth ? (double*)malloc(sizeof(double) * 3 * (size_t)N) : NULL;
+    for (int d = d0; d < d1; ++d) h->ev[d] = 0;
+
+    /* substeps S1 .. S8 (drones of one env are coupled only through the smooth pair force) */
+    for (int sub = 0; sub < c->substeps; ++sub) {
+        if (smooth) for (int d = d0; d < d1; ++d) smooth_pair_acc(h, e, d, pacc + 3 * (d - d0));
+        for (int d = d0; d < d1; ++d)
+            substep_drone(h, e, d, sub, actions + 4 * (size_t)d, smooth ? pacc + 3 * (d - d0) : NULL,
+                          fhat + 4 * (d - d0));
+    }
+
+    /* binary32 positions and arm length for the canonical keys */
+    float* xf = (float*)malloc(sizeof(float) * 3 * (size_t)N);
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < 3; ++k) xf[3 * i + k] = (float)h->st[(size_t)(d0 + i) * OR_NST + OR_S_X + k];
+    float lf = (float)p[OR_P_ARM];
+    float thr = pair_threshold(lf, lf);
+
+    /* S9: collision set: pair (i, j) collides iff key_ij < fl32((l_i + l_j)^2) */
+    uint8_t* coll = (uint8_t*)calloc((size_t)N * N, 1);
+    if ((c->flags & OR_F_COLLISIONS) && N >= 2) {
+        for (int i = 0; i < N; ++i)
+            for (int j = i + 1; j < N; ++j) {
+                float k = or_pair_key(xf + 3 * i, xf + 3 * j);
+                note_margin(h, d0 + i, ((double)k - (double)thr) / (double)thr);
+                note_margin(h, d0 + j, ((double)k - (double)thr) / (double)thr);
+                if (k < thr) {
+                    coll[i * N + j] = coll[j * N + i] = 1;
+                    h->ev[d0 + i] |= OR_EV_HIT_QUAD; h->ev[d0 + j] |= OR_EV_HIT_QUAD;
+                }
+            }
+    }
+    /* S10: Jacobi response from pre-collision velocities: for every colliding and
+     * approaching pair, v_i gets ((v_j - v_i).n) n with n = (x_i - x_j)/|x_i - x_j|;
+     * then once per responding drone v <- alpha_c (v + sum + eps_v), w <- w + eps_w. */
+    if (!smooth && (c->flags & OR_F_COLLISIONS) && N >= 2) {
+        double* dv = (double*)calloc((size_t)3 * N, sizeof(double));
+        uint8_t* resp = (uint8_t*)calloc((size_t)N, 1);
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                if (i == j || !coll[i * N + j]) continue;
+                const double* xi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_X;
+                const double* xj = h->st + (size_t)(d0 + j) * OR_NST + OR_S_X;
+                const double* vi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_V;
+                const double* vj = h->st + (size_t)(d0 + j) * OR_NST + OR_S_V;
+                double dx[3] = {xi[0] - xj[0], xi[1] - xj[1], xi[2] - xj[2]};
+                double dvv[3] = {vi[0] - vj[0], vi[1] - vj[1], vi[2] - vj[2]};
+                double app = dvv[0] * dx[0] + dvv[1] * dx[1] + dvv[2] * dx[2];
+                double scl = sqrt((dvv[0] * dvv[0] + dvv[1] * dvv[1] + dvv[2] * dvv[2]) *
+                                  (dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]));
+                if (scl > 0.0) note_margin(h, d0 + i, app / scl);
+                if (!(app < 0.0)) continue;
+                double dist = sqrt(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
+                double n[3] = {0.0, 0.0, 1.0};
+                if (dist > 0.0) { n[0] = dx[0] / dist; n[1] = dx[1] / dist; n[2] = dx[2] / dist; }
+                double vn = (vj[0] - vi[0]) * n[0] + (vj[1] - vi[1]) * n[1] + (vj[2] - vi[2]) * n[2];
+                for (int k = 0; k < 3; ++k) dv[3 * i + k] += vn * n[k];
+                resp[i] = 1;
+            }
+        for (int i = 0; i < N; ++i) {
+            if (!resp[i]) continue;
+            double nn[6];
+            draw_six_normals(h, h->tick, (uint32_t)(d0 + i), OR_TAG_COLL, 0, nn);
+            double* vi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_V;
+            double* wi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_W;
+            for (int k = 0; k < 3; ++k) {
+                vi[k] = c->alpha_c * (vi[k] + dv[3 * i + k] + c->coll_sigma_v * nn[k]);
+                wi[k] = wi[k] + c->coll_sigma_w * nn[3 + k];
+            }
+        }
+        free(dv); free(resp);
+    }
+
+    /* S11: K nearest by (key, local index) ascending over j != i. */
+    int32_t* nbr = (int32_t*)malloc(sizeof(int32_t) * (size_t)(keff > 0 ? keff : 1) * N);
+    if (keff > 0) {
+        knn_item* items = (knn_item*)malloc(sizeof(knn_item) * (size_t)N);
+        for (int i = 0; i < N; ++i) {
+            int m = 0;
+            for (int j = 0; j < N; ++j)
+                if (j != i) { items[m].key = f32_bits(or_pair_key(xf + 3 * i, xf + 3 * j)); items[m].j = j; ++m; }
+            qsort(items, (size_t)m, sizeof(knn_item), knn_cmp);
+            for (int k = 0; k < keff; ++k) nbr[i * keff + k] = items[k].j;
+            /* near-ties at the ranks that matter (including the K-th vs the next) */
+            for (int k = 0; k < keff && k + 1 < m; ++k) {
+                float ka, kb; uint32_t ua = items[k].key, ub = items[k + 1].key;
+                memcpy(&ka, &ua, 4); memcpy(&kb, &ub, 4);
+                double den = (double)kb > 0.0 ? (double)kb : 1.0;
+                note_margin(h, d0 + i, ((double)kb - (double)ka) / den);
+            }
+        }
+        free(items);
+    }
+    if (c->flags & OR_F_RECORD_KNN) {
+        for (int i = 0; i < N; ++i)
+            for (int k = 0; k < K; ++k) h->knn[(size_t)(d0 + i) * K + k] = k < keff ? nbr[i * keff + k] : -1;
+    }
+
+    /* S12 / S13: observation, reward */
+    for (int i = 0; i < N; ++i) {
+        int d = d0 + i;
+        double* s = h->st + (size_t)d * OR_NST;
+        const double *x = s + OR_S_X, *v = s + OR_S_V, *R = s + OR_S_R, *w = s + OR_S_W;
+        double* fprev = s + OR_S_FPREV;
+        const double* fh = fhat + 4 * i;
+        if (obs) {
+            double* o = obs + (size_t)d * od;
+            double ex[3] = {0, 0, 0}, evv[3] = {0, 0, 0}, ew[3] = {0, 0, 0};
+            if (c->flags & OR_F_OBS_NOISE) {
+                /* Sec. III-C noise read as U(-s, s) for position and velocity and
+                 * N(0, s^2) for body rates. */
+                double u0[4], u1[4], u2[4], n0, n1, n2, n3;
+                draw_block(h, h->tick, (uint32_t)d, OR_TAG_OBS, 0, 0, u0);
+                draw_block(h, h->tick, (uint32_t)d, OR_TAG_OBS, 0, 1, u1);
+                draw_block(h, h->tick, (uint32_t)d, OR_TAG_OBS, 0, 2, u2);
+                ex[0] = (2.0 * u0[0] - 1.0) * c->obs_sigma_x;
+                ex[1] = (2.0 * u0[1] - 1.0) * c->obs_sigma_x;
+                ex[2] = (2.0 * u0[2] - 1.0) * c->obs_sigma_x;
+                evv[0] = (2.0 * u0[3] - 1.0) * c->obs_sigma_v;
+                evv[1] = (2.0 * u1[0] - 1.0) * c->obs_sigma_v;
+                evv[2] = (2.0 * u1[1] - 1.0) * c->obs_sigma_v;
+                box_muller(u1[2], u1[3], &n0, &n1);
+                box_muller(u2[0], u2[1], &n2, &n3);
+                ew[0] = n0 * c->obs_sigma_w; ew[1] = n1 * c->obs_sigma_w; ew[2] = n2 * c->obs_sigma_w;
+            }
+            for (int k = 0; k < 3; ++k) {
+                o[k] = x[k] - goal[k] + ex[k];
+                o[3 + k] = v[k] + evv[k];
+                o[15 + k] = w[k] + ew[k];
+            }
+            for (int k = 0; k < 9; ++k) o[6 + k] = R[k];
+            for (int k = 0; k < K; ++k) {
+                double* on = o + 18 + 6 * k;
+                if (k < keff) {
+                    const double* sj = h->st + (size_t)(d0 + nbr[i * keff + k]) * OR_NST;
+                    for (int q = 0; q < 3; ++q) { on[q] = sj[OR_S_X + q] - x[q]; on[3 + q] = sj[OR_S_V + q] - v[q]; }
+                } else {
+                    for (int q = 0; q < 6; ++q) on[q] = 0.0;
+                }
+            }
+        }
+        if (rew) {
+            const double* W = c->w;
+            double dxg[3] = {x[0] - goal[0], x[1] - goal[1], x[2] - goal[2]};
+            double dfa[4] = {fh[0] - fprev[0], fh[1] - fprev[1], fh[2] - fprev[2], fh[3] - fprev[3]};
+            double r = 0.0;
+            r += W[OR_W_POS] * sqrt(dxg[0] * dxg[0] + dxg[1] * dxg[1] + dxg[2] * dxg[2]);
+            r += W[OR_W_VEL] * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            r += W[OR_W_ORI] * R[8];
+            r += W[OR_W_SPIN] * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+            r += W[OR_W_ACT] * sqrt(fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
+            r += W[OR_W_DACT] * sqrt(dfa[0] * dfa[0] + dfa[1] * dfa[1] + dfa[2] * dfa[2] + dfa[3] * dfa[3]);
+            r += W[OR_W_ROT] * (R[0] + R[4] + R[8] - 1.0) / 2.0;
+            r += W[OR_W_YAW] * R[0];
+            uint32_t ev = h->ev[d];
+            r += W[OR_W_HIT_FLOOR] * ((ev & OR_EV_HIT_FLOOR) ? 1.0 : 0.0);
+            r += W[OR_W_ON_FLOOR] * ((ev & OR_EV_ON_FLOOR) ? 1.0 : 0.0);
+            r += W[OR_W_HIT_WALL] * ((ev & OR_EV_HIT_WALL) ? 1.0 : 0.0);
+            r += W[OR_W_HIT_CEIL] * ((ev & OR_EV_HIT_CEIL) ? 1.0 : 0.0);
+            r += W[OR_W_HIT_QUAD] * ((ev & OR_EV_HIT_QUAD) ? 1.0 : 0.0);
+            double alpha_prox = c->prox_factor * p[OR_P_ARM];
+            double near = 0.0;
+            for (int k = 0; k < keff; ++k) {
+                const double* xj = h->st + (size_t)(d0 + nbr[i * keff + k]) * OR_NST + OR_S_X;
+                double dd = sqrt((xj[0] - x[0]) * (xj[0] - x[0]) + (xj[1] - x[1]) * (xj[1] - x[1]) +
+                                 (xj[2] - x[2]) * (xj[2] - x[2]));
+                near += fmax(1.0 - dd / alpha_prox, 0.0);
+            }
+            r += W[OR_W_NEAR] * near;
+            rew[d] = r;
+        }
+        if (loss) {
+            double l = 0.0;
+            for (int k = 0; k < 3; ++k) l += (x[k] - goal[k]) * (x[k] - goal[k]);
+            for (int r = 0; r < 4; ++r) l += 1e-3 * fh[r] * fh[r];
+            loss[d] += l;
+        }
+        for (int r = 0; r < 4; ++r) fprev[r] = fh[r];
+    }
+
+    h->ep_t[e] += 1;
+    int is_done = h->ep_t[e] >= c->episode_steps;
+    if (done) done[e] = (uint8_t)is_done;
+    if (is_done && (c->flags & OR_F_AUTO_RESET)) reset_env_all(h, h->key, h->tick, OR_TAG_AUTO_ENV, OR_TAG_AUTO_DRONE, e);
+
+    free(nbr); free(coll); free(xf); free(fhat); free(pacc);
+}
+
+typedef struct {
+    or_env* h; int e0, e1; const double* actions; double* obs; double* rew; uint8_t* done; double* loss;
+} step_job;
+
+static void* step_worker(void* arg) {
+    step_job* j = (step_job*)arg;
+    for (int e = j->e0; e < j->e1; ++e) step_env(j->h, e, j->actions, j->obs, j->rew, j->done, j->loss);
+    return NULL;
+}
+
+/* One control step of every environment. Environments are independent, so
+ * they may be split over n_threads host threads by contiguous env ranges. */
+void or_step(or_env* h, const double* actions, double* obs, double* rew, uint8_t* done, double* loss,
+             int n_threads) {
+    int E = h->cfg.n_envs;
+    if (n_threads <= 1 || E < 2) {
+        step_job j = {h, 0, E, actions, obs, rew, done, loss};
+        step_worker(&j);
+    } else {
+        if (n_threads > E) n_threads = E;
+        pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)n_threads);
+        step_job* jobs = (step_job*)malloc(sizeof(step_job) * (size_t)n_threads);
+        for (int t = 0; t < n_threads; ++t) {
+            jobs[t].h = h; jobs[t].e0 = (int)((long)E * t / n_threads); jobs[t].e1 = (int)((long)E * (t + 1) / n_threads);
+            jobs[t].actions = actions; jobs[t].obs = obs; jobs[t].rew = rew; jobs[t].done = done; jobs[t].loss = loss;
+            pthread_create(&th[t], NULL, step_worker, &jobs[t]);
+        }
+        for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+        free(th); free(jobs);
+    }
+    h->tick += 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* State access (binary64 copies, caller-owned buffers; NULL skips a part).   */
+/* ------------------------------------------------------------------------- */
+void or_get_state(const or_env* h, double* st, double* prm, double* goal, int32_t* ep_t, uint32_t* tick) {
+    if (st) memcpy(st, h->st, sizeof(double) * (size_t)h->n_drones * OR_NST);
+    if (prm) memcpy(prm, h->prm, sizeof(double) * (size_t)h->cfg.n_envs * OR_NPRM);
+    if (goal) memcpy(goal, h->goal, sizeof(double) * (size_t)h->cfg.n_envs * 3);
+    if (ep_t) memcpy(ep_t, h->ep_t, sizeof(int32_t) * (size_t)h->cfg.n_envs);
+    if (tick) *tick = h->tick;
+}
+
+void or_set_state(or_env* h, const double* st, const double* prm, const double* goal, const int32_t* ep_t,
+                  const uint32_t* tick) {
+    if (st) memcpy(h->st, st, sizeof(double) * (size_t)h->n_drones * OR_NST);
+    if (prm) memcpy(h->prm, prm, sizeof(double) * (size_t)h->cfg.n_envs * OR_NPRM);
+    if (goal) memcpy(h->goal, goal, sizeof(double) * (size_t)h->cfg.n_envs * 3);
+    if (ep_t) memcpy(h->ep_t, ep_t, sizeof(int32_t) * (size_t)h->cfg.n_envs);
+    if (tick) h->tick = *tick;
+}
+
+void or_get_events(const or_env* h, uint32_t* ev, int32_t* knn, double* margin) {
+    if (ev) memcpy(ev, h->ev, sizeof(uint32_t) * (size_t)h->n_drones);
+    if (knn && h->cfg.k_neighbors > 0)
+        memcpy(knn, h->knn, sizeof(int32_t) * (size_t)h->n_drones * h->cfg.k_neighbors);
+    if (margin) memcpy(margin, h->margin, sizeof(double) * (size_t)h->n_drones);
+}
+
+void or_clear_margin(or_env* h) {
+    for (int d = 0; d < h->n_drones; ++d) h->margin[d] = INFINITY;
+}
+
+/* Standalone canonical KNN / collision set on given binary32 positions
+ * (S9 + S11 only): used to check index decisions on inputs the dynamics
+ * leave untouched. pos: [D][3]; arm: [E]; knn: [D][K] (-1 padded). */
+void or_pairs_f32(const float* pos, const float* arm, const int32_t* env_off, int n_envs, int K,
+                  int32_t* knn, uint8_t* hit) {
+    for (int e = 0; e < n_envs; ++e) {
+        int d0 = env_off[e], N = env_off[e + 1] - d0;
+        int keff = K < N - 1 ? K : N - 1;
+        float thr = pair_threshold(arm[e], arm[e]);
+        knn_item* items = (knn_item*)malloc(sizeof(knn_item) * (size_t)(N > 0 ? N : 1));
+        for (int i = 0; i < N; ++i) {
+            int m = 0; hit[d0 + i] = 0;
+            for (int j = 0; j < N; ++j) {
+                if (j == i) continue;
+                float k = or_pair_key(pos + 3 * (d0 + i), pos + 3 * (d0 + j));
+                if (k < thr) hit[d0 + i] = 1;
+                items[m].key = f32_bits(k); items[m].j = j; ++m;
+            }
+            qsort(items, (size_t)m, sizeof(knn_item), knn_cmp);
+            for (int k = 0; k < K; ++k) knn[(size_t)(d0 + i) * K + k] = k < keff ? items[k].j : -1;
+        }
+        free(items);
+    }
+}
