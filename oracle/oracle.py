@@ -45,6 +45,7 @@ class OrConfig(C.Structure):
         ("room_hx", C.c_double), ("room_hy", C.c_double), ("room_h", C.c_double),
         ("dr_lo", C.c_double), ("dr_hi", C.c_double),
         ("smooth_beta", C.c_double), ("smooth_kc", C.c_double), ("prox_factor", C.c_double),
+        ("omega_max", C.c_double),
         ("w", C.c_double * 14),
     ]
 

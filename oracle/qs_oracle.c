@@ -221,6 +221,7 @@ void or_default_config(or_config* c) {
     c->smooth_beta = 200.0;
     c->smooth_kc = 20.0;
     c->prox_factor = 4.0;
+    c->omega_max = 40.0;
     /* goal-reaching weights: position, spin, and each collision indicator */
     c->w[OR_W_POS] = -1.0;
     c->w[OR_W_SPIN] = -0.1;
@@ -365,11 +366,14 @@ static void note_margin(or_env* h, int d, double m) {
     if (m < h->margin[d]) h->margin[d] = m;
 }
 
-/* Same, but an exact zero is not a near-decision: it arises only from values
- * both implementations set exactly (a drone parked at z = 0, clamped onto a
- * wall, or at rest). */
-static void note_margin_nz(or_env* h, int d, double m) {
-    if (m != 0.0) note_margin(h, d, m);
+/* Margin of the decision a < b (or a <= b): |a - b| / max(|a|, |b|), the
+ * relative cancellation that rounding of a and b would have to overcome. An
+ * exact tie of exact values (a drone parked at z = 0, clamped onto a wall,
+ * at rest) is not a near-decision: both implementations set those exactly. */
+static void note_cmp(or_env* h, int d, double a, double b) {
+    double den = fmax(fabs(a), fabs(b));
+    if (den == 0.0) return;
+    note_margin(h, d, (a - b) / den);
 }
 
 /* softplus_beta(u) = log(1 + exp(beta u)) / beta, evaluated without overflow */
@@ -460,7 +464,7 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
         /* Ground, "on the floor": thrust too weak to lift off -> friction arrests the
          * horizontal motion; no vertical motion. */
         if (x[2] <= 0.0) {
-            note_margin(h, d, (F[2] - m * g) / (m * g));
+            note_cmp(h, d, F[2], m * g);
             if (F[2] < m * g) {
                 on_floor = 1;
                 h->ev[d] |= OR_EV_ON_FLOOR;
@@ -469,7 +473,7 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
                 if (v[0] == 0.0 && v[1] == 0.0) {
                     /* at rest: friction opposes the horizontal thrust, up to its size */
                     double nf = sqrt(fx * fx + fy * fy);
-                    note_margin(h, d, (nf - ffric) / (m * g));
+                    note_cmp(h, d, nf, ffric);
                     double keep = nf > ffric ? (nf - ffric) / nf : 0.0;
                     fx *= keep; fy *= keep;
                 } else {
@@ -497,11 +501,18 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
     if (on_floor && moving) {
         /* friction never reverses the sliding direction within one substep */
         double dot = v[0] * vold[0] + v[1] * vold[1];
-        note_margin(h, d, dot / (vold[0] * vold[0] + vold[1] * vold[1]));
+        note_cmp(h, d, vold[0] * vold[0] + vold[1] * vold[1], vold[0] * vold[0] + vold[1] * vold[1] - dot);
         if (dot < 0.0) { v[0] = 0.0; v[1] = 0.0; }
     }
     for (int k = 0; k < 3; ++k) x[k] += v[k] * dt;
-    for (int k = 0; k < 3; ++k) w[k] += wdot[k] * dt;
+    /* body rates are bounded by |w_k| <= omega_max (the paper is silent; the
+     * Crazyflie 2.x gyroscope saturates near 2000 deg/s); without a bound the
+     * explicit gyroscopic term diverges under random per-rotor commands */
+    for (int k = 0; k < 3; ++k) {
+        w[k] += wdot[k] * dt;
+        if (w[k] > c->omega_max) w[k] = c->omega_max;
+        if (w[k] < -c->omega_max) w[k] = -c->omega_max;
+    }
     double M[9];
     for (int i = 0; i < 3; ++i) {
         /* row_i(R [w]x) = row_i(R) x w */
@@ -522,8 +533,8 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
     /* S7: ground hit: velocities and momenta to zero, body z-axis set upright
      * keeping the heading (yaw) of the first body axis. */
     if (c->flags & OR_F_FLOOR) {
-        note_margin_nz(h, d, x[2]);
-        if (x[2] <= 0.0) note_margin_nz(h, d, v[2]);
+        note_cmp(h, d, x[2] - v[2] * dt, -v[2] * dt);          /* z+ = z + v dt vs 0 */
+        if (x[2] <= 0.0) note_cmp(h, d, v[2] - acc[2] * dt, -acc[2] * dt); /* v+ = v + a dt vs 0 */
         if (x[2] <= 0.0 && v[2] < 0.0) {
             h->ev[d] |= OR_EV_HIT_FLOOR;
             x[2] = 0.0;
@@ -544,12 +555,12 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
         int hit_wall = 0, hit_ceil = 0;
         const double lim[2] = {c->room_hx, c->room_hy};
         for (int k = 0; k < 2; ++k) {
-            note_margin_nz(h, d, x[k] - lim[k]);
-            note_margin_nz(h, d, x[k] + lim[k]);
+            note_cmp(h, d, x[k], lim[k]);
+            note_cmp(h, d, x[k], -lim[k]);
             if (x[k] > lim[k] && v[k] > 0.0) { v[k] = 0.0; x[k] = lim[k]; hit_wall = 1; }
             else if (x[k] < -lim[k] && v[k] < 0.0) { v[k] = 0.0; x[k] = -lim[k]; hit_wall = 1; }
         }
-        note_margin_nz(h, d, x[2] - c->room_h);
+        note_cmp(h, d, x[2], c->room_h);
         if (x[2] > c->room_h && v[2] > 0.0) { v[2] = 0.0; x[2] = c->room_h; hit_ceil = 1; }
         if (hit_wall || hit_ceil) {
             double n[6];

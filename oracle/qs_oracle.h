@@ -75,6 +75,7 @@ typedef struct {
     double dr_lo, dr_hi;
     double smooth_beta, smooth_kc;
     double prox_factor;
+    double omega_max;
     double w[OR_NW];
 } or_config;
 

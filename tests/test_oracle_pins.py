@@ -599,3 +599,16 @@ def test_smooth_pair_forces_cancel():
     expect = st[:, 3:6].sum(0) + np.array([0, 0, -3 * c.gravity * 10 * c.dt])
     assert np.abs(s[:, 3:6].sum(0) - expect).max() < 1e-11
     assert np.abs(s[:, 3:6] - st[:, 3:6]).max() > 0.1  # the penalty acted
+
+
+def test_body_rate_bound():
+    """Body rates saturate at omega_max per axis (reading; the paper is silent)."""
+    c, o = make(flags=0)
+    st = base_state(uf=0.0, fprev=0.0, x=(0, 0, 900.0))
+    st[0, 15:18] = (0.0, 0.0, 60.0)
+    o.set_state(st, nominal(c)[None], np.zeros((1, 3)), np.zeros(1, np.int32), 0)
+    o.step(np.zeros((1, 4)))
+    s = o.get_state()["state"][0]
+    assert s[17] == c.omega_max == 40.0 and s[15] == 0.0 and s[16] == 0.0
+    R = s[6:15].reshape(3, 3)
+    assert abs(math.atan2(R[1, 0], R[0, 0]) - 2 * math.atan(c.dt * 40.0)) < 1e-12
