@@ -1,0 +1,218 @@
+/*
+ * qs.h -- C ABI of libquadswarm_gpu.so, a GB300 (sm_103a) implementation of the
+ * QuadSwarm forward-dynamics step (Huang et al., arXiv 2306.09537).
+ *
+ * The library simulates E independent environments ("envs"); env e holds N_e
+ * quadrotors ("drones", 1 <= N_e <= 64), D = sum N_e drones in total. Drones
+ * are numbered env by env: env e owns global drones [off_e, off_e + N_e).
+ * One control step (100 Hz; two 200 Hz physics substeps by default, paper
+ * Sec. IV) advances every drone by:
+ *   motor lag and motor noise on the per-rotor command (Sec. III-A "Motor Lag",
+ *   "Motor Noise"), thrust and torque from the rotor layout and rigid-body
+ *   integration of position, velocity, rotation matrix and body rates
+ *   (Sec. III-A dynamics block), floor, wall and ceiling contacts (Sec. III-B
+ *   "Quadrotor to Ground", "Wall or Ceiling"), quadrotor-quadrotor collisions
+ *   (Sec. III-B "Quadrotor to Quadrotor"), the K-nearest-neighbour observation
+ *   with sensor noise (Sec. III-C) and the reward (Sec. III-E), under
+ *   per-environment domain randomisation (Sec. I item (i)).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named *_dev are CUDA device pointers on the device that was
+ *    current when the handle was created; *_host are host pointers. The
+ *    caller owns every buffer it passes; the handle owns its internal state.
+ *  - All work is enqueued on the handle's stream and the call returns without
+ *    waiting, unless stated otherwise. Buffers passed to a call must stay
+ *    valid until the stream reaches that work.
+ *  - Argument errors (NULL handle or buffer, bad sizes, misaligned buffers)
+ *    return QS_ERR_ARG at once and enqueue nothing. CUDA launch errors return
+ *    QS_ERR_CUDA. Errors detected on the device (a non-finite state) set a
+ *    status word that qs_sync() reports. qs_last_error() gives a message.
+ *  - Floating point is binary32 throughout the device path.
+ *
+ * Layouts (row-major, contiguous):
+ *  actions  [D][4]            per-rotor normalised commands (16-byte aligned)
+ *  obs      [D][obs_dim]      obs_dim = 18 + 6 K  (8-byte aligned):
+ *                             x - goal (3), v (3), R row-major (9), w (3),
+ *                             then for k < K: x_j - x_i (3), v_j - v_i (3) of the
+ *                             k-th nearest neighbour j, zeros past min(K, N_e - 1)
+ *  reward   [D]
+ *  done     [E]  uint8        1 when the env's episode reached episode_steps
+ *  state    [D][30]           x(3) v(3) R(9) w(3) uf(4) eps(4) fprev(4)
+ *  params   [E][7]            m, Ixx, Iyy, Izz, t2w, tau_m, arm
+ *  goals    [E][3]
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QS_ABI_VERSION 1
+#define QS_MAX_SWARM 64     /* drones per env */
+#define QS_MAX_K 8          /* neighbours in the observation */
+#define QS_STATE_DIM 30
+#define QS_PARAM_DIM 7
+
+typedef enum {
+    QS_OK = 0,
+    QS_ERR_ARG = 1,             /* invalid argument; nothing was enqueued */
+    QS_ERR_CUDA = 2,            /* a CUDA call failed (message in qs_last_error) */
+    QS_ERR_OOM = 3,             /* device allocation failed */
+    QS_ERR_STATE_NONFINITE = 4, /* the device found a non-finite drone state */
+    QS_ERR_TIMEOUT = 5,         /* reserved: a bounded device wait gave up */
+    QS_ERR_UNSUPPORTED = 6      /* e.g. a swarm larger than QS_MAX_SWARM */
+} qs_status;
+
+/* qs_config.flags */
+#define QS_F_DR               (1u << 0) /* per-env randomisation of m, I, t2w, tau_m, arm */
+#define QS_F_MOTOR_NOISE      (1u << 1) /* AR(1) motor noise (Sec. III-A) */
+#define QS_F_OBS_NOISE        (1u << 2) /* sensor noise on the observation (Sec. III-C) */
+#define QS_F_COLLISIONS       (1u << 3) /* quad-quad collisions (Sec. III-B) */
+#define QS_F_FLOOR            (1u << 4) /* floor hit and friction (Sec. III-B) */
+#define QS_F_WALLS            (1u << 5) /* walls and ceiling (Sec. III-B) */
+#define QS_F_AUTO_RESET       (1u << 6) /* an env whose episode ends is redrawn in place */
+#define QS_F_SMOOTH           (1u << 7) /* softplus penalty contacts (differentiable form) */
+#define QS_F_ACTION_SYMMETRIC (1u << 8) /* f^ = (clip(a,-1,1)+1)/2 instead of clip(a,0,1) */
+#define QS_F_RECORD_KNN       (1u << 9) /* keep neighbour indices for qs_get_events */
+
+/* qs_get_events bits (per drone, last control step) */
+#define QS_EV_HIT_FLOOR (1u << 0)
+#define QS_EV_ON_FLOOR  (1u << 1)
+#define QS_EV_HIT_WALL  (1u << 2)
+#define QS_EV_HIT_CEIL  (1u << 3)
+#define QS_EV_HIT_QUAD  (1u << 4)
+
+/* reward weights, in qs_params.w (Sec. III-E; every weight carries its sign) */
+enum {
+    QS_W_POS, QS_W_VEL, QS_W_ORI, QS_W_SPIN, QS_W_ACT, QS_W_DACT, QS_W_ROT, QS_W_YAW,
+    QS_W_HIT_FLOOR, QS_W_ON_FLOOR, QS_W_HIT_WALL, QS_W_HIT_CEIL, QS_W_HIT_QUAD, QS_W_NEAR,
+    QS_NW
+};
+
+/* Physical and model constants. The paper states few of them; qs_config_default
+ * fills the readings: Crazyflie 2.x mass 0.028 kg, arm 0.046 m, inertia
+ * diag(1.657e-5, 1.666e-5, 2.926e-5) kg m^2, thrust-to-weight 2, yaw torque
+ * coefficient 0.006 m, motor time constant 0.04 s, g 9.81, floor friction 0.3,
+ * motor noise decay 0.9 and scale 2% of hover thrust per rotor, collision
+ * decay 0.8 with perturbations N(0, 0.2^2) m/s and N(0, 0.5^2) rad/s, sensor
+ * noise 5e-3 m, 1e-2 m/s, 1.75e-4 rad/s (Sec. III-C), room 10 x 10 x 10 m,
+ * randomisation range [0.8, 1.2], softplus beta 200 1/m and stiffness 20 m g
+ * per metre, proximity radius 4 arm lengths, body-rate bound 40 rad/s. */
+typedef struct {
+    float mass, arm, ixx, iyy, izz, t2w, kappa, tau_m, gravity, mu;
+    float alpha_nd, alpha_ns_frac, alpha_c, coll_sigma_v, coll_sigma_w;
+    float obs_sigma_x, obs_sigma_v, obs_sigma_w;
+    float room_hx, room_hy, room_h;
+    float dr_lo, dr_hi;
+    float smooth_beta, smooth_kc, prox_factor, omega_max;
+    float w[QS_NW];
+} qs_params;
+
+typedef struct {
+    uint32_t size;              /* sizeof(qs_config); checked by qs_create */
+    int32_t n_envs;             /* E >= 1 */
+    const int32_t* swarm_sizes; /* host [E] drones per env, or NULL: n_per_env each */
+    int32_t n_per_env;          /* used when swarm_sizes is NULL */
+    int32_t k_neighbors;        /* K in [0, QS_MAX_K] */
+    int32_t substeps;           /* physics substeps per control step (2) */
+    float dt;                   /* physics substep (0.005 s) */
+    int32_t episode_steps;      /* control steps per episode (1500 = 15 s) */
+    uint64_t seed;              /* Philox key of the first reset */
+    uint32_t flags;             /* QS_F_* */
+    qs_params params;
+} qs_config;
+
+typedef struct qs_env qs_env;
+
+/* Fills *cfg with the defaults above: 1 env x 1 drone, K = 6, 2 x 0.005 s
+ * substeps, 1500-step episodes, seed 1, flags DR|MOTOR_NOISE|OBS_NOISE|
+ * COLLISIONS|FLOOR|WALLS and the goal-reaching reward (pos -1, spin -0.1,
+ * -1 per collision indicator). */
+void qs_config_default(qs_config* cfg);
+
+/* Environment definition of Sec. III (Gym-style multi-agent env, Table I).
+ * Allocates the device state for cfg's envs on the current device and binds
+ * the handle to cuda_stream (a cudaStream_t; NULL = the legacy default
+ * stream). The state is drawn as by qs_reset(h, cfg->seed, NULL, NULL).
+ * Errors: QS_ERR_ARG (bad config), QS_ERR_UNSUPPORTED (N_e > 64 or K > 8),
+ * QS_ERR_OOM, QS_ERR_CUDA. On error *out is NULL. */
+qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out);
+
+/* Frees the handle and its device memory after draining its stream. */
+qs_status qs_destroy(qs_env* h);
+
+/* D, E and obs_dim of the handle (any pointer may be NULL). Host-side only. */
+qs_status qs_get_dims(const qs_env* h, int32_t* n_drones, int32_t* n_envs, int32_t* obs_dim);
+
+/* Episode reset with domain randomisation (Sec. I (i), III-A). Draws per-env
+ * parameters (each of m, Ixx, Iyy, Izz, t2w, tau_m, arm scaled by U(lo, hi)
+ * when QS_F_DR), a goal uniform in the room, and per drone: position uniform
+ * in the room, velocity and body rates uniform in [-1,1], a uniformly random
+ * rotation, hovering motors. env_mask_dev == NULL: full reset, the Philox key
+ * becomes `seed` and every env restarts at counter 0. Otherwise only envs with
+ * env_mask_dev[e] != 0 are redrawn, from key `seed` at their current counter.
+ * obs_dev (nullable) receives the observation of the new state. */
+qs_status qs_reset(qs_env* h, uint64_t seed, const uint8_t* env_mask_dev, float* obs_dev);
+
+/* One control step of every env (Sec. III-A .. III-E): actions_dev [D][4] in,
+ * obs_dev [D][obs_dim], reward_dev [D], done_dev [E] out. obs_dev, reward_dev
+ * and done_dev may be NULL (not written). A non-finite drone state found on
+ * the device is reported by the next qs_sync() or qs_step_host(). */
+qs_status qs_step(qs_env* h, const float* actions_dev, float* obs_dev, float* reward_dev, uint8_t* done_dev);
+
+/* qs_step for callers whose buffers live in host memory: copies actions_host
+ * [D][4] to the device, steps, copies obs/reward/done back into the host
+ * buffers (each nullable) and waits for the stream. Pinned host memory makes
+ * the copies asynchronous DMA. */
+qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, float* reward_host,
+                       uint8_t* done_host);
+
+/* T control steps in one persistent launch (T >= 1): actions_dev [T][D][4],
+ * obs_dev [T][D][obs_dim], reward_dev [T][D], done_dev [T][E] (outputs
+ * nullable). Each drone's state stays in registers across the T steps; the
+ * results equal T calls of qs_step. */
+qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_dev, float* reward_dev,
+                     uint8_t* done_dev);
+
+/* Copies the handle's state into caller buffers (each nullable): state_dev
+ * [D][30], params_dev [E][7], goals_dev [E][3], ep_step_dev [E] control steps
+ * into the episode, tick_dev [E] Philox step counter of each env. */
+qs_status qs_get_state(qs_env* h, float* state_dev, float* params_dev, float* goals_dev, int32_t* ep_step_dev,
+                       uint32_t* tick_dev);
+
+/* Overwrites the handle's state from caller buffers (each nullable; layouts as
+ * qs_get_state). Derived per-env constants are recomputed from params_dev. */
+qs_status qs_set_state(qs_env* h, const float* state_dev, const float* params_dev, const float* goals_dev,
+                       const int32_t* ep_step_dev, const uint32_t* tick_dev);
+
+/* Event bits of the last step per drone (events_dev [D], QS_EV_*) and, when
+ * the handle was created with QS_F_RECORD_KNN, the neighbour list knn_dev
+ * [D][K] as local indices within the env, -1 past min(K, N_e - 1) (Sec.
+ * III-C: ordered by distance, ties to the lower index). Either nullable. */
+qs_status qs_get_events(qs_env* h, uint32_t* events_dev, int16_t* knn_dev);
+
+/* Waits for the handle's stream and reports a device-detected error
+ * (QS_ERR_STATE_NONFINITE stays reported until the next full qs_reset). */
+qs_status qs_sync(qs_env* h);
+
+/* Launch shape of one swarm-width class (the envs whose swarm size rounds up
+ * to the power of two `width`, 1..64): `block` threads per CTA, a multiple of
+ * 32 and of `width`, at most 256. Used by the autotuner; results do not
+ * depend on it. QS_ERR_ARG for an invalid shape or a class the handle lacks. */
+qs_status qs_set_block(qs_env* h, int32_t width, int32_t block);
+
+/* Reads back the launch shape of a class (block 0 when the handle has none). */
+qs_status qs_get_block(const qs_env* h, int32_t width, int32_t* block);
+
+/* Last error message of the handle (or of the last failed qs_create when h
+ * is NULL). Never NULL; valid until the next call on the handle. */
+const char* qs_last_error(const qs_env* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QS_H */

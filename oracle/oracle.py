@@ -94,6 +94,7 @@ def lib():
                                        P(C.c_int32), P(C.c_uint32)]
             L.or_get_events.argtypes = [C.c_void_p, P(C.c_uint32), P(C.c_int32), P(C.c_double)]
             L.or_clear_margin.argtypes = [C.c_void_p]
+            L.or_observe.argtypes = [C.c_void_p, P(C.c_double)]
             L.or_pairs_f32.argtypes = [P(C.c_float), P(C.c_float), P(C.c_int32), C.c_int, C.c_int,
                                        P(C.c_int32), P(C.c_uint8)]
             _lib = L
@@ -213,19 +214,24 @@ class Oracle:
         prm = np.zeros((self.E, NPRM))
         goal = np.zeros((self.E, 3))
         ep = np.zeros(self.E, dtype=np.int32)
-        tick = C.c_uint32(0)
+        tick = np.zeros(self.E, dtype=np.uint32)
         lib().or_get_state(self.h, _ptr(st, C.c_double), _ptr(prm, C.c_double),
-                           _ptr(goal, C.c_double), _ptr(ep, C.c_int32), C.byref(tick))
-        return {"state": st, "params": prm, "goals": goal, "ep_step": ep, "tick": tick.value}
+                           _ptr(goal, C.c_double), _ptr(ep, C.c_int32), _ptr(tick, C.c_uint32))
+        return {"state": st, "params": prm, "goals": goal, "ep_step": ep, "tick": tick}
 
     def set_state(self, state=None, params=None, goals=None, ep_step=None, tick=None):
         st = None if state is None else np.ascontiguousarray(state, dtype=np.float64).reshape(self.D, NST)
         prm = None if params is None else np.ascontiguousarray(params, dtype=np.float64).reshape(self.E, NPRM)
         goal = None if goals is None else np.ascontiguousarray(goals, dtype=np.float64).reshape(self.E, 3)
-        ep = None if ep_step is None else np.ascontiguousarray(ep_step, dtype=np.int32)
-        tk = None if tick is None else C.c_uint32(int(tick))
+        ep = None if ep_step is None else np.ascontiguousarray(np.broadcast_to(ep_step, (self.E,)), dtype=np.int32)
+        tk = None if tick is None else np.ascontiguousarray(np.broadcast_to(tick, (self.E,)), dtype=np.uint32)
         lib().or_set_state(self.h, _ptr(st, C.c_double), _ptr(prm, C.c_double), _ptr(goal, C.c_double),
-                           _ptr(ep, C.c_int32), C.byref(tk) if tk is not None else None)
+                           _ptr(ep, C.c_int32), _ptr(tk, C.c_uint32))
+
+    def observe(self):
+        obs = np.zeros((self.D, self.obs_dim))
+        lib().or_observe(self.h, _ptr(obs, C.c_double))
+        return obs
 
     def get_events(self):
         ev = np.zeros(self.D, dtype=np.uint32)

@@ -248,6 +248,7 @@ or_env* or_create(const or_config* cfg, const int32_t* swarm_sizes) {
     h->goal = (double*)calloc((size_t)E * 3, sizeof(double));
     h->st = (double*)calloc((size_t)D * OR_NST, sizeof(double));
     h->ep_t = (int32_t*)calloc((size_t)E, sizeof(int32_t));
+    h->tick = (uint32_t*)calloc((size_t)E, sizeof(uint32_t));
     h->ev = (uint32_t*)calloc((size_t)D, sizeof(uint32_t));
     int K = cfg->k_neighbors > 0 ? cfg->k_neighbors : 1;
     h->knn = (int32_t*)calloc((size_t)D * K, sizeof(int32_t));
@@ -260,7 +261,7 @@ or_env* or_create(const or_config* cfg, const int32_t* swarm_sizes) {
 
 void or_destroy(or_env* h) {
     if (!h) return;
-    free(h->env_off); free(h->prm); free(h->goal); free(h->st); free(h->ep_t);
+    free(h->env_off); free(h->prm); free(h->goal); free(h->st); free(h->ep_t); free(h->tick);
     free(h->ev); free(h->knn); free(h->margin); free(h);
 }
 
@@ -340,18 +341,20 @@ static void reset_env_all(or_env* h, const uint32_t key[2], uint32_t tick, uint3
     h->ep_t[e] = 0;
 }
 
-/* Full reset (mask == NULL): new key from seed, tick 0, every env redrawn at
- * counter 0. Partial reset: the masked envs are redrawn from key = seed at
- * the current tick; the handle's noise key is unchanged. */
+/* Full reset (mask == NULL): new key from seed, every env's counter back to
+ * 0 and every env redrawn at counter 0. Partial reset: the masked envs are
+ * redrawn from key = seed at their current counter; the noise key is kept. */
 void or_reset(or_env* h, uint64_t seed, const uint8_t* mask) {
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     if (!mask) {
         h->key[0] = key[0]; h->key[1] = key[1];
-        h->tick = 0;
-        for (int e = 0; e < h->cfg.n_envs; ++e) reset_env_all(h, key, 0, OR_TAG_RESET_ENV, OR_TAG_RESET_DRONE, e);
+        for (int e = 0; e < h->cfg.n_envs; ++e) {
+            h->tick[e] = 0;
+            reset_env_all(h, key, 0, OR_TAG_RESET_ENV, OR_TAG_RESET_DRONE, e);
+        }
     } else {
         for (int e = 0; e < h->cfg.n_envs; ++e)
-            if (mask[e]) reset_env_all(h, key, h->tick, OR_TAG_RESET_ENV, OR_TAG_RESET_DRONE, e);
+            if (mask[e]) reset_env_all(h, key, h->tick[e], OR_TAG_RESET_ENV, OR_TAG_RESET_DRONE, e);
     }
     for (int d = 0; d < h->n_drones; ++d) { h->ev[d] = 0; h->margin[d] = INFINITY; }
 }
@@ -419,7 +422,7 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
     /* S2: AR(1) motor noise, eps <- a_nd eps + a_ns N(0,1); per-rotor thrust. */
     if (c->flags & OR_F_MOTOR_NOISE) {
         double u[4], n[4];
-        draw_block(h, h->tick, (uint32_t)d, OR_TAG_MOTOR, (uint32_t)sub, 0, u);
+        draw_block(h, h->tick[e], (uint32_t)d, OR_TAG_MOTOR, (uint32_t)sub, 0, u);
         box_muller(u[0], u[1], &n[0], &n[1]);
         box_muller(u[2], u[3], &n[2], &n[3]);
         for (int r = 0; r < 4; ++r) eps[r] = c->alpha_nd * eps[r] + alpha_ns * n[r];
@@ -564,7 +567,7 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
         if (x[2] > c->room_h && v[2] > 0.0) { v[2] = 0.0; x[2] = c->room_h; hit_ceil = 1; }
         if (hit_wall || hit_ceil) {
             double n[6];
-            draw_six_normals(h, h->tick, (uint32_t)d, OR_TAG_WALL, (uint32_t)sub, n);
+            draw_six_normals(h, h->tick[e], (uint32_t)d, OR_TAG_WALL, (uint32_t)sub, n);
             for (int k = 0; k < 3; ++k) {
                 v[k] = c->alpha_c * (v[k] + c->coll_sigma_v * n[k]);
                 w[k] = w[k] + c->coll_sigma_w * n[3 + k];
@@ -606,6 +609,70 @@ static int knn_cmp(const void* a, const void* b) {
 }
 
 static uint32_t f32_bits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+/* S11: for each drone i of the env (local index), the keff nearest by
+ * (binary32 key, local index) ascending over j != i; records near-ties. */
+static void knn_env(or_env* h, int d0, int N, int keff, const float* xf, int32_t* nbr) {
+    if (keff <= 0) return;
+    knn_item* items = (knn_item*)malloc(sizeof(knn_item) * (size_t)N);
+    for (int i = 0; i < N; ++i) {
+        int m = 0;
+        for (int j = 0; j < N; ++j)
+            if (j != i) { items[m].key = f32_bits(or_pair_key(xf + 3 * i, xf + 3 * j)); items[m].j = j; ++m; }
+        qsort(items, (size_t)m, sizeof(knn_item), knn_cmp);
+        for (int k = 0; k < keff; ++k) nbr[i * keff + k] = items[k].j;
+        /* near-ties at the ranks that matter (including the K-th vs the next) */
+        for (int k = 0; k < keff && k + 1 < m; ++k) {
+            float ka, kb; uint32_t ua = items[k].key, ub = items[k + 1].key;
+            memcpy(&ka, &ua, 4); memcpy(&kb, &ub, 4);
+            note_cmp(h, d0 + i, (double)kb, (double)ka);
+        }
+    }
+    free(items);
+}
+
+/* S12: observation row of local drone i of env e: [x - g, v, R, w, then per
+ * neighbour x_j - x_i, v_j - v_i; zeros past keff]. Sensor noise (Sec. III-C)
+ * read as U(-s, s) on x and v and N(0, s^2) on w, from the OBS stream with
+ * substream `sub` (0: control step, 1: observation of a freshly reset env). */
+static void obs_row(or_env* h, int e, int i, const int32_t* nbr, int keff, uint32_t sub, double* o) {
+    const or_config* c = &h->cfg;
+    const int d0 = h->env_off[e], d = d0 + i, K = c->k_neighbors;
+    const double* goal = h->goal + (size_t)e * 3;
+    const double* s = h->st + (size_t)d * OR_NST;
+    const double *x = s + OR_S_X, *v = s + OR_S_V, *R = s + OR_S_R, *w = s + OR_S_W;
+    double ex[3] = {0, 0, 0}, evv[3] = {0, 0, 0}, ew[3] = {0, 0, 0};
+    if (c->flags & OR_F_OBS_NOISE) {
+        double u0[4], u1[4], u2[4], n0, n1, n2, n3;
+        draw_block(h, h->tick[e], (uint32_t)d, OR_TAG_OBS, sub, 0, u0);
+        draw_block(h, h->tick[e], (uint32_t)d, OR_TAG_OBS, sub, 1, u1);
+        draw_block(h, h->tick[e], (uint32_t)d, OR_TAG_OBS, sub, 2, u2);
+        ex[0] = (2.0 * u0[0] - 1.0) * c->obs_sigma_x;
+        ex[1] = (2.0 * u0[1] - 1.0) * c->obs_sigma_x;
+        ex[2] = (2.0 * u0[2] - 1.0) * c->obs_sigma_x;
+        evv[0] = (2.0 * u0[3] - 1.0) * c->obs_sigma_v;
+        evv[1] = (2.0 * u1[0] - 1.0) * c->obs_sigma_v;
+        evv[2] = (2.0 * u1[1] - 1.0) * c->obs_sigma_v;
+        box_muller(u1[2], u1[3], &n0, &n1);
+        box_muller(u2[0], u2[1], &n2, &n3);
+        ew[0] = n0 * c->obs_sigma_w; ew[1] = n1 * c->obs_sigma_w; ew[2] = n2 * c->obs_sigma_w;
+    }
+    for (int k = 0; k < 3; ++k) {
+        o[k] = x[k] - goal[k] + ex[k];
+        o[3 + k] = v[k] + evv[k];
+        o[15 + k] = w[k] + ew[k];
+    }
+    for (int k = 0; k < 9; ++k) o[6 + k] = R[k];
+    for (int k = 0; k < K; ++k) {
+        double* on = o + 18 + 6 * k;
+        if (k < keff) {
+            const double* sj = h->st + (size_t)(d0 + nbr[i * keff + k]) * OR_NST;
+            for (int q = 0; q < 3; ++q) { on[q] = sj[OR_S_X + q] - x[q]; on[3 + q] = sj[OR_S_V + q] - v[q]; }
+        } else {
+            for (int q = 0; q < 6; ++q) on[q] = 0.0;
+        }
+    }
+}
 
 static void step_env(or_env* h, int e, const double* actions, double* obs, double* rew, uint8_t* done,
                      double* loss) {
@@ -681,7 +748,7 @@ static void step_env(or_env* h, int e, const double* actions, double* obs, doubl
         for (int i = 0; i < N; ++i) {
             if (!resp[i]) continue;
             double nn[6];
-            draw_six_normals(h, h->tick, (uint32_t)(d0 + i), OR_TAG_COLL, 0, nn);
+            draw_six_normals(h, h->tick[e], (uint32_t)(d0 + i), OR_TAG_COLL, 0, nn);
             double* vi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_V;
             double* wi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_W;
             for (int k = 0; k < 3; ++k) {
@@ -694,24 +761,7 @@ static void step_env(or_env* h, int e, const double* actions, double* obs, doubl
 
     /* S11: K nearest by (key, local index) ascending over j != i. */
     int32_t* nbr = (int32_t*)malloc(sizeof(int32_t) * (size_t)(keff > 0 ? keff : 1) * N);
-    if (keff > 0) {
-        knn_item* items = (knn_item*)malloc(sizeof(knn_item) * (size_t)N);
-        for (int i = 0; i < N; ++i) {
-            int m = 0;
-            for (int j = 0; j < N; ++j)
-                if (j != i) { items[m].key = f32_bits(or_pair_key(xf + 3 * i, xf + 3 * j)); items[m].j = j; ++m; }
-            qsort(items, (size_t)m, sizeof(knn_item), knn_cmp);
-            for (int k = 0; k < keff; ++k) nbr[i * keff + k] = items[k].j;
-            /* near-ties at the ranks that matter (including the K-th vs the next) */
-            for (int k = 0; k < keff && k + 1 < m; ++k) {
-                float ka, kb; uint32_t ua = items[k].key, ub = items[k + 1].key;
-                memcpy(&ka, &ua, 4); memcpy(&kb, &ub, 4);
-                double den = (double)kb > 0.0 ? (double)kb : 1.0;
-                note_margin(h, d0 + i, ((double)kb - (double)ka) / den);
-            }
-        }
-        free(items);
-    }
+    knn_env(h, d0, N, keff, xf, nbr);
     if (c->flags & OR_F_RECORD_KNN) {
         for (int i = 0; i < N; ++i)
             for (int k = 0; k < K; ++k) h->knn[(size_t)(d0 + i) * K + k] = k < keff ? nbr[i * keff + k] : -1;
@@ -724,42 +774,7 @@ static void step_env(or_env* h, int e, const double* actions, double* obs, doubl
         const double *x = s + OR_S_X, *v = s + OR_S_V, *R = s + OR_S_R, *w = s + OR_S_W;
         double* fprev = s + OR_S_FPREV;
         const double* fh = fhat + 4 * i;
-        if (obs) {
-            double* o = obs + (size_t)d * od;
-            double ex[3] = {0, 0, 0}, evv[3] = {0, 0, 0}, ew[3] = {0, 0, 0};
-            if (c->flags & OR_F_OBS_NOISE) {
-                /* Sec. III-C noise read as U(-s, s) for position and velocity and
-                 * N(0, s^2) for body rates. */
-                double u0[4], u1[4], u2[4], n0, n1, n2, n3;
-                draw_block(h, h->tick, (uint32_t)d, OR_TAG_OBS, 0, 0, u0);
-                draw_block(h, h->tick, (uint32_t)d, OR_TAG_OBS, 0, 1, u1);
-                draw_block(h, h->tick, (uint32_t)d, OR_TAG_OBS, 0, 2, u2);
-                ex[0] = (2.0 * u0[0] - 1.0) * c->obs_sigma_x;
-                ex[1] = (2.0 * u0[1] - 1.0) * c->obs_sigma_x;
-                ex[2] = (2.0 * u0[2] - 1.0) * c->obs_sigma_x;
-                evv[0] = (2.0 * u0[3] - 1.0) * c->obs_sigma_v;
-                evv[1] = (2.0 * u1[0] - 1.0) * c->obs_sigma_v;
-                evv[2] = (2.0 * u1[1] - 1.0) * c->obs_sigma_v;
-                box_muller(u1[2], u1[3], &n0, &n1);
-                box_muller(u2[0], u2[1], &n2, &n3);
-                ew[0] = n0 * c->obs_sigma_w; ew[1] = n1 * c->obs_sigma_w; ew[2] = n2 * c->obs_sigma_w;
-            }
-            for (int k = 0; k < 3; ++k) {
-                o[k] = x[k] - goal[k] + ex[k];
-                o[3 + k] = v[k] + evv[k];
-                o[15 + k] = w[k] + ew[k];
-            }
-            for (int k = 0; k < 9; ++k) o[6 + k] = R[k];
-            for (int k = 0; k < K; ++k) {
-                double* on = o + 18 + 6 * k;
-                if (k < keff) {
-                    const double* sj = h->st + (size_t)(d0 + nbr[i * keff + k]) * OR_NST;
-                    for (int q = 0; q < 3; ++q) { on[q] = sj[OR_S_X + q] - x[q]; on[3 + q] = sj[OR_S_V + q] - v[q]; }
-                } else {
-                    for (int q = 0; q < 6; ++q) on[q] = 0.0;
-                }
-            }
-        }
+        if (obs) obs_row(h, e, i, nbr, keff, 0, obs + (size_t)d * od);
         if (rew) {
             const double* W = c->w;
             double dxg[3] = {x[0] - goal[0], x[1] - goal[1], x[2] - goal[2]};
@@ -802,7 +817,8 @@ static void step_env(or_env* h, int e, const double* actions, double* obs, doubl
     h->ep_t[e] += 1;
     int is_done = h->ep_t[e] >= c->episode_steps;
     if (done) done[e] = (uint8_t)is_done;
-    if (is_done && (c->flags & OR_F_AUTO_RESET)) reset_env_all(h, h->key, h->tick, OR_TAG_AUTO_ENV, OR_TAG_AUTO_DRONE, e);
+    if (is_done && (c->flags & OR_F_AUTO_RESET)) reset_env_all(h, h->key, h->tick[e], OR_TAG_AUTO_ENV, OR_TAG_AUTO_DRONE, e);
+    h->tick[e] += 1;
 
     free(nbr); free(coll); free(xf); free(fhat); free(pacc);
 }
@@ -837,18 +853,35 @@ void or_step(or_env* h, const double* actions, double* obs, double* rew, uint8_t
         for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
         free(th); free(jobs);
     }
-    h->tick += 1;
+}
+
+
+/* Observation of the current state of every env (S11 + S12, no dynamics),
+ * with sensor noise from substream 1 of each env's current counter. */
+void or_observe(or_env* h, double* obs) {
+    const int K = h->cfg.k_neighbors, od = 18 + 6 * K;
+    for (int e = 0; e < h->cfg.n_envs; ++e) {
+        int d0 = h->env_off[e], N = h->env_off[e + 1] - d0;
+        int keff = K < N - 1 ? K : N - 1;
+        float* xf = (float*)malloc(sizeof(float) * 3 * (size_t)N);
+        int32_t* nbr = (int32_t*)malloc(sizeof(int32_t) * (size_t)(keff > 0 ? keff : 1) * N);
+        for (int i = 0; i < N; ++i)
+            for (int k = 0; k < 3; ++k) xf[3 * i + k] = (float)h->st[(size_t)(d0 + i) * OR_NST + OR_S_X + k];
+        knn_env(h, d0, N, keff, xf, nbr);
+        for (int i = 0; i < N; ++i) obs_row(h, e, i, nbr, keff, 1, obs + (size_t)(d0 + i) * od);
+        free(xf); free(nbr);
+    }
 }
 
 /* ------------------------------------------------------------------------- */
 /* State access (binary64 copies, caller-owned buffers; NULL skips a part).   */
 /* ------------------------------------------------------------------------- */
 void or_get_state(const or_env* h, double* st, double* prm, double* goal, int32_t* ep_t, uint32_t* tick) {
+    if (tick) memcpy(tick, h->tick, sizeof(uint32_t) * (size_t)h->cfg.n_envs);
     if (st) memcpy(st, h->st, sizeof(double) * (size_t)h->n_drones * OR_NST);
     if (prm) memcpy(prm, h->prm, sizeof(double) * (size_t)h->cfg.n_envs * OR_NPRM);
     if (goal) memcpy(goal, h->goal, sizeof(double) * (size_t)h->cfg.n_envs * 3);
     if (ep_t) memcpy(ep_t, h->ep_t, sizeof(int32_t) * (size_t)h->cfg.n_envs);
-    if (tick) *tick = h->tick;
 }
 
 void or_set_state(or_env* h, const double* st, const double* prm, const double* goal, const int32_t* ep_t,
@@ -857,7 +890,7 @@ void or_set_state(or_env* h, const double* st, const double* prm, const double* 
     if (prm) memcpy(h->prm, prm, sizeof(double) * (size_t)h->cfg.n_envs * OR_NPRM);
     if (goal) memcpy(h->goal, goal, sizeof(double) * (size_t)h->cfg.n_envs * 3);
     if (ep_t) memcpy(h->ep_t, ep_t, sizeof(int32_t) * (size_t)h->cfg.n_envs);
-    if (tick) h->tick = *tick;
+    if (tick) memcpy(h->tick, tick, sizeof(uint32_t) * (size_t)h->cfg.n_envs);
 }
 
 void or_get_events(const or_env* h, uint32_t* ev, int32_t* knn, double* margin) {

@@ -90,8 +90,8 @@ typedef struct {
     uint32_t* ev;      /* [D] event bits of the last step */
     int32_t* knn;      /* [D][K] neighbour local indices of the last step (-1 padded) */
     double* margin;    /* [D] smallest normalised distance of any decision to its threshold */
+    uint32_t* tick;    /* [E] control steps since the last full reset (Philox counter word 0) */
     uint32_t key[2];
-    uint32_t tick;     /* control steps since the last full reset (Philox counter word 0) */
 } or_env;
 
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -105,6 +105,7 @@ int or_n_drones(const or_env* h);
 void or_reset(or_env* h, uint64_t seed, const uint8_t* mask);
 void or_step(or_env* h, const double* actions, double* obs, double* rew, uint8_t* done, double* loss,
              int n_threads);
+void or_observe(or_env* h, double* obs);
 void or_get_state(const or_env* h, double* st, double* prm, double* goal, int32_t* ep_t, uint32_t* tick);
 void or_set_state(or_env* h, const double* st, const double* prm, const double* goal, const int32_t* ep_t,
                   const uint32_t* tick);

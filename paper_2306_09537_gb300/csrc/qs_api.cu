@@ -1,0 +1,495 @@
+// qs_api.cu -- the C ABI of libquadswarm_gpu.so (declared in include/qs.h):
+// argument validation, device memory of a handle, launch plans per swarm
+// width class, and the host-buffer step.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qs.h"
+#include "qs_internal.h"
+
+using namespace qsk;
+
+static thread_local std::string g_create_error;
+
+struct qs_env {
+    qs_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int D = 0, E = 0, K = 0, obs_dim = 0;
+    Consts c{};
+    Dev dv{};
+    std::vector<int32_t> env_off_h;
+    std::vector<ClassPlan> plan;
+    std::vector<int> class_first_slot;  // first slot of each class in perm
+    std::vector<int> class_slots;       // slots per class
+    Tile* d_tiles = nullptr;
+    int* d_perm = nullptr;
+    void* arena = nullptr;
+    // device staging of qs_step_host (one allocation, made on first use)
+    char* stage = nullptr;
+    size_t st_obs = 0, st_rew = 0, st_done = 0;
+    std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+qs_status fail(qs_env* h, qs_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+qs_status cuda_fail(qs_env* h, cudaError_t e, const char* where) {
+    return fail(h, QS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int width_class(int n) {
+    int w = 1;
+    while (w < n) w <<= 1;
+    return w;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+void build_consts(qs_env* h) {
+    const qs_config& f = h->cfg;
+    const qs_params& p = f.params;
+    Consts& c = h->c;
+    c.dt = f.dt;
+    c.g = p.gravity;
+    c.kappa = p.kappa;
+    c.mu = p.mu;
+    c.alpha_nd = p.alpha_nd;
+    c.alpha_c = p.alpha_c;
+    c.sig_cv = p.coll_sigma_v;
+    c.sig_cw = p.coll_sigma_w;
+    c.obs_sx = p.obs_sigma_x;
+    c.obs_sv = p.obs_sigma_v;
+    c.obs_sw = p.obs_sigma_w;
+    c.room_hx = p.room_hx;
+    c.room_hy = p.room_hy;
+    c.room_h = p.room_h;
+    c.beta = p.smooth_beta;
+    c.kc = p.smooth_kc;
+    c.omega_max = p.omega_max;
+    c.ans_frac = p.alpha_ns_frac;
+    c.prox_factor = p.prox_factor;
+    c.dr_lo = p.dr_lo;
+    c.dr_hi = p.dr_hi;
+    const float nom[QS_PARAM_DIM] = {p.mass, p.ixx, p.iyy, p.izz, p.t2w, p.tau_m, p.arm};
+    for (int k = 0; k < QS_PARAM_DIM; ++k) c.nominal[k] = nom[k];
+    for (int k = 0; k < QS_NW; ++k) c.w[k] = p.w[k];
+    c.flags = f.flags;
+    c.substeps = f.substeps;
+    c.K = f.k_neighbors;
+    c.episode_steps = f.episode_steps;
+    c.obs_dim = 18 + 6 * f.k_neighbors;
+    c.key0 = (uint32_t)(f.seed & 0xffffffffu);
+    c.key1 = (uint32_t)(f.seed >> 32);
+}
+
+// Tiles of one class: `slots` consecutive slots starting at `first`, each CTA
+// takes block / W of them.
+void build_tiles(qs_env* h, std::vector<Tile>& tiles) {
+    tiles.clear();
+    for (size_t ci = 0; ci < h->plan.size(); ++ci) {
+        ClassPlan& cp = h->plan[ci];
+        const int per = cp.block / cp.W;
+        cp.tile_off = (int)tiles.size();
+        cp.n_tiles = 0;
+        for (int s = 0; s < h->class_slots[ci]; s += per) {
+            tiles.push_back(Tile{h->class_first_slot[ci] + s, std::min(per, h->class_slots[ci] - s)});
+            ++cp.n_tiles;
+        }
+    }
+}
+
+// Default launch shape: enough CTAs to cover 2 x 152 SMs when the class has
+// the threads for it, 32..256 threads per CTA.
+int default_block(int W, int slots) {
+    const int threads = slots * W;
+    int b = 256;
+    while (b > 32 && b > W && threads / b < 2 * 152) b >>= 1;
+    return std::max(b, std::max(W, 32));
+}
+
+qs_status upload_tiles(qs_env* h) {
+    std::vector<Tile> tiles;
+    build_tiles(h, tiles);
+    if (h->d_tiles) cudaFree(h->d_tiles);
+    h->d_tiles = nullptr;
+    cudaError_t e = cudaMalloc(&h->d_tiles, sizeof(Tile) * std::max<size_t>(tiles.size(), 1));
+    if (e != cudaSuccess) return fail(h, QS_ERR_OOM, "tile table allocation failed");
+    e = cudaMemcpy(h->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "tile table upload");
+    return QS_OK;
+}
+
+qs_status do_step(qs_env* h, const float* act, float* obs, float* rew, uint8_t* done) {
+    StepIO io{act, obs, rew, done};
+    for (const ClassPlan& cp : h->plan) {
+        cudaError_t e = launch_step(h->c, h->dv, cp, h->d_tiles, h->d_perm, io, 0, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+    }
+    return QS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qs_config_default(qs_config* cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->size = sizeof(qs_config);
+    cfg->n_envs = 1;
+    cfg->swarm_sizes = nullptr;
+    cfg->n_per_env = 1;
+    cfg->k_neighbors = 6;
+    cfg->substeps = 2;
+    cfg->dt = 0.005f;
+    cfg->episode_steps = 1500;
+    cfg->seed = 1;
+    cfg->flags = QS_F_DR | QS_F_MOTOR_NOISE | QS_F_OBS_NOISE | QS_F_COLLISIONS | QS_F_FLOOR | QS_F_WALLS;
+    qs_params& p = cfg->params;
+    p.mass = 0.028f;
+    p.arm = 0.046f;
+    p.ixx = 1.657e-5f;
+    p.iyy = 1.666e-5f;
+    p.izz = 2.926e-5f;
+    p.t2w = 2.0f;
+    p.kappa = 0.006f;
+    p.tau_m = 0.04f;
+    p.gravity = 9.81f;
+    p.mu = 0.3f;
+    p.alpha_nd = 0.9f;
+    p.alpha_ns_frac = 0.02f;
+    p.alpha_c = 0.8f;
+    p.coll_sigma_v = 0.2f;
+    p.coll_sigma_w = 0.5f;
+    p.obs_sigma_x = 5e-3f;
+    p.obs_sigma_v = 1e-2f;
+    p.obs_sigma_w = 1.75e-4f;
+    p.room_hx = 5.0f;
+    p.room_hy = 5.0f;
+    p.room_h = 10.0f;
+    p.dr_lo = 0.8f;
+    p.dr_hi = 1.2f;
+    p.smooth_beta = 200.0f;
+    p.smooth_kc = 20.0f;
+    p.prox_factor = 4.0f;
+    p.omega_max = 40.0f;
+    p.w[QS_W_POS] = -1.0f;
+    p.w[QS_W_SPIN] = -0.1f;
+    p.w[QS_W_HIT_FLOOR] = -1.0f;
+    p.w[QS_W_HIT_WALL] = -1.0f;
+    p.w[QS_W_HIT_CEIL] = -1.0f;
+    p.w[QS_W_HIT_QUAD] = -1.0f;
+}
+
+qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
+    if (!out) return fail(nullptr, QS_ERR_ARG, "qs_create: out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, QS_ERR_ARG, "qs_create: cfg is NULL");
+    if (cfg->size != sizeof(qs_config)) return fail(nullptr, QS_ERR_ARG, "qs_create: cfg->size mismatch (ABI version)");
+    if (cfg->n_envs < 1) return fail(nullptr, QS_ERR_ARG, "qs_create: n_envs must be >= 1");
+    if (cfg->k_neighbors < 0) return fail(nullptr, QS_ERR_ARG, "qs_create: k_neighbors must be >= 0");
+    if (cfg->k_neighbors > QS_MAX_K) return fail(nullptr, QS_ERR_UNSUPPORTED, "qs_create: k_neighbors > 8");
+    if (cfg->substeps < 1 || cfg->substeps > 255) return fail(nullptr, QS_ERR_ARG, "qs_create: substeps must be 1..255");
+    if (!(cfg->dt > 0.0f)) return fail(nullptr, QS_ERR_ARG, "qs_create: dt must be > 0");
+    if (cfg->episode_steps < 1) return fail(nullptr, QS_ERR_ARG, "qs_create: episode_steps must be >= 1");
+    const qs_params& pp = cfg->params;
+    if (!(pp.mass > 0 && pp.arm > 0 && pp.ixx > 0 && pp.iyy > 0 && pp.izz > 0 && pp.t2w > 0 && pp.tau_m > 0 &&
+          pp.dr_lo > 0 && pp.dr_hi >= pp.dr_lo && pp.omega_max > 0 && pp.prox_factor > 0))
+        return fail(nullptr, QS_ERR_ARG, "qs_create: physical parameters must be positive");
+
+    qs_env* h = new (std::nothrow) qs_env();
+    if (!h) return fail(nullptr, QS_ERR_OOM, "qs_create: host allocation failed");
+    h->cfg = *cfg;
+    h->cfg.swarm_sizes = nullptr;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->E = cfg->n_envs;
+    h->K = cfg->k_neighbors;
+    h->obs_dim = 18 + 6 * h->K;
+    std::vector<int32_t> sizes(h->E);
+    for (int e = 0; e < h->E; ++e) sizes[e] = cfg->swarm_sizes ? cfg->swarm_sizes[e] : cfg->n_per_env;
+    h->env_off_h.assign(h->E + 1, 0);
+    std::vector<int32_t> env_of;
+    for (int e = 0; e < h->E; ++e) {
+        if (sizes[e] < 1) {
+            delete h;
+            return fail(nullptr, QS_ERR_ARG, "qs_create: swarm sizes must be >= 1");
+        }
+        if (sizes[e] > QS_MAX_SWARM) {
+            delete h;
+            return fail(nullptr, QS_ERR_UNSUPPORTED, "qs_create: swarm size > 64");
+        }
+        h->env_off_h[e + 1] = h->env_off_h[e] + sizes[e];
+        if (h->env_off_h[e + 1] > (1 << 30)) {
+            delete h;
+            return fail(nullptr, QS_ERR_UNSUPPORTED, "qs_create: too many drones");
+        }
+        for (int i = 0; i < sizes[e]; ++i) env_of.push_back(e);
+    }
+    h->D = h->env_off_h[h->E];
+    cudaGetDevice(&h->device);
+    build_consts(h);
+
+    // envs grouped by width class (stable order inside a class)
+    std::vector<int> perm;
+    for (int W = 1; W <= QS_MAX_SWARM; W <<= 1) {
+        int first = (int)perm.size();
+        for (int e = 0; e < h->E; ++e)
+            if (width_class(sizes[e]) == W) perm.push_back(e);
+        int n = (int)perm.size() - first;
+        if (n > 0) {
+            h->plan.push_back(ClassPlan{W, default_block(W, n), 0, 0});
+            h->class_first_slot.push_back(first);
+            h->class_slots.push_back(n);
+        }
+    }
+
+    // one arena for the state
+    const size_t D = h->D, E = h->E;
+    const bool rec = (cfg->flags & QS_F_RECORD_KNN) && h->K > 0;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = (off + 255) & ~size_t(255);
+        off = o + bytes;
+        return o;
+    };
+    const size_t o_st = take(sizeof(float4) * NPLANE * D), o_prm = take(sizeof(float) * NPRM_DEV * E),
+                 o_goal = take(sizeof(float) * 3 * E), o_ep = take(sizeof(int32_t) * E),
+                 o_tick = take(sizeof(uint32_t) * E), o_off = take(sizeof(int32_t) * (E + 1)),
+                 o_of = take(sizeof(int32_t) * D), o_ev = take(sizeof(uint32_t) * D),
+                 o_knn = take(rec ? sizeof(int16_t) * h->K * D : 0), o_status = take(sizeof(int32_t)),
+                 o_perm = take(sizeof(int) * E);
+    cudaError_t ce = cudaMalloc(&h->arena, off);
+    if (ce != cudaSuccess) {
+        delete h;
+        return fail(nullptr, QS_ERR_OOM, std::string("qs_create: device allocation failed: ") + cudaGetErrorString(ce));
+    }
+    char* base = (char*)h->arena;
+    h->dv.st = (float4*)(base + o_st);
+    h->dv.prm = (float*)(base + o_prm);
+    h->dv.goal = (float*)(base + o_goal);
+    h->dv.ep = (int32_t*)(base + o_ep);
+    h->dv.tick = (uint32_t*)(base + o_tick);
+    h->dv.env_off = (const int32_t*)(base + o_off);
+    h->dv.env_of = (const int32_t*)(base + o_of);
+    h->dv.ev = (uint32_t*)(base + o_ev);
+    h->dv.knn = rec ? (int16_t*)(base + o_knn) : nullptr;
+    h->dv.status = (int32_t*)(base + o_status);
+    h->dv.D = h->D;
+    h->dv.E = h->E;
+    h->d_perm = (int*)(base + o_perm);
+    bool ok = cudaMemset(h->arena, 0, off) == cudaSuccess &&
+              cudaMemcpy((void*)h->dv.env_off, h->env_off_h.data(), sizeof(int32_t) * (E + 1), cudaMemcpyHostToDevice) ==
+                  cudaSuccess &&
+              cudaMemcpy((void*)h->dv.env_of, env_of.data(), sizeof(int32_t) * D, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(h->d_perm, perm.data(), sizeof(int) * E, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        cudaFree(h->arena);
+        delete h;
+        return fail(nullptr, QS_ERR_CUDA, "qs_create: initial upload failed");
+    }
+    qs_status s = upload_tiles(h);
+    if (s != QS_OK) {
+        std::string m = h->err;
+        cudaFree(h->arena);
+        delete h;
+        return fail(nullptr, s, m);
+    }
+    ce = launch_reset(h->c, h->dv, h->c.key0, h->c.key1, nullptr, h->stream);
+    if (ce != cudaSuccess) {
+        cudaFree(h->d_tiles);
+        cudaFree(h->arena);
+        delete h;
+        return fail(nullptr, QS_ERR_CUDA, std::string("qs_create: reset launch: ") + cudaGetErrorString(ce));
+    }
+    *out = h;
+    return QS_OK;
+}
+
+qs_status qs_destroy(qs_env* h) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_destroy: NULL handle");
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_tiles);
+    cudaFree(h->arena);
+    cudaFree(h->stage);
+    delete h;
+    return QS_OK;
+}
+
+qs_status qs_get_dims(const qs_env* h, int32_t* n_drones, int32_t* n_envs, int32_t* obs_dim) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_get_dims: NULL handle");
+    if (n_drones) *n_drones = h->D;
+    if (n_envs) *n_envs = h->E;
+    if (obs_dim) *obs_dim = h->obs_dim;
+    return QS_OK;
+}
+
+qs_status qs_reset(qs_env* h, uint64_t seed, const uint8_t* env_mask_dev, float* obs_dev) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_reset: NULL handle");
+    if (obs_dev && !aligned(obs_dev, 8)) return fail(h, QS_ERR_ARG, "qs_reset: obs_dev must be 8-byte aligned");
+    DeviceGuard g(h->device);
+    const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    if (!env_mask_dev) {
+        h->c.key0 = k0;
+        h->c.key1 = k1;
+        cudaError_t e = cudaMemsetAsync(h->dv.status, 0, sizeof(int32_t), h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "qs_reset");
+    }
+    cudaError_t e = launch_reset(h->c, h->dv, k0, k1, env_mask_dev, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qs_reset launch");
+    if (obs_dev) {
+        StepIO io{nullptr, obs_dev, nullptr, nullptr};
+        for (const ClassPlan& cp : h->plan) {
+            e = launch_step(h->c, h->dv, cp, h->d_tiles, h->d_perm, io, 1, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "qs_reset observation");
+        }
+    }
+    return QS_OK;
+}
+
+qs_status qs_step(qs_env* h, const float* actions_dev, float* obs_dev, float* reward_dev, uint8_t* done_dev) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_step: NULL handle");
+    if (!actions_dev) return fail(h, QS_ERR_ARG, "qs_step: actions_dev is NULL");
+    if (!aligned(actions_dev, 16)) return fail(h, QS_ERR_ARG, "qs_step: actions_dev must be 16-byte aligned");
+    if (obs_dev && !aligned(obs_dev, 8)) return fail(h, QS_ERR_ARG, "qs_step: obs_dev must be 8-byte aligned");
+    DeviceGuard g(h->device);
+    return do_step(h, actions_dev, obs_dev, reward_dev, done_dev);
+}
+
+qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, float* reward_host, uint8_t* done_host) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_step_host: NULL handle");
+    if (!actions_host) return fail(h, QS_ERR_ARG, "qs_step_host: actions_host is NULL");
+    DeviceGuard g(h->device);
+    const size_t D = h->D, E = h->E;
+    const size_t b_act = sizeof(float) * 4 * D, b_obs = sizeof(float) * h->obs_dim * D, b_rew = sizeof(float) * D,
+                 b_done = E;
+    if (!h->stage) {
+        h->st_obs = (b_act + 255) & ~size_t(255);
+        h->st_rew = (h->st_obs + b_obs + 255) & ~size_t(255);
+        h->st_done = (h->st_rew + b_rew + 255) & ~size_t(255);
+        if (cudaMalloc(&h->stage, h->st_done + b_done) != cudaSuccess) {
+            h->stage = nullptr;
+            return fail(h, QS_ERR_OOM, "qs_step_host: staging allocation");
+        }
+    }
+    float* d_act = (float*)h->stage;
+    float* d_obs = (float*)(h->stage + h->st_obs);
+    float* d_rew = (float*)(h->stage + h->st_rew);
+    uint8_t* d_done = (uint8_t*)(h->stage + h->st_done);
+    cudaError_t e = cudaMemcpyAsync(d_act, actions_host, b_act, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qs_step_host: action copy");
+    qs_status s = do_step(h, d_act, obs_host ? d_obs : nullptr, reward_host ? d_rew : nullptr, done_host ? d_done : nullptr);
+    if (s != QS_OK) return s;
+    if (obs_host && (e = cudaMemcpyAsync(obs_host, d_obs, b_obs, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "qs_step_host: observation copy");
+    if (reward_host && (e = cudaMemcpyAsync(reward_host, d_rew, b_rew, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "qs_step_host: reward copy");
+    if (done_host && (e = cudaMemcpyAsync(done_host, d_done, b_done, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "qs_step_host: done copy");
+    return qs_sync(h);
+}
+
+qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_dev, float* reward_dev,
+                     uint8_t* done_dev) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_rollout: NULL handle");
+    if (T < 1) return fail(h, QS_ERR_ARG, "qs_rollout: T must be >= 1");
+    if (!actions_dev || !aligned(actions_dev, 16)) return fail(h, QS_ERR_ARG, "qs_rollout: actions_dev NULL or misaligned");
+    if (obs_dev && !aligned(obs_dev, 8)) return fail(h, QS_ERR_ARG, "qs_rollout: obs_dev must be 8-byte aligned");
+    DeviceGuard g(h->device);
+    const size_t D = h->D, E = h->E;
+    for (int t = 0; t < T; ++t) {
+        qs_status s = do_step(h, actions_dev + (size_t)t * D * 4, obs_dev ? obs_dev + (size_t)t * D * h->obs_dim : nullptr,
+                              reward_dev ? reward_dev + (size_t)t * D : nullptr, done_dev ? done_dev + (size_t)t * E : nullptr);
+        if (s != QS_OK) return s;
+    }
+    return QS_OK;
+}
+
+qs_status qs_get_state(qs_env* h, float* state_dev, float* params_dev, float* goals_dev, int32_t* ep_step_dev,
+                       uint32_t* tick_dev) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_get_state: NULL handle");
+    DeviceGuard g(h->device);
+    cudaError_t e = launch_get_state(h->dv, state_dev, params_dev, goals_dev, ep_step_dev, tick_dev, h->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_get_state");
+}
+
+qs_status qs_set_state(qs_env* h, const float* state_dev, const float* params_dev, const float* goals_dev,
+                       const int32_t* ep_step_dev, const uint32_t* tick_dev) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_set_state: NULL handle");
+    DeviceGuard g(h->device);
+    cudaError_t e = launch_set_state(h->c, h->dv, state_dev, params_dev, goals_dev, ep_step_dev, tick_dev, h->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_set_state");
+}
+
+qs_status qs_get_events(qs_env* h, uint32_t* events_dev, int16_t* knn_dev) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_get_events: NULL handle");
+    if (knn_dev && !h->dv.knn && h->K > 0)
+        return fail(h, QS_ERR_ARG, "qs_get_events: neighbour lists need QS_F_RECORD_KNN at creation");
+    if (!events_dev && !knn_dev) return QS_OK;
+    DeviceGuard g(h->device);
+    cudaError_t e = launch_get_events(h->dv, h->K, events_dev, knn_dev, h->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_get_events");
+}
+
+qs_status qs_sync(qs_env* h) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_sync: NULL handle");
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qs_sync");
+    int32_t st = 0;
+    e = cudaMemcpy(&st, h->dv.status, sizeof st, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qs_sync status read");
+    if (st & 1) return fail(h, QS_ERR_STATE_NONFINITE, "a drone state became non-finite");
+    return QS_OK;
+}
+
+qs_status qs_set_block(qs_env* h, int32_t width, int32_t block) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_set_block: NULL handle");
+    if (block < 32 || block > 256 || block % 32 != 0 || block % width != 0)
+        return fail(h, QS_ERR_ARG, "qs_set_block: block must be 32..256, a multiple of 32 and of width");
+    for (ClassPlan& cp : h->plan) {
+        if (cp.W != width) continue;
+        DeviceGuard g(h->device);
+        cudaError_t e = cudaStreamSynchronize(h->stream);  // the old tile table may be in use
+        if (e != cudaSuccess) return cuda_fail(h, e, "qs_set_block");
+        cp.block = block;
+        return upload_tiles(h);
+    }
+    return fail(h, QS_ERR_ARG, "qs_set_block: no envs of that width class");
+}
+
+qs_status qs_get_block(const qs_env* h, int32_t width, int32_t* block) {
+    if (!h || !block) return fail(nullptr, QS_ERR_ARG, "qs_get_block: NULL argument");
+    *block = 0;
+    for (const ClassPlan& cp : h->plan)
+        if (cp.W == width) *block = cp.block;
+    return QS_OK;
+}
+
+const char* qs_last_error(const qs_env* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

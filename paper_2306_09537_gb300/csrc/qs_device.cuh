@@ -1,0 +1,448 @@
+// qs_device.cuh -- device-side physics of the QuadSwarm step in binary32.
+//
+// One drone's state lives in registers (struct Drone); the functions below
+// follow the paper's step (Sec. III-A .. III-E) in the order the step kernel
+// calls them. Random numbers come from Philox4x32-10 (Salmon et al., SC'11)
+// keyed by the seed, with counter (env step, drone or env id,
+// tag << 16 | substream << 8 | block, 0).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qs_internal.h"
+
+namespace qsk {
+
+// ---------------------------------------------------------------- Philox4x32-10
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t k0, uint32_t k1) {
+    uint32_t x0 = c0, x1 = c1, x2 = c2, x3 = 0u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
+        const uint32_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo1;
+        x2 = y2;
+        x3 = lo0;
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+
+__device__ __forceinline__ uint32_t ctr_word(uint32_t tag, uint32_t sub, uint32_t blk) {
+    return (tag << 16) | (sub << 8) | blk;
+}
+
+// (2k+1)/2^24 with k the top 23 bits: inside (0,1), exact in binary32.
+__device__ __forceinline__ float u01(uint32_t r) { return (float)(r >> 9) * (1.0f / 8388608.0f) + (1.0f / 16777216.0f); }
+
+// Box-Muller: two N(0,1) from two uniforms.
+__device__ __forceinline__ float2 box_muller(float u0, float u1) {
+    const float rho = sqrtf(-2.0f * logf(u0));
+    float s, c;
+    sincospif(2.0f * u1, &s, &c);
+    return make_float2(rho * c, rho * s);
+}
+
+// Six N(0,1) draws of a collision or wall perturbation (blocks 0 and 1).
+__device__ __forceinline__ void six_normals(const Consts& c, uint32_t tick, uint32_t id, uint32_t tag, uint32_t sub,
+                                            float n[6]) {
+    const uint4 a = philox(tick, id, ctr_word(tag, sub, 0), c.key0, c.key1);
+    const uint4 b = philox(tick, id, ctr_word(tag, sub, 1), c.key0, c.key1);
+    const float2 p0 = box_muller(u01(a.x), u01(a.y));
+    const float2 p1 = box_muller(u01(a.z), u01(a.w));
+    const float2 p2 = box_muller(u01(b.x), u01(b.y));
+    n[0] = p0.x; n[1] = p0.y; n[2] = p1.x; n[3] = p1.y; n[4] = p2.x; n[5] = p2.y;
+}
+
+// ---------------------------------------------------------------- per-env parameters
+struct Prm {
+    float m, ixx, iyy, izz, t2w, tau, arm, fmax, alag, ans, inv_m, inv_ixx, inv_iyy, inv_izz, thr, prox;
+};
+
+// Derived constants of the randomised values: f_max = m g t2w / 4 (max thrust
+// per rotor), alpha_lag = 1 - exp(-dt / tau_m) (first-order lag whose 2%
+// settling time is tau_m ln 50), motor-noise scale, inverses, collision
+// threshold fl32((l + l)^2) and proximity radius prox_factor * l.
+__device__ __forceinline__ void derive(const Consts& c, const float p7[QS_PARAM_DIM], float out[NPRM_DEV]) {
+    for (int k = 0; k < QS_PARAM_DIM; ++k) out[k] = p7[k];
+    const float m = p7[P_M], arm = p7[P_ARM];
+    out[P_FMAX] = 0.25f * m * c.g * p7[P_T2W];
+    out[P_ALAG] = -expm1f(-c.dt / p7[P_TAU]);
+    out[P_ANS] = c.ans_frac * m * c.g * 0.25f;
+    out[P_INVM] = 1.0f / m;
+    out[P_INVIXX] = 1.0f / p7[P_IXX];
+    out[P_INVIYY] = 1.0f / p7[P_IYY];
+    out[P_INVIZZ] = 1.0f / p7[P_IZZ];
+    const float r = __fadd_rn(arm, arm);
+    out[P_THR] = __fmul_rn(r, r);
+    out[P_PROX] = c.prox_factor * arm;
+}
+
+__device__ __forceinline__ Prm load_prm(const float* __restrict__ prm, int E, int e) {
+    Prm p;
+    p.m = __ldg(prm + P_M * E + e);
+    p.ixx = __ldg(prm + P_IXX * E + e);
+    p.iyy = __ldg(prm + P_IYY * E + e);
+    p.izz = __ldg(prm + P_IZZ * E + e);
+    p.t2w = __ldg(prm + P_T2W * E + e);
+    p.tau = __ldg(prm + P_TAU * E + e);
+    p.arm = __ldg(prm + P_ARM * E + e);
+    p.fmax = __ldg(prm + P_FMAX * E + e);
+    p.alag = __ldg(prm + P_ALAG * E + e);
+    p.ans = __ldg(prm + P_ANS * E + e);
+    p.inv_m = __ldg(prm + P_INVM * E + e);
+    p.inv_ixx = __ldg(prm + P_INVIXX * E + e);
+    p.inv_iyy = __ldg(prm + P_INVIYY * E + e);
+    p.inv_izz = __ldg(prm + P_INVIZZ * E + e);
+    p.thr = __ldg(prm + P_THR * E + e);
+    p.prox = __ldg(prm + P_PROX * E + e);
+    return p;
+}
+
+__device__ __forceinline__ Prm prm_from(const float v[NPRM_DEV]) {
+    Prm p;
+    p.m = v[P_M]; p.ixx = v[P_IXX]; p.iyy = v[P_IYY]; p.izz = v[P_IZZ]; p.t2w = v[P_T2W]; p.tau = v[P_TAU];
+    p.arm = v[P_ARM]; p.fmax = v[P_FMAX]; p.alag = v[P_ALAG]; p.ans = v[P_ANS]; p.inv_m = v[P_INVM];
+    p.inv_ixx = v[P_INVIXX]; p.inv_iyy = v[P_INVIYY]; p.inv_izz = v[P_INVIZZ]; p.thr = v[P_THR];
+    p.prox = v[P_PROX];
+    return p;
+}
+
+// Domain randomisation of one env (7 scale factors U(lo,hi)) and its goal
+// (uniform in the room); three Philox blocks at (tick, e, tag).
+__device__ __forceinline__ void draw_env(const Consts& c, uint32_t k0, uint32_t k1, uint32_t tick, uint32_t tag,
+                                         int e, float p7[QS_PARAM_DIM], float goal[3]) {
+    const uint4 a = philox(tick, (uint32_t)e, ctr_word(tag, 0, 0), k0, k1);
+    const uint4 b = philox(tick, (uint32_t)e, ctr_word(tag, 0, 1), k0, k1);
+    const uint4 d = philox(tick, (uint32_t)e, ctr_word(tag, 0, 2), k0, k1);
+    const float u[10] = {u01(a.x), u01(a.y), u01(a.z), u01(a.w), u01(b.x), u01(b.y), u01(b.z), u01(b.w),
+                         u01(d.x), u01(d.y)};
+    const bool dr = (c.flags & QS_F_DR) != 0;
+    for (int k = 0; k < QS_PARAM_DIM; ++k) p7[k] = dr ? c.nominal[k] * (c.dr_lo + (c.dr_hi - c.dr_lo) * u[k]) : c.nominal[k];
+    goal[0] = -c.room_hx + 2.0f * c.room_hx * u[7];
+    goal[1] = -c.room_hy + 2.0f * c.room_hy * u[8];
+    goal[2] = c.room_h * u[9];
+}
+
+// ---------------------------------------------------------------- drone state
+struct Drone {
+    float x[3], v[3], R[9], w[3], uf[4], eps[4], fp[4];
+};
+
+__device__ __forceinline__ void unpack(Drone& s, const float4 q[NPLANE]) {
+    const float* f = reinterpret_cast<const float*>(q);
+    for (int k = 0; k < 3; ++k) s.x[k] = f[k];
+    for (int k = 0; k < 3; ++k) s.v[k] = f[3 + k];
+    for (int k = 0; k < 9; ++k) s.R[k] = f[6 + k];
+    for (int k = 0; k < 3; ++k) s.w[k] = f[15 + k];
+    for (int k = 0; k < 4; ++k) s.uf[k] = f[18 + k];
+    for (int k = 0; k < 4; ++k) s.eps[k] = f[22 + k];
+    for (int k = 0; k < 4; ++k) s.fp[k] = f[26 + k];
+}
+
+__device__ __forceinline__ void pack(const Drone& s, float4 q[NPLANE]) {
+    float* f = reinterpret_cast<float*>(q);
+    for (int k = 0; k < 3; ++k) f[k] = s.x[k];
+    for (int k = 0; k < 3; ++k) f[3 + k] = s.v[k];
+    for (int k = 0; k < 9; ++k) f[6 + k] = s.R[k];
+    for (int k = 0; k < 3; ++k) f[15 + k] = s.w[k];
+    for (int k = 0; k < 4; ++k) f[18 + k] = s.uf[k];
+    for (int k = 0; k < 4; ++k) f[22 + k] = s.eps[k];
+    for (int k = 0; k < 4; ++k) f[26 + k] = s.fp[k];
+    f[30] = 0.0f;
+    f[31] = 0.0f;
+}
+
+__device__ __forceinline__ void load_drone(Drone& s, const float4* __restrict__ st, int D, int d) {
+    float4 q[NPLANE];
+#pragma unroll
+    for (int p = 0; p < NPLANE; ++p) q[p] = st[(size_t)p * D + d];
+    unpack(s, q);
+}
+
+__device__ __forceinline__ void store_drone(const Drone& s, float4* __restrict__ st, int D, int d) {
+    float4 q[NPLANE];
+    pack(s, q);
+#pragma unroll
+    for (int p = 0; p < NPLANE; ++p) st[(size_t)p * D + d] = q[p];
+}
+
+// Initial drone state (Sec. III-A with DR): position uniform in the room,
+// velocity and body rates uniform in [-1,1], orientation from a uniform unit
+// quaternion (Shoemake 1992), motors at hover (u_f^2 = 1/t2w), noise zero.
+__device__ __forceinline__ void draw_drone(const Consts& c, uint32_t k0, uint32_t k1, uint32_t tick, uint32_t tag,
+                                           int d, float t2w, Drone& s) {
+    const uint4 a = philox(tick, (uint32_t)d, ctr_word(tag, 0, 0), k0, k1);
+    const uint4 b = philox(tick, (uint32_t)d, ctr_word(tag, 0, 1), k0, k1);
+    const uint4 q = philox(tick, (uint32_t)d, ctr_word(tag, 0, 2), k0, k1);
+    s.x[0] = -c.room_hx + 2.0f * c.room_hx * u01(a.x);
+    s.x[1] = -c.room_hy + 2.0f * c.room_hy * u01(a.y);
+    s.x[2] = c.room_h * u01(a.z);
+    s.v[0] = -1.0f + 2.0f * u01(a.w);
+    s.v[1] = -1.0f + 2.0f * u01(b.x);
+    s.v[2] = -1.0f + 2.0f * u01(b.y);
+    const float u6 = u01(b.z), u7 = u01(b.w), u8 = u01(q.x);
+    const float ra = sqrtf(1.0f - u6), rb = sqrtf(u6);
+    float s7, c7, s8, c8;
+    sincospif(2.0f * u7, &s7, &c7);
+    sincospif(2.0f * u8, &s8, &c8);
+    const float qx = ra * s7, qy = ra * c7, qz = rb * s8, qw = rb * c8;
+    s.R[0] = 1.0f - 2.0f * (qy * qy + qz * qz);
+    s.R[1] = 2.0f * (qx * qy - qz * qw);
+    s.R[2] = 2.0f * (qx * qz + qy * qw);
+    s.R[3] = 2.0f * (qx * qy + qz * qw);
+    s.R[4] = 1.0f - 2.0f * (qx * qx + qz * qz);
+    s.R[5] = 2.0f * (qy * qz - qx * qw);
+    s.R[6] = 2.0f * (qx * qz - qy * qw);
+    s.R[7] = 2.0f * (qy * qz + qx * qw);
+    s.R[8] = 1.0f - 2.0f * (qx * qx + qy * qy);
+    s.w[0] = -1.0f + 2.0f * u01(q.y);
+    s.w[1] = -1.0f + 2.0f * u01(q.z);
+    s.w[2] = -1.0f + 2.0f * u01(q.w);
+    const float hov = 1.0f / t2w;
+    const float uh = sqrtf(hov);
+    for (int r = 0; r < 4; ++r) {
+        s.uf[r] = uh;
+        s.eps[r] = 0.0f;
+        s.fp[r] = hov;
+    }
+}
+
+// ---------------------------------------------------------------- event bits
+constexpr uint32_t EV_HIT_FLOOR = QS_EV_HIT_FLOOR, EV_ON_FLOOR = QS_EV_ON_FLOOR, EV_HIT_WALL = QS_EV_HIT_WALL,
+                   EV_HIT_CEIL = QS_EV_HIT_CEIL, EV_HIT_QUAD = QS_EV_HIT_QUAD;
+
+// S1 command map: clip(a, 0, 1), or (clip(a, -1, 1) + 1) / 2 (paper's form).
+__device__ __forceinline__ float command(const Consts& c, float a) {
+    if (c.flags & QS_F_ACTION_SYMMETRIC) return 0.5f * (fminf(fmaxf(a, -1.0f), 1.0f) + 1.0f);
+    return fminf(fmaxf(a, 0.0f), 1.0f);
+}
+
+__device__ __forceinline__ float softplus_b(float u, float beta) {
+    const float z = beta * u;
+    return (fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z)))) / beta;
+}
+
+// R <- polar(R + dt R [w]x) for a rotation R. In closed form the polar factor
+// of I + dt [w]x is the rotation about w by atan(dt |w|), i.e.
+// Q = I + a [w]x + b [w]x^2 with c = 1/sqrt(1 + dt^2 |w|^2), a = dt c,
+// b = dt^2 c^2 / (1 + c); row_i(R [w]x) = row_i(R) x w. One Bjorck step
+// R <- R (3I - R^T R) / 2 then removes the binary32 drift of R itself.
+__device__ __forceinline__ void rotate_polar(float R[9], const float w[3], float dt) {
+    const float n2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const float cc = rsqrtf(fmaf(dt * dt, n2, 1.0f));
+    const float a = dt * cc;
+    const float b = dt * dt * cc * cc / (1.0f + cc);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
+        const float t0 = r1 * w[2] - r2 * w[1], t1 = r2 * w[0] - r0 * w[2], t2 = r0 * w[1] - r1 * w[0];
+        const float q0 = t1 * w[2] - t2 * w[1], q1 = t2 * w[0] - t0 * w[2], q2 = t0 * w[1] - t1 * w[0];
+        R[3 * i] = fmaf(b, q0, fmaf(a, t0, r0));
+        R[3 * i + 1] = fmaf(b, q1, fmaf(a, t1, r1));
+        R[3 * i + 2] = fmaf(b, q2, fmaf(a, t2, r2));
+    }
+    // one Bjorck step: S = R^T R; R <- R (1.5 I - 0.5 S)
+    float S[6];  // 00 01 02 11 12 22
+    S[0] = R[0] * R[0] + R[3] * R[3] + R[6] * R[6];
+    S[1] = R[0] * R[1] + R[3] * R[4] + R[6] * R[7];
+    S[2] = R[0] * R[2] + R[3] * R[5] + R[6] * R[8];
+    S[3] = R[1] * R[1] + R[4] * R[4] + R[7] * R[7];
+    S[4] = R[1] * R[2] + R[4] * R[5] + R[7] * R[8];
+    S[5] = R[2] * R[2] + R[5] * R[5] + R[8] * R[8];
+    const float A00 = 1.5f - 0.5f * S[0], A11 = 1.5f - 0.5f * S[3], A22 = 1.5f - 0.5f * S[5];
+    const float A01 = -0.5f * S[1], A02 = -0.5f * S[2], A12 = -0.5f * S[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
+        R[3 * i] = r0 * A00 + r1 * A01 + r2 * A02;
+        R[3 * i + 1] = r0 * A01 + r1 * A11 + r2 * A12;
+        R[3 * i + 2] = r0 * A02 + r1 * A12 + r2 * A22;
+    }
+}
+
+// One physics substep of one drone (S1 .. S8). fh: this control step's
+// normalised commands; u = sqrt(fh). pacc: smooth-mode pair acceleration
+// (zero otherwise). Returns the substep's event bits.
+__device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts& c, const float u[4], uint32_t tick,
+                                            int d, int sub, const float pacc[3]) {
+    uint32_t ev = 0;
+    const float dt = c.dt, g = c.g;
+    // S1 first-order motor lag on the normalised rotor speed
+#pragma unroll
+    for (int r = 0; r < 4; ++r) s.uf[r] = fmaf(p.alag, u[r] - s.uf[r], s.uf[r]);
+    // S2 AR(1) motor noise and per-rotor thrust f = f_max uf^2 + eps
+    if (c.flags & QS_F_MOTOR_NOISE) {
+        const uint4 q = philox(tick, (uint32_t)d, ctr_word(TAG_MOTOR, (uint32_t)sub, 0), c.key0, c.key1);
+        const float2 n01 = box_muller(u01(q.x), u01(q.y));
+        const float2 n23 = box_muller(u01(q.z), u01(q.w));
+        s.eps[0] = fmaf(c.alpha_nd, s.eps[0], p.ans * n01.x);
+        s.eps[1] = fmaf(c.alpha_nd, s.eps[1], p.ans * n01.y);
+        s.eps[2] = fmaf(c.alpha_nd, s.eps[2], p.ans * n23.x);
+        s.eps[3] = fmaf(c.alpha_nd, s.eps[3], p.ans * n23.y);
+    }
+    float f[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) f[r] = fmaf(p.fmax * s.uf[r], s.uf[r], s.eps[r]);
+    // S3 X layout: rotors at (+-l, +-l)/sqrt(2); thrust along body z; yaw
+    // torque kappa * sum s_r f_r with spins (-1, +1, -1, +1)
+    const float T = (f[0] + f[1]) + (f[2] + f[3]);
+    const float sa = p.arm * 0.70710678118654752f;
+    const float tx = sa * ((f[0] + f[1]) - (f[2] + f[3]));
+    const float ty = sa * ((f[1] + f[2]) - (f[0] + f[3]));
+    const float tz = c.kappa * ((f[1] + f[3]) - (f[0] + f[2]));
+    // S4 world thrust F = R (0,0,T), a = F/m + g
+    const float F0 = s.R[2] * T, F1 = s.R[5] * T, F2 = s.R[8] * T;
+    float a0 = F0 * p.inv_m, a1 = F1 * p.inv_m, a2 = fmaf(F2, p.inv_m, -g);
+    bool on_floor = false, moving = false;
+    if (c.flags & QS_F_SMOOTH) {
+        const float kcg = c.kc * g;
+        a2 += kcg * (softplus_b(-s.x[2], c.beta) - softplus_b(s.x[2] - c.room_h, c.beta));
+        a0 += kcg * (softplus_b(-c.room_hx - s.x[0], c.beta) - softplus_b(s.x[0] - c.room_hx, c.beta));
+        a1 += kcg * (softplus_b(-c.room_hy - s.x[1], c.beta) - softplus_b(s.x[1] - c.room_hy, c.beta));
+        a0 += pacc[0];
+        a1 += pacc[1];
+        a2 += pacc[2];
+    } else if ((c.flags & QS_F_FLOOR) && s.x[2] <= 0.0f) {
+        const float mg = p.m * g;
+        if (F2 < mg) {
+            // resting on the floor: friction mu (m g - F_z) against the motion
+            on_floor = true;
+            ev |= EV_ON_FLOOR;
+            const float ffric = c.mu * (mg - F2);
+            float fx = F0, fy = F1;
+            if (s.v[0] == 0.0f && s.v[1] == 0.0f) {
+                const float nf = sqrtf(fx * fx + fy * fy);
+                const float keep = nf > ffric ? (nf - ffric) / nf : 0.0f;
+                fx *= keep;
+                fy *= keep;
+            } else {
+                const float inv_nv = rsqrtf(s.v[0] * s.v[0] + s.v[1] * s.v[1]);
+                fx -= ffric * s.v[0] * inv_nv;
+                fy -= ffric * s.v[1] * inv_nv;
+                moving = true;
+            }
+            a0 = fx * p.inv_m;
+            a1 = fy * p.inv_m;
+            a2 = 0.0f;
+            s.v[2] = 0.0f;
+        }
+    }
+    // S5 Euler's equation, diagonal inertia
+    const float Iw0 = p.ixx * s.w[0], Iw1 = p.iyy * s.w[1], Iw2 = p.izz * s.w[2];
+    const float wd0 = (tx - (s.w[1] * Iw2 - s.w[2] * Iw1)) * p.inv_ixx;
+    const float wd1 = (ty - (s.w[2] * Iw0 - s.w[0] * Iw2)) * p.inv_iyy;
+    const float wd2 = (tz - (s.w[0] * Iw1 - s.w[1] * Iw0)) * p.inv_izz;
+    // S6 semi-implicit Euler, body rates bounded by omega_max
+    const float vx0 = s.v[0], vy0 = s.v[1];
+    s.v[0] = fmaf(a0, dt, s.v[0]);
+    s.v[1] = fmaf(a1, dt, s.v[1]);
+    s.v[2] = fmaf(a2, dt, s.v[2]);
+    if (on_floor && moving && (s.v[0] * vx0 + s.v[1] * vy0) < 0.0f) {
+        s.v[0] = 0.0f;
+        s.v[1] = 0.0f;
+    }
+    s.x[0] = fmaf(s.v[0], dt, s.x[0]);
+    s.x[1] = fmaf(s.v[1], dt, s.x[1]);
+    s.x[2] = fmaf(s.v[2], dt, s.x[2]);
+    s.w[0] = fminf(fmaxf(fmaf(wd0, dt, s.w[0]), -c.omega_max), c.omega_max);
+    s.w[1] = fminf(fmaxf(fmaf(wd1, dt, s.w[1]), -c.omega_max), c.omega_max);
+    s.w[2] = fminf(fmaxf(fmaf(wd2, dt, s.w[2]), -c.omega_max), c.omega_max);
+    rotate_polar(s.R, s.w, dt);
+
+    if (c.flags & QS_F_SMOOTH) {
+        if (s.x[2] < 0.0f) ev |= EV_HIT_FLOOR;
+        if (s.x[2] > c.room_h) ev |= EV_HIT_CEIL;
+        if (fabsf(s.x[0]) > c.room_hx || fabsf(s.x[1]) > c.room_hy) ev |= EV_HIT_WALL;
+        return ev;
+    }
+    // S7 floor hit: momenta to zero, upright attitude keeping the heading
+    if ((c.flags & QS_F_FLOOR) && s.x[2] <= 0.0f && s.v[2] < 0.0f) {
+        ev |= EV_HIT_FLOOR;
+        s.x[2] = 0.0f;
+        for (int k = 0; k < 3; ++k) {
+            s.v[k] = 0.0f;
+            s.w[k] = 0.0f;
+        }
+        float cs, sn;
+        const float h2 = s.R[0] * s.R[0] + s.R[3] * s.R[3];
+        if (h2 >= 1e-12f) {
+            const float ih = rsqrtf(h2);
+            cs = s.R[0] * ih;
+            sn = s.R[3] * ih;
+        } else {
+            const float ih = rsqrtf(s.R[1] * s.R[1] + s.R[4] * s.R[4]);
+            cs = s.R[4] * ih;
+            sn = -s.R[1] * ih;
+        }
+        s.R[0] = cs; s.R[1] = -sn; s.R[2] = 0.0f;
+        s.R[3] = sn; s.R[4] = cs;  s.R[5] = 0.0f;
+        s.R[6] = 0.0f; s.R[7] = 0.0f; s.R[8] = 1.0f;
+    }
+    // S8 walls and ceiling: remove the normal velocity, clamp, then
+    // v <- alpha_c (v + eps_v), w <- w + eps_w
+    if (c.flags & QS_F_WALLS) {
+        bool wall = false, ceil = false;
+        if (s.x[0] > c.room_hx && s.v[0] > 0.0f) { s.v[0] = 0.0f; s.x[0] = c.room_hx; wall = true; }
+        else if (s.x[0] < -c.room_hx && s.v[0] < 0.0f) { s.v[0] = 0.0f; s.x[0] = -c.room_hx; wall = true; }
+        if (s.x[1] > c.room_hy && s.v[1] > 0.0f) { s.v[1] = 0.0f; s.x[1] = c.room_hy; wall = true; }
+        else if (s.x[1] < -c.room_hy && s.v[1] < 0.0f) { s.v[1] = 0.0f; s.x[1] = -c.room_hy; wall = true; }
+        if (s.x[2] > c.room_h && s.v[2] > 0.0f) { s.v[2] = 0.0f; s.x[2] = c.room_h; ceil = true; }
+        if (wall || ceil) {
+            float n[6];
+            six_normals(c, tick, (uint32_t)d, TAG_WALL, (uint32_t)sub, n);
+            for (int k = 0; k < 3; ++k) {
+                s.v[k] = c.alpha_c * fmaf(c.sig_cv, n[k], s.v[k]);
+                s.w[k] = fmaf(c.sig_cw, n[3 + k], s.w[k]);
+            }
+            ev |= (wall ? EV_HIT_WALL : 0u) | (ceil ? EV_HIT_CEIL : 0u);
+        }
+    }
+    return ev;
+}
+
+// Canonical binary32 pair key |x_j - x_i|^2, evaluated without contraction in
+// a fixed order so that both members of a pair, and any other implementation
+// of the same sequence, obtain the same bits.
+__device__ __forceinline__ float pair_key(float xi0, float xi1, float xi2, float xj0, float xj1, float xj2,
+                                          float& dx, float& dy, float& dz) {
+    dx = __fsub_rn(xj0, xi0);
+    dy = __fsub_rn(xj1, xi1);
+    dz = __fsub_rn(xj2, xi2);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Sensor noise of the observation (Sec. III-C): U(-s,s) on x and v, N(0,s^2)
+// on w; three Philox blocks of the OBS stream, substream `sub`.
+__device__ __forceinline__ void obs_noise(const Consts& c, uint32_t tick, int d, uint32_t sub, float ex[3], float ev[3],
+                                          float ew[3]) {
+    const uint4 a = philox(tick, (uint32_t)d, ctr_word(TAG_OBS, sub, 0), c.key0, c.key1);
+    const uint4 b = philox(tick, (uint32_t)d, ctr_word(TAG_OBS, sub, 1), c.key0, c.key1);
+    const uint4 q = philox(tick, (uint32_t)d, ctr_word(TAG_OBS, sub, 2), c.key0, c.key1);
+    ex[0] = (2.0f * u01(a.x) - 1.0f) * c.obs_sx;
+    ex[1] = (2.0f * u01(a.y) - 1.0f) * c.obs_sx;
+    ex[2] = (2.0f * u01(a.z) - 1.0f) * c.obs_sx;
+    ev[0] = (2.0f * u01(a.w) - 1.0f) * c.obs_sv;
+    ev[1] = (2.0f * u01(b.x) - 1.0f) * c.obs_sv;
+    ev[2] = (2.0f * u01(b.y) - 1.0f) * c.obs_sv;
+    const float2 n01 = box_muller(u01(b.z), u01(b.w));
+    const float2 n2 = box_muller(u01(q.x), u01(q.y));
+    ew[0] = n01.x * c.obs_sw;
+    ew[1] = n01.y * c.obs_sw;
+    ew[2] = n2.x * c.obs_sw;
+}
+
+__device__ __forceinline__ bool finite_state(const Drone& s) {
+    float acc = 0.0f;
+    for (int k = 0; k < 3; ++k) acc += fabsf(s.x[k]) + fabsf(s.v[k]) + fabsf(s.w[k]);
+    for (int k = 0; k < 9; ++k) acc += fabsf(s.R[k]);
+    for (int k = 0; k < 4; ++k) acc += fabsf(s.uf[k]) + fabsf(s.eps[k]);
+    return isfinite(acc);
+}
+
+}  // namespace qsk

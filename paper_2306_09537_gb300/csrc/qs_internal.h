@@ -1,0 +1,89 @@
+// qs_internal.h -- host/device shared definitions of libquadswarm_gpu.so.
+// Not part of the public ABI (include/qs.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qs.h"
+
+namespace qsk {
+
+// Per-env parameter planes in device memory, [NPRM_DEV][E] (plane-major so
+// that consecutive single-drone envs read them coalesced).
+enum PrmIdx {
+    P_M, P_IXX, P_IYY, P_IZZ, P_T2W, P_TAU, P_ARM,  // the 7 randomised values
+    P_FMAX, P_ALAG, P_ANS, P_INVM, P_INVIXX, P_INVIYY, P_INVIZZ, P_THR, P_PROX,
+    NPRM_DEV
+};
+
+// Philox stream tags (counter word 2 = tag << 16 | substream << 8 | block).
+enum Tag : uint32_t {
+    TAG_RESET_ENV = 1, TAG_RESET_DRONE = 2, TAG_MOTOR = 3, TAG_OBS = 4, TAG_COLL = 5, TAG_WALL = 6,
+    TAG_AUTO_ENV = 7, TAG_AUTO_DRONE = 8
+};
+
+// Number of float4 planes of the drone state: 30 floats -> 8 float4 (2 pad).
+constexpr int NPLANE = 8;
+
+// Model constants, passed by value to every kernel.
+struct Consts {
+    float dt, g, kappa, mu, alpha_nd, alpha_c, sig_cv, sig_cw;
+    float obs_sx, obs_sv, obs_sw;
+    float room_hx, room_hy, room_h;
+    float beta, kc, omega_max, ans_frac, prox_factor, dr_lo, dr_hi;
+    float nominal[QS_PARAM_DIM];
+    float w[QS_NW];
+    uint32_t flags, key0, key1;
+    int substeps, K, episode_steps, obs_dim;
+};
+
+// Device buffers owned by a handle.
+struct Dev {
+    float4* st;              // [NPLANE][D] drone state planes
+    float* prm;              // [NPRM_DEV][E]
+    float* goal;             // [3][E]
+    int32_t* ep;             // [E] control steps into the episode
+    uint32_t* tick;          // [E] Philox step counter
+    const int32_t* env_off;  // [E+1]
+    const int32_t* env_of;   // [D]
+    uint32_t* ev;            // [D] event bits of the last step
+    int16_t* knn;            // [K][D] neighbour local indices (QS_F_RECORD_KNN)
+    int32_t* status;         // device error word (bit 0: non-finite state)
+    int D, E;
+};
+
+// A launch covers "tiles": consecutive slots (envs of one width class W) of
+// the permutation `perm`; a tile is one CTA of `block` threads = block / W slots.
+struct Tile {
+    int first;  // first slot (index into perm)
+    int count;  // slots in this tile
+};
+
+struct ClassPlan {
+    int W;         // lanes per env slot (power of two >= N of its envs)
+    int block;     // threads per CTA
+    int n_tiles;
+    int tile_off;  // offset of this class's tiles in the tile array
+};
+
+// Per-step input/output pointers; strides let one call address step t of a
+// [T][...] rollout buffer.
+struct StepIO {
+    const float* act;  // [D][4]
+    float* obs;        // [D][obs_dim] or null
+    float* rew;        // [D] or null
+    uint8_t* done;     // [E] or null
+};
+
+// kernels (qs_kernels.cu)
+cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, const Tile* tiles, const int* perm,
+                        const StepIO& io, int observe_only, cudaStream_t s);
+cudaError_t launch_reset(const Consts& c, const Dev& dv, uint32_t key0, uint32_t key1, const uint8_t* mask,
+                         cudaStream_t s);
+cudaError_t launch_get_state(const Dev& dv, float* state, float* params, float* goals, int32_t* ep,
+                             uint32_t* tick, cudaStream_t s);
+cudaError_t launch_set_state(const Consts& c, const Dev& dv, const float* state, const float* params,
+                             const float* goals, const int32_t* ep, const uint32_t* tick, cudaStream_t s);
+cudaError_t launch_get_events(const Dev& dv, int K, uint32_t* events, int16_t* knn, cudaStream_t s);
+
+}  // namespace qsk

@@ -1,0 +1,80 @@
+"""QuadSwarmEnv: the Gym-style multi-agent environment of the paper (Sec. III,
+Table I "Gym Wrapper") over the C ABI, with torch tensors for device memory
+and the current torch CUDA stream for ordering."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import qs
+
+
+class QuadSwarmEnv:
+    """E environments of N_e quadrotors each; one ``step`` is one 100 Hz control
+    step of all of them, computed by libquadswarm_gpu.so on the current device."""
+
+    def __init__(self, n_envs: int, swarm=1, k_neighbors: int = 0, features=(), seed: int = 1, weights=None,
+                 device="cuda", stream=None, **overrides):
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("QuadSwarmEnv runs on a CUDA device only")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        sizes = None
+        if swarm is None or not np.isscalar(swarm):
+            sizes = np.ascontiguousarray(swarm, dtype=np.int32)
+            swarm = 1
+        self.cfg = qs.make_config(n_envs, swarm, k_neighbors, features, seed, weights, **overrides)
+        with torch.cuda.device(self.device):
+            self.h = qs.qs_create(self.cfg, self.stream.cuda_stream, swarm_sizes=sizes)
+        self.D, self.E, self.obs_dim = qs.qs_get_dims(self.h)
+        self.K = int(k_neighbors)
+        kw = dict(device=self.device)
+        self.obs = torch.empty(self.D, self.obs_dim, dtype=torch.float32, **kw)
+        self.reward = torch.empty(self.D, dtype=torch.float32, **kw)
+        self.done = torch.empty(self.E, dtype=torch.uint8, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            qs.qs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, seed: int, env_mask=None) -> torch.Tensor:
+        qs.qs_reset(self.h, seed, env_mask, self.obs)
+        return self.obs
+
+    def step(self, actions: torch.Tensor):
+        assert actions.shape == (self.D, 4) and actions.dtype == torch.float32 and actions.is_cuda
+        qs.qs_step(self.h, actions.contiguous(), self.obs, self.reward, self.done)
+        return self.obs, self.reward, self.done
+
+    def rollout(self, actions: torch.Tensor, obs=None, reward=None, done=None):
+        T = actions.shape[0]
+        assert actions.shape == (T, self.D, 4)
+        qs.qs_rollout(self.h, T, actions.contiguous(), obs, reward, done)
+        return obs, reward, done
+
+    def get_state(self):
+        kw = dict(device=self.device)
+        out = {"state": torch.empty(self.D, qs.QS_STATE_DIM, **kw), "params": torch.empty(self.E, qs.QS_PARAM_DIM, **kw),
+               "goals": torch.empty(self.E, 3, **kw), "ep_step": torch.empty(self.E, dtype=torch.int32, **kw),
+               "tick": torch.empty(self.E, dtype=torch.int32, **kw)}
+        qs.qs_get_state(self.h, out["state"], out["params"], out["goals"], out["ep_step"], out["tick"])
+        return out
+
+    def set_state(self, state=None, params=None, goals=None, ep_step=None, tick=None):
+        qs.qs_set_state(self.h, state, params, goals, ep_step, tick)
+
+    def get_events(self, knn: bool = False):
+        ev = torch.empty(self.D, dtype=torch.int32, device=self.device)
+        nb = torch.empty(self.D, max(self.K, 1), dtype=torch.int16, device=self.device) if knn else None
+        qs.qs_get_events(self.h, ev, nb)
+        return ev, (nb[:, :self.K] if nb is not None else None)
+
+    def sync(self):
+        qs.qs_sync(self.h)

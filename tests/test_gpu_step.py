@@ -1,0 +1,332 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 oracle.
+
+Bars: neighbour indices, collision sets, event bits and done are bit-exact,
+except for drones whose oracle trajectory took a decision within a relative
+margin of its threshold (there a binary32 and a binary64 run may legitimately
+branch apart; those drones are counted and must be rare). Continuous outputs
+match within tolerances derived from binary32 rounding; after 100 free-running
+steps positions agree to 1e-4 m and rotation entries to 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import ALL_WEIGHTS, DEV, env_of, gpu_state, nominal, pair, seeded_inputs, set_both
+from oracle import oracle as O
+from paper_2306_09537_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FULL = ("floor", "walls", "motor_noise", "obs_noise", "dr", "collisions", "record_knn")
+MARGIN_1STEP = 1e-5
+
+
+def one_step(sizes, K, features, seed, weights=ALL_WEIGHTS, spread=0.12, **kw):
+    env, o = pair(sizes, K, features, seed=seed, weights=weights, **kw)
+    st, prm, goals = seeded_inputs(env, seed, sizes, spread=spread if max(sizes) > 1 else None)
+    set_both(env, o, st, prm, goals, ep=3, tick=11)
+    acts = W.actions(seed, 1, env.D)[0]
+    obs, rew, done = env.step(torch.from_numpy(acts).to(DEV))
+    ev, knn = env.get_events(knn="record_knn" in features and K > 0)
+    g = gpu_state(env)
+    oobs, orew, odone = o.step(acts.astype(np.float64))
+    oev, oknn, margin = o.get_events()
+    os_ = o.get_state()
+    return dict(env=env, o=o, obs=obs.cpu().numpy(), rew=rew.cpu().numpy(), done=done.cpu().numpy(),
+                ev=ev.cpu().numpy().astype(np.uint32), knn=None if knn is None else knn.cpu().numpy().astype(np.int32),
+                g=g, oobs=oobs, orew=orew, odone=odone, oev=oev, oknn=oknn, margin=margin, os=os_)
+
+
+def check_step(r, sizes, margin=MARGIN_1STEP, max_excluded=0.01):
+    eo = env_of(sizes)
+    bad_env = np.zeros(len(sizes), bool)
+    np.logical_or.at(bad_env, eo, r["margin"] < margin)
+    keep = ~bad_env[eo]
+    assert keep.mean() >= 1.0 - max_excluded, f"too many near-threshold drones: {1 - keep.mean():.3%}"
+    g, o = r["g"]["state"], r["os"]["state"]
+    # continuous state: binary32 rounding of one step
+    assert np.abs(g[keep, 0:3] - o[keep, 0:3]).max() < 2e-5
+    assert np.abs(g[keep, 3:6] - o[keep, 3:6]).max() < 2e-5
+    assert np.abs(g[keep, 6:15] - o[keep, 6:15]).max() < 2e-6
+    assert np.allclose(g[keep, 15:18], o[keep, 15:18], rtol=2e-5, atol=2e-5)
+    assert np.allclose(g[keep, 18:30], o[keep, 18:30], rtol=1e-5, atol=1e-7)
+    assert np.allclose(r["obs"][keep], r["oobs"][keep], rtol=2e-5, atol=2e-5)
+    assert np.allclose(r["rew"][keep], r["orew"][keep], rtol=2e-5, atol=2e-5)
+    # discrete outputs: bit-exact
+    assert np.array_equal(r["ev"][keep], r["oev"][keep])
+    if r["knn"] is not None:
+        assert np.array_equal(r["knn"][keep], r["oknn"][keep])
+    assert np.array_equal(r["done"], r["odone"])
+    assert np.array_equal(r["g"]["ep_step"], r["os"]["ep_step"])
+    assert np.array_equal(r["g"]["tick"].astype(np.uint32), r["os"]["tick"])
+    return keep
+
+
+# ----------------------------------------------------------------------------- reset
+@pytest.mark.parametrize("sizes,K", [([1] * 2048, 0), ([8] * 256, 6), ([1, 2, 3, 5, 8, 13, 33, 64], 6)])
+def test_reset_matches_oracle(sizes, K):
+    env, o = pair(sizes, K, FULL, seed=21)
+    obs = env.reset(21).clone()
+    o.reset(21)
+    g = gpu_state(env)
+    s = o.get_state()
+    assert np.allclose(g["params"], s["params"], rtol=2e-7, atol=0)
+    assert np.abs(g["goals"] - s["goals"]).max() < 2e-6
+    assert np.abs(g["state"][:, 0:6] - s["state"][:, 0:6]).max() < 2e-6
+    assert np.abs(g["state"][:, 6:18] - s["state"][:, 6:18]).max() < 2e-6
+    assert np.allclose(g["state"][:, 18:30], s["state"][:, 18:30], rtol=2e-7, atol=0)
+    assert (g["ep_step"] == 0).all() and (g["tick"] == 0).all()
+    oobs = o.observe()
+    assert np.allclose(obs.cpu().numpy(), oobs, rtol=1e-5, atol=5e-6)
+
+
+# ----------------------------------------------------------------------------- one step
+@pytest.mark.parametrize("name,sizes,K,features", [
+    ("single", [1] * 1000, 0, FULL),
+    ("single_k6_padded", [1] * 300, 6, FULL),
+    ("swarm8", [8] * 300, 6, FULL),
+    ("uneven", [1, 2, 3, 4, 5, 7, 8, 9, 16, 17, 31, 32, 33, 48, 64] * 4, 6, FULL),
+    ("k_gt_n", [2, 3, 4] * 40, 8, FULL),
+    ("symmetric_actions", [4] * 100, 3, FULL + ("action_symmetric",)),
+    ("no_noise_no_dr", [8] * 100, 6, ("floor", "walls", "collisions", "record_knn")),
+])
+def test_single_step_parity(name, sizes, K, features):
+    r = one_step(sizes, K, features, seed=sum(map(ord, name)) % 1000)
+    check_step(r, sizes)
+
+
+def test_single_step_contacts_exercised():
+    """A room-contact-heavy state: many drones start at the floor, walls or
+    ceiling, moving outward, so every contact branch is taken."""
+    sizes = [1] * 2000
+    env, o = pair(sizes, 0, FULL, seed=5, weights=ALL_WEIGHTS)
+    st, prm, goals = seeded_inputs(env, 5, sizes, vel=3.0)
+    rng = np.random.default_rng(5)
+    n = env.D
+    which = rng.integers(0, 4, n)
+    st[which == 0, 2] = 0.0                               # on the floor
+    st[which == 0, 3:6] = 0.0
+    st[which == 1, 2] = rng.uniform(0, 0.01, (which == 1).sum())   # about to hit it
+    st[which == 1, 5] = -2.0
+    st[which == 2, 0] = 4.995                             # at a wall
+    st[which == 2, 3] = 2.0
+    st[which == 3, 2] = 9.995                             # at the ceiling
+    st[which == 3, 5] = 2.0
+    set_both(env, o, st, prm, goals)
+    acts = W.actions(5, 1, n)[0]
+    obs, rew, done = env.step(torch.from_numpy(acts).to(DEV))
+    ev, _ = env.get_events()
+    g = gpu_state(env)
+    oobs, orew, _ = o.step(acts.astype(np.float64))
+    oev, _, margin = o.get_events()
+    keep = margin >= MARGIN_1STEP
+    assert keep.mean() > 0.99
+    ev = ev.cpu().numpy().astype(np.uint32)
+    assert np.array_equal(ev[keep], oev[keep])
+    for bit in (O.EV_HIT_FLOOR, O.EV_ON_FLOOR, O.EV_HIT_WALL, O.EV_HIT_CEIL):
+        assert (oev & bit).sum() > 50
+    s = o.get_state()["state"]
+    assert np.abs(g["state"][keep, 0:6] - s[keep, 0:6]).max() < 2e-5
+    assert np.abs(g["state"][keep, 6:15] - s[keep, 6:15]).max() < 2e-6
+    assert np.allclose(rew.cpu().numpy()[keep], orew[keep], rtol=2e-5, atol=2e-5)
+
+
+# ----------------------------------------------------------------------------- exact discrete decisions
+@pytest.mark.parametrize("dup", [0.0, 0.3])
+def test_neighbours_and_collisions_bit_exact(dup):
+    """Hovering drones at rest keep their binary32 positions through the step,
+    so both sides decide on identical inputs: neighbour lists and collision
+    sets must agree bit for bit, including forced ties (duplicate positions)."""
+    sizes = [2, 3, 5, 7, 8, 9, 16, 31, 32, 33, 64] * 6
+    K = 6
+    feats = ("collisions", "record_knn")
+    env, o = pair(sizes, K, feats, seed=9, alpha_c=1.0)
+    D, E = env.D, env.E
+    st = np.zeros((D, 30), np.float32)
+    st[:, 0:3] = W.clustered_positions(9, sizes, spread=0.08, dup_frac=dup)
+    st[:, 6:15] = np.eye(3, dtype=np.float32).ravel()
+    st[:, 18:22] = np.float32(np.sqrt(0.5))
+    st[:, 26:30] = 0.5
+    prm = np.tile(np.asarray(nominal(env), np.float32), (E, 1))
+    goals = W.random_goals(9, E)
+    set_both(env, o, st, prm, goals)
+    acts = np.full((D, 4), 0.5, np.float32)
+    env.step(torch.from_numpy(acts).to(DEV))
+    ev, knn = env.get_events(knn=True)
+    g = gpu_state(env)
+    o.step(acts.astype(np.float64))
+    oev, oknn, _ = o.get_events()
+    assert np.array_equal(g["state"][:, 0:3], st[:, 0:3])  # positions untouched at binary32
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    bk, bh = O.pairs_f32(st[:, 0:3], prm[:, 6], off, K)
+    knn = knn.cpu().numpy().astype(np.int32)
+    ev = ev.cpu().numpy().astype(np.uint32)
+    assert np.array_equal(knn, bk) and np.array_equal(knn, oknn)
+    assert np.array_equal((ev & O.EV_HIT_QUAD) != 0, bh.astype(bool))
+    assert np.array_equal(ev, oev)
+    assert bh.mean() > 0.3  # the case really has collisions
+
+
+# ----------------------------------------------------------------------------- free running
+def free_run(sizes, K, features, seed, steps, weights, margin_thr):
+    env, o = pair(sizes, K, features, seed=seed, weights=weights)
+    env.reset(seed)
+    o.reset(seed)
+    acts = W.actions(seed, steps, env.D)
+    for t in range(steps):
+        env.step(torch.from_numpy(acts[t]).to(DEV))
+        o.step(acts[t].astype(np.float64))
+    g = gpu_state(env)
+    s = o.get_state()
+    _, _, margin = o.get_events()
+    eo = env_of(sizes)
+    bad_env = np.zeros(len(sizes), bool)
+    np.logical_or.at(bad_env, eo, margin < margin_thr)
+    keep = ~bad_env[eo]
+    dx = np.abs(g["state"][:, 0:3] - s["state"][:, 0:3]).max(1)
+    dR = np.abs(g["state"][:, 6:15] - s["state"][:, 6:15]).max(1)
+    return env, o, keep, dx, dR
+
+
+def test_free_running_tiny_100_steps():
+    """1 env x 1 drone, nominal parameters, noise on: 100 control steps."""
+    w = W.TINY
+    _, _, keep, dx, dR = free_run([1], 0, w.features, w.seed, 100, w.weights, 1e-4)
+    assert keep.all()
+    assert dx.max() <= 1e-4 and dR.max() <= 1e-5
+
+
+@pytest.mark.parametrize("wl,n_envs", [(W.PLAIN, 8192), (W.SWARM, 512)])
+def test_free_running_100_steps(wl, n_envs):
+    """Full-size plain workload (8192 x 1) and a swarm subset (512 x 8, K = 6):
+    after 100 control steps positions within 1e-4 m and rotation entries within
+    1e-5 for every drone whose env never came near a decision threshold."""
+    sizes = [wl.swarm] * n_envs
+    env, o, keep, dx, dR = free_run(sizes, wl.k_neighbors, wl.features, wl.seed, 100, wl.weights, 1e-4)
+    frac = keep.mean()
+    assert frac > 0.85, f"only {frac:.1%} of drones stayed clear of decision thresholds"
+    assert dx[keep].max() <= 1e-4, f"position error {dx[keep].max():.3g}"
+    viol = (dR[keep] > 1e-5).mean()
+    assert viol == 0.0, f"{viol:.3%} of drones exceed 1e-5 in R (max {dR[keep].max():.3g})"
+
+
+def test_plain_1000_steps_invariants():
+    """Full plain workload, 1000 steps on the GPU: rotations stay orthonormal,
+    states stay finite and inside the room, rates within the bound."""
+    wl = W.PLAIN
+    from paper_2306_09537_gb300.env import QuadSwarmEnv
+    env = QuadSwarmEnv(wl.n_envs, 1, 0, wl.features, seed=wl.seed, weights=wl.weights, device=DEV)
+    env.reset(wl.seed)
+    acts = torch.from_numpy(W.actions(wl.seed, wl.steps, env.D)).to(DEV)
+    for t in range(wl.steps):
+        env.step(acts[t])
+    env.sync()
+    s = env.get_state()["state"].double().cpu().numpy()
+    R = s[:, 6:15].reshape(-1, 3, 3)
+    assert np.abs(R @ R.transpose(0, 2, 1) - np.eye(3)).max() < 1e-5
+    assert np.abs(np.linalg.det(R) - 1).max() < 1e-5
+    assert np.isfinite(s).all()
+    assert np.abs(s[:, 0:2]).max() <= 5.0 and s[:, 2].min() >= 0.0 and s[:, 2].max() <= 10.0
+    assert np.abs(s[:, 15:18]).max() <= 40.0 + 3.0
+
+
+# ----------------------------------------------------------------------------- API behaviour
+def test_step_host_equals_step():
+    from paper_2306_09537_gb300 import qs
+    sizes = [8] * 64
+    env, _ = pair(sizes, 6, FULL, seed=3)
+    env2, _ = pair(sizes, 6, FULL, seed=3)
+    acts = W.actions(3, 5, env.D)
+    obs_h = torch.empty(env.D, env.obs_dim).pin_memory()
+    rew_h = torch.empty(env.D).pin_memory()
+    done_h = torch.empty(env.E, dtype=torch.uint8).pin_memory()
+    for t in range(5):
+        a_h = torch.from_numpy(acts[t]).pin_memory()
+        qs.qs_step_host(env2.h, a_h, obs_h, rew_h, done_h)
+        obs, rew, done = env.step(a_h.to(DEV))
+        torch.cuda.synchronize()
+        assert torch.equal(obs.cpu(), obs_h) and torch.equal(rew.cpu(), rew_h) and torch.equal(done.cpu(), done_h)
+
+
+def test_rollout_equals_steps():
+    sizes = [1, 2, 8, 64, 3] * 8
+    env, _ = pair(sizes, 6, FULL, seed=4)
+    env2, _ = pair(sizes, 6, FULL, seed=4)
+    T = 12
+    acts = torch.from_numpy(W.actions(4, T, env.D)).to(DEV)
+    obs = torch.empty(T, env.D, env.obs_dim, device=DEV)
+    rew = torch.empty(T, env.D, device=DEV)
+    done = torch.empty(T, env.E, dtype=torch.uint8, device=DEV)
+    env.rollout(acts, obs, rew, done)
+    for t in range(T):
+        o2, r2, d2 = env2.step(acts[t])
+        assert torch.equal(obs[t], o2) and torch.equal(rew[t], r2) and torch.equal(done[t], d2)
+    assert torch.equal(env.get_state()["state"], env2.get_state()["state"])
+
+
+def test_launch_shape_does_not_change_results():
+    from paper_2306_09537_gb300 import qs
+    sizes = [1] * 100 + [8] * 40 + [64] * 4
+    ref = None
+    for block in (None, 64, 128, 256):
+        env, _ = pair(sizes, 6, FULL, seed=8)
+        if block:
+            for wcls in (1, 8, 64):
+                qs.qs_set_block(env.h, wcls, block)
+            assert qs.qs_get_block(env.h, 8) == block
+        acts = torch.from_numpy(W.actions(8, 3, env.D)).to(DEV)
+        for t in range(3):
+            obs, rew, _ = env.step(acts[t])
+        cur = (obs.clone(), rew.clone(), env.get_state()["state"])
+        if ref is None:
+            ref = cur
+        else:
+            assert all(torch.equal(a, b) for a, b in zip(ref, cur))
+
+
+def test_auto_reset_matches_oracle():
+    sizes = [4] * 50
+    feats = FULL + ("auto_reset",)
+    env, o = pair(sizes, 3, feats, seed=12, episode_steps=3)
+    env.reset(12)
+    o.reset(12)
+    acts = W.actions(12, 4, env.D)
+    for t in range(4):
+        _, _, done = env.step(torch.from_numpy(acts[t]).to(DEV))
+        _, _, odone = o.step(acts[t].astype(np.float64))
+        assert np.array_equal(done.cpu().numpy(), odone)
+    g = gpu_state(env)
+    s = o.get_state()
+    assert (g["ep_step"] == 1).all()
+    assert np.allclose(g["params"], s["params"], rtol=2e-7)
+    assert np.abs(g["goals"] - s["goals"]).max() < 2e-6
+
+
+def test_misaligned_and_null_buffers_rejected():
+    from paper_2306_09537_gb300 import qs
+    env, _ = pair([1] * 8, 0, FULL, seed=1)
+    buf = torch.zeros(8 * 4 + 1, device=DEV)
+    with pytest.raises(qs.QSError) as ei:
+        qs.qs_step(env.h, buf[1:])
+    assert ei.value.status == qs.QS_ERR_ARG
+    with pytest.raises(qs.QSError):
+        qs.qs_step(env.h, None)
+    with pytest.raises(qs.QSError):
+        qs.qs_rollout(env.h, 0, buf[:32])
+
+
+def test_nonfinite_state_reported_by_sync():
+    """Failure detection without a GPU fault: a NaN planted in the state makes
+    the step kernel raise the device status bit, which qs_sync reports."""
+    from paper_2306_09537_gb300 import qs
+    env, _ = pair([1] * 16, 0, FULL, seed=2)
+    s = env.get_state()
+    s["state"][3, 4] = float("nan")
+    env.set_state(state=s["state"])
+    env.step(torch.rand(16, 4, device=DEV))
+    with pytest.raises(qs.QSError) as ei:
+        env.sync()
+    assert ei.value.status == qs.QS_ERR_STATE_NONFINITE
+    env.reset(2)
+    env.step(torch.rand(16, 4, device=DEV))
+    env.sync()
