@@ -92,7 +92,8 @@ def lib():
                                        P(C.c_int32), P(C.c_uint32)]
             L.or_set_state.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double), P(C.c_double),
                                        P(C.c_int32), P(C.c_uint32)]
-            L.or_get_events.argtypes = [C.c_void_p, P(C.c_uint32), P(C.c_int32), P(C.c_double)]
+            L.or_get_events.argtypes = [C.c_void_p, P(C.c_uint32), P(C.c_int32), P(C.c_double), P(C.c_double),
+                                        P(C.c_double)]
             L.or_clear_margin.argtypes = [C.c_void_p]
             L.or_observe.argtypes = [C.c_void_p, P(C.c_double)]
             L.or_pairs_f32.argtypes = [P(C.c_float), P(C.c_float), P(C.c_int32), C.c_int, C.c_int,
@@ -237,8 +238,23 @@ class Oracle:
         ev = np.zeros(self.D, dtype=np.uint32)
         knn = np.zeros((self.D, max(self.K, 1)), dtype=np.int32)
         margin = np.zeros(self.D)
-        lib().or_get_events(self.h, _ptr(ev, C.c_uint32), _ptr(knn, C.c_int32), _ptr(margin, C.c_double))
+        margin_knn = np.zeros(self.D)
+        cond = np.zeros(self.D)
+        lib().or_get_events(self.h, _ptr(ev, C.c_uint32), _ptr(knn, C.c_int32), _ptr(margin, C.c_double),
+                            _ptr(margin_knn, C.c_double), _ptr(cond, C.c_double))
+        self.last_margin_knn = margin_knn
+        self.last_cond = cond
         return ev, knn[:, :self.K], margin
+
+    def margins(self):
+        """(dynamics margin since the last reset/clear, neighbour-order margin of the last step)."""
+        _, _, m = self.get_events()
+        return m, self.last_margin_knn
+
+    def conditioning(self):
+        """Smallest heading-extraction length of any floor reset since the last reset/clear."""
+        self.get_events()
+        return self.last_cond
 
     def clear_margin(self):
         lib().or_clear_margin(self.h)

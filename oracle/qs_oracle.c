@@ -253,16 +253,18 @@ or_env* or_create(const or_config* cfg, const int32_t* swarm_sizes) {
     int K = cfg->k_neighbors > 0 ? cfg->k_neighbors : 1;
     h->knn = (int32_t*)calloc((size_t)D * K, sizeof(int32_t));
     h->margin = (double*)calloc((size_t)D, sizeof(double));
+    h->margin_knn = (double*)calloc((size_t)D, sizeof(double));
+    h->cond = (double*)calloc((size_t)D, sizeof(double));
     h->key[0] = (uint32_t)(cfg->seed & 0xffffffffu);
     h->key[1] = (uint32_t)(cfg->seed >> 32);
-    for (int d = 0; d < D; ++d) h->margin[d] = INFINITY;
+    for (int d = 0; d < D; ++d) h->margin[d] = h->margin_knn[d] = h->cond[d] = INFINITY;
     return h;
 }
 
 void or_destroy(or_env* h) {
     if (!h) return;
     free(h->env_off); free(h->prm); free(h->goal); free(h->st); free(h->ep_t); free(h->tick);
-    free(h->ev); free(h->knn); free(h->margin); free(h);
+    free(h->ev); free(h->knn); free(h->margin); free(h->margin_knn); free(h->cond); free(h);
 }
 
 int or_n_drones(const or_env* h) { return h->n_drones; }
@@ -356,7 +358,7 @@ void or_reset(or_env* h, uint64_t seed, const uint8_t* mask) {
         for (int e = 0; e < h->cfg.n_envs; ++e)
             if (mask[e]) reset_env_all(h, key, h->tick[e], OR_TAG_RESET_ENV, OR_TAG_RESET_DRONE, e);
     }
-    for (int d = 0; d < h->n_drones; ++d) { h->ev[d] = 0; h->margin[d] = INFINITY; }
+    for (int d = 0; d < h->n_drones; ++d) { h->ev[d] = 0; h->margin[d] = h->margin_knn[d] = h->cond[d] = INFINITY; }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -543,6 +545,9 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
             x[2] = 0.0;
             for (int k = 0; k < 3; ++k) { v[k] = 0.0; w[k] = 0.0; }
             double cs, sn, hyp = sqrt(R[0] * R[0] + R[3] * R[3]);
+            /* the heading is read off the horizontal part of the body x-axis, of
+             * length hyp: an error e in R becomes about e / hyp in the heading */
+            if (hyp < h->cond[d]) h->cond[d] = hyp;
             if (hyp >= 1e-6) { cs = R[0] / hyp; sn = R[3] / hyp; }
             else { double h2 = sqrt(R[1] * R[1] + R[4] * R[4]); cs = R[4] / h2; sn = -R[1] / h2; }
             double Rz[9] = {cs, -sn, 0.0, sn, cs, 0.0, 0.0, 0.0, 1.0};
@@ -550,21 +555,30 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
         }
     }
 
-    /* S8: walls x = +-hx, y = +-hy and ceiling z = H. The quad-quad rule with a
-     * static partner: the normal velocity component is removed (not
-     * reflected), then v <- alpha_c (v + eps_v), w <- w + eps_w; the position is
-     * clamped back onto the boundary. */
+    /* S8: walls x = +-hx, y = +-hy and ceiling z = H. A drone past a boundary
+     * is put back onto it. If it was moving outward, the quad-quad rule with a
+     * static partner applies: the normal velocity component is removed (not
+     * reflected), then v <- alpha_c (v + eps_v), w <- w + eps_w. (A drone whose
+     * velocity the floor rule just zeroed is clamped without a response.) */
     if (c->flags & OR_F_WALLS) {
         int hit_wall = 0, hit_ceil = 0;
         const double lim[2] = {c->room_hx, c->room_hy};
         for (int k = 0; k < 2; ++k) {
             note_cmp(h, d, x[k], lim[k]);
             note_cmp(h, d, x[k], -lim[k]);
-            if (x[k] > lim[k] && v[k] > 0.0) { v[k] = 0.0; x[k] = lim[k]; hit_wall = 1; }
-            else if (x[k] < -lim[k] && v[k] < 0.0) { v[k] = 0.0; x[k] = -lim[k]; hit_wall = 1; }
+            if (x[k] > lim[k]) {
+                if (v[k] > 0.0) { v[k] = 0.0; hit_wall = 1; }
+                x[k] = lim[k];
+            } else if (x[k] < -lim[k]) {
+                if (v[k] < 0.0) { v[k] = 0.0; hit_wall = 1; }
+                x[k] = -lim[k];
+            }
         }
         note_cmp(h, d, x[2], c->room_h);
-        if (x[2] > c->room_h && v[2] > 0.0) { v[2] = 0.0; x[2] = c->room_h; hit_ceil = 1; }
+        if (x[2] > c->room_h) {
+            if (v[2] > 0.0) { v[2] = 0.0; hit_ceil = 1; }
+            x[2] = c->room_h;
+        }
         if (hit_wall || hit_ceil) {
             double n[6];
             draw_six_normals(h, h->tick[e], (uint32_t)d, OR_TAG_WALL, (uint32_t)sub, n);
@@ -621,11 +635,15 @@ static void knn_env(or_env* h, int d0, int N, int keff, const float* xf, int32_t
             if (j != i) { items[m].key = f32_bits(or_pair_key(xf + 3 * i, xf + 3 * j)); items[m].j = j; ++m; }
         qsort(items, (size_t)m, sizeof(knn_item), knn_cmp);
         for (int k = 0; k < keff; ++k) nbr[i * keff + k] = items[k].j;
-        /* near-ties at the ranks that matter (including the K-th vs the next) */
+        /* near-ties at the ranks that matter (including the K-th vs the next);
+         * they change only the observation, so they have their own margin */
+        h->margin_knn[d0 + i] = INFINITY;
         for (int k = 0; k < keff && k + 1 < m; ++k) {
             float ka, kb; uint32_t ua = items[k].key, ub = items[k + 1].key;
             memcpy(&ka, &ua, 4); memcpy(&kb, &ub, 4);
-            note_cmp(h, d0 + i, (double)kb, (double)ka);
+            double den = fmax((double)ka, (double)kb);
+            double mk = den > 0.0 ? ((double)kb - (double)ka) / den : 0.0;
+            if (mk < h->margin_knn[d0 + i]) h->margin_knn[d0 + i] = mk;
         }
     }
     free(items);
@@ -893,7 +911,9 @@ void or_set_state(or_env* h, const double* st, const double* prm, const double* 
     if (tick) memcpy(h->tick, tick, sizeof(uint32_t) * (size_t)h->cfg.n_envs);
 }
 
-void or_get_events(const or_env* h, uint32_t* ev, int32_t* knn, double* margin) {
+void or_get_events(const or_env* h, uint32_t* ev, int32_t* knn, double* margin, double* margin_knn, double* cond) {
+    if (cond) memcpy(cond, h->cond, sizeof(double) * (size_t)h->n_drones);
+    if (margin_knn) memcpy(margin_knn, h->margin_knn, sizeof(double) * (size_t)h->n_drones);
     if (ev) memcpy(ev, h->ev, sizeof(uint32_t) * (size_t)h->n_drones);
     if (knn && h->cfg.k_neighbors > 0)
         memcpy(knn, h->knn, sizeof(int32_t) * (size_t)h->n_drones * h->cfg.k_neighbors);
@@ -901,7 +921,7 @@ void or_get_events(const or_env* h, uint32_t* ev, int32_t* knn, double* margin) 
 }
 
 void or_clear_margin(or_env* h) {
-    for (int d = 0; d < h->n_drones; ++d) h->margin[d] = INFINITY;
+    for (int d = 0; d < h->n_drones; ++d) h->margin[d] = h->cond[d] = INFINITY;
 }
 
 /* Standalone canonical KNN / collision set on given binary32 positions

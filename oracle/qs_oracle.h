@@ -89,7 +89,9 @@ typedef struct {
     int32_t* ep_t;     /* [E] control steps since the env's episode began */
     uint32_t* ev;      /* [D] event bits of the last step */
     int32_t* knn;      /* [D][K] neighbour local indices of the last step (-1 padded) */
-    double* margin;    /* [D] smallest normalised distance of any decision to its threshold */
+    double* margin;    /* [D] smallest normalised distance of a dynamics decision to its threshold */
+    double* margin_knn; /* [D] smallest relative gap between ranked neighbour keys, last step */
+    double* cond;      /* [D] smallest heading-extraction length of a floor reset (conditioning) */
     uint32_t* tick;    /* [E] control steps since the last full reset (Philox counter word 0) */
     uint32_t key[2];
 } or_env;
@@ -109,7 +111,7 @@ void or_observe(or_env* h, double* obs);
 void or_get_state(const or_env* h, double* st, double* prm, double* goal, int32_t* ep_t, uint32_t* tick);
 void or_set_state(or_env* h, const double* st, const double* prm, const double* goal, const int32_t* ep_t,
                   const uint32_t* tick);
-void or_get_events(const or_env* h, uint32_t* ev, int32_t* knn, double* margin);
+void or_get_events(const or_env* h, uint32_t* ev, int32_t* knn, double* margin, double* margin_knn, double* cond);
 void or_clear_margin(or_env* h);
 void or_pairs_f32(const float* pos, const float* arm, const int32_t* env_off, int n_envs, int K,
                   int32_t* knn, uint8_t* hit);

@@ -130,8 +130,12 @@ __device__ __forceinline__ void draw_env(const Consts& c, uint32_t k0, uint32_t 
 }
 
 // ---------------------------------------------------------------- drone state
+// w + wlo is the body rate carried at about twice binary32 precision: adding
+// the per-substep increment dt * dw/dt (~1e-2) onto |w| up to 40 rad/s would
+// otherwise lose up to ulp(40)/2 per substep, an error that the attitude
+// integrates (Kahan's compensated summation keeps the lost low-order bits).
 struct Drone {
-    float x[3], v[3], R[9], w[3], uf[4], eps[4], fp[4];
+    float x[3], v[3], R[9], w[3], uf[4], eps[4], fp[4], wlo[3];
 };
 
 __device__ __forceinline__ void unpack(Drone& s, const float4 q[NPLANE]) {
@@ -143,6 +147,7 @@ __device__ __forceinline__ void unpack(Drone& s, const float4 q[NPLANE]) {
     for (int k = 0; k < 4; ++k) s.uf[k] = f[18 + k];
     for (int k = 0; k < 4; ++k) s.eps[k] = f[22 + k];
     for (int k = 0; k < 4; ++k) s.fp[k] = f[26 + k];
+    for (int k = 0; k < 3; ++k) s.wlo[k] = f[32 + k];
 }
 
 __device__ __forceinline__ void pack(const Drone& s, float4 q[NPLANE]) {
@@ -156,6 +161,16 @@ __device__ __forceinline__ void pack(const Drone& s, float4 q[NPLANE]) {
     for (int k = 0; k < 4; ++k) f[26 + k] = s.fp[k];
     f[30] = 0.0f;
     f[31] = 0.0f;
+    for (int k = 0; k < 3; ++k) f[32 + k] = s.wlo[k];
+    f[35] = 0.0f;
+}
+
+// hi + lo <- hi + lo + delta, keeping the rounding error of the sum in lo.
+__device__ __forceinline__ void comp_add(float& hi, float& lo, float delta) {
+    const float y = delta + lo;
+    const float t = hi + y;
+    lo = y - (t - hi);
+    hi = t;
 }
 
 __device__ __forceinline__ void load_drone(Drone& s, const float4* __restrict__ st, int D, int d) {
@@ -204,6 +219,7 @@ __device__ __forceinline__ void draw_drone(const Consts& c, uint32_t k0, uint32_
     s.w[0] = -1.0f + 2.0f * u01(q.y);
     s.w[1] = -1.0f + 2.0f * u01(q.z);
     s.w[2] = -1.0f + 2.0f * u01(q.w);
+    s.wlo[0] = s.wlo[1] = s.wlo[2] = 0.0f;
     const float hov = 1.0f / t2w;
     const float uh = sqrtf(hov);
     for (int r = 0; r < 4; ++r) {
@@ -235,7 +251,7 @@ __device__ __forceinline__ float softplus_b(float u, float beta) {
 // R <- R (3I - R^T R) / 2 then removes the binary32 drift of R itself.
 __device__ __forceinline__ void rotate_polar(float R[9], const float w[3], float dt) {
     const float n2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    const float cc = rsqrtf(fmaf(dt * dt, n2, 1.0f));
+    const float cc = __frsqrt_rn(fmaf(dt * dt, n2, 1.0f));  // correctly rounded: no drift of the angle
     const float a = dt * cc;
     const float b = dt * dt * cc * cc / (1.0f + cc);
 #pragma unroll
@@ -350,9 +366,15 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     s.x[0] = fmaf(s.v[0], dt, s.x[0]);
     s.x[1] = fmaf(s.v[1], dt, s.x[1]);
     s.x[2] = fmaf(s.v[2], dt, s.x[2]);
-    s.w[0] = fminf(fmaxf(fmaf(wd0, dt, s.w[0]), -c.omega_max), c.omega_max);
-    s.w[1] = fminf(fmaxf(fmaf(wd1, dt, s.w[1]), -c.omega_max), c.omega_max);
-    s.w[2] = fminf(fmaxf(fmaf(wd2, dt, s.w[2]), -c.omega_max), c.omega_max);
+    const float wd[3] = {wd0, wd1, wd2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        comp_add(s.w[k], s.wlo[k], wd[k] * dt);
+        if (fabsf(s.w[k]) > c.omega_max) {
+            s.w[k] = copysignf(c.omega_max, s.w[k]);
+            s.wlo[k] = 0.0f;
+        }
+    }
     rotate_polar(s.R, s.w, dt);
 
     if (c.flags & QS_F_SMOOTH) {
@@ -368,6 +390,7 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
         for (int k = 0; k < 3; ++k) {
             s.v[k] = 0.0f;
             s.w[k] = 0.0f;
+            s.wlo[k] = 0.0f;
         }
         float cs, sn;
         const float h2 = s.R[0] * s.R[0] + s.R[3] * s.R[3];
@@ -384,21 +407,35 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
         s.R[3] = sn; s.R[4] = cs;  s.R[5] = 0.0f;
         s.R[6] = 0.0f; s.R[7] = 0.0f; s.R[8] = 1.0f;
     }
-    // S8 walls and ceiling: remove the normal velocity, clamp, then
+    // S8 walls and ceiling: a drone past a boundary is put back onto it; if it
+    // was moving outward its normal velocity is removed and
     // v <- alpha_c (v + eps_v), w <- w + eps_w
     if (c.flags & QS_F_WALLS) {
         bool wall = false, ceil = false;
-        if (s.x[0] > c.room_hx && s.v[0] > 0.0f) { s.v[0] = 0.0f; s.x[0] = c.room_hx; wall = true; }
-        else if (s.x[0] < -c.room_hx && s.v[0] < 0.0f) { s.v[0] = 0.0f; s.x[0] = -c.room_hx; wall = true; }
-        if (s.x[1] > c.room_hy && s.v[1] > 0.0f) { s.v[1] = 0.0f; s.x[1] = c.room_hy; wall = true; }
-        else if (s.x[1] < -c.room_hy && s.v[1] < 0.0f) { s.v[1] = 0.0f; s.x[1] = -c.room_hy; wall = true; }
-        if (s.x[2] > c.room_h && s.v[2] > 0.0f) { s.v[2] = 0.0f; s.x[2] = c.room_h; ceil = true; }
+        if (s.x[0] > c.room_hx) {
+            if (s.v[0] > 0.0f) { s.v[0] = 0.0f; wall = true; }
+            s.x[0] = c.room_hx;
+        } else if (s.x[0] < -c.room_hx) {
+            if (s.v[0] < 0.0f) { s.v[0] = 0.0f; wall = true; }
+            s.x[0] = -c.room_hx;
+        }
+        if (s.x[1] > c.room_hy) {
+            if (s.v[1] > 0.0f) { s.v[1] = 0.0f; wall = true; }
+            s.x[1] = c.room_hy;
+        } else if (s.x[1] < -c.room_hy) {
+            if (s.v[1] < 0.0f) { s.v[1] = 0.0f; wall = true; }
+            s.x[1] = -c.room_hy;
+        }
+        if (s.x[2] > c.room_h) {
+            if (s.v[2] > 0.0f) { s.v[2] = 0.0f; ceil = true; }
+            s.x[2] = c.room_h;
+        }
         if (wall || ceil) {
             float n[6];
             six_normals(c, tick, (uint32_t)d, TAG_WALL, (uint32_t)sub, n);
             for (int k = 0; k < 3; ++k) {
                 s.v[k] = c.alpha_c * fmaf(c.sig_cv, n[k], s.v[k]);
-                s.w[k] = fmaf(c.sig_cw, n[3 + k], s.w[k]);
+                comp_add(s.w[k], s.wlo[k], c.sig_cw * n[3 + k]);
             }
             ev |= (wall ? EV_HIT_WALL : 0u) | (ceil ? EV_HIT_CEIL : 0u);
         }

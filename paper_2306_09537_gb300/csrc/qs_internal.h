@@ -22,8 +22,11 @@ enum Tag : uint32_t {
     TAG_AUTO_ENV = 7, TAG_AUTO_DRONE = 8
 };
 
-// Number of float4 planes of the drone state: 30 floats -> 8 float4 (2 pad).
-constexpr int NPLANE = 8;
+// Number of float4 planes of the drone state: the 30 public floats fill
+// planes 0..7 (2 pad); plane 8 holds the low-order parts of the body rates
+// (compensated accumulation, see Drone::wlo) and 1 pad.
+constexpr int NPLANE = 9;
+constexpr int NPLANE_PUBLIC = 8;
 
 // Model constants, passed by value to every kernel.
 struct Consts {

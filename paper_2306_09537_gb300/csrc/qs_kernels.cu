@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_step(const Consts c, const Dev dv
             s.v[0] = c.alpha_c * (s.v[0] + dvs0 + c.sig_cv * n[0]);
             s.v[1] = c.alpha_c * (s.v[1] + dvs1 + c.sig_cv * n[1]);
             s.v[2] = c.alpha_c * (s.v[2] + dvs2 + c.sig_cv * n[2]);
-            s.w[0] = fmaf(c.sig_cw, n[3], s.w[0]);
-            s.w[1] = fmaf(c.sig_cw, n[4], s.w[1]);
-            s.w[2] = fmaf(c.sig_cw, n[5], s.w[2]);
+            comp_add(s.w[0], s.wlo[0], c.sig_cw * n[3]);
+            comp_add(s.w[1], s.wlo[1], c.sig_cw * n[4]);
+            comp_add(s.w[2], s.wlo[2], c.sig_cw * n[5]);
         }
         __syncthreads();
         if (act) {  // post-collision velocities for the neighbour observation
@@ -328,8 +328,7 @@ __global__ void k_set_drones(const Dev dv, const float* __restrict__ in) {
     float4 q[NPLANE];
     float* f = reinterpret_cast<float*>(q);
     for (int k = 0; k < QS_STATE_DIM; ++k) f[k] = in[(size_t)d * QS_STATE_DIM + k];
-    f[30] = 0.f;
-    f[31] = 0.f;
+    for (int k = QS_STATE_DIM; k < 4 * NPLANE; ++k) f[k] = 0.f;  // pads and body-rate low parts
     for (int p = 0; p < NPLANE; ++p) dv.st[(size_t)p * dv.D + d] = q[p];
 }
 
