@@ -1,0 +1,300 @@
+"""Benchmark of the QuadSwarm forward-dynamics step on GB300.
+
+One benchmark step = one 100 Hz control step of every drone of the plain
+workload (8192 envs x 1 quadrotor, per-env randomisation, room contacts,
+motor and sensor noise, goal-reaching reward), i.e. one qs_step call. The
+metric is quadrotor-steps/s (the paper's "simulation samples per second",
+Sec. IV). Inputs (the per-step command stream) are resident in device memory
+before the timed region; L2 is flushed between timed steps and each step is
+timed with CUDA events on the handle's stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gpu,reference}]
+
+--impl reference times the FP64 CPU oracle (the only reference this build
+has) on the host cores for the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2306_09537_gb300 import workloads as W  # noqa: E402
+
+METRIC = "quadrotor-steps/sec on 1 GB300 (plain vs batched vs fwd+adjoint), % of roofline"
+UNIT = "quadrotor-steps/s"
+WL = W.PLAIN
+BENCH_FEATURES = WL.features + ("auto_reset",)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+# Algorithmic cost of one quadrotor-step of the per-call form (state in HBM
+# between calls); see the design notes for the derivation.
+def algorithmic_bytes(D, E, obs_dim):
+    per_drone = 2 * 120 + 16 + 4 * obs_dim + 4 + 4          # state r+w, action, obs, reward, events
+    per_env = 7 * 4 + 3 * 4 + 2 * 4 + 2 * 4 + 1               # params, goal, episode step r+w, tick r+w, done
+    return D * per_drone + E * per_env
+
+
+OPS_PER_QUAD_STEP_N1 = 1080  # FP32/INT32 lane operations, 2 substeps, N = 1 (derivation in the design notes)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU oracle legs
+def oracle_run(steps, n_envs=None, threads=None, seed=None):
+    """Runs the oracle on the bench workload; returns (quad-steps/s, cores, sample)."""
+    from oracle import oracle as O
+    flags = 0
+    names = {"dr": O.F_DR, "motor_noise": O.F_MOTOR_NOISE, "obs_noise": O.F_OBS_NOISE, "collisions": O.F_COLLISIONS,
+             "floor": O.F_FLOOR, "walls": O.F_WALLS, "auto_reset": O.F_AUTO_RESET}
+    for f in BENCH_FEATURES:
+        flags |= names[f]
+    E = n_envs or WL.n_envs
+    oc = O.default_config(n_envs=E, k_neighbors=WL.k_neighbors, flags=flags, seed=seed or WL.seed)
+    oc.w[:] = [0.0] * 14
+    O.set_config(oc, weights=WL.weights)
+    o = O.Oracle(oc)
+    o.reset(seed or WL.seed)
+    period = min(steps, 100)
+    acts = W.actions(WL.seed, period, o.D).astype(np.float64)
+    cores = threads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    for t in range(steps):
+        o.step(acts[t % period], n_threads=cores)
+    dt = time.perf_counter() - t0
+    return o.D * steps / dt, cores, f"{E} envs x {steps} control steps of the plain workload, binary64, {cores} threads"
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    # each bench step = one control step of all 8192 envs on the oracle
+    from oracle import oracle as O  # noqa: F401
+    oracle_run(max(1, args.warmup))
+    v, cores, sample = oracle_run(args.steps)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": WL.n_envs / v * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WL.name, "n_envs": WL.n_envs, "swarm": 1, "k_neighbors": WL.k_neighbors,
+                       "features": list(BENCH_FEATURES)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU leg
+def run_gpu(args, world, rank, local):
+    import torch
+
+    from paper_2306_09537_gb300 import qs
+    from paper_2306_09537_gb300.env import QuadSwarmEnv
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    seed = WL.seed + 1000 * rank  # each rank simulates its own envs (weak scaling)
+    with torch.cuda.stream(stream):
+        env = QuadSwarmEnv(WL.n_envs, 1, WL.k_neighbors, BENCH_FEATURES, seed=seed, weights=WL.weights, device=dev,
+                           stream=stream)
+        env.reset(seed)
+        steps, warm = args.steps, args.warmup
+        period = min(steps + warm, 1000)
+        acts = torch.from_numpy(W.actions(seed, period, env.D)).to(dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        n_classes = 1
+        for t in range(warm):
+            env.step(acts[t % period])
+        stream.synchronize()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            t_wall = time.perf_counter()
+            for t in range(steps):
+                flush.zero_()
+                ev0[t].record(stream)
+                env.step(acts[(warm + t) % period])
+                ev1[t].record(stream)
+            stream.synchronize()
+            t_wall = time.perf_counter() - t_wall
+        barrier(world)
+        torch.cuda.synchronize()
+        per = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])  # ms
+        total_ms = max_over_ranks(float(per.sum()), world)
+        env.sync()
+
+        # end to end through the host-buffer entry point (pinned memory)
+        a_host = torch.from_numpy(W.actions(seed + 1, 64, env.D)).pin_memory()
+        obs_h = torch.empty(env.D, env.obs_dim).pin_memory()
+        rew_h = torch.empty(env.D).pin_memory()
+        done_h = torch.empty(env.E, dtype=torch.uint8).pin_memory()
+        e2e_steps = min(steps, 500)
+        for t in range(3):
+            qs.qs_step_host(env.h, a_host[t % 64], obs_h, rew_h, done_h)
+        barrier(world)
+        t0 = time.perf_counter()
+        for t in range(e2e_steps):
+            qs.qs_step_host(env.h, a_host[t % 64], obs_h, rew_h, done_h)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+
+    D, E, od = env.D, env.E, env.obs_dim
+    value = world * D * steps / (total_ms * 1e-3)
+    hbm, sm_max, src = peaks()
+    launch_s = float(per.mean()) * 1e-3
+    ab = algorithmic_bytes(D, E, od)
+    ach_gbs = ab / launch_s / 1e9
+    ops = OPS_PER_QUAD_STEP_N1 * D
+    alu_peak = 152 * 128 * sm_max * 1e6 / 1e9  # G lane-ops/s
+    ach_gops = ops / launch_s / 1e9
+    t_hbm, t_alu = ab / (hbm * 1e9), ops / (alu_peak * 1e9)
+    if t_hbm >= t_alu:
+        roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm,
+                "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs" if src == "measured" else "fallback 6.8 TB/s"}
+    else:
+        roof = {"bound": "alu", "achieved": ach_gops, "peak": alu_peak, "unit": "Gop/s", "frac": ach_gops / alu_peak,
+                "peak_source": "152 SMs x 128 FP32/INT32 lanes x max SM clock"}
+    roof.update({"kernel": "qsk::k_step<1>", "traffic": None, "algorithmic_bytes_per_launch": ab,
+                 "algorithmic_ops_per_launch": ops,
+                 "alt": {"hbm_frac": ach_gbs / hbm, "alu_frac": ach_gops / alu_peak}})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warm,
+            "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WL.name, "n_envs": WL.n_envs, "swarm": 1, "k_neighbors": WL.k_neighbors,
+                       "features": list(BENCH_FEATURES), "form": "per-call qs_step, state in HBM",
+                       "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "e2e": {"value": world * D * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": D * 16,
+                    "d2h_bytes_per_step": D * od * 4 + D * 4 + E},
+            "gpu_launches": steps * n_classes, "roofline": roof,
+            "clocks": clk.summary(), "wall_s_timed": t_wall}
+    env.close()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    line = run_gpu(args, world, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            v, cores, sample = oracle_run(200)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
