@@ -171,12 +171,25 @@ qs_status qs_step(qs_env* h, const float* actions_dev, float* obs_dev, float* re
 qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, float* reward_host,
                        uint8_t* done_host);
 
-/* T control steps in one persistent launch (T >= 1): actions_dev [T][D][4],
+/* T control steps (T >= 1) of every env, batched: actions_dev [T][D][4],
  * obs_dev [T][D][obs_dim], reward_dev [T][D], done_dev [T][E] (outputs
- * nullable). Each drone's state stays in registers across the T steps; the
- * results equal T calls of qs_step. */
+ * nullable). Results equal T calls of qs_step. One persistent launch covers
+ * envs of every swarm size: its CTAs take tiles of envs from a work counter
+ * (largest swarms first) and keep each drone's state in registers across the
+ * steps of a launch. The T steps run as ceil(T / fuse) launches (see
+ * qs_set_rollout_shape). On a non-default stream the launches are captured
+ * into a CUDA graph on the first call and replayed while T, the buffers and
+ * the shape stay the same. Not callable during a caller's own stream capture
+ * when a (re)capture is needed. */
 qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_dev, float* reward_dev,
                      uint8_t* done_dev);
+
+/* Launch shape of qs_rollout: `block` threads per CTA (32..256, a multiple of
+ * 32, at least the widest swarm class), `fuse` control steps per launch
+ * (0 = all T steps in one launch), `use_graph` (0/1). Results do not depend
+ * on the shape. Used by the autotuner. */
+qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t use_graph);
+qs_status qs_get_rollout_shape(const qs_env* h, int32_t* block, int32_t* fuse, int32_t* use_graph);
 
 /* Copies the handle's state into caller buffers (each nullable): state_dev
  * [D][30], params_dev [E][7], goals_dev [E][3], ep_step_dev [E] control steps

@@ -32,6 +32,19 @@ struct qs_env {
     Tile* d_tiles = nullptr;
     int* d_perm = nullptr;
     void* arena = nullptr;
+    // rollout: one tile table over all classes (costliest first), launch shape
+    Tile* d_rtiles = nullptr;
+    int n_rtiles = 0;
+    int rollout_block = 128;
+    int rollout_fuse = 0;   // control steps per launch (0: all T in one launch)
+    int rollout_grid = 0;   // resident CTAs for rollout_block
+    int use_graph = 1;
+    int* d_counter = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    struct {
+        int T, fuse, block;
+        const void *a, *o, *r, *d;
+    } graph_key{};
     // device staging of qs_step_host (one allocation, made on first use)
     char* stage = nullptr;
     size_t st_obs = 0, st_rew = 0, st_done = 0;
@@ -116,10 +129,29 @@ void build_tiles(qs_env* h, std::vector<Tile>& tiles) {
         cp.tile_off = (int)tiles.size();
         cp.n_tiles = 0;
         for (int s = 0; s < h->class_slots[ci]; s += per) {
-            tiles.push_back(Tile{h->class_first_slot[ci] + s, std::min(per, h->class_slots[ci] - s)});
+            tiles.push_back(Tile{h->class_first_slot[ci] + s, std::min(per, h->class_slots[ci] - s), cp.W, 0});
             ++cp.n_tiles;
         }
     }
+}
+
+// Rollout tiles: every class cut into tiles of rollout_block threads, widest
+// class first (its tiles cost the most: the pair pass is O(N^2)), so that the
+// persistent CTAs take the long tiles before the short ones.
+void build_rollout_tiles(qs_env* h, std::vector<Tile>& tiles) {
+    tiles.clear();
+    for (int ci = (int)h->plan.size() - 1; ci >= 0; --ci) {
+        const int W = h->plan[ci].W;
+        const int per = h->rollout_block / W;
+        for (int s = 0; s < h->class_slots[ci]; s += per)
+            tiles.push_back(Tile{h->class_first_slot[ci] + s, std::min(per, h->class_slots[ci] - s), W, 0});
+    }
+}
+
+void drop_graph(qs_env* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_key = {};
 }
 
 // Default launch shape: enough CTAs to cover 2 x 152 SMs when the class has
@@ -132,14 +164,33 @@ int default_block(int W, int slots) {
 }
 
 qs_status upload_tiles(qs_env* h) {
-    std::vector<Tile> tiles;
+    std::vector<Tile> tiles, rtiles;
     build_tiles(h, tiles);
+    build_rollout_tiles(h, rtiles);
+    drop_graph(h);
     if (h->d_tiles) cudaFree(h->d_tiles);
     h->d_tiles = nullptr;
-    cudaError_t e = cudaMalloc(&h->d_tiles, sizeof(Tile) * std::max<size_t>(tiles.size(), 1));
+    h->d_rtiles = nullptr;
+    const size_t n = tiles.size() + rtiles.size();
+    cudaError_t e = cudaMalloc(&h->d_tiles, sizeof(Tile) * std::max<size_t>(n, 1));
     if (e != cudaSuccess) return fail(h, QS_ERR_OOM, "tile table allocation failed");
-    e = cudaMemcpy(h->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice);
+    tiles.insert(tiles.end(), rtiles.begin(), rtiles.end());
+    e = cudaMemcpy(h->d_tiles, tiles.data(), sizeof(Tile) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(h, e, "tile table upload");
+    h->d_rtiles = h->d_tiles + (n - rtiles.size());
+    h->n_rtiles = (int)rtiles.size();
+    h->rollout_grid = rollout_grid(h->rollout_block);
+    return QS_OK;
+}
+
+// Enqueues the rollout of T steps: ceil(T / fuse) persistent launches.
+qs_status enqueue_rollout(qs_env* h, int T, const RolloutIO& io) {
+    const int fuse = h->rollout_fuse > 0 ? h->rollout_fuse : T;
+    for (int t0 = 0; t0 < T; t0 += fuse) {
+        cudaError_t e = launch_rollout(h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm, h->d_counter,
+                                       io, t0, std::min(fuse, T - t0), h->rollout_grid, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "rollout launch");
+    }
     return QS_OK;
 }
 
@@ -281,7 +332,7 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
                  o_tick = take(sizeof(uint32_t) * E), o_off = take(sizeof(int32_t) * (E + 1)),
                  o_of = take(sizeof(int32_t) * D), o_ev = take(sizeof(uint32_t) * D),
                  o_knn = take(rec ? sizeof(int16_t) * h->K * D : 0), o_status = take(sizeof(int32_t)),
-                 o_perm = take(sizeof(int) * E);
+                 o_perm = take(sizeof(int) * E), o_cnt = take(sizeof(int));
     cudaError_t ce = cudaMalloc(&h->arena, off);
     if (ce != cudaSuccess) {
         delete h;
@@ -301,6 +352,7 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
     h->dv.D = h->D;
     h->dv.E = h->E;
     h->d_perm = (int*)(base + o_perm);
+    h->d_counter = (int*)(base + o_cnt);
     bool ok = cudaMemset(h->arena, 0, off) == cudaSuccess &&
               cudaMemcpy((void*)h->dv.env_off, h->env_off_h.data(), sizeof(int32_t) * (E + 1), cudaMemcpyHostToDevice) ==
                   cudaSuccess &&
@@ -333,6 +385,7 @@ qs_status qs_destroy(qs_env* h) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_destroy: NULL handle");
     DeviceGuard g(h->device);
     cudaStreamSynchronize(h->stream);
+    drop_graph(h);
     cudaFree(h->d_tiles);
     cudaFree(h->arena);
     cudaFree(h->stage);
@@ -420,12 +473,59 @@ qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_
     if (!actions_dev || !aligned(actions_dev, 16)) return fail(h, QS_ERR_ARG, "qs_rollout: actions_dev NULL or misaligned");
     if (obs_dev && !aligned(obs_dev, 8)) return fail(h, QS_ERR_ARG, "qs_rollout: obs_dev must be 8-byte aligned");
     DeviceGuard g(h->device);
-    const size_t D = h->D, E = h->E;
-    for (int t = 0; t < T; ++t) {
-        qs_status s = do_step(h, actions_dev + (size_t)t * D * 4, obs_dev ? obs_dev + (size_t)t * D * h->obs_dim : nullptr,
-                              reward_dev ? reward_dev + (size_t)t * D : nullptr, done_dev ? done_dev + (size_t)t * E : nullptr);
-        if (s != QS_OK) return s;
+    const RolloutIO io{actions_dev, obs_dev, reward_dev, done_dev};
+    // Graph replay: the launches of one (T, buffers, shape) are captured once
+    // and replayed; any change of buffers or shape re-captures. The legacy
+    // default stream cannot be captured, so it launches directly.
+    if (!h->use_graph || h->stream == nullptr) return enqueue_rollout(h, T, io);
+    const auto& k = h->graph_key;
+    if (h->graph && k.T == T && k.fuse == h->rollout_fuse && k.block == h->rollout_block && k.a == actions_dev &&
+        k.o == obs_dev && k.r == reward_dev && k.d == done_dev) {
+        cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+        return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "rollout graph launch");
     }
+    drop_graph(h);
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rollout capture begin");
+    qs_status s = enqueue_rollout(h, T, io);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->stream, &graph);
+    if (s != QS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "rollout capture end");
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return cuda_fail(h, e, "rollout graph instantiate");
+    }
+    h->graph_key = {T, h->rollout_fuse, h->rollout_block, actions_dev, obs_dev, reward_dev, done_dev};
+    e = cudaGraphLaunch(h->graph, h->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "rollout graph launch");
+}
+
+qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t use_graph) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_set_rollout_shape: NULL handle");
+    int maxW = 1;
+    for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
+    if (block < 32 || block > 256 || block % 32 != 0 || block < maxW || fuse < 0)
+        return fail(h, QS_ERR_ARG, "qs_set_rollout_shape: block must be 32..256, a multiple of 32, >= the widest class; fuse >= 0");
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->stream);  // the old tables may be in use
+    if (e != cudaSuccess) return cuda_fail(h, e, "qs_set_rollout_shape");
+    h->rollout_block = block;
+    h->rollout_fuse = fuse;
+    h->use_graph = use_graph ? 1 : 0;
+    return upload_tiles(h);
+}
+
+qs_status qs_get_rollout_shape(const qs_env* h, int32_t* block, int32_t* fuse, int32_t* use_graph) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_get_rollout_shape: NULL handle");
+    if (block) *block = h->rollout_block;
+    if (fuse) *fuse = h->rollout_fuse;
+    if (use_graph) *use_graph = h->use_graph;
     return QS_OK;
 }
 

@@ -60,6 +60,8 @@ struct Dev {
 struct Tile {
     int first;  // first slot (index into perm)
     int count;  // slots in this tile
+    int W;      // width class of its slots
+    int pad;
 };
 
 struct ClassPlan {
@@ -78,9 +80,25 @@ struct StepIO {
     uint8_t* done;     // [E] or null
 };
 
-// kernels (qs_kernels.cu)
+// [T][...] buffers of a rollout (outputs nullable).
+struct RolloutIO {
+    const float* act;  // [T][D][4]
+    float* obs;        // [T][D][obs_dim]
+    float* rew;        // [T][D]
+    uint8_t* done;     // [T][E]
+};
+
+// kernels (qs_step.cu)
 cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, const Tile* tiles, const int* perm,
                         const StepIO& io, int observe_only, cudaStream_t s);
+// Persistent launch over n_tiles tiles (any classes) of `block` threads;
+// steps t0 .. t0+nsteps-1 of the io buffers. grid <= 0: one CTA per tile.
+cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int block, const int* perm,
+                           int* counter, const RolloutIO& io, int t0, int nsteps, int grid, cudaStream_t s);
+// CTAs of `block` threads the device keeps resident at once for k_rollout.
+int rollout_grid(int block);
+
+// kernels (qs_kernels.cu)
 cudaError_t launch_reset(const Consts& c, const Dev& dv, uint32_t key0, uint32_t key1, const uint8_t* mask,
                          cudaStream_t s);
 cudaError_t launch_get_state(const Dev& dv, float* state, float* params, float* goals, int32_t* ep,

@@ -1,0 +1,381 @@
+// qs_step.cu -- the fused control step (S1..S13) on sm_103a, in two forms:
+//
+//  k_step<W>   one control step per launch (qs_step): state read from and
+//              written back to HBM.
+//  k_rollout   T control steps per launch (qs_rollout): a persistent kernel
+//              whose CTAs pull tiles of envs from a work counter (widest,
+//              costliest classes first) and keep each drone's state in
+//              registers across the T steps; one launch covers envs of every
+//              swarm size.
+//
+// Layout: a CTA processes env "slots" of one width class W (a power of two >=
+// the env's swarm size N); thread `lane` of a slot carries drone `lane` of the
+// env. For W > 1 the slot exchanges positions and velocities through shared
+// memory for the O(N^2) pair pass (collisions, Sec. III-B) and the K-nearest
+// neighbour selection (Sec. II-B, III-C), which each thread keeps as a sorted
+// register list of 64-bit keys (binary32 distance bits << 32 | index).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qs_device.cuh"
+#include "qs_internal.h"
+
+namespace qsk {
+
+constexpr int MAX_BLOCK = 256;
+
+// Per-env values a thread keeps in registers.
+struct EnvRegs {
+    Prm p;
+    float g0, g1, g2;
+    int ep;
+    uint32_t tick;
+    bool redrawn;  // auto-reset drew new parameters / goal this launch
+};
+
+__device__ __forceinline__ void load_env(EnvRegs& er, const Dev& dv, int e) {
+    er.p = load_prm(dv.prm, dv.E, e);
+    er.g0 = dv.goal[e];
+    er.g1 = dv.goal[dv.E + e];
+    er.g2 = dv.goal[2 * dv.E + e];
+    er.ep = dv.ep[e];
+    er.tick = dv.tick[e];
+    er.redrawn = false;
+}
+
+// Written by lane 0 of the slot at the end of a launch.
+__device__ __forceinline__ void store_env(const EnvRegs& er, const Dev& dv, int e) {
+    dv.ep[e] = er.ep;
+    dv.tick[e] = er.tick;
+    if (er.redrawn) {
+        const float v[NPRM_DEV] = {er.p.m, er.p.ixx, er.p.iyy, er.p.izz, er.p.t2w, er.p.tau, er.p.arm, er.p.fmax,
+                                   er.p.alag, er.p.ans, er.p.inv_m, er.p.inv_ixx, er.p.inv_iyy, er.p.inv_izz,
+                                   er.p.thr, er.p.prox};
+        for (int k = 0; k < NPRM_DEV; ++k) dv.prm[(size_t)k * dv.E + e] = v[k];
+        dv.goal[e] = er.g0;
+        dv.goal[dv.E + e] = er.g1;
+        dv.goal[2 * dv.E + e] = er.g2;
+    }
+}
+
+// Inserts cand into the ascending list best[0..K).
+__device__ __forceinline__ void topk_insert(uint64_t best[QS_MAX_K], int K, uint64_t cand) {
+#pragma unroll
+    for (int k = 0; k < QS_MAX_K; ++k) {
+        if (k < K && cand < best[k]) {
+            const uint64_t t = best[k];
+            best[k] = cand;
+            cand = t;
+        }
+    }
+}
+
+// One control step of the slot's drones. All threads of the CTA call it (the
+// pair pass synchronises the CTA); `act` marks threads that carry a drone.
+// Outputs for this step: obs/rew rows of drone d, done[e] (lane 0). W is
+// uniform over the CTA; a compile-time W folds away after inlining.
+__device__ __forceinline__ void step_body(const int W, const Consts& c, const Dev& dv, Drone& s, EnvRegs& er, uint32_t& ev_out,
+                                          float* sx, float* sv, const bool act, const int lane, const int N,
+                                          const int sbase, const int e, const int d, const float* __restrict__ act_in,
+                                          float* __restrict__ obs, float* __restrict__ rew, uint8_t* __restrict__ done,
+                                          const int observe_only) {
+    const int nt = blockDim.x;
+    const int K = c.K;
+    const int keff = min(K, N - 1);
+    const uint32_t tick = er.tick;
+    float fh[4] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t ev = 0;
+    if (act && !observe_only) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(act_in) + d);
+        fh[0] = command(c, a.x);
+        fh[1] = command(c, a.y);
+        fh[2] = command(c, a.z);
+        fh[3] = command(c, a.w);
+        const float u[4] = {sqrtf(fh[0]), sqrtf(fh[1]), sqrtf(fh[2]), sqrtf(fh[3])};
+        const float zero3[3] = {0.f, 0.f, 0.f};
+        for (int sub = 0; sub < c.substeps; ++sub) ev |= substep(s, er.p, c, u, tick, d, sub, zero3);
+    }
+
+    // ---- pair pass: collisions (S9, S10) and K nearest neighbours (S11)
+    uint64_t best[QS_MAX_K];
+#pragma unroll
+    for (int k = 0; k < QS_MAX_K; ++k) best[k] = ~0ull;
+    if (W > 1) {
+        if (act) {
+            sx[threadIdx.x] = s.x[0];
+            sx[nt + threadIdx.x] = s.x[1];
+            sx[2 * nt + threadIdx.x] = s.x[2];
+            sv[threadIdx.x] = s.v[0];
+            sv[nt + threadIdx.x] = s.v[1];
+            sv[2 * nt + threadIdx.x] = s.v[2];
+        }
+        __syncthreads();
+        float dvs0 = 0.f, dvs1 = 0.f, dvs2 = 0.f;
+        bool responded = false;
+        if (act && N > 1) {
+            const bool coll = (c.flags & QS_F_COLLISIONS) && !(c.flags & QS_F_SMOOTH) && !observe_only;
+            const bool flag_coll = (c.flags & QS_F_COLLISIONS) && !observe_only;
+            for (int j = 0; j < N; ++j) {
+                if (j == lane) continue;
+                const int tj = sbase + j;
+                float dx, dy, dz;
+                const float key = pair_key(s.x[0], s.x[1], s.x[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx, dy, dz);
+                if (flag_coll && key < er.p.thr) {
+                    ev |= EV_HIT_QUAD;
+                    if (coll) {
+                        // approaching iff (v_i - v_j) . (x_i - x_j) < 0
+                        const float rv0 = s.v[0] - sv[tj], rv1 = s.v[1] - sv[nt + tj], rv2 = s.v[2] - sv[2 * nt + tj];
+                        const float app = -(rv0 * dx + rv1 * dy + rv2 * dz);
+                        if (app < 0.0f) {
+                            float n0 = 0.f, n1 = 0.f, n2 = 1.f;
+                            if (key > 0.0f) {
+                                const float inv = rsqrtf(key);
+                                n0 = -dx * inv;
+                                n1 = -dy * inv;
+                                n2 = -dz * inv;
+                            }
+                            const float vn = -(rv0 * n0 + rv1 * n1 + rv2 * n2);  // (v_j - v_i) . n
+                            dvs0 = fmaf(vn, n0, dvs0);
+                            dvs1 = fmaf(vn, n1, dvs1);
+                            dvs2 = fmaf(vn, n2, dvs2);
+                            responded = true;
+                        }
+                    }
+                }
+                if (keff > 0) topk_insert(best, keff, ((uint64_t)__float_as_uint(key) << 32) | (uint32_t)j);
+            }
+        }
+        if (responded) {
+            float n[6];
+            six_normals(c, tick, (uint32_t)d, TAG_COLL, 0, n);
+            s.v[0] = c.alpha_c * (s.v[0] + dvs0 + c.sig_cv * n[0]);
+            s.v[1] = c.alpha_c * (s.v[1] + dvs1 + c.sig_cv * n[1]);
+            s.v[2] = c.alpha_c * (s.v[2] + dvs2 + c.sig_cv * n[2]);
+            comp_add(s.w[0], s.wlo[0], c.sig_cw * n[3]);
+            comp_add(s.w[1], s.wlo[1], c.sig_cw * n[4]);
+            comp_add(s.w[2], s.wlo[2], c.sig_cw * n[5]);
+        }
+        __syncthreads();
+        if (act) {  // post-collision velocities for the neighbour observation
+            sv[threadIdx.x] = s.v[0];
+            sv[nt + threadIdx.x] = s.v[1];
+            sv[2 * nt + threadIdx.x] = s.v[2];
+        }
+        __syncthreads();
+    }
+    if (!act) return;
+
+    // ---- S12 observation
+    if (obs) {
+        float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
+        if (c.flags & QS_F_OBS_NOISE) obs_noise(c, tick, d, observe_only ? 1u : 0u, ex, evv, ew);
+        float2* o2 = reinterpret_cast<float2*>(obs + (size_t)d * c.obs_dim);
+        o2[0] = make_float2(s.x[0] - er.g0 + ex[0], s.x[1] - er.g1 + ex[1]);
+        o2[1] = make_float2(s.x[2] - er.g2 + ex[2], s.v[0] + evv[0]);
+        o2[2] = make_float2(s.v[1] + evv[1], s.v[2] + evv[2]);
+        o2[3] = make_float2(s.R[0], s.R[1]);
+        o2[4] = make_float2(s.R[2], s.R[3]);
+        o2[5] = make_float2(s.R[4], s.R[5]);
+        o2[6] = make_float2(s.R[6], s.R[7]);
+        o2[7] = make_float2(s.R[8], s.w[0] + ew[0]);
+        o2[8] = make_float2(s.w[1] + ew[1], s.w[2] + ew[2]);
+#pragma unroll
+        for (int k = 0; k < QS_MAX_K; ++k) {
+            if (k >= K) break;
+            float2* on = o2 + 9 + 3 * k;
+            if (W > 1 && k < keff) {
+                const int tj = sbase + (int)(best[k] & 0xffffffffu);
+                on[0] = make_float2(sx[tj] - s.x[0], sx[nt + tj] - s.x[1]);
+                on[1] = make_float2(sx[2 * nt + tj] - s.x[2], sv[tj] - s.v[0]);
+                on[2] = make_float2(sv[nt + tj] - s.v[1], sv[2 * nt + tj] - s.v[2]);
+            } else {
+                on[0] = make_float2(0.f, 0.f);
+                on[1] = make_float2(0.f, 0.f);
+                on[2] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+    if (observe_only) return;
+
+    if ((c.flags & QS_F_RECORD_KNN) && dv.knn) {
+#pragma unroll
+        for (int k = 0; k < QS_MAX_K; ++k)
+            if (k < K) dv.knn[(size_t)k * dv.D + d] = k < keff ? (int16_t)(best[k] & 0xffffu) : (int16_t)-1;
+    }
+    ev_out = ev;
+
+    // ---- S13 reward and done
+    if (rew) {
+        const float dgx = s.x[0] - er.g0, dgy = s.x[1] - er.g1, dgz = s.x[2] - er.g2;
+        float r = c.w[QS_W_POS] * sqrtf(dgx * dgx + dgy * dgy + dgz * dgz);
+        r += c.w[QS_W_VEL] * sqrtf(s.v[0] * s.v[0] + s.v[1] * s.v[1] + s.v[2] * s.v[2]);
+        r += c.w[QS_W_ORI] * s.R[8];
+        r += c.w[QS_W_SPIN] * sqrtf(s.w[0] * s.w[0] + s.w[1] * s.w[1] + s.w[2] * s.w[2]);
+        r += c.w[QS_W_ACT] * sqrtf(fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
+        const float q0 = fh[0] - s.fp[0], q1 = fh[1] - s.fp[1], q2 = fh[2] - s.fp[2], q3 = fh[3] - s.fp[3];
+        r += c.w[QS_W_DACT] * sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+        r += c.w[QS_W_ROT] * 0.5f * (s.R[0] + s.R[4] + s.R[8] - 1.0f);
+        r += c.w[QS_W_YAW] * s.R[0];
+        r += (ev & EV_HIT_FLOOR) ? c.w[QS_W_HIT_FLOOR] : 0.0f;
+        r += (ev & EV_ON_FLOOR) ? c.w[QS_W_ON_FLOOR] : 0.0f;
+        r += (ev & EV_HIT_WALL) ? c.w[QS_W_HIT_WALL] : 0.0f;
+        r += (ev & EV_HIT_CEIL) ? c.w[QS_W_HIT_CEIL] : 0.0f;
+        r += (ev & EV_HIT_QUAD) ? c.w[QS_W_HIT_QUAD] : 0.0f;
+        if (W > 1 && c.w[QS_W_NEAR] != 0.0f) {
+            float near = 0.0f;
+#pragma unroll
+            for (int k = 0; k < QS_MAX_K; ++k) {
+                if (k < keff) {
+                    const float key = __uint_as_float((uint32_t)(best[k] >> 32));
+                    near += fmaxf(1.0f - sqrtf(key) / er.p.prox, 0.0f);
+                }
+            }
+            r += c.w[QS_W_NEAR] * near;
+        }
+        rew[d] = r;
+    }
+    s.fp[0] = fh[0];
+    s.fp[1] = fh[1];
+    s.fp[2] = fh[2];
+    s.fp[3] = fh[3];
+
+    const int ep = er.ep + 1;
+    const bool is_done = ep >= c.episode_steps;
+    if (lane == 0 && done) done[e] = is_done ? 1 : 0;
+    er.ep = (is_done && (c.flags & QS_F_AUTO_RESET)) ? 0 : ep;
+    er.tick = tick + 1;
+    if (is_done && (c.flags & QS_F_AUTO_RESET)) {
+        // the env starts a new episode in place (new randomisation and goal);
+        // every lane draws the env's values itself, so no exchange is needed
+        float p7[QS_PARAM_DIM], goal[3], full[NPRM_DEV];
+        draw_env(c, c.key0, c.key1, tick, TAG_AUTO_ENV, e, p7, goal);
+        derive(c, p7, full);
+        er.p = prm_from(full);
+        er.g0 = goal[0];
+        er.g1 = goal[1];
+        er.g2 = goal[2];
+        er.redrawn = true;
+        draw_drone(c, c.key0, c.key1, tick, TAG_AUTO_DRONE, d, p7[P_T2W], s);
+    }
+    if (!finite_state(s)) atomicOr(dv.status, 1);
+}
+
+struct SlotMap {
+    int slot, lane, e, d0, N, d, sbase;
+    bool act;
+};
+
+__device__ __forceinline__ SlotMap map_slot(const Dev& dv, const Tile& tile, const int* __restrict__ perm, int W) {
+    SlotMap m;
+    m.slot = threadIdx.x / W;
+    m.lane = threadIdx.x - m.slot * W;
+    const bool ok = m.slot < tile.count;
+    m.e = ok ? perm[tile.first + m.slot] : 0;
+    m.d0 = ok ? dv.env_off[m.e] : 0;
+    m.N = ok ? dv.env_off[m.e + 1] - m.d0 : 0;
+    m.act = m.lane < m.N;
+    m.d = m.d0 + m.lane;
+    m.sbase = m.slot * W;
+    return m;
+}
+
+template <int W>
+__global__ void __launch_bounds__(MAX_BLOCK) k_step(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+                                                    const int* __restrict__ perm, const StepIO io, const int observe_only) {
+    extern __shared__ float sm[];
+    const SlotMap m = map_slot(dv, tiles[blockIdx.x], perm, W);
+    Drone s;
+    EnvRegs er;
+    uint32_t ev = 0;
+    if (m.act) {
+        load_drone(s, dv.st, dv.D, m.d);
+        load_env(er, dv, m.e);
+    }
+    step_body(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d, io.act, io.obs,
+              io.rew, io.done, observe_only);
+    if (!m.act || observe_only) return;
+    dv.ev[m.d] = ev;
+    store_drone(s, dv.st, dv.D, m.d);
+    if (m.lane == 0) store_env(er, dv, m.e);
+}
+
+// T steps of one tile with the state in registers.
+__device__ __forceinline__ void rollout_tile(const Consts& c, const Dev& dv, const Tile& tile, const int* __restrict__ perm,
+                                             float* sm, const RolloutIO& io, int t0, int nsteps) {
+    const int W = tile.W;
+    const SlotMap m = map_slot(dv, tile, perm, W);
+    Drone s;
+    EnvRegs er;
+    uint32_t ev = 0;
+    if (m.act) {
+        load_drone(s, dv.st, dv.D, m.d);
+        load_env(er, dv, m.e);
+    }
+    const size_t D = dv.D, E = dv.E;
+    for (int t = t0; t < t0 + nsteps; ++t) {
+        step_body(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d,
+                  io.act + (size_t)t * D * 4, io.obs ? io.obs + (size_t)t * D * c.obs_dim : nullptr,
+                  io.rew ? io.rew + (size_t)t * D : nullptr, io.done ? io.done + (size_t)t * E : nullptr, 0);
+    }
+    if (m.act) {
+        dv.ev[m.d] = ev;
+        store_drone(s, dv.st, dv.D, m.d);
+        if (m.lane == 0) store_env(er, dv, m.e);
+    }
+}
+
+// Persistent rollout: CTAs take tiles from *counter (zeroed before the launch)
+// until none is left. Tiles are ordered costliest first.
+__global__ void __launch_bounds__(MAX_BLOCK) k_rollout(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+                                                       const int n_tiles, const int* __restrict__ perm,
+                                                       int* __restrict__ counter, const RolloutIO io, const int t0,
+                                                       const int nsteps) {
+    extern __shared__ float sm[];
+    __shared__ int s_next;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int ti = s_next;
+        __syncthreads();  // everyone has read s_next before thread 0 overwrites it
+        if (ti >= n_tiles) return;
+        rollout_tile(c, dv, tiles[ti], perm, sm, io, t0, nsteps);
+    }
+}
+
+cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, const Tile* tiles, const int* perm,
+                        const StepIO& io, int observe_only, cudaStream_t st) {
+    if (cp.n_tiles == 0) return cudaSuccess;
+    const size_t smem = (cp.W > 1) ? sizeof(float) * 6 * cp.block : 0;
+    const Tile* t = tiles + cp.tile_off;
+    switch (cp.W) {
+        case 1: k_step<1><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 2: k_step<2><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 4: k_step<4><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 8: k_step<8><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 16: k_step<16><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 32: k_step<32><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 64: k_step<64><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int rollout_grid(int block) {
+    int dev = 0, n_sm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rollout, block, sizeof(float) * 6 * block);
+    return (occ > 0 ? occ : 1) * n_sm;
+}
+
+cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int block, const int* perm,
+                           int* counter, const RolloutIO& io, int t0, int nsteps, int grid, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(float) * 6 * block;
+    const int g = grid > 0 ? grid : n_tiles;
+    k_rollout<<<g < n_tiles ? g : n_tiles, block, smem, st>>>(c, dv, tiles, n_tiles, perm, counter, io, t0, nsteps);
+    return cudaGetLastError();
+}
+
+}  // namespace qsk

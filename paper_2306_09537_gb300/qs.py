@@ -29,8 +29,8 @@ W_NAMES = ["pos", "vel", "ori", "spin", "act", "dact", "rot", "yaw", "hit_floor"
            "hit_quad", "near"]
 
 EXPORTS = ["qs_config_default", "qs_create", "qs_destroy", "qs_get_dims", "qs_reset", "qs_step", "qs_step_host",
-           "qs_rollout", "qs_get_state", "qs_set_state", "qs_get_events", "qs_sync", "qs_set_block", "qs_get_block",
-           "qs_last_error"]
+           "qs_rollout", "qs_set_rollout_shape", "qs_get_rollout_shape", "qs_get_state", "qs_set_state",
+           "qs_get_events", "qs_sync", "qs_set_block", "qs_get_block", "qs_last_error"]
 
 
 class qs_params(C.Structure):
@@ -73,6 +73,8 @@ def _load():
     L.qs_step.argtypes = [V, V, V, V, V]
     L.qs_step_host.argtypes = [V, V, V, V, V]
     L.qs_rollout.argtypes = [V, C.c_int32, V, V, V, V]
+    L.qs_set_rollout_shape.argtypes = [V, C.c_int32, C.c_int32, C.c_int32]
+    L.qs_get_rollout_shape.argtypes = [V, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
     L.qs_get_state.argtypes = [V, V, V, V, V, V]
     L.qs_set_state.argtypes = [V, V, V, V, V, V]
     L.qs_get_events.argtypes = [V, V, V]
@@ -164,6 +166,16 @@ def qs_step_host(h, actions, obs=None, reward=None, done=None):
 
 def qs_rollout(h, T: int, actions, obs=None, reward=None, done=None):
     return _check(_L.qs_rollout(h, int(T), _p(actions), _p(obs), _p(reward), _p(done)), h)
+
+
+def qs_set_rollout_shape(h, block: int, fuse: int = 0, use_graph: bool = True):
+    return _check(_L.qs_set_rollout_shape(h, int(block), int(fuse), int(bool(use_graph))), h)
+
+
+def qs_get_rollout_shape(h):
+    b, f, g = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(_L.qs_get_rollout_shape(h, C.byref(b), C.byref(f), C.byref(g)), h)
+    return b.value, f.value, bool(g.value)
 
 
 def qs_get_state(h, state=None, params=None, goals=None, ep_step=None, tick=None):

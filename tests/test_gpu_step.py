@@ -292,19 +292,68 @@ def test_step_host_equals_step():
         assert torch.equal(obs.cpu(), obs_h) and torch.equal(rew.cpu(), rew_h) and torch.equal(done.cpu(), done_h)
 
 
-def test_rollout_equals_steps():
-    sizes = [1, 2, 8, 64, 3] * 8
-    env, _ = pair(sizes, 6, FULL, seed=4)
-    env2, _ = pair(sizes, 6, FULL, seed=4)
-    T = 12
-    acts = torch.from_numpy(W.actions(4, T, env.D)).to(DEV)
+def _rollout_vs_steps(sizes, K, T, shape=None, feats=FULL + ("auto_reset",), seed=4, episode_steps=7):
+    from paper_2306_09537_gb300 import qs
+    env, _ = pair(sizes, K, feats, seed=seed, episode_steps=episode_steps)
+    env2, _ = pair(sizes, K, feats, seed=seed, episode_steps=episode_steps)
+    if shape is not None:
+        qs.qs_set_rollout_shape(env.h, *shape)
+    acts = torch.from_numpy(W.actions(seed, T, env.D)).to(DEV)
     obs = torch.empty(T, env.D, env.obs_dim, device=DEV)
     rew = torch.empty(T, env.D, device=DEV)
     done = torch.empty(T, env.E, dtype=torch.uint8, device=DEV)
     env.rollout(acts, obs, rew, done)
+    ro = (obs.clone(), rew.clone(), done.clone())
+    ref_obs, ref_rew, ref_done = [], [], []
     for t in range(T):
         o2, r2, d2 = env2.step(acts[t])
-        assert torch.equal(obs[t], o2) and torch.equal(rew[t], r2) and torch.equal(done[t], d2)
+        ref_obs.append(o2.clone())
+        ref_rew.append(r2.clone())
+        ref_done.append(d2.clone())
+    s1, s2 = env.get_state(), env2.get_state()
+    ev1, _ = env.get_events()
+    ev2, _ = env2.get_events()
+    return env, acts, ro, (torch.stack(ref_obs), torch.stack(ref_rew), torch.stack(ref_done)), (s1, s2), (ev1, ev2)
+
+
+def test_rollout_equals_steps():
+    """The persistent register-resident rollout (one launch for every swarm
+    size, auto-reset crossing episode boundaries) reproduces T per-call steps."""
+    sizes = [1, 2, 8, 64, 3, 33, 16, 5] * 6
+    _, _, ro, ref, (s1, s2), (ev1, ev2) = _rollout_vs_steps(sizes, 6, 12)
+    for a, b in zip(ro, ref):
+        assert torch.equal(a, b)
+    for k in ("state", "params", "goals", "ep_step", "tick"):
+        assert torch.equal(s1[k], s2[k]), k
+    assert torch.equal(ev1, ev2)
+
+
+@pytest.mark.parametrize("shape", [(64, 0, True), (128, 5, True), (256, 3, False), (64, 1, False)])
+def test_rollout_shape_does_not_change_results(shape):
+    sizes = [1, 2, 8, 64, 4] * 5
+    _, _, ro, ref, (s1, s2), _ = _rollout_vs_steps(sizes, 6, 9, shape=shape)
+    for a, b in zip(ro, ref):
+        assert torch.equal(a, b)
+    assert torch.equal(s1["state"], s2["state"])
+
+
+def test_rollout_graph_replay():
+    """A second rollout with the same buffers replays the captured graph and
+    continues the simulation exactly as per-call steps would."""
+    from paper_2306_09537_gb300 import qs
+    sizes = [8] * 40 + [1] * 64
+    env, _ = pair(sizes, 6, FULL, seed=6)
+    env2, _ = pair(sizes, 6, FULL, seed=6)
+    T = 5
+    acts = torch.from_numpy(W.actions(6, T, env.D)).to(DEV)
+    obs = torch.empty(T, env.D, env.obs_dim, device=DEV)
+    rew = torch.empty(T, env.D, device=DEV)
+    for rep in range(3):
+        env.rollout(acts, obs, rew, None)
+        for t in range(T):
+            o2, r2, _ = env2.step(acts[t])
+            assert torch.equal(obs[t], o2) and torch.equal(rew[t], r2)
+    assert qs.qs_get_rollout_shape(env.h)[2] is True
     assert torch.equal(env.get_state()["state"], env2.get_state()["state"])
 
 
