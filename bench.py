@@ -272,6 +272,119 @@ def run_gpu(args, world, rank, local):
     return line
 
 
+def _events_ms(fn, stream, reps=3, flush=None):
+    import torch
+    out = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+    return float(np.median(out))
+
+
+def rollout_bytes(D, E, obs_dim):
+    """Algorithmic bytes per quadrotor-step of the batched form (state stays on chip)."""
+    return D * (16 + 4 * obs_dim + 4) + E * 1
+
+
+def run_forms(dev, stream, seed):
+    """The batched, swarm, uneven and env-count-sweep forms (extra keys)."""
+    import torch
+
+    from paper_2306_09537_gb300 import autotune, qs
+    from paper_2306_09537_gb300.env import QuadSwarmEnv
+    hbm, sm_max, _ = peaks()
+    alu_peak = 152 * 128 * sm_max * 1e6
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    forms = {}
+    with torch.cuda.stream(stream):
+        def make(wl, n_envs=None, feats=None):
+            sizes = wl.sizes() if n_envs is None else np.full(n_envs, wl.swarm, np.int32)
+            env = QuadSwarmEnv(len(sizes), sizes if wl.swarm is None else wl.swarm, wl.k_neighbors,
+                               feats or (wl.features + ("auto_reset",)), seed=seed, weights=wl.weights, device=dev,
+                               stream=stream)
+            env.reset(seed)
+            return env
+
+        def per_call(env, acts, steps):
+            for t in range(3):
+                env.step(acts[t % acts.shape[0]])
+            tot = 0.0
+            for t in range(steps):
+                tot += _events_ms(lambda: env.step(acts[t % acts.shape[0]]), stream, reps=1, flush=flush)
+            return tot / steps
+
+        def rollout(env, acts, T, reps=3):
+            obs = torch.empty(T, env.D, env.obs_dim, device=dev)
+            rew = torch.empty(T, env.D, device=dev)
+            done = torch.empty(T, env.E, dtype=torch.uint8, device=dev)
+            env.rollout(acts[:T], obs, rew, done)  # capture + warm
+            ms = _events_ms(lambda: env.rollout(acts[:T], obs, rew, done), stream, reps=reps, flush=flush) / T
+            del obs, rew, done
+            return ms
+
+        # plain 8192 x 1: batched rollout of the 1000-step episode chunk
+        env = make(W.PLAIN)
+        tuned = autotune.tune(env, horizon=64)
+        acts = torch.from_numpy(W.actions(seed, 1000, env.D)).to(dev)
+        ms = rollout(env, acts, 1000)
+        forms["plain_rollout"] = {"value": env.D / ms * 1e3, "ms_per_step": ms, "T": 1000,
+                                  "shape": list(tuned["rollout"]), "launches_per_rollout":
+                                  -(-1000 // (tuned["rollout"][1] or 1000))}
+        env.close()
+        del acts
+
+        # swarm 2048 x 8, K = 6: per-call and batched
+        env = make(W.SWARM)
+        tuned = autotune.tune(env, horizon=64)
+        acts = torch.from_numpy(W.actions(seed, 500, env.D)).to(dev)
+        ms_call = per_call(env, acts, 300)
+        ms_roll = rollout(env, acts, 500)
+        forms["swarm_call"] = {"value": env.D / ms_call * 1e3, "ms_per_step": ms_call}
+        forms["swarm_rollout"] = {"value": env.D / ms_roll * 1e3, "ms_per_step": ms_roll, "T": 500,
+                                  "shape": list(tuned["rollout"])}
+        env.close()
+        del acts
+
+        # uneven swarms, 4096 envs, sizes {1..64}: one persistent launch vs per-size launches
+        env = make(W.UNEVEN)
+        tuned = autotune.tune(env, horizon=64)
+        acts = torch.from_numpy(W.actions(seed, 256, env.D)).to(dev)
+        ms_roll = rollout(env, acts, 256)
+        ms_call = per_call(env, acts, 256)
+        n_classes = len(tuned["step_blocks"])
+        forms["uneven_batched"] = {"value": env.D / ms_roll * 1e3, "ms_per_step": ms_roll, "T": 256,
+                                   "drones": env.D, "shape": list(tuned["rollout"])}
+        forms["uneven_per_size_launches"] = {"value": env.D / ms_call * 1e3, "ms_per_step": ms_call,
+                                             "launches_per_step": n_classes}
+        forms["uneven_speedup_vs_per_size"] = ms_call / ms_roll
+        env.close()
+        del acts
+
+        # env-count sweep of the batched plain form (1 drone per env)
+        sweep = []
+        for E in (8192, 65536, 262144, 1048576):
+            env = make(W.PLAIN, n_envs=E)
+            qs.qs_set_rollout_shape(env.h, 128, 0, True)
+            T = 50
+            acts = torch.from_numpy(W.actions(seed, T, env.D)).to(dev)
+            ms = rollout(env, acts, T)
+            s = ms * 1e-3
+            ab = rollout_bytes(env.D, env.E, env.obs_dim)
+            sweep.append({"n_envs": E, "value": env.D / s, "ms_per_step": ms,
+                          "hbm_frac": ab / s / 1e9 / hbm,
+                          "alu_frac": OPS_PER_QUAD_STEP_N1 * env.D / s / alu_peak})
+            env.close()
+            del acts
+        forms["plain_rollout_sweep"] = sweep
+    return forms
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -279,6 +392,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched / swarm / uneven / sweep forms")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -286,6 +400,10 @@ def main():
         run_reference(args, world, rank)
         return
     line = run_gpu(args, world, rank, local)
+    if rank == 0 and not args.no_forms:
+        import torch
+        dev = torch.device("cuda", local)
+        line["forms"] = run_forms(dev, torch.cuda.Stream(device=dev), WL.seed)
     if rank == 0:
         if not args.no_cpu_baseline:
             v, cores, sample = oracle_run(200)

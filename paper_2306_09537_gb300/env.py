@@ -23,6 +23,7 @@ class QuadSwarmEnv:
         if swarm is None or not np.isscalar(swarm):
             sizes = np.ascontiguousarray(swarm, dtype=np.int32)
             swarm = 1
+        self.sizes, self.features, self.weights, self.overrides = sizes, tuple(features), weights, dict(overrides)
         self.cfg = qs.make_config(n_envs, swarm, k_neighbors, features, seed, weights, **overrides)
         with torch.cuda.device(self.device):
             self.h = qs.qs_create(self.cfg, self.stream.cuda_stream, swarm_sizes=sizes)
