@@ -191,6 +191,29 @@ qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_
 qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t use_graph);
 qs_status qs_get_rollout_shape(const qs_env* h, int32_t* block, int32_t* fuse, int32_t* use_graph);
 
+/* Differentiable rollout (smooth-contact form; the handle must be created with
+ * QS_F_SMOOTH). The floor, walls, ceiling and quad-quad contacts of Sec. III-B
+ * become softplus penalty accelerations k_c sp_beta(penetration)/m along the
+ * contact normal, so the step is differentiable; motor noise stays a fixed
+ * additive draw. From the initial drone states x0_dev [D][30] (state layout
+ * above; the handle's parameters, goals and Philox counters; the handle's own
+ * state is neither read nor changed) and commands actions_dev [T][D][4], the
+ * forward pass writes the per-drone loss
+ *     loss_dev[d] = sum_{t=1..T} |x_d(t) - goal|^2 + 1e-3 |f^_d(t)|^2
+ * and stores a checkpoint every ckpt_every control steps in the caller's
+ * workspace_dev (qs_diff_workspace_size bytes, 16-byte aligned). The backward
+ * pass takes dloss_dev [D] (d objective / d loss_dev[d]) and the same T,
+ * ckpt_every, actions and workspace, recomputes each checkpoint segment's
+ * substeps into the workspace and runs the hand-written adjoint of the whole
+ * step (dynamics, integrator with re-orthonormalisation, smooth contacts),
+ * writing grad_actions_dev [T][D][4] and grad_x0_dev [D][30] (zero for the
+ * previous-command entries, which do not enter the loss). */
+qs_status qs_diff_workspace_size(const qs_env* h, int32_t T, int32_t ckpt_every, size_t* bytes);
+qs_status qs_diff_forward(qs_env* h, int32_t T, int32_t ckpt_every, const float* x0_dev, const float* actions_dev,
+                          float* loss_dev, void* workspace_dev);
+qs_status qs_diff_backward(qs_env* h, int32_t T, int32_t ckpt_every, const float* actions_dev, const float* dloss_dev,
+                           void* workspace_dev, float* grad_actions_dev, float* grad_x0_dev);
+
 /* Copies the handle's state into caller buffers (each nullable): state_dev
  * [D][30], params_dev [E][7], goals_dev [E][3], ep_step_dev [E] control steps
  * into the episode, tick_dev [E] Philox step counter of each env. */

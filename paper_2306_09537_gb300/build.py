@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "_build", "libquadswarm_gpu.so")
-SOURCES = ["qs_api.cu", "qs_kernels.cu", "qs_step.cu"]
+SOURCES = ["qs_api.cu", "qs_kernels.cu", "qs_step.cu", "qs_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1,0 +1,528 @@
+// qs_adjoint.cu -- the differentiable rollout: a forward pass in the smooth-
+// contact form that stores checkpoints, and the hand-written adjoint (reverse
+// mode) of the whole step, recomputing each checkpoint segment's substeps.
+//
+// Loss of a rollout of T control steps from x0 under commands a_t:
+//   L_d = sum_t |x_d(t) - g_e|^2 + 1e-3 |f^_d(t)|^2   (per drone d; x after step t)
+// The smooth form replaces the floor, wall, ceiling and pair responses by
+// softplus penalty accelerations k_c sp_beta(penetration) / m along the
+// contact normal (sp_beta(u) = log(1 + exp(beta u)) / beta); motor noise is a
+// fixed additive draw (its Philox counters do not depend on the state).
+//
+// Adjoint of one substep (state s -> s'; all quantities of drone i):
+//   uf' = uf + alpha (u - uf),  eps' = a_nd eps + a_ns n,  f_r = fmax uf'_r^2 + eps'_r
+//   T = sum f, tau = (sa(f0+f1-f2-f3), sa(f1+f2-f0-f3), kappa(f1+f3-f0-f2))
+//   a = T R e_z / m + g + wall(x) + sum_j psi(d_ij) (x_i - x_j),  psi(d) = k sp(2l - d) / d
+//   wdot = I^-1 (tau - w x I w),  v' = v + a dt,  x' = x + v' dt,  w' = clamp(w + wdot dt)
+//   R' = B(R Q(w')),  Q = I + a(w) [w]x + b(w) [w]x^2 (the polar factor of I + dt [w]x),
+//   B(M) = M (3 I - M^T M) / 2 (one Bjorck step).
+// The reverse pass applies the transposed Jacobian of each line in reverse
+// order; the pair term couples drone i to its partners through
+// lambda_x_i += sum_j J_ij (lambda_a_i - lambda_a_j), J_ij = psi I + (psi'/d) r r^T,
+// with lambda_a exchanged through shared memory.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qs_device.cuh"
+#include "qs_internal.h"
+
+namespace qsk {
+
+constexpr int ADJ_BLOCK_MAX = 256;
+constexpr int NSUB = 29;  // floats of a saved substep input: x v R w wlo uf eps
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// Wall / floor / ceiling penalty acceleration and its diagonal derivative.
+__device__ __forceinline__ void wall_acc(const Consts& c, const float x[3], float acc[3], float dacc[3]) {
+    const float kcg = c.kc * c.g, b = c.beta;
+    acc[0] = kcg * (softplus_b(-c.room_hx - x[0], b) - softplus_b(x[0] - c.room_hx, b));
+    acc[1] = kcg * (softplus_b(-c.room_hy - x[1], b) - softplus_b(x[1] - c.room_hy, b));
+    acc[2] = kcg * (softplus_b(-x[2], b) - softplus_b(x[2] - c.room_h, b));
+    dacc[0] = -kcg * (sigmoidf_(b * (-c.room_hx - x[0])) + sigmoidf_(b * (x[0] - c.room_hx)));
+    dacc[1] = -kcg * (sigmoidf_(b * (-c.room_hy - x[1])) + sigmoidf_(b * (x[1] - c.room_hy)));
+    dacc[2] = -kcg * (sigmoidf_(-b * x[2]) + sigmoidf_(b * (x[2] - c.room_h)));
+}
+
+// Smooth pair acceleration of the thread's drone from the slot's positions in
+// shared memory (sx[3][nt]); j == lane and coincident drones contribute 0.
+__device__ __forceinline__ void pair_acc(const Consts& c, const float x[3], const float* sx, int nt, int sbase, int lane,
+                                         int N, float arm, float out[3]) {
+    out[0] = out[1] = out[2] = 0.f;
+    const float kcg = c.kc * c.g;
+    for (int j = 0; j < N; ++j) {
+        if (j == lane) continue;
+        const int tj = sbase + j;
+        const float r0 = x[0] - sx[tj], r1 = x[1] - sx[nt + tj], r2 = x[2] - sx[2 * nt + tj];
+        const float d2 = r0 * r0 + r1 * r1 + r2 * r2;
+        if (d2 == 0.f) continue;
+        const float d = sqrtf(d2);
+        const float psi = kcg * softplus_b(2.f * arm - d, c.beta) / d;
+        out[0] = fmaf(psi, r0, out[0]);
+        out[1] = fmaf(psi, r1, out[1]);
+        out[2] = fmaf(psi, r2, out[2]);
+    }
+}
+
+// lambda_x += sum_j J_ij (lam_a_i - lam_a_j)
+__device__ __forceinline__ void pair_vjp(const Consts& c, const float x[3], const float la[3], const float* sx,
+                                         const float* sla, int nt, int sbase, int lane, int N, float arm, float lx[3]) {
+    const float kcg = c.kc * c.g, b = c.beta;
+    for (int j = 0; j < N; ++j) {
+        if (j == lane) continue;
+        const int tj = sbase + j;
+        const float r0 = x[0] - sx[tj], r1 = x[1] - sx[nt + tj], r2 = x[2] - sx[2 * nt + tj];
+        const float d2 = r0 * r0 + r1 * r1 + r2 * r2;
+        if (d2 == 0.f) continue;
+        const float d = sqrtf(d2), id = 1.f / d;
+        const float pen = 2.f * arm - d;
+        const float sp = softplus_b(pen, b), sg = sigmoidf_(b * pen);
+        const float psi = kcg * sp * id;
+        const float dpsi = kcg * (-sg * id - sp * id * id);  // d psi / d d
+        const float q0 = la[0] - sla[tj], q1 = la[1] - sla[nt + tj], q2 = la[2] - sla[2 * nt + tj];
+        const float rq = (r0 * q0 + r1 * q1 + r2 * q2) * dpsi * id;
+        lx[0] += psi * q0 + rq * r0;
+        lx[1] += psi * q1 + rq * r1;
+        lx[2] += psi * q2 + rq * r2;
+    }
+}
+
+// Adjoint of the substep map of the smooth form. s: substep input (as saved);
+// l: in = lambda of the output state, out = lambda of the input state
+// (x v R w uf eps); la: lambda of the acceleration (for the pair exchange);
+// lu: accumulated lambda of the rotor-speed command u.
+__device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const Consts& c, const float u[4],
+                                            const float pacc[3], uint32_t tick, int d, int sub, float lx[3], float lv[3],
+                                            float lR[9], float lw[3], float luf[4], float leps[4], float la[3],
+                                            float lu[4]) {
+    const float dt = c.dt;
+    // ---- recompute the forward intermediates
+    float uf1[4], eps1[4], f[4];
+    for (int r = 0; r < 4; ++r) uf1[r] = fmaf(p.alag, u[r] - s.uf[r], s.uf[r]);
+    float nrm[4] = {0.f, 0.f, 0.f, 0.f};
+    if (c.flags & QS_F_MOTOR_NOISE) {
+        const uint4 q = philox(tick, (uint32_t)d, ctr_word(TAG_MOTOR, (uint32_t)sub, 0), c.key0, c.key1);
+        const float2 n01 = box_muller(u01(q.x), u01(q.y));
+        const float2 n23 = box_muller(u01(q.z), u01(q.w));
+        nrm[0] = n01.x; nrm[1] = n01.y; nrm[2] = n23.x; nrm[3] = n23.y;
+        for (int r = 0; r < 4; ++r) eps1[r] = fmaf(c.alpha_nd, s.eps[r], p.ans * nrm[r]);
+    } else {
+        for (int r = 0; r < 4; ++r) eps1[r] = s.eps[r];
+    }
+    for (int r = 0; r < 4; ++r) f[r] = fmaf(p.fmax * uf1[r], uf1[r], eps1[r]);
+    const float T = (f[0] + f[1]) + (f[2] + f[3]);
+    const float sa = p.arm * 0.70710678118654752f;
+    const float Iw[3] = {p.ixx * s.w[0], p.iyy * s.w[1], p.izz * s.w[2]};
+    const float tx = sa * ((f[0] + f[1]) - (f[2] + f[3]));
+    const float ty = sa * ((f[1] + f[2]) - (f[0] + f[3]));
+    const float tz = c.kappa * ((f[1] + f[3]) - (f[0] + f[2]));
+    const float wd[3] = {(tx - (s.w[1] * Iw[2] - s.w[2] * Iw[1])) * p.inv_ixx,
+                         (ty - (s.w[2] * Iw[0] - s.w[0] * Iw[2])) * p.inv_iyy,
+                         (tz - (s.w[0] * Iw[1] - s.w[1] * Iw[0])) * p.inv_izz};
+    // w' exactly as the forward computed it (compensated), and the clamp mask
+    float w1[3], pass[3];
+    for (int k = 0; k < 3; ++k) {
+        float hi = s.w[k], lo = s.wlo[k];
+        comp_add(hi, lo, wd[k] * dt);
+        pass[k] = fabsf(hi) > c.omega_max ? 0.f : 1.f;
+        w1[k] = fabsf(hi) > c.omega_max ? copysignf(c.omega_max, hi) : hi;
+    }
+    // M = R Q(w1)
+    const float n2 = w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2];
+    const float cc = __frsqrt_rn(fmaf(dt * dt, n2, 1.0f));
+    const float qa = dt * cc;
+    const float qb = dt * dt * cc * cc / (1.0f + cc);
+    // W = [w1]x, W2 = W W
+    const float Wm[9] = {0.f, -w1[2], w1[1], w1[2], 0.f, -w1[0], -w1[1], w1[0], 0.f};
+    float W2[9], Q[9], M[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float acc = 0.f;
+            for (int k = 0; k < 3; ++k) acc += Wm[3 * i + k] * Wm[3 * k + j];
+            W2[3 * i + j] = acc;
+            Q[3 * i + j] = (i == j ? 1.f : 0.f) + qa * Wm[3 * i + j] + qb * acc;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float acc = 0.f;
+            for (int k = 0; k < 3; ++k) acc += s.R[3 * i + k] * Q[3 * k + j];
+            M[3 * i + j] = acc;
+        }
+
+    // ---- reverse
+    // R' = B(M): G_M = 1.5 L - 0.5 (L S + M L^T M + M M^T L), S = M^T M
+    float S[9], MMt[9], GM[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float a1 = 0.f, a2 = 0.f;
+            for (int k = 0; k < 3; ++k) {
+                a1 += M[3 * k + i] * M[3 * k + j];
+                a2 += M[3 * i + k] * M[3 * j + k];
+            }
+            S[3 * i + j] = a1;
+            MMt[3 * i + j] = a2;
+        }
+    float LtM[9];  // L^T M
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float acc = 0.f;
+            for (int k = 0; k < 3; ++k) acc += lR[3 * k + i] * M[3 * k + j];
+            LtM[3 * i + j] = acc;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float t1 = 0.f, t2 = 0.f, t3 = 0.f;
+            for (int k = 0; k < 3; ++k) {
+                t1 += lR[3 * i + k] * S[3 * k + j];
+                t2 += M[3 * i + k] * LtM[3 * k + j];
+                t3 += MMt[3 * i + k] * lR[3 * k + j];
+            }
+            GM[3 * i + j] = 1.5f * lR[3 * i + j] - 0.5f * (t1 + t2 + t3);
+        }
+    // M = R Q: lambda_R = G_M Q^T, G_Q = R^T G_M
+    float GQ[9], lRin[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float a1 = 0.f, a2 = 0.f;
+            for (int k = 0; k < 3; ++k) {
+                a1 += GM[3 * i + k] * Q[3 * j + k];
+                a2 += s.R[3 * k + i] * GM[3 * k + j];
+            }
+            lRin[3 * i + j] = a1;
+            GQ[3 * i + j] = a2;
+        }
+    // Q(w1) = I + qa W + qb W^2: lambda_w1 from Q
+    //  <G, [dw]x> = dw . vex(G),  vex(G) = (G21 - G12, G02 - G20, G10 - G01)
+    //  <G, [dw]x W + W [dw]x> = dw . vex(-(G W) - (W G))   (W^T = -W)
+    float GW[9], WG[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float a1 = 0.f, a2 = 0.f;
+            for (int k = 0; k < 3; ++k) {
+                a1 += GQ[3 * i + k] * Wm[3 * k + j];
+                a2 += Wm[3 * i + k] * GQ[3 * k + j];
+            }
+            GW[3 * i + j] = -(a1 + a2);
+            WG[3 * i + j] = 0.f;
+        }
+    (void)WG;
+    const float vG[3] = {GQ[7] - GQ[5], GQ[2] - GQ[6], GQ[3] - GQ[1]};
+    const float vGW[3] = {GW[7] - GW[5], GW[2] - GW[6], GW[3] - GW[1]};
+    float gA = 0.f, gB = 0.f;
+    for (int k = 0; k < 9; ++k) {
+        gA += GQ[k] * Wm[k];
+        gB += GQ[k] * W2[k];
+    }
+    // a = dt c, b = dt^2 c^2 / (1 + c), c = (1 + dt^2 |w|^2)^(-1/2):
+    // dc/dw = -dt^2 c^3 w, da/dw = dt dc/dw, db/dw = dt^2 c (2 + c) / (1 + c)^2 dc/dw
+    const float dcs = -dt * dt * cc * cc * cc;
+    const float dadc = dt, dbdc = dt * dt * cc * (2.f + cc) / ((1.f + cc) * (1.f + cc));
+    float lw1[3];
+    for (int k = 0; k < 3; ++k)
+        lw1[k] = lw[k] + qa * vG[k] + qb * vGW[k] + (gA * dadc + gB * dbdc) * dcs * w1[k];
+    // w1 = clamp(w + wdot dt)
+    float lwd[3];
+    for (int k = 0; k < 3; ++k) {
+        const float g = lw1[k] * pass[k];
+        lw[k] = g;
+        lwd[k] = g * dt;
+    }
+    // x' = x + v' dt ; v' = v + a dt
+    float lv1[3];
+    for (int k = 0; k < 3; ++k) lv1[k] = lv[k] + dt * lx[k];
+    for (int k = 0; k < 3; ++k) {
+        lv[k] = lv1[k];
+        la[k] = dt * lv1[k];
+    }
+    // wdot = I^-1 (tau - w x I w): lambda_tau = mu, lambda_w -= (I w) x mu + I (mu x w)
+    const float mu[3] = {lwd[0] * p.inv_ixx, lwd[1] * p.inv_iyy, lwd[2] * p.inv_izz};
+    const float c1[3] = {Iw[1] * mu[2] - Iw[2] * mu[1], Iw[2] * mu[0] - Iw[0] * mu[2], Iw[0] * mu[1] - Iw[1] * mu[0]};
+    const float c2[3] = {mu[1] * s.w[2] - mu[2] * s.w[1], mu[2] * s.w[0] - mu[0] * s.w[2], mu[0] * s.w[1] - mu[1] * s.w[0]};
+    lw[0] -= c1[0] + p.ixx * c2[0];
+    lw[1] -= c1[1] + p.iyy * c2[1];
+    lw[2] -= c1[2] + p.izz * c2[2];
+    // a = T R e_z / m + g + wall(x) + pair: walls on the diagonal, thrust
+    float wacc[3], dwall[3];
+    wall_acc(c, s.x, wacc, dwall);
+    for (int k = 0; k < 3; ++k) lx[k] += dwall[k] * la[k];
+    const float b3[3] = {s.R[2], s.R[5], s.R[8]};
+    const float lT = (la[0] * b3[0] + la[1] * b3[1] + la[2] * b3[2]) * p.inv_m;
+    lRin[2] += T * la[0] * p.inv_m;
+    lRin[5] += T * la[1] * p.inv_m;
+    lRin[8] += T * la[2] * p.inv_m;
+    for (int k = 0; k < 9; ++k) lR[k] = lRin[k];
+    // T, tau from f
+    const float gx = mu[0] * sa, gy = mu[1] * sa, gz = mu[2] * c.kappa;
+    const float lf[4] = {lT + gx - gy - gz, lT + gx + gy + gz, lT - gx + gy - gz, lT - gx - gy + gz};
+    // f = fmax uf1^2 + eps1; eps1 = a_nd eps + a_ns n; uf1 = uf + alpha (u - uf)
+    for (int r = 0; r < 4; ++r) {
+        const float luf1 = luf[r] + 2.f * p.fmax * uf1[r] * lf[r];
+        const float leps1 = leps[r] + lf[r];
+        leps[r] = (c.flags & QS_F_MOTOR_NOISE) ? c.alpha_nd * leps1 : leps1;
+        luf[r] = (1.f - p.alag) * luf1;
+        lu[r] += p.alag * luf1;
+    }
+    (void)pacc;
+    (void)wacc;
+}
+
+// ---------------------------------------------------------------- workspace
+// [n_ckpt][NPLANE][D] float4 checkpoints, then [C * substeps][NSUB][D] floats.
+size_t diff_workspace_bytes(int D, int T, int C, int substeps) {
+    const int nck = (T + C - 1) / C;
+    const size_t ck = (size_t)nck * NPLANE * D * sizeof(float4);
+    const size_t sc = (size_t)C * substeps * NSUB * D * sizeof(float);
+    return ck + sc + 256;
+}
+
+__device__ __forceinline__ void save_sub(float* sc, size_t D, int idx, int d, const Drone& s) {
+    float* b = sc + (size_t)idx * NSUB * D + d;
+    int k = 0;
+    for (int q = 0; q < 3; ++q) b[(k++) * D] = s.x[q];
+    for (int q = 0; q < 3; ++q) b[(k++) * D] = s.v[q];
+    for (int q = 0; q < 9; ++q) b[(k++) * D] = s.R[q];
+    for (int q = 0; q < 3; ++q) b[(k++) * D] = s.w[q];
+    for (int q = 0; q < 3; ++q) b[(k++) * D] = s.wlo[q];
+    for (int q = 0; q < 4; ++q) b[(k++) * D] = s.uf[q];
+    for (int q = 0; q < 4; ++q) b[(k++) * D] = s.eps[q];
+}
+
+__device__ __forceinline__ void load_sub(const float* sc, size_t D, int idx, int d, Drone& s) {
+    const float* b = sc + (size_t)idx * NSUB * D + d;
+    int k = 0;
+    for (int q = 0; q < 3; ++q) s.x[q] = b[(k++) * D];
+    for (int q = 0; q < 3; ++q) s.v[q] = b[(k++) * D];
+    for (int q = 0; q < 9; ++q) s.R[q] = b[(k++) * D];
+    for (int q = 0; q < 3; ++q) s.w[q] = b[(k++) * D];
+    for (int q = 0; q < 3; ++q) s.wlo[q] = b[(k++) * D];
+    for (int q = 0; q < 4; ++q) s.uf[q] = b[(k++) * D];
+    for (int q = 0; q < 4; ++q) s.eps[q] = b[(k++) * D];
+}
+
+__device__ __forceinline__ void read_x0(Drone& s, const float* __restrict__ x0, int d) {
+    const float* r = x0 + (size_t)d * QS_STATE_DIM;
+    for (int k = 0; k < 3; ++k) s.x[k] = r[k];
+    for (int k = 0; k < 3; ++k) s.v[k] = r[3 + k];
+    for (int k = 0; k < 9; ++k) s.R[k] = r[6 + k];
+    for (int k = 0; k < 3; ++k) s.w[k] = r[15 + k];
+    for (int k = 0; k < 4; ++k) s.uf[k] = r[18 + k];
+    for (int k = 0; k < 4; ++k) s.eps[k] = r[22 + k];
+    for (int k = 0; k < 4; ++k) s.fp[k] = r[26 + k];
+    s.wlo[0] = s.wlo[1] = s.wlo[2] = 0.f;
+}
+
+// One smooth substep of the slot's drones (pair force from the positions at
+// the substep start, staged in shared memory).
+__device__ __forceinline__ void smooth_substep(const Consts& c, Drone& s, const Prm& p, const float u[4], uint32_t tick,
+                                               int d, int sub, bool act, float* sx, int nt, int sbase, int lane, int N) {
+    if (act) {
+        sx[threadIdx.x] = s.x[0];
+        sx[nt + threadIdx.x] = s.x[1];
+        sx[2 * nt + threadIdx.x] = s.x[2];
+    }
+    __syncthreads();
+    float pa[3] = {0.f, 0.f, 0.f};
+    if (act) pair_acc(c, s.x, sx, nt, sbase, lane, N, p.arm, pa);
+    __syncthreads();
+    if (act) substep(s, p, c, u, tick, d, sub, pa);
+}
+
+struct DiffArgs {
+    const float* x0;       // [D][30]
+    const float* act;      // [T][D][4]
+    float* loss;           // [D]
+    const float* dloss;    // [D]
+    float* grad_act;       // [T][D][4]
+    float* grad_x0;        // [D][30]
+    float4* ckpt;          // [nck][NPLANE][D]
+    float* scratch;        // [C * substeps][NSUB][D]
+    int T, C;
+};
+
+__device__ __forceinline__ void command4(const Consts& c, const float* act, size_t D, int t, int d, float fh[4], float u[4],
+                                         float msk[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(act + (size_t)t * D * 4) + d);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    for (int r = 0; r < 4; ++r) {
+        fh[r] = command(c, av[r]);
+        u[r] = sqrtf(fh[r]);
+        // d f^ / d a: 1 inside the clip range (1/2 for the symmetric map), 0 outside
+        const bool in = (c.flags & QS_F_ACTION_SYMMETRIC) ? (av[r] > -1.f && av[r] < 1.f) : (av[r] > 0.f && av[r] < 1.f);
+        msk[r] = in ? ((c.flags & QS_F_ACTION_SYMMETRIC) ? 0.5f : 1.f) : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_fwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+                                                            const int* __restrict__ perm, const DiffArgs a) {
+    extern __shared__ float sm[];
+    const Tile tile = tiles[blockIdx.x];
+    const int W = tile.W, nt = blockDim.x;
+    const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
+    const bool ok = slot < tile.count;
+    const int e = ok ? perm[tile.first + slot] : 0;
+    const int d0 = ok ? dv.env_off[e] : 0, N = ok ? dv.env_off[e + 1] - d0 : 0;
+    const bool act = lane < N;
+    const int d = d0 + lane, sbase = slot * W;
+    const size_t D = dv.D;
+    Drone s;
+    Prm p;
+    float g[3] = {0.f, 0.f, 0.f};
+    uint32_t tick0 = 0;
+    if (act) {
+        read_x0(s, a.x0, d);
+        p = load_prm(dv.prm, dv.E, e);
+        g[0] = dv.goal[e];
+        g[1] = dv.goal[dv.E + e];
+        g[2] = dv.goal[2 * dv.E + e];
+        tick0 = dv.tick[e];
+    }
+    float L = 0.f;
+    for (int t = 0; t < a.T; ++t) {
+        if (act && t % a.C == 0) {
+            float4 q[NPLANE];
+            pack(s, q);
+            float4* ck = a.ckpt + (size_t)(t / a.C) * NPLANE * D;
+            for (int pl = 0; pl < NPLANE; ++pl) ck[(size_t)pl * D + d] = q[pl];
+        }
+        float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4];
+        if (act) command4(c, a.act, D, t, d, fh, u, msk);
+        for (int sub = 0; sub < c.substeps; ++sub)
+            smooth_substep(c, s, p, u, tick0 + t, d, sub, act, sm, nt, sbase, lane, N);
+        if (act) {
+            const float dx = s.x[0] - g[0], dy = s.x[1] - g[1], dz = s.x[2] - g[2];
+            L += dx * dx + dy * dy + dz * dz + 1e-3f * (fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
+        }
+    }
+    if (act) {
+        a.loss[d] = L;
+        if (!finite_state(s)) atomicOr(dv.status, 1);
+    }
+}
+
+__global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+                                                            const int* __restrict__ perm, const DiffArgs a) {
+    extern __shared__ float sm[];
+    const Tile tile = tiles[blockIdx.x];
+    const int W = tile.W, nt = blockDim.x;
+    const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
+    const bool ok = slot < tile.count;
+    const int e = ok ? perm[tile.first + slot] : 0;
+    const int d0 = ok ? dv.env_off[e] : 0, N = ok ? dv.env_off[e + 1] - d0 : 0;
+    const bool act = lane < N;
+    const int d = d0 + lane, sbase = slot * W;
+    const size_t D = dv.D;
+    float* sx = sm;            // [3][nt] positions
+    float* sla = sm + 3 * nt;  // [3][nt] lambda of the acceleration
+    Prm p;
+    float g[3] = {0.f, 0.f, 0.f};
+    uint32_t tick0 = 0;
+    float dl = 0.f;
+    if (act) {
+        p = load_prm(dv.prm, dv.E, e);
+        g[0] = dv.goal[e];
+        g[1] = dv.goal[dv.E + e];
+        g[2] = dv.goal[2 * dv.E + e];
+        tick0 = dv.tick[e];
+        dl = a.dloss[d];
+    }
+    float lx[3] = {0.f, 0.f, 0.f}, lv[3] = {0.f, 0.f, 0.f}, lR[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float lw[3] = {0.f, 0.f, 0.f}, luf[4] = {0.f, 0.f, 0.f, 0.f}, leps[4] = {0.f, 0.f, 0.f, 0.f};
+    const int S = c.substeps;
+    const int nseg = (a.T + a.C - 1) / a.C;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int tb = seg * a.C, te = min(a.T, tb + a.C);
+        // recompute the segment, saving every substep input
+        Drone s;
+        if (act) {
+            float4 q[NPLANE];
+            const float4* ck = a.ckpt + (size_t)seg * NPLANE * D;
+            for (int pl = 0; pl < NPLANE; ++pl) q[pl] = ck[(size_t)pl * D + d];
+            unpack(s, q);
+        }
+        for (int t = tb; t < te; ++t) {
+            float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4];
+            if (act) command4(c, a.act, D, t, d, fh, u, msk);
+            for (int sub = 0; sub < S; ++sub) {
+                if (act) save_sub(a.scratch, D, (t - tb) * S + sub, d, s);
+                smooth_substep(c, s, p, u, tick0 + t, d, sub, act, sx, nt, sbase, lane, N);
+            }
+        }
+        // reverse through the segment; s holds the state after step te - 1
+        float xpost[3] = {s.x[0], s.x[1], s.x[2]};
+        for (int t = te - 1; t >= tb; --t) {
+            float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4] = {0.f, 0.f, 0.f, 0.f};
+            if (act) command4(c, a.act, D, t, d, fh, u, msk);
+            // loss of step t: |x(t) - g|^2 + 1e-3 |f^|^2
+            for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (xpost[k] - g[k]);
+            float lu[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int sub = S - 1; sub >= 0; --sub) {
+                Drone si;
+                if (act) load_sub(a.scratch, D, (t - tb) * S + sub, d, si);
+                if (act) {
+                    sx[threadIdx.x] = si.x[0];
+                    sx[nt + threadIdx.x] = si.x[1];
+                    sx[2 * nt + threadIdx.x] = si.x[2];
+                }
+                __syncthreads();
+                float pa[3] = {0.f, 0.f, 0.f}, la[3] = {0.f, 0.f, 0.f};
+                if (act) {
+                    pair_acc(c, si.x, sx, nt, sbase, lane, N, p.arm, pa);
+                    substep_vjp(si, p, c, u, pa, tick0 + t, d, sub, lx, lv, lR, lw, luf, leps, la, lu);
+                    sla[threadIdx.x] = la[0];
+                    sla[nt + threadIdx.x] = la[1];
+                    sla[2 * nt + threadIdx.x] = la[2];
+                }
+                __syncthreads();
+                if (act) pair_vjp(c, si.x, la, sx, sla, nt, sbase, lane, N, p.arm, lx);
+                __syncthreads();
+                if (sub == 0) {
+                    xpost[0] = si.x[0];
+                    xpost[1] = si.x[1];
+                    xpost[2] = si.x[2];
+                }
+            }
+            if (act) {
+                float ga[4];
+                for (int r = 0; r < 4; ++r) {
+                    // u = sqrt(f^): du/df^ = 1 / (2u)
+                    const float du = u[r] > 0.f ? 0.5f / u[r] : 0.f;
+                    ga[r] = msk[r] * (lu[r] * du + dl * 2e-3f * fh[r]);
+                }
+                reinterpret_cast<float4*>(a.grad_act + (size_t)t * D * 4)[d] = make_float4(ga[0], ga[1], ga[2], ga[3]);
+            }
+        }
+    }
+    if (act) {
+        float* gx = a.grad_x0 + (size_t)d * QS_STATE_DIM;
+        for (int k = 0; k < 3; ++k) gx[k] = lx[k];
+        for (int k = 0; k < 3; ++k) gx[3 + k] = lv[k];
+        for (int k = 0; k < 9; ++k) gx[6 + k] = lR[k];
+        for (int k = 0; k < 3; ++k) gx[15 + k] = lw[k];
+        for (int k = 0; k < 4; ++k) gx[18 + k] = luf[k];
+        for (int k = 0; k < 4; ++k) gx[22 + k] = leps[k];
+        for (int k = 0; k < 4; ++k) gx[26 + k] = 0.f;  // f^_prev does not enter the loss
+    }
+}
+
+cudaError_t launch_diff(int backward, const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int block,
+                        const int* perm, const float* x0, const float* act, float* loss, const float* dloss,
+                        float* grad_act, float* grad_x0, void* workspace, int T, int C, cudaStream_t st) {
+    DiffArgs a;
+    a.x0 = x0;
+    a.act = act;
+    a.loss = loss;
+    a.dloss = dloss;
+    a.grad_act = grad_act;
+    a.grad_x0 = grad_x0;
+    a.T = T;
+    a.C = C;
+    const int nck = (T + C - 1) / C;
+    a.ckpt = reinterpret_cast<float4*>(workspace);
+    a.scratch = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + (size_t)nck * NPLANE * dv.D * sizeof(float4));
+    const size_t smem = sizeof(float) * 6 * block;
+    if (backward) k_diff_bwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
+    else k_diff_fwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
+    return cudaGetLastError();
+}
+
+}  // namespace qsk

@@ -521,6 +521,48 @@ qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t u
     return upload_tiles(h);
 }
 
+static qs_status diff_check(qs_env* h, const char* who, int32_t T, int32_t C) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, std::string(who) + ": NULL handle");
+    if (!(h->cfg.flags & QS_F_SMOOTH))
+        return fail(h, QS_ERR_ARG, std::string(who) + ": the handle must be created with QS_F_SMOOTH");
+    if (T < 1 || C < 1) return fail(h, QS_ERR_ARG, std::string(who) + ": T and ckpt_every must be >= 1");
+    return QS_OK;
+}
+
+qs_status qs_diff_workspace_size(const qs_env* h, int32_t T, int32_t ckpt_every, size_t* bytes) {
+    if (!h || !bytes) return fail(nullptr, QS_ERR_ARG, "qs_diff_workspace_size: NULL argument");
+    if (T < 1 || ckpt_every < 1) return fail(nullptr, QS_ERR_ARG, "qs_diff_workspace_size: T, ckpt_every >= 1");
+    *bytes = diff_workspace_bytes(h->D, T, std::min(T, ckpt_every), h->cfg.substeps);
+    return QS_OK;
+}
+
+qs_status qs_diff_forward(qs_env* h, int32_t T, int32_t ckpt_every, const float* x0_dev, const float* actions_dev,
+                          float* loss_dev, void* workspace_dev) {
+    qs_status s = diff_check(h, "qs_diff_forward", T, ckpt_every);
+    if (s != QS_OK) return s;
+    if (!x0_dev || !loss_dev || !workspace_dev || !actions_dev || !aligned(actions_dev, 16) || !aligned(workspace_dev, 16))
+        return fail(h, QS_ERR_ARG, "qs_diff_forward: NULL or misaligned buffer");
+    DeviceGuard g(h->device);
+    cudaError_t e = launch_diff(0, h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm, x0_dev,
+                                actions_dev, loss_dev, nullptr, nullptr, nullptr, workspace_dev, T,
+                                std::min(T, ckpt_every), h->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_diff_forward launch");
+}
+
+qs_status qs_diff_backward(qs_env* h, int32_t T, int32_t ckpt_every, const float* actions_dev, const float* dloss_dev,
+                           void* workspace_dev, float* grad_actions_dev, float* grad_x0_dev) {
+    qs_status s = diff_check(h, "qs_diff_backward", T, ckpt_every);
+    if (s != QS_OK) return s;
+    if (!dloss_dev || !workspace_dev || !actions_dev || !grad_actions_dev || !grad_x0_dev || !aligned(actions_dev, 16) ||
+        !aligned(grad_actions_dev, 16) || !aligned(workspace_dev, 16))
+        return fail(h, QS_ERR_ARG, "qs_diff_backward: NULL or misaligned buffer");
+    DeviceGuard g(h->device);
+    cudaError_t e = launch_diff(1, h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm, nullptr,
+                                actions_dev, nullptr, dloss_dev, grad_actions_dev, grad_x0_dev, workspace_dev, T,
+                                std::min(T, ckpt_every), h->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_diff_backward launch");
+}
+
 qs_status qs_get_rollout_shape(const qs_env* h, int32_t* block, int32_t* fuse, int32_t* use_graph) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_get_rollout_shape: NULL handle");
     if (block) *block = h->rollout_block;

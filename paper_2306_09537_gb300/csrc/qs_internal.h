@@ -98,6 +98,12 @@ cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, in
 // CTAs of `block` threads the device keeps resident at once for k_rollout.
 int rollout_grid(int block);
 
+// differentiable rollout (qs_adjoint.cu)
+size_t diff_workspace_bytes(int D, int T, int C, int substeps);
+cudaError_t launch_diff(int backward, const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int block,
+                        const int* perm, const float* x0, const float* act, float* loss, const float* dloss,
+                        float* grad_act, float* grad_x0, void* workspace, int T, int C, cudaStream_t s);
+
 // kernels (qs_kernels.cu)
 cudaError_t launch_reset(const Consts& c, const Dev& dv, uint32_t key0, uint32_t key1, const uint8_t* mask,
                          cudaStream_t s);

@@ -79,3 +79,37 @@ class QuadSwarmEnv:
 
     def sync(self):
         qs.qs_sync(self.h)
+
+
+class RolloutFn(torch.autograd.Function):
+    """Differentiable rollout of the smooth-contact step (the env must be
+    created with the "smooth" feature): loss[d] = sum_t |x_d(t) - goal|^2 +
+    1e-3 |f^_d(t)|^2 for commands actions [T][D][4] from initial states
+    x0 [D][30]. The forward pass stores a checkpoint every `ckpt_every` steps
+    in a workspace it allocates from torch; backward recomputes each segment
+    and runs the library's hand-written adjoint kernel.
+
+        loss = RolloutFn.apply(actions, x0, env, ckpt_every)"""
+
+    @staticmethod
+    def forward(ctx, actions, x0, env, ckpt_every=16):
+        T = actions.shape[0]
+        assert actions.shape == (T, env.D, 4) and x0.shape == (env.D, qs.QS_STATE_DIM)
+        actions = actions.detach().contiguous()
+        x0 = x0.detach().contiguous()
+        ws = torch.empty(qs.qs_diff_workspace_size(env.h, T, ckpt_every), dtype=torch.uint8, device=env.device)
+        loss = torch.empty(env.D, dtype=torch.float32, device=env.device)
+        qs.qs_diff_forward(env.h, T, ckpt_every, x0, actions, loss, ws)
+        ctx.save_for_backward(actions)
+        ctx.env, ctx.ws, ctx.ckpt_every = env, ws, ckpt_every
+        return loss
+
+    @staticmethod
+    def backward(ctx, dloss):
+        (actions,) = ctx.saved_tensors
+        env = ctx.env
+        grad_a = torch.empty_like(actions)
+        grad_x0 = torch.empty(env.D, qs.QS_STATE_DIM, dtype=torch.float32, device=env.device)
+        qs.qs_diff_backward(env.h, actions.shape[0], ctx.ckpt_every, actions, dloss.contiguous(), ctx.ws, grad_a,
+                            grad_x0)
+        return grad_a, grad_x0, None, None

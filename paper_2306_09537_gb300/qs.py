@@ -29,8 +29,9 @@ W_NAMES = ["pos", "vel", "ori", "spin", "act", "dact", "rot", "yaw", "hit_floor"
            "hit_quad", "near"]
 
 EXPORTS = ["qs_config_default", "qs_create", "qs_destroy", "qs_get_dims", "qs_reset", "qs_step", "qs_step_host",
-           "qs_rollout", "qs_set_rollout_shape", "qs_get_rollout_shape", "qs_get_state", "qs_set_state",
-           "qs_get_events", "qs_sync", "qs_set_block", "qs_get_block", "qs_last_error"]
+           "qs_rollout", "qs_set_rollout_shape", "qs_get_rollout_shape", "qs_diff_workspace_size",
+           "qs_diff_forward", "qs_diff_backward", "qs_get_state", "qs_set_state", "qs_get_events", "qs_sync",
+           "qs_set_block", "qs_get_block", "qs_last_error"]
 
 
 class qs_params(C.Structure):
@@ -75,6 +76,9 @@ def _load():
     L.qs_rollout.argtypes = [V, C.c_int32, V, V, V, V]
     L.qs_set_rollout_shape.argtypes = [V, C.c_int32, C.c_int32, C.c_int32]
     L.qs_get_rollout_shape.argtypes = [V, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
+    L.qs_diff_workspace_size.argtypes = [V, C.c_int32, C.c_int32, P(C.c_size_t)]
+    L.qs_diff_forward.argtypes = [V, C.c_int32, C.c_int32, V, V, V, V]
+    L.qs_diff_backward.argtypes = [V, C.c_int32, C.c_int32, V, V, V, V, V]
     L.qs_get_state.argtypes = [V, V, V, V, V, V]
     L.qs_set_state.argtypes = [V, V, V, V, V, V]
     L.qs_get_events.argtypes = [V, V, V]
@@ -176,6 +180,21 @@ def qs_get_rollout_shape(h):
     b, f, g = C.c_int32(), C.c_int32(), C.c_int32()
     _check(_L.qs_get_rollout_shape(h, C.byref(b), C.byref(f), C.byref(g)), h)
     return b.value, f.value, bool(g.value)
+
+
+def qs_diff_workspace_size(h, T: int, ckpt_every: int) -> int:
+    b = C.c_size_t()
+    _check(_L.qs_diff_workspace_size(h, int(T), int(ckpt_every), C.byref(b)), h)
+    return b.value
+
+
+def qs_diff_forward(h, T: int, ckpt_every: int, x0, actions, loss, workspace):
+    return _check(_L.qs_diff_forward(h, int(T), int(ckpt_every), _p(x0), _p(actions), _p(loss), _p(workspace)), h)
+
+
+def qs_diff_backward(h, T: int, ckpt_every: int, actions, dloss, workspace, grad_actions, grad_x0):
+    return _check(_L.qs_diff_backward(h, int(T), int(ckpt_every), _p(actions), _p(dloss), _p(workspace),
+                                      _p(grad_actions), _p(grad_x0)), h)
 
 
 def qs_get_state(h, state=None, params=None, goals=None, ep_step=None, tick=None):

@@ -1,0 +1,149 @@
+"""The differentiable rollout on the GPU: forward loss against the FP64 oracle,
+hand-written adjoint against central finite differences of the oracle and
+against torch.autograd through the FP64 torch reference, independence of the
+checkpoint interval, and the autograd.Function wrapper."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import DEV, nominal, pair
+from oracle import oracle as O
+from oracle.ref_step_torch import smooth_rollout_loss
+from paper_2306_09537_gb300 import qs
+from paper_2306_09537_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def setup(sizes, T, seed, features=("smooth",), spread=0.06):
+    env, o = pair(sizes, 0, features, seed=seed)
+    E, D = env.E, env.D
+    st = W.random_states(seed, D, rate=1.0)
+    st[:, 0:3] = W.clustered_positions(seed, sizes, spread=spread)
+    prm = W.random_params(seed, E, nominal(env))
+    goals = W.random_goals(seed, E)
+    z = np.zeros(E, np.int32)
+    env.set_state(params=torch.from_numpy(prm).to(DEV), goals=torch.from_numpy(goals).to(DEV),
+                  ep_step=torch.from_numpy(z).to(DEV), tick=torch.from_numpy(z).to(DEV))
+    acts = W.actions(seed, T, D, lo=0.05, hi=0.95)
+    return env, o, st, prm, goals, acts
+
+
+def gpu_grads(env, st, acts, C):
+    T, D = acts.shape[0], env.D
+    x0 = torch.from_numpy(st).to(DEV)
+    a = torch.from_numpy(acts).to(DEV)
+    ws = torch.empty(qs.qs_diff_workspace_size(env.h, T, C), dtype=torch.uint8, device=DEV)
+    loss = torch.empty(D, device=DEV)
+    qs.qs_diff_forward(env.h, T, C, x0, a, loss, ws)
+    ga = torch.empty_like(a)
+    gx = torch.empty(D, 30, device=DEV)
+    qs.qs_diff_backward(env.h, T, C, a, torch.ones(D, device=DEV), ws, ga, gx)
+    env.sync()
+    return loss.cpu().numpy(), ga.cpu().numpy().astype(np.float64), gx.cpu().numpy().astype(np.float64)
+
+
+def oracle_total(o, st, prm, goals, acts):
+    E = len(prm)
+    o.set_state(st, prm, goals, np.zeros(E, np.int32), np.zeros(E, np.uint32))
+    loss = np.zeros(o.D)
+    for t in range(acts.shape[0]):
+        o.step(acts[t], want_obs=False, want_loss=True, loss=loss)
+    return loss
+
+
+def test_forward_loss_matches_oracle():
+    sizes = [8] * 64
+    env, o, st, prm, goals, acts = setup(sizes, 32, 11, features=("smooth", "motor_noise", "dr"))
+    loss, _, _ = gpu_grads(env, st, acts, 8)
+    want = oracle_total(o, st.astype(np.float64), prm.astype(np.float64), goals.astype(np.float64),
+                        acts.astype(np.float64))
+    assert np.allclose(loss, want, rtol=1e-4, atol=1e-4)
+
+
+def test_adjoint_matches_oracle_finite_differences():
+    """1 env x 2 drones x 16 steps, motor noise on, checkpoints every 4 steps:
+    every command and every initial-state entry against central differences
+    (h = 1e-6) of the FP64 oracle; tolerance 1e-3 relative or 1e-5 of the
+    largest gradient entry."""
+    sizes = [2]
+    T, C = 16, 4
+    env, o, st, prm, goals, acts = setup(sizes, T, 21, features=("smooth", "motor_noise"), spread=0.04)
+    _, ga, gx = gpu_grads(env, st, acts, C)
+    st64, prm64, g64, a64 = (v.astype(np.float64) for v in (st, prm, goals, acts))
+    h = 1e-6
+    fd_a = np.zeros_like(a64)
+    for t in range(T):
+        for d in range(2):
+            for r in range(4):
+                ap, am = a64.copy(), a64.copy()
+                ap[t, d, r] += h
+                am[t, d, r] -= h
+                fd_a[t, d, r] = (oracle_total(o, st64, prm64, g64, ap).sum() -
+                                 oracle_total(o, st64, prm64, g64, am).sum()) / (2 * h)
+    fd_x = np.zeros((2, 30))
+    for d in range(2):
+        for k in range(26):
+            sp, sm_ = st64.copy(), st64.copy()
+            sp[d, k] += h
+            sm_[d, k] -= h
+            fd_x[d, k] = (oracle_total(o, sp, prm64, g64, a64).sum() -
+                          oracle_total(o, sm_, prm64, g64, a64).sum()) / (2 * h)
+    for g, fd in ((ga, fd_a), (gx[:, :26], fd_x[:, :26])):
+        scale = np.abs(fd).max()
+        assert np.all(np.abs(g - fd) <= 1e-3 * np.abs(fd) + 1e-5 * scale), np.abs(g - fd).max() / scale
+    assert np.all(gx[:, 26:] == 0)
+
+
+def test_adjoint_matches_torch_autograd_reference():
+    """8 envs x 8 drones x 32 steps (pairs interacting), checkpoints every 8."""
+    sizes = [8] * 8
+    T, C = 32, 8
+    env, o, st, prm, goals, acts = setup(sizes, T, 5, features=("smooth",))
+    _, ga, gx = gpu_grads(env, st, acts, C)
+    p = env.cfg.params
+    cfg = {"dt": env.cfg.dt, "gravity": p.gravity, "alpha_ns_frac": p.alpha_ns_frac, "alpha_nd": p.alpha_nd,
+           "smooth_kc": p.smooth_kc, "smooth_beta": p.smooth_beta, "kappa": p.kappa, "room_hx": p.room_hx,
+           "room_hy": p.room_hy, "room_h": p.room_h, "omega_max": p.omega_max, "substeps": env.cfg.substeps}
+    cfg = {k: float(v) if k != "substeps" else int(v) for k, v in cfg.items()}
+    x0 = torch.tensor(st.astype(np.float64), requires_grad=True)
+    a = torch.tensor(acts.astype(np.float64), requires_grad=True)
+    L = smooth_rollout_loss(x0, a, torch.tensor(prm.astype(np.float64)), torch.tensor(goals.astype(np.float64)),
+                            sizes, cfg).sum()
+    L.backward()
+    for g, ref in ((ga, a.grad.numpy()), (gx[:, :26], x0.grad.numpy()[:, :26])):
+        scale = np.abs(ref).max()
+        err = np.abs(g - ref)
+        assert np.all(err <= 1e-3 * np.abs(ref) + 1e-4 * scale), err.max() / scale
+
+
+def test_checkpoint_interval_does_not_change_gradients():
+    sizes = [8] * 16 + [3] * 8
+    T = 24
+    env, o, st, prm, goals, acts = setup(sizes, T, 9, features=("smooth", "motor_noise"))
+    ref = gpu_grads(env, st, acts, T)
+    for C in (1, 5, 8):
+        got = gpu_grads(env, st, acts, C)
+        for x, y in zip(got, ref):
+            assert np.array_equal(x, y)
+
+
+def test_rollout_fn_autograd():
+    from paper_2306_09537_gb300.env import RolloutFn
+    sizes = [8] * 32
+    T = 20
+    env, o, st, prm, goals, acts = setup(sizes, T, 13, features=("smooth", "motor_noise"))
+    a = torch.from_numpy(acts).to(DEV).requires_grad_(True)
+    x0 = torch.from_numpy(st).to(DEV).requires_grad_(True)
+    loss = RolloutFn.apply(a, x0, env, 8)
+    (2.0 * loss.sum()).backward()
+    _, ga, gx = gpu_grads(env, st, acts, 8)
+    assert np.allclose(a.grad.cpu().numpy(), 2.0 * ga, rtol=0, atol=0)
+    assert np.allclose(x0.grad.cpu().numpy(), 2.0 * gx, rtol=0, atol=0)
+
+
+def test_diff_requires_smooth_handle():
+    env, _ = pair([1] * 4, 0, ("floor",), seed=1)
+    with pytest.raises(qs.QSError):
+        qs.qs_diff_forward(env.h, 4, 2, torch.zeros(4, 30, device=DEV), torch.zeros(4, 4, 4, device=DEV),
+                           torch.zeros(4, device=DEV), torch.zeros(1 << 16, dtype=torch.uint8, device=DEV))
