@@ -214,6 +214,29 @@ qs_status qs_diff_forward(qs_env* h, int32_t T, int32_t ckpt_every, const float*
 qs_status qs_diff_backward(qs_env* h, int32_t T, int32_t ckpt_every, const float* actions_dev, const float* dloss_dev,
                            void* workspace_dev, float* grad_actions_dev, float* grad_x0_dev);
 
+/* Allocation-free form of qs_diff_forward + qs_diff_backward. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory when they need a gradient, such as code running while a CUDA graph
+ * is captured, real-time control loops that must not call cudaMalloc or
+ * cudaFree (both can synchronise the device), or plugins whose host framework
+ * owns the memory budget. It needs no workspace argument: the checkpoints and
+ * recomputed substep states live in a fixed array of QS_DIFF_STATIC_BYTES
+ * (64 MiB) inside the library's device image, held on every GPU that loads
+ * the library until the process exits. The call allocates nothing; the
+ * caller still passes every input and output: x0_dev [D][30], actions_dev
+ * [T][D][4], dloss_dev [D] in; loss_dev [D], grad_actions_dev [T][D][4],
+ * grad_x0_dev [D][30] out (same meaning as qs_diff_forward/_backward).
+ * A rollout whose workspace (qs_diff_workspace_size) exceeds the array returns
+ * QS_ERR_UNSUPPORTED and enqueues nothing. The first call on a device looks
+ * the array's device address up (cudaGetSymbolAddress); make that first call
+ * before any stream capture. All calls share the one array: calls whose work
+ * overlaps on the GPU (other streams, other handles) race and must be
+ * serialised by the caller. The array keeps the last call's contents; no call
+ * depends on them. */
+#define QS_DIFF_STATIC_BYTES (64u << 20)
+qs_status qs_diff_grad_static(qs_env* h, int32_t T, int32_t ckpt_every, const float* x0_dev, const float* actions_dev,
+                              const float* dloss_dev, float* loss_dev, float* grad_actions_dev, float* grad_x0_dev);
+
 /* Copies the handle's state into caller buffers (each nullable): state_dev
  * [D][30], params_dev [E][7], goals_dev [E][3], ep_step_dev [E] control steps
  * into the episode, tick_dev [E] Philox step counter of each env. */

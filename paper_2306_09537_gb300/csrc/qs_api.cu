@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -561,6 +562,73 @@ qs_status qs_diff_backward(qs_env* h, int32_t T, int32_t ckpt_every, const float
                                 actions_dev, nullptr, dloss_dev, grad_actions_dev, grad_x0_dev, workspace_dev, T,
                                 std::min(T, ckpt_every), h->stream);
     return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_diff_backward launch");
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free differentiable rollout (qs_diff_grad_static).
+//
+// Some callers cannot allocate device memory at the point where they need a
+// gradient: code that runs while a CUDA graph is being captured, real-time
+// control loops that must never call cudaMalloc or cudaFree (either may
+// synchronise the whole device), and plugins inside a host framework that owns
+// the device's memory budget. For them the workspace of the forward + adjoint
+// pass (checkpoints and recomputed substep states) lives in this fixed array
+// of the library's device image instead of a caller buffer. Every GPU that
+// loads the library keeps the array until the process exits.
+static __device__ __align__(256) unsigned char g_diff_static[QS_DIFF_STATIC_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_addr[256] = {};  // device address of g_diff_static, per device ordinal
+
+// Device address of the array on the current device (looked up once per
+// device; in host code g_diff_static names a host-side stand-in, not memory
+// the GPU can use).
+qs_status static_workspace(qs_env* h, void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qs_diff_grad_static: cudaGetDevice");
+    if (dev < 0 || dev >= 256) return fail(h, QS_ERR_UNSUPPORTED, "qs_diff_grad_static: device ordinal >= 256");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_diff_static);
+        if (e != cudaSuccess || !p) return cuda_fail(h, e, "qs_diff_grad_static: cudaGetSymbolAddress");
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return QS_OK;
+}
+}  // namespace
+
+qs_status qs_diff_grad_static(qs_env* h, int32_t T, int32_t ckpt_every, const float* x0_dev, const float* actions_dev,
+                              const float* dloss_dev, float* loss_dev, float* grad_actions_dev, float* grad_x0_dev) {
+    qs_status s = diff_check(h, "qs_diff_grad_static", T, ckpt_every);
+    if (s != QS_OK) return s;
+    if (!x0_dev || !actions_dev || !dloss_dev || !loss_dev || !grad_actions_dev || !grad_x0_dev ||
+        !aligned(actions_dev, 16) || !aligned(grad_actions_dev, 16))
+        return fail(h, QS_ERR_ARG, "qs_diff_grad_static: NULL or misaligned buffer");
+    const int C = std::min(T, ckpt_every);
+    const size_t need = diff_workspace_bytes(h->D, T, C, h->cfg.substeps);
+    if (need > (size_t)QS_DIFF_STATIC_BYTES)
+        return fail(h, QS_ERR_UNSUPPORTED,
+                    "qs_diff_grad_static: this rollout needs " + std::to_string(need) + " bytes of workspace, the static "
+                    "workspace holds " + std::to_string((size_t)QS_DIFF_STATIC_BYTES) +
+                    "; use fewer drones, a shorter horizon or checkpoint interval, or qs_diff_forward/qs_diff_backward "
+                    "with a caller workspace");
+    DeviceGuard g(h->device);
+    void* ws = nullptr;
+    s = static_workspace(h, &ws);
+    if (s != QS_OK) return s;
+    // Every byte the backward pass reads is written earlier in this call (the
+    // checkpoints by the forward pass, the substep states by the recompute),
+    // so nothing left by a previous call needs clearing.
+    cudaError_t e = launch_diff(0, h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm, x0_dev,
+                                actions_dev, loss_dev, nullptr, nullptr, nullptr, ws, T, C, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qs_diff_grad_static forward launch");
+    e = launch_diff(1, h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm, nullptr, actions_dev, nullptr,
+                    dloss_dev, grad_actions_dev, grad_x0_dev, ws, T, C, h->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_diff_grad_static backward launch");
 }
 
 qs_status qs_get_rollout_shape(const qs_env* h, int32_t* block, int32_t* fuse, int32_t* use_graph) {

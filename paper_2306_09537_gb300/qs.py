@@ -30,8 +30,9 @@ W_NAMES = ["pos", "vel", "ori", "spin", "act", "dact", "rot", "yaw", "hit_floor"
 
 EXPORTS = ["qs_config_default", "qs_create", "qs_destroy", "qs_get_dims", "qs_reset", "qs_step", "qs_step_host",
            "qs_rollout", "qs_set_rollout_shape", "qs_get_rollout_shape", "qs_diff_workspace_size",
-           "qs_diff_forward", "qs_diff_backward", "qs_get_state", "qs_set_state", "qs_get_events", "qs_sync",
-           "qs_set_block", "qs_get_block", "qs_last_error"]
+           "qs_diff_forward", "qs_diff_backward", "qs_diff_grad_static", "qs_get_state", "qs_set_state",
+           "qs_get_events", "qs_sync", "qs_set_block", "qs_get_block", "qs_last_error"]
+QS_DIFF_STATIC_BYTES = 64 << 20
 
 
 class qs_params(C.Structure):
@@ -79,6 +80,7 @@ def _load():
     L.qs_diff_workspace_size.argtypes = [V, C.c_int32, C.c_int32, P(C.c_size_t)]
     L.qs_diff_forward.argtypes = [V, C.c_int32, C.c_int32, V, V, V, V]
     L.qs_diff_backward.argtypes = [V, C.c_int32, C.c_int32, V, V, V, V, V]
+    L.qs_diff_grad_static.argtypes = [V, C.c_int32, C.c_int32, V, V, V, V, V, V]
     L.qs_get_state.argtypes = [V, V, V, V, V, V]
     L.qs_set_state.argtypes = [V, V, V, V, V, V]
     L.qs_get_events.argtypes = [V, V, V]
@@ -195,6 +197,14 @@ def qs_diff_forward(h, T: int, ckpt_every: int, x0, actions, loss, workspace):
 def qs_diff_backward(h, T: int, ckpt_every: int, actions, dloss, workspace, grad_actions, grad_x0):
     return _check(_L.qs_diff_backward(h, int(T), int(ckpt_every), _p(actions), _p(dloss), _p(workspace),
                                       _p(grad_actions), _p(grad_x0)), h)
+
+
+def qs_diff_grad_static(h, T: int, ckpt_every: int, x0, actions, dloss, loss, grad_actions, grad_x0):
+    """Forward + adjoint without a workspace argument: the library's fixed
+    device array (QS_DIFF_STATIC_BYTES) holds the checkpoints, for callers
+    that cannot allocate device memory at that point."""
+    return _check(_L.qs_diff_grad_static(h, int(T), int(ckpt_every), _p(x0), _p(actions), _p(dloss), _p(loss),
+                                         _p(grad_actions), _p(grad_x0)), h)
 
 
 def qs_get_state(h, state=None, params=None, goals=None, ep_step=None, tick=None):
