@@ -258,10 +258,14 @@ qs_status qs_get_events(qs_env* h, uint32_t* events_dev, int16_t* knn_dev);
  * (QS_ERR_STATE_NONFINITE stays reported until the next full qs_reset). */
 qs_status qs_sync(qs_env* h);
 
-/* Launch shape of one swarm-width class (the envs whose swarm size rounds up
- * to the power of two `width`, 1..64): `block` threads per CTA, a multiple of
- * 32 and of `width`, at most 256. Used by the autotuner; results do not
+/* Launch shape of qs_step for one swarm-width class (the envs whose swarm size
+ * rounds up to the power of two `width`, 1..64): `block` threads per CTA, a
+ * multiple of 32 and of `width`, at most 256; or QS_BLOCK_WARP_SPECIALISED
+ * (widths <= 32, the default there): CTAs of two warps per 32 drones, one
+ * integrating the dynamics while the other draws the motor and sensor noise
+ * and writes the observation rows. Used by the autotuner; results do not
  * depend on it. QS_ERR_ARG for an invalid shape or a class the handle lacks. */
+#define QS_BLOCK_WARP_SPECIALISED 1
 qs_status qs_set_block(qs_env* h, int32_t width, int32_t block);
 
 /* Reads back the launch shape of a class (block 0 when the handle has none). */

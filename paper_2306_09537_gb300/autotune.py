@@ -52,8 +52,11 @@ def tune(env, steps: int = 32, horizon: int = 64, reps: int = 3, apply: bool = T
         with torch.cuda.stream(stream):
             for w in classes:
                 best = None
-                for b in (32, 64, 128, 256):
-                    if b % w or b < w:
+                for b in (qs.QS_BLOCK_WARP_SPECIALISED, 32, 64, 128, 256):
+                    if b == qs.QS_BLOCK_WARP_SPECIALISED:
+                        if w > 32:
+                            continue
+                    elif b % w or b < w:
                         continue
                     qs.qs_set_block(twin.h, w, b)
 

@@ -101,7 +101,7 @@ __device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const 
     for (int r = 0; r < 4; ++r) uf1[r] = fmaf(p.alag, u[r] - s.uf[r], s.uf[r]);
     float nrm[4] = {0.f, 0.f, 0.f, 0.f};
     if (c.flags & QS_F_MOTOR_NOISE) {
-        const uint4 q = philox(tick, (uint32_t)d, ctr_word(TAG_MOTOR, (uint32_t)sub, 0), c.key0, c.key1);
+        const uint4 q = philox_rk(tick, (uint32_t)d, ctr_word(TAG_MOTOR, (uint32_t)sub, 0), c.rk);
         const float2 n01 = box_muller(u01(q.x), u01(q.y));
         const float2 n23 = box_muller(u01(q.z), u01(q.w));
         nrm[0] = n01.x; nrm[1] = n01.y; nrm[2] = n23.x; nrm[3] = n23.y;

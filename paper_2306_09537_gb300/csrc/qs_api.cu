@@ -30,6 +30,7 @@ struct qs_env {
     std::vector<ClassPlan> plan;
     std::vector<int> class_first_slot;  // first slot of each class in perm
     std::vector<int> class_slots;       // slots per class
+    std::vector<int> perm_h;            // envs grouped by width class (host copy of d_perm)
     Tile* d_tiles = nullptr;
     int* d_perm = nullptr;
     void* arena = nullptr;
@@ -118,6 +119,7 @@ void build_consts(qs_env* h) {
     c.obs_dim = 18 + 6 * f.k_neighbors;
     c.key0 = (uint32_t)(f.seed & 0xffffffffu);
     c.key1 = (uint32_t)(f.seed >> 32);
+    set_round_keys(c);
 }
 
 // Tiles of one class: `slots` consecutive slots starting at `first`, each CTA
@@ -130,7 +132,10 @@ void build_tiles(qs_env* h, std::vector<Tile>& tiles) {
         cp.tile_off = (int)tiles.size();
         cp.n_tiles = 0;
         for (int s = 0; s < h->class_slots[ci]; s += per) {
-            tiles.push_back(Tile{h->class_first_slot[ci] + s, std::min(per, h->class_slots[ci] - s), cp.W, 0});
+            const int first = h->class_first_slot[ci] + s, count = std::min(per, h->class_slots[ci] - s);
+            int contig = 1;
+            for (int i = 1; i < count; ++i) contig &= h->perm_h[first + i] == h->perm_h[first] + i;
+            tiles.push_back(Tile{first, count, cp.W, contig});
             ++cp.n_tiles;
         }
     }
@@ -313,7 +318,9 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
             if (width_class(sizes[e]) == W) perm.push_back(e);
         int n = (int)perm.size() - first;
         if (n > 0) {
-            h->plan.push_back(ClassPlan{W, default_block(W, n), 0, 0});
+            // width <= 32: warp-specialised per-call step on tiles of 32 drone lanes
+            const int ws = W <= 32 ? 1 : 0;
+            h->plan.push_back(ClassPlan{W, ws ? 32 : default_block(W, n), ws, 0, 0});
             h->class_first_slot.push_back(first);
             h->class_slots.push_back(n);
         }
@@ -364,6 +371,7 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
         delete h;
         return fail(nullptr, QS_ERR_CUDA, "qs_create: initial upload failed");
     }
+    h->perm_h = perm;
     qs_status s = upload_tiles(h);
     if (s != QS_OK) {
         std::string m = h->err;
@@ -410,6 +418,7 @@ qs_status qs_reset(qs_env* h, uint64_t seed, const uint8_t* env_mask_dev, float*
     if (!env_mask_dev) {
         h->c.key0 = k0;
         h->c.key1 = k1;
+        set_round_keys(h->c);
         cudaError_t e = cudaMemsetAsync(h->dv.status, 0, sizeof(int32_t), h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "qs_reset");
     }
@@ -679,14 +688,17 @@ qs_status qs_sync(qs_env* h) {
 
 qs_status qs_set_block(qs_env* h, int32_t width, int32_t block) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_set_block: NULL handle");
-    if (block < 32 || block > 256 || block % 32 != 0 || block % width != 0)
-        return fail(h, QS_ERR_ARG, "qs_set_block: block must be 32..256, a multiple of 32 and of width");
+    const bool ws = block == QS_BLOCK_WARP_SPECIALISED;
+    if (ws ? width > 32 : (block < 32 || block > 256 || block % 32 != 0 || block % width != 0))
+        return fail(h, QS_ERR_ARG, "qs_set_block: block must be 32..256, a multiple of 32 and of width, or "
+                                   "QS_BLOCK_WARP_SPECIALISED for widths <= 32");
     for (ClassPlan& cp : h->plan) {
         if (cp.W != width) continue;
         DeviceGuard g(h->device);
         cudaError_t e = cudaStreamSynchronize(h->stream);  // the old tile table may be in use
         if (e != cudaSuccess) return cuda_fail(h, e, "qs_set_block");
-        cp.block = block;
+        cp.ws = ws ? 1 : 0;
+        cp.block = ws ? 32 : block;
         return upload_tiles(h);
     }
     return fail(h, QS_ERR_ARG, "qs_set_block: no envs of that width class");
@@ -696,7 +708,7 @@ qs_status qs_get_block(const qs_env* h, int32_t width, int32_t* block) {
     if (!h || !block) return fail(nullptr, QS_ERR_ARG, "qs_get_block: NULL argument");
     *block = 0;
     for (const ClassPlan& cp : h->plan)
-        if (cp.W == width) *block = cp.block;
+        if (cp.W == width) *block = cp.ws ? QS_BLOCK_WARP_SPECIALISED : cp.block;
     return QS_OK;
 }
 

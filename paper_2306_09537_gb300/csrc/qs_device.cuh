@@ -33,6 +33,25 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return make_uint4(x0, x1, x2, x3);
 }
 
+// Same generator with the ten round keys precomputed (the Weyl schedule is the
+// same for every thread): each round is two 32x32->64 multiplies and two
+// three-input XORs.
+__device__ __forceinline__ uint4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, const uint32_t rk[20]) {
+    uint32_t x0 = c0, x1 = c1, x2 = c2, x3 = 0u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * x0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;
+        const uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ rk[2 * r];
+        const uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ rk[2 * r + 1];
+        x1 = (uint32_t)p1;
+        x3 = (uint32_t)p0;
+        x0 = y0;
+        x2 = y2;
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+
 __device__ __forceinline__ uint32_t ctr_word(uint32_t tag, uint32_t sub, uint32_t blk) {
     return (tag << 16) | (sub << 8) | blk;
 }
@@ -51,8 +70,8 @@ __device__ __forceinline__ float2 box_muller(float u0, float u1) {
 // Six N(0,1) draws of a collision or wall perturbation (blocks 0 and 1).
 __device__ __forceinline__ void six_normals(const Consts& c, uint32_t tick, uint32_t id, uint32_t tag, uint32_t sub,
                                             float n[6]) {
-    const uint4 a = philox(tick, id, ctr_word(tag, sub, 0), c.key0, c.key1);
-    const uint4 b = philox(tick, id, ctr_word(tag, sub, 1), c.key0, c.key1);
+    const uint4 a = philox_rk(tick, id, ctr_word(tag, sub, 0), c.rk);
+    const uint4 b = philox_rk(tick, id, ctr_word(tag, sub, 1), c.rk);
     const float2 p0 = box_muller(u01(a.x), u01(a.y));
     const float2 p1 = box_muller(u01(a.z), u01(a.w));
     const float2 p2 = box_muller(u01(b.x), u01(b.y));
@@ -285,8 +304,20 @@ __device__ __forceinline__ void rotate_polar(float R[9], const float w[3], float
 // One physics substep of one drone (S1 .. S8). fh: this control step's
 // normalised commands; u = sqrt(fh). pacc: smooth-mode pair acceleration
 // (zero otherwise). Returns the substep's event bits.
+__device__ __forceinline__ void motor_normals(const Consts& c, uint32_t tick, int d, int sub, float n[4]) {
+    const uint4 q = philox_rk(tick, (uint32_t)d, ctr_word(TAG_MOTOR, (uint32_t)sub, 0), c.rk);
+    const float2 n01 = box_muller(u01(q.x), u01(q.y));
+    const float2 n23 = box_muller(u01(q.z), u01(q.w));
+    n[0] = n01.x;
+    n[1] = n01.y;
+    n[2] = n23.x;
+    n[3] = n23.y;
+}
+
+// nrm: this substep's four motor-noise normals when already drawn elsewhere
+// (nullptr: draw them here).
 __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts& c, const float u[4], uint32_t tick,
-                                            int d, int sub, const float pacc[3]) {
+                                            int d, int sub, const float pacc[3], const float* nrm = nullptr) {
     uint32_t ev = 0;
     const float dt = c.dt, g = c.g;
     // S1 first-order motor lag on the normalised rotor speed
@@ -294,13 +325,17 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     for (int r = 0; r < 4; ++r) s.uf[r] = fmaf(p.alag, u[r] - s.uf[r], s.uf[r]);
     // S2 AR(1) motor noise and per-rotor thrust f = f_max uf^2 + eps
     if (c.flags & QS_F_MOTOR_NOISE) {
-        const uint4 q = philox(tick, (uint32_t)d, ctr_word(TAG_MOTOR, (uint32_t)sub, 0), c.key0, c.key1);
-        const float2 n01 = box_muller(u01(q.x), u01(q.y));
-        const float2 n23 = box_muller(u01(q.z), u01(q.w));
-        s.eps[0] = fmaf(c.alpha_nd, s.eps[0], p.ans * n01.x);
-        s.eps[1] = fmaf(c.alpha_nd, s.eps[1], p.ans * n01.y);
-        s.eps[2] = fmaf(c.alpha_nd, s.eps[2], p.ans * n23.x);
-        s.eps[3] = fmaf(c.alpha_nd, s.eps[3], p.ans * n23.y);
+        float n[4];
+        if (nrm) {
+            n[0] = nrm[0];
+            n[1] = nrm[1];
+            n[2] = nrm[2];
+            n[3] = nrm[3];
+        } else {
+            motor_normals(c, tick, d, sub, n);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) s.eps[r] = fmaf(c.alpha_nd, s.eps[r], p.ans * n[r]);
     }
     float f[4];
 #pragma unroll
@@ -458,9 +493,9 @@ __device__ __forceinline__ float pair_key(float xi0, float xi1, float xi2, float
 // on w; three Philox blocks of the OBS stream, substream `sub`.
 __device__ __forceinline__ void obs_noise(const Consts& c, uint32_t tick, int d, uint32_t sub, float ex[3], float ev[3],
                                           float ew[3]) {
-    const uint4 a = philox(tick, (uint32_t)d, ctr_word(TAG_OBS, sub, 0), c.key0, c.key1);
-    const uint4 b = philox(tick, (uint32_t)d, ctr_word(TAG_OBS, sub, 1), c.key0, c.key1);
-    const uint4 q = philox(tick, (uint32_t)d, ctr_word(TAG_OBS, sub, 2), c.key0, c.key1);
+    const uint4 a = philox_rk(tick, (uint32_t)d, ctr_word(TAG_OBS, sub, 0), c.rk);
+    const uint4 b = philox_rk(tick, (uint32_t)d, ctr_word(TAG_OBS, sub, 1), c.rk);
+    const uint4 q = philox_rk(tick, (uint32_t)d, ctr_word(TAG_OBS, sub, 2), c.rk);
     ex[0] = (2.0f * u01(a.x) - 1.0f) * c.obs_sx;
     ex[1] = (2.0f * u01(a.y) - 1.0f) * c.obs_sx;
     ex[2] = (2.0f * u01(a.z) - 1.0f) * c.obs_sx;

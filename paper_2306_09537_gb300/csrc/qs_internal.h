@@ -37,8 +37,20 @@ struct Consts {
     float nominal[QS_PARAM_DIM];
     float w[QS_NW];
     uint32_t flags, key0, key1;
+    uint32_t rk[20];  // Philox round keys (k0, k1) of rounds 0..9 for key (key0, key1)
     int substeps, K, episode_steps, obs_dim;
 };
+
+// Fills c.rk from c.key0 / c.key1 (Weyl increments 0x9E3779B9, 0xBB67AE85).
+inline void set_round_keys(Consts& c) {
+    uint32_t k0 = c.key0, k1 = c.key1;
+    for (int r = 0; r < 10; ++r) {
+        c.rk[2 * r] = k0;
+        c.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
 
 // Device buffers owned by a handle.
 struct Dev {
@@ -61,12 +73,13 @@ struct Tile {
     int first;  // first slot (index into perm)
     int count;  // slots in this tile
     int W;      // width class of its slots
-    int pad;
+    int pad;    // 1: the tile's envs are consecutive, so its drones are contiguous
 };
 
 struct ClassPlan {
     int W;         // lanes per env slot (power of two >= N of its envs)
-    int block;     // threads per CTA
+    int block;     // threads per CTA (32 drone lanes per tile when ws)
+    int ws;        // warp-specialised per-call step (W <= 32)
     int n_tiles;
     int tile_off;  // offset of this class's tiles in the tile array
 };

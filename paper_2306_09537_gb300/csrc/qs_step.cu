@@ -70,6 +70,121 @@ __device__ __forceinline__ void topk_insert(uint64_t best[QS_MAX_K], int K, uint
     }
 }
 
+// S9 + S11 for the thread's drone (slot-local index `lane`) against the slot's
+// staged positions / pre-collision velocities (planes of stride nt): collision
+// flag, the Jacobi sum of ((v_j - v_i).n) n over colliding approaching
+// partners (S10), and the sorted neighbour list.
+__device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float thr, int lane, int N, int sbase,
+                                          const float* sx, const float* sv, int nt, int keff, bool coll, bool flag_coll,
+                                          uint32_t& ev, uint64_t best[QS_MAX_K], float dvs[3]) {
+    bool responded = false;
+    for (int j = 0; j < N; ++j) {
+        if (j == lane) continue;
+        const int tj = sbase + j;
+        float dx, dy, dz;
+        const float key = pair_key(s.x[0], s.x[1], s.x[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx, dy, dz);
+        if (flag_coll && key < thr) {
+            ev |= EV_HIT_QUAD;
+            if (coll) {
+                // approaching iff (v_i - v_j) . (x_i - x_j) < 0
+                const float rv0 = s.v[0] - sv[tj], rv1 = s.v[1] - sv[nt + tj], rv2 = s.v[2] - sv[2 * nt + tj];
+                const float app = -(rv0 * dx + rv1 * dy + rv2 * dz);
+                if (app < 0.0f) {
+                    float n0 = 0.f, n1 = 0.f, n2 = 1.f;
+                    if (key > 0.0f) {
+                        const float inv = rsqrtf(key);
+                        n0 = -dx * inv;
+                        n1 = -dy * inv;
+                        n2 = -dz * inv;
+                    }
+                    const float vn = -(rv0 * n0 + rv1 * n1 + rv2 * n2);  // (v_j - v_i) . n
+                    dvs[0] = fmaf(vn, n0, dvs[0]);
+                    dvs[1] = fmaf(vn, n1, dvs[1]);
+                    dvs[2] = fmaf(vn, n2, dvs[2]);
+                    responded = true;
+                }
+            }
+        }
+        if (keff > 0) topk_insert(best, keff, ((uint64_t)__float_as_uint(key) << 32) | (uint32_t)j);
+    }
+    return responded;
+}
+
+// S10: v <- alpha_c (v + sum + eps_v), w <- w + eps_w for a responding drone.
+__device__ __forceinline__ void apply_response(const Consts& c, Drone& s, uint32_t tick, int d, const float dvs[3]) {
+    float n[6];
+    six_normals(c, tick, (uint32_t)d, TAG_COLL, 0, n);
+    s.v[0] = c.alpha_c * (s.v[0] + dvs[0] + c.sig_cv * n[0]);
+    s.v[1] = c.alpha_c * (s.v[1] + dvs[1] + c.sig_cv * n[1]);
+    s.v[2] = c.alpha_c * (s.v[2] + dvs[2] + c.sig_cv * n[2]);
+    comp_add(s.w[0], s.wlo[0], c.sig_cw * n[3]);
+    comp_add(s.w[1], s.wlo[1], c.sig_cw * n[4]);
+    comp_add(s.w[2], s.wlo[2], c.sig_cw * n[5]);
+}
+
+// S13 reward of one drone (Sec. III-E): weighted state terms, event indicators
+// and the proximity term over its neighbours (keys = squared distances).
+__device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s, const EnvRegs& er, const float fh[4],
+                                                uint32_t ev, const uint64_t best[QS_MAX_K], int keff) {
+    const float dgx = s.x[0] - er.g0, dgy = s.x[1] - er.g1, dgz = s.x[2] - er.g2;
+    float r = c.w[QS_W_POS] * sqrtf(dgx * dgx + dgy * dgy + dgz * dgz);
+    r += c.w[QS_W_VEL] * sqrtf(s.v[0] * s.v[0] + s.v[1] * s.v[1] + s.v[2] * s.v[2]);
+    r += c.w[QS_W_ORI] * s.R[8];
+    r += c.w[QS_W_SPIN] * sqrtf(s.w[0] * s.w[0] + s.w[1] * s.w[1] + s.w[2] * s.w[2]);
+    r += c.w[QS_W_ACT] * sqrtf(fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
+    const float q0 = fh[0] - s.fp[0], q1 = fh[1] - s.fp[1], q2 = fh[2] - s.fp[2], q3 = fh[3] - s.fp[3];
+    r += c.w[QS_W_DACT] * sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    r += c.w[QS_W_ROT] * 0.5f * (s.R[0] + s.R[4] + s.R[8] - 1.0f);
+    r += c.w[QS_W_YAW] * s.R[0];
+    r += (ev & EV_HIT_FLOOR) ? c.w[QS_W_HIT_FLOOR] : 0.0f;
+    r += (ev & EV_ON_FLOOR) ? c.w[QS_W_ON_FLOOR] : 0.0f;
+    r += (ev & EV_HIT_WALL) ? c.w[QS_W_HIT_WALL] : 0.0f;
+    r += (ev & EV_HIT_CEIL) ? c.w[QS_W_HIT_CEIL] : 0.0f;
+    r += (ev & EV_HIT_QUAD) ? c.w[QS_W_HIT_QUAD] : 0.0f;
+    if (keff > 0 && c.w[QS_W_NEAR] != 0.0f) {
+        float near = 0.0f;
+#pragma unroll
+        for (int k = 0; k < QS_MAX_K; ++k) {
+            if (k < keff) {
+                const float key = __uint_as_float((uint32_t)(best[k] >> 32));
+                near += fmaxf(1.0f - sqrtf(key) / er.p.prox, 0.0f);
+            }
+        }
+        r += c.w[QS_W_NEAR] * near;
+    }
+    return r;
+}
+
+// End of a control step: previous command, episode counter, done flag,
+// Philox counter, in-place auto-reset, non-finite check.
+__device__ __forceinline__ void end_step(const Consts& c, const Dev& dv, Drone& s, EnvRegs& er, const float fh[4],
+                                         int lane, int e, int d, uint8_t* __restrict__ done) {
+    s.fp[0] = fh[0];
+    s.fp[1] = fh[1];
+    s.fp[2] = fh[2];
+    s.fp[3] = fh[3];
+    const uint32_t tick = er.tick;
+    const int ep = er.ep + 1;
+    const bool is_done = ep >= c.episode_steps;
+    if (lane == 0 && done) done[e] = is_done ? 1 : 0;
+    er.ep = (is_done && (c.flags & QS_F_AUTO_RESET)) ? 0 : ep;
+    er.tick = tick + 1;
+    if (is_done && (c.flags & QS_F_AUTO_RESET)) {
+        // the env starts a new episode in place (new randomisation and goal);
+        // every lane draws the env's values itself, so no exchange is needed
+        float p7[QS_PARAM_DIM], goal[3], full[NPRM_DEV];
+        draw_env(c, c.key0, c.key1, tick, TAG_AUTO_ENV, e, p7, goal);
+        derive(c, p7, full);
+        er.p = prm_from(full);
+        er.g0 = goal[0];
+        er.g1 = goal[1];
+        er.g2 = goal[2];
+        er.redrawn = true;
+        draw_drone(c, c.key0, c.key1, tick, TAG_AUTO_DRONE, d, p7[P_T2W], s);
+    }
+    if (!finite_state(s)) atomicOr(dv.status, 1);
+}
+
 // One control step of the slot's drones. All threads of the CTA call it (the
 // pair pass synchronises the CTA); `act` marks threads that carry a drone.
 // Outputs for this step: obs/rew rows of drone d, done[e] (lane 0). W is
@@ -110,51 +225,14 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
             sv[2 * nt + threadIdx.x] = s.v[2];
         }
         __syncthreads();
-        float dvs0 = 0.f, dvs1 = 0.f, dvs2 = 0.f;
+        float dvs[3] = {0.f, 0.f, 0.f};
         bool responded = false;
         if (act && N > 1) {
             const bool coll = (c.flags & QS_F_COLLISIONS) && !(c.flags & QS_F_SMOOTH) && !observe_only;
             const bool flag_coll = (c.flags & QS_F_COLLISIONS) && !observe_only;
-            for (int j = 0; j < N; ++j) {
-                if (j == lane) continue;
-                const int tj = sbase + j;
-                float dx, dy, dz;
-                const float key = pair_key(s.x[0], s.x[1], s.x[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx, dy, dz);
-                if (flag_coll && key < er.p.thr) {
-                    ev |= EV_HIT_QUAD;
-                    if (coll) {
-                        // approaching iff (v_i - v_j) . (x_i - x_j) < 0
-                        const float rv0 = s.v[0] - sv[tj], rv1 = s.v[1] - sv[nt + tj], rv2 = s.v[2] - sv[2 * nt + tj];
-                        const float app = -(rv0 * dx + rv1 * dy + rv2 * dz);
-                        if (app < 0.0f) {
-                            float n0 = 0.f, n1 = 0.f, n2 = 1.f;
-                            if (key > 0.0f) {
-                                const float inv = rsqrtf(key);
-                                n0 = -dx * inv;
-                                n1 = -dy * inv;
-                                n2 = -dz * inv;
-                            }
-                            const float vn = -(rv0 * n0 + rv1 * n1 + rv2 * n2);  // (v_j - v_i) . n
-                            dvs0 = fmaf(vn, n0, dvs0);
-                            dvs1 = fmaf(vn, n1, dvs1);
-                            dvs2 = fmaf(vn, n2, dvs2);
-                            responded = true;
-                        }
-                    }
-                }
-                if (keff > 0) topk_insert(best, keff, ((uint64_t)__float_as_uint(key) << 32) | (uint32_t)j);
-            }
+            responded = pair_scan(c, s, er.p.thr, lane, N, sbase, sx, sv, nt, keff, coll, flag_coll, ev, best, dvs);
         }
-        if (responded) {
-            float n[6];
-            six_normals(c, tick, (uint32_t)d, TAG_COLL, 0, n);
-            s.v[0] = c.alpha_c * (s.v[0] + dvs0 + c.sig_cv * n[0]);
-            s.v[1] = c.alpha_c * (s.v[1] + dvs1 + c.sig_cv * n[1]);
-            s.v[2] = c.alpha_c * (s.v[2] + dvs2 + c.sig_cv * n[2]);
-            comp_add(s.w[0], s.wlo[0], c.sig_cw * n[3]);
-            comp_add(s.w[1], s.wlo[1], c.sig_cw * n[4]);
-            comp_add(s.w[2], s.wlo[2], c.sig_cw * n[5]);
-        }
+        if (responded) apply_response(c, s, tick, d, dvs);
         __syncthreads();
         if (act) {  // post-collision velocities for the neighbour observation
             sv[threadIdx.x] = s.v[0];
@@ -205,59 +283,8 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
     ev_out = ev;
 
     // ---- S13 reward and done
-    if (rew) {
-        const float dgx = s.x[0] - er.g0, dgy = s.x[1] - er.g1, dgz = s.x[2] - er.g2;
-        float r = c.w[QS_W_POS] * sqrtf(dgx * dgx + dgy * dgy + dgz * dgz);
-        r += c.w[QS_W_VEL] * sqrtf(s.v[0] * s.v[0] + s.v[1] * s.v[1] + s.v[2] * s.v[2]);
-        r += c.w[QS_W_ORI] * s.R[8];
-        r += c.w[QS_W_SPIN] * sqrtf(s.w[0] * s.w[0] + s.w[1] * s.w[1] + s.w[2] * s.w[2]);
-        r += c.w[QS_W_ACT] * sqrtf(fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
-        const float q0 = fh[0] - s.fp[0], q1 = fh[1] - s.fp[1], q2 = fh[2] - s.fp[2], q3 = fh[3] - s.fp[3];
-        r += c.w[QS_W_DACT] * sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
-        r += c.w[QS_W_ROT] * 0.5f * (s.R[0] + s.R[4] + s.R[8] - 1.0f);
-        r += c.w[QS_W_YAW] * s.R[0];
-        r += (ev & EV_HIT_FLOOR) ? c.w[QS_W_HIT_FLOOR] : 0.0f;
-        r += (ev & EV_ON_FLOOR) ? c.w[QS_W_ON_FLOOR] : 0.0f;
-        r += (ev & EV_HIT_WALL) ? c.w[QS_W_HIT_WALL] : 0.0f;
-        r += (ev & EV_HIT_CEIL) ? c.w[QS_W_HIT_CEIL] : 0.0f;
-        r += (ev & EV_HIT_QUAD) ? c.w[QS_W_HIT_QUAD] : 0.0f;
-        if (W > 1 && c.w[QS_W_NEAR] != 0.0f) {
-            float near = 0.0f;
-#pragma unroll
-            for (int k = 0; k < QS_MAX_K; ++k) {
-                if (k < keff) {
-                    const float key = __uint_as_float((uint32_t)(best[k] >> 32));
-                    near += fmaxf(1.0f - sqrtf(key) / er.p.prox, 0.0f);
-                }
-            }
-            r += c.w[QS_W_NEAR] * near;
-        }
-        rew[d] = r;
-    }
-    s.fp[0] = fh[0];
-    s.fp[1] = fh[1];
-    s.fp[2] = fh[2];
-    s.fp[3] = fh[3];
-
-    const int ep = er.ep + 1;
-    const bool is_done = ep >= c.episode_steps;
-    if (lane == 0 && done) done[e] = is_done ? 1 : 0;
-    er.ep = (is_done && (c.flags & QS_F_AUTO_RESET)) ? 0 : ep;
-    er.tick = tick + 1;
-    if (is_done && (c.flags & QS_F_AUTO_RESET)) {
-        // the env starts a new episode in place (new randomisation and goal);
-        // every lane draws the env's values itself, so no exchange is needed
-        float p7[QS_PARAM_DIM], goal[3], full[NPRM_DEV];
-        draw_env(c, c.key0, c.key1, tick, TAG_AUTO_ENV, e, p7, goal);
-        derive(c, p7, full);
-        er.p = prm_from(full);
-        er.g0 = goal[0];
-        er.g1 = goal[1];
-        er.g2 = goal[2];
-        er.redrawn = true;
-        draw_drone(c, c.key0, c.key1, tick, TAG_AUTO_DRONE, d, p7[P_T2W], s);
-    }
-    if (!finite_state(s)) atomicOr(dv.status, 1);
+    if (rew) rew[d] = compute_reward(c, s, er, fh, ev, best, W > 1 ? keff : 0);
+    end_step(c, dv, s, er, fh, lane, e, d, done);
 }
 
 struct SlotMap {
@@ -342,9 +369,207 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_rollout(const Consts c, const Dev
     }
 }
 
+// ---------------------------------------------------------------- warp-specialised step
+// A CTA of 64 threads steps up to 32 drones (slots of width W <= 32 inside
+// warp 0). Warp 0 (dynamics) carries one drone per lane through the substeps
+// and the pair pass. Warp 1 (noise) draws the motor-noise normals of the
+// first WS_SUB substeps into shared memory ahead of the dynamics, then the
+// observation noise while the dynamics run, and finally assembles the
+// observation rows of the CTA's drones in shared memory and stores them; when
+// the CTA's drones are contiguous in memory the rows form one block written
+// with 16-byte stores. The warps meet at two CTA barriers: after the motor
+// normals (B1) and after warp 0 publishes the final states (B2). This takes
+// the Philox and Box-Muller work off each drone's dependent chain.
+constexpr int WS_SUB = 4;
+constexpr int WS_OBS_MAX = 18 + 6 * QS_MAX_K;
+
+struct WsShared {
+    float nrm[WS_SUB][4][32];  // motor-noise normals [substep][rotor][lane]
+    float st[18][32];          // x v R w of each lane after the step (post-collision)
+    float sx[3][32];           // pair-pass staging: positions
+    float sv[3][32];           //                    velocities
+    float g[3][32];            // goal of each lane's env
+    int nb[QS_MAX_K][32];      // CTA lane of each neighbour
+    int keff[32];
+    float rows[32 * WS_OBS_MAX];
+};
+
+__global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+                                                const int* __restrict__ perm, const StepIO io) {
+    __shared__ WsShared sh;
+    const Tile tile = tiles[blockIdx.x];
+    const int W = tile.W;
+    const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = l / W, lane = l - slot * W;
+    const bool ok = slot < tile.count;
+    const int e = ok ? perm[tile.first + slot] : 0;
+    const int d0 = ok ? dv.env_off[e] : 0;
+    const int N = ok ? dv.env_off[e + 1] - d0 : 0;
+    const bool act = lane < N;
+    const int d = d0 + lane;
+    const int sbase = slot * W;
+    const int K = c.K;
+    const int nahead = min(c.substeps, WS_SUB);
+    const bool mnoise = (c.flags & QS_F_MOTOR_NOISE) != 0;
+
+    if (warp == 1) {
+        // ---------------- noise warp
+        const uint32_t tick = act ? dv.tick[e] : 0u;  // warp 0 writes it only after B2
+        if (act && mnoise) {
+            for (int sub = 0; sub < nahead; ++sub) {
+                float n[4];
+                motor_normals(c, tick, d, sub, n);
+                sh.nrm[sub][0][l] = n[0];
+                sh.nrm[sub][1][l] = n[1];
+                sh.nrm[sub][2][l] = n[2];
+                sh.nrm[sub][3][l] = n[3];
+            }
+        }
+        __syncthreads();  // B1
+        float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
+        if (act && io.obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, d, 0u, ex, evv, ew);
+        __syncthreads();  // B2
+        if (!io.obs) return;
+        const int od = c.obs_dim;
+        const bool contig = tile.pad != 0;
+        const int d_first = dv.env_off[perm[tile.first]];
+        const int ridx = contig ? d - d_first : l;
+        if (act) {
+            float* row = sh.rows + ridx * od;
+            row[0] = sh.st[0][l] - sh.g[0][l] + ex[0];
+            row[1] = sh.st[1][l] - sh.g[1][l] + ex[1];
+            row[2] = sh.st[2][l] - sh.g[2][l] + ex[2];
+            row[3] = sh.st[3][l] + evv[0];
+            row[4] = sh.st[4][l] + evv[1];
+            row[5] = sh.st[5][l] + evv[2];
+            for (int k = 6; k < 15; ++k) row[k] = sh.st[k][l];
+            row[15] = sh.st[15][l] + ew[0];
+            row[16] = sh.st[16][l] + ew[1];
+            row[17] = sh.st[17][l] + ew[2];
+            const int ke = sh.keff[l];
+            for (int k = 0; k < K; ++k) {
+                float* on = row + 18 + 6 * k;
+                if (k < ke) {
+                    const int j = sh.nb[k][l];
+                    for (int q = 0; q < 6; ++q) on[q] = sh.st[q][j] - sh.st[q][l];
+                } else {
+                    for (int q = 0; q < 6; ++q) on[q] = 0.f;
+                }
+            }
+        }
+        __syncwarp();
+        if (contig) {
+            const int e_last = perm[tile.first + tile.count - 1];
+            const int n_floats = (dv.env_off[e_last + 1] - d_first) * od;
+            float* dst = io.obs + (size_t)d_first * od;
+            if (((uintptr_t)dst & 15u) == 0) {
+                const int n4 = n_floats >> 2;
+                const float4* src4 = reinterpret_cast<const float4*>(sh.rows);
+                float4* dst4 = reinterpret_cast<float4*>(dst);
+                for (int i = l; i < n4; i += 32) dst4[i] = src4[i];
+                for (int i = (n4 << 2) + l; i < n_floats; i += 32) dst[i] = sh.rows[i];
+            } else {
+                const int n2 = n_floats >> 1;  // obs rows hold an even number of floats
+                const float2* src2 = reinterpret_cast<const float2*>(sh.rows);
+                float2* dst2 = reinterpret_cast<float2*>(dst);
+                for (int i = l; i < n2; i += 32) dst2[i] = src2[i];
+            }
+        } else if (act) {
+            const float2* src2 = reinterpret_cast<const float2*>(sh.rows + ridx * od);
+            float2* dst2 = reinterpret_cast<float2*>(io.obs + (size_t)d * od);
+            for (int i = 0; i < od / 2; ++i) dst2[i] = src2[i];
+        }
+        return;
+    }
+
+    // ---------------- dynamics warp
+    Drone s;
+    EnvRegs er;
+    float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t ev = 0;
+    if (act) {
+        load_drone(s, dv.st, dv.D, d);
+        load_env(er, dv, e);
+        const float4 a = __ldg(reinterpret_cast<const float4*>(io.act) + d);
+        fh[0] = command(c, a.x);
+        fh[1] = command(c, a.y);
+        fh[2] = command(c, a.z);
+        fh[3] = command(c, a.w);
+        u[0] = sqrtf(fh[0]);
+        u[1] = sqrtf(fh[1]);
+        u[2] = sqrtf(fh[2]);
+        u[3] = sqrtf(fh[3]);
+    }
+    __syncthreads();  // B1: motor normals ready
+    if (act) {
+        const float zero3[3] = {0.f, 0.f, 0.f};
+        for (int sub = 0; sub < c.substeps; ++sub) {
+            if (mnoise && sub < nahead) {
+                const float n[4] = {sh.nrm[sub][0][l], sh.nrm[sub][1][l], sh.nrm[sub][2][l], sh.nrm[sub][3][l]};
+                ev |= substep(s, er.p, c, u, er.tick, d, sub, zero3, n);
+            } else {
+                ev |= substep(s, er.p, c, u, er.tick, d, sub, zero3);
+            }
+        }
+    }
+    const int keff = min(K, N - 1);
+    uint64_t best[QS_MAX_K];
+#pragma unroll
+    for (int k = 0; k < QS_MAX_K; ++k) best[k] = ~0ull;
+    if (W > 1) {
+        if (act) {
+            sh.sx[0][l] = s.x[0];
+            sh.sx[1][l] = s.x[1];
+            sh.sx[2][l] = s.x[2];
+            sh.sv[0][l] = s.v[0];
+            sh.sv[1][l] = s.v[1];
+            sh.sv[2][l] = s.v[2];
+        }
+        __syncwarp();
+        float dvs[3] = {0.f, 0.f, 0.f};
+        bool responded = false;
+        if (act && N > 1) {
+            const bool coll = (c.flags & QS_F_COLLISIONS) && !(c.flags & QS_F_SMOOTH);
+            const bool flag_coll = (c.flags & QS_F_COLLISIONS) != 0;
+            responded = pair_scan(c, s, er.p.thr, lane, N, sbase, &sh.sx[0][0], &sh.sv[0][0], 32, keff, coll, flag_coll,
+                                  ev, best, dvs);
+        }
+        if (responded) apply_response(c, s, er.tick, d, dvs);
+    }
+    if (act) {  // publish the observed state (post-collision) for the noise warp
+        const float v18[18] = {s.x[0], s.x[1], s.x[2], s.v[0], s.v[1], s.v[2], s.R[0], s.R[1], s.R[2],
+                               s.R[3], s.R[4], s.R[5], s.R[6], s.R[7], s.R[8], s.w[0], s.w[1], s.w[2]};
+#pragma unroll
+        for (int k = 0; k < 18; ++k) sh.st[k][l] = v18[k];
+        sh.g[0][l] = er.g0;
+        sh.g[1][l] = er.g1;
+        sh.g[2][l] = er.g2;
+        sh.keff[l] = W > 1 ? keff : 0;
+#pragma unroll
+        for (int k = 0; k < QS_MAX_K; ++k)
+            if (k < keff) sh.nb[k][l] = sbase + (int)(best[k] & 0xffffffffu);
+    }
+    __syncthreads();  // B2
+    if (!act) return;
+    if ((c.flags & QS_F_RECORD_KNN) && dv.knn) {
+#pragma unroll
+        for (int k = 0; k < QS_MAX_K; ++k)
+            if (k < K) dv.knn[(size_t)k * dv.D + d] = (W > 1 && k < keff) ? (int16_t)(best[k] & 0xffffu) : (int16_t)-1;
+    }
+    if (io.rew) io.rew[d] = compute_reward(c, s, er, fh, ev, best, W > 1 ? keff : 0);
+    end_step(c, dv, s, er, fh, lane, e, d, io.done);
+    dv.ev[d] = ev;
+    store_drone(s, dv.st, dv.D, d);
+    if (lane == 0) store_env(er, dv, e);
+}
+
 cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, const Tile* tiles, const int* perm,
                         const StepIO& io, int observe_only, cudaStream_t st) {
     if (cp.n_tiles == 0) return cudaSuccess;
+    if (cp.ws && !observe_only) {
+        k_step_ws<<<cp.n_tiles, 64, 0, st>>>(c, dv, tiles + cp.tile_off, perm, io);
+        return cudaGetLastError();
+    }
     const size_t smem = (cp.W > 1) ? sizeof(float) * 6 * cp.block : 0;
     const Tile* t = tiles + cp.tile_off;
     switch (cp.W) {

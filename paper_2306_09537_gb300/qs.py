@@ -17,6 +17,7 @@ QS_OK, QS_ERR_ARG, QS_ERR_CUDA, QS_ERR_OOM, QS_ERR_STATE_NONFINITE, QS_ERR_TIMEO
 STATUS_NAMES = ["QS_OK", "QS_ERR_ARG", "QS_ERR_CUDA", "QS_ERR_OOM", "QS_ERR_STATE_NONFINITE", "QS_ERR_TIMEOUT",
                 "QS_ERR_UNSUPPORTED"]
 QS_MAX_SWARM, QS_MAX_K, QS_STATE_DIM, QS_PARAM_DIM = 64, 8, 30, 7
+QS_BLOCK_WARP_SPECIALISED = 1
 
 F_DR, F_MOTOR_NOISE, F_OBS_NOISE, F_COLLISIONS = 1 << 0, 1 << 1, 1 << 2, 1 << 3
 F_FLOOR, F_WALLS, F_AUTO_RESET, F_SMOOTH = 1 << 4, 1 << 5, 1 << 6, 1 << 7

@@ -359,13 +359,13 @@ def test_rollout_graph_replay():
 
 def test_launch_shape_does_not_change_results():
     from paper_2306_09537_gb300 import qs
-    sizes = [1] * 100 + [8] * 40 + [64] * 4
+    sizes = [1] * 100 + [8] * 40 + [64] * 4 + [3, 5, 2] * 7
     ref = None
-    for block in (None, 64, 128, 256):
+    for block in (None, 64, 128, 256, qs.QS_BLOCK_WARP_SPECIALISED):
         env, _ = pair(sizes, 6, FULL, seed=8)
         if block:
-            for wcls in (1, 8, 64):
-                qs.qs_set_block(env.h, wcls, block)
+            for wcls in (1, 2, 4, 8, 64):
+                qs.qs_set_block(env.h, wcls, block if (wcls <= 32 or block != qs.QS_BLOCK_WARP_SPECIALISED) else 128)
             assert qs.qs_get_block(env.h, 8) == block
         acts = torch.from_numpy(W.actions(8, 3, env.D)).to(DEV)
         for t in range(3):
