@@ -330,7 +330,7 @@ def run_forms(dev, stream, seed):
 
         # plain 8192 x 1: batched rollout of the 1000-step episode chunk
         env = make(W.PLAIN)
-        tuned = autotune.tune(env, horizon=64)
+        tuned = autotune.tune(env, horizon=1000)
         acts = torch.from_numpy(W.actions(seed, 1000, env.D)).to(dev)
         ms = rollout(env, acts, 1000)
         forms["plain_rollout"] = {"value": env.D / ms * 1e3, "ms_per_step": ms, "T": 1000,
@@ -341,7 +341,7 @@ def run_forms(dev, stream, seed):
 
         # swarm 2048 x 8, K = 6: per-call and batched
         env = make(W.SWARM)
-        tuned = autotune.tune(env, horizon=64)
+        tuned = autotune.tune(env, horizon=500)
         acts = torch.from_numpy(W.actions(seed, 500, env.D)).to(dev)
         ms_call = per_call(env, acts, 300)
         ms_roll = rollout(env, acts, 500)
@@ -353,7 +353,7 @@ def run_forms(dev, stream, seed):
 
         # uneven swarms, 4096 envs, sizes {1..64}: one persistent launch vs per-size launches
         env = make(W.UNEVEN)
-        tuned = autotune.tune(env, horizon=64)
+        tuned = autotune.tune(env, horizon=256)
         acts = torch.from_numpy(W.actions(seed, 256, env.D)).to(dev)
         ms_roll = rollout(env, acts, 256)
         ms_call = per_call(env, acts, 256)
@@ -414,8 +414,55 @@ def run_forms(dev, stream, seed):
     return forms
 
 
+def profile_case(name, local):
+    """One small case of a form, for ncu captures (a few hundred MB on device)."""
+    import torch
+
+    from paper_2306_09537_gb300 import qs
+    from paper_2306_09537_gb300.env import QuadSwarmEnv
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        if name == "rollout":  # 65536 single-drone envs, 32-step rollouts
+            env = QuadSwarmEnv(65536, 1, 0, BENCH_FEATURES, seed=2, weights=WL.weights, device=dev, stream=stream)
+            env.reset(2)
+            T = 32
+            acts = torch.from_numpy(W.actions(2, T, env.D)).to(dev)
+            obs = torch.empty(T, env.D, env.obs_dim, device=dev)
+            rew = torch.empty(T, env.D, device=dev)
+            for _ in range(3):
+                env.rollout(acts, obs, rew, None)
+        elif name == "swarm_call":  # 2048 envs x 8, K = 6, per-call steps
+            wl = W.SWARM
+            env = QuadSwarmEnv(wl.n_envs, wl.swarm, wl.k_neighbors, wl.features, seed=3, weights=wl.weights,
+                               device=dev, stream=stream)
+            env.reset(3)
+            acts = torch.from_numpy(W.actions(3, 20, env.D)).to(dev)
+            for t in range(20):
+                env.step(acts[t])
+        elif name == "adjoint":  # 1024 envs x 8, 32 steps, checkpoints every 16
+            wl = W.DIFF
+            env = QuadSwarmEnv(wl.n_envs, wl.swarm, 0, wl.features, seed=5, device=dev, stream=stream)
+            env.reset(5)
+            T, C = 32, 16
+            x0 = env.get_state()["state"].contiguous()
+            acts = torch.from_numpy(W.actions(5, T, env.D, lo=0.05, hi=0.95)).to(dev)
+            ws = torch.empty(qs.qs_diff_workspace_size(env.h, T, C), dtype=torch.uint8, device=dev)
+            loss = torch.empty(env.D, device=dev)
+            ga = torch.empty_like(acts)
+            gx = torch.empty(env.D, 30, device=dev)
+            for _ in range(2):
+                qs.qs_diff_forward(env.h, T, C, x0, acts, loss, ws)
+                qs.qs_diff_backward(env.h, T, C, acts, torch.ones(env.D, device=dev), ws, ga, gx)
+        env.sync()
+        env.close()
+    print(json.dumps({"profile_case": name, "ok": True}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", choices=["rollout", "swarm_call", "adjoint"], default=None,
+                    help="run one small case of a form (for ncu captures) and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
@@ -424,6 +471,9 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / swarm / uneven / sweep forms")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.profile_case:
+        profile_case(args.profile_case, int(os.environ.get("LOCAL_RANK", "0")))
+        return
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -3,7 +3,7 @@
  * QuadSwarm forward-dynamics step (Huang et al., arXiv 2306.09537).
  *
  * The library simulates E independent environments ("envs"); env e holds N_e
- * quadrotors ("drones", 1 <= N_e <= 64), D = sum N_e drones in total. Drones
+ * quadrotors ("drones", 1 <= N_e <= 128), D = sum N_e drones in total. Drones
  * are numbered env by env: env e owns global drones [off_e, off_e + N_e).
  * One control step (100 Hz; two 200 Hz physics substeps by default, paper
  * Sec. IV) advances every drone by:
@@ -52,7 +52,7 @@ extern "C" {
 #endif
 
 #define QS_ABI_VERSION 1
-#define QS_MAX_SWARM 64     /* drones per env */
+#define QS_MAX_SWARM 128    /* drones per env (the paper's largest team, Sec. V) */
 #define QS_MAX_K 8          /* neighbours in the observation */
 #define QS_STATE_DIM 30
 #define QS_PARAM_DIM 7
@@ -138,7 +138,7 @@ void qs_config_default(qs_config* cfg);
  * Allocates the device state for cfg's envs on the current device and binds
  * the handle to cuda_stream (a cudaStream_t; NULL = the legacy default
  * stream). The state is drawn as by qs_reset(h, cfg->seed, NULL, NULL).
- * Errors: QS_ERR_ARG (bad config), QS_ERR_UNSUPPORTED (N_e > 64 or K > 8),
+ * Errors: QS_ERR_ARG (bad config), QS_ERR_UNSUPPORTED (N_e > 128 or K > 8),
  * QS_ERR_OOM, QS_ERR_CUDA. On error *out is NULL. */
 qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out);
 
@@ -259,7 +259,7 @@ qs_status qs_get_events(qs_env* h, uint32_t* events_dev, int16_t* knn_dev);
 qs_status qs_sync(qs_env* h);
 
 /* Launch shape of qs_step for one swarm-width class (the envs whose swarm size
- * rounds up to the power of two `width`, 1..64): `block` threads per CTA, a
+ * rounds up to the power of two `width`, 1..128): `block` threads per CTA, a
  * multiple of 32 and of `width`, at most 256; or QS_BLOCK_WARP_SPECIALISED
  * (widths <= 32, the default there): CTAs of two warps per 32 drones, one
  * integrating the dynamics while the other draws the motor and sensor noise

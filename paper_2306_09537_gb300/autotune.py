@@ -77,7 +77,7 @@ def tune(env, steps: int = 32, horizon: int = 64, reps: int = 3, apply: bool = T
             for b in (64, 128, 256):
                 if b < maxw:
                     continue
-                for fuse in (0, max(1, horizon // 4), 1):
+                for fuse in (0, max(1, horizon // 8)):
                     for graph in (True, False):
                         qs.qs_set_rollout_shape(twin.h, b, fuse, graph)
 

@@ -37,6 +37,10 @@ struct qs_env {
     // rollout: one tile table over all classes (costliest first), launch shape
     Tile* d_rtiles = nullptr;
     int n_rtiles = 0;
+    // differentiable rollout: small CTAs (one or two warps), one tile each
+    Tile* d_dtiles = nullptr;
+    int n_dtiles = 0;
+    int diff_block = 32;
     int rollout_block = 128;
     int rollout_fuse = 0;   // control steps per launch (0: all T in one launch)
     int rollout_grid = 0;   // resident CTAs for rollout_block
@@ -144,11 +148,11 @@ void build_tiles(qs_env* h, std::vector<Tile>& tiles) {
 // Rollout tiles: every class cut into tiles of rollout_block threads, widest
 // class first (its tiles cost the most: the pair pass is O(N^2)), so that the
 // persistent CTAs take the long tiles before the short ones.
-void build_rollout_tiles(qs_env* h, std::vector<Tile>& tiles) {
+void build_rollout_tiles(qs_env* h, std::vector<Tile>& tiles, int block) {
     tiles.clear();
     for (int ci = (int)h->plan.size() - 1; ci >= 0; --ci) {
         const int W = h->plan[ci].W;
-        const int per = h->rollout_block / W;
+        const int per = block / W;
         for (int s = 0; s < h->class_slots[ci]; s += per)
             tiles.push_back(Tile{h->class_first_slot[ci] + s, std::min(per, h->class_slots[ci] - s), W, 0});
     }
@@ -170,21 +174,29 @@ int default_block(int W, int slots) {
 }
 
 qs_status upload_tiles(qs_env* h) {
-    std::vector<Tile> tiles, rtiles;
+    std::vector<Tile> tiles, rtiles, dtiles;
     build_tiles(h, tiles);
-    build_rollout_tiles(h, rtiles);
+    build_rollout_tiles(h, rtiles, h->rollout_block);
+    int maxW = 1;
+    for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
+    h->diff_block = std::max(32, maxW);  // many small CTAs: the adjoint is latency-bound
+    build_rollout_tiles(h, dtiles, h->diff_block);
     drop_graph(h);
     if (h->d_tiles) cudaFree(h->d_tiles);
     h->d_tiles = nullptr;
     h->d_rtiles = nullptr;
-    const size_t n = tiles.size() + rtiles.size();
+    h->d_dtiles = nullptr;
+    const size_t n0 = tiles.size(), n1 = rtiles.size(), n = n0 + n1 + dtiles.size();
     cudaError_t e = cudaMalloc(&h->d_tiles, sizeof(Tile) * std::max<size_t>(n, 1));
     if (e != cudaSuccess) return fail(h, QS_ERR_OOM, "tile table allocation failed");
     tiles.insert(tiles.end(), rtiles.begin(), rtiles.end());
+    tiles.insert(tiles.end(), dtiles.begin(), dtiles.end());
     e = cudaMemcpy(h->d_tiles, tiles.data(), sizeof(Tile) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(h, e, "tile table upload");
-    h->d_rtiles = h->d_tiles + (n - rtiles.size());
-    h->n_rtiles = (int)rtiles.size();
+    h->d_rtiles = h->d_tiles + n0;
+    h->n_rtiles = (int)n1;
+    h->d_dtiles = h->d_tiles + n0 + n1;
+    h->n_dtiles = (int)dtiles.size();
     h->rollout_grid = rollout_grid(h->rollout_block);
     return QS_OK;
 }
@@ -297,7 +309,7 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
         }
         if (sizes[e] > QS_MAX_SWARM) {
             delete h;
-            return fail(nullptr, QS_ERR_UNSUPPORTED, "qs_create: swarm size > 64");
+            return fail(nullptr, QS_ERR_UNSUPPORTED, "qs_create: swarm size > 128");
         }
         h->env_off_h[e + 1] = h->env_off_h[e] + sizes[e];
         if (h->env_off_h[e + 1] > (1 << 30)) {
@@ -553,7 +565,7 @@ qs_status qs_diff_forward(qs_env* h, int32_t T, int32_t ckpt_every, const float*
     if (!x0_dev || !loss_dev || !workspace_dev || !actions_dev || !aligned(actions_dev, 16) || !aligned(workspace_dev, 16))
         return fail(h, QS_ERR_ARG, "qs_diff_forward: NULL or misaligned buffer");
     DeviceGuard g(h->device);
-    cudaError_t e = launch_diff(0, h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm, x0_dev,
+    cudaError_t e = launch_diff(0, h->c, h->dv, h->d_dtiles, h->n_dtiles, h->diff_block, h->d_perm, x0_dev,
                                 actions_dev, loss_dev, nullptr, nullptr, nullptr, workspace_dev, T,
                                 std::min(T, ckpt_every), h->stream);
     return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_diff_forward launch");
@@ -567,7 +579,7 @@ qs_status qs_diff_backward(qs_env* h, int32_t T, int32_t ckpt_every, const float
         !aligned(grad_actions_dev, 16) || !aligned(workspace_dev, 16))
         return fail(h, QS_ERR_ARG, "qs_diff_backward: NULL or misaligned buffer");
     DeviceGuard g(h->device);
-    cudaError_t e = launch_diff(1, h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm, nullptr,
+    cudaError_t e = launch_diff(1, h->c, h->dv, h->d_dtiles, h->n_dtiles, h->diff_block, h->d_perm, nullptr,
                                 actions_dev, nullptr, dloss_dev, grad_actions_dev, grad_x0_dev, workspace_dev, T,
                                 std::min(T, ckpt_every), h->stream);
     return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_diff_backward launch");
@@ -632,10 +644,10 @@ qs_status qs_diff_grad_static(qs_env* h, int32_t T, int32_t ckpt_every, const fl
     // Every byte the backward pass reads is written earlier in this call (the
     // checkpoints by the forward pass, the substep states by the recompute),
     // so nothing left by a previous call needs clearing.
-    cudaError_t e = launch_diff(0, h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm, x0_dev,
+    cudaError_t e = launch_diff(0, h->c, h->dv, h->d_dtiles, h->n_dtiles, h->diff_block, h->d_perm, x0_dev,
                                 actions_dev, loss_dev, nullptr, nullptr, nullptr, ws, T, C, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "qs_diff_grad_static forward launch");
-    e = launch_diff(1, h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm, nullptr, actions_dev, nullptr,
+    e = launch_diff(1, h->c, h->dv, h->d_dtiles, h->n_dtiles, h->diff_block, h->d_perm, nullptr, actions_dev, nullptr,
                     dloss_dev, grad_actions_dev, grad_x0_dev, ws, T, C, h->stream);
     return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_diff_grad_static backward launch");
 }

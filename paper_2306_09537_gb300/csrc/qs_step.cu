@@ -580,6 +580,7 @@ cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, con
         case 16: k_step<16><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
         case 32: k_step<32><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
         case 64: k_step<64><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 128: k_step<128><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

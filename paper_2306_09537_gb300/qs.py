@@ -16,7 +16,7 @@ from . import build as _build
 QS_OK, QS_ERR_ARG, QS_ERR_CUDA, QS_ERR_OOM, QS_ERR_STATE_NONFINITE, QS_ERR_TIMEOUT, QS_ERR_UNSUPPORTED = range(7)
 STATUS_NAMES = ["QS_OK", "QS_ERR_ARG", "QS_ERR_CUDA", "QS_ERR_OOM", "QS_ERR_STATE_NONFINITE", "QS_ERR_TIMEOUT",
                 "QS_ERR_UNSUPPORTED"]
-QS_MAX_SWARM, QS_MAX_K, QS_STATE_DIM, QS_PARAM_DIM = 64, 8, 30, 7
+QS_MAX_SWARM, QS_MAX_K, QS_STATE_DIM, QS_PARAM_DIM = 128, 8, 30, 7
 QS_BLOCK_WARP_SPECIALISED = 1
 
 F_DR, F_MOTOR_NOISE, F_OBS_NOISE, F_COLLISIONS = 1 << 0, 1 << 1, 1 << 2, 1 << 3

@@ -56,7 +56,7 @@ def test_config_size_and_defaults_match_oracle(qs):
 
 @pytest.mark.parametrize("field,value,status", [
     ("n_envs", 0, 1), ("k_neighbors", -1, 1), ("k_neighbors", 9, 6), ("substeps", 0, 1), ("dt", 0.0, 1),
-    ("episode_steps", 0, 1), ("n_per_env", 0, 1), ("n_per_env", 65, 6), ("size", 4, 1)])
+    ("episode_steps", 0, 1), ("n_per_env", 0, 1), ("n_per_env", 129, 6), ("size", 4, 1)])
 def test_create_rejects_bad_config_without_device(qs, field, value, status):
     cfg = qs.qs_config_default()
     setattr(cfg, field, value)
