@@ -274,9 +274,11 @@ __device__ __forceinline__ float softplus_b(float u, float beta) {
 // R <- R (3I - R^T R) / 2 then removes the binary32 drift of R itself.
 __device__ __forceinline__ void rotate_polar(float R[9], const float w[3], float dt) {
     const float n2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    const float cc = __frsqrt_rn(fmaf(dt * dt, n2, 1.0f));  // correctly rounded: no drift of the angle
+    const float q = fmaf(dt * dt, n2, 1.0f);
+    float cc = rsqrtf(q);
+    cc = cc * fmaf(-0.5f * q * cc, cc, 1.5f);  // one Newton step: ~1 ulp, no drift of the angle
     const float a = dt * cc;
-    const float b = dt * dt * cc * cc / (1.0f + cc);
+    const float b = dt * dt * cc * cc * __frcp_rn(1.0f + cc);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
@@ -373,7 +375,7 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
             float fx = F0, fy = F1;
             if (s.v[0] == 0.0f && s.v[1] == 0.0f) {
                 const float nf = sqrtf(fx * fx + fy * fy);
-                const float keep = nf > ffric ? (nf - ffric) / nf : 0.0f;
+                const float keep = nf > ffric ? (nf - ffric) * __frcp_rn(nf) : 0.0f;
                 fx *= keep;
                 fy *= keep;
             } else {

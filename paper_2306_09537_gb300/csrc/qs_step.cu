@@ -143,11 +143,12 @@ __device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s,
     r += (ev & EV_HIT_QUAD) ? c.w[QS_W_HIT_QUAD] : 0.0f;
     if (keff > 0 && c.w[QS_W_NEAR] != 0.0f) {
         float near = 0.0f;
+        const float inv_prox = __frcp_rn(er.p.prox);
 #pragma unroll
         for (int k = 0; k < QS_MAX_K; ++k) {
             if (k < keff) {
                 const float key = __uint_as_float((uint32_t)(best[k] >> 32));
-                near += fmaxf(1.0f - sqrtf(key) / er.p.prox, 0.0f);
+                near += fmaxf(1.0f - sqrtf(key) * inv_prox, 0.0f);
             }
         }
         r += c.w[QS_W_NEAR] * near;
