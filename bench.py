@@ -255,7 +255,7 @@ def run_gpu(args, world, rank, local):
     else:
         roof = {"bound": "alu", "achieved": ach_gops, "peak": alu_peak, "unit": "Gop/s", "frac": ach_gops / alu_peak,
                 "peak_source": "152 SMs x 128 FP32/INT32 lanes x max SM clock"}
-    roof.update({"kernel": "qsk::k_step<1>", "traffic": None, "algorithmic_bytes_per_launch": ab,
+    roof.update({"kernel": "qsk::k_step_ws", "traffic": None, "algorithmic_bytes_per_launch": ab,
                  "algorithmic_ops_per_launch": ops,
                  "alt": {"hbm_frac": ach_gbs / hbm, "alu_frac": ach_gops / alu_peak}})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warm,

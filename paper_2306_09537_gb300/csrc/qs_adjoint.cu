@@ -31,7 +31,15 @@ namespace qsk {
 constexpr int ADJ_BLOCK_MAX = 256;
 constexpr int NSUB = 29;  // floats of a saved substep input: x v R w wlo uf eps
 
-__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
+__device__ __forceinline__ float sigmoidf_(float z) { return __frcp_rn(1.0f + __expf(-z)); }
+
+// Pairs farther apart than 2 l + 88 / beta have softplus_beta(2 l - d) below
+// exp(-88) / beta: their penalty and its derivatives vanish in binary32
+// sums of order-g accelerations, so they are skipped.
+__device__ __forceinline__ bool pair_far(float d2, float arm, float beta) {
+    const float r = 2.f * arm + 88.f / beta;
+    return d2 > r * r;
+}
 
 // Wall / floor / ceiling penalty acceleration and its diagonal derivative.
 __device__ __forceinline__ void wall_acc(const Consts& c, const float x[3], float acc[3], float dacc[3]) {
@@ -55,9 +63,9 @@ __device__ __forceinline__ void pair_acc(const Consts& c, const float x[3], cons
         const int tj = sbase + j;
         const float r0 = x[0] - sx[tj], r1 = x[1] - sx[nt + tj], r2 = x[2] - sx[2 * nt + tj];
         const float d2 = r0 * r0 + r1 * r1 + r2 * r2;
-        if (d2 == 0.f) continue;
+        if (d2 == 0.f || pair_far(d2, arm, c.beta)) continue;
         const float d = sqrtf(d2);
-        const float psi = kcg * softplus_b(2.f * arm - d, c.beta) / d;
+        const float psi = kcg * softplus_b(2.f * arm - d, c.beta) * __frcp_rn(d);
         out[0] = fmaf(psi, r0, out[0]);
         out[1] = fmaf(psi, r1, out[1]);
         out[2] = fmaf(psi, r2, out[2]);
@@ -73,8 +81,8 @@ __device__ __forceinline__ void pair_vjp(const Consts& c, const float x[3], cons
         const int tj = sbase + j;
         const float r0 = x[0] - sx[tj], r1 = x[1] - sx[nt + tj], r2 = x[2] - sx[2 * nt + tj];
         const float d2 = r0 * r0 + r1 * r1 + r2 * r2;
-        if (d2 == 0.f) continue;
-        const float d = sqrtf(d2), id = 1.f / d;
+        if (d2 == 0.f || pair_far(d2, arm, c.beta)) continue;
+        const float d = sqrtf(d2), id = __frcp_rn(d);
         const float pen = 2.f * arm - d;
         const float sp = softplus_b(pen, b), sg = sigmoidf_(b * pen);
         const float psi = kcg * sp * id;

@@ -262,9 +262,15 @@ __device__ __forceinline__ float command(const Consts& c, float a) {
     return fminf(fmaxf(a, 0.0f), 1.0f);
 }
 
+// softplus_beta(u) = log(1 + exp(beta u)) / beta. Below z = beta u = -16 it
+// equals exp(z) / beta to binary32 precision (log1p(x) = x - x^2/2 + ...,
+// x < 1.2e-7), which the hardware exponential gives in a few instructions;
+// contact penalties far from any contact take that path.
 __device__ __forceinline__ float softplus_b(float u, float beta) {
     const float z = beta * u;
-    return (fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z)))) / beta;
+    const float ib = __frcp_rn(beta);
+    if (z < -16.0f) return __expf(z) * ib;
+    return (fmaxf(z, 0.0f) + log1pf(__expf(-fabsf(z)))) * ib;
 }
 
 // R <- polar(R + dt R [w]x) for a rotation R. In closed form the polar factor
