@@ -132,6 +132,11 @@ def barrier(world):
         dist.barrier()
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank simulates its own envs (weak scaling, no data exchange)."""
+    return WL.seed + 1000 * rank
+
+
 def max_over_ranks(x, world):
     if world == 1:
         return x
@@ -193,7 +198,7 @@ def run_gpu(args, world, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
-    seed = WL.seed + 1000 * rank  # each rank simulates its own envs (weak scaling)
+    seed = rank_seed(rank)
     with torch.cuda.stream(stream):
         env = QuadSwarmEnv(WL.n_envs, 1, WL.k_neighbors, BENCH_FEATURES, seed=seed, weights=WL.weights, device=dev,
                            stream=stream)
