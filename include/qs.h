@@ -78,6 +78,7 @@ typedef enum {
 #define QS_F_SMOOTH           (1u << 7) /* softplus penalty contacts (differentiable form) */
 #define QS_F_ACTION_SYMMETRIC (1u << 8) /* f^ = (clip(a,-1,1)+1)/2 instead of clip(a,0,1) */
 #define QS_F_RECORD_KNN       (1u << 9) /* keep neighbour indices for qs_get_events */
+#define QS_F_DOWNWASH         (1u << 10) /* downwash from drones overlapping above (Sec. III-B) */
 
 /* qs_get_events bits (per drone, last control step) */
 #define QS_EV_HIT_FLOOR (1u << 0)
@@ -101,7 +102,13 @@ enum {
  * decay 0.8 with perturbations N(0, 0.2^2) m/s and N(0, 0.5^2) rad/s, sensor
  * noise 5e-3 m, 1e-2 m/s, 1.75e-4 rad/s (Sec. III-C), room 10 x 10 x 10 m,
  * randomisation range [0.8, 1.2], softplus beta 200 1/m and stiffness 20 m g
- * per metre, proximity radius 4 arm lengths, body-rate bound 40 rad/s. */
+ * per metre, proximity radius 4 arm lengths, body-rate bound 40 rad/s;
+ * downwash (Sec. III-B, constants not given): a drone overlapping another from
+ * above (horizontal distance < l_i + l_j, height difference dz in
+ * (0, dw_height)) adds dw_k1 (dw_k2 dz + dw_b1) downward acceleration to it
+ * for the control step, with k1 = 2.4525 m/s^2 (g/4), k2 = -2 1/m, b1 = 1,
+ * dw_height 0.5 m, noise N(0, 0.1^2) m/s^2 on the acceleration and
+ * N(0, 1^2) rad/s^2 on the angular acceleration. */
 typedef struct {
     float mass, arm, ixx, iyy, izz, t2w, kappa, tau_m, gravity, mu;
     float alpha_nd, alpha_ns_frac, alpha_c, coll_sigma_v, coll_sigma_w;
@@ -109,6 +116,7 @@ typedef struct {
     float room_hx, room_hy, room_h;
     float dr_lo, dr_hi;
     float smooth_beta, smooth_kc, prox_factor, omega_max;
+    float dw_k1, dw_k2, dw_b1, dw_height, dw_sigma_a, dw_sigma_w;
     float w[QS_NW];
 } qs_params;
 
@@ -207,7 +215,9 @@ qs_status qs_get_rollout_shape(const qs_env* h, int32_t* block, int32_t* fuse, i
  * substeps into the workspace and runs the hand-written adjoint of the whole
  * step (dynamics, integrator with re-orthonormalisation, smooth contacts),
  * writing grad_actions_dev [T][D][4] and grad_x0_dev [D][30] (zero for the
- * previous-command entries, which do not enter the loss). */
+ * previous-command entries, which do not enter the loss). A handle created
+ * with QS_F_DOWNWASH returns QS_ERR_UNSUPPORTED: the smooth form has no
+ * downwash term. */
 qs_status qs_diff_workspace_size(const qs_env* h, int32_t T, int32_t ckpt_every, size_t* bytes);
 qs_status qs_diff_forward(qs_env* h, int32_t T, int32_t ckpt_every, const float* x0_dev, const float* actions_dev,
                           float* loss_dev, void* workspace_dev);

@@ -23,7 +23,7 @@ _lib = None
 # configuration flags (same bit meaning as the oracle header)
 F_DR, F_MOTOR_NOISE, F_OBS_NOISE, F_COLLISIONS = 1 << 0, 1 << 1, 1 << 2, 1 << 3
 F_FLOOR, F_WALLS, F_AUTO_RESET, F_SMOOTH = 1 << 4, 1 << 5, 1 << 6, 1 << 7
-F_ACTION_SYMMETRIC, F_RECORD_KNN = 1 << 8, 1 << 9
+F_ACTION_SYMMETRIC, F_RECORD_KNN, F_DOWNWASH = 1 << 8, 1 << 9, 1 << 10
 EV_HIT_FLOOR, EV_ON_FLOOR, EV_HIT_WALL, EV_HIT_CEIL, EV_HIT_QUAD = 1, 2, 4, 8, 16
 NST, NPRM = 30, 7
 W_NAMES = ["pos", "vel", "ori", "spin", "act", "dact", "rot", "yaw", "hit_floor", "on_floor",
@@ -46,6 +46,8 @@ class OrConfig(C.Structure):
         ("dr_lo", C.c_double), ("dr_hi", C.c_double),
         ("smooth_beta", C.c_double), ("smooth_kc", C.c_double), ("prox_factor", C.c_double),
         ("omega_max", C.c_double),
+        ("dw_k1", C.c_double), ("dw_k2", C.c_double), ("dw_b1", C.c_double), ("dw_height", C.c_double),
+        ("dw_sigma_a", C.c_double), ("dw_sigma_w", C.c_double),
         ("w", C.c_double * 14),
     ]
 

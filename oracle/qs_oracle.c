@@ -222,6 +222,14 @@ void or_default_config(or_config* c) {
     c->smooth_kc = 20.0;
     c->prox_factor = 4.0;
     c->omega_max = 40.0;
+    /* downwash: a quarter of g on the lower drone at zero separation, fading
+     * linearly to zero 0.5 m below the upper one (the paper gives no constants) */
+    c->dw_k1 = 2.4525;
+    c->dw_k2 = -2.0;
+    c->dw_b1 = 1.0;
+    c->dw_height = 0.5;
+    c->dw_sigma_a = 0.1;
+    c->dw_sigma_w = 1.0;
     /* goal-reaching weights: position, spin, and each collision indicator */
     c->w[OR_W_POS] = -1.0;
     c->w[OR_W_SPIN] = -0.1;
@@ -775,6 +783,51 @@ static void step_env(or_env* h, int e, const double* actions, double* obs, doubl
             }
         }
         free(dv); free(resp);
+    }
+
+    /* S10b: downwash (Sec. III-B "Downwash"). A drone j above drone i that
+     * overlaps it in the xy plane (horizontal distance below l_i + l_j) within
+     * dw_height vertically pushes i down with acceleration k1 (k2 dz + b1),
+     * dz = z_j - z_i; several such drones add up. An affected drone also gets
+     * acceleration noise N(0, s_a^2 I) and angular-acceleration noise
+     * N(0, s_w^2 I). The test uses the post-substep positions, like the
+     * collision set, and the effect acts over the control step (duration
+     * substeps * dt) on the velocity and body rates. */
+    if ((c->flags & OR_F_DOWNWASH) && N >= 2) {
+        const double Tc = c->substeps * c->dt;
+        const double r = 2.0 * p[OR_P_ARM];
+        double* az = (double*)calloc((size_t)N, sizeof(double));
+        uint8_t* hit = (uint8_t*)calloc((size_t)N, 1);
+        for (int i = 0; i < N; ++i) {
+            const double* xi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_X;
+            for (int j = 0; j < N; ++j) {
+                if (j == i) continue;
+                const double* xj = h->st + (size_t)(d0 + j) * OR_NST + OR_S_X;
+                double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+                double rxy2 = dx * dx + dy * dy;
+                note_cmp(h, d0 + i, rxy2, r * r);
+                if (rxy2 < r * r) {
+                    note_cmp(h, d0 + i, xj[2], xi[2]);
+                    note_cmp(h, d0 + i, dz, c->dw_height);
+                }
+                if (rxy2 < r * r && dz > 0.0 && dz < c->dw_height) {
+                    az[i] -= c->dw_k1 * (c->dw_k2 * dz + c->dw_b1);
+                    hit[i] = 1;
+                }
+            }
+        }
+        for (int i = 0; i < N; ++i) {
+            if (!hit[i]) continue;
+            double nn[6];
+            draw_six_normals(h, h->tick[e], (uint32_t)(d0 + i), OR_TAG_DOWNWASH, 0, nn);
+            double* vi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_V;
+            double* wi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_W;
+            for (int k = 0; k < 3; ++k) {
+                vi[k] += Tc * ((k == 2 ? az[i] : 0.0) + c->dw_sigma_a * nn[k]);
+                wi[k] += Tc * c->dw_sigma_w * nn[3 + k];
+            }
+        }
+        free(az); free(hit);
     }
 
     /* S11: K nearest by (key, local index) ascending over j != i. */

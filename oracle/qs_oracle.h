@@ -18,6 +18,7 @@
 #define OR_F_SMOOTH           (1u << 7)
 #define OR_F_ACTION_SYMMETRIC (1u << 8)
 #define OR_F_RECORD_KNN       (1u << 9)
+#define OR_F_DOWNWASH         (1u << 10)
 
 /* per-drone event bits of the last control step */
 #define OR_EV_HIT_FLOOR (1u << 0)
@@ -35,6 +36,7 @@
 #define OR_TAG_WALL        6u
 #define OR_TAG_AUTO_ENV    7u
 #define OR_TAG_AUTO_DRONE  8u
+#define OR_TAG_DOWNWASH    9u
 
 /* per-drone state row: x(3) v(3) R(9, row-major) w(3) uf(4) eps(4) fprev(4) */
 #define OR_NST 30
@@ -76,6 +78,7 @@ typedef struct {
     double smooth_beta, smooth_kc;
     double prox_factor;
     double omega_max;
+    double dw_k1, dw_k2, dw_b1, dw_height, dw_sigma_a, dw_sigma_w; /* downwash */
     double w[OR_NW];
 } or_config;
 

@@ -113,6 +113,12 @@ void build_consts(qs_env* h) {
     c.prox_factor = p.prox_factor;
     c.dr_lo = p.dr_lo;
     c.dr_hi = p.dr_hi;
+    c.dw_k1 = p.dw_k1;
+    c.dw_k2 = p.dw_k2;
+    c.dw_b1 = p.dw_b1;
+    c.dw_h = p.dw_height;
+    c.dw_sa = p.dw_sigma_a;
+    c.dw_sw = p.dw_sigma_w;
     const float nom[QS_PARAM_DIM] = {p.mass, p.ixx, p.iyy, p.izz, p.t2w, p.tau_m, p.arm};
     for (int k = 0; k < QS_PARAM_DIM; ++k) c.nominal[k] = nom[k];
     for (int k = 0; k < QS_NW; ++k) c.w[k] = p.w[k];
@@ -266,6 +272,12 @@ void qs_config_default(qs_config* cfg) {
     p.smooth_kc = 20.0f;
     p.prox_factor = 4.0f;
     p.omega_max = 40.0f;
+    p.dw_k1 = 2.4525f;
+    p.dw_k2 = -2.0f;
+    p.dw_b1 = 1.0f;
+    p.dw_height = 0.5f;
+    p.dw_sigma_a = 0.1f;
+    p.dw_sigma_w = 1.0f;
     p.w[QS_W_POS] = -1.0f;
     p.w[QS_W_SPIN] = -0.1f;
     p.w[QS_W_HIT_FLOOR] = -1.0f;
@@ -547,6 +559,8 @@ static qs_status diff_check(qs_env* h, const char* who, int32_t T, int32_t C) {
     if (!h) return fail(nullptr, QS_ERR_ARG, std::string(who) + ": NULL handle");
     if (!(h->cfg.flags & QS_F_SMOOTH))
         return fail(h, QS_ERR_ARG, std::string(who) + ": the handle must be created with QS_F_SMOOTH");
+    if (h->cfg.flags & QS_F_DOWNWASH)
+        return fail(h, QS_ERR_UNSUPPORTED, std::string(who) + ": the differentiable rollout has no downwash term");
     if (T < 1 || C < 1) return fail(h, QS_ERR_ARG, std::string(who) + ": T and ckpt_every must be >= 1");
     return QS_OK;
 }

@@ -19,7 +19,7 @@ enum PrmIdx {
 // Philox stream tags (counter word 2 = tag << 16 | substream << 8 | block).
 enum Tag : uint32_t {
     TAG_RESET_ENV = 1, TAG_RESET_DRONE = 2, TAG_MOTOR = 3, TAG_OBS = 4, TAG_COLL = 5, TAG_WALL = 6,
-    TAG_AUTO_ENV = 7, TAG_AUTO_DRONE = 8
+    TAG_AUTO_ENV = 7, TAG_AUTO_DRONE = 8, TAG_DOWNWASH = 9
 };
 
 // Number of float4 planes of the drone state: the 30 public floats fill
@@ -34,6 +34,7 @@ struct Consts {
     float obs_sx, obs_sv, obs_sw;
     float room_hx, room_hy, room_h;
     float beta, kc, omega_max, ans_frac, prox_factor, dr_lo, dr_hi;
+    float dw_k1, dw_k2, dw_b1, dw_h, dw_sa, dw_sw;  // downwash
     float nominal[QS_PARAM_DIM];
     float w[QS_NW];
     uint32_t flags, key0, key1;

@@ -76,13 +76,21 @@ __device__ __forceinline__ void topk_insert(uint64_t best[QS_MAX_K], int K, uint
 // partners (S10), and the sorted neighbour list.
 __device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float thr, int lane, int N, int sbase,
                                           const float* sx, const float* sv, int nt, int keff, bool coll, bool flag_coll,
-                                          uint32_t& ev, uint64_t best[QS_MAX_K], float dvs[3]) {
+                                          uint32_t& ev, uint64_t best[QS_MAX_K], float dvs[3], float& dw_az,
+                                          bool& dw_hit) {
     bool responded = false;
+    const bool dw = (c.flags & QS_F_DOWNWASH) != 0;
     for (int j = 0; j < N; ++j) {
         if (j == lane) continue;
         const int tj = sbase + j;
         float dx, dy, dz;
         const float key = pair_key(s.x[0], s.x[1], s.x[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx, dy, dz);
+        // downwash: j overlaps this drone from above (horizontal distance below
+        // l_i + l_j, height difference in (0, dw_h))
+        if (dw && __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) < thr && dz > 0.0f && dz < c.dw_h) {
+            dw_az -= c.dw_k1 * fmaf(c.dw_k2, dz, c.dw_b1);
+            dw_hit = true;
+        }
         if (flag_coll && key < thr) {
             ev |= EV_HIT_QUAD;
             if (coll) {
@@ -108,6 +116,20 @@ __device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float
         if (keff > 0) topk_insert(best, keff, ((uint64_t)__float_as_uint(key) << 32) | (uint32_t)j);
     }
     return responded;
+}
+
+// Downwash over the control step (duration substeps * dt): v_z += T az plus
+// acceleration noise, w += T * angular-acceleration noise.
+__device__ __forceinline__ void apply_downwash(const Consts& c, Drone& s, uint32_t tick, int d, float az) {
+    float n[6];
+    six_normals(c, tick, (uint32_t)d, TAG_DOWNWASH, 0, n);
+    const float Tc = c.dt * (float)c.substeps;
+    s.v[0] = fmaf(Tc, c.dw_sa * n[0], s.v[0]);
+    s.v[1] = fmaf(Tc, c.dw_sa * n[1], s.v[1]);
+    s.v[2] = fmaf(Tc, fmaf(c.dw_sa, n[2], az), s.v[2]);
+    comp_add(s.w[0], s.wlo[0], Tc * c.dw_sw * n[3]);
+    comp_add(s.w[1], s.wlo[1], Tc * c.dw_sw * n[4]);
+    comp_add(s.w[2], s.wlo[2], Tc * c.dw_sw * n[5]);
 }
 
 // S10: v <- alpha_c (v + sum + eps_v), w <- w + eps_w for a responding drone.
@@ -227,13 +249,16 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
         }
         __syncthreads();
         float dvs[3] = {0.f, 0.f, 0.f};
-        bool responded = false;
+        bool responded = false, dw_hit = false;
+        float dw_az = 0.f;
         if (act && N > 1) {
             const bool coll = (c.flags & QS_F_COLLISIONS) && !(c.flags & QS_F_SMOOTH) && !observe_only;
             const bool flag_coll = (c.flags & QS_F_COLLISIONS) && !observe_only;
-            responded = pair_scan(c, s, er.p.thr, lane, N, sbase, sx, sv, nt, keff, coll, flag_coll, ev, best, dvs);
+            responded = pair_scan(c, s, er.p.thr, lane, N, sbase, sx, sv, nt, keff, coll, flag_coll, ev, best, dvs,
+                                  dw_az, dw_hit);
         }
         if (responded) apply_response(c, s, tick, d, dvs);
+        if (dw_hit && !observe_only) apply_downwash(c, s, tick, d, dw_az);
         __syncthreads();
         if (act) {  // post-collision velocities for the neighbour observation
             sv[threadIdx.x] = s.v[0];
@@ -528,14 +553,16 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
         }
         __syncwarp();
         float dvs[3] = {0.f, 0.f, 0.f};
-        bool responded = false;
+        bool responded = false, dw_hit = false;
+        float dw_az = 0.f;
         if (act && N > 1) {
             const bool coll = (c.flags & QS_F_COLLISIONS) && !(c.flags & QS_F_SMOOTH);
             const bool flag_coll = (c.flags & QS_F_COLLISIONS) != 0;
             responded = pair_scan(c, s, er.p.thr, lane, N, sbase, &sh.sx[0][0], &sh.sv[0][0], 32, keff, coll, flag_coll,
-                                  ev, best, dvs);
+                                  ev, best, dvs, dw_az, dw_hit);
         }
         if (responded) apply_response(c, s, er.tick, d, dvs);
+        if (dw_hit) apply_downwash(c, s, er.tick, d, dw_az);
     }
     if (act) {  // publish the observed state (post-collision) for the noise warp
         const float v18[18] = {s.x[0], s.x[1], s.x[2], s.v[0], s.v[1], s.v[2], s.R[0], s.R[1], s.R[2],

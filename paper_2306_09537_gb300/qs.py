@@ -21,10 +21,10 @@ QS_BLOCK_WARP_SPECIALISED = 1
 
 F_DR, F_MOTOR_NOISE, F_OBS_NOISE, F_COLLISIONS = 1 << 0, 1 << 1, 1 << 2, 1 << 3
 F_FLOOR, F_WALLS, F_AUTO_RESET, F_SMOOTH = 1 << 4, 1 << 5, 1 << 6, 1 << 7
-F_ACTION_SYMMETRIC, F_RECORD_KNN = 1 << 8, 1 << 9
+F_ACTION_SYMMETRIC, F_RECORD_KNN, F_DOWNWASH = 1 << 8, 1 << 9, 1 << 10
 FEATURE_FLAGS = {"dr": F_DR, "motor_noise": F_MOTOR_NOISE, "obs_noise": F_OBS_NOISE, "collisions": F_COLLISIONS,
                  "floor": F_FLOOR, "walls": F_WALLS, "auto_reset": F_AUTO_RESET, "smooth": F_SMOOTH,
-                 "action_symmetric": F_ACTION_SYMMETRIC, "record_knn": F_RECORD_KNN}
+                 "action_symmetric": F_ACTION_SYMMETRIC, "record_knn": F_RECORD_KNN, "downwash": F_DOWNWASH}
 EV_HIT_FLOOR, EV_ON_FLOOR, EV_HIT_WALL, EV_HIT_CEIL, EV_HIT_QUAD = 1, 2, 4, 8, 16
 W_NAMES = ["pos", "vel", "ori", "spin", "act", "dact", "rot", "yaw", "hit_floor", "on_floor", "hit_wall", "hit_ceil",
            "hit_quad", "near"]
@@ -41,7 +41,8 @@ class qs_params(C.Structure):
         "mass", "arm", "ixx", "iyy", "izz", "t2w", "kappa", "tau_m", "gravity", "mu",
         "alpha_nd", "alpha_ns_frac", "alpha_c", "coll_sigma_v", "coll_sigma_w",
         "obs_sigma_x", "obs_sigma_v", "obs_sigma_w", "room_hx", "room_hy", "room_h",
-        "dr_lo", "dr_hi", "smooth_beta", "smooth_kc", "prox_factor", "omega_max")] + [("w", C.c_float * 14)]
+        "dr_lo", "dr_hi", "smooth_beta", "smooth_kc", "prox_factor", "omega_max",
+        "dw_k1", "dw_k2", "dw_b1", "dw_height", "dw_sigma_a", "dw_sigma_w")] + [("w", C.c_float * 14)]
 
 
 class qs_config(C.Structure):

@@ -137,3 +137,32 @@ def clustered_positions(seed: int, sizes, spread: float = 0.15, dup_frac: float 
                     p[i] = p[rng.integers(0, int(n))]
         out.append(p)
     return np.concatenate(out, axis=0).astype(np.float32)
+
+
+def stacked_positions(seed: int, sizes, per_column: int = 3, offset: float = 0.04, gap=(0.1, 0.6),
+                      pitch: float = 0.5, room=(5.0, 5.0, 10.0)) -> np.ndarray:
+    """Binary32 positions [D][3] in vertical columns of up to `per_column`
+    drones (formation flight with drones above one another): within a column
+    each drone sits `gap` metres (uniform) above the previous one, offset
+    horizontally by up to `offset` m per axis; columns stand `pitch` m apart
+    on a grid around a random centre per env."""
+    rng = np.random.Generator(np.random.Philox(key=np.uint64(0x57AC_0000 + seed)))
+    out = []
+    for n in sizes:
+        n = int(n)
+        ncol = (n + per_column - 1) // per_column
+        side = int(np.ceil(np.sqrt(ncol)))
+        span = (side - 1) * pitch
+        c = np.array([rng.uniform(-room[0] + 1, room[0] - 1 - span), rng.uniform(-room[1] + 1, room[1] - 1 - span),
+                      rng.uniform(1.0, room[2] - 1.0 - per_column * gap[1])])
+        p = np.zeros((n, 3))
+        for i in range(n):
+            col, lvl = divmod(i, per_column)
+            base = c + np.array([(col % side) * pitch, (col // side) * pitch, 0.0])
+            if lvl == 0:
+                p[i] = base
+            else:
+                p[i] = p[i - 1] + np.array([0.0, 0.0, rng.uniform(*gap)])
+            p[i, 0:2] = base[0:2] + rng.uniform(-offset, offset, 2)
+        out.append(p)
+    return np.concatenate(out, axis=0).astype(np.float32)

@@ -147,3 +147,12 @@ def test_diff_requires_smooth_handle():
     with pytest.raises(qs.QSError):
         qs.qs_diff_forward(env.h, 4, 2, torch.zeros(4, 30, device=DEV), torch.zeros(4, 4, 4, device=DEV),
                            torch.zeros(4, device=DEV), torch.zeros(1 << 16, dtype=torch.uint8, device=DEV))
+
+
+def test_diff_rejects_downwash():
+    """The smooth form has no downwash term: a handle with downwash on is refused."""
+    env, _ = pair([2] * 4, 1, ("smooth", "floor", "downwash"), seed=1)
+    with pytest.raises(qs.QSError) as e:
+        qs.qs_diff_forward(env.h, 4, 2, torch.zeros(8, 30, device=DEV), torch.zeros(4, 8, 4, device=DEV),
+                           torch.zeros(8, device=DEV), torch.zeros(1 << 16, dtype=torch.uint8, device=DEV))
+    assert e.value.status == qs.QS_ERR_UNSUPPORTED

@@ -161,6 +161,38 @@ def test_single_step_contacts_exercised():
     assert np.allclose(rew.cpu().numpy()[keep], orew[keep], rtol=2e-5, atol=2e-5)
 
 
+@pytest.mark.parametrize("sizes", [[8] * 200, [3, 5, 17, 33, 64, 128] * 3])
+def test_downwash_parity(sizes):
+    """Drones stacked in columns (Sec. III-B downwash): the warp-specialised
+    step (swarms up to 32) and the general step (wider swarms) match the
+    oracle, and the downwash term really changed the step."""
+    feats = FULL + ("downwash",)
+    env, o = pair(sizes, 6, feats, seed=8, weights=ALL_WEIGHTS)
+    st, prm, goals = seeded_inputs(env, 8, sizes)
+    st[:, 0:3] = W.stacked_positions(8, sizes)
+    set_both(env, o, st, prm, goals, ep=3, tick=11)
+    acts = W.actions(8, 1, env.D)[0]
+    obs, rew, done = env.step(torch.from_numpy(acts).to(DEV))
+    ev, knn = env.get_events(knn=True)
+    r = dict(obs=obs.cpu().numpy(), rew=rew.cpu().numpy(), done=done.cpu().numpy(),
+             ev=ev.cpu().numpy().astype(np.uint32), knn=knn.cpu().numpy().astype(np.int32), g=gpu_state(env))
+    r["oobs"], r["orew"], r["odone"] = o.step(acts.astype(np.float64))
+    r["oev"], r["oknn"], _ = o.get_events()
+    r["margin"], r["margin_knn"] = o.margins()
+    r["os"] = o.get_state()
+    check_step(r, sizes)
+    # the same step without downwash: most drones under another one must differ
+    _, o2 = pair(sizes, 6, FULL, seed=8, weights=ALL_WEIGHTS)
+    set_both(env, o2, st, prm, goals, ep=3, tick=11)
+    o2.step(acts.astype(np.float64))
+    dv = np.abs(o2.get_state()["state"][:, 3:6] - r["os"]["state"][:, 3:6]).max(axis=1)
+    assert (dv > 1e-3).mean() > 0.2
+    # and the GPU saw the same: its velocities follow the downwash run, not the plain one
+    gv = r["g"]["state"][:, 3:6]
+    hit = dv > 1e-3
+    assert np.abs(gv[hit] - r["os"]["state"][hit, 3:6]).max() < 1e-3 < np.abs(gv[hit] - o2.get_state()["state"][hit, 3:6]).max()
+
+
 # ----------------------------------------------------------------------------- exact discrete decisions
 @pytest.mark.parametrize("dup", [0.0, 0.3])
 def test_neighbours_and_collisions_bit_exact(dup):

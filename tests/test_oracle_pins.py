@@ -612,3 +612,59 @@ def test_body_rate_bound():
     assert s[17] == c.omega_max == 40.0 and s[15] == 0.0 and s[16] == 0.0
     R = s[6:15].reshape(3, 3)
     assert abs(math.atan2(R[1, 0], R[0, 0]) - 2 * math.atan(c.dt * 40.0)) < 1e-12
+
+
+# --------------------------------------------------------------------------- downwash
+def _downwash_case(above, sig=0.0):
+    """Drone 0 hovering at (0,0,5); drones in `above` at the given offsets."""
+    n = 1 + len(above)
+    c, o = make(n_envs=1, sizes=[n], flags=O.F_DOWNWASH, dw_sigma_a=sig, dw_sigma_w=sig)
+    st = base_state(n)
+    for k, off in enumerate(above):
+        st[1 + k, 0:3] = np.array([0.0, 0.0, 5.0]) + np.asarray(off)
+    o.set_state(st, nominal(c)[None], np.zeros((1, 3)), np.zeros(1, np.int32), 0)
+    o.step(np.full((n, 4), 0.5))
+    return c, o.get_state()["state"]
+
+
+def test_downwash_closed_form():
+    """Sec. III-B downwash on the lower drone: k1 (k2 dz + b1) for a drone
+    overlapping it from above within the height window, acting for one control
+    step; none on the upper drone, none outside the window; contributions add."""
+    for dz in (0.1, 0.25, 0.4):
+        c, s = _downwash_case([(0.01, -0.02, dz)])
+        Tc = c.substeps * c.dt
+        want = -Tc * c.dw_k1 * (c.dw_k2 * dz + c.dw_b1)
+        assert abs(s[0, 5] - want) < 1e-12 and np.abs(s[0, 3:5]).max() < 1e-12
+        assert np.abs(s[1, 3:6]).max() < 1e-12
+        assert np.abs(s[:, 15:18]).max() < 1e-12
+    assert abs(_downwash_case([(0.0, 0.0, 0.25)])[1][0, 5] - 0.5 * _downwash_case([(0.0, 0.0, 0.0001)])[1][0, 5]) < 1e-5
+    for off in ((0.2, 0.0, 0.2), (0.0, 0.0, 0.6), (0.0, 0.0, -0.2)):  # beside, too high, below
+        _, s = _downwash_case([off])
+        assert np.abs(s[0, 3:6]).max() < 1e-12
+    c, s2 = _downwash_case([(0.0, 0.01, 0.1), (0.01, 0.0, 0.3)])
+    Tc = c.substeps * c.dt
+    want = -Tc * c.dw_k1 * ((c.dw_k2 * 0.1 + c.dw_b1) + (c.dw_k2 * 0.3 + c.dw_b1))
+    assert abs(s2[0, 5] - want) < 1e-12
+
+
+def test_downwash_noise_moments():
+    """The downwash disturbances eps_d and eps_wd (Sec. III-B) are zero-mean
+    Gaussian with the configured scales, act for one control step, and reach
+    only the drone underneath."""
+    E = 4000
+    c, o = make(n_envs=E, sizes=[2] * E, flags=O.F_DOWNWASH)
+    st = base_state(2 * E)
+    st[1::2, 2] += 0.2
+    o.set_state(st, np.tile(nominal(c), (E, 1)), np.zeros((E, 3)), np.zeros(E, np.int32), 0)
+    o.step(np.full((2 * E, 4), 0.5))
+    s = o.get_state()["state"]
+    Tc = c.substeps * c.dt
+    lower, upper = s[0::2], s[1::2]
+    dv = lower[:, 3:6] - np.array([0.0, 0.0, -Tc * c.dw_k1 * (c.dw_k2 * 0.2 + c.dw_b1)])
+    for k in range(3):
+        assert abs(dv[:, k].mean()) < 4 * Tc * c.dw_sigma_a / math.sqrt(E)
+        assert abs(dv[:, k].std() / (Tc * c.dw_sigma_a) - 1.0) < 0.05
+        assert abs(lower[:, 15 + k].std() / (Tc * c.dw_sigma_w) - 1.0) < 0.05
+    assert abs(np.corrcoef(dv[:, 0], lower[:, 15])[0, 1]) < 0.06
+    assert np.abs(upper[:, 3:6]).max() < 1e-12 and np.abs(upper[:, 15:18]).max() < 1e-12
