@@ -29,13 +29,28 @@ NST, NPRM = 30, 7
 W_NAMES = ["pos", "vel", "ori", "spin", "act", "dact", "rot", "yaw", "hit_floor", "on_floor",
            "hit_wall", "hit_ceil", "hit_quad", "near"]
 TAG_RESET_ENV, TAG_RESET_DRONE, TAG_MOTOR, TAG_OBS, TAG_COLL, TAG_WALL = 1, 2, 3, 4, 5, 6
+TAG_SCN, TAG_AUTO_SCN, TAG_WAYPOINT, TAG_SWAP = 10, 11, 12, 13
+# training scenarios (Sec. III-D) and goal formations
+SCN_NAMES = ["single", "static", "dynamic", "swap", "shrink_expand", "swarm_vs_swarm", "pursuit_lissajous",
+             "pursuit_bezier"]
+FORM_NAMES = ["circle", "grid", "sphere", "cylinder", "cube"]
+NSCN = 18
+R_TYPE, R_F0, R_F1, R_TSW, R_SEED_LO, R_C0, R_C1, R_FREQ, R_PHASE, R_SEED_HI = 0, 1, 2, 3, 4, 5, 8, 11, 14, 17
+
+
+def scenario_mask(names) -> int:
+    """Bit mask of the named scenarios (SCN_NAMES)."""
+    m = 0
+    for n in names:
+        m |= 1 << SCN_NAMES.index(n)
+    return m
 
 
 class OrConfig(C.Structure):
     _fields_ = [
         ("n_envs", C.c_int32), ("k_neighbors", C.c_int32), ("substeps", C.c_int32),
         ("episode_steps", C.c_int32), ("dt", C.c_double), ("seed", C.c_uint64),
-        ("flags", C.c_uint32), ("pad_", C.c_uint32),
+        ("flags", C.c_uint32), ("scenarios", C.c_uint32),
         ("mass", C.c_double), ("arm", C.c_double), ("ixx", C.c_double), ("iyy", C.c_double),
         ("izz", C.c_double), ("t2w", C.c_double), ("kappa", C.c_double), ("tau_m", C.c_double),
         ("gravity", C.c_double), ("mu", C.c_double),
@@ -48,6 +63,8 @@ class OrConfig(C.Structure):
         ("omega_max", C.c_double),
         ("dw_k1", C.c_double), ("dw_k2", C.c_double), ("dw_b1", C.c_double), ("dw_height", C.c_double),
         ("dw_sigma_a", C.c_double), ("dw_sigma_w", C.c_double),
+        ("form_spacing", C.c_double), ("form_rmax", C.c_double), ("scn_margin", C.c_double),
+        ("se_min", C.c_double), ("se_period", C.c_double), ("liss_f", C.c_double), ("bez_seg", C.c_double),
         ("w", C.c_double * 14),
     ]
 
@@ -98,6 +115,10 @@ def lib():
                                         P(C.c_double)]
             L.or_clear_margin.argtypes = [C.c_void_p]
             L.or_observe.argtypes = [C.c_void_p, P(C.c_double)]
+            L.or_get_scenario.argtypes = [C.c_void_p, P(C.c_double)]
+            L.or_set_scenario.argtypes = [C.c_void_p, P(C.c_double)]
+            L.or_goals.argtypes = [C.c_void_p, P(C.c_double)]
+            L.or_formation_offset.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, P(C.c_double)]
             L.or_pairs_f32.argtypes = [P(C.c_float), P(C.c_float), P(C.c_int32), C.c_int, C.c_int,
                                        P(C.c_int32), P(C.c_uint8)]
             _lib = L
@@ -146,6 +167,14 @@ def pairs_f32(pos, arm, env_off, K):
     lib().or_pairs_f32(_ptr(pos, C.c_float), _ptr(arm, C.c_float), _ptr(off, C.c_int32),
                        len(off) - 1, int(K), _ptr(knn, C.c_int32), _ptr(hit, C.c_uint8))
     return knn[:, :K], hit
+
+
+def formation_offset(form, k: int, n: int, s: float, rmax: float) -> np.ndarray:
+    """Offset of goal slot k of an n-goal formation (FORM_NAMES or index)."""
+    f = FORM_NAMES.index(form) if isinstance(form, str) else int(form)
+    out = np.zeros(3)
+    lib().or_formation_offset(f, int(k), int(n), float(s), float(rmax), _ptr(out, C.c_double))
+    return out
 
 
 def default_config(**kw) -> OrConfig:
@@ -230,6 +259,21 @@ class Oracle:
         tk = None if tick is None else np.ascontiguousarray(np.broadcast_to(tick, (self.E,)), dtype=np.uint32)
         lib().or_set_state(self.h, _ptr(st, C.c_double), _ptr(prm, C.c_double), _ptr(goal, C.c_double),
                            _ptr(ep, C.c_int32), _ptr(tk, C.c_uint32))
+
+    def get_scenario(self) -> np.ndarray:
+        rec = np.zeros((self.E, NSCN))
+        lib().or_get_scenario(self.h, _ptr(rec, C.c_double))
+        return rec
+
+    def set_scenario(self, rec):
+        r = np.ascontiguousarray(rec, dtype=np.float64).reshape(self.E, NSCN)
+        lib().or_set_scenario(self.h, _ptr(r, C.c_double))
+
+    def goals(self) -> np.ndarray:
+        """Per-drone goals [D][3] at each env's current control step."""
+        g = np.zeros((self.D, 3))
+        lib().or_goals(self.h, _ptr(g, C.c_double))
+        return g
 
     def observe(self):
         obs = np.zeros((self.D, self.obs_dim))

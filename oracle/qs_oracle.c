@@ -230,6 +230,18 @@ void or_default_config(or_config* c) {
     c->dw_height = 0.5;
     c->dw_sigma_a = 0.1;
     c->dw_sigma_w = 1.0;
+    /* scenarios (Sec. III-D gives no sizes or rates): goals 0.5 m apart, circle
+     * radius at most 4 m, centres 1.5 m clear of the room's faces, shrink to
+     * half size and back every 4 s, evader loops at about 0.1 Hz, 3 s Bezier
+     * segments */
+    c->scenarios = 0;
+    c->form_spacing = 0.5;
+    c->form_rmax = 4.0;
+    c->scn_margin = 1.5;
+    c->se_min = 0.5;
+    c->se_period = 400.0;
+    c->liss_f = 0.1;
+    c->bez_seg = 300.0;
     /* goal-reaching weights: position, spin, and each collision indicator */
     c->w[OR_W_POS] = -1.0;
     c->w[OR_W_SPIN] = -0.1;
@@ -254,6 +266,7 @@ or_env* or_create(const or_config* cfg, const int32_t* swarm_sizes) {
     h->n_drones = D;
     h->prm = (double*)calloc((size_t)E * OR_NPRM, sizeof(double));
     h->goal = (double*)calloc((size_t)E * 3, sizeof(double));
+    h->scn = (double*)calloc((size_t)E * OR_NSCN, sizeof(double));
     h->st = (double*)calloc((size_t)D * OR_NST, sizeof(double));
     h->ep_t = (int32_t*)calloc((size_t)E, sizeof(int32_t));
     h->tick = (uint32_t*)calloc((size_t)E, sizeof(uint32_t));
@@ -271,7 +284,7 @@ or_env* or_create(const or_config* cfg, const int32_t* swarm_sizes) {
 
 void or_destroy(or_env* h) {
     if (!h) return;
-    free(h->env_off); free(h->prm); free(h->goal); free(h->st); free(h->ep_t); free(h->tick);
+    free(h->env_off); free(h->prm); free(h->goal); free(h->scn); free(h->st); free(h->ep_t); free(h->tick);
     free(h->ev); free(h->knn); free(h->margin); free(h->margin_knn); free(h->cond); free(h);
 }
 
@@ -298,6 +311,239 @@ static void reset_env_params(or_env* h, const uint32_t key[2], uint32_t tick, ui
     g[0] = -c->room_hx + 2.0 * c->room_hx * u[7];
     g[1] = -c->room_hy + 2.0 * c->room_hy * u[8];
     g[2] = c->room_h * u[9];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Training scenarios (Sec. III-D): goal formations and their schedules.      */
+/* ------------------------------------------------------------------------- */
+
+/* smallest m >= 1 with m^p >= n (p = 2 or 3) */
+static int root_ceil(int n, int p) {
+    int m = 1;
+    while ((p == 2 ? m * m : m * m * m) < n) ++m;
+    return m;
+}
+
+/* The golden angle (3 - sqrt 5) / 2 turns as a 32-bit fixed-point fraction, so
+ * that k times it, taken modulo one turn, is exact integer arithmetic. */
+static uint32_t golden_turn_q32(void) { return (uint32_t)floor(4294967296.0 * (3.0 - sqrt(5.0)) / 2.0); }
+
+/* Offset from the formation's centre of goal slot k (0 <= k < n) of a
+ * formation of n goals with spacing s.
+ *   circle:   n goals evenly on a horizontal circle, each an arc s from the
+ *             next (radius s n / 2 pi, at most rmax);
+ *   grid:     a horizontal square grid of side m = ceil(sqrt n), filled row by
+ *             row, centred on its occupied rows;
+ *   sphere:   the Fibonacci lattice: heights z_k = 1 - (2k+1)/n, azimuth
+ *             advancing by the golden angle, radius s sqrt(n / 4 pi) (area s^2
+ *             per goal);
+ *   cylinder: L horizontal rings (L the smallest with 4 L^2 >= n) of
+ *             m = ceil(n / L) goals each, radius as for a circle of m goals,
+ *             rings s apart and centred on the occupied ones;
+ *   cube:     a cubic grid of side m = ceil(cbrt n), filled along x, then y,
+ *             then z, centred on its occupied layers. */
+void or_formation_offset(int form, int k, int n, double s, double rmax, double out[3]) {
+    out[0] = out[1] = out[2] = 0.0;
+    if (form == OR_FORM_CIRCLE) {
+        double r = fmin(s * n / (2.0 * M_PI), rmax), th = 2.0 * M_PI * k / n;
+        out[0] = r * cos(th);
+        out[1] = r * sin(th);
+    } else if (form == OR_FORM_GRID) {
+        int m = root_ceil(n, 2), rows = (n + m - 1) / m;
+        out[0] = s * ((k % m) - 0.5 * (m - 1));
+        out[1] = s * ((k / m) - 0.5 * (rows - 1));
+    } else if (form == OR_FORM_SPHERE) {
+        double r = s * sqrt(n / (4.0 * M_PI));
+        double z = 1.0 - (2.0 * k + 1.0) / n, rho = sqrt(1.0 - z * z);
+        uint32_t turn = (uint32_t)k * golden_turn_q32(); /* modulo 2^32: one turn */
+        double phi = 2.0 * M_PI * (turn / 4294967296.0);
+        out[0] = r * rho * cos(phi);
+        out[1] = r * rho * sin(phi);
+        out[2] = r * z;
+    } else if (form == OR_FORM_CYLINDER) {
+        int L = 1;
+        while (4 * L * L < n) ++L;
+        int m = (n + L - 1) / L, used = (n + m - 1) / m;
+        double r = fmin(s * m / (2.0 * M_PI), rmax), th = 2.0 * M_PI * (k % m) / m;
+        out[0] = r * cos(th);
+        out[1] = r * sin(th);
+        out[2] = s * ((k / m) - 0.5 * (used - 1));
+    } else if (form == OR_FORM_CUBE) {
+        int m = root_ceil(n, 3), layers = (n + m * m - 1) / (m * m);
+        out[0] = s * ((k % m) - 0.5 * (m - 1));
+        out[1] = s * (((k / m) % m) - 0.5 * (m - 1));
+        out[2] = s * ((k / (m * m)) - 0.5 * (layers - 1));
+    }
+}
+
+/* floor(top24(r) * n / 2^24): an exact uniform integer choice in [0, n) */
+static uint32_t pick(uint32_t r, uint32_t n) { return (uint32_t)(((uint64_t)(r >> 8) * n) >> 24); }
+
+static void raw_block(const uint32_t key_in[2], uint32_t c0, uint32_t c1, uint32_t c2, uint32_t r[4]) {
+    uint32_t ctr[4] = {c0, c1, c2, 0u};
+    uint32_t key[2] = {key_in[0], key_in[1]};
+    or_philox4x32_10(ctr, key, r);
+}
+
+/* S0: scenario record of env e, five Philox blocks at (tick, e, tag << 16 |
+ * block). The type is uniform over the enabled ones, each formation uniform
+ * over the five, the switch step uniform in [T/4, 3T/4] (T the episode
+ * length; at least 1), the centres uniform in the room shrunk by the
+ * clearance m on every face; a 32-bit seed keys the evader's waypoints and
+ * the swap permutation. Lissajous: centre uniform within 1 m (per axis) of the
+ * room's middle, amplitude U(0.5, 1) times the half-extent the clearance
+ * leaves, frequency U(0.5, 1.5) times the base, phase U(0, 1) turns. With
+ * only the single goal enabled the record stays zero and draws nothing. */
+static void draw_scenario(or_env* h, const uint32_t key[2], uint32_t tick, uint32_t tag, int e) {
+    const or_config* c = &h->cfg;
+    double* rec = h->scn + (size_t)e * OR_NSCN;
+    for (int k = 0; k < OR_NSCN; ++k) rec[k] = 0.0;
+    const uint32_t mask = c->scenarios & ((1u << OR_NSCN_TYPES) - 1u);
+    if ((mask & ~1u) == 0) return;
+    uint32_t r[5][4];
+    for (uint32_t b = 0; b < 5; ++b) raw_block(key, tick, (uint32_t)e, (tag << 16) | b, r[b]);
+    uint32_t n_en = 0;
+    for (int t = 0; t < OR_NSCN_TYPES; ++t) n_en += (mask >> t) & 1u;
+    uint32_t idx = pick(r[0][0], n_en);
+    int type = 0;
+    for (int t = 0; t < OR_NSCN_TYPES; ++t) {
+        if (!((mask >> t) & 1u)) continue;
+        if (idx == 0) { type = t; break; }
+        --idx;
+    }
+    rec[OR_R_TYPE] = type;
+    rec[OR_R_F0] = pick(r[0][1], OR_NFORM);
+    rec[OR_R_F1] = pick(r[0][2], OR_NFORM);
+    int lo = c->episode_steps / 4, hi = 3 * c->episode_steps / 4;
+    if (lo < 1) lo = 1;
+    if (hi < lo) hi = lo;
+    rec[OR_R_TSW] = lo + (int)pick(r[0][3], (uint32_t)(hi - lo + 1));
+    rec[OR_R_SEED_LO] = r[1][3] & 0xffffu;
+    rec[OR_R_SEED_HI] = r[1][3] >> 16;
+    const double m = c->scn_margin, hx = c->room_hx, hy = c->room_hy, hz = c->room_h;
+    if (type == OR_SCN_PURSUIT_LISSAJOUS) {
+        const double a[3] = {hx - m, hy - m, 0.5 * hz - m};
+        rec[OR_R_C0 + 0] = -1.0 + 2.0 * or_uniform(r[1][0]);
+        rec[OR_R_C0 + 1] = -1.0 + 2.0 * or_uniform(r[1][1]);
+        rec[OR_R_C0 + 2] = 0.5 * hz - 1.0 + 2.0 * or_uniform(r[1][2]);
+        for (int k = 0; k < 3; ++k) {
+            rec[OR_R_C1 + k] = a[k] * (0.5 + 0.5 * or_uniform(r[2][k]));
+            rec[OR_R_FREQ + k] = c->liss_f * (0.5 + or_uniform(r[3][k]));
+            rec[OR_R_PHASE + k] = or_uniform(r[4][k]);
+        }
+    } else {
+        for (int q = 0; q < 2; ++q) {
+            double* cc = rec + (q ? OR_R_C1 : OR_R_C0);
+            const uint32_t* rr = r[1 + q];
+            cc[0] = -hx + m + 2.0 * (hx - m) * or_uniform(rr[0]);
+            cc[1] = -hy + m + 2.0 * (hy - m) * or_uniform(rr[1]);
+            cc[2] = m + (hz - 2.0 * m) * or_uniform(rr[2]);
+        }
+    }
+}
+
+static uint32_t rec_seed(const double* rec) {
+    return (uint32_t)rec[OR_R_SEED_LO] | ((uint32_t)rec[OR_R_SEED_HI] << 16);
+}
+
+/* Goal slot of drone i after a swap: the rank of its key among the N keys of
+ * the env (ties to the lower index), key_j = first word of the Philox block at
+ * (seed, j, SWAP << 16) -- a uniformly random permutation of the slots. */
+static int swap_slot(const or_env* h, uint32_t seed, int i, int N) {
+    uint32_t r[4], ki;
+    raw_block(h->key, seed, (uint32_t)i, OR_TAG_SWAP << 16, r);
+    ki = r[0];
+    int rank = 0;
+    for (int j = 0; j < N; ++j) {
+        raw_block(h->key, seed, (uint32_t)j, OR_TAG_SWAP << 16, r);
+        if (r[0] < ki || (r[0] == ki && j < i)) ++rank;
+    }
+    return rank;
+}
+
+/* Evader waypoint j >= -1: uniform in the room shrunk by the clearance, from
+ * the Philox block at (seed, j + 1, WAYPOINT << 16). */
+static void waypoint(const or_env* h, uint32_t seed, int j, double w[3]) {
+    const or_config* c = &h->cfg;
+    const double m = c->scn_margin;
+    uint32_t r[4];
+    raw_block(h->key, seed, (uint32_t)(j + 1), OR_TAG_WAYPOINT << 16, r);
+    w[0] = -c->room_hx + m + 2.0 * (c->room_hx - m) * or_uniform(r[0]);
+    w[1] = -c->room_hy + m + 2.0 * (c->room_hy - m) * or_uniform(r[1]);
+    w[2] = m + (c->room_h - 2.0 * m) * or_uniform(r[2]);
+}
+
+/* Goal of local drone i (of N) of env e at control step tau of its episode.
+ *   single:          the env's goal;
+ *   static:          formation F0 around centre 0;
+ *   dynamic goals:   from the switch step on, formation F1 around centre 1;
+ *   swap goals:      from the switch step on, drone i takes slot swap_slot(i);
+ *   shrink & expand: formation F0 scaled by 1 - (1 - se_min)(1 - cos(2 pi tau / P)) / 2;
+ *   swarm vs swarm:  the first ceil(N/2) drones form group 0, the rest group 1,
+ *                    each a formation of its own size; group g is around centre g
+ *                    in F0, and from the switch step on around the other
+ *                    group's centre in F1;
+ *   Lissajous:       every drone chases c + A sin(2 pi (f tau T + phase)) per axis,
+ *                    T = substeps dt the control period;
+ *   Bezier:          every drone chases a point moving through the waypoints, one
+ *                    per S = bez_seg control steps: on segment q = floor(tau / S)
+ *                    the cubic Bezier curve from W_q to W_{q+1} with inner control
+ *                    points W_q + (W_{q+1} - W_{q-1})/6 and W_{q+1} - (W_{q+2} - W_q)/6
+ *                    (Catmull-Rom tangents, so the path is C1), at u = (tau - qS)/S. */
+static void drone_goal(const or_env* h, int e, int i, int N, int tau, double g[3]) {
+    const or_config* c = &h->cfg;
+    const double* rec = h->scn + (size_t)e * OR_NSCN;
+    const int type = (int)rec[OR_R_TYPE];
+    if ((c->scenarios & ~1u) == 0 || type == OR_SCN_SINGLE) {
+        for (int k = 0; k < 3; ++k) g[k] = h->goal[(size_t)e * 3 + k];
+        return;
+    }
+    const double s = c->form_spacing, rmax = c->form_rmax;
+    const int sw = tau >= (int)rec[OR_R_TSW];
+    const int f0 = (int)rec[OR_R_F0], f1 = (int)rec[OR_R_F1];
+    const double *c0 = rec + OR_R_C0, *c1 = rec + OR_R_C1;
+    double off[3];
+    if (type == OR_SCN_STATIC || type == OR_SCN_SHRINK_EXPAND) {
+        or_formation_offset(f0, i, N, s, rmax, off);
+        double lam = 1.0;
+        if (type == OR_SCN_SHRINK_EXPAND)
+            lam = 1.0 - (1.0 - c->se_min) * 0.5 * (1.0 - cos(2.0 * M_PI * tau / c->se_period));
+        for (int k = 0; k < 3; ++k) g[k] = c0[k] + lam * off[k];
+    } else if (type == OR_SCN_DYNAMIC) {
+        or_formation_offset(sw ? f1 : f0, i, N, s, rmax, off);
+        for (int k = 0; k < 3; ++k) g[k] = (sw ? c1[k] : c0[k]) + off[k];
+    } else if (type == OR_SCN_SWAP) {
+        const int slot = sw ? swap_slot(h, rec_seed(rec), i, N) : i;
+        or_formation_offset(f0, slot, N, s, rmax, off);
+        for (int k = 0; k < 3; ++k) g[k] = c0[k] + off[k];
+    } else if (type == OR_SCN_SWARM_VS_SWARM) {
+        const int n0 = (N + 1) / 2, grp = i >= n0;
+        const int kk = i - grp * n0, ng = grp ? N - n0 : n0;
+        or_formation_offset(sw ? f1 : f0, kk, ng, s, rmax, off);
+        const double* cc = (grp ^ sw) ? c1 : c0;
+        for (int k = 0; k < 3; ++k) g[k] = cc[k] + off[k];
+    } else if (type == OR_SCN_PURSUIT_LISSAJOUS) {
+        const double T = c->substeps * c->dt;
+        for (int k = 0; k < 3; ++k) {
+            double p = rec[OR_R_FREQ + k] * tau * T + rec[OR_R_PHASE + k];
+            g[k] = c0[k] + c1[k] * sin(2.0 * M_PI * (p - floor(p)));
+        }
+    } else if (type == OR_SCN_PURSUIT_BEZIER) {
+        const int S = (int)c->bez_seg, q = tau / S;
+        const double u = (double)(tau - q * S) / S, v = 1.0 - u;
+        const uint32_t seed = rec_seed(rec);
+        double wm[3], w0[3], w1[3], w2[3];
+        waypoint(h, seed, q - 1, wm);
+        waypoint(h, seed, q, w0);
+        waypoint(h, seed, q + 1, w1);
+        waypoint(h, seed, q + 2, w2);
+        for (int k = 0; k < 3; ++k) {
+            double p1 = w0[k] + (w1[k] - wm[k]) / 6.0, p2 = w1[k] - (w2[k] - w0[k]) / 6.0;
+            g[k] = v * v * v * w0[k] + 3.0 * v * v * u * p1 + 3.0 * v * u * u * p2 + u * u * u * w1[k];
+        }
+    } else {
+        for (int k = 0; k < 3; ++k) g[k] = h->goal[(size_t)e * 3 + k];
+    }
 }
 
 /* S0: per-drone initial state. Position uniform in the room, velocity and
@@ -347,6 +593,7 @@ static void reset_drone(or_env* h, const uint32_t key[2], uint32_t tick, uint32_
 static void reset_env_all(or_env* h, const uint32_t key[2], uint32_t tick, uint32_t tag_env,
                           uint32_t tag_drone, int e) {
     reset_env_params(h, key, tick, tag_env, e);
+    draw_scenario(h, key, tick, tag_env == OR_TAG_AUTO_ENV ? OR_TAG_AUTO_SCN : OR_TAG_SCN, e);
     for (int d = h->env_off[e]; d < h->env_off[e + 1]; ++d) reset_drone(h, key, tick, tag_drone, e, d);
     h->ep_t[e] = 0;
 }
@@ -661,10 +908,10 @@ static void knn_env(or_env* h, int d0, int N, int keff, const float* xf, int32_t
  * neighbour x_j - x_i, v_j - v_i; zeros past keff]. Sensor noise (Sec. III-C)
  * read as U(-s, s) on x and v and N(0, s^2) on w, from the OBS stream with
  * substream `sub` (0: control step, 1: observation of a freshly reset env). */
-static void obs_row(or_env* h, int e, int i, const int32_t* nbr, int keff, uint32_t sub, double* o) {
+static void obs_row(or_env* h, int e, int i, const int32_t* nbr, int keff, uint32_t sub, const double goal[3],
+                    double* o) {
     const or_config* c = &h->cfg;
     const int d0 = h->env_off[e], d = d0 + i, K = c->k_neighbors;
-    const double* goal = h->goal + (size_t)e * 3;
     const double* s = h->st + (size_t)d * OR_NST;
     const double *x = s + OR_S_X, *v = s + OR_S_V, *R = s + OR_S_R, *w = s + OR_S_W;
     double ex[3] = {0, 0, 0}, evv[3] = {0, 0, 0}, ew[3] = {0, 0, 0};
@@ -708,7 +955,6 @@ static void step_env(or_env* h, int e, const double* actions, double* obs, doubl
     const int keff = K < N - 1 ? K : N - 1;
     const int od = 18 + 6 * K;
     const double* p = h->prm + (size_t)e * OR_NPRM;
-    const double* goal = h->goal + (size_t)e * 3;
     const int smooth = (c->flags & OR_F_SMOOTH) != 0;
 
     double* fhat = (double*)malloc(sizeof(double) * 4 * (size_t)N);
@@ -845,7 +1091,10 @@ static void step_env(or_env* h, int e, const double* actions, double* obs, doubl
         const double *x = s + OR_S_X, *v = s + OR_S_V, *R = s + OR_S_R, *w = s + OR_S_W;
         double* fprev = s + OR_S_FPREV;
         const double* fh = fhat + 4 * i;
-        if (obs) obs_row(h, e, i, nbr, keff, 0, obs + (size_t)d * od);
+        /* the goal at the end of the step (Sec. III-D scenarios), tau = steps done */
+        double goal[3];
+        drone_goal(h, e, i, N, h->ep_t[e] + 1, goal);
+        if (obs) obs_row(h, e, i, nbr, keff, 0, goal, obs + (size_t)d * od);
         if (rew) {
             const double* W = c->w;
             double dxg[3] = {x[0] - goal[0], x[1] - goal[1], x[2] - goal[2]};
@@ -939,7 +1188,11 @@ void or_observe(or_env* h, double* obs) {
         for (int i = 0; i < N; ++i)
             for (int k = 0; k < 3; ++k) xf[3 * i + k] = (float)h->st[(size_t)(d0 + i) * OR_NST + OR_S_X + k];
         knn_env(h, d0, N, keff, xf, nbr);
-        for (int i = 0; i < N; ++i) obs_row(h, e, i, nbr, keff, 1, obs + (size_t)(d0 + i) * od);
+        for (int i = 0; i < N; ++i) {
+            double goal[3];
+            drone_goal(h, e, i, N, h->ep_t[e], goal);
+            obs_row(h, e, i, nbr, keff, 1, goal, obs + (size_t)(d0 + i) * od);
+        }
         free(xf); free(nbr);
     }
 }
@@ -962,6 +1215,22 @@ void or_set_state(or_env* h, const double* st, const double* prm, const double* 
     if (goal) memcpy(h->goal, goal, sizeof(double) * (size_t)h->cfg.n_envs * 3);
     if (ep_t) memcpy(h->ep_t, ep_t, sizeof(int32_t) * (size_t)h->cfg.n_envs);
     if (tick) memcpy(h->tick, tick, sizeof(uint32_t) * (size_t)h->cfg.n_envs);
+}
+
+void or_get_scenario(const or_env* h, double* rec) {
+    memcpy(rec, h->scn, sizeof(double) * (size_t)h->cfg.n_envs * OR_NSCN);
+}
+
+void or_set_scenario(or_env* h, const double* rec) {
+    memcpy(h->scn, rec, sizeof(double) * (size_t)h->cfg.n_envs * OR_NSCN);
+}
+
+/* Goals [D][3] of every drone at its env's current control step. */
+void or_goals(const or_env* h, double* goals) {
+    for (int e = 0; e < h->cfg.n_envs; ++e) {
+        const int d0 = h->env_off[e], N = h->env_off[e + 1] - d0;
+        for (int i = 0; i < N; ++i) drone_goal(h, e, i, N, h->ep_t[e], goals + 3 * (size_t)(d0 + i));
+    }
 }
 
 void or_get_events(const or_env* h, uint32_t* ev, int32_t* knn, double* margin, double* margin_knn, double* cond) {

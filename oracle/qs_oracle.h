@@ -37,6 +37,33 @@
 #define OR_TAG_AUTO_ENV    7u
 #define OR_TAG_AUTO_DRONE  8u
 #define OR_TAG_DOWNWASH    9u
+#define OR_TAG_SCN         10u /* scenario record of a reset */
+#define OR_TAG_AUTO_SCN    11u /* scenario record of an auto-reset */
+#define OR_TAG_WAYPOINT    12u /* evader waypoints (counter word 0 = the record's seed) */
+#define OR_TAG_SWAP        13u /* goal-swap permutation keys (counter word 0 = the record's seed) */
+
+/* training scenarios (Sec. III-D); or_config.scenarios is a mask of 1 << type */
+enum {
+    OR_SCN_SINGLE, OR_SCN_STATIC, OR_SCN_DYNAMIC, OR_SCN_SWAP, OR_SCN_SHRINK_EXPAND,
+    OR_SCN_SWARM_VS_SWARM, OR_SCN_PURSUIT_LISSAJOUS, OR_SCN_PURSUIT_BEZIER, OR_NSCN_TYPES
+};
+/* goal formations */
+enum { OR_FORM_CIRCLE, OR_FORM_GRID, OR_FORM_SPHERE, OR_FORM_CYLINDER, OR_FORM_CUBE, OR_NFORM };
+/* per-env scenario record [OR_NSCN]: type, formation before / after the
+ * switch, switch step, seed (low 16 bits), centre 0 (3), centre 1 or the
+ * Lissajous amplitudes (3), Lissajous frequencies in Hz (3), Lissajous phases
+ * in turns (3), seed (high 16 bits) */
+#define OR_NSCN 18
+#define OR_R_TYPE 0
+#define OR_R_F0 1
+#define OR_R_F1 2
+#define OR_R_TSW 3
+#define OR_R_SEED_LO 4
+#define OR_R_C0 5
+#define OR_R_C1 8
+#define OR_R_FREQ 11
+#define OR_R_PHASE 14
+#define OR_R_SEED_HI 17
 
 /* per-drone state row: x(3) v(3) R(9, row-major) w(3) uf(4) eps(4) fprev(4) */
 #define OR_NST 30
@@ -69,7 +96,7 @@ typedef struct {
     int32_t n_envs, k_neighbors, substeps, episode_steps;
     double dt;
     uint64_t seed;
-    uint32_t flags, pad_;
+    uint32_t flags, scenarios; /* scenarios: mask of 1 << OR_SCN_* drawn from at each reset */
     double mass, arm, ixx, iyy, izz, t2w, kappa, tau_m, gravity, mu;
     double alpha_nd, alpha_ns_frac, alpha_c, coll_sigma_v, coll_sigma_w;
     double obs_sigma_x, obs_sigma_v, obs_sigma_w;
@@ -79,6 +106,11 @@ typedef struct {
     double prox_factor;
     double omega_max;
     double dw_k1, dw_k2, dw_b1, dw_height, dw_sigma_a, dw_sigma_w; /* downwash */
+    /* scenarios: goal spacing, radius cap of circles and cylinders, clearance of
+     * centres from the room's faces, smallest scale of shrink & expand and its
+     * period (control steps), base Lissajous frequency (Hz), control steps per
+     * Bezier segment */
+    double form_spacing, form_rmax, scn_margin, se_min, se_period, liss_f, bez_seg;
     double w[OR_NW];
 } or_config;
 
@@ -88,6 +120,7 @@ typedef struct {
     int32_t* env_off;  /* [E+1] */
     double* prm;       /* [E][OR_NPRM] */
     double* goal;      /* [E][3] */
+    double* scn;       /* [E][OR_NSCN] scenario records */
     double* st;        /* [D][OR_NST] */
     int32_t* ep_t;     /* [E] control steps since the env's episode began */
     uint32_t* ev;      /* [D] event bits of the last step */
@@ -114,6 +147,10 @@ void or_observe(or_env* h, double* obs);
 void or_get_state(const or_env* h, double* st, double* prm, double* goal, int32_t* ep_t, uint32_t* tick);
 void or_set_state(or_env* h, const double* st, const double* prm, const double* goal, const int32_t* ep_t,
                   const uint32_t* tick);
+void or_get_scenario(const or_env* h, double* rec);
+void or_set_scenario(or_env* h, const double* rec);
+void or_goals(const or_env* h, double* goals);
+void or_formation_offset(int form, int k, int n, double s, double rmax, double out[3]);
 void or_get_events(const or_env* h, uint32_t* ev, int32_t* knn, double* margin, double* margin_knn, double* cond);
 void or_clear_margin(or_env* h);
 void or_pairs_f32(const float* pos, const float* arm, const int32_t* env_off, int n_envs, int K,

@@ -668,3 +668,250 @@ def test_downwash_noise_moments():
         assert abs(lower[:, 15 + k].std() / (Tc * c.dw_sigma_w) - 1.0) < 0.05
     assert abs(np.corrcoef(dv[:, 0], lower[:, 15])[0, 1]) < 0.06
     assert np.abs(upper[:, 3:6]).max() < 1e-12 and np.abs(upper[:, 15:18]).max() < 1e-12
+
+
+# --------------------------------------------------------------------------- scenarios (Sec. III-D)
+FORM_SIZES = [1, 2, 3, 5, 8, 17, 64, 100, 128]
+
+
+def _offsets(form, n, s=0.5, rmax=4.0):
+    return np.array([O.formation_offset(form, k, n, s, rmax) for k in range(n)])
+
+
+def _min_dist(p):
+    d = np.linalg.norm(p[:, None] - p[None], axis=2) + np.eye(len(p)) * 1e9
+    return d.min()
+
+
+def test_formation_circle_and_cylinder():
+    s = 0.5
+    for n in FORM_SIZES:
+        p = _offsets("circle", n, s)
+        r = np.hypot(p[:, 0], p[:, 1])
+        want_r = min(s * n / (2 * math.pi), 4.0)
+        assert np.allclose(r, want_r, rtol=1e-12) and np.abs(p[:, 2]).max() == 0.0
+        if n >= 2:  # evenly spaced: neighbouring goals a chord 2 r sin(pi/n) apart, arc s when uncapped
+            ang = np.sort(np.mod(np.arctan2(p[:, 1], p[:, 0]), 2 * math.pi))
+            gaps = np.diff(np.concatenate([ang, [ang[0] + 2 * math.pi]]))
+            assert np.allclose(gaps, 2 * math.pi / n, atol=1e-12)
+            if want_r < 4.0:
+                assert abs(want_r * 2 * math.pi / n - s) < 1e-12
+        p = _offsets("cylinder", n, s)
+        L = next(L for L in range(1, 20) if 4 * L * L >= n)
+        m = -(-n // L)
+        r = np.hypot(p[:, 0], p[:, 1])
+        assert np.allclose(r, min(s * m / (2 * math.pi), 4.0), rtol=1e-12)
+        levels = np.unique(np.round(p[:, 2] / s, 9))
+        assert np.allclose(np.diff(levels), 1.0) and abs(levels.mean()) < 1e-9  # rings s apart, centred
+        assert max(np.sum(np.isclose(p[:, 2], z * s)) for z in levels) <= m
+        if n >= 2:
+            assert _min_dist(p) > 1e-6  # distinct goals
+
+
+def test_formation_grid_and_cube():
+    s = 0.5
+    for n in FORM_SIZES:
+        for form, dim in (("grid", 2), ("cube", 3)):
+            p = _offsets(form, n, s)
+            q = p / s
+            m = next(m for m in range(1, 20) if m ** dim >= n)
+            # every coordinate on the half-spacing lattice, goals distinct, nearest neighbours s apart
+            assert np.allclose(2 * q, np.round(2 * q), atol=1e-12)
+            if dim == 2:
+                assert np.abs(p[:, 2]).max() == 0.0
+            if n >= 2:
+                assert abs(_min_dist(p) - s) < 1e-12
+            assert len({tuple(np.round(r, 9)) for r in q}) == n
+            ext = q.max(axis=0) - q.min(axis=0)
+            assert ext[:dim].max() <= m - 1 + 1e-12
+            if n == m ** dim:  # a full grid is centred
+                assert np.abs(p.mean(axis=0)).max() < 1e-12
+
+
+def test_formation_sphere_fibonacci():
+    s = 0.5
+    golden = (3 - math.sqrt(5)) / 2  # turns
+    for n in FORM_SIZES:
+        p = _offsets("sphere", n, s)
+        r = s * math.sqrt(n / (4 * math.pi))
+        assert np.allclose(np.linalg.norm(p, axis=1), r, rtol=1e-12)
+        assert abs(4 * math.pi * r * r / n - s * s) < 1e-12       # area s^2 per goal
+        z = p[:, 2] / r
+        assert np.allclose(np.diff(z), -2.0 / n, atol=1e-12) and abs(z.mean()) < 1e-12
+        if n >= 2:
+            az = np.arctan2(p[:, 1], p[:, 0]) / (2 * math.pi)
+            step = np.mod(np.diff(az) - golden + 0.5, 1.0) - 0.5   # azimuth advances by the golden angle
+            ok = np.abs(z[:-1]) < 1 - 1e-9
+            assert np.abs(step[ok[:len(step)]]).max() < 1e-8
+            assert _min_dist(p) > 0.3 * s
+    p = _offsets("sphere", 128, s)
+    assert np.linalg.norm(p.mean(axis=0)) < 0.02 * s * math.sqrt(128 / (4 * math.pi))
+
+
+def _scn_oracle(sizes, mask, seed=7, episode_steps=1500, **kw):
+    c, o = make(n_envs=len(sizes), sizes=sizes, scenarios=mask, episode_steps=episode_steps, **kw)
+    o.reset(seed)
+    return c, o
+
+
+def test_scenario_draw_distribution():
+    E = 24000
+    c, o = _scn_oracle([1] * E, 0xFF)
+    rec = o.get_scenario()
+    t = rec[:, O.R_TYPE].astype(int)
+    cnt = np.bincount(t, minlength=8)
+    assert (np.abs(cnt - E / 8) < 5 * math.sqrt(E / 8)).all()
+    for col in (O.R_F0, O.R_F1):
+        cf = np.bincount(rec[:, col].astype(int), minlength=5)
+        assert len(cf) == 5 and (np.abs(cf - E / 5) < 5 * math.sqrt(E / 5)).all()
+    tsw = rec[:, O.R_TSW]
+    assert tsw.min() >= 375 and tsw.max() <= 1125 and np.all(tsw == np.round(tsw))
+    assert abs(tsw.mean() - 750) < 5 * 217 / math.sqrt(E)
+    form = t != O.SCN_NAMES.index("pursuit_lissajous")
+    for q in (O.R_C0, O.R_C1):
+        cc = rec[form & (t != 0), q:q + 3]
+        assert cc[:, 0].min() >= -3.5 and cc[:, 0].max() <= 3.5 and cc[:, 2].min() >= 1.5 and cc[:, 2].max() <= 8.5
+        assert abs(cc[:, 0].mean()) < 0.05 and abs(cc[:, 2].mean() - 5.0) < 0.05
+    li = t == O.SCN_NAMES.index("pursuit_lissajous")
+    A = rec[li, O.R_C1:O.R_C1 + 3]
+    assert (A >= 0.5 * np.array([3.5, 3.5, 3.5]) - 1e-12).all() and (A <= 3.5 + 1e-12).all()
+    f = rec[li, O.R_FREQ:O.R_FREQ + 3]
+    assert f.min() >= 0.05 and f.max() <= 0.15
+    seeds = rec[:, O.R_SEED_LO] + 65536 * rec[:, O.R_SEED_HI]
+    assert len(np.unique(seeds[t != 0])) > 0.99 * (t != 0).sum()
+    # a subset of scenarios draws only from that subset; the single goal alone draws no record
+    _, o2 = _scn_oracle([1] * 2000, O.scenario_mask(["static", "swap"]))
+    assert set(np.unique(o2.get_scenario()[:, O.R_TYPE]).astype(int)) == {1, 3}
+    _, o3 = _scn_oracle([1] * 10, O.scenario_mask(["single"]))
+    assert np.abs(o3.get_scenario()).max() == 0.0
+
+
+def _with_record(sizes, rec, ep):
+    """Oracle whose envs all carry scenario record `rec`, at control step ep."""
+    E = len(sizes)
+    c, o = _scn_oracle(sizes, 0xFF)
+    o.set_scenario(np.tile(rec, (E, 1)))
+    s = o.get_state()
+    o.set_state(ep_step=np.full(E, ep, np.int32))
+    return c, o
+
+
+def _record(kind, f0=0, f1=1, tsw=10, seed=12345, c0=(0.5, -1.0, 4.0), c1=(-2.0, 1.5, 6.0), freq=(0.1, 0.13, 0.07),
+            phase=(0.1, 0.6, 0.3)):
+    r = np.zeros(O.NSCN)
+    r[O.R_TYPE] = O.SCN_NAMES.index(kind)
+    r[O.R_F0], r[O.R_F1], r[O.R_TSW] = f0, f1, tsw
+    r[O.R_SEED_LO], r[O.R_SEED_HI] = seed & 0xFFFF, seed >> 16
+    r[O.R_C0:O.R_C0 + 3] = c0
+    r[O.R_C1:O.R_C1 + 3] = c1
+    r[O.R_FREQ:O.R_FREQ + 3] = freq
+    r[O.R_PHASE:O.R_PHASE + 3] = phase
+    return r
+
+
+def _goals_at(c, o, ep):
+    o.set_state(ep_step=np.full(o.E, ep, np.int32))
+    return o.goals()
+
+
+def test_scenario_static_dynamic_swarm_vs_swarm():
+    n = 9
+    c, o = _with_record([n], _record("static", f0=2), 0)
+    want = np.array([0.5, -1.0, 4.0]) + _offsets("sphere", n)
+    for ep in (0, 9, 10, 700):
+        assert np.allclose(_goals_at(c, o, ep), want, atol=1e-12)
+    c, o = _with_record([n], _record("dynamic", f0=0, f1=4, tsw=10), 0)
+    assert np.allclose(_goals_at(c, o, 9), np.array([0.5, -1.0, 4.0]) + _offsets("circle", n), atol=1e-12)
+    assert np.allclose(_goals_at(c, o, 10), np.array([-2.0, 1.5, 6.0]) + _offsets("cube", n), atol=1e-12)
+    # swarm vs swarm: 5 + 4 drones; each group a formation of its own size; centres swap at the switch
+    c, o = _with_record([n], _record("swarm_vs_swarm", f0=1, f1=3, tsw=10), 0)
+    g = _goals_at(c, o, 9)
+    assert np.allclose(g[:5], np.array([0.5, -1.0, 4.0]) + _offsets("grid", 5), atol=1e-12)
+    assert np.allclose(g[5:], np.array([-2.0, 1.5, 6.0]) + _offsets("grid", 4), atol=1e-12)
+    g = _goals_at(c, o, 10)
+    assert np.allclose(g[:5], np.array([-2.0, 1.5, 6.0]) + _offsets("cylinder", 5), atol=1e-12)
+    assert np.allclose(g[5:], np.array([0.5, -1.0, 4.0]) + _offsets("cylinder", 4), atol=1e-12)
+
+
+def test_scenario_swap_is_a_permutation():
+    for n in (2, 3, 8, 17, 64):
+        perms = []
+        for seed in (1, 2, 3):
+            c, o = _with_record([n], _record("swap", f0=1, tsw=10, seed=seed), 0)
+            before = _goals_at(c, o, 9)
+            after = _goals_at(c, o, 10)
+            assert np.allclose(before, np.array([0.5, -1.0, 4.0]) + _offsets("grid", n), atol=1e-12)
+            # the same set of goals, reassigned one to one
+            idx = [int(np.argmin(np.linalg.norm(before - a, axis=1))) for a in after]
+            assert sorted(idx) == list(range(n))
+            assert np.allclose(after, before[idx], atol=1e-12)
+            assert np.allclose(_goals_at(c, o, 500), after, atol=0)  # fixed for the rest of the episode
+            perms.append(tuple(idx))
+        if n >= 8:
+            assert len(set(perms)) == 3 and all(p != tuple(range(n)) for p in perms)
+
+
+def test_scenario_shrink_expand():
+    n, P = 8, 400
+    c, o = _with_record([n], _record("shrink_expand", f0=4), 0)
+    base = _offsets("cube", n)
+    c0 = np.array([0.5, -1.0, 4.0])
+    for ep, lam in ((0, 1.0), (P // 4, 0.75), (P // 2, 0.5), (P, 1.0), (3 * P // 2, 0.5)):
+        assert np.allclose(_goals_at(c, o, ep) - c0, lam * base, atol=1e-12), ep
+
+
+def test_scenario_lissajous_is_sinusoidal():
+    """Each axis of the evader follows c + A sin(w tau + phi): it satisfies the
+    three-term recurrence y(t+1) + y(t-1) = 2 cos(w) y(t) of a pure sinusoid
+    with w = 2 pi f T, stays within c +- A, and starts at c + A sin(2 pi phase)."""
+    c, o = _with_record([3], _record("pursuit_lissajous", c1=(2.0, 3.0, 1.5)), 0)
+    T = c.substeps * c.dt
+    cen, A = np.array([0.5, -1.0, 4.0]), np.array([2.0, 3.0, 1.5])
+    f, ph = np.array([0.1, 0.13, 0.07]), np.array([0.1, 0.6, 0.3])
+    ys = np.array([_goals_at(c, o, t)[0] - cen for t in range(0, 1500, 7)])
+    g3 = _goals_at(c, o, 0)
+    assert np.allclose(g3, g3[0], atol=0)  # all drones chase the one evader
+    assert np.allclose(g3[0], cen + A * np.sin(2 * math.pi * ph), atol=1e-12)
+    for t in (1, 50, 777, 1400):
+        y0, y1, y2 = (_goals_at(c, o, t + k)[0] - cen for k in (-1, 0, 1))
+        assert np.allclose(y0 + y2, 2 * np.cos(2 * math.pi * f * T) * y1, atol=1e-12)
+    assert (np.abs(ys) <= A + 1e-12).all() and (np.abs(ys).max(axis=0) > 0.9 * A).all()
+
+
+def test_scenario_bezier_through_waypoints_c1():
+    """The evader passes the waypoints at segment boundaries and its path is C1
+    there, with Catmull-Rom tangents: the step after a knot W_q is about
+    (W_{q+1} - W_{q-1}) / (2S), the same on either side."""
+    S = 300
+    c, o = _with_record([2], _record("pursuit_bezier"), 0)
+    knots = np.array([_goals_at(c, o, q * S)[0] for q in range(5)])
+    assert (np.abs(knots[:, :2]) <= 3.5).all() and (knots[:, 2] >= 1.5).all() and (knots[:, 2] <= 8.5).all()
+    for q in (1, 2, 3):
+        left = knots[q] - _goals_at(c, o, q * S - 1)[0]
+        right = _goals_at(c, o, q * S + 1)[0] - knots[q]
+        tangent = (knots[q + 1] - knots[q - 1]) / (2 * S)
+        assert np.allclose(left, tangent, atol=20.0 / S ** 2) and np.allclose(right, tangent, atol=20.0 / S ** 2)
+    mid = _goals_at(c, o, S // 2)[0]
+    assert np.linalg.norm(mid - knots[0]) > 1e-3 and np.linalg.norm(mid - knots[1]) > 1e-3
+
+
+def test_scenario_goal_used_by_the_step():
+    """The observation and the position reward of a step use the goal at the
+    step's end (tau = steps done), which is what or_goals reports after it."""
+    sizes = [8, 5]
+    c, o = _scn_oracle(sizes, O.scenario_mask(["dynamic"]), w=[0.0] * 13 + [0.0])
+    rec = np.array([_record("dynamic", f0=0, f1=1, tsw=4)] * 2)
+    o.set_scenario(rec)
+    o.set_state(ep_step=np.full(2, 3, np.int32))
+    st = o.get_state()["state"]
+    obs, rew, _ = o.step(np.full((13, 4), 0.5))
+    g = o.goals()                      # tau = 4: after the switch
+    x = o.get_state()["state"][:, 0:3]
+    assert np.allclose(obs[:, 0:3], x - g, atol=1e-12)
+    assert np.allclose(g, np.concatenate([np.array([-2.0, 1.5, 6.0]) + _offsets("grid", n) for n in sizes]))
+    assert np.abs(rew).max() == 0.0
+    _, o2 = _scn_oracle(sizes, O.scenario_mask(["dynamic"]), w=[-1.0] + [0.0] * 13)
+    o2.set_scenario(rec)
+    o2.set_state(state=st, ep_step=np.full(2, 3, np.int32))
+    _, rew2, _ = o2.step(np.full((13, 4), 0.5))
+    assert np.allclose(rew2, -np.linalg.norm(x - g, axis=1), atol=1e-12)
