@@ -308,11 +308,11 @@ def run_forms(dev, stream, seed):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     forms = {}
     with torch.cuda.stream(stream):
-        def make(wl, n_envs=None, feats=None):
+        def make(wl, n_envs=None, feats=None, scenarios=()):
             sizes = wl.sizes() if n_envs is None else np.full(n_envs, wl.swarm, np.int32)
             env = QuadSwarmEnv(len(sizes), sizes if wl.swarm is None else wl.swarm, wl.k_neighbors,
                                feats or (wl.features + ("auto_reset",)), seed=seed, weights=wl.weights, device=dev,
-                               stream=stream)
+                               stream=stream, scenarios=scenarios)
             env.reset(seed)
             return env
 
@@ -355,6 +355,20 @@ def run_forms(dev, stream, seed):
                                   "shape": list(tuned["rollout"])}
         env.close()
         del acts
+
+        # swarm 2048 x 8 with every training scenario (per-drone goals, Sec. III-D), and with downwash
+        for name, kw in (("swarm_scenarios", dict(scenarios=tuple(qs.SCENARIOS))),
+                         ("swarm_downwash", dict(feats=W.SWARM.features + ("auto_reset", "downwash")))):
+            env = make(W.SWARM, **kw)
+            tuned = autotune.tune(env, horizon=500)
+            acts = torch.from_numpy(W.actions(seed, 500, env.D)).to(dev)
+            ms_call = per_call(env, acts, 300)
+            ms_roll = rollout(env, acts, 500)
+            forms[name + "_call"] = {"value": env.D / ms_call * 1e3, "ms_per_step": ms_call}
+            forms[name + "_rollout"] = {"value": env.D / ms_roll * 1e3, "ms_per_step": ms_roll, "T": 500,
+                                        "shape": list(tuned["rollout"])}
+            env.close()
+            del acts
 
         # uneven swarms, 4096 envs, sizes {1..64}: one persistent launch vs per-size launches
         env = make(W.UNEVEN)

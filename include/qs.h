@@ -39,7 +39,9 @@
  *  done     [E]  uint8        1 when the env's episode reached episode_steps
  *  state    [D][30]           x(3) v(3) R(9) w(3) uf(4) eps(4) fprev(4)
  *  params   [E][7]            m, Ixx, Iyy, Izz, t2w, tau_m, arm
- *  goals    [E][3]
+ *  goals    [E][3]            the single goal of each env (scenario "single")
+ *  scenario [E][QS_NSCN]      scenario record of each env (see QS_SCN_*)
+ *  drone goals [D][3]         each drone's goal at its env's current step
  */
 #ifndef QS_H
 #define QS_H
@@ -80,6 +82,47 @@ typedef enum {
 #define QS_F_RECORD_KNN       (1u << 9) /* keep neighbour indices for qs_get_events */
 #define QS_F_DOWNWASH         (1u << 10) /* downwash from drones overlapping above (Sec. III-B) */
 
+/* Training scenarios (Sec. III-D). qs_config.scenarios is a mask of
+ * (1u << QS_SCN_*); at every reset each env draws its scenario uniformly from
+ * the enabled ones, together with a scenario record (below). The goal of each
+ * drone is then a function of the record, the drone's index i in its swarm,
+ * the swarm size N and the env's control step tau (the observation and reward
+ * of a step use tau = the steps done at its end):
+ *   SINGLE           the env's goal (goals [E][3]; the default, mask 0 or 1)
+ *   STATIC           formation F0 around centre 0
+ *   DYNAMIC          from the switch step on, formation F1 around centre 1
+ *   SWAP             from the switch step on, the drones take the same goals
+ *                    in a random order (drone i takes the rank of its Philox
+ *                    key among the env's N keys)
+ *   SHRINK_EXPAND    F0 scaled by 1 - (1 - se_min)(1 - cos(2 pi tau / se_period)) / 2
+ *   SWARM_VS_SWARM   two groups (the first ceil(N/2) drones and the rest), each
+ *                    a formation around its own centre; at the switch step the
+ *                    formation becomes F1 and the groups swap centres
+ *   PURSUIT_LISSAJOUS every drone chases c + A sin(2 pi (f tau T + phase)) per axis
+ *                    (T = substeps dt)
+ *   PURSUIT_BEZIER   every drone chases a point moving along cubic Bezier
+ *                    segments (Catmull-Rom tangents) through random waypoints,
+ *                    bez_seg control steps per segment
+ * Formations (QS_FORM_*) of n goals, spacing form_spacing: a horizontal circle
+ * (radius n s / 2 pi, at most form_rmax), a horizontal square grid, a
+ * Fibonacci-lattice sphere (area s^2 per goal), stacked rings (cylinder), a
+ * cubic grid. */
+enum {
+    QS_SCN_SINGLE, QS_SCN_STATIC, QS_SCN_DYNAMIC, QS_SCN_SWAP, QS_SCN_SHRINK_EXPAND, QS_SCN_SWARM_VS_SWARM,
+    QS_SCN_PURSUIT_LISSAJOUS, QS_SCN_PURSUIT_BEZIER, QS_NSCN_TYPES
+};
+enum { QS_FORM_CIRCLE, QS_FORM_GRID, QS_FORM_SPHERE, QS_FORM_CYLINDER, QS_FORM_CUBE, QS_NFORM };
+/* Scenario record (floats holding small integers where noted): type, formation
+ * before and after the switch, switch step (uniform in [T/4, 3T/4] of the
+ * episode), 32-bit seed as low / high 16 bits, centre 0 (3), centre 1 or the
+ * Lissajous amplitudes (3), Lissajous frequencies in Hz (3) and phases in
+ * turns (3). All zero under SINGLE. */
+#define QS_NSCN 18
+enum {
+    QS_R_TYPE = 0, QS_R_F0 = 1, QS_R_F1 = 2, QS_R_TSW = 3, QS_R_SEED_LO = 4, QS_R_C0 = 5, QS_R_C1 = 8,
+    QS_R_FREQ = 11, QS_R_PHASE = 14, QS_R_SEED_HI = 17
+};
+
 /* qs_get_events bits (per drone, last control step) */
 #define QS_EV_HIT_FLOOR (1u << 0)
 #define QS_EV_ON_FLOOR  (1u << 1)
@@ -108,7 +151,10 @@ enum {
  * (0, dw_height)) adds dw_k1 (dw_k2 dz + dw_b1) downward acceleration to it
  * for the control step, with k1 = 2.4525 m/s^2 (g/4), k2 = -2 1/m, b1 = 1,
  * dw_height 0.5 m, noise N(0, 0.1^2) m/s^2 on the acceleration and
- * N(0, 1^2) rad/s^2 on the angular acceleration. */
+ * N(0, 1^2) rad/s^2 on the angular acceleration; scenarios (Sec. III-D gives
+ * no sizes or rates): goals 0.5 m apart, circle radius at most 4 m, centres
+ * 1.5 m clear of the room's faces, shrink to half size and back every 400
+ * steps, Lissajous base frequency 0.1 Hz, 300 steps per Bezier segment. */
 typedef struct {
     float mass, arm, ixx, iyy, izz, t2w, kappa, tau_m, gravity, mu;
     float alpha_nd, alpha_ns_frac, alpha_c, coll_sigma_v, coll_sigma_w;
@@ -117,6 +163,7 @@ typedef struct {
     float dr_lo, dr_hi;
     float smooth_beta, smooth_kc, prox_factor, omega_max;
     float dw_k1, dw_k2, dw_b1, dw_height, dw_sigma_a, dw_sigma_w;
+    float form_spacing, form_rmax, scn_margin, se_min, se_period, liss_f, bez_seg;
     float w[QS_NW];
 } qs_params;
 
@@ -131,6 +178,7 @@ typedef struct {
     int32_t episode_steps;      /* control steps per episode (1500 = 15 s) */
     uint64_t seed;              /* Philox key of the first reset */
     uint32_t flags;             /* QS_F_* */
+    uint32_t scenarios;         /* mask of 1u << QS_SCN_* (0: single goal) */
     qs_params params;
 } qs_config;
 
@@ -216,8 +264,8 @@ qs_status qs_get_rollout_shape(const qs_env* h, int32_t* block, int32_t* fuse, i
  * step (dynamics, integrator with re-orthonormalisation, smooth contacts),
  * writing grad_actions_dev [T][D][4] and grad_x0_dev [D][30] (zero for the
  * previous-command entries, which do not enter the loss). A handle created
- * with QS_F_DOWNWASH returns QS_ERR_UNSUPPORTED: the smooth form has no
- * downwash term. */
+ * with QS_F_DOWNWASH or with scenarios other than the single goal returns
+ * QS_ERR_UNSUPPORTED: the smooth form has neither. */
 qs_status qs_diff_workspace_size(const qs_env* h, int32_t T, int32_t ckpt_every, size_t* bytes);
 qs_status qs_diff_forward(qs_env* h, int32_t T, int32_t ckpt_every, const float* x0_dev, const float* actions_dev,
                           float* loss_dev, void* workspace_dev);
@@ -257,6 +305,17 @@ qs_status qs_get_state(qs_env* h, float* state_dev, float* params_dev, float* go
  * qs_get_state). Derived per-env constants are recomputed from params_dev. */
 qs_status qs_set_state(qs_env* h, const float* state_dev, const float* params_dev, const float* goals_dev,
                        const int32_t* ep_step_dev, const uint32_t* tick_dev);
+
+/* Scenario records [E][QS_NSCN] of every env (layout above): copied out to,
+ * or overwritten from, a caller buffer. A record whose type is not enabled in
+ * the handle's mask is still evaluated as written. */
+qs_status qs_get_scenario(qs_env* h, float* records_dev);
+qs_status qs_set_scenario(qs_env* h, const float* records_dev);
+
+/* Goal of every drone at its env's current control step (Sec. III-D), into
+ * goals_dev [D][3]: what the next observation after a reset, or the reward of
+ * the step that ended at this control step, measured against. */
+qs_status qs_get_goals(qs_env* h, float* goals_dev);
 
 /* Event bits of the last step per drone (events_dev [D], QS_EV_*) and, when
  * the handle was created with QS_F_RECORD_KNN, the neighbour list knn_dev

@@ -17,7 +17,7 @@ _CACHE: dict = {}
 
 def _signature(env) -> tuple:
     c = env.cfg
-    return (env.D, env.E, env.K, int(c.flags), int(c.substeps), tuple(np.asarray(env.sizes).tolist())
+    return (env.D, env.E, env.K, int(c.flags), int(c.scenarios), int(c.substeps), tuple(np.asarray(env.sizes).tolist())
             if env.sizes is not None else int(c.n_per_env))
 
 
@@ -42,7 +42,7 @@ def tune(env, steps: int = 32, horizon: int = 64, reps: int = 3, apply: bool = T
     else:
         twin = QuadSwarmEnv(env.E, env.sizes if env.sizes is not None else int(env.cfg.n_per_env), env.K,
                             env.features, seed=int(env.cfg.seed), weights=env.weights, device=env.device,
-                            stream=env.stream, **env.overrides)
+                            stream=env.stream, scenarios=env.scenarios, **env.overrides)
         stream = twin.stream
         classes = sorted({int(2 ** np.ceil(np.log2(n))) if n > 1 else 1 for n in
                           (np.asarray(twin.sizes) if twin.sizes is not None else [int(twin.cfg.n_per_env)])})

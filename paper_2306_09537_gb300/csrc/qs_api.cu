@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <string>
@@ -119,6 +120,16 @@ void build_consts(qs_env* h) {
     c.dw_h = p.dw_height;
     c.dw_sa = p.dw_sigma_a;
     c.dw_sw = p.dw_sigma_w;
+    c.scn_mask = f.scenarios & ((1u << QS_NSCN_TYPES) - 1u);
+    c.form_s = p.form_spacing;
+    c.form_rmax = p.form_rmax;
+    c.scn_m = p.scn_margin;
+    c.se_min = p.se_min;
+    c.se_period = p.se_period;
+    c.liss_f = p.liss_f;
+    c.bez_seg = (int)p.bez_seg;
+    // golden angle (3 - sqrt 5) / 2 turns as a 32-bit fixed-point fraction
+    c.golden_q32 = (uint32_t)std::floor(4294967296.0 * (3.0 - std::sqrt(5.0)) / 2.0);
     const float nom[QS_PARAM_DIM] = {p.mass, p.ixx, p.iyy, p.izz, p.t2w, p.tau_m, p.arm};
     for (int k = 0; k < QS_PARAM_DIM; ++k) c.nominal[k] = nom[k];
     for (int k = 0; k < QS_NW; ++k) c.w[k] = p.w[k];
@@ -203,7 +214,7 @@ qs_status upload_tiles(qs_env* h) {
     h->n_rtiles = (int)n1;
     h->d_dtiles = h->d_tiles + n0 + n1;
     h->n_dtiles = (int)dtiles.size();
-    h->rollout_grid = rollout_grid(h->rollout_block);
+    h->rollout_grid = rollout_grid(h->rollout_block, (h->c.scn_mask & ~1u) != 0);
     return QS_OK;
 }
 
@@ -278,6 +289,14 @@ void qs_config_default(qs_config* cfg) {
     p.dw_height = 0.5f;
     p.dw_sigma_a = 0.1f;
     p.dw_sigma_w = 1.0f;
+    cfg->scenarios = 0;
+    p.form_spacing = 0.5f;
+    p.form_rmax = 4.0f;
+    p.scn_margin = 1.5f;
+    p.se_min = 0.5f;
+    p.se_period = 400.0f;
+    p.liss_f = 0.1f;
+    p.bez_seg = 300.0f;
     p.w[QS_W_POS] = -1.0f;
     p.w[QS_W_SPIN] = -0.1f;
     p.w[QS_W_HIT_FLOOR] = -1.0f;
@@ -298,6 +317,11 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
     if (!(cfg->dt > 0.0f)) return fail(nullptr, QS_ERR_ARG, "qs_create: dt must be > 0");
     if (cfg->episode_steps < 1) return fail(nullptr, QS_ERR_ARG, "qs_create: episode_steps must be >= 1");
     const qs_params& pp = cfg->params;
+    if (cfg->scenarios >> QS_NSCN_TYPES) return fail(nullptr, QS_ERR_ARG, "qs_create: unknown scenario bits");
+    if ((cfg->scenarios & ~1u) &&
+        !(pp.form_spacing > 0.0f && pp.form_rmax > 0.0f && pp.se_period > 0.0f && pp.bez_seg >= 1.0f &&
+          pp.scn_margin >= 0.0f && pp.liss_f >= 0.0f))
+        return fail(nullptr, QS_ERR_ARG, "qs_create: scenario constants out of range");
     if (!(pp.mass > 0 && pp.arm > 0 && pp.ixx > 0 && pp.iyy > 0 && pp.izz > 0 && pp.t2w > 0 && pp.tau_m > 0 &&
           pp.dr_lo > 0 && pp.dr_hi >= pp.dr_lo && pp.omega_max > 0 && pp.prox_factor > 0))
         return fail(nullptr, QS_ERR_ARG, "qs_create: physical parameters must be positive");
@@ -364,7 +388,8 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
                  o_tick = take(sizeof(uint32_t) * E), o_off = take(sizeof(int32_t) * (E + 1)),
                  o_of = take(sizeof(int32_t) * D), o_ev = take(sizeof(uint32_t) * D),
                  o_knn = take(rec ? sizeof(int16_t) * h->K * D : 0), o_status = take(sizeof(int32_t)),
-                 o_perm = take(sizeof(int) * E), o_cnt = take(sizeof(int));
+                 o_perm = take(sizeof(int) * E), o_cnt = take(sizeof(int)),
+                 o_scn = take(sizeof(float) * 2 * QS_NSCN * E), o_sel = take(E);
     cudaError_t ce = cudaMalloc(&h->arena, off);
     if (ce != cudaSuccess) {
         delete h;
@@ -381,6 +406,8 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
     h->dv.ev = (uint32_t*)(base + o_ev);
     h->dv.knn = rec ? (int16_t*)(base + o_knn) : nullptr;
     h->dv.status = (int32_t*)(base + o_status);
+    h->dv.scn = (float*)(base + o_scn);
+    h->dv.scn_sel = (uint8_t*)(base + o_sel);
     h->dv.D = h->D;
     h->dv.E = h->E;
     h->d_perm = (int*)(base + o_perm);
@@ -561,6 +588,8 @@ static qs_status diff_check(qs_env* h, const char* who, int32_t T, int32_t C) {
         return fail(h, QS_ERR_ARG, std::string(who) + ": the handle must be created with QS_F_SMOOTH");
     if (h->cfg.flags & QS_F_DOWNWASH)
         return fail(h, QS_ERR_UNSUPPORTED, std::string(who) + ": the differentiable rollout has no downwash term");
+    if (h->c.scn_mask & ~1u)
+        return fail(h, QS_ERR_UNSUPPORTED, std::string(who) + ": the differentiable rollout uses the single goal only");
     if (T < 1 || C < 1) return fail(h, QS_ERR_ARG, std::string(who) + ": T and ckpt_every must be >= 1");
     return QS_OK;
 }
@@ -698,6 +727,30 @@ qs_status qs_get_events(qs_env* h, uint32_t* events_dev, int16_t* knn_dev) {
     DeviceGuard g(h->device);
     cudaError_t e = launch_get_events(h->dv, h->K, events_dev, knn_dev, h->stream);
     return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_get_events");
+}
+
+qs_status qs_get_scenario(qs_env* h, float* records_dev) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_get_scenario: NULL handle");
+    if (!records_dev) return fail(h, QS_ERR_ARG, "qs_get_scenario: records_dev is NULL");
+    DeviceGuard g(h->device);
+    cudaError_t e = launch_scenario_io(h->dv, records_dev, nullptr, h->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_get_scenario");
+}
+
+qs_status qs_set_scenario(qs_env* h, const float* records_dev) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_set_scenario: NULL handle");
+    if (!records_dev) return fail(h, QS_ERR_ARG, "qs_set_scenario: records_dev is NULL");
+    DeviceGuard g(h->device);
+    cudaError_t e = launch_scenario_io(h->dv, nullptr, records_dev, h->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_set_scenario");
+}
+
+qs_status qs_get_goals(qs_env* h, float* goals_dev) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_get_goals: NULL handle");
+    if (!goals_dev) return fail(h, QS_ERR_ARG, "qs_get_goals: goals_dev is NULL");
+    DeviceGuard g(h->device);
+    cudaError_t e = launch_goals(h->c, h->dv, goals_dev, h->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_get_goals");
 }
 
 qs_status qs_sync(qs_env* h) {

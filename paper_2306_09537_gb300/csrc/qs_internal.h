@@ -19,7 +19,8 @@ enum PrmIdx {
 // Philox stream tags (counter word 2 = tag << 16 | substream << 8 | block).
 enum Tag : uint32_t {
     TAG_RESET_ENV = 1, TAG_RESET_DRONE = 2, TAG_MOTOR = 3, TAG_OBS = 4, TAG_COLL = 5, TAG_WALL = 6,
-    TAG_AUTO_ENV = 7, TAG_AUTO_DRONE = 8, TAG_DOWNWASH = 9
+    TAG_AUTO_ENV = 7, TAG_AUTO_DRONE = 8, TAG_DOWNWASH = 9, TAG_SCN = 10, TAG_AUTO_SCN = 11, TAG_WAYPOINT = 12,
+    TAG_SWAP = 13
 };
 
 // Number of float4 planes of the drone state: the 30 public floats fill
@@ -35,6 +36,13 @@ struct Consts {
     float room_hx, room_hy, room_h;
     float beta, kc, omega_max, ans_frac, prox_factor, dr_lo, dr_hi;
     float dw_k1, dw_k2, dw_b1, dw_h, dw_sa, dw_sw;  // downwash
+    // scenarios: enabled mask, goal spacing, circle radius cap, clearance,
+    // shrink/expand minimum and period, Lissajous base frequency, Bezier
+    // segment steps, golden angle as a 32-bit turn fraction
+    uint32_t scn_mask;
+    float form_s, form_rmax, scn_m, se_min, se_period, liss_f;
+    int bez_seg;
+    uint32_t golden_q32;
     float nominal[QS_PARAM_DIM];
     float w[QS_NW];
     uint32_t flags, key0, key1;
@@ -65,6 +73,8 @@ struct Dev {
     uint32_t* ev;            // [D] event bits of the last step
     int16_t* knn;            // [K][D] neighbour local indices (QS_F_RECORD_KNN)
     int32_t* status;         // device error word (bit 0: non-finite state)
+    float* scn;              // [2][QS_NSCN][E] scenario records, double-buffered (null: single goal only)
+    uint8_t* scn_sel;        // [E] active buffer of each env's record
     int D, E;
 };
 
@@ -109,8 +119,9 @@ cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, con
 // steps t0 .. t0+nsteps-1 of the io buffers. grid <= 0: one CTA per tile.
 cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int block, const int* perm,
                            int* counter, const RolloutIO& io, int t0, int nsteps, int grid, cudaStream_t s);
-// CTAs of `block` threads the device keeps resident at once for k_rollout.
-int rollout_grid(int block);
+// CTAs of `block` threads the device keeps resident at once for k_rollout
+// (the instance with or without the scenario goals).
+int rollout_grid(int block, bool scenarios);
 
 // differentiable rollout (qs_adjoint.cu)
 size_t diff_workspace_bytes(int D, int T, int C, int substeps);
@@ -126,5 +137,7 @@ cudaError_t launch_get_state(const Dev& dv, float* state, float* params, float* 
 cudaError_t launch_set_state(const Consts& c, const Dev& dv, const float* state, const float* params,
                              const float* goals, const int32_t* ep, const uint32_t* tick, cudaStream_t s);
 cudaError_t launch_get_events(const Dev& dv, int K, uint32_t* events, int16_t* knn, cudaStream_t s);
+cudaError_t launch_scenario_io(const Dev& dv, float* out, const float* in, cudaStream_t s);
+cudaError_t launch_goals(const Consts& c, const Dev& dv, float* goals, cudaStream_t s);
 
 }  // namespace qsk

@@ -5,6 +5,7 @@
 
 #include "qs_device.cuh"
 #include "qs_internal.h"
+#include "qs_scenario.cuh"
 
 namespace qsk {
 
@@ -21,6 +22,10 @@ __global__ void k_reset_env(const Consts c, const Dev dv, uint32_t k0, uint32_t 
     dv.goal[e] = goal[0];
     dv.goal[dv.E + e] = goal[1];
     dv.goal[2 * dv.E + e] = goal[2];
+    float rec[QS_NSCN];
+    draw_scenario(c, k0, k1, tick, TAG_SCN, e, rec);
+    store_scenario(dv, 0, e, rec);
+    dv.scn_sel[e] = 0;
     dv.ep[e] = 0;
     if (!mask) dv.tick[e] = 0;
 }
@@ -101,6 +106,58 @@ cudaError_t launch_set_state(const Consts& c, const Dev& dv, const float* state,
                              const int32_t* ep, const uint32_t* tick, cudaStream_t st) {
     if (state) k_set_drones<<<(dv.D + 127) / 128, 128, 0, st>>>(dv, state);
     if (params || goals || ep || tick) k_set_envs<<<(dv.E + 127) / 128, 128, 0, st>>>(c, dv, params, goals, ep, tick);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- scenarios
+// Copies the active scenario records out to [E][QS_NSCN] (out != null) or in
+// from it.
+__global__ void k_scenario_io(const Dev dv, float* __restrict__ out, const float* __restrict__ in) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= dv.E) return;
+    float* base = dv.scn + (size_t)dv.scn_sel[e] * QS_NSCN * dv.E + e;
+    for (int k = 0; k < QS_NSCN; ++k) {
+        if (out)
+            out[(size_t)e * QS_NSCN + k] = base[(size_t)k * dv.E];
+        else
+            base[(size_t)k * dv.E] = in[(size_t)e * QS_NSCN + k];
+    }
+}
+
+cudaError_t launch_scenario_io(const Dev& dv, float* out, const float* in, cudaStream_t st) {
+    k_scenario_io<<<(dv.E + 127) / 128, 128, 0, st>>>(dv, out, in);
+    return cudaGetLastError();
+}
+
+// Goal [3] of every drone at its env's current control step; a swap slot is
+// the rank of the drone's key among its env's keys (recomputed per drone:
+// this kernel serves inspection, not the step).
+__global__ void k_goals(const Consts c, const Dev dv, float* __restrict__ goals) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= dv.D) return;
+    const int e = dv.env_of[d], d0 = dv.env_off[e], N = dv.env_off[e + 1] - d0, i = d - d0;
+    const int tau = dv.ep[e], sel = dv.scn_sel[e];
+    const float genv[3] = {dv.goal[e], dv.goal[dv.E + e], dv.goal[2 * dv.E + e]};
+    float g[3] = {genv[0], genv[1], genv[2]};
+    if (c.scn_mask & ~1u) {
+        int slot = i;
+        if (swap_active(dv, sel, e, tau)) {
+            const uint32_t seed = scn_seed(dv, sel, e), ki = swap_key(c, seed, i);
+            slot = 0;
+            for (int j = 0; j < N; ++j) {
+                const uint32_t kj = swap_key(c, seed, j);
+                slot += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+            }
+        }
+        scenario_goal(c, dv, sel, e, i, N, tau, slot, genv, g);
+    }
+    goals[(size_t)d * 3 + 0] = g[0];
+    goals[(size_t)d * 3 + 1] = g[1];
+    goals[(size_t)d * 3 + 2] = g[2];
+}
+
+cudaError_t launch_goals(const Consts& c, const Dev& dv, float* goals, cudaStream_t st) {
+    k_goals<<<(dv.D + 127) / 128, 128, 0, st>>>(c, dv, goals);
     return cudaGetLastError();
 }
 

@@ -19,10 +19,14 @@
 
 #include "qs_device.cuh"
 #include "qs_internal.h"
+#include "qs_scenario.cuh"
 
 namespace qsk {
 
 constexpr int MAX_BLOCK = 256;
+// dynamic shared memory of the step and rollout kernels, per thread: staged
+// position (3) and velocity (3) of the pair pass, swap key (1)
+constexpr int SMEM_PLANES = 7;
 
 // Per-env values a thread keeps in registers.
 struct EnvRegs {
@@ -30,20 +34,24 @@ struct EnvRegs {
     float g0, g1, g2;
     int ep;
     uint32_t tick;
+    int sel;       // active buffer of the env's scenario record
     bool redrawn;  // auto-reset drew new parameters / goal this launch
 };
 
-__device__ __forceinline__ void load_env(EnvRegs& er, const Dev& dv, int e) {
+template <bool SCN>
+__device__ __forceinline__ void load_env(EnvRegs& er, const Consts& c, const Dev& dv, int e) {
     er.p = load_prm(dv.prm, dv.E, e);
     er.g0 = dv.goal[e];
     er.g1 = dv.goal[dv.E + e];
     er.g2 = dv.goal[2 * dv.E + e];
     er.ep = dv.ep[e];
     er.tick = dv.tick[e];
+    er.sel = (SCN && (c.scn_mask & ~1u)) ? dv.scn_sel[e] : 0;
     er.redrawn = false;
 }
 
 // Written by lane 0 of the slot at the end of a launch.
+template <bool SCN>
 __device__ __forceinline__ void store_env(const EnvRegs& er, const Dev& dv, int e) {
     dv.ep[e] = er.ep;
     dv.tick[e] = er.tick;
@@ -55,7 +63,20 @@ __device__ __forceinline__ void store_env(const EnvRegs& er, const Dev& dv, int 
         dv.goal[e] = er.g0;
         dv.goal[dv.E + e] = er.g1;
         dv.goal[2 * dv.E + e] = er.g2;
+        if (SCN) dv.scn_sel[e] = (uint8_t)er.sel;
     }
+}
+
+// Goal slot of drone `lane` under an active swap: the rank of its key among
+// the keys staged by its env's drones at skey[sbase .. sbase + N) (ties to
+// the lower index).
+__device__ __forceinline__ int swap_rank(const uint32_t* skey, int sbase, int N, int lane, uint32_t myk) {
+    int slot = 0;
+    for (int j = 0; j < N; ++j) {
+        const uint32_t kj = skey[sbase + j];
+        slot += (kj < myk || (kj == myk && j < lane)) ? 1 : 0;
+    }
+    return slot;
 }
 
 // Inserts cand into the ascending list best[0..K).
@@ -146,9 +167,9 @@ __device__ __forceinline__ void apply_response(const Consts& c, Drone& s, uint32
 
 // S13 reward of one drone (Sec. III-E): weighted state terms, event indicators
 // and the proximity term over its neighbours (keys = squared distances).
-__device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s, const EnvRegs& er, const float fh[4],
-                                                uint32_t ev, const uint64_t best[QS_MAX_K], int keff) {
-    const float dgx = s.x[0] - er.g0, dgy = s.x[1] - er.g1, dgz = s.x[2] - er.g2;
+__device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s, const EnvRegs& er, const float g[3],
+                                                const float fh[4], uint32_t ev, const uint64_t best[QS_MAX_K], int keff) {
+    const float dgx = s.x[0] - g[0], dgy = s.x[1] - g[1], dgz = s.x[2] - g[2];
     float r = c.w[QS_W_POS] * sqrtf(dgx * dgx + dgy * dgy + dgz * dgz);
     r += c.w[QS_W_VEL] * sqrtf(s.v[0] * s.v[0] + s.v[1] * s.v[1] + s.v[2] * s.v[2]);
     r += c.w[QS_W_ORI] * s.R[8];
@@ -180,6 +201,7 @@ __device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s,
 
 // End of a control step: previous command, episode counter, done flag,
 // Philox counter, in-place auto-reset, non-finite check.
+template <bool SCN>
 __device__ __forceinline__ void end_step(const Consts& c, const Dev& dv, Drone& s, EnvRegs& er, const float fh[4],
                                          int lane, int e, int d, uint8_t* __restrict__ done) {
     s.fp[0] = fh[0];
@@ -204,6 +226,16 @@ __device__ __forceinline__ void end_step(const Consts& c, const Dev& dv, Drone& 
         er.g2 = goal[2];
         er.redrawn = true;
         draw_drone(c, c.key0, c.key1, tick, TAG_AUTO_DRONE, d, p7[P_T2W], s);
+        if (SCN && (c.scn_mask & ~1u)) {
+            // the next episode's record goes to the other buffer: lanes of
+            // this env may still be reading the current one for this step
+            er.sel ^= 1;
+            if (lane == 0) {
+                float rec[QS_NSCN];
+                draw_scenario(c, c.key0, c.key1, tick, TAG_AUTO_SCN, e, rec);
+                store_scenario(dv, er.sel, e, rec);
+            }
+        }
     }
     if (!finite_state(s)) atomicOr(dv.status, 1);
 }
@@ -212,6 +244,7 @@ __device__ __forceinline__ void end_step(const Consts& c, const Dev& dv, Drone& 
 // pair pass synchronises the CTA); `act` marks threads that carry a drone.
 // Outputs for this step: obs/rew rows of drone d, done[e] (lane 0). W is
 // uniform over the CTA; a compile-time W folds away after inlining.
+template <bool SCN>
 __device__ __forceinline__ void step_body(const int W, const Consts& c, const Dev& dv, Drone& s, EnvRegs& er, uint32_t& ev_out,
                                           float* sx, float* sv, const bool act, const int lane, const int N,
                                           const int sbase, const int e, const int d, const float* __restrict__ act_in,
@@ -221,6 +254,11 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
     const int K = c.K;
     const int keff = min(K, N - 1);
     const uint32_t tick = er.tick;
+    const bool scn = SCN && (c.scn_mask & ~1u) != 0;  // the SCN = false instance carries no scenario code
+    const int tau = observe_only ? er.ep : er.ep + 1;  // the goal is the one at the step's end
+    uint32_t* skey = reinterpret_cast<uint32_t*>(sv + 3 * nt);
+    bool swp = false;
+    uint32_t myk = 0;
     float fh[4] = {0.f, 0.f, 0.f, 0.f};
     uint32_t ev = 0;
     if (act && !observe_only) {
@@ -264,18 +302,30 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
             sv[threadIdx.x] = s.v[0];
             sv[nt + threadIdx.x] = s.v[1];
             sv[2 * nt + threadIdx.x] = s.v[2];
+            if (scn && swap_active(dv, er.sel, e, tau)) {
+                swp = true;
+                myk = swap_key(c, scn_seed(dv, er.sel, e), lane);
+                skey[threadIdx.x] = myk;
+            }
         }
         __syncthreads();
     }
     if (!act) return;
+
+    // ---- the drone's goal at the end of the step (Sec. III-D scenarios)
+    float gl[3] = {er.g0, er.g1, er.g2};
+    if (scn) {
+        const int slot = swp ? swap_rank(skey, sbase, N, lane, myk) : lane;
+        scenario_goal(c, dv, er.sel, e, lane, N, tau, slot, gl, gl);
+    }
 
     // ---- S12 observation
     if (obs) {
         float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
         if (c.flags & QS_F_OBS_NOISE) obs_noise(c, tick, d, observe_only ? 1u : 0u, ex, evv, ew);
         float2* o2 = reinterpret_cast<float2*>(obs + (size_t)d * c.obs_dim);
-        o2[0] = make_float2(s.x[0] - er.g0 + ex[0], s.x[1] - er.g1 + ex[1]);
-        o2[1] = make_float2(s.x[2] - er.g2 + ex[2], s.v[0] + evv[0]);
+        o2[0] = make_float2(s.x[0] - gl[0] + ex[0], s.x[1] - gl[1] + ex[1]);
+        o2[1] = make_float2(s.x[2] - gl[2] + ex[2], s.v[0] + evv[0]);
         o2[2] = make_float2(s.v[1] + evv[1], s.v[2] + evv[2]);
         o2[3] = make_float2(s.R[0], s.R[1]);
         o2[4] = make_float2(s.R[2], s.R[3]);
@@ -309,8 +359,8 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
     ev_out = ev;
 
     // ---- S13 reward and done
-    if (rew) rew[d] = compute_reward(c, s, er, fh, ev, best, W > 1 ? keff : 0);
-    end_step(c, dv, s, er, fh, lane, e, d, done);
+    if (rew) rew[d] = compute_reward(c, s, er, gl, fh, ev, best, W > 1 ? keff : 0);
+    end_step<SCN>(c, dv, s, er, fh, lane, e, d, done);
 }
 
 struct SlotMap {
@@ -332,7 +382,7 @@ __device__ __forceinline__ SlotMap map_slot(const Dev& dv, const Tile& tile, con
     return m;
 }
 
-template <int W>
+template <int W, bool SCN>
 __global__ void __launch_bounds__(MAX_BLOCK) k_step(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                     const int* __restrict__ perm, const StepIO io, const int observe_only) {
     extern __shared__ float sm[];
@@ -342,17 +392,18 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_step(const Consts c, const Dev dv
     uint32_t ev = 0;
     if (m.act) {
         load_drone(s, dv.st, dv.D, m.d);
-        load_env(er, dv, m.e);
+        load_env<SCN>(er, c, dv, m.e);
     }
-    step_body(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d, io.act, io.obs,
+    step_body<SCN>(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d, io.act, io.obs,
               io.rew, io.done, observe_only);
     if (!m.act || observe_only) return;
     dv.ev[m.d] = ev;
     store_drone(s, dv.st, dv.D, m.d);
-    if (m.lane == 0) store_env(er, dv, m.e);
+    if (m.lane == 0) store_env<SCN>(er, dv, m.e);
 }
 
 // T steps of one tile with the state in registers.
+template <bool SCN>
 __device__ __forceinline__ void rollout_tile(const Consts& c, const Dev& dv, const Tile& tile, const int* __restrict__ perm,
                                              float* sm, const RolloutIO& io, int t0, int nsteps) {
     const int W = tile.W;
@@ -362,23 +413,24 @@ __device__ __forceinline__ void rollout_tile(const Consts& c, const Dev& dv, con
     uint32_t ev = 0;
     if (m.act) {
         load_drone(s, dv.st, dv.D, m.d);
-        load_env(er, dv, m.e);
+        load_env<SCN>(er, c, dv, m.e);
     }
     const size_t D = dv.D, E = dv.E;
     for (int t = t0; t < t0 + nsteps; ++t) {
-        step_body(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d,
+        step_body<SCN>(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d,
                   io.act + (size_t)t * D * 4, io.obs ? io.obs + (size_t)t * D * c.obs_dim : nullptr,
                   io.rew ? io.rew + (size_t)t * D : nullptr, io.done ? io.done + (size_t)t * E : nullptr, 0);
     }
     if (m.act) {
         dv.ev[m.d] = ev;
         store_drone(s, dv.st, dv.D, m.d);
-        if (m.lane == 0) store_env(er, dv, m.e);
+        if (m.lane == 0) store_env<SCN>(er, dv, m.e);
     }
 }
 
 // Persistent rollout: CTAs take tiles from *counter (zeroed before the launch)
 // until none is left. Tiles are ordered costliest first.
+template <bool SCN>
 __global__ void __launch_bounds__(MAX_BLOCK) k_rollout(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                        const int n_tiles, const int* __restrict__ perm,
                                                        int* __restrict__ counter, const RolloutIO io, const int t0,
@@ -391,7 +443,7 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_rollout(const Consts c, const Dev
         const int ti = s_next;
         __syncthreads();  // everyone has read s_next before thread 0 overwrites it
         if (ti >= n_tiles) return;
-        rollout_tile(c, dv, tiles[ti], perm, sm, io, t0, nsteps);
+        rollout_tile<SCN>(c, dv, tiles[ti], perm, sm, io, t0, nsteps);
     }
 }
 
@@ -414,7 +466,8 @@ struct WsShared {
     float st[18][32];          // x v R w of each lane after the step (post-collision)
     float sx[3][32];           // pair-pass staging: positions
     float sv[3][32];           //                    velocities
-    float g[3][32];            // goal of each lane's env
+    float g[3][32];            // goal of each lane's drone
+    uint32_t key[32];          // swap keys
     int nb[QS_MAX_K][32];      // CTA lane of each neighbour
     int keff[32];
     float rows[32 * WS_OBS_MAX];
@@ -515,7 +568,7 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
     uint32_t ev = 0;
     if (act) {
         load_drone(s, dv.st, dv.D, d);
-        load_env(er, dv, e);
+        load_env<true>(er, c, dv, e);
         const float4 a = __ldg(reinterpret_cast<const float4*>(io.act) + d);
         fh[0] = command(c, a.x);
         fh[1] = command(c, a.y);
@@ -564,14 +617,33 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
         if (responded) apply_response(c, s, er.tick, d, dvs);
         if (dw_hit) apply_downwash(c, s, er.tick, d, dw_az);
     }
+    // the drone's goal at the end of the step (Sec. III-D scenarios)
+    float gl[3] = {er.g0, er.g1, er.g2};
+    if (c.scn_mask & ~1u) {
+        const int tau = er.ep + 1;
+        bool swp = false;
+        uint32_t myk = 0;
+        if (W > 1) {
+            if (act && swap_active(dv, er.sel, e, tau)) {
+                swp = true;
+                myk = swap_key(c, scn_seed(dv, er.sel, e), lane);
+                sh.key[l] = myk;
+            }
+            __syncwarp();
+        }
+        if (act) {
+            const int slot = swp ? swap_rank(sh.key, sbase, N, lane, myk) : lane;
+            scenario_goal(c, dv, er.sel, e, lane, N, tau, slot, gl, gl);
+        }
+    }
     if (act) {  // publish the observed state (post-collision) for the noise warp
         const float v18[18] = {s.x[0], s.x[1], s.x[2], s.v[0], s.v[1], s.v[2], s.R[0], s.R[1], s.R[2],
                                s.R[3], s.R[4], s.R[5], s.R[6], s.R[7], s.R[8], s.w[0], s.w[1], s.w[2]};
 #pragma unroll
         for (int k = 0; k < 18; ++k) sh.st[k][l] = v18[k];
-        sh.g[0][l] = er.g0;
-        sh.g[1][l] = er.g1;
-        sh.g[2][l] = er.g2;
+        sh.g[0][l] = gl[0];
+        sh.g[1][l] = gl[1];
+        sh.g[2][l] = gl[2];
         sh.keff[l] = W > 1 ? keff : 0;
 #pragma unroll
         for (int k = 0; k < QS_MAX_K; ++k)
@@ -584,11 +656,28 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
         for (int k = 0; k < QS_MAX_K; ++k)
             if (k < K) dv.knn[(size_t)k * dv.D + d] = (W > 1 && k < keff) ? (int16_t)(best[k] & 0xffffu) : (int16_t)-1;
     }
-    if (io.rew) io.rew[d] = compute_reward(c, s, er, fh, ev, best, W > 1 ? keff : 0);
-    end_step(c, dv, s, er, fh, lane, e, d, io.done);
+    if (io.rew) io.rew[d] = compute_reward(c, s, er, gl, fh, ev, best, W > 1 ? keff : 0);
+    end_step<true>(c, dv, s, er, fh, lane, e, d, io.done);
     dv.ev[d] = ev;
     store_drone(s, dv.st, dv.D, d);
-    if (lane == 0) store_env(er, dv, e);
+    if (lane == 0) store_env<true>(er, dv, e);
+}
+
+template <bool SCN>
+cudaError_t launch_k_step(const Consts& c, const Dev& dv, const ClassPlan& cp, const Tile* t, const int* perm,
+                          const StepIO& io, int observe_only, size_t smem, cudaStream_t st) {
+    switch (cp.W) {
+        case 1: k_step<1, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 2: k_step<2, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 4: k_step<4, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 8: k_step<8, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 16: k_step<16, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 32: k_step<32, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 64: k_step<64, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 128: k_step<128, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, const Tile* tiles, const int* perm,
@@ -598,27 +687,20 @@ cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, con
         k_step_ws<<<cp.n_tiles, 64, 0, st>>>(c, dv, tiles + cp.tile_off, perm, io);
         return cudaGetLastError();
     }
-    const size_t smem = (cp.W > 1) ? sizeof(float) * 6 * cp.block : 0;
+    const size_t smem = (cp.W > 1) ? sizeof(float) * SMEM_PLANES * cp.block : 0;
     const Tile* t = tiles + cp.tile_off;
-    switch (cp.W) {
-        case 1: k_step<1><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 2: k_step<2><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 4: k_step<4><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 8: k_step<8><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 16: k_step<16><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 32: k_step<32><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 64: k_step<64><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 128: k_step<128><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    return (c.scn_mask & ~1u) ? launch_k_step<true>(c, dv, cp, t, perm, io, observe_only, smem, st)
+                              : launch_k_step<false>(c, dv, cp, t, perm, io, observe_only, smem, st);
 }
 
-int rollout_grid(int block) {
+int rollout_grid(int block, bool scn) {
     int dev = 0, n_sm = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rollout, block, sizeof(float) * 6 * block);
+    if (scn)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rollout<true>, block, sizeof(float) * SMEM_PLANES * block);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rollout<false>, block, sizeof(float) * SMEM_PLANES * block);
     return (occ > 0 ? occ : 1) * n_sm;
 }
 
@@ -626,9 +708,13 @@ cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, in
                            int* counter, const RolloutIO& io, int t0, int nsteps, int grid, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(float) * 6 * block;
+    const size_t smem = sizeof(float) * SMEM_PLANES * block;
     const int g = grid > 0 ? grid : n_tiles;
-    k_rollout<<<g < n_tiles ? g : n_tiles, block, smem, st>>>(c, dv, tiles, n_tiles, perm, counter, io, t0, nsteps);
+    const int grid_n = g < n_tiles ? g : n_tiles;
+    if (c.scn_mask & ~1u)
+        k_rollout<true><<<grid_n, block, smem, st>>>(c, dv, tiles, n_tiles, perm, counter, io, t0, nsteps);
+    else
+        k_rollout<false><<<grid_n, block, smem, st>>>(c, dv, tiles, n_tiles, perm, counter, io, t0, nsteps);
     return cudaGetLastError();
 }
 

@@ -14,7 +14,7 @@ class QuadSwarmEnv:
     step of all of them, computed by libquadswarm_gpu.so on the current device."""
 
     def __init__(self, n_envs: int, swarm=1, k_neighbors: int = 0, features=(), seed: int = 1, weights=None,
-                 device="cuda", stream=None, **overrides):
+                 device="cuda", stream=None, scenarios=(), **overrides):
         self.device = torch.device(device)
         if self.device.type != "cuda":
             raise ValueError("QuadSwarmEnv runs on a CUDA device only")
@@ -24,7 +24,9 @@ class QuadSwarmEnv:
             sizes = np.ascontiguousarray(swarm, dtype=np.int32)
             swarm = 1
         self.sizes, self.features, self.weights, self.overrides = sizes, tuple(features), weights, dict(overrides)
-        self.cfg = qs.make_config(n_envs, swarm, k_neighbors, features, seed, weights, **overrides)
+        self.scenarios = tuple(scenarios)
+        self.cfg = qs.make_config(n_envs, swarm, k_neighbors, features, seed, weights, scenarios=scenarios,
+                                  **overrides)
         with torch.cuda.device(self.device):
             self.h = qs.qs_create(self.cfg, self.stream.cuda_stream, swarm_sizes=sizes)
         self.D, self.E, self.obs_dim = qs.qs_get_dims(self.h)
@@ -76,6 +78,21 @@ class QuadSwarmEnv:
         nb = torch.empty(self.D, max(self.K, 1), dtype=torch.int16, device=self.device) if knn else None
         qs.qs_get_events(self.h, ev, nb)
         return ev, (nb[:, :self.K] if nb is not None else None)
+
+    def get_scenario(self) -> torch.Tensor:
+        """Scenario records [E][QS_NSCN] (Sec. III-D)."""
+        out = torch.empty(self.E, qs.QS_NSCN, device=self.device)
+        qs.qs_get_scenario(self.h, out)
+        return out
+
+    def set_scenario(self, records: torch.Tensor):
+        qs.qs_set_scenario(self.h, records.contiguous())
+
+    def get_goals(self) -> torch.Tensor:
+        """Goal [D][3] of every drone at its env's current control step."""
+        out = torch.empty(self.D, 3, device=self.device)
+        qs.qs_get_goals(self.h, out)
+        return out
 
     def sync(self):
         qs.qs_sync(self.h)

@@ -32,7 +32,21 @@ W_NAMES = ["pos", "vel", "ori", "spin", "act", "dact", "rot", "yaw", "hit_floor"
 EXPORTS = ["qs_config_default", "qs_create", "qs_destroy", "qs_get_dims", "qs_reset", "qs_step", "qs_step_host",
            "qs_rollout", "qs_set_rollout_shape", "qs_get_rollout_shape", "qs_diff_workspace_size",
            "qs_diff_forward", "qs_diff_backward", "qs_diff_grad_static", "qs_get_state", "qs_set_state",
-           "qs_get_events", "qs_sync", "qs_set_block", "qs_get_block", "qs_last_error"]
+           "qs_get_events", "qs_get_scenario", "qs_set_scenario", "qs_get_goals", "qs_sync", "qs_set_block",
+           "qs_get_block", "qs_last_error"]
+# training scenarios (Sec. III-D) and goal formations, in the order of QS_SCN_* / QS_FORM_*
+SCENARIOS = ["single", "static", "dynamic", "swap", "shrink_expand", "swarm_vs_swarm", "pursuit_lissajous",
+             "pursuit_bezier"]
+FORMATIONS = ["circle", "grid", "sphere", "cylinder", "cube"]
+QS_NSCN = 18
+
+
+def scenario_mask(names) -> int:
+    """Bit mask (qs_config.scenarios) of the named scenarios."""
+    m = 0
+    for n in names:
+        m |= 1 << SCENARIOS.index(n)
+    return m
 QS_DIFF_STATIC_BYTES = 64 << 20
 
 
@@ -42,13 +56,15 @@ class qs_params(C.Structure):
         "alpha_nd", "alpha_ns_frac", "alpha_c", "coll_sigma_v", "coll_sigma_w",
         "obs_sigma_x", "obs_sigma_v", "obs_sigma_w", "room_hx", "room_hy", "room_h",
         "dr_lo", "dr_hi", "smooth_beta", "smooth_kc", "prox_factor", "omega_max",
-        "dw_k1", "dw_k2", "dw_b1", "dw_height", "dw_sigma_a", "dw_sigma_w")] + [("w", C.c_float * 14)]
+        "dw_k1", "dw_k2", "dw_b1", "dw_height", "dw_sigma_a", "dw_sigma_w",
+        "form_spacing", "form_rmax", "scn_margin", "se_min", "se_period", "liss_f", "bez_seg")] + [("w", C.c_float * 14)]
 
 
 class qs_config(C.Structure):
     _fields_ = [("size", C.c_uint32), ("n_envs", C.c_int32), ("swarm_sizes", C.POINTER(C.c_int32)),
                 ("n_per_env", C.c_int32), ("k_neighbors", C.c_int32), ("substeps", C.c_int32), ("dt", C.c_float),
-                ("episode_steps", C.c_int32), ("seed", C.c_uint64), ("flags", C.c_uint32), ("params", qs_params)]
+                ("episode_steps", C.c_int32), ("seed", C.c_uint64), ("flags", C.c_uint32), ("scenarios", C.c_uint32),
+                ("params", qs_params)]
 
 
 class QSError(RuntimeError):
@@ -86,6 +102,9 @@ def _load():
     L.qs_get_state.argtypes = [V, V, V, V, V, V]
     L.qs_set_state.argtypes = [V, V, V, V, V, V]
     L.qs_get_events.argtypes = [V, V, V]
+    L.qs_get_scenario.argtypes = [V, V]
+    L.qs_set_scenario.argtypes = [V, V]
+    L.qs_get_goals.argtypes = [V, V]
     L.qs_sync.argtypes = [V]
     L.qs_set_block.argtypes = [V, C.c_int32, C.c_int32]
     L.qs_get_block.argtypes = [V, C.c_int32, P(C.c_int32)]
@@ -221,6 +240,18 @@ def qs_get_events(h, events=None, knn=None):
     return _check(_L.qs_get_events(h, _p(events), _p(knn)), h)
 
 
+def qs_get_scenario(h, records):
+    return _check(_L.qs_get_scenario(h, _p(records)), h)
+
+
+def qs_set_scenario(h, records):
+    return _check(_L.qs_set_scenario(h, _p(records)), h)
+
+
+def qs_get_goals(h, goals):
+    return _check(_L.qs_get_goals(h, _p(goals)), h)
+
+
 def qs_sync(h):
     return _check(_L.qs_sync(h), h)
 
@@ -235,9 +266,11 @@ def qs_get_block(h, width: int) -> int:
     return b.value
 
 
-def make_config(n_envs=1, swarm=1, k_neighbors=0, features=(), seed=1, weights=None, **overrides) -> qs_config:
-    """qs_config from the library defaults, feature names and overrides."""
+def make_config(n_envs=1, swarm=1, k_neighbors=0, features=(), seed=1, weights=None, scenarios=(),
+                **overrides) -> qs_config:
+    """qs_config from the library defaults, feature names, scenario names and overrides."""
     cfg = qs_config_default()
+    cfg.scenarios = scenario_mask(scenarios)
     cfg.n_envs = int(n_envs)
     cfg.n_per_env = int(swarm) if swarm is not None else 1
     cfg.k_neighbors = int(k_neighbors)

@@ -14,16 +14,17 @@ ALL_WEIGHTS = {n: 0.1 * (i + 1) * (-1) ** i for i, n in enumerate(O.W_NAMES)}
 DEV = torch.device("cuda:0")
 
 
-def pair(sizes, K, features, seed=1, weights=None, **overrides):
+def pair(sizes, K, features, seed=1, weights=None, scenarios=(), **overrides):
     """(QuadSwarmEnv, Oracle) with the same configuration."""
     from paper_2306_09537_gb300.env import QuadSwarmEnv
     sizes = np.asarray(sizes, dtype=np.int32)
     E = len(sizes)
-    env = QuadSwarmEnv(E, sizes, K, features, seed=seed, weights=weights, device=DEV, **overrides)
+    env = QuadSwarmEnv(E, sizes, K, features, seed=seed, weights=weights, device=DEV, scenarios=scenarios,
+                       **overrides)
     flags = 0
     for f in features:
         flags |= OR_FLAGS[f]
-    oc = O.default_config(n_envs=E, k_neighbors=K, flags=flags, seed=seed)
+    oc = O.default_config(n_envs=E, k_neighbors=K, flags=flags, seed=seed, scenarios=O.scenario_mask(scenarios))
     if weights is not None:
         oc.w[:] = [0.0] * 14
         O.set_config(oc, weights=weights)

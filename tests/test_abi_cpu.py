@@ -45,13 +45,14 @@ def test_config_size_and_defaults_match_oracle(qs):
     for name in ("mass", "arm", "ixx", "iyy", "izz", "t2w", "kappa", "tau_m", "gravity", "mu", "alpha_nd",
                  "alpha_ns_frac", "alpha_c", "coll_sigma_v", "coll_sigma_w", "obs_sigma_x", "obs_sigma_v",
                  "obs_sigma_w", "room_hx", "room_hy", "room_h", "dr_lo", "dr_hi", "smooth_beta", "smooth_kc",
-                 "prox_factor", "omega_max", "dw_k1", "dw_k2", "dw_b1", "dw_height", "dw_sigma_a", "dw_sigma_w"):
+                 "prox_factor", "omega_max", "dw_k1", "dw_k2", "dw_b1", "dw_height", "dw_sigma_a", "dw_sigma_w",
+                 "form_spacing", "form_rmax", "scn_margin", "se_min", "se_period", "liss_f", "bez_seg"):
         assert getattr(p, name) == np.float32(getattr(oc, name)), name
     for i in range(14):
         assert p.w[i] == np.float32(oc.w[i])
     assert cfg.substeps == oc.substeps and math.isclose(cfg.dt, oc.dt, rel_tol=1e-7)
     assert cfg.episode_steps == oc.episode_steps and cfg.k_neighbors == oc.k_neighbors
-    assert cfg.flags == oc.flags
+    assert cfg.flags == oc.flags and cfg.scenarios == oc.scenarios == 0
 
 
 @pytest.mark.parametrize("field,value,status", [
