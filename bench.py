@@ -31,6 +31,12 @@ sys.path.insert(0, ROOT)
 from paper_2306_09537_gb300 import workloads as W  # noqa: E402
 
 METRIC = "quadrotor-steps/sec on 1 GB300 (plain vs batched vs fwd+adjoint), % of roofline"
+# DRAM bytes (read + write) of one k_step_ws<false> launch of the plain 8192 x 1 step,
+# from an ncu capture of this command's headline kernel (L2 flushed before the
+# launch; the outputs stay in L2 during the launch, so the write count is 0).
+# Valid while k_step_ws<false> is unchanged.
+K_STEP_WS_DRAM_BYTES = 2144768 + 0
+K_STEP_WS_DRAM_SOURCE = "profiles/k_step_ws_plain_8192x1.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
 UNIT = "quadrotor-steps/s"
 WL = W.PLAIN
 BENCH_FEATURES = WL.features + ("auto_reset",)
@@ -260,7 +266,8 @@ def run_gpu(args, world, rank, local):
     else:
         roof = {"bound": "alu", "achieved": ach_gops, "peak": alu_peak, "unit": "Gop/s", "frac": ach_gops / alu_peak,
                 "peak_source": "152 SMs x 128 FP32/INT32 lanes x max SM clock"}
-    roof.update({"kernel": "qsk::k_step_ws", "traffic": None, "algorithmic_bytes_per_launch": ab,
+    roof.update({"kernel": "qsk::k_step_ws<false>", "traffic": K_STEP_WS_DRAM_BYTES, "traffic_source": K_STEP_WS_DRAM_SOURCE,
+                 "algorithmic_bytes_per_launch": ab,
                  "algorithmic_ops_per_launch": ops,
                  "alt": {"hbm_frac": ach_gbs / hbm, "alu_frac": ach_gops / alu_peak}})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warm,
@@ -430,6 +437,21 @@ def run_forms(dev, stream, seed):
             env.close()
             del acts
         forms["plain_rollout_sweep"] = sweep
+
+        # env-count sweep of the per-call plain step (the headline form): from
+        # latency-bound at 8192 drones to HBM-bound once the state outgrows L2
+        sweep = []
+        for E in (8192, 65536, 262144, 1048576):
+            env = make(W.PLAIN, n_envs=E)
+            acts = torch.from_numpy(W.actions(seed, 8, env.D)).to(dev)
+            ms = per_call(env, acts, 20)
+            s = ms * 1e-3
+            ab = algorithmic_bytes(env.D, env.E, env.obs_dim)
+            sweep.append({"n_envs": E, "value": env.D / s, "ms_per_step": ms, "hbm_frac": ab / s / 1e9 / hbm,
+                          "alu_frac": OPS_PER_QUAD_STEP_N1 * env.D / s / alu_peak})
+            env.close()
+            del acts
+        forms["plain_call_sweep"] = sweep
     return forms
 
 

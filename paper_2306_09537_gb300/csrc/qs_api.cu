@@ -214,7 +214,7 @@ qs_status upload_tiles(qs_env* h) {
     h->n_rtiles = (int)n1;
     h->d_dtiles = h->d_tiles + n0 + n1;
     h->n_dtiles = (int)dtiles.size();
-    h->rollout_grid = rollout_grid(h->rollout_block, (h->c.scn_mask & ~1u) != 0);
+    h->rollout_grid = rollout_grid(h->rollout_block, (h->c.scn_mask & ~1u) != 0 || (h->c.flags & QS_F_DOWNWASH) != 0);
     return QS_OK;
 }
 

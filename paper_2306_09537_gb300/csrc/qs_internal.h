@@ -120,8 +120,8 @@ cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, con
 cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int block, const int* perm,
                            int* counter, const RolloutIO& io, int t0, int nsteps, int grid, cudaStream_t s);
 // CTAs of `block` threads the device keeps resident at once for k_rollout
-// (the instance with or without the scenario goals).
-int rollout_grid(int block, bool scenarios);
+// (the instance with or without scenarios and downwash).
+int rollout_grid(int block, bool extended);
 
 // differentiable rollout (qs_adjoint.cu)
 size_t diff_workspace_bytes(int D, int T, int C, int substeps);

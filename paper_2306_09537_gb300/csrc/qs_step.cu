@@ -28,6 +28,11 @@ constexpr int MAX_BLOCK = 256;
 // position (3) and velocity (3) of the pair pass, swap key (1)
 constexpr int SMEM_PLANES = 7;
 
+// The step kernels come in two instances: EXT = true carries the training
+// scenarios (per-drone goals) and the downwash term, EXT = false neither, so
+// the common configuration keeps the smaller code and register budget.
+inline bool extended(const Consts& c) { return (c.scn_mask & ~1u) != 0 || (c.flags & QS_F_DOWNWASH) != 0; }
+
 // Per-env values a thread keeps in registers.
 struct EnvRegs {
     Prm p;
@@ -38,7 +43,7 @@ struct EnvRegs {
     bool redrawn;  // auto-reset drew new parameters / goal this launch
 };
 
-template <bool SCN>
+template <bool EXT>
 __device__ __forceinline__ void load_env(EnvRegs& er, const Consts& c, const Dev& dv, int e) {
     er.p = load_prm(dv.prm, dv.E, e);
     er.g0 = dv.goal[e];
@@ -46,12 +51,12 @@ __device__ __forceinline__ void load_env(EnvRegs& er, const Consts& c, const Dev
     er.g2 = dv.goal[2 * dv.E + e];
     er.ep = dv.ep[e];
     er.tick = dv.tick[e];
-    er.sel = (SCN && (c.scn_mask & ~1u)) ? dv.scn_sel[e] : 0;
+    er.sel = (EXT && (c.scn_mask & ~1u)) ? dv.scn_sel[e] : 0;
     er.redrawn = false;
 }
 
 // Written by lane 0 of the slot at the end of a launch.
-template <bool SCN>
+template <bool EXT>
 __device__ __forceinline__ void store_env(const EnvRegs& er, const Dev& dv, int e) {
     dv.ep[e] = er.ep;
     dv.tick[e] = er.tick;
@@ -63,7 +68,7 @@ __device__ __forceinline__ void store_env(const EnvRegs& er, const Dev& dv, int 
         dv.goal[e] = er.g0;
         dv.goal[dv.E + e] = er.g1;
         dv.goal[2 * dv.E + e] = er.g2;
-        if (SCN) dv.scn_sel[e] = (uint8_t)er.sel;
+        if (EXT) dv.scn_sel[e] = (uint8_t)er.sel;
     }
 }
 
@@ -97,10 +102,9 @@ __device__ __forceinline__ void topk_insert(uint64_t best[QS_MAX_K], int K, uint
 // partners (S10), and the sorted neighbour list.
 __device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float thr, int lane, int N, int sbase,
                                           const float* sx, const float* sv, int nt, int keff, bool coll, bool flag_coll,
-                                          uint32_t& ev, uint64_t best[QS_MAX_K], float dvs[3], float& dw_az,
-                                          bool& dw_hit) {
+                                          uint32_t& ev, uint64_t best[QS_MAX_K], float dvs[3], const bool dw,
+                                          float& dw_az, bool& dw_hit) {
     bool responded = false;
-    const bool dw = (c.flags & QS_F_DOWNWASH) != 0;
     for (int j = 0; j < N; ++j) {
         if (j == lane) continue;
         const int tj = sbase + j;
@@ -201,7 +205,7 @@ __device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s,
 
 // End of a control step: previous command, episode counter, done flag,
 // Philox counter, in-place auto-reset, non-finite check.
-template <bool SCN>
+template <bool EXT>
 __device__ __forceinline__ void end_step(const Consts& c, const Dev& dv, Drone& s, EnvRegs& er, const float fh[4],
                                          int lane, int e, int d, uint8_t* __restrict__ done) {
     s.fp[0] = fh[0];
@@ -226,7 +230,7 @@ __device__ __forceinline__ void end_step(const Consts& c, const Dev& dv, Drone& 
         er.g2 = goal[2];
         er.redrawn = true;
         draw_drone(c, c.key0, c.key1, tick, TAG_AUTO_DRONE, d, p7[P_T2W], s);
-        if (SCN && (c.scn_mask & ~1u)) {
+        if (EXT && (c.scn_mask & ~1u)) {
             // the next episode's record goes to the other buffer: lanes of
             // this env may still be reading the current one for this step
             er.sel ^= 1;
@@ -244,17 +248,19 @@ __device__ __forceinline__ void end_step(const Consts& c, const Dev& dv, Drone& 
 // pair pass synchronises the CTA); `act` marks threads that carry a drone.
 // Outputs for this step: obs/rew rows of drone d, done[e] (lane 0). W is
 // uniform over the CTA; a compile-time W folds away after inlining.
-template <bool SCN>
+template <bool EXT>
 __device__ __forceinline__ void step_body(const int W, const Consts& c, const Dev& dv, Drone& s, EnvRegs& er, uint32_t& ev_out,
                                           float* sx, float* sv, const bool act, const int lane, const int N,
-                                          const int sbase, const int e, const int d, const float* __restrict__ act_in,
+                                          const int sbase, const int e, const int d, const float4 a,
                                           float* __restrict__ obs, float* __restrict__ rew, uint8_t* __restrict__ done,
                                           const int observe_only) {
     const int nt = blockDim.x;
     const int K = c.K;
     const int keff = min(K, N - 1);
     const uint32_t tick = er.tick;
-    const bool scn = SCN && (c.scn_mask & ~1u) != 0;  // the SCN = false instance carries no scenario code
+    // the EXT = false instance carries neither scenario nor downwash code
+    const bool scn = EXT && (c.scn_mask & ~1u) != 0;
+    const bool dw = EXT && (c.flags & QS_F_DOWNWASH) != 0;
     const int tau = observe_only ? er.ep : er.ep + 1;  // the goal is the one at the step's end
     uint32_t* skey = reinterpret_cast<uint32_t*>(sv + 3 * nt);
     bool swp = false;
@@ -262,7 +268,6 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
     float fh[4] = {0.f, 0.f, 0.f, 0.f};
     uint32_t ev = 0;
     if (act && !observe_only) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(act_in) + d);
         fh[0] = command(c, a.x);
         fh[1] = command(c, a.y);
         fh[2] = command(c, a.z);
@@ -293,10 +298,10 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
             const bool coll = (c.flags & QS_F_COLLISIONS) && !(c.flags & QS_F_SMOOTH) && !observe_only;
             const bool flag_coll = (c.flags & QS_F_COLLISIONS) && !observe_only;
             responded = pair_scan(c, s, er.p.thr, lane, N, sbase, sx, sv, nt, keff, coll, flag_coll, ev, best, dvs,
-                                  dw_az, dw_hit);
+                                  dw && !observe_only, dw_az, dw_hit);
         }
         if (responded) apply_response(c, s, tick, d, dvs);
-        if (dw_hit && !observe_only) apply_downwash(c, s, tick, d, dw_az);
+        if (dw && dw_hit && !observe_only) apply_downwash(c, s, tick, d, dw_az);
         __syncthreads();
         if (act) {  // post-collision velocities for the neighbour observation
             sv[threadIdx.x] = s.v[0];
@@ -360,7 +365,7 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
 
     // ---- S13 reward and done
     if (rew) rew[d] = compute_reward(c, s, er, gl, fh, ev, best, W > 1 ? keff : 0);
-    end_step<SCN>(c, dv, s, er, fh, lane, e, d, done);
+    end_step<EXT>(c, dv, s, er, fh, lane, e, d, done);
 }
 
 struct SlotMap {
@@ -382,7 +387,7 @@ __device__ __forceinline__ SlotMap map_slot(const Dev& dv, const Tile& tile, con
     return m;
 }
 
-template <int W, bool SCN>
+template <int W, bool EXT>
 __global__ void __launch_bounds__(MAX_BLOCK) k_step(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                     const int* __restrict__ perm, const StepIO io, const int observe_only) {
     extern __shared__ float sm[];
@@ -392,18 +397,20 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_step(const Consts c, const Dev dv
     uint32_t ev = 0;
     if (m.act) {
         load_drone(s, dv.st, dv.D, m.d);
-        load_env<SCN>(er, c, dv, m.e);
+        load_env<EXT>(er, c, dv, m.e);
     }
-    step_body<SCN>(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d, io.act, io.obs,
+    const float4 a = (m.act && !observe_only) ? __ldg(reinterpret_cast<const float4*>(io.act) + m.d)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+    step_body<EXT>(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d, a, io.obs,
               io.rew, io.done, observe_only);
     if (!m.act || observe_only) return;
     dv.ev[m.d] = ev;
     store_drone(s, dv.st, dv.D, m.d);
-    if (m.lane == 0) store_env<SCN>(er, dv, m.e);
+    if (m.lane == 0) store_env<EXT>(er, dv, m.e);
 }
 
 // T steps of one tile with the state in registers.
-template <bool SCN>
+template <bool EXT>
 __device__ __forceinline__ void rollout_tile(const Consts& c, const Dev& dv, const Tile& tile, const int* __restrict__ perm,
                                              float* sm, const RolloutIO& io, int t0, int nsteps) {
     const int W = tile.W;
@@ -413,25 +420,31 @@ __device__ __forceinline__ void rollout_tile(const Consts& c, const Dev& dv, con
     uint32_t ev = 0;
     if (m.act) {
         load_drone(s, dv.st, dv.D, m.d);
-        load_env<SCN>(er, c, dv, m.e);
+        load_env<EXT>(er, c, dv, m.e);
     }
     const size_t D = dv.D, E = dv.E;
+    const float4* act4 = reinterpret_cast<const float4*>(io.act) + m.d;
+    // the commands of step t + 1 are loaded while step t computes, so their
+    // HBM latency leaves each step's dependent chain
+    float4 a_next = m.act ? __ldg(act4 + (size_t)t0 * D) : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int t = t0; t < t0 + nsteps; ++t) {
-        step_body<SCN>(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d,
-                  io.act + (size_t)t * D * 4, io.obs ? io.obs + (size_t)t * D * c.obs_dim : nullptr,
-                  io.rew ? io.rew + (size_t)t * D : nullptr, io.done ? io.done + (size_t)t * E : nullptr, 0);
+        const float4 a = a_next;
+        if (m.act && t + 1 < t0 + nsteps) a_next = __ldg(act4 + (size_t)(t + 1) * D);
+        step_body<EXT>(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d, a,
+                       io.obs ? io.obs + (size_t)t * D * c.obs_dim : nullptr, io.rew ? io.rew + (size_t)t * D : nullptr,
+                       io.done ? io.done + (size_t)t * E : nullptr, 0);
     }
     if (m.act) {
         dv.ev[m.d] = ev;
         store_drone(s, dv.st, dv.D, m.d);
-        if (m.lane == 0) store_env<SCN>(er, dv, m.e);
+        if (m.lane == 0) store_env<EXT>(er, dv, m.e);
     }
 }
 
 // Persistent rollout: CTAs take tiles from *counter (zeroed before the launch)
 // until none is left. Tiles are ordered costliest first.
-template <bool SCN>
-__global__ void __launch_bounds__(MAX_BLOCK) k_rollout(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+template <bool EXT>
+__global__ void __launch_bounds__(MAX_BLOCK, 2) k_rollout(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                        const int n_tiles, const int* __restrict__ perm,
                                                        int* __restrict__ counter, const RolloutIO io, const int t0,
                                                        const int nsteps) {
@@ -443,7 +456,7 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_rollout(const Consts c, const Dev
         const int ti = s_next;
         __syncthreads();  // everyone has read s_next before thread 0 overwrites it
         if (ti >= n_tiles) return;
-        rollout_tile<SCN>(c, dv, tiles[ti], perm, sm, io, t0, nsteps);
+        rollout_tile<EXT>(c, dv, tiles[ti], perm, sm, io, t0, nsteps);
     }
 }
 
@@ -473,6 +486,7 @@ struct WsShared {
     float rows[32 * WS_OBS_MAX];
 };
 
+template <bool EXT>
 __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                 const int* __restrict__ perm, const StepIO io) {
     __shared__ WsShared sh;
@@ -490,6 +504,7 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
     const int K = c.K;
     const int nahead = min(c.substeps, WS_SUB);
     const bool mnoise = (c.flags & QS_F_MOTOR_NOISE) != 0;
+    const bool dw = EXT && (c.flags & QS_F_DOWNWASH) != 0;  // EXT = false: no downwash or scenario code
 
     if (warp == 1) {
         // ---------------- noise warp
@@ -568,7 +583,7 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
     uint32_t ev = 0;
     if (act) {
         load_drone(s, dv.st, dv.D, d);
-        load_env<true>(er, c, dv, e);
+        load_env<EXT>(er, c, dv, e);
         const float4 a = __ldg(reinterpret_cast<const float4*>(io.act) + d);
         fh[0] = command(c, a.x);
         fh[1] = command(c, a.y);
@@ -612,14 +627,14 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
             const bool coll = (c.flags & QS_F_COLLISIONS) && !(c.flags & QS_F_SMOOTH);
             const bool flag_coll = (c.flags & QS_F_COLLISIONS) != 0;
             responded = pair_scan(c, s, er.p.thr, lane, N, sbase, &sh.sx[0][0], &sh.sv[0][0], 32, keff, coll, flag_coll,
-                                  ev, best, dvs, dw_az, dw_hit);
+                                  ev, best, dvs, dw, dw_az, dw_hit);
         }
         if (responded) apply_response(c, s, er.tick, d, dvs);
-        if (dw_hit) apply_downwash(c, s, er.tick, d, dw_az);
+        if (dw && dw_hit) apply_downwash(c, s, er.tick, d, dw_az);
     }
     // the drone's goal at the end of the step (Sec. III-D scenarios)
     float gl[3] = {er.g0, er.g1, er.g2};
-    if (c.scn_mask & ~1u) {
+    if (EXT && (c.scn_mask & ~1u)) {
         const int tau = er.ep + 1;
         bool swp = false;
         uint32_t myk = 0;
@@ -657,24 +672,24 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
             if (k < K) dv.knn[(size_t)k * dv.D + d] = (W > 1 && k < keff) ? (int16_t)(best[k] & 0xffffu) : (int16_t)-1;
     }
     if (io.rew) io.rew[d] = compute_reward(c, s, er, gl, fh, ev, best, W > 1 ? keff : 0);
-    end_step<true>(c, dv, s, er, fh, lane, e, d, io.done);
+    end_step<EXT>(c, dv, s, er, fh, lane, e, d, io.done);
     dv.ev[d] = ev;
     store_drone(s, dv.st, dv.D, d);
-    if (lane == 0) store_env<true>(er, dv, e);
+    if (lane == 0) store_env<EXT>(er, dv, e);
 }
 
-template <bool SCN>
+template <bool EXT>
 cudaError_t launch_k_step(const Consts& c, const Dev& dv, const ClassPlan& cp, const Tile* t, const int* perm,
                           const StepIO& io, int observe_only, size_t smem, cudaStream_t st) {
     switch (cp.W) {
-        case 1: k_step<1, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 2: k_step<2, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 4: k_step<4, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 8: k_step<8, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 16: k_step<16, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 32: k_step<32, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 64: k_step<64, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
-        case 128: k_step<128, SCN><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 1: k_step<1, EXT><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 2: k_step<2, EXT><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 4: k_step<4, EXT><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 8: k_step<8, EXT><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 16: k_step<16, EXT><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 32: k_step<32, EXT><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 64: k_step<64, EXT><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
+        case 128: k_step<128, EXT><<<cp.n_tiles, cp.block, smem, st>>>(c, dv, t, perm, io, observe_only); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -683,21 +698,25 @@ cudaError_t launch_k_step(const Consts& c, const Dev& dv, const ClassPlan& cp, c
 cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, const Tile* tiles, const int* perm,
                         const StepIO& io, int observe_only, cudaStream_t st) {
     if (cp.n_tiles == 0) return cudaSuccess;
+    const bool ext = extended(c);
     if (cp.ws && !observe_only) {
-        k_step_ws<<<cp.n_tiles, 64, 0, st>>>(c, dv, tiles + cp.tile_off, perm, io);
+        if (ext)
+            k_step_ws<true><<<cp.n_tiles, 64, 0, st>>>(c, dv, tiles + cp.tile_off, perm, io);
+        else
+            k_step_ws<false><<<cp.n_tiles, 64, 0, st>>>(c, dv, tiles + cp.tile_off, perm, io);
         return cudaGetLastError();
     }
     const size_t smem = (cp.W > 1) ? sizeof(float) * SMEM_PLANES * cp.block : 0;
     const Tile* t = tiles + cp.tile_off;
-    return (c.scn_mask & ~1u) ? launch_k_step<true>(c, dv, cp, t, perm, io, observe_only, smem, st)
-                              : launch_k_step<false>(c, dv, cp, t, perm, io, observe_only, smem, st);
+    return ext ? launch_k_step<true>(c, dv, cp, t, perm, io, observe_only, smem, st)
+               : launch_k_step<false>(c, dv, cp, t, perm, io, observe_only, smem, st);
 }
 
-int rollout_grid(int block, bool scn) {
+int rollout_grid(int block, bool ext) {
     int dev = 0, n_sm = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (scn)
+    if (ext)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rollout<true>, block, sizeof(float) * SMEM_PLANES * block);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rollout<false>, block, sizeof(float) * SMEM_PLANES * block);
@@ -711,7 +730,7 @@ cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, in
     const size_t smem = sizeof(float) * SMEM_PLANES * block;
     const int g = grid > 0 ? grid : n_tiles;
     const int grid_n = g < n_tiles ? g : n_tiles;
-    if (c.scn_mask & ~1u)
+    if (extended(c))
         k_rollout<true><<<grid_n, block, smem, st>>>(c, dv, tiles, n_tiles, perm, counter, io, t0, nsteps);
     else
         k_rollout<false><<<grid_n, block, smem, st>>>(c, dv, tiles, n_tiles, perm, counter, io, t0, nsteps);
