@@ -181,12 +181,23 @@ void drop_graph(qs_env* h) {
     h->graph_key = {};
 }
 
-// Default launch shape: enough CTAs to cover 2 x 152 SMs when the class has
-// the threads for it, 32..256 threads per CTA.
-int default_block(int W, int slots) {
-    const int threads = slots * W;
+// One wave of warp-specialised CTAs: 8 two-warp CTAs of 32 drones per SM.
+long ws_wave(int n_sm) { return (long)n_sm * 8 * 32; }
+
+// The warp-specialised step wins while a class is latency-bound: up to about
+// one wave of its CTAs.
+bool use_ws(int W, int slots, int n_sm) { return W <= 32 && (long)slots * W <= ws_wave(n_sm); }
+
+// Default launch shape of the general per-call kernel: 64 threads per CTA (or
+// W) for classes beyond a wave (small CTAs interleave their load, compute and
+// store phases best: measured at 262,144 and 1,048,576 single-drone envs);
+// else enough CTAs to cover 2 CTAs per SM when the class has the threads for
+// it, 32..256 threads per CTA.
+int default_block(int W, int slots, int n_sm) {
+    const long threads = (long)slots * W;
+    if (threads > ws_wave(n_sm)) return std::max(64, W);
     int b = 256;
-    while (b > 32 && b > W && threads / b < 2 * 152) b >>= 1;
+    while (b > 32 && b > W && threads / b < 2 * n_sm) b >>= 1;
     return std::max(b, std::max(W, 32));
 }
 
@@ -358,6 +369,8 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
     cudaGetDevice(&h->device);
     build_consts(h);
 
+    int n_sm = 152;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
     // envs grouped by width class (stable order inside a class)
     std::vector<int> perm;
     for (int W = 1; W <= QS_MAX_SWARM; W <<= 1) {
@@ -366,9 +379,9 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
             if (width_class(sizes[e]) == W) perm.push_back(e);
         int n = (int)perm.size() - first;
         if (n > 0) {
-            // width <= 32: warp-specialised per-call step on tiles of 32 drone lanes
-            const int ws = W <= 32 ? 1 : 0;
-            h->plan.push_back(ClassPlan{W, ws ? 32 : default_block(W, n), ws, 0, 0});
+            // latency-bound classes: warp-specialised per-call step on tiles of 32 drone lanes
+            const int ws = use_ws(W, n, n_sm) ? 1 : 0;
+            h->plan.push_back(ClassPlan{W, ws ? 32 : default_block(W, n, n_sm), ws, 0, 0});
             h->class_first_slot.push_back(first);
             h->class_slots.push_back(n);
         }
