@@ -240,10 +240,14 @@ qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, fl
 qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_dev, float* reward_dev,
                      uint8_t* done_dev);
 
-/* Launch shape of qs_rollout: `block` threads per CTA (32..256, a multiple of
- * 32, at least the widest swarm class), `fuse` control steps per launch
- * (0 = all T steps in one launch), `use_graph` (0/1). Results do not depend
- * on the shape. Used by the autotuner. */
+/* Launch shape of qs_rollout: `block` threads per CTA of the persistent
+ * kernel (32..256, a multiple of 32, at least the widest swarm class), or
+ * QS_BLOCK_WARP_SPECIALISED (every class at most 32 wide; the default when
+ * the handle also has at most about one wave of 32-drone CTAs): per 32 drones
+ * one CTA whose dynamics warp integrates while a second warp draws the noise
+ * and stores the observation rows, every step; `fuse` control steps per
+ * launch (0 = all T steps in one launch), `use_graph` (0/1). Results do not
+ * depend on the shape. Used by the autotuner. */
 qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t use_graph);
 qs_status qs_get_rollout_shape(const qs_env* h, int32_t* block, int32_t* fuse, int32_t* use_graph);
 

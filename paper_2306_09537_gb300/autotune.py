@@ -74,8 +74,11 @@ def tune(env, steps: int = 32, horizon: int = 64, reps: int = 3, apply: bool = T
             rew = torch.empty(horizon, twin.D, device=twin.device)
             best = None
             maxw = max(classes)
-            for b in (64, 128, 256):
-                if b < maxw:
+            for b in (qs.QS_BLOCK_WARP_SPECIALISED, 64, 128, 256):
+                if b == qs.QS_BLOCK_WARP_SPECIALISED:
+                    if maxw > 32:
+                        continue
+                elif b < maxw:
                     continue
                 for fuse in (0, max(1, horizon // 8)):
                     for graph in (True, False):

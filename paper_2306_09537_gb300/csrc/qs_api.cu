@@ -41,8 +41,11 @@ struct qs_env {
     // differentiable rollout: small CTAs (one or two warps), one tile each
     Tile* d_dtiles = nullptr;
     int n_dtiles = 0;
+    // warp-specialised rollout: tiles of 32 drone lanes (every class <= 32 wide)
+    Tile* d_wtiles = nullptr;
+    int n_wtiles = 0;
     int diff_block = 32;
-    int rollout_block = 128;
+    int rollout_block = 128;  // or QS_BLOCK_WARP_SPECIALISED
     int rollout_fuse = 0;   // control steps per launch (0: all T in one launch)
     int rollout_grid = 0;   // resident CTAs for rollout_block
     int use_graph = 1;
@@ -175,6 +178,23 @@ void build_rollout_tiles(qs_env* h, std::vector<Tile>& tiles, int block) {
     }
 }
 
+// Tiles of the warp-specialised rollout: 32 drone lanes per CTA, block 32 of
+// build_tiles for every class; none when a class is wider than 32.
+void build_ws_tiles(qs_env* h, std::vector<Tile>& tiles) {
+    tiles.clear();
+    for (size_t ci = 0; ci < h->plan.size(); ++ci)
+        if (h->plan[ci].W > 32) return;
+    for (size_t ci = 0; ci < h->plan.size(); ++ci) {
+        const int W = h->plan[ci].W, per = 32 / W;
+        for (int s = 0; s < h->class_slots[ci]; s += per) {
+            const int first = h->class_first_slot[ci] + s, count = std::min(per, h->class_slots[ci] - s);
+            int contig = 1;
+            for (int i = 1; i < count; ++i) contig &= h->perm_h[first + i] == h->perm_h[first] + i;
+            tiles.push_back(Tile{first, count, W, contig});
+        }
+    }
+}
+
 void drop_graph(qs_env* h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -201,10 +221,14 @@ int default_block(int W, int slots, int n_sm) {
     return std::max(b, std::max(W, 32));
 }
 
+bool rollout_is_ws(const qs_env* h) { return h->rollout_block == QS_BLOCK_WARP_SPECIALISED; }
+
 qs_status upload_tiles(qs_env* h) {
-    std::vector<Tile> tiles, rtiles, dtiles;
+    std::vector<Tile> tiles, rtiles, dtiles, wtiles;
     build_tiles(h, tiles);
-    build_rollout_tiles(h, rtiles, h->rollout_block);
+    const int rblock = rollout_is_ws(h) ? 128 : h->rollout_block;  // the persistent kernel's tiles stay available
+    build_rollout_tiles(h, rtiles, rblock);
+    build_ws_tiles(h, wtiles);
     int maxW = 1;
     for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
     h->diff_block = std::max(32, maxW);  // many small CTAs: the adjoint is latency-bound
@@ -214,18 +238,22 @@ qs_status upload_tiles(qs_env* h) {
     h->d_tiles = nullptr;
     h->d_rtiles = nullptr;
     h->d_dtiles = nullptr;
-    const size_t n0 = tiles.size(), n1 = rtiles.size(), n = n0 + n1 + dtiles.size();
+    h->d_wtiles = nullptr;
+    const size_t n0 = tiles.size(), n1 = rtiles.size(), n2 = dtiles.size(), n = n0 + n1 + n2 + wtiles.size();
     cudaError_t e = cudaMalloc(&h->d_tiles, sizeof(Tile) * std::max<size_t>(n, 1));
     if (e != cudaSuccess) return fail(h, QS_ERR_OOM, "tile table allocation failed");
     tiles.insert(tiles.end(), rtiles.begin(), rtiles.end());
     tiles.insert(tiles.end(), dtiles.begin(), dtiles.end());
+    tiles.insert(tiles.end(), wtiles.begin(), wtiles.end());
     e = cudaMemcpy(h->d_tiles, tiles.data(), sizeof(Tile) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(h, e, "tile table upload");
     h->d_rtiles = h->d_tiles + n0;
     h->n_rtiles = (int)n1;
     h->d_dtiles = h->d_tiles + n0 + n1;
-    h->n_dtiles = (int)dtiles.size();
-    h->rollout_grid = rollout_grid(h->rollout_block, (h->c.scn_mask & ~1u) != 0 || (h->c.flags & QS_F_DOWNWASH) != 0);
+    h->n_dtiles = (int)n2;
+    h->d_wtiles = h->d_tiles + n0 + n1 + n2;
+    h->n_wtiles = (int)wtiles.size();
+    h->rollout_grid = rollout_grid(rblock, (h->c.scn_mask & ~1u) != 0 || (h->c.flags & QS_F_DOWNWASH) != 0);
     return QS_OK;
 }
 
@@ -233,8 +261,11 @@ qs_status upload_tiles(qs_env* h) {
 qs_status enqueue_rollout(qs_env* h, int T, const RolloutIO& io) {
     const int fuse = h->rollout_fuse > 0 ? h->rollout_fuse : T;
     for (int t0 = 0; t0 < T; t0 += fuse) {
-        cudaError_t e = launch_rollout(h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm, h->d_counter,
-                                       io, t0, std::min(fuse, T - t0), h->rollout_grid, h->stream);
+        const int n = std::min(fuse, T - t0);
+        cudaError_t e = rollout_is_ws(h)
+                            ? launch_rollout_ws(h->c, h->dv, h->d_wtiles, h->n_wtiles, h->d_perm, io, t0, n, h->stream)
+                            : launch_rollout(h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm,
+                                             h->d_counter, io, t0, n, h->rollout_grid, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "rollout launch");
     }
     return QS_OK;
@@ -385,6 +416,14 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
             h->class_first_slot.push_back(first);
             h->class_slots.push_back(n);
         }
+    }
+    // the warp-specialised rollout while every class is at most 32 wide and the
+    // handle fits about one wave of its CTAs (latency-bound), else the
+    // persistent kernel
+    {
+        int maxW = 1;
+        for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
+        if (maxW <= 32 && (long)h->D <= ws_wave(n_sm)) h->rollout_block = QS_BLOCK_WARP_SPECIALISED;
     }
 
     // one arena for the state
@@ -584,8 +623,11 @@ qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t u
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_set_rollout_shape: NULL handle");
     int maxW = 1;
     for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
-    if (block < 32 || block > 256 || block % 32 != 0 || block < maxW || fuse < 0)
-        return fail(h, QS_ERR_ARG, "qs_set_rollout_shape: block must be 32..256, a multiple of 32, >= the widest class; fuse >= 0");
+    const bool ws = block == QS_BLOCK_WARP_SPECIALISED && maxW <= 32;
+    if (!ws && (block < 32 || block > 256 || block % 32 != 0 || block < maxW))
+        return fail(h, QS_ERR_ARG, "qs_set_rollout_shape: block must be 32..256, a multiple of 32, >= the widest class, "
+                                   "or QS_BLOCK_WARP_SPECIALISED when every class is at most 32 wide");
+    if (fuse < 0) return fail(h, QS_ERR_ARG, "qs_set_rollout_shape: fuse must be >= 0");
     DeviceGuard g(h->device);
     cudaError_t e = cudaStreamSynchronize(h->stream);  // the old tables may be in use
     if (e != cudaSuccess) return cuda_fail(h, e, "qs_set_rollout_shape");

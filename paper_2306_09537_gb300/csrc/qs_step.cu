@@ -489,105 +489,119 @@ struct WsShared {
     float rows[32 * WS_OBS_MAX];
 };
 
+// Slot geometry of a warp-specialised CTA: lane l of each warp stands for
+// slot-local drone `lane` of slot `slot` (W lanes per slot, 32 per CTA).
+struct WsMap {
+    int W, l, slot, lane, e, d0, N, d, sbase;
+    bool act;
+};
+
+__device__ __forceinline__ WsMap ws_map(const Dev& dv, const Tile& tile, const int* __restrict__ perm) {
+    WsMap m;
+    m.W = tile.W;
+    m.l = threadIdx.x & 31;
+    m.slot = m.l / m.W;
+    m.lane = m.l - m.slot * m.W;
+    const bool ok = m.slot < tile.count;
+    m.e = ok ? perm[tile.first + m.slot] : 0;
+    m.d0 = ok ? dv.env_off[m.e] : 0;
+    m.N = ok ? dv.env_off[m.e + 1] - m.d0 : 0;
+    m.act = m.lane < m.N;
+    m.d = m.d0 + m.lane;
+    m.sbase = m.slot * m.W;
+    return m;
+}
+
+// Noise warp: the motor-noise normals of the first WS_SUB substeps of the
+// step at Philox counter `tick`, into shared memory.
+__device__ __forceinline__ void ws_motor_normals(const Consts& c, WsShared& sh, const WsMap& m, uint32_t tick) {
+    if (!m.act || !(c.flags & QS_F_MOTOR_NOISE)) return;
+    const int nahead = min(c.substeps, WS_SUB);
+    for (int sub = 0; sub < nahead; ++sub) {
+        float n[4];
+        motor_normals(c, tick, m.d, sub, n);
+        sh.nrm[sub][0][m.l] = n[0];
+        sh.nrm[sub][1][m.l] = n[1];
+        sh.nrm[sub][2][m.l] = n[2];
+        sh.nrm[sub][3][m.l] = n[3];
+    }
+}
+
+// Noise warp, after B2: the observation rows of the CTA's drones from the
+// published post-step states plus sensor noise, assembled in shared memory and
+// stored to obs; when the CTA's drones are contiguous the rows form one block
+// written with 16-byte stores.
+__device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, const Tile& tile, const int* __restrict__ perm,
+                                             WsShared& sh, const WsMap& m, float* __restrict__ obs, const float ex[3],
+                                             const float evv[3], const float ew[3]) {
+    const int od = c.obs_dim, K = c.K, l = m.l;
+    const bool contig = tile.pad != 0;
+    const int d_first = dv.env_off[perm[tile.first]];
+    const int ridx = contig ? m.d - d_first : l;
+    if (m.act) {
+        float* row = sh.rows + ridx * od;
+        row[0] = sh.st[0][l] - sh.g[0][l] + ex[0];
+        row[1] = sh.st[1][l] - sh.g[1][l] + ex[1];
+        row[2] = sh.st[2][l] - sh.g[2][l] + ex[2];
+        row[3] = sh.st[3][l] + evv[0];
+        row[4] = sh.st[4][l] + evv[1];
+        row[5] = sh.st[5][l] + evv[2];
+        for (int k = 6; k < 15; ++k) row[k] = sh.st[k][l];
+        row[15] = sh.st[15][l] + ew[0];
+        row[16] = sh.st[16][l] + ew[1];
+        row[17] = sh.st[17][l] + ew[2];
+        const int ke = sh.keff[l];
+        for (int k = 0; k < K; ++k) {
+            float* on = row + 18 + 6 * k;
+            if (k < ke) {
+                const int j = sh.nb[k][l];
+                for (int q = 0; q < 6; ++q) on[q] = sh.st[q][j] - sh.st[q][l];
+            } else {
+                for (int q = 0; q < 6; ++q) on[q] = 0.f;
+            }
+        }
+    }
+    __syncwarp();
+    if (contig) {
+        const int e_last = perm[tile.first + tile.count - 1];
+        const int n_floats = (dv.env_off[e_last + 1] - d_first) * od;
+        float* dst = obs + (size_t)d_first * od;
+        if (((uintptr_t)dst & 15u) == 0) {
+            const int n4 = n_floats >> 2;
+            const float4* src4 = reinterpret_cast<const float4*>(sh.rows);
+            float4* dst4 = reinterpret_cast<float4*>(dst);
+            for (int i = l; i < n4; i += 32) dst4[i] = src4[i];
+            for (int i = (n4 << 2) + l; i < n_floats; i += 32) dst[i] = sh.rows[i];
+        } else {
+            const int n2 = n_floats >> 1;  // obs rows hold an even number of floats
+            const float2* src2 = reinterpret_cast<const float2*>(sh.rows);
+            float2* dst2 = reinterpret_cast<float2*>(dst);
+            for (int i = l; i < n2; i += 32) dst2[i] = src2[i];
+        }
+    } else if (m.act) {
+        const float2* src2 = reinterpret_cast<const float2*>(sh.rows + ridx * od);
+        float2* dst2 = reinterpret_cast<float2*>(obs + (size_t)m.d * od);
+        for (int i = 0; i < od / 2; ++i) dst2[i] = src2[i];
+    }
+}
+
+// Dynamics warp: one control step of the lane's drone with command a. Meets
+// the noise warp at B1 (motor normals ready) and B2 (post-step state, goal and
+// neighbours published for the observation rows), then writes the knn record,
+// reward and done and ends the step. Every thread of the warp calls it.
 template <bool EXT>
-__global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
-                                                const int* __restrict__ perm, const StepIO io) {
-    __shared__ WsShared sh;
-    const Tile tile = tiles[blockIdx.x];
-    const int W = tile.W;
-    const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int slot = l / W, lane = l - slot * W;
-    const bool ok = slot < tile.count;
-    const int e = ok ? perm[tile.first + slot] : 0;
-    const int d0 = ok ? dv.env_off[e] : 0;
-    const int N = ok ? dv.env_off[e + 1] - d0 : 0;
-    const bool act = lane < N;
-    const int d = d0 + lane;
-    const int sbase = slot * W;
+__device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv, WsShared& sh, const WsMap& m, Drone& s,
+                                                 EnvRegs& er, uint32_t& ev_out, const float4 a,
+                                                 float* __restrict__ rew, uint8_t* __restrict__ done) {
+    const int W = m.W, l = m.l, lane = m.lane, N = m.N, e = m.e, d = m.d, sbase = m.sbase;
+    const bool act = m.act;
     const int K = c.K;
     const int nahead = min(c.substeps, WS_SUB);
     const bool mnoise = (c.flags & QS_F_MOTOR_NOISE) != 0;
     const bool dw = EXT && (c.flags & QS_F_DOWNWASH) != 0;  // EXT = false: no downwash or scenario code
-
-    if (warp == 1) {
-        // ---------------- noise warp
-        const uint32_t tick = act ? dv.tick[e] : 0u;  // warp 0 writes it only after B2
-        if (act && mnoise) {
-            for (int sub = 0; sub < nahead; ++sub) {
-                float n[4];
-                motor_normals(c, tick, d, sub, n);
-                sh.nrm[sub][0][l] = n[0];
-                sh.nrm[sub][1][l] = n[1];
-                sh.nrm[sub][2][l] = n[2];
-                sh.nrm[sub][3][l] = n[3];
-            }
-        }
-        __syncthreads();  // B1
-        float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
-        if (act && io.obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, d, 0u, ex, evv, ew);
-        __syncthreads();  // B2
-        if (!io.obs) return;
-        const int od = c.obs_dim;
-        const bool contig = tile.pad != 0;
-        const int d_first = dv.env_off[perm[tile.first]];
-        const int ridx = contig ? d - d_first : l;
-        if (act) {
-            float* row = sh.rows + ridx * od;
-            row[0] = sh.st[0][l] - sh.g[0][l] + ex[0];
-            row[1] = sh.st[1][l] - sh.g[1][l] + ex[1];
-            row[2] = sh.st[2][l] - sh.g[2][l] + ex[2];
-            row[3] = sh.st[3][l] + evv[0];
-            row[4] = sh.st[4][l] + evv[1];
-            row[5] = sh.st[5][l] + evv[2];
-            for (int k = 6; k < 15; ++k) row[k] = sh.st[k][l];
-            row[15] = sh.st[15][l] + ew[0];
-            row[16] = sh.st[16][l] + ew[1];
-            row[17] = sh.st[17][l] + ew[2];
-            const int ke = sh.keff[l];
-            for (int k = 0; k < K; ++k) {
-                float* on = row + 18 + 6 * k;
-                if (k < ke) {
-                    const int j = sh.nb[k][l];
-                    for (int q = 0; q < 6; ++q) on[q] = sh.st[q][j] - sh.st[q][l];
-                } else {
-                    for (int q = 0; q < 6; ++q) on[q] = 0.f;
-                }
-            }
-        }
-        __syncwarp();
-        if (contig) {
-            const int e_last = perm[tile.first + tile.count - 1];
-            const int n_floats = (dv.env_off[e_last + 1] - d_first) * od;
-            float* dst = io.obs + (size_t)d_first * od;
-            if (((uintptr_t)dst & 15u) == 0) {
-                const int n4 = n_floats >> 2;
-                const float4* src4 = reinterpret_cast<const float4*>(sh.rows);
-                float4* dst4 = reinterpret_cast<float4*>(dst);
-                for (int i = l; i < n4; i += 32) dst4[i] = src4[i];
-                for (int i = (n4 << 2) + l; i < n_floats; i += 32) dst[i] = sh.rows[i];
-            } else {
-                const int n2 = n_floats >> 1;  // obs rows hold an even number of floats
-                const float2* src2 = reinterpret_cast<const float2*>(sh.rows);
-                float2* dst2 = reinterpret_cast<float2*>(dst);
-                for (int i = l; i < n2; i += 32) dst2[i] = src2[i];
-            }
-        } else if (act) {
-            const float2* src2 = reinterpret_cast<const float2*>(sh.rows + ridx * od);
-            float2* dst2 = reinterpret_cast<float2*>(io.obs + (size_t)d * od);
-            for (int i = 0; i < od / 2; ++i) dst2[i] = src2[i];
-        }
-        return;
-    }
-
-    // ---------------- dynamics warp
-    Drone s;
-    EnvRegs er;
     float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f};
     uint32_t ev = 0;
     if (act) {
-        load_drone(s, dv.st, dv.D, d);
-        load_env<EXT>(er, c, dv, e);
-        const float4 a = __ldg(reinterpret_cast<const float4*>(io.act) + d);
         fh[0] = command(c, a.x);
         fh[1] = command(c, a.y);
         fh[2] = command(c, a.z);
@@ -674,11 +688,95 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
         for (int k = 0; k < QS_MAX_K; ++k)
             if (k < K) dv.knn[(size_t)k * dv.D + d] = (W > 1 && k < keff) ? (int16_t)(best[k] & 0xffffu) : (int16_t)-1;
     }
-    if (io.rew) io.rew[d] = compute_reward(c, s, er, gl, fh, ev, best, W > 1 ? keff : 0);
-    end_step<EXT>(c, dv, s, er, fh, lane, e, d, io.done);
-    dv.ev[d] = ev;
-    store_drone(s, dv.st, dv.D, d);
-    if (lane == 0) store_env<EXT>(er, dv, e);
+    if (rew) rew[d] = compute_reward(c, s, er, gl, fh, ev, best, W > 1 ? keff : 0);
+    end_step<EXT>(c, dv, s, er, fh, lane, e, d, done);
+    ev_out = ev;
+}
+
+template <bool EXT>
+__global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+                                                const int* __restrict__ perm, const StepIO io) {
+    __shared__ WsShared sh;
+    const Tile tile = tiles[blockIdx.x];
+    const WsMap m = ws_map(dv, tile, perm);
+    if (threadIdx.x >= 32) {
+        // ---------------- noise warp
+        const uint32_t tick = m.act ? dv.tick[m.e] : 0u;  // warp 0 writes it only after B2
+        ws_motor_normals(c, sh, m, tick);
+        __syncthreads();  // B1
+        float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
+        if (m.act && io.obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, m.d, 0u, ex, evv, ew);
+        __syncthreads();  // B2
+        if (io.obs) ws_store_obs(c, dv, tile, perm, sh, m, io.obs, ex, evv, ew);
+        return;
+    }
+    // ---------------- dynamics warp
+    Drone s;
+    EnvRegs er;
+    uint32_t ev = 0;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m.act) {
+        load_drone(s, dv.st, dv.D, m.d);
+        load_env<EXT>(er, c, dv, m.e);
+        a = __ldg(reinterpret_cast<const float4*>(io.act) + m.d);
+    }
+    ws_dynamics_step<EXT>(c, dv, sh, m, s, er, ev, a, io.rew, io.done);
+    if (!m.act) return;
+    dv.ev[m.d] = ev;
+    store_drone(s, dv.st, dv.D, m.d);
+    if (m.lane == 0) store_env<EXT>(er, dv, m.e);
+}
+
+// Persistent warp-specialised rollout for latency-bound handles (every swarm
+// class at most 32 wide): one CTA per tile of 32 drone lanes runs steps
+// t0 .. t0 + nsteps - 1 with the drones in the dynamics warp's registers,
+// while the noise warp draws each step's sensor noise during the dynamics,
+// then stores that step's observation rows and draws the next step's motor
+// normals. The two warps meet at B1 and B2 of every step.
+template <bool EXT>
+__global__ void __launch_bounds__(64) k_rollout_ws(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+                                                   const int* __restrict__ perm, const RolloutIO io, const int t0,
+                                                   const int nsteps) {
+    __shared__ WsShared sh;
+    const Tile tile = tiles[blockIdx.x];
+    const WsMap m = ws_map(dv, tile, perm);
+    const size_t D = dv.D, E = dv.E;
+    if (threadIdx.x >= 32) {
+        // ---------------- noise warp; the env's Philox counter advances by one per step
+        const uint32_t tick0 = m.act ? dv.tick[m.e] : 0u;  // warp 0 writes it after the last step
+        ws_motor_normals(c, sh, m, tick0);
+        for (int t = 0; t < nsteps; ++t) {
+            const uint32_t tick = tick0 + (uint32_t)t;
+            float* obs = io.obs ? io.obs + (size_t)(t0 + t) * D * c.obs_dim : nullptr;
+            __syncthreads();  // B1 of step t
+            float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
+            if (m.act && obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, m.d, 0u, ex, evv, ew);
+            __syncthreads();  // B2 of step t
+            if (obs) ws_store_obs(c, dv, tile, perm, sh, m, obs, ex, evv, ew);
+            if (t + 1 < nsteps) ws_motor_normals(c, sh, m, tick + 1);
+        }
+        return;
+    }
+    // ---------------- dynamics warp
+    Drone s;
+    EnvRegs er;
+    uint32_t ev = 0;
+    if (m.act) {
+        load_drone(s, dv.st, dv.D, m.d);
+        load_env<EXT>(er, c, dv, m.e);
+    }
+    const float4* act4 = reinterpret_cast<const float4*>(io.act) + m.d;
+    float4 a_next = m.act ? __ldg(act4 + (size_t)t0 * D) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = 0; t < nsteps; ++t) {
+        const float4 a = a_next;
+        if (m.act && t + 1 < nsteps) a_next = __ldg(act4 + (size_t)(t0 + t + 1) * D);
+        ws_dynamics_step<EXT>(c, dv, sh, m, s, er, ev, a, io.rew ? io.rew + (size_t)(t0 + t) * D : nullptr,
+                              io.done ? io.done + (size_t)(t0 + t) * E : nullptr);
+    }
+    if (!m.act) return;
+    dv.ev[m.d] = ev;
+    store_drone(s, dv.st, dv.D, m.d);
+    if (m.lane == 0) store_env<EXT>(er, dv, m.e);
 }
 
 template <bool EXT>
@@ -724,6 +822,16 @@ int rollout_grid(int block, bool ext) {
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rollout<false>, block, sizeof(float) * SMEM_PLANES * block);
     return (occ > 0 ? occ : 1) * n_sm;
+}
+
+cudaError_t launch_rollout_ws(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, const int* perm,
+                              const RolloutIO& io, int t0, int nsteps, cudaStream_t st) {
+    if (n_tiles == 0) return cudaSuccess;
+    if (extended(c))
+        k_rollout_ws<true><<<n_tiles, 64, 0, st>>>(c, dv, tiles, perm, io, t0, nsteps);
+    else
+        k_rollout_ws<false><<<n_tiles, 64, 0, st>>>(c, dv, tiles, perm, io, t0, nsteps);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int block, const int* perm,

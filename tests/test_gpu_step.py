@@ -362,6 +362,48 @@ def test_rollout_equals_steps():
     assert torch.equal(ev1, ev2)
 
 
+@pytest.mark.parametrize("shape", [None, (1, 0, True), (1, 5, False), (1, 1, True), (64, 0, False)])
+@pytest.mark.parametrize("extended", [False, True])
+def test_ws_rollout_equals_steps(shape, extended):
+    """Classes at most 32 wide: the warp-specialised persistent rollout (the
+    default for such handles; noise and observation rows on a second warp)
+    reproduces per-call steps across auto-reset episodes, also with the
+    scenario goals and downwash compiled in."""
+    from paper_2306_09537_gb300 import qs
+    sizes = [1, 2, 3, 5, 8, 13, 16, 31, 32] * 6
+    feats = FULL + ("auto_reset",) + (("downwash",) if extended else ())
+    kw = dict(scenarios=("static", "swap", "pursuit_bezier", "swarm_vs_swarm")) if extended else {}
+    env, _ = pair(sizes, 6, feats, seed=6, episode_steps=7, **kw)
+    env2, _ = pair(sizes, 6, feats, seed=6, episode_steps=7, **kw)
+    if shape is None:
+        assert qs.qs_get_rollout_shape(env.h)[0] == qs.QS_BLOCK_WARP_SPECIALISED
+    else:
+        qs.qs_set_rollout_shape(env.h, *shape)
+    T = 17
+    acts = torch.from_numpy(W.actions(6, T, env.D)).to(DEV)
+    obs = torch.empty(T, env.D, env.obs_dim, device=DEV)
+    rew = torch.empty(T, env.D, device=DEV)
+    done = torch.empty(T, env.E, dtype=torch.uint8, device=DEV)
+    env.rollout(acts, obs, rew, done)
+    for t in range(T):
+        o2, r2, d2 = env2.step(acts[t])
+        assert torch.equal(obs[t], o2) and torch.equal(rew[t], r2) and torch.equal(done[t], d2), t
+    s1, s2 = env.get_state(), env2.get_state()
+    for k in ("state", "params", "goals", "ep_step", "tick"):
+        assert torch.equal(s1[k], s2[k]), k
+    assert torch.equal(env.get_events()[0], env2.get_events()[0])
+    if extended:
+        assert torch.equal(env.get_scenario(), env2.get_scenario())
+
+
+def test_ws_rollout_needs_narrow_classes():
+    from paper_2306_09537_gb300 import qs
+    env, _ = pair([4, 64], 2, FULL, seed=1)
+    assert qs.qs_get_rollout_shape(env.h)[0] != qs.QS_BLOCK_WARP_SPECIALISED
+    with pytest.raises(qs.QSError):
+        qs.qs_set_rollout_shape(env.h, qs.QS_BLOCK_WARP_SPECIALISED, 0, 1)
+
+
 @pytest.mark.parametrize("shape", [(64, 0, True), (128, 5, True), (256, 3, False), (64, 1, False)])
 def test_rollout_shape_does_not_change_results(shape):
     sizes = [1, 2, 8, 64, 4] * 5
