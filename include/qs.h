@@ -220,10 +220,13 @@ qs_status qs_reset(qs_env* h, uint64_t seed, const uint8_t* env_mask_dev, float*
  * the device is reported by the next qs_sync() or qs_step_host(). */
 qs_status qs_step(qs_env* h, const float* actions_dev, float* obs_dev, float* reward_dev, uint8_t* done_dev);
 
-/* qs_step for callers whose buffers live in host memory: copies actions_host
- * [D][4] to the device, steps, copies obs/reward/done back into the host
- * buffers (each nullable) and waits for the stream. Pinned host memory makes
- * the copies asynchronous DMA. */
+/* qs_step for callers whose buffers live in host memory: actions_host [D][4]
+ * in; obs/reward/done out (each nullable); waits for the stream and reports
+ * like qs_sync. A page-locked buffer (cudaHostAlloc / cudaHostRegister, e.g.
+ * torch pin_memory) that the device can address (actions 16-byte aligned, obs
+ * 8-byte aligned) is read or written by the step kernel in place, over
+ * NVLink-C2C on a Grace host; any other buffer goes through a device staging
+ * buffer and one asynchronous copy. */
 qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, float* reward_host,
                        uint8_t* done_host);
 

@@ -58,6 +58,7 @@ struct qs_env {
     // device staging of qs_step_host (one allocation, made on first use)
     char* stage = nullptr;
     size_t st_obs = 0, st_rew = 0, st_done = 0;
+    int32_t* status_h = nullptr;  // pinned host copy of the device status word (qs_sync)
     std::string err;
 };
 
@@ -501,6 +502,7 @@ qs_status qs_destroy(qs_env* h) {
     cudaFree(h->d_tiles);
     cudaFree(h->arena);
     cudaFree(h->stage);
+    if (h->status_h) cudaFreeHost(h->status_h);
     delete h;
     return QS_OK;
 }
@@ -546,6 +548,18 @@ qs_status qs_step(qs_env* h, const float* actions_dev, float* obs_dev, float* re
     return do_step(h, actions_dev, obs_dev, reward_dev, done_dev);
 }
 
+// Device address of page-locked (pinned or registered) host memory that the
+// device can load from and store to directly, or null for any other pointer.
+void* mapped_host(const void* p, size_t align) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // an unregistered pointer is not an error here
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || !aligned(a.devicePointer, align)) return nullptr;
+    return a.devicePointer;
+}
+
 qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, float* reward_host, uint8_t* done_host) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_step_host: NULL handle");
     if (!actions_host) return fail(h, QS_ERR_ARG, "qs_step_host: actions_host is NULL");
@@ -553,7 +567,15 @@ qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, fl
     const size_t D = h->D, E = h->E;
     const size_t b_act = sizeof(float) * 4 * D, b_obs = sizeof(float) * h->obs_dim * D, b_rew = sizeof(float) * D,
                  b_done = E;
-    if (!h->stage) {
+    // page-locked host buffers are read and written by the step kernel in place
+    // (over NVLink-C2C on a Grace host); other host memory goes through device
+    // staging buffers and one copy each way
+    const float* a_map = (const float*)mapped_host(actions_host, 16);
+    float* o_map = obs_host ? (float*)mapped_host(obs_host, 8) : nullptr;
+    float* r_map = reward_host ? (float*)mapped_host(reward_host, 4) : nullptr;
+    uint8_t* dn_map = done_host ? (uint8_t*)mapped_host(done_host, 1) : nullptr;
+    const bool staged = !a_map || (obs_host && !o_map) || (reward_host && !r_map) || (done_host && !dn_map);
+    if (staged && !h->stage) {
         h->st_obs = (b_act + 255) & ~size_t(255);
         h->st_rew = (h->st_obs + b_obs + 255) & ~size_t(255);
         h->st_done = (h->st_rew + b_rew + 255) & ~size_t(255);
@@ -562,19 +584,24 @@ qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, fl
             return fail(h, QS_ERR_OOM, "qs_step_host: staging allocation");
         }
     }
-    float* d_act = (float*)h->stage;
-    float* d_obs = (float*)(h->stage + h->st_obs);
-    float* d_rew = (float*)(h->stage + h->st_rew);
-    uint8_t* d_done = (uint8_t*)(h->stage + h->st_done);
-    cudaError_t e = cudaMemcpyAsync(d_act, actions_host, b_act, cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "qs_step_host: action copy");
-    qs_status s = do_step(h, d_act, obs_host ? d_obs : nullptr, reward_host ? d_rew : nullptr, done_host ? d_done : nullptr);
+    cudaError_t e = cudaSuccess;
+    const float* d_act = a_map;
+    if (!d_act) {
+        d_act = (float*)h->stage;
+        e = cudaMemcpyAsync((void*)d_act, actions_host, b_act, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "qs_step_host: action copy");
+    }
+    float* d_obs = !obs_host ? nullptr : o_map ? o_map : (float*)(h->stage + h->st_obs);
+    float* d_rew = !reward_host ? nullptr : r_map ? r_map : (float*)(h->stage + h->st_rew);
+    uint8_t* d_done = !done_host ? nullptr : dn_map ? dn_map : (uint8_t*)(h->stage + h->st_done);
+    qs_status s = do_step(h, d_act, d_obs, d_rew, d_done);
     if (s != QS_OK) return s;
-    if (obs_host && (e = cudaMemcpyAsync(obs_host, d_obs, b_obs, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+    if (obs_host && !o_map && (e = cudaMemcpyAsync(obs_host, d_obs, b_obs, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "qs_step_host: observation copy");
-    if (reward_host && (e = cudaMemcpyAsync(reward_host, d_rew, b_rew, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+    if (reward_host && !r_map &&
+        (e = cudaMemcpyAsync(reward_host, d_rew, b_rew, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "qs_step_host: reward copy");
-    if (done_host && (e = cudaMemcpyAsync(done_host, d_done, b_done, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+    if (done_host && !dn_map && (e = cudaMemcpyAsync(done_host, d_done, b_done, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "qs_step_host: done copy");
     return qs_sync(h);
 }
@@ -811,12 +838,16 @@ qs_status qs_get_goals(qs_env* h, float* goals_dev) {
 qs_status qs_sync(qs_env* h) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_sync: NULL handle");
     DeviceGuard g(h->device);
-    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (!h->status_h && cudaHostAlloc((void**)&h->status_h, sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) {
+        h->status_h = nullptr;
+        return fail(h, QS_ERR_OOM, "qs_sync: pinned status word");
+    }
+    // the status word follows the stream's work, so one wait covers both
+    cudaError_t e = cudaMemcpyAsync(h->status_h, h->dv.status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qs_sync status copy");
+    e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "qs_sync");
-    int32_t st = 0;
-    e = cudaMemcpy(&st, h->dv.status, sizeof st, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(h, e, "qs_sync status read");
-    if (st & 1) return fail(h, QS_ERR_STATE_NONFINITE, "a drone state became non-finite");
+    if (*h->status_h & 1) return fail(h, QS_ERR_STATE_NONFINITE, "a drone state became non-finite");
     return QS_OK;
 }
 

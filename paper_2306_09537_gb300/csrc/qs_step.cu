@@ -478,7 +478,7 @@ constexpr int WS_SUB = 4;
 constexpr int WS_OBS_MAX = 18 + 6 * QS_MAX_K;
 
 struct WsShared {
-    float nrm[WS_SUB][4][32];  // motor-noise normals [substep][rotor][lane]
+    float nrm[2][WS_SUB][4][32];  // motor-noise normals [buffer][substep][rotor][lane]
     float st[18][32];          // x v R w of each lane after the step (post-collision)
     float sx[3][32];           // pair-pass staging: positions
     float sv[3][32];           //                    velocities
@@ -513,17 +513,17 @@ __device__ __forceinline__ WsMap ws_map(const Dev& dv, const Tile& tile, const i
 }
 
 // Noise warp: the motor-noise normals of the first WS_SUB substeps of the
-// step at Philox counter `tick`, into shared memory.
-__device__ __forceinline__ void ws_motor_normals(const Consts& c, WsShared& sh, const WsMap& m, uint32_t tick) {
+// step at Philox counter `tick`, into shared-memory buffer nb.
+__device__ __forceinline__ void ws_motor_normals(const Consts& c, WsShared& sh, const WsMap& m, uint32_t tick, int nb) {
     if (!m.act || !(c.flags & QS_F_MOTOR_NOISE)) return;
     const int nahead = min(c.substeps, WS_SUB);
     for (int sub = 0; sub < nahead; ++sub) {
         float n[4];
         motor_normals(c, tick, m.d, sub, n);
-        sh.nrm[sub][0][m.l] = n[0];
-        sh.nrm[sub][1][m.l] = n[1];
-        sh.nrm[sub][2][m.l] = n[2];
-        sh.nrm[sub][3][m.l] = n[3];
+        sh.nrm[nb][sub][0][m.l] = n[0];
+        sh.nrm[nb][sub][1][m.l] = n[1];
+        sh.nrm[nb][sub][2][m.l] = n[2];
+        sh.nrm[nb][sub][3][m.l] = n[3];
     }
 }
 
@@ -585,13 +585,14 @@ __device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, con
     }
 }
 
-// Dynamics warp: one control step of the lane's drone with command a. Meets
-// the noise warp at B1 (motor normals ready) and B2 (post-step state, goal and
+// Dynamics warp: one control step of the lane's drone with command a and the
+// motor normals of buffer nb. Meets the noise warp at B1 (motor normals ready)
+// and B2 (post-step state, goal and
 // neighbours published for the observation rows), then writes the knn record,
 // reward and done and ends the step. Every thread of the warp calls it.
 template <bool EXT>
 __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv, WsShared& sh, const WsMap& m, Drone& s,
-                                                 EnvRegs& er, uint32_t& ev_out, const float4 a,
+                                                 EnvRegs& er, uint32_t& ev_out, const float4 a, const int nb,
                                                  float* __restrict__ rew, uint8_t* __restrict__ done) {
     const int W = m.W, l = m.l, lane = m.lane, N = m.N, e = m.e, d = m.d, sbase = m.sbase;
     const bool act = m.act;
@@ -616,7 +617,8 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
         const float zero3[3] = {0.f, 0.f, 0.f};
         for (int sub = 0; sub < c.substeps; ++sub) {
             if (mnoise && sub < nahead) {
-                const float n[4] = {sh.nrm[sub][0][l], sh.nrm[sub][1][l], sh.nrm[sub][2][l], sh.nrm[sub][3][l]};
+                const float n[4] = {sh.nrm[nb][sub][0][l], sh.nrm[nb][sub][1][l], sh.nrm[nb][sub][2][l],
+                                    sh.nrm[nb][sub][3][l]};
                 ev |= substep(s, er.p, c, u, er.tick, d, sub, zero3, n);
             } else {
                 ev |= substep(s, er.p, c, u, er.tick, d, sub, zero3);
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
     if (threadIdx.x >= 32) {
         // ---------------- noise warp
         const uint32_t tick = m.act ? dv.tick[m.e] : 0u;  // warp 0 writes it only after B2
-        ws_motor_normals(c, sh, m, tick);
+        ws_motor_normals(c, sh, m, tick, 0);
         __syncthreads();  // B1
         float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
         if (m.act && io.obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, m.d, 0u, ex, evv, ew);
@@ -720,7 +722,7 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
         load_env<EXT>(er, c, dv, m.e);
         a = __ldg(reinterpret_cast<const float4*>(io.act) + m.d);
     }
-    ws_dynamics_step<EXT>(c, dv, sh, m, s, er, ev, a, io.rew, io.done);
+    ws_dynamics_step<EXT>(c, dv, sh, m, s, er, ev, a, 0, io.rew, io.done);
     if (!m.act) return;
     dv.ev[m.d] = ev;
     store_drone(s, dv.st, dv.D, m.d);
@@ -729,10 +731,10 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
 
 // Persistent warp-specialised rollout for latency-bound handles (every swarm
 // class at most 32 wide): one CTA per tile of 32 drone lanes runs steps
-// t0 .. t0 + nsteps - 1 with the drones in the dynamics warp's registers,
-// while the noise warp draws each step's sensor noise during the dynamics,
-// then stores that step's observation rows and draws the next step's motor
-// normals. The two warps meet at B1 and B2 of every step.
+// t0 .. t0 + nsteps - 1 with the drones in the dynamics warp's registers.
+// While the dynamics warp integrates step t, the noise warp draws step t's
+// sensor noise and step t + 1's motor normals (double-buffered), then stores
+// step t's observation rows. The two warps meet at B1 and B2 of every step.
 template <bool EXT>
 __global__ void __launch_bounds__(64) k_rollout_ws(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                    const int* __restrict__ perm, const RolloutIO io, const int t0,
@@ -744,16 +746,17 @@ __global__ void __launch_bounds__(64) k_rollout_ws(const Consts c, const Dev dv,
     if (threadIdx.x >= 32) {
         // ---------------- noise warp; the env's Philox counter advances by one per step
         const uint32_t tick0 = m.act ? dv.tick[m.e] : 0u;  // warp 0 writes it after the last step
-        ws_motor_normals(c, sh, m, tick0);
+        ws_motor_normals(c, sh, m, tick0, 0);
         for (int t = 0; t < nsteps; ++t) {
             const uint32_t tick = tick0 + (uint32_t)t;
             float* obs = io.obs ? io.obs + (size_t)(t0 + t) * D * c.obs_dim : nullptr;
-            __syncthreads();  // B1 of step t
+            __syncthreads();  // B1 of step t: buffer t & 1 holds step t's normals
             float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
             if (m.act && obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, m.d, 0u, ex, evv, ew);
+            // the other buffer was last read by the dynamics warp before B2 of step t - 1
+            if (t + 1 < nsteps) ws_motor_normals(c, sh, m, tick + 1, (t + 1) & 1);
             __syncthreads();  // B2 of step t
             if (obs) ws_store_obs(c, dv, tile, perm, sh, m, obs, ex, evv, ew);
-            if (t + 1 < nsteps) ws_motor_normals(c, sh, m, tick + 1);
         }
         return;
     }
@@ -770,7 +773,7 @@ __global__ void __launch_bounds__(64) k_rollout_ws(const Consts c, const Dev dv,
     for (int t = 0; t < nsteps; ++t) {
         const float4 a = a_next;
         if (m.act && t + 1 < nsteps) a_next = __ldg(act4 + (size_t)(t0 + t + 1) * D);
-        ws_dynamics_step<EXT>(c, dv, sh, m, s, er, ev, a, io.rew ? io.rew + (size_t)(t0 + t) * D : nullptr,
+        ws_dynamics_step<EXT>(c, dv, sh, m, s, er, ev, a, t & 1, io.rew ? io.rew + (size_t)(t0 + t) * D : nullptr,
                               io.done ? io.done + (size_t)(t0 + t) * E : nullptr);
     }
     if (!m.act) return;
