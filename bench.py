@@ -473,6 +473,27 @@ def profile_case(name, local):
             rew = torch.empty(T, env.D, device=dev)
             for _ in range(3):
                 env.rollout(acts, obs, rew, None)
+        elif name in ("rollout_ws", "scenario_rollout"):
+            # 8192 single-drone envs, or 2048 envs x 8 (K = 6) with every
+            # scenario type: 100-step rollouts in the handle's default shape
+            # (the warp-specialised rollout at these sizes)
+            wl = W.PLAIN if name == "rollout_ws" else W.SWARM
+            scn = () if name == "rollout_ws" else tuple(qs.SCENARIOS)
+            env = QuadSwarmEnv(wl.n_envs, wl.swarm, wl.k_neighbors, wl.features + ("auto_reset",), seed=2,
+                               weights=wl.weights, device=dev, stream=stream, scenarios=scn)
+            env.reset(2)
+            T = 100
+            acts = torch.from_numpy(W.actions(2, T, env.D)).to(dev)
+            obs = torch.empty(T, env.D, env.obs_dim, device=dev)
+            rew = torch.empty(T, env.D, device=dev)
+            for _ in range(3):
+                env.rollout(acts, obs, rew, None)
+        elif name == "call_large":  # per-call steps of 262,144 single-drone envs (HBM-bound form)
+            env = QuadSwarmEnv(262144, 1, 0, BENCH_FEATURES, seed=2, weights=WL.weights, device=dev, stream=stream)
+            env.reset(2)
+            acts = torch.from_numpy(W.actions(2, 8, env.D)).to(dev)
+            for t in range(8):
+                env.step(acts[t])
         elif name == "swarm_call":  # 2048 envs x 8, K = 6, per-call steps
             wl = W.SWARM
             env = QuadSwarmEnv(wl.n_envs, wl.swarm, wl.k_neighbors, wl.features, seed=3, weights=wl.weights,
@@ -502,7 +523,8 @@ def profile_case(name, local):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", choices=["rollout", "swarm_call", "adjoint"], default=None,
+    ap.add_argument("--profile-case", choices=["rollout", "rollout_ws", "scenario_rollout", "call_large", "swarm_call",
+                                               "adjoint"], default=None,
                     help="run one small case of a form (for ncu captures) and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
