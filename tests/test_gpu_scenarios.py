@@ -151,3 +151,48 @@ def test_diff_refuses_scenarios():
         qs.qs_diff_forward(env.h, 4, 2, torch.zeros(8, 30, device=DEV), torch.zeros(4, 8, 4, device=DEV),
                            torch.zeros(8, device=DEV), torch.zeros(1 << 16, dtype=torch.uint8, device=DEV))
     assert e.value.status == qs.QS_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("scenarios", [(), ALL])
+def test_partial_reset_matches_oracle(scenarios):
+    """qs_reset with an env mask after a few steps: the masked envs are
+    redrawn from key `seed` at their current Philox counter (parameters, goal,
+    scenario record, drones, episode step 0), the others keep their state and
+    counters, and the observation of every env follows (sensor-noise substream
+    1). Compared with the oracle's masked reset."""
+    sizes = [1, 2, 3, 8, 17, 32, 64, 128] * 3
+    env, o = pair(sizes, 6, FEATS, seed=31, scenarios=scenarios)
+    env.reset(31)
+    o.reset(31)
+    if scenarios:
+        share_records(env, o)
+    st, prm, goals = seeded_inputs(env, 31, sizes, spread=1.0)
+    set_both(env, o, st, prm, goals, ep=5, tick=9)
+    for t in range(3):
+        a = W.actions(31 + t, 1, env.D)[0]
+        env.step(torch.from_numpy(a).to(DEV))
+        o.step(a.astype(np.float64), want_obs=False)
+    mask = (np.arange(len(sizes)) % 3 != 1).astype(np.uint8)
+    obs = env.reset(77, torch.from_numpy(mask).to(DEV)).clone()
+    o.reset(77, mask)
+    g, s = gpu_state(env), o.get_state()
+    redrawn = mask.astype(bool)
+    eo = env_of(sizes)
+    dr = redrawn[eo]
+    # redrawn envs: the draw of a reset (binary32 vs binary64 arithmetic)
+    assert np.allclose(g["params"][redrawn], s["params"][redrawn], rtol=2e-7, atol=0)
+    assert np.abs(g["goals"][redrawn] - s["goals"][redrawn]).max() < 2e-6
+    assert np.abs(g["state"][dr, 0:18] - s["state"][dr, 0:18]).max() < 2e-6
+    assert np.allclose(g["state"][dr, 18:30], s["state"][dr, 18:30], rtol=2e-7, atol=0)
+    assert (g["ep_step"][redrawn] == 0).all()
+    # counters: a masked reset keeps every env's Philox counter
+    assert np.array_equal(g["tick"].astype(np.uint32), s["tick"])
+    assert np.array_equal(g["ep_step"], s["ep_step"])
+    if scenarios:
+        gr, orr = env.get_scenario().cpu().numpy(), o.get_scenario()
+        assert np.array_equal(gr[redrawn][:, INT_FIELDS], orr[redrawn][:, INT_FIELDS])
+        assert np.allclose(gr[redrawn], orr[redrawn], rtol=1e-6, atol=1e-6)
+        assert np.array_equal(gr[~redrawn], orr[~redrawn].astype(np.float32))
+    # the reset observation of the redrawn envs (the others' drift is chaotic)
+    oobs = o.observe()
+    assert np.allclose(obs.cpu().numpy()[dr], oobs[dr], rtol=1e-5, atol=2e-5)
