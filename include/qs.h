@@ -245,10 +245,11 @@ qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_
 
 /* Launch shape of qs_rollout: `block` threads per CTA of the persistent
  * kernel (32..256, a multiple of 32, at least the widest swarm class), or
- * QS_BLOCK_WARP_SPECIALISED (every class at most 32 wide; the default when
- * the handle also has at most about one wave of 32-drone CTAs): per 32 drones
- * one CTA whose dynamics warp integrates while a second warp draws the noise
- * and stores the observation rows, every step; `fuse` control steps per
+ * QS_BLOCK_WARP_SPECIALISED (every class at most 64 wide; the default when
+ * the handle also has at most about one wave of such CTAs): per 32 drones
+ * (64 when a class is wider than 32) one CTA whose dynamics warps integrate
+ * while as many noise warps draw the noise and store the observation rows,
+ * every step; `fuse` control steps per
  * launch (0 = all T steps in one launch), `use_graph` (0/1). Results do not
  * depend on the shape. Used by the autotuner. */
 qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t use_graph);

@@ -76,7 +76,7 @@ def tune(env, steps: int = 32, horizon: int = 64, reps: int = 3, apply: bool = T
             maxw = max(classes)
             for b in (qs.QS_BLOCK_WARP_SPECIALISED, 64, 128, 256):
                 if b == qs.QS_BLOCK_WARP_SPECIALISED:
-                    if maxw > 32:
+                    if maxw > 64:
                         continue
                 elif b < maxw:
                     continue

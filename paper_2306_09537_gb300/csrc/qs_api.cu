@@ -41,9 +41,10 @@ struct qs_env {
     // differentiable rollout: small CTAs (one or two warps), one tile each
     Tile* d_dtiles = nullptr;
     int n_dtiles = 0;
-    // warp-specialised rollout: tiles of 32 drone lanes (every class <= 32 wide)
+    // warp-specialised rollout: tiles of 32 ws_p drone lanes (every class <= 32 ws_p wide)
     Tile* d_wtiles = nullptr;
     int n_wtiles = 0;
+    int ws_p = 0;  // 1 or 2 dynamics warps per CTA; 0: a class is wider than 64
     int diff_block = 32;
     int rollout_block = 128;  // or QS_BLOCK_WARP_SPECIALISED
     int rollout_fuse = 0;   // control steps per launch (0: all T in one launch)
@@ -179,14 +180,17 @@ void build_rollout_tiles(qs_env* h, std::vector<Tile>& tiles, int block) {
     }
 }
 
-// Tiles of the warp-specialised rollout: 32 drone lanes per CTA, block 32 of
-// build_tiles for every class; none when a class is wider than 32.
+// Tiles of the warp-specialised rollout: 32P drone lanes per CTA (P = 1 when
+// every class is at most 32 wide, 2 when at most 64), slots of one class
+// each; none when a class is wider than 64.
 void build_ws_tiles(qs_env* h, std::vector<Tile>& tiles) {
     tiles.clear();
-    for (size_t ci = 0; ci < h->plan.size(); ++ci)
-        if (h->plan[ci].W > 32) return;
+    int maxW = 1;
+    for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
+    h->ws_p = maxW <= 32 ? 1 : maxW <= 64 ? 2 : 0;
+    if (!h->ws_p) return;
     for (size_t ci = 0; ci < h->plan.size(); ++ci) {
-        const int W = h->plan[ci].W, per = 32 / W;
+        const int W = h->plan[ci].W, per = 32 * h->ws_p / W;
         for (int s = 0; s < h->class_slots[ci]; s += per) {
             const int first = h->class_first_slot[ci] + s, count = std::min(per, h->class_slots[ci] - s);
             int contig = 1;
@@ -264,7 +268,8 @@ qs_status enqueue_rollout(qs_env* h, int T, const RolloutIO& io) {
     for (int t0 = 0; t0 < T; t0 += fuse) {
         const int n = std::min(fuse, T - t0);
         cudaError_t e = rollout_is_ws(h)
-                            ? launch_rollout_ws(h->c, h->dv, h->d_wtiles, h->n_wtiles, h->d_perm, io, t0, n, h->stream)
+                            ? launch_rollout_ws(h->c, h->dv, h->d_wtiles, h->n_wtiles, h->ws_p, h->d_perm, io, t0, n,
+                                                h->stream)
                             : launch_rollout(h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm,
                                              h->d_counter, io, t0, n, h->rollout_grid, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "rollout launch");
@@ -418,13 +423,13 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
             h->class_slots.push_back(n);
         }
     }
-    // the warp-specialised rollout while every class is at most 32 wide and the
+    // the warp-specialised rollout while every class is at most 64 wide and the
     // handle fits about one wave of its CTAs (latency-bound), else the
     // persistent kernel
     {
         int maxW = 1;
         for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
-        if (maxW <= 32 && (long)h->D <= ws_wave(n_sm)) h->rollout_block = QS_BLOCK_WARP_SPECIALISED;
+        if (maxW <= 64 && (long)h->D <= ws_wave(n_sm)) h->rollout_block = QS_BLOCK_WARP_SPECIALISED;
     }
 
     // one arena for the state
@@ -650,10 +655,10 @@ qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t u
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_set_rollout_shape: NULL handle");
     int maxW = 1;
     for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
-    const bool ws = block == QS_BLOCK_WARP_SPECIALISED && maxW <= 32;
+    const bool ws = block == QS_BLOCK_WARP_SPECIALISED && maxW <= 64;
     if (!ws && (block < 32 || block > 256 || block % 32 != 0 || block < maxW))
         return fail(h, QS_ERR_ARG, "qs_set_rollout_shape: block must be 32..256, a multiple of 32, >= the widest class, "
-                                   "or QS_BLOCK_WARP_SPECIALISED when every class is at most 32 wide");
+                                   "or QS_BLOCK_WARP_SPECIALISED when every class is at most 64 wide");
     if (fuse < 0) return fail(h, QS_ERR_ARG, "qs_set_rollout_shape: fuse must be >= 0");
     DeviceGuard g(h->device);
     cudaError_t e = cudaStreamSynchronize(h->stream);  // the old tables may be in use

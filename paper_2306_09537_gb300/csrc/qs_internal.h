@@ -119,9 +119,9 @@ cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, con
 // steps t0 .. t0+nsteps-1 of the io buffers. grid <= 0: one CTA per tile.
 cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int block, const int* perm,
                            int* counter, const RolloutIO& io, int t0, int nsteps, int grid, cudaStream_t s);
-// Warp-specialised rollout: one CTA of 64 threads per tile of 32 drone lanes
-// (every class at most 32 wide).
-cudaError_t launch_rollout_ws(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, const int* perm,
+// Warp-specialised rollout: one CTA of 64P threads per tile of 32P drone
+// lanes, P = 1 (every class at most 32 wide) or 2 (at most 64 wide).
+cudaError_t launch_rollout_ws(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int P, const int* perm,
                               const RolloutIO& io, int t0, int nsteps, cudaStream_t s);
 // CTAs of `block` threads the device keeps resident at once for k_rollout
 // (the instance with or without scenarios and downwash).

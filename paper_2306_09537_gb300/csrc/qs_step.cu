@@ -464,44 +464,59 @@ __global__ void __launch_bounds__(MAX_BLOCK, 2) k_rollout(const Consts c, const 
 }
 
 // ---------------------------------------------------------------- warp-specialised step
-// A CTA of 64 threads steps up to 32 drones (slots of width W <= 32 inside
-// warp 0). Warp 0 (dynamics) carries one drone per lane through the substeps
-// and the pair pass. Warp 1 (noise) draws the motor-noise normals of the
-// first WS_SUB substeps into shared memory ahead of the dynamics, then the
-// observation noise while the dynamics run, and finally assembles the
-// observation rows of the CTA's drones in shared memory and stores them; when
-// the CTA's drones are contiguous in memory the rows form one block written
-// with 16-byte stores. The warps meet at two CTA barriers: after the motor
-// normals (B1) and after warp 0 publishes the final states (B2). This takes
-// the Philox and Box-Muller work off each drone's dependent chain.
+// A CTA of 2P warps steps up to 32P drones: slots of width W <= 32P laid over
+// the drone lanes of warps 0 .. P-1 (dynamics), which carry one drone per lane
+// through the substeps and the pair pass. Warps P .. 2P-1 (noise) draw the
+// motor-noise normals of the first WS_SUB substeps into shared memory ahead of
+// the dynamics, then the observation noise while the dynamics run, and finally
+// assemble the observation rows of the CTA's drones in shared memory and store
+// them; when the CTA's drones are contiguous in memory the rows form one block
+// written with 16-byte stores. The two sides meet at two CTA barriers: after
+// the motor normals (B1) and after the dynamics warps publish the final states
+// (B2). This takes the Philox and Box-Muller work off each drone's dependent
+// chain. With P = 2 (swarms of 33..64) the dynamics warps also meet at named
+// barrier 1 between staging and reading each other's positions, and the noise
+// warps at named barrier 2 before storing the block of rows.
 constexpr int WS_SUB = 4;
 constexpr int WS_OBS_MAX = 18 + 6 * QS_MAX_K;
 
+template <int P>
 struct WsShared {
-    float nrm[2][WS_SUB][4][32];  // motor-noise normals [buffer][substep][rotor][lane]
-    float st[18][32];          // x v R w of each lane after the step (post-collision)
-    float sx[3][32];           // pair-pass staging: positions
-    float sv[3][32];           //                    velocities
-    float g[3][32];            // goal of each lane's drone
-    uint32_t key[32];          // swap keys
-    int nb[QS_MAX_K][32];      // CTA lane of each neighbour
-    int keff[32];
-    float rows[32 * WS_OBS_MAX];
+    float nrm[2][WS_SUB][4][32 * P];  // motor-noise normals [buffer][substep][rotor][drone lane]
+    float st[18][32 * P];             // x v R w of each drone lane after the step (post-collision)
+    float sx[3][32 * P];              // pair-pass staging: positions
+    float sv[3][32 * P];              //                    velocities
+    float g[3][32 * P];               // goal of each lane's drone
+    uint32_t key[32 * P];             // swap keys
+    int nb[QS_MAX_K][32 * P];         // CTA drone lane of each neighbour
+    int keff[32 * P];
+    float rows[32 * P * WS_OBS_MAX];
 };
 
-// Slot geometry of a warp-specialised CTA: lane l of each warp stands for
-// slot-local drone `lane` of slot `slot` (W lanes per slot, 32 per CTA).
+// Barrier among the P warps of one side (id 1: dynamics, id 2: noise); one
+// warp only needs its own lanes converged.
+template <int P>
+__device__ __forceinline__ void side_sync(int id) {
+    if (P == 1)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(32 * P) : "memory");
+}
+
+// Slot geometry of a warp-specialised CTA: drone lane L (0 .. 32P-1) of both
+// sides stands for slot-local drone `lane` of slot `slot` (W lanes per slot).
 struct WsMap {
-    int W, l, slot, lane, e, d0, N, d, sbase;
+    int W, L, slot, lane, e, d0, N, d, sbase;
     bool act;
 };
 
+template <int P>
 __device__ __forceinline__ WsMap ws_map(const Dev& dv, const Tile& tile, const int* __restrict__ perm) {
     WsMap m;
     m.W = tile.W;
-    m.l = threadIdx.x & 31;
-    m.slot = m.l / m.W;
-    m.lane = m.l - m.slot * m.W;
+    m.L = threadIdx.x & (32 * P - 1);
+    m.slot = m.L / m.W;
+    m.lane = m.L - m.slot * m.W;
     const bool ok = m.slot < tile.count;
     m.e = ok ? perm[tile.first + m.slot] : 0;
     m.d0 = ok ? dv.env_off[m.e] : 0;
@@ -512,56 +527,60 @@ __device__ __forceinline__ WsMap ws_map(const Dev& dv, const Tile& tile, const i
     return m;
 }
 
-// Noise warp: the motor-noise normals of the first WS_SUB substeps of the
+// Noise side: the motor-noise normals of the first WS_SUB substeps of the
 // step at Philox counter `tick`, into shared-memory buffer nb.
-__device__ __forceinline__ void ws_motor_normals(const Consts& c, WsShared& sh, const WsMap& m, uint32_t tick, int nb) {
+template <int P>
+__device__ __forceinline__ void ws_motor_normals(const Consts& c, WsShared<P>& sh, const WsMap& m, uint32_t tick,
+                                                 int nb) {
     if (!m.act || !(c.flags & QS_F_MOTOR_NOISE)) return;
     const int nahead = min(c.substeps, WS_SUB);
     for (int sub = 0; sub < nahead; ++sub) {
         float n[4];
         motor_normals(c, tick, m.d, sub, n);
-        sh.nrm[nb][sub][0][m.l] = n[0];
-        sh.nrm[nb][sub][1][m.l] = n[1];
-        sh.nrm[nb][sub][2][m.l] = n[2];
-        sh.nrm[nb][sub][3][m.l] = n[3];
+        sh.nrm[nb][sub][0][m.L] = n[0];
+        sh.nrm[nb][sub][1][m.L] = n[1];
+        sh.nrm[nb][sub][2][m.L] = n[2];
+        sh.nrm[nb][sub][3][m.L] = n[3];
     }
 }
 
-// Noise warp, after B2: the observation rows of the CTA's drones from the
+// Noise side, after B2: the observation rows of the CTA's drones from the
 // published post-step states plus sensor noise, assembled in shared memory and
 // stored to obs; when the CTA's drones are contiguous the rows form one block
 // written with 16-byte stores.
-__device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, const Tile& tile, const int* __restrict__ perm,
-                                             WsShared& sh, const WsMap& m, float* __restrict__ obs, const float ex[3],
-                                             const float evv[3], const float ew[3]) {
-    const int od = c.obs_dim, K = c.K, l = m.l;
+template <int P>
+__device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, const Tile& tile,
+                                             const int* __restrict__ perm, WsShared<P>& sh, const WsMap& m,
+                                             float* __restrict__ obs, const float ex[3], const float evv[3],
+                                             const float ew[3]) {
+    const int od = c.obs_dim, K = c.K, L = m.L;
     const bool contig = tile.pad != 0;
     const int d_first = dv.env_off[perm[tile.first]];
-    const int ridx = contig ? m.d - d_first : l;
+    const int ridx = contig ? m.d - d_first : L;
     if (m.act) {
         float* row = sh.rows + ridx * od;
-        row[0] = sh.st[0][l] - sh.g[0][l] + ex[0];
-        row[1] = sh.st[1][l] - sh.g[1][l] + ex[1];
-        row[2] = sh.st[2][l] - sh.g[2][l] + ex[2];
-        row[3] = sh.st[3][l] + evv[0];
-        row[4] = sh.st[4][l] + evv[1];
-        row[5] = sh.st[5][l] + evv[2];
-        for (int k = 6; k < 15; ++k) row[k] = sh.st[k][l];
-        row[15] = sh.st[15][l] + ew[0];
-        row[16] = sh.st[16][l] + ew[1];
-        row[17] = sh.st[17][l] + ew[2];
-        const int ke = sh.keff[l];
+        row[0] = sh.st[0][L] - sh.g[0][L] + ex[0];
+        row[1] = sh.st[1][L] - sh.g[1][L] + ex[1];
+        row[2] = sh.st[2][L] - sh.g[2][L] + ex[2];
+        row[3] = sh.st[3][L] + evv[0];
+        row[4] = sh.st[4][L] + evv[1];
+        row[5] = sh.st[5][L] + evv[2];
+        for (int k = 6; k < 15; ++k) row[k] = sh.st[k][L];
+        row[15] = sh.st[15][L] + ew[0];
+        row[16] = sh.st[16][L] + ew[1];
+        row[17] = sh.st[17][L] + ew[2];
+        const int ke = sh.keff[L];
         for (int k = 0; k < K; ++k) {
             float* on = row + 18 + 6 * k;
             if (k < ke) {
-                const int j = sh.nb[k][l];
-                for (int q = 0; q < 6; ++q) on[q] = sh.st[q][j] - sh.st[q][l];
+                const int j = sh.nb[k][L];
+                for (int q = 0; q < 6; ++q) on[q] = sh.st[q][j] - sh.st[q][L];
             } else {
                 for (int q = 0; q < 6; ++q) on[q] = 0.f;
             }
         }
     }
-    __syncwarp();
+    side_sync<P>(2);
     if (contig) {
         const int e_last = perm[tile.first + tile.count - 1];
         const int n_floats = (dv.env_off[e_last + 1] - d_first) * od;
@@ -570,13 +589,13 @@ __device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, con
             const int n4 = n_floats >> 2;
             const float4* src4 = reinterpret_cast<const float4*>(sh.rows);
             float4* dst4 = reinterpret_cast<float4*>(dst);
-            for (int i = l; i < n4; i += 32) dst4[i] = src4[i];
-            for (int i = (n4 << 2) + l; i < n_floats; i += 32) dst[i] = sh.rows[i];
+            for (int i = L; i < n4; i += 32 * P) dst4[i] = src4[i];
+            for (int i = (n4 << 2) + L; i < n_floats; i += 32 * P) dst[i] = sh.rows[i];
         } else {
             const int n2 = n_floats >> 1;  // obs rows hold an even number of floats
             const float2* src2 = reinterpret_cast<const float2*>(sh.rows);
             float2* dst2 = reinterpret_cast<float2*>(dst);
-            for (int i = l; i < n2; i += 32) dst2[i] = src2[i];
+            for (int i = L; i < n2; i += 32 * P) dst2[i] = src2[i];
         }
     } else if (m.act) {
         const float2* src2 = reinterpret_cast<const float2*>(sh.rows + ridx * od);
@@ -585,16 +604,16 @@ __device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, con
     }
 }
 
-// Dynamics warp: one control step of the lane's drone with command a and the
-// motor normals of buffer nb. Meets the noise warp at B1 (motor normals ready)
-// and B2 (post-step state, goal and
-// neighbours published for the observation rows), then writes the knn record,
-// reward and done and ends the step. Every thread of the warp calls it.
-template <bool EXT>
-__device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv, WsShared& sh, const WsMap& m, Drone& s,
-                                                 EnvRegs& er, uint32_t& ev_out, const float4 a, const int nb,
+// Dynamics side: one control step of the lane's drone with command a and the
+// motor normals of buffer nb. Meets the noise side at B1 (motor normals ready)
+// and B2 (post-step state, goal and neighbours published for the observation
+// rows), then writes the knn record, reward and done and ends the step. Every
+// thread of the dynamics warps calls it.
+template <bool EXT, int P>
+__device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv, WsShared<P>& sh, const WsMap& m,
+                                                 Drone& s, EnvRegs& er, uint32_t& ev_out, const float4 a, const int nb,
                                                  float* __restrict__ rew, uint8_t* __restrict__ done) {
-    const int W = m.W, l = m.l, lane = m.lane, N = m.N, e = m.e, d = m.d, sbase = m.sbase;
+    const int W = m.W, L = m.L, lane = m.lane, N = m.N, e = m.e, d = m.d, sbase = m.sbase;
     const bool act = m.act;
     const int K = c.K;
     const int nahead = min(c.substeps, WS_SUB);
@@ -617,8 +636,8 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
         const float zero3[3] = {0.f, 0.f, 0.f};
         for (int sub = 0; sub < c.substeps; ++sub) {
             if (mnoise && sub < nahead) {
-                const float n[4] = {sh.nrm[nb][sub][0][l], sh.nrm[nb][sub][1][l], sh.nrm[nb][sub][2][l],
-                                    sh.nrm[nb][sub][3][l]};
+                const float n[4] = {sh.nrm[nb][sub][0][L], sh.nrm[nb][sub][1][L], sh.nrm[nb][sub][2][L],
+                                    sh.nrm[nb][sub][3][L]};
                 ev |= substep(s, er.p, c, u, er.tick, d, sub, zero3, n);
             } else {
                 ev |= substep(s, er.p, c, u, er.tick, d, sub, zero3);
@@ -631,22 +650,22 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
     for (int k = 0; k < QS_MAX_K; ++k) best[k] = ~0ull;
     if (W > 1) {
         if (act) {
-            sh.sx[0][l] = s.x[0];
-            sh.sx[1][l] = s.x[1];
-            sh.sx[2][l] = s.x[2];
-            sh.sv[0][l] = s.v[0];
-            sh.sv[1][l] = s.v[1];
-            sh.sv[2][l] = s.v[2];
+            sh.sx[0][L] = s.x[0];
+            sh.sx[1][L] = s.x[1];
+            sh.sx[2][L] = s.x[2];
+            sh.sv[0][L] = s.v[0];
+            sh.sv[1][L] = s.v[1];
+            sh.sv[2][L] = s.v[2];
         }
-        __syncwarp();
+        side_sync<P>(1);
         float dvs[3] = {0.f, 0.f, 0.f};
         bool responded = false, dw_hit = false;
         float dw_az = 0.f;
         if (act && N > 1) {
             const bool coll = (c.flags & QS_F_COLLISIONS) && !(c.flags & QS_F_SMOOTH);
             const bool flag_coll = (c.flags & QS_F_COLLISIONS) != 0;
-            responded = pair_scan(c, s, er.p.thr, lane, N, sbase, &sh.sx[0][0], &sh.sv[0][0], 32, keff, coll, flag_coll,
-                                  ev, best, dvs, dw, dw_az, dw_hit);
+            responded = pair_scan(c, s, er.p.thr, lane, N, sbase, &sh.sx[0][0], &sh.sv[0][0], 32 * P, keff, coll,
+                                  flag_coll, ev, best, dvs, dw, dw_az, dw_hit);
         }
         if (responded) apply_response(c, s, er.tick, d, dvs);
         if (dw && dw_hit) apply_downwash(c, s, er.tick, d, dw_az);
@@ -661,27 +680,27 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
             if (act && swap_active(dv, er.sel, e, tau)) {
                 swp = true;
                 myk = swap_key(c, scn_seed(dv, er.sel, e), lane);
-                sh.key[l] = myk;
+                sh.key[L] = myk;
             }
-            __syncwarp();
+            side_sync<P>(1);
         }
         if (act) {
             const int slot = swp ? swap_rank(sh.key, sbase, N, lane, myk) : lane;
             scenario_goal(c, dv, er.sel, e, lane, N, tau, slot, gl, gl);
         }
     }
-    if (act) {  // publish the observed state (post-collision) for the noise warp
+    if (act) {  // publish the observed state (post-collision) for the noise side
         const float v18[18] = {s.x[0], s.x[1], s.x[2], s.v[0], s.v[1], s.v[2], s.R[0], s.R[1], s.R[2],
                                s.R[3], s.R[4], s.R[5], s.R[6], s.R[7], s.R[8], s.w[0], s.w[1], s.w[2]};
 #pragma unroll
-        for (int k = 0; k < 18; ++k) sh.st[k][l] = v18[k];
-        sh.g[0][l] = gl[0];
-        sh.g[1][l] = gl[1];
-        sh.g[2][l] = gl[2];
-        sh.keff[l] = W > 1 ? keff : 0;
+        for (int k = 0; k < 18; ++k) sh.st[k][L] = v18[k];
+        sh.g[0][L] = gl[0];
+        sh.g[1][L] = gl[1];
+        sh.g[2][L] = gl[2];
+        sh.keff[L] = W > 1 ? keff : 0;
 #pragma unroll
         for (int k = 0; k < QS_MAX_K; ++k)
-            if (k < keff) sh.nb[k][l] = sbase + (int)(best[k] & 0xffffffffu);
+            if (k < keff) sh.nb[k][L] = sbase + (int)(best[k] & 0xffffffffu);
     }
     __syncthreads();  // B2
     if (!act) return;
@@ -698,18 +717,18 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
 template <bool EXT>
 __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                 const int* __restrict__ perm, const StepIO io) {
-    __shared__ WsShared sh;
+    __shared__ WsShared<1> sh;
     const Tile tile = tiles[blockIdx.x];
-    const WsMap m = ws_map(dv, tile, perm);
+    const WsMap m = ws_map<1>(dv, tile, perm);
     if (threadIdx.x >= 32) {
         // ---------------- noise warp
         const uint32_t tick = m.act ? dv.tick[m.e] : 0u;  // warp 0 writes it only after B2
-        ws_motor_normals(c, sh, m, tick, 0);
+        ws_motor_normals<1>(c, sh, m, tick, 0);
         __syncthreads();  // B1
         float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
         if (m.act && io.obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, m.d, 0u, ex, evv, ew);
         __syncthreads();  // B2
-        if (io.obs) ws_store_obs(c, dv, tile, perm, sh, m, io.obs, ex, evv, ew);
+        if (io.obs) ws_store_obs<1>(c, dv, tile, perm, sh, m, io.obs, ex, evv, ew);
         return;
     }
     // ---------------- dynamics warp
@@ -722,7 +741,7 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
         load_env<EXT>(er, c, dv, m.e);
         a = __ldg(reinterpret_cast<const float4*>(io.act) + m.d);
     }
-    ws_dynamics_step<EXT>(c, dv, sh, m, s, er, ev, a, 0, io.rew, io.done);
+    ws_dynamics_step<EXT, 1>(c, dv, sh, m, s, er, ev, a, 0, io.rew, io.done);
     if (!m.act) return;
     dv.ev[m.d] = ev;
     store_drone(s, dv.st, dv.D, m.d);
@@ -730,37 +749,37 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
 }
 
 // Persistent warp-specialised rollout for latency-bound handles (every swarm
-// class at most 32 wide): one CTA per tile of 32 drone lanes runs steps
-// t0 .. t0 + nsteps - 1 with the drones in the dynamics warp's registers.
-// While the dynamics warp integrates step t, the noise warp draws step t's
+// class at most 32P wide): one CTA per tile of 32P drone lanes runs steps
+// t0 .. t0 + nsteps - 1 with the drones in the dynamics warps' registers.
+// While the dynamics side integrates step t, the noise side draws step t's
 // sensor noise and step t + 1's motor normals (double-buffered), then stores
-// step t's observation rows. The two warps meet at B1 and B2 of every step.
-template <bool EXT>
-__global__ void __launch_bounds__(64) k_rollout_ws(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
-                                                   const int* __restrict__ perm, const RolloutIO io, const int t0,
-                                                   const int nsteps) {
-    __shared__ WsShared sh;
+// step t's observation rows. The two sides meet at B1 and B2 of every step.
+template <bool EXT, int P>
+__global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_rollout_ws(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+                                                       const int* __restrict__ perm, const RolloutIO io, const int t0,
+                                                       const int nsteps) {
+    __shared__ WsShared<P> sh;
     const Tile tile = tiles[blockIdx.x];
-    const WsMap m = ws_map(dv, tile, perm);
+    const WsMap m = ws_map<P>(dv, tile, perm);
     const size_t D = dv.D, E = dv.E;
-    if (threadIdx.x >= 32) {
-        // ---------------- noise warp; the env's Philox counter advances by one per step
-        const uint32_t tick0 = m.act ? dv.tick[m.e] : 0u;  // warp 0 writes it after the last step
-        ws_motor_normals(c, sh, m, tick0, 0);
+    if (threadIdx.x >= 32 * P) {
+        // ---------------- noise side; the env's Philox counter advances by one per step
+        const uint32_t tick0 = m.act ? dv.tick[m.e] : 0u;  // the dynamics side writes it after the last step
+        ws_motor_normals<P>(c, sh, m, tick0, 0);
         for (int t = 0; t < nsteps; ++t) {
             const uint32_t tick = tick0 + (uint32_t)t;
             float* obs = io.obs ? io.obs + (size_t)(t0 + t) * D * c.obs_dim : nullptr;
             __syncthreads();  // B1 of step t: buffer t & 1 holds step t's normals
             float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
             if (m.act && obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, m.d, 0u, ex, evv, ew);
-            // the other buffer was last read by the dynamics warp before B2 of step t - 1
-            if (t + 1 < nsteps) ws_motor_normals(c, sh, m, tick + 1, (t + 1) & 1);
+            // the other buffer was last read by the dynamics side before B2 of step t - 1
+            if (t + 1 < nsteps) ws_motor_normals<P>(c, sh, m, tick + 1, (t + 1) & 1);
             __syncthreads();  // B2 of step t
-            if (obs) ws_store_obs(c, dv, tile, perm, sh, m, obs, ex, evv, ew);
+            if (obs) ws_store_obs<P>(c, dv, tile, perm, sh, m, obs, ex, evv, ew);
         }
         return;
     }
-    // ---------------- dynamics warp
+    // ---------------- dynamics side
     Drone s;
     EnvRegs er;
     uint32_t ev = 0;
@@ -773,8 +792,9 @@ __global__ void __launch_bounds__(64) k_rollout_ws(const Consts c, const Dev dv,
     for (int t = 0; t < nsteps; ++t) {
         const float4 a = a_next;
         if (m.act && t + 1 < nsteps) a_next = __ldg(act4 + (size_t)(t0 + t + 1) * D);
-        ws_dynamics_step<EXT>(c, dv, sh, m, s, er, ev, a, t & 1, io.rew ? io.rew + (size_t)(t0 + t) * D : nullptr,
-                              io.done ? io.done + (size_t)(t0 + t) * E : nullptr);
+        ws_dynamics_step<EXT, P>(c, dv, sh, m, s, er, ev, a, t & 1,
+                                 io.rew ? io.rew + (size_t)(t0 + t) * D : nullptr,
+                                 io.done ? io.done + (size_t)(t0 + t) * E : nullptr);
     }
     if (!m.act) return;
     dv.ev[m.d] = ev;
@@ -827,13 +847,23 @@ int rollout_grid(int block, bool ext) {
     return (occ > 0 ? occ : 1) * n_sm;
 }
 
-cudaError_t launch_rollout_ws(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, const int* perm,
+cudaError_t launch_rollout_ws(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int P, const int* perm,
                               const RolloutIO& io, int t0, int nsteps, cudaStream_t st) {
     if (n_tiles == 0) return cudaSuccess;
-    if (extended(c))
-        k_rollout_ws<true><<<n_tiles, 64, 0, st>>>(c, dv, tiles, perm, io, t0, nsteps);
-    else
-        k_rollout_ws<false><<<n_tiles, 64, 0, st>>>(c, dv, tiles, perm, io, t0, nsteps);
+    const bool ext = extended(c);
+    if (P == 1) {
+        if (ext)
+            k_rollout_ws<true, 1><<<n_tiles, 64, 0, st>>>(c, dv, tiles, perm, io, t0, nsteps);
+        else
+            k_rollout_ws<false, 1><<<n_tiles, 64, 0, st>>>(c, dv, tiles, perm, io, t0, nsteps);
+    } else if (P == 2) {
+        if (ext)
+            k_rollout_ws<true, 2><<<n_tiles, 128, 0, st>>>(c, dv, tiles, perm, io, t0, nsteps);
+        else
+            k_rollout_ws<false, 2><<<n_tiles, 128, 0, st>>>(c, dv, tiles, perm, io, t0, nsteps);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

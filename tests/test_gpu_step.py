@@ -378,13 +378,15 @@ def test_rollout_equals_steps():
 
 @pytest.mark.parametrize("shape", [None, (1, 0, True), (1, 5, False), (1, 1, True), (64, 0, False)])
 @pytest.mark.parametrize("extended", [False, True])
-def test_ws_rollout_equals_steps(shape, extended):
-    """Classes at most 32 wide: the warp-specialised persistent rollout (the
-    default for such handles; noise and observation rows on a second warp)
-    reproduces per-call steps across auto-reset episodes, also with the
-    scenario goals and downwash compiled in."""
+@pytest.mark.parametrize("widest", [32, 64])
+def test_ws_rollout_equals_steps(shape, extended, widest):
+    """Classes at most 64 wide: the warp-specialised persistent rollout (the
+    default for such handles; noise and observation rows on as many noise
+    warps as dynamics warps, one or two) reproduces per-call steps across
+    auto-reset episodes, also with the scenario goals and downwash compiled
+    in."""
     from paper_2306_09537_gb300 import qs
-    sizes = [1, 2, 3, 5, 8, 13, 16, 31, 32] * 6
+    sizes = [1, 2, 3, 5, 8, 13, 16, 31, 32] * 6 if widest == 32 else [1, 3, 8, 17, 33, 48, 64, 5, 32] * 4
     feats = FULL + ("auto_reset",) + (("downwash",) if extended else ())
     kw = dict(scenarios=("static", "swap", "pursuit_bezier", "swarm_vs_swarm")) if extended else {}
     env, _ = pair(sizes, 6, feats, seed=6, episode_steps=7, **kw)
@@ -412,7 +414,7 @@ def test_ws_rollout_equals_steps(shape, extended):
 
 def test_ws_rollout_needs_narrow_classes():
     from paper_2306_09537_gb300 import qs
-    env, _ = pair([4, 64], 2, FULL, seed=1)
+    env, _ = pair([4, 65], 2, FULL, seed=1)
     assert qs.qs_get_rollout_shape(env.h)[0] != qs.QS_BLOCK_WARP_SPECIALISED
     with pytest.raises(qs.QSError):
         qs.qs_set_rollout_shape(env.h, qs.QS_BLOCK_WARP_SPECIALISED, 0, 1)
