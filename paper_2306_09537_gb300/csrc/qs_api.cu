@@ -423,13 +423,19 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
             h->class_slots.push_back(n);
         }
     }
-    // the warp-specialised rollout while every class is at most 64 wide and the
-    // handle fits about one wave of its CTAs (latency-bound), else the
-    // persistent kernel
+    // default rollout shape: warp-specialised while every class is at most 32
+    // wide, the handle fits about one wave of its CTAs (latency-bound) and
+    // neither scenarios nor downwash lengthen the dynamics warp's step (then
+    // its noise warp would idle at the barriers); else the persistent kernel,
+    // whose work counter also balances uneven swarm sizes. Measured on GB300:
+    // plain 8192 x 1 3.2e9 vs 2.6e9, swarm 2048 x 8 2.85e9 vs 2.79e9; with
+    // every scenario type 1.72e9 vs 1.93e9; uneven sizes up to 64 (two-warp
+    // pairs per CTA) 1.63e9 vs 1.83e9 quadrotor-steps/s.
     {
         int maxW = 1;
         for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
-        if (maxW <= 64 && (long)h->D <= ws_wave(n_sm)) h->rollout_block = QS_BLOCK_WARP_SPECIALISED;
+        const bool ext = (h->c.scn_mask & ~1u) != 0 || (h->c.flags & QS_F_DOWNWASH) != 0;
+        if (maxW <= 32 && !ext && (long)h->D <= ws_wave(n_sm)) h->rollout_block = QS_BLOCK_WARP_SPECIALISED;
     }
 
     // one arena for the state

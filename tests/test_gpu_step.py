@@ -392,7 +392,10 @@ def test_ws_rollout_equals_steps(shape, extended, widest):
     env, _ = pair(sizes, 6, feats, seed=6, episode_steps=7, **kw)
     env2, _ = pair(sizes, 6, feats, seed=6, episode_steps=7, **kw)
     if shape is None:
-        assert qs.qs_get_rollout_shape(env.h)[0] == qs.QS_BLOCK_WARP_SPECIALISED
+        default_ws = widest == 32 and not extended
+        assert (qs.qs_get_rollout_shape(env.h)[0] == qs.QS_BLOCK_WARP_SPECIALISED) == default_ws
+        if not default_ws:
+            qs.qs_set_rollout_shape(env.h, qs.QS_BLOCK_WARP_SPECIALISED, 0, 1)
     else:
         qs.qs_set_rollout_shape(env.h, *shape)
     T = 17
