@@ -264,4 +264,35 @@ __device__ __forceinline__ void scenario_goal(const Consts& c, const Dev& dv, in
     for (int q = 0; q < 3; ++q) g[q] = fmaf(lam, off[q], scn_at(dv, sel, e, cen + q));
 }
 
+// A drone's goal carried in registers across the steps of a rollout, valid
+// for episode steps from <= tau < until (until = -1: empty). Static goals hold
+// for the whole episode; dynamic, swap and swarm-vs-swarm goals before and
+// from the switch step; the moving ones (shrink & expand, pursuit) for one
+// step. Keeps the per-step goal work, which diverges across the envs of a
+// warp, to the steps where a goal changes.
+struct GoalCache {
+    float g[3];
+    int from, until;
+};
+
+__device__ __forceinline__ bool goal_cached(const GoalCache& gc, int tau) { return tau >= gc.from && tau < gc.until; }
+
+__device__ __forceinline__ void goal_cache_set(GoalCache& gc, const Dev& dv, int sel, int e, int tau, const float g[3]) {
+    const int type = (int)scn_at(dv, sel, e, QS_R_TYPE);
+    const int tsw = (int)scn_at(dv, sel, e, QS_R_TSW);
+    int from = tau, until = tau + 1;
+    if (type == QS_SCN_SINGLE || type == QS_SCN_STATIC || type >= QS_NSCN_TYPES) {
+        from = 0;
+        until = 0x7fffffff;
+    } else if (type == QS_SCN_DYNAMIC || type == QS_SCN_SWAP || type == QS_SCN_SWARM_VS_SWARM) {
+        from = tau < tsw ? 0 : tsw;
+        until = tau < tsw ? tsw : 0x7fffffff;
+    }
+    gc.g[0] = g[0];
+    gc.g[1] = g[1];
+    gc.g[2] = g[2];
+    gc.from = from;
+    gc.until = until;
+}
+
 }  // namespace qsk

@@ -253,7 +253,7 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
                                           float* sx, float* sv, const bool act, const int lane, const int N,
                                           const int sbase, const int e, const int d, const float4 a,
                                           float* __restrict__ obs, float* __restrict__ rew, uint8_t* __restrict__ done,
-                                          const int observe_only) {
+                                          const int observe_only, GoalCache& gc) {
     const int nt = blockDim.x;
     const int K = c.K;
     const int keff = min(K, N - 1);
@@ -307,7 +307,7 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
             sv[threadIdx.x] = s.v[0];
             sv[nt + threadIdx.x] = s.v[1];
             sv[2 * nt + threadIdx.x] = s.v[2];
-            if (scn && swap_active(dv, er.sel, e, tau)) {
+            if (scn && !goal_cached(gc, tau) && swap_active(dv, er.sel, e, tau)) {
                 swp = true;
                 myk = swap_key(c, scn_seed(dv, er.sel, e), lane);
                 skey[threadIdx.x] = myk;
@@ -320,8 +320,15 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
     // ---- the drone's goal at the end of the step (Sec. III-D scenarios)
     float gl[3] = {er.g0, er.g1, er.g2};
     if (scn) {
-        const int slot = swp ? swap_rank(skey, sbase, N, lane, myk) : lane;
-        scenario_goal(c, dv, er.sel, e, lane, N, tau, slot, gl, gl);
+        if (goal_cached(gc, tau)) {
+            gl[0] = gc.g[0];
+            gl[1] = gc.g[1];
+            gl[2] = gc.g[2];
+        } else {
+            const int slot = swp ? swap_rank(skey, sbase, N, lane, myk) : lane;
+            scenario_goal(c, dv, er.sel, e, lane, N, tau, slot, gl, gl);
+            goal_cache_set(gc, dv, er.sel, e, tau, gl);
+        }
     }
 
     // ---- S12 observation
@@ -366,6 +373,7 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
     // ---- S13 reward and done
     if (rew) rew[d] = compute_reward(c, s, er, gl, fh, ev, best, W > 1 ? keff : 0);
     end_step<EXT>(c, dv, s, er, fh, lane, e, d, done);
+    if (scn && er.ep == 0) gc.until = -1;  // an auto-reset drew a new record
 }
 
 struct SlotMap {
@@ -404,8 +412,9 @@ __global__ void __launch_bounds__(MAX_BLOCK, (W == 1 ? 3 : 1)) k_step(const Cons
     }
     const float4 a = (m.act && !observe_only) ? __ldg(reinterpret_cast<const float4*>(io.act) + m.d)
                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+    GoalCache gc{{0.f, 0.f, 0.f}, 0, -1};
     step_body<EXT>(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d, a, io.obs,
-              io.rew, io.done, observe_only);
+              io.rew, io.done, observe_only, gc);
     if (!m.act || observe_only) return;
     dv.ev[m.d] = ev;
     store_drone(s, dv.st, dv.D, m.d);
@@ -430,12 +439,13 @@ __device__ __forceinline__ void rollout_tile(const Consts& c, const Dev& dv, con
     // the commands of step t + 1 are loaded while step t computes, so their
     // HBM latency leaves each step's dependent chain
     float4 a_next = m.act ? __ldg(act4 + (size_t)t0 * D) : make_float4(0.f, 0.f, 0.f, 0.f);
+    GoalCache gc{{0.f, 0.f, 0.f}, 0, -1};
     for (int t = t0; t < t0 + nsteps; ++t) {
         const float4 a = a_next;
         if (m.act && t + 1 < t0 + nsteps) a_next = __ldg(act4 + (size_t)(t + 1) * D);
         step_body<EXT>(W, c, dv, s, er, ev, sm, sm + 3 * blockDim.x, m.act, m.lane, m.N, m.sbase, m.e, m.d, a,
                        io.obs ? io.obs + (size_t)t * D * c.obs_dim : nullptr, io.rew ? io.rew + (size_t)t * D : nullptr,
-                       io.done ? io.done + (size_t)t * E : nullptr, 0);
+                       io.done ? io.done + (size_t)t * E : nullptr, 0, gc);
     }
     if (m.act) {
         dv.ev[m.d] = ev;
@@ -612,7 +622,7 @@ __device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, con
 template <bool EXT, int P>
 __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv, WsShared<P>& sh, const WsMap& m,
                                                  Drone& s, EnvRegs& er, uint32_t& ev_out, const float4 a, const int nb,
-                                                 float* __restrict__ rew, uint8_t* __restrict__ done) {
+                                                 float* __restrict__ rew, uint8_t* __restrict__ done, GoalCache& gc) {
     const int W = m.W, L = m.L, lane = m.lane, N = m.N, e = m.e, d = m.d, sbase = m.sbase;
     const bool act = m.act;
     const int K = c.K;
@@ -674,19 +684,25 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
     float gl[3] = {er.g0, er.g1, er.g2};
     if (EXT && (c.scn_mask & ~1u)) {
         const int tau = er.ep + 1;
+        const bool hit = goal_cached(gc, tau);  // the same for every lane of an env
         bool swp = false;
         uint32_t myk = 0;
         if (W > 1) {
-            if (act && swap_active(dv, er.sel, e, tau)) {
+            if (act && !hit && swap_active(dv, er.sel, e, tau)) {
                 swp = true;
                 myk = swap_key(c, scn_seed(dv, er.sel, e), lane);
                 sh.key[L] = myk;
             }
             side_sync<P>(1);
         }
-        if (act) {
+        if (act && hit) {
+            gl[0] = gc.g[0];
+            gl[1] = gc.g[1];
+            gl[2] = gc.g[2];
+        } else if (act) {
             const int slot = swp ? swap_rank(sh.key, sbase, N, lane, myk) : lane;
             scenario_goal(c, dv, er.sel, e, lane, N, tau, slot, gl, gl);
+            goal_cache_set(gc, dv, er.sel, e, tau, gl);
         }
     }
     if (act) {  // publish the observed state (post-collision) for the noise side
@@ -711,6 +727,7 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
     }
     if (rew) rew[d] = compute_reward(c, s, er, gl, fh, ev, best, W > 1 ? keff : 0);
     end_step<EXT>(c, dv, s, er, fh, lane, e, d, done);
+    if (EXT && er.ep == 0) gc.until = -1;  // an auto-reset drew a new record
     ev_out = ev;
 }
 
@@ -741,7 +758,8 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
         load_env<EXT>(er, c, dv, m.e);
         a = __ldg(reinterpret_cast<const float4*>(io.act) + m.d);
     }
-    ws_dynamics_step<EXT, 1>(c, dv, sh, m, s, er, ev, a, 0, io.rew, io.done);
+    GoalCache gc{{0.f, 0.f, 0.f}, 0, -1};
+    ws_dynamics_step<EXT, 1>(c, dv, sh, m, s, er, ev, a, 0, io.rew, io.done, gc);
     if (!m.act) return;
     dv.ev[m.d] = ev;
     store_drone(s, dv.st, dv.D, m.d);
@@ -789,12 +807,13 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_rollout_ws(const C
     }
     const float4* act4 = reinterpret_cast<const float4*>(io.act) + m.d;
     float4 a_next = m.act ? __ldg(act4 + (size_t)t0 * D) : make_float4(0.f, 0.f, 0.f, 0.f);
+    GoalCache gc{{0.f, 0.f, 0.f}, 0, -1};
     for (int t = 0; t < nsteps; ++t) {
         const float4 a = a_next;
         if (m.act && t + 1 < nsteps) a_next = __ldg(act4 + (size_t)(t0 + t + 1) * D);
         ws_dynamics_step<EXT, P>(c, dv, sh, m, s, er, ev, a, t & 1,
                                  io.rew ? io.rew + (size_t)(t0 + t) * D : nullptr,
-                                 io.done ? io.done + (size_t)(t0 + t) * E : nullptr);
+                                 io.done ? io.done + (size_t)(t0 + t) * E : nullptr, gc);
     }
     if (!m.act) return;
     dv.ev[m.d] = ev;
