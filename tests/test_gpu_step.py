@@ -518,3 +518,65 @@ def test_nonfinite_state_reported_by_sync():
     env.reset(2)
     env.step(torch.rand(16, 4, device=DEV))
     env.sync()
+
+
+# ----------------------------------------------------------------------------- full sizes
+def _one_step_through(env, o, acts, path):
+    """One control step of env through the per-call step or a one-step
+    rollout in the given shape; returns the outputs as check_step wants."""
+    from paper_2306_09537_gb300 import qs
+    a = torch.from_numpy(acts).to(DEV)
+    if path == "call":
+        obs, rew, done = env.step(a)
+    else:
+        qs.qs_set_rollout_shape(env.h, *path)
+        obs = torch.empty(1, env.D, env.obs_dim, device=DEV)
+        rew = torch.empty(1, env.D, device=DEV)
+        done = torch.empty(1, env.E, dtype=torch.uint8, device=DEV)
+        env.rollout(a[None], obs, rew, done)
+        obs, rew, done = obs[0], rew[0], done[0]
+    ev, knn = env.get_events(knn=True)
+    r = dict(obs=obs.cpu().numpy(), rew=rew.cpu().numpy(), done=done.cpu().numpy(),
+             ev=ev.cpu().numpy().astype(np.uint32), knn=knn.cpu().numpy().astype(np.int32), g=gpu_state(env))
+    r["oobs"], r["orew"], r["odone"] = o.step(acts.astype(np.float64), n_threads=8)
+    r["oev"], r["oknn"], _ = o.get_events()
+    r["margin"], r["margin_knn"] = o.margins()
+    r["os"] = o.get_state()
+    return r
+
+
+@pytest.mark.parametrize("wl_name,path", [
+    ("swarm_2048x8_k6", "call"), ("swarm_2048x8_k6", (1, 0, False)), ("swarm_2048x8_k6", (64, 0, True)),
+    ("uneven_4096", "call"), ("uneven_4096", (64, 0, True)), ("uneven_4096", (128, 0, False)),
+])
+def test_full_size_one_step_parity(wl_name, path):
+    """The swarm (2048 x 8, K = 6) and uneven (4096 envs, 40,408 drones)
+    workloads at full size, from the method's reset state, through the per-call
+    step and through one-step rollouts in the shapes the benchmark's autotuner
+    chooses between: the one-step bars against the oracle."""
+    wl = W.WORKLOADS[wl_name]
+    sizes = wl.sizes()
+    feats = FULL if "collisions" in wl.features else tuple(f for f in FULL if f != "collisions")
+    env, o = pair(sizes, wl.k_neighbors, feats, seed=wl.seed, weights=ALL_WEIGHTS)
+    o.reset(wl.seed)
+    s0 = o.get_state()  # the oracle's own reset, rounded to binary32, goes to both sides
+    set_both(env, o, s0["state"].astype(np.float32), s0["params"].astype(np.float32),
+             s0["goals"].astype(np.float32), ep=3, tick=11)
+    acts = W.actions(wl.seed, 1, env.D)[0]
+    r = _one_step_through(env, o, acts, path)
+    check_step(r, sizes)
+
+
+def test_max_swarm_and_k_bit_exact_knn():
+    """Swarms of the maximum size (128) with the maximum K (8) through the
+    per-call step and the persistent rollout: neighbour lists bit-exact."""
+    sizes = [128] * 24
+    env, o = pair(sizes, 8, FULL, seed=17, weights=ALL_WEIGHTS)
+    st, prm, goals = seeded_inputs(env, 17, sizes, spread=1.0)
+    set_both(env, o, st, prm, goals, ep=3, tick=11)
+    acts = W.actions(17, 1, env.D)[0]
+    r = _one_step_through(env, o, acts, "call")
+    check_step(r, sizes)
+    set_both(env, o, st, prm, goals, ep=3, tick=11)
+    r = _one_step_through(env, o, acts, (128, 0, True))
+    check_step(r, sizes)
