@@ -392,34 +392,37 @@ def run_forms(dev, stream, seed):
         env.close()
         del acts
 
-        # differentiable rollout: 1024 x 8, T = 128, checkpoints every 16, smooth contacts
+        # differentiable rollout: 1024 x 8, T = 128, checkpoints every 16, smooth
+        # contacts; and the same with the step's own (discrete) contacts
         wl = W.DIFF
-        env = QuadSwarmEnv(wl.n_envs, wl.swarm, wl.k_neighbors, wl.features, seed=seed, weights=wl.weights,
-                           device=dev, stream=stream)
-        env.reset(seed)
-        T, C = wl.horizon, wl.ckpt_every
-        x0 = env.get_state()["state"].contiguous()
-        acts = torch.from_numpy(W.actions(seed, T, env.D, lo=0.05, hi=0.95)).to(dev)
-        ws = torch.empty(qs.qs_diff_workspace_size(env.h, T, C), dtype=torch.uint8, device=dev)
-        loss = torch.empty(env.D, device=dev)
-        dl = torch.ones(env.D, device=dev)
-        ga = torch.empty_like(acts)
-        gx = torch.empty(env.D, 30, device=dev)
+        for name, feats in (("fwd_adjoint", wl.features),
+                            ("fwd_adjoint_discrete", ("dr", "motor_noise", "floor", "walls", "collisions"))):
+            env = QuadSwarmEnv(wl.n_envs, wl.swarm, wl.k_neighbors, feats, seed=seed, weights=wl.weights,
+                               device=dev, stream=stream)
+            env.reset(seed)
+            T, C = wl.horizon, wl.ckpt_every
+            x0 = env.get_state()["state"].contiguous()
+            acts = torch.from_numpy(W.actions(seed, T, env.D, lo=0.05, hi=0.95)).to(dev)
+            ws = torch.empty(qs.qs_diff_workspace_size(env.h, T, C), dtype=torch.uint8, device=dev)
+            loss = torch.empty(env.D, device=dev)
+            dl = torch.ones(env.D, device=dev)
+            ga = torch.empty_like(acts)
+            gx = torch.empty(env.D, 30, device=dev)
 
-        def fwd():
-            qs.qs_diff_forward(env.h, T, C, x0, acts, loss, ws)
+            def fwd():
+                qs.qs_diff_forward(env.h, T, C, x0, acts, loss, ws)
 
-        def fwd_bwd():
-            fwd()
-            qs.qs_diff_backward(env.h, T, C, acts, dl, ws, ga, gx)
-        fwd_bwd()
-        ms_f = _events_ms(fwd, stream, reps=3, flush=flush)
-        ms_fb = _events_ms(fwd_bwd, stream, reps=3, flush=flush)
-        forms["fwd_adjoint"] = {"value": env.D * T / ms_fb * 1e3, "ms_per_rollout": ms_fb, "T": T, "ckpt_every": C,
-                                "drones": env.D, "forward_only_value": env.D * T / ms_f * 1e3,
-                                "workspace_bytes": int(ws.numel())}
-        env.close()
-        del acts, ws
+            def fwd_bwd():
+                fwd()
+                qs.qs_diff_backward(env.h, T, C, acts, dl, ws, ga, gx)
+            fwd_bwd()
+            ms_f = _events_ms(fwd, stream, reps=3, flush=flush)
+            ms_fb = _events_ms(fwd_bwd, stream, reps=3, flush=flush)
+            forms[name] = {"value": env.D * T / ms_fb * 1e3, "ms_per_rollout": ms_fb, "T": T, "ckpt_every": C,
+                           "drones": env.D, "forward_only_value": env.D * T / ms_f * 1e3,
+                           "workspace_bytes": int(ws.numel()), "features": list(feats)}
+            env.close()
+            del acts, ws
 
         # env-count sweep of the batched plain form (1 drone per env)
         sweep = []
@@ -549,7 +552,8 @@ def main():
         f = line["forms"]
         # throughput of each form relative to the plain per-call GPU step (same binary32 accuracy)
         f["ratio_vs_plain_call"] = {k: f[k]["value"] / line["value"] for k in
-                                    ("plain_rollout", "swarm_call", "swarm_rollout", "uneven_batched", "fwd_adjoint")}
+                                    ("plain_rollout", "swarm_call", "swarm_rollout", "uneven_batched", "fwd_adjoint",
+                                     "fwd_adjoint_discrete")}
     if rank == 0:
         if not args.no_cpu_baseline:
             v, cores, sample = oracle_run(200)

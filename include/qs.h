@@ -256,25 +256,30 @@ qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_
 qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t use_graph);
 qs_status qs_get_rollout_shape(const qs_env* h, int32_t* block, int32_t* fuse, int32_t* use_graph);
 
-/* Differentiable rollout (smooth-contact form; the handle must be created with
- * QS_F_SMOOTH). The floor, walls, ceiling and quad-quad contacts of Sec. III-B
- * become softplus penalty accelerations k_c sp_beta(penetration)/m along the
- * contact normal, so the step is differentiable; motor noise stays a fixed
- * additive draw. From the initial drone states x0_dev [D][30] (state layout
- * above; the handle's parameters, goals and Philox counters; the handle's own
- * state is neither read nor changed) and commands actions_dev [T][D][4], the
- * forward pass writes the per-drone loss
+/* Differentiable rollout. From the initial drone states x0_dev [D][30] (state
+ * layout above; the handle's parameters, goals and Philox counters; the
+ * handle's own state is neither read nor changed) and commands actions_dev
+ * [T][D][4], the forward pass writes the per-drone loss
  *     loss_dev[d] = sum_{t=1..T} |x_d(t) - goal|^2 + 1e-3 |f^_d(t)|^2
  * and stores a checkpoint every ckpt_every control steps in the caller's
  * workspace_dev (qs_diff_workspace_size bytes, 16-byte aligned). The backward
  * pass takes dloss_dev [D] (d objective / d loss_dev[d]) and the same T,
  * ckpt_every, actions and workspace, recomputes each checkpoint segment's
  * substeps into the workspace and runs the hand-written adjoint of the whole
- * step (dynamics, integrator with re-orthonormalisation, smooth contacts),
- * writing grad_actions_dev [T][D][4] and grad_x0_dev [D][30] (zero for the
- * previous-command entries, which do not enter the loss). A handle created
- * with QS_F_DOWNWASH or with scenarios other than the single goal returns
- * QS_ERR_UNSUPPORTED: the smooth form has neither. */
+ * step (dynamics, integrator with re-orthonormalisation, contacts), writing
+ * grad_actions_dev [T][D][4] and grad_x0_dev [D][30] (zero for the
+ * previous-command entries, which do not enter the loss). Motor noise is a
+ * fixed additive draw. Two contact models:
+ *  - QS_F_SMOOTH: the floor, walls, ceiling and quad-quad contacts of
+ *    Sec. III-B become softplus penalty accelerations k_c sp_beta(pen)/m
+ *    along the contact normal, so the step is smooth;
+ *  - otherwise the contacts as the step runs them (floor friction and hit,
+ *    walls and ceiling, collisions with their perturbations); the gradient is
+ *    the derivative of the contact branch each decision took (the map is
+ *    piecewise smooth; resets that set a state component to a constant pass
+ *    no gradient through it).
+ * A handle created with QS_F_DOWNWASH or with scenarios other than the single
+ * goal returns QS_ERR_UNSUPPORTED. */
 qs_status qs_diff_workspace_size(const qs_env* h, int32_t T, int32_t ckpt_every, size_t* bytes);
 qs_status qs_diff_forward(qs_env* h, int32_t T, int32_t ckpt_every, const float* x0_dev, const float* actions_dev,
                           float* loss_dev, void* workspace_dev);

@@ -95,46 +95,10 @@ __device__ __forceinline__ void pair_vjp(const Consts& c, const float x[3], cons
     }
 }
 
-// Adjoint of the substep map of the smooth form. s: substep input (as saved);
-// l: in = lambda of the output state, out = lambda of the input state
-// (x v R w uf eps); la: lambda of the acceleration (for the pair exchange);
-// lu: accumulated lambda of the rotor-speed command u.
-__device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const Consts& c, const float u[4],
-                                            const float pacc[3], uint32_t tick, int d, int sub, float lx[3], float lv[3],
-                                            float lR[9], float lw[3], float luf[4], float leps[4], float la[3],
-                                            float lu[4]) {
-    const float dt = c.dt;
-    // ---- recompute the forward intermediates
-    float uf1[4], eps1[4], f[4];
-    for (int r = 0; r < 4; ++r) uf1[r] = fmaf(p.alag, u[r] - s.uf[r], s.uf[r]);
-    float nrm[4] = {0.f, 0.f, 0.f, 0.f};
-    if (c.flags & QS_F_MOTOR_NOISE) {
-        const uint4 q = philox_rk(tick, (uint32_t)d, ctr_word(TAG_MOTOR, (uint32_t)sub, 0), c.rk);
-        const float2 n01 = box_muller(u01(q.x), u01(q.y));
-        const float2 n23 = box_muller(u01(q.z), u01(q.w));
-        nrm[0] = n01.x; nrm[1] = n01.y; nrm[2] = n23.x; nrm[3] = n23.y;
-        for (int r = 0; r < 4; ++r) eps1[r] = fmaf(c.alpha_nd, s.eps[r], p.ans * nrm[r]);
-    } else {
-        for (int r = 0; r < 4; ++r) eps1[r] = s.eps[r];
-    }
-    for (int r = 0; r < 4; ++r) f[r] = fmaf(p.fmax * uf1[r], uf1[r], eps1[r]);
-    const float T = (f[0] + f[1]) + (f[2] + f[3]);
-    const float sa = p.arm * 0.70710678118654752f;
-    const float Iw[3] = {p.ixx * s.w[0], p.iyy * s.w[1], p.izz * s.w[2]};
-    const float tx = sa * ((f[0] + f[1]) - (f[2] + f[3]));
-    const float ty = sa * ((f[1] + f[2]) - (f[0] + f[3]));
-    const float tz = c.kappa * ((f[1] + f[3]) - (f[0] + f[2]));
-    const float wd[3] = {(tx - (s.w[1] * Iw[2] - s.w[2] * Iw[1])) * p.inv_ixx,
-                         (ty - (s.w[2] * Iw[0] - s.w[0] * Iw[2])) * p.inv_iyy,
-                         (tz - (s.w[0] * Iw[1] - s.w[1] * Iw[0])) * p.inv_izz};
-    // w' exactly as the forward computed it (compensated), and the clamp mask
-    float w1[3], pass[3];
-    for (int k = 0; k < 3; ++k) {
-        float hi = s.w[k], lo = s.wlo[k];
-        comp_add(hi, lo, wd[k] * dt);
-        pass[k] = fabsf(hi) > c.omega_max ? 0.f : 1.f;
-        w1[k] = fabsf(hi) > c.omega_max ? copysignf(c.omega_max, hi) : hi;
-    }
+// Adjoint of R' = B(R Q(w1)) (Q the polar factor of I + dt [w1]x, B one
+// Bjorck step): lR holds lambda of R' on entry and lambda of R on return;
+// lw1 receives lambda of w1 (added to its entry value).
+__device__ __forceinline__ void rotation_vjp(const float R[9], const float w1[3], float dt, float lR[9], float lw1[3]) {
     // M = R Q(w1)
     const float n2 = w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2];
     const float cc = __frsqrt_rn(fmaf(dt * dt, n2, 1.0f));
@@ -153,7 +117,7 @@ __device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const 
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
             float acc = 0.f;
-            for (int k = 0; k < 3; ++k) acc += s.R[3 * i + k] * Q[3 * k + j];
+            for (int k = 0; k < 3; ++k) acc += R[3 * i + k] * Q[3 * k + j];
             M[3 * i + j] = acc;
         }
 
@@ -194,7 +158,7 @@ __device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const 
             float a1 = 0.f, a2 = 0.f;
             for (int k = 0; k < 3; ++k) {
                 a1 += GM[3 * i + k] * Q[3 * j + k];
-                a2 += s.R[3 * k + i] * GM[3 * k + j];
+                a2 += R[3 * k + i] * GM[3 * k + j];
             }
             lRin[3 * i + j] = a1;
             GQ[3 * i + j] = a2;
@@ -225,9 +189,56 @@ __device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const 
     // dc/dw = -dt^2 c^3 w, da/dw = dt dc/dw, db/dw = dt^2 c (2 + c) / (1 + c)^2 dc/dw
     const float dcs = -dt * dt * cc * cc * cc;
     const float dadc = dt, dbdc = dt * dt * cc * (2.f + cc) / ((1.f + cc) * (1.f + cc));
-    float lw1[3];
     for (int k = 0; k < 3; ++k)
-        lw1[k] = lw[k] + qa * vG[k] + qb * vGW[k] + (gA * dadc + gB * dbdc) * dcs * w1[k];
+        lw1[k] += qa * vG[k] + qb * vGW[k] + (gA * dadc + gB * dbdc) * dcs * w1[k];
+    for (int k = 0; k < 9; ++k) lR[k] = lRin[k];
+}
+
+// Adjoint of the substep map of the smooth form. s: substep input (as saved);
+// l: in = lambda of the output state, out = lambda of the input state
+// (x v R w uf eps); la: lambda of the acceleration (for the pair exchange);
+// lu: accumulated lambda of the rotor-speed command u.
+__device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const Consts& c, const float u[4],
+                                            const float pacc[3], uint32_t tick, int d, int sub, float lx[3], float lv[3],
+                                            float lR[9], float lw[3], float luf[4], float leps[4], float la[3],
+                                            float lu[4]) {
+    const float dt = c.dt;
+    // ---- recompute the forward intermediates
+    float uf1[4], eps1[4], f[4];
+    for (int r = 0; r < 4; ++r) uf1[r] = fmaf(p.alag, u[r] - s.uf[r], s.uf[r]);
+    float nrm[4] = {0.f, 0.f, 0.f, 0.f};
+    if (c.flags & QS_F_MOTOR_NOISE) {
+        const uint4 q = philox_rk(tick, (uint32_t)d, ctr_word(TAG_MOTOR, (uint32_t)sub, 0), c.rk);
+        const float2 n01 = box_muller(u01(q.x), u01(q.y));
+        const float2 n23 = box_muller(u01(q.z), u01(q.w));
+        nrm[0] = n01.x; nrm[1] = n01.y; nrm[2] = n23.x; nrm[3] = n23.y;
+        for (int r = 0; r < 4; ++r) eps1[r] = fmaf(c.alpha_nd, s.eps[r], p.ans * nrm[r]);
+    } else {
+        for (int r = 0; r < 4; ++r) eps1[r] = s.eps[r];
+    }
+    for (int r = 0; r < 4; ++r) f[r] = fmaf(p.fmax * uf1[r], uf1[r], eps1[r]);
+    const float T = (f[0] + f[1]) + (f[2] + f[3]);
+    const float sa = p.arm * 0.70710678118654752f;
+    const float Iw[3] = {p.ixx * s.w[0], p.iyy * s.w[1], p.izz * s.w[2]};
+    const float tx = sa * ((f[0] + f[1]) - (f[2] + f[3]));
+    const float ty = sa * ((f[1] + f[2]) - (f[0] + f[3]));
+    const float tz = c.kappa * ((f[1] + f[3]) - (f[0] + f[2]));
+    const float wd[3] = {(tx - (s.w[1] * Iw[2] - s.w[2] * Iw[1])) * p.inv_ixx,
+                         (ty - (s.w[2] * Iw[0] - s.w[0] * Iw[2])) * p.inv_iyy,
+                         (tz - (s.w[0] * Iw[1] - s.w[1] * Iw[0])) * p.inv_izz};
+    // w' exactly as the forward computed it (compensated), and the clamp mask
+    float w1[3], pass[3];
+    for (int k = 0; k < 3; ++k) {
+        float hi = s.w[k], lo = s.wlo[k];
+        comp_add(hi, lo, wd[k] * dt);
+        pass[k] = fabsf(hi) > c.omega_max ? 0.f : 1.f;
+        w1[k] = fabsf(hi) > c.omega_max ? copysignf(c.omega_max, hi) : hi;
+    }
+    // R' = B(R Q(w1))
+    float lw1[3] = {lw[0], lw[1], lw[2]};
+    float lRin[9];
+    for (int k = 0; k < 9; ++k) lRin[k] = lR[k];
+    rotation_vjp(s.R, w1, dt, lRin, lw1);
     // w1 = clamp(w + wdot dt)
     float lwd[3];
     for (int k = 0; k < 3; ++k) {
@@ -275,11 +286,13 @@ __device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const 
 }
 
 // ---------------------------------------------------------------- workspace
-// [n_ckpt][NPLANE][D] float4 checkpoints, then [C * substeps][NSUB][D] floats.
+// [n_ckpt][NPLANE][D] float4 checkpoints, then [C * (substeps + 1)][NSUB][D]
+// floats (each substep's input and, for the discrete form, each step's
+// pre-collision state).
 size_t diff_workspace_bytes(int D, int T, int C, int substeps) {
     const int nck = (T + C - 1) / C;
     const size_t ck = (size_t)nck * NPLANE * D * sizeof(float4);
-    const size_t sc = (size_t)C * substeps * NSUB * D * sizeof(float);
+    const size_t sc = (size_t)C * (substeps + 1) * NSUB * D * sizeof(float);
     return ck + sc + 256;
 }
 
@@ -512,6 +525,434 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
     }
 }
 
+// ---------------------------------------------------------------- discrete contacts
+// The differentiable rollout of the step as the simulator runs it: floor,
+// wall and ceiling contacts and quadrotor collisions resolved at the substep
+// or step where they are detected (Sec. III-B). The map is piecewise smooth;
+// its derivative is the Jacobian of the branch each contact decision took
+// (a decision's threshold is met on a set of measure zero). Contact resets
+// whose outcome does not depend on the state (the floor hit zeroes the
+// velocity and body rates; a wall removes the normal velocity and holds the
+// drone on the boundary) pass no gradient through the reset components; the
+// perturbations are additive draws and drop out.
+
+// Adjoint of one discrete substep. s: substep input; the lambdas hold the
+// output's on entry and the input's on return; lu accumulates lambda of u.
+__device__ __forceinline__ void discrete_substep_vjp(const Drone& s, const Prm& p, const Consts& c, const float u[4],
+                                                     uint32_t tick, int d, int sub, float lx[3], float lv[3],
+                                                     float lR[9], float lw[3], float luf[4], float leps[4],
+                                                     float lu[4]) {
+    const float dt = c.dt, g = c.g;
+    // ---- the forward substep again, with its decisions (as in substep())
+    float uf1[4], eps1[4], f[4];
+    for (int r = 0; r < 4; ++r) uf1[r] = fmaf(p.alag, u[r] - s.uf[r], s.uf[r]);
+    if (c.flags & QS_F_MOTOR_NOISE) {
+        float n[4];
+        motor_normals(c, tick, d, sub, n);
+        for (int r = 0; r < 4; ++r) eps1[r] = fmaf(c.alpha_nd, s.eps[r], p.ans * n[r]);
+    } else {
+        for (int r = 0; r < 4; ++r) eps1[r] = s.eps[r];
+    }
+    for (int r = 0; r < 4; ++r) f[r] = fmaf(p.fmax * uf1[r], uf1[r], eps1[r]);
+    const float T = (f[0] + f[1]) + (f[2] + f[3]);
+    const float sa = p.arm * 0.70710678118654752f;
+    const float tx = sa * ((f[0] + f[1]) - (f[2] + f[3]));
+    const float ty = sa * ((f[1] + f[2]) - (f[0] + f[3]));
+    const float tz = c.kappa * ((f[1] + f[3]) - (f[0] + f[2]));
+    const float F0 = s.R[2] * T, F1 = s.R[5] * T, F2 = s.R[8] * T;
+    float a[3] = {F0 * p.inv_m, F1 * p.inv_m, fmaf(F2, p.inv_m, -g)};
+    const float mg = p.m * g;
+    const bool on_floor = (c.flags & QS_F_FLOOR) && s.x[2] <= 0.0f && F2 < mg;
+    const bool still = on_floor && s.v[0] == 0.0f && s.v[1] == 0.0f;
+    const float ffric = on_floor ? c.mu * (mg - F2) : 0.0f;
+    float nf = 0.f, keep = 0.f, vh[2] = {0.f, 0.f}, inv_nv = 0.f;
+    if (on_floor) {
+        float fx = F0, fy = F1;
+        if (still) {
+            nf = sqrtf(fx * fx + fy * fy);
+            keep = nf > ffric ? (nf - ffric) * __frcp_rn(nf) : 0.0f;
+            fx *= keep;
+            fy *= keep;
+        } else {
+            inv_nv = rsqrtf(s.v[0] * s.v[0] + s.v[1] * s.v[1]);
+            vh[0] = s.v[0] * inv_nv;
+            vh[1] = s.v[1] * inv_nv;
+            fx -= ffric * s.v[0] * inv_nv;
+            fy -= ffric * s.v[1] * inv_nv;
+        }
+        a[0] = fx * p.inv_m;
+        a[1] = fy * p.inv_m;
+        a[2] = 0.0f;
+    }
+    const float Iw[3] = {p.ixx * s.w[0], p.iyy * s.w[1], p.izz * s.w[2]};
+    const float wd[3] = {(tx - (s.w[1] * Iw[2] - s.w[2] * Iw[1])) * p.inv_ixx,
+                         (ty - (s.w[2] * Iw[0] - s.w[0] * Iw[2])) * p.inv_iyy,
+                         (tz - (s.w[0] * Iw[1] - s.w[1] * Iw[0])) * p.inv_izz};
+    float v1[3] = {fmaf(a[0], dt, s.v[0]), fmaf(a[1], dt, s.v[1]), fmaf(a[2], dt, on_floor ? 0.0f : s.v[2])};
+    const bool stop = on_floor && !still && (v1[0] * s.v[0] + v1[1] * s.v[1]) < 0.0f;
+    if (stop) v1[0] = v1[1] = 0.0f;
+    float x1[3] = {fmaf(v1[0], dt, s.x[0]), fmaf(v1[1], dt, s.x[1]), fmaf(v1[2], dt, s.x[2])};
+    float w1[3], pass[3];
+    for (int k = 0; k < 3; ++k) {
+        float hi = s.w[k], lo = s.wlo[k];
+        comp_add(hi, lo, wd[k] * dt);
+        pass[k] = fabsf(hi) > c.omega_max ? 0.f : 1.f;
+        w1[k] = fabsf(hi) > c.omega_max ? copysignf(c.omega_max, hi) : hi;
+    }
+    float R1[9];
+    for (int k = 0; k < 9; ++k) R1[k] = s.R[k];
+    rotate_polar(R1, w1, dt);
+    const bool hit = (c.flags & QS_F_FLOOR) && x1[2] <= 0.0f && v1[2] < 0.0f;
+    if (hit) {
+        x1[2] = 0.0f;
+        v1[0] = v1[1] = v1[2] = 0.0f;
+    }
+    bool clamp_x[3] = {false, false, false}, zero_v[3] = {false, false, false}, bump = false;
+    if (c.flags & QS_F_WALLS) {
+        const float lim[3] = {c.room_hx, c.room_hy, c.room_h};
+        for (int k = 0; k < 3; ++k) {
+            if (x1[k] > lim[k]) {
+                clamp_x[k] = true;
+                zero_v[k] = v1[k] > 0.0f;
+            } else if (k < 2 && x1[k] < -lim[k]) {
+                clamp_x[k] = true;
+                zero_v[k] = v1[k] < 0.0f;
+            }
+            bump |= zero_v[k];
+        }
+    }
+
+    // ---- reverse
+    // walls: v <- alpha_c (v + eps) after the outward components are removed; x held on the boundary
+    if (bump)
+        for (int k = 0; k < 3; ++k) lv[k] *= c.alpha_c;
+    for (int k = 0; k < 3; ++k) {
+        if (zero_v[k]) lv[k] = 0.0f;
+        if (clamp_x[k]) lx[k] = 0.0f;
+    }
+    // floor hit: x_z = 0, v = w = 0, R upright keeping the heading of R1's x-axis
+    if (hit) {
+        lx[2] = 0.0f;
+        lv[0] = lv[1] = lv[2] = 0.0f;
+        lw[0] = lw[1] = lw[2] = 0.0f;
+        const float lcs = lR[0] + lR[4], lsn = lR[3] - lR[1];
+        for (int k = 0; k < 9; ++k) lR[k] = 0.0f;
+        const float h2 = R1[0] * R1[0] + R1[3] * R1[3];
+        if (h2 >= 1e-12f) {  // cs = R0 / h, sn = R3 / h
+            const float ih = rsqrtf(h2), ih3 = ih * ih * ih;
+            lR[0] = (lcs * R1[3] * R1[3] - lsn * R1[0] * R1[3]) * ih3;
+            lR[3] = (lsn * R1[0] * R1[0] - lcs * R1[0] * R1[3]) * ih3;
+        } else {  // cs = R4 / h, sn = -R1 / h
+            const float ih = rsqrtf(R1[1] * R1[1] + R1[4] * R1[4]), ih3 = ih * ih * ih;
+            lR[1] = (-lcs * R1[1] * R1[4] - lsn * R1[4] * R1[4]) * ih3;
+            lR[4] = (lcs * R1[1] * R1[1] + lsn * R1[1] * R1[4]) * ih3;
+        }
+    }
+    // R1 = B(R Q(w1))
+    float lw1[3] = {lw[0], lw[1], lw[2]};
+    rotation_vjp(s.R, w1, dt, lR, lw1);
+    // w1 = clamp(w + wdot dt)
+    float lwd[3];
+    for (int k = 0; k < 3; ++k) {
+        const float gk = lw1[k] * pass[k];
+        lw[k] = gk;
+        lwd[k] = gk * dt;
+    }
+    // x1 = x + v1 dt; the stop rule; v1 = v + a dt (v_z first set to 0 on the floor)
+    float lv1[3];
+    for (int k = 0; k < 3; ++k) lv1[k] = lv[k] + dt * lx[k];
+    if (stop) lv1[0] = lv1[1] = 0.0f;
+    float la[3];
+    for (int k = 0; k < 3; ++k) {
+        la[k] = dt * lv1[k];
+        lv[k] = lv1[k];
+    }
+    if (on_floor) lv[2] = 0.0f;
+    // Euler: lambda_tau = mu, lambda_w -= (I w) x mu + I (mu x w)
+    const float mu[3] = {lwd[0] * p.inv_ixx, lwd[1] * p.inv_iyy, lwd[2] * p.inv_izz};
+    const float c1[3] = {Iw[1] * mu[2] - Iw[2] * mu[1], Iw[2] * mu[0] - Iw[0] * mu[2], Iw[0] * mu[1] - Iw[1] * mu[0]};
+    const float c2[3] = {mu[1] * s.w[2] - mu[2] * s.w[1], mu[2] * s.w[0] - mu[0] * s.w[2], mu[0] * s.w[1] - mu[1] * s.w[0]};
+    lw[0] -= c1[0] + p.ixx * c2[0];
+    lw[1] -= c1[1] + p.iyy * c2[1];
+    lw[2] -= c1[2] + p.izz * c2[2];
+    // acceleration from the world thrust F = R e_z T (with floor friction on the floor)
+    float lF[3];
+    if (!on_floor) {
+        for (int k = 0; k < 3; ++k) lF[k] = la[k] * p.inv_m;
+    } else {
+        const float lf0 = la[0] * p.inv_m, lf1 = la[1] * p.inv_m;  // a_z = 0 on the floor
+        if (still) {
+            if (keep > 0.0f) {  // f = F_xy (1 - ffric / nf), ffric = mu (m g - F_z)
+                const float q = (F0 * lf0 + F1 * lf1) * __frcp_rn(nf);
+                lF[0] = keep * lf0 + ffric * F0 * q * __frcp_rn(nf * nf);
+                lF[1] = keep * lf1 + ffric * F1 * q * __frcp_rn(nf * nf);
+                lF[2] = c.mu * q;
+            } else {
+                lF[0] = lF[1] = lF[2] = 0.0f;
+            }
+        } else {  // f = F_xy - ffric v / |v|
+            lF[0] = lf0;
+            lF[1] = lf1;
+            const float q = vh[0] * lf0 + vh[1] * lf1;
+            lF[2] = c.mu * q;
+            lv[0] -= ffric * inv_nv * (lf0 - vh[0] * q);
+            lv[1] -= ffric * inv_nv * (lf1 - vh[1] * q);
+        }
+    }
+    const float lT = lF[0] * s.R[2] + lF[1] * s.R[5] + lF[2] * s.R[8];
+    lR[2] += T * lF[0];
+    lR[5] += T * lF[1];
+    lR[8] += T * lF[2];
+    // motors (as in the smooth form)
+    const float gx = mu[0] * sa, gy = mu[1] * sa, gz = mu[2] * c.kappa;
+    const float lf[4] = {lT + gx - gy - gz, lT + gx + gy + gz, lT - gx + gy - gz, lT - gx - gy + gz};
+    for (int r = 0; r < 4; ++r) {
+        const float luf1 = luf[r] + 2.f * p.fmax * uf1[r] * lf[r];
+        const float leps1 = leps[r] + lf[r];
+        leps[r] = (c.flags & QS_F_MOTOR_NOISE) ? c.alpha_nd * leps1 : leps1;
+        luf[r] = (1.f - p.alag) * luf1;
+        lu[r] += p.alag * luf1;
+    }
+}
+
+// The collision pass of a control step (S9, S10) as the step kernels run it:
+// positions and pre-collision velocities staged in shared memory (sx, sv:
+// [3][nt]). Every thread of the CTA calls it.
+__device__ __forceinline__ void discrete_collisions(const Consts& c, Drone& s, const Prm& p, uint32_t tick, int d,
+                                                    bool act, float* sx, float* sv, int nt, int sbase, int lane, int N) {
+    if (act) {
+        sx[threadIdx.x] = s.x[0];
+        sx[nt + threadIdx.x] = s.x[1];
+        sx[2 * nt + threadIdx.x] = s.x[2];
+        sv[threadIdx.x] = s.v[0];
+        sv[nt + threadIdx.x] = s.v[1];
+        sv[2 * nt + threadIdx.x] = s.v[2];
+    }
+    __syncthreads();
+    float dvs[3] = {0.f, 0.f, 0.f};
+    bool responded = false;
+    if (act && N > 1) {
+        uint32_t ev = 0;
+        uint64_t best[QS_MAX_K];
+        float az = 0.f;
+        bool dwh = false;
+        responded = pair_scan(c, s, p.thr, lane, N, sbase, sx, sv, nt, 0, true, true, ev, best, dvs, false, az, dwh);
+    }
+    __syncthreads();
+    if (responded) apply_response(c, s, tick, d, dvs);
+}
+
+// Adjoint of the collision pass: xs, vs the pre-collision position and
+// velocity of the thread's drone (as staged: sx, sv), sl the lambda of every
+// drone's post-collision velocity. For a responding drone i,
+//   v_i' = alpha_c (v_i + sum_j ((v_j - v_i) . n_ij) n_ij + eps),
+//   n_ij = (x_i - x_j) / d_ij,
+// so lambda_v_i = alpha_c (lambda_v_i' + sum_j n n^T (lambda_v_j' - lambda_v_i'))
+// and lambda_x_i += sum_j alpha_c / d P ((n . q) (v_j - v_i) + vn q) with
+// q = lambda_v_i' - lambda_v_j', P = I - n n^T, vn = (v_j - v_i) . n
+// (the partner relation is symmetric, so every partner also responded).
+__device__ __forceinline__ void collision_vjp(const Consts& c, const float xs[3], const float vs[3], float thr,
+                                              const float* sx, const float* sv, const float* sl, int nt, int sbase,
+                                              int lane, int N, float lx[3], float lv[3]) {
+    const float l0[3] = {lv[0], lv[1], lv[2]};
+    float acc_v[3] = {0.f, 0.f, 0.f}, acc_x[3] = {0.f, 0.f, 0.f};
+    bool responded = false;
+    for (int j = 0; j < N; ++j) {
+        if (j == lane) continue;
+        const int tj = sbase + j;
+        float dx, dy, dz;
+        const float key = pair_key(xs[0], xs[1], xs[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx, dy, dz);
+        if (!(key < thr)) continue;
+        const float rv0 = vs[0] - sv[tj], rv1 = vs[1] - sv[nt + tj], rv2 = vs[2] - sv[2 * nt + tj];
+        if (!(-(rv0 * dx + rv1 * dy + rv2 * dz) < 0.0f)) continue;  // approaching
+        responded = true;
+        float n[3] = {0.f, 0.f, 1.f}, inv = 0.f;
+        if (key > 0.0f) {
+            inv = rsqrtf(key);
+            n[0] = -dx * inv;
+            n[1] = -dy * inv;
+            n[2] = -dz * inv;
+        }
+        const float q[3] = {l0[0] - sl[tj], l0[1] - sl[nt + tj], l0[2] - sl[2 * nt + tj]};
+        const float nq = n[0] * q[0] + n[1] * q[1] + n[2] * q[2];
+        for (int k = 0; k < 3; ++k) acc_v[k] -= n[k] * nq;
+        if (key > 0.0f) {
+            const float dv[3] = {-rv0, -rv1, -rv2};  // v_j - v_i
+            const float vn = dv[0] * n[0] + dv[1] * n[1] + dv[2] * n[2];
+            float y[3];
+            for (int k = 0; k < 3; ++k) y[k] = nq * dv[k] + vn * q[k];
+            const float ny = n[0] * y[0] + n[1] * y[1] + n[2] * y[2];
+            for (int k = 0; k < 3; ++k) acc_x[k] += (y[k] - ny * n[k]) * inv;
+        }
+    }
+    if (responded) {
+        for (int k = 0; k < 3; ++k) {
+            lv[k] = c.alpha_c * (l0[k] + acc_v[k]);
+            lx[k] += c.alpha_c * acc_x[k];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+                                                             const int* __restrict__ perm, const DiffArgs a) {
+    extern __shared__ float sm[];
+    const Tile tile = tiles[blockIdx.x];
+    const int W = tile.W, nt = blockDim.x;
+    const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
+    const bool ok = slot < tile.count;
+    const int e = ok ? perm[tile.first + slot] : 0;
+    const int d0 = ok ? dv.env_off[e] : 0, N = ok ? dv.env_off[e + 1] - d0 : 0;
+    const bool act = lane < N;
+    const int d = d0 + lane, sbase = slot * W;
+    const size_t D = dv.D;
+    const bool coll = (c.flags & QS_F_COLLISIONS) != 0;
+    Drone s;
+    Prm p;
+    float g[3] = {0.f, 0.f, 0.f};
+    uint32_t tick0 = 0;
+    if (act) {
+        read_x0(s, a.x0, d);
+        p = load_prm(dv.prm, dv.E, e);
+        g[0] = dv.goal[e];
+        g[1] = dv.goal[dv.E + e];
+        g[2] = dv.goal[2 * dv.E + e];
+        tick0 = dv.tick[e];
+    }
+    const float zero3[3] = {0.f, 0.f, 0.f};
+    float L = 0.f;
+    for (int t = 0; t < a.T; ++t) {
+        if (act && t % a.C == 0) {
+            float4 q[NPLANE];
+            pack(s, q);
+            float4* ck = a.ckpt + (size_t)(t / a.C) * NPLANE * D;
+            for (int pl = 0; pl < NPLANE; ++pl) ck[(size_t)pl * D + d] = q[pl];
+        }
+        float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4];
+        if (act) {
+            command4(c, a.act, D, t, d, fh, u, msk);
+            for (int sub = 0; sub < c.substeps; ++sub) substep(s, p, c, u, tick0 + t, d, sub, zero3);
+        }
+        if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sm, sm + 3 * nt, nt, sbase, lane, N);
+        if (act) {
+            const float dx = s.x[0] - g[0], dy = s.x[1] - g[1], dz = s.x[2] - g[2];
+            L += dx * dx + dy * dy + dz * dz + 1e-3f * (fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
+        }
+    }
+    if (act) {
+        a.loss[d] = L;
+        if (!finite_state(s)) atomicOr(dv.status, 1);
+    }
+}
+
+__global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+                                                             const int* __restrict__ perm, const DiffArgs a) {
+    extern __shared__ float sm[];
+    const Tile tile = tiles[blockIdx.x];
+    const int W = tile.W, nt = blockDim.x;
+    const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
+    const bool ok = slot < tile.count;
+    const int e = ok ? perm[tile.first + slot] : 0;
+    const int d0 = ok ? dv.env_off[e] : 0, N = ok ? dv.env_off[e + 1] - d0 : 0;
+    const bool act = lane < N;
+    const int d = d0 + lane, sbase = slot * W;
+    const size_t D = dv.D;
+    const bool coll = (c.flags & QS_F_COLLISIONS) != 0;
+    float* sx = sm;            // [3][nt] positions
+    float* sv = sm + 3 * nt;   // [3][nt] velocities
+    float* sl = sm + 6 * nt;   // [3][nt] lambda of the post-collision velocity
+    Prm p;
+    float g[3] = {0.f, 0.f, 0.f};
+    uint32_t tick0 = 0;
+    float dl = 0.f;
+    if (act) {
+        p = load_prm(dv.prm, dv.E, e);
+        g[0] = dv.goal[e];
+        g[1] = dv.goal[dv.E + e];
+        g[2] = dv.goal[2 * dv.E + e];
+        tick0 = dv.tick[e];
+        dl = a.dloss[d];
+    }
+    float lx[3] = {0.f, 0.f, 0.f}, lv[3] = {0.f, 0.f, 0.f}, lR[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float lw[3] = {0.f, 0.f, 0.f}, luf[4] = {0.f, 0.f, 0.f, 0.f}, leps[4] = {0.f, 0.f, 0.f, 0.f};
+    const int S = c.substeps, S1 = c.substeps + 1;  // saved states per step: each substep's input, then the pre-collision state
+    const float zero3[3] = {0.f, 0.f, 0.f};
+    const int nseg = (a.T + a.C - 1) / a.C;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int tb = seg * a.C, te = min(a.T, tb + a.C);
+        // recompute the segment, saving every substep input and each step's pre-collision state
+        Drone s;
+        if (act) {
+            float4 q[NPLANE];
+            const float4* ck = a.ckpt + (size_t)seg * NPLANE * D;
+            for (int pl = 0; pl < NPLANE; ++pl) q[pl] = ck[(size_t)pl * D + d];
+            unpack(s, q);
+        }
+        for (int t = tb; t < te; ++t) {
+            float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4];
+            if (act) {
+                command4(c, a.act, D, t, d, fh, u, msk);
+                for (int sub = 0; sub < S; ++sub) {
+                    save_sub(a.scratch, D, (t - tb) * S1 + sub, d, s);
+                    substep(s, p, c, u, tick0 + t, d, sub, zero3);
+                }
+                save_sub(a.scratch, D, (t - tb) * S1 + S, d, s);
+            }
+            if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sx, sv, nt, sbase, lane, N);
+        }
+        // reverse through the segment
+        for (int t = te - 1; t >= tb; --t) {
+            float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4] = {0.f, 0.f, 0.f, 0.f};
+            Drone sc;
+            if (act) {
+                command4(c, a.act, D, t, d, fh, u, msk);
+                load_sub(a.scratch, D, (t - tb) * S1 + S, d, sc);
+                // loss of step t: |x(t) - g|^2 + 1e-3 |f^|^2 (the collision pass leaves x unchanged)
+                for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (sc.x[k] - g[k]);
+            }
+            if (coll) {
+                if (act) {
+                    sx[threadIdx.x] = sc.x[0];
+                    sx[nt + threadIdx.x] = sc.x[1];
+                    sx[2 * nt + threadIdx.x] = sc.x[2];
+                    sv[threadIdx.x] = sc.v[0];
+                    sv[nt + threadIdx.x] = sc.v[1];
+                    sv[2 * nt + threadIdx.x] = sc.v[2];
+                    sl[threadIdx.x] = lv[0];
+                    sl[nt + threadIdx.x] = lv[1];
+                    sl[2 * nt + threadIdx.x] = lv[2];
+                }
+                __syncthreads();
+                if (act && N > 1) collision_vjp(c, sc.x, sc.v, p.thr, sx, sv, sl, nt, sbase, lane, N, lx, lv);
+                __syncthreads();
+            }
+            float lu[4] = {0.f, 0.f, 0.f, 0.f};
+            if (act) {
+                for (int sub = S - 1; sub >= 0; --sub) {
+                    Drone si;
+                    load_sub(a.scratch, D, (t - tb) * S1 + sub, d, si);
+                    discrete_substep_vjp(si, p, c, u, tick0 + t, d, sub, lx, lv, lR, lw, luf, leps, lu);
+                }
+                float ga[4];
+                for (int r = 0; r < 4; ++r) {
+                    const float du = u[r] > 0.f ? 0.5f / u[r] : 0.f;
+                    ga[r] = msk[r] * (lu[r] * du + dl * 2e-3f * fh[r]);
+                }
+                reinterpret_cast<float4*>(a.grad_act + (size_t)t * D * 4)[d] = make_float4(ga[0], ga[1], ga[2], ga[3]);
+            }
+        }
+    }
+    if (act) {
+        float* gx = a.grad_x0 + (size_t)d * QS_STATE_DIM;
+        for (int k = 0; k < 3; ++k) gx[k] = lx[k];
+        for (int k = 0; k < 3; ++k) gx[3 + k] = lv[k];
+        for (int k = 0; k < 9; ++k) gx[6 + k] = lR[k];
+        for (int k = 0; k < 3; ++k) gx[15 + k] = lw[k];
+        for (int k = 0; k < 4; ++k) gx[18 + k] = luf[k];
+        for (int k = 0; k < 4; ++k) gx[22 + k] = leps[k];
+        for (int k = 0; k < 4; ++k) gx[26 + k] = 0.f;  // f^_prev does not enter the loss
+    }
+}
+
 cudaError_t launch_diff(int backward, const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int block,
                         const int* perm, const float* x0, const float* act, float* loss, const float* dloss,
                         float* grad_act, float* grad_x0, void* workspace, int T, int C, cudaStream_t st) {
@@ -527,9 +968,14 @@ cudaError_t launch_diff(int backward, const Consts& c, const Dev& dv, const Tile
     const int nck = (T + C - 1) / C;
     a.ckpt = reinterpret_cast<float4*>(workspace);
     a.scratch = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + (size_t)nck * NPLANE * dv.D * sizeof(float4));
-    const size_t smem = sizeof(float) * 6 * block;
-    if (backward) k_diff_bwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
-    else k_diff_fwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
+    const size_t smem = sizeof(float) * 9 * block;
+    if (c.flags & QS_F_SMOOTH) {
+        if (backward) k_diff_bwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
+        else k_diff_fwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
+    } else {
+        if (backward) k_diffd_bwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
+        else k_diffd_fwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
+    }
     return cudaGetLastError();
 }
 

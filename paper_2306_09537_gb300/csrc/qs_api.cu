@@ -677,8 +677,6 @@ qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t u
 
 static qs_status diff_check(qs_env* h, const char* who, int32_t T, int32_t C) {
     if (!h) return fail(nullptr, QS_ERR_ARG, std::string(who) + ": NULL handle");
-    if (!(h->cfg.flags & QS_F_SMOOTH))
-        return fail(h, QS_ERR_ARG, std::string(who) + ": the handle must be created with QS_F_SMOOTH");
     if (h->cfg.flags & QS_F_DOWNWASH)
         return fail(h, QS_ERR_UNSUPPORTED, std::string(who) + ": the differentiable rollout has no downwash term");
     if (h->c.scn_mask & ~1u)

@@ -84,65 +84,6 @@ __device__ __forceinline__ int swap_rank(const uint32_t* skey, int sbase, int N,
     return slot;
 }
 
-// Inserts cand into the ascending list best[0..K).
-__device__ __forceinline__ void topk_insert(uint64_t best[QS_MAX_K], int K, uint64_t cand) {
-#pragma unroll
-    for (int k = 0; k < QS_MAX_K; ++k) {
-        if (k < K && cand < best[k]) {
-            const uint64_t t = best[k];
-            best[k] = cand;
-            cand = t;
-        }
-    }
-}
-
-// S9 + S11 for the thread's drone (slot-local index `lane`) against the slot's
-// staged positions / pre-collision velocities (planes of stride nt): collision
-// flag, the Jacobi sum of ((v_j - v_i).n) n over colliding approaching
-// partners (S10), and the sorted neighbour list.
-__device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float thr, int lane, int N, int sbase,
-                                          const float* sx, const float* sv, int nt, int keff, bool coll, bool flag_coll,
-                                          uint32_t& ev, uint64_t best[QS_MAX_K], float dvs[3], const bool dw,
-                                          float& dw_az, bool& dw_hit) {
-    bool responded = false;
-    for (int j = 0; j < N; ++j) {
-        if (j == lane) continue;
-        const int tj = sbase + j;
-        float dx, dy, dz;
-        const float key = pair_key(s.x[0], s.x[1], s.x[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx, dy, dz);
-        // downwash: j overlaps this drone from above (horizontal distance below
-        // l_i + l_j, height difference in (0, dw_h))
-        if (dw && __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) < thr && dz > 0.0f && dz < c.dw_h) {
-            dw_az -= c.dw_k1 * fmaf(c.dw_k2, dz, c.dw_b1);
-            dw_hit = true;
-        }
-        if (flag_coll && key < thr) {
-            ev |= EV_HIT_QUAD;
-            if (coll) {
-                // approaching iff (v_i - v_j) . (x_i - x_j) < 0
-                const float rv0 = s.v[0] - sv[tj], rv1 = s.v[1] - sv[nt + tj], rv2 = s.v[2] - sv[2 * nt + tj];
-                const float app = -(rv0 * dx + rv1 * dy + rv2 * dz);
-                if (app < 0.0f) {
-                    float n0 = 0.f, n1 = 0.f, n2 = 1.f;
-                    if (key > 0.0f) {
-                        const float inv = rsqrtf(key);
-                        n0 = -dx * inv;
-                        n1 = -dy * inv;
-                        n2 = -dz * inv;
-                    }
-                    const float vn = -(rv0 * n0 + rv1 * n1 + rv2 * n2);  // (v_j - v_i) . n
-                    dvs[0] = fmaf(vn, n0, dvs[0]);
-                    dvs[1] = fmaf(vn, n1, dvs[1]);
-                    dvs[2] = fmaf(vn, n2, dvs[2]);
-                    responded = true;
-                }
-            }
-        }
-        if (keff > 0) topk_insert(best, keff, ((uint64_t)__float_as_uint(key) << 32) | (uint32_t)j);
-    }
-    return responded;
-}
-
 // Downwash over the control step (duration substeps * dt): v_z += T az plus
 // acceleration noise, w += T * angular-acceleration noise.
 __device__ __forceinline__ void apply_downwash(const Consts& c, Drone& s, uint32_t tick, int d, float az) {
@@ -155,18 +96,6 @@ __device__ __forceinline__ void apply_downwash(const Consts& c, Drone& s, uint32
     comp_add(s.w[0], s.wlo[0], Tc * c.dw_sw * n[3]);
     comp_add(s.w[1], s.wlo[1], Tc * c.dw_sw * n[4]);
     comp_add(s.w[2], s.wlo[2], Tc * c.dw_sw * n[5]);
-}
-
-// S10: v <- alpha_c (v + sum + eps_v), w <- w + eps_w for a responding drone.
-__device__ __forceinline__ void apply_response(const Consts& c, Drone& s, uint32_t tick, int d, const float dvs[3]) {
-    float n[6];
-    six_normals(c, tick, (uint32_t)d, TAG_COLL, 0, n);
-    s.v[0] = c.alpha_c * (s.v[0] + dvs[0] + c.sig_cv * n[0]);
-    s.v[1] = c.alpha_c * (s.v[1] + dvs[1] + c.sig_cv * n[1]);
-    s.v[2] = c.alpha_c * (s.v[2] + dvs[2] + c.sig_cv * n[2]);
-    comp_add(s.w[0], s.wlo[0], c.sig_cw * n[3]);
-    comp_add(s.w[1], s.wlo[1], c.sig_cw * n[4]);
-    comp_add(s.w[2], s.wlo[2], c.sig_cw * n[5]);
 }
 
 // S13 reward of one drone (Sec. III-E): weighted state terms, event indicators

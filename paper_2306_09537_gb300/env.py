@@ -99,8 +99,9 @@ class QuadSwarmEnv:
 
 
 class RolloutFn(torch.autograd.Function):
-    """Differentiable rollout of the smooth-contact step (the env must be
-    created with the "smooth" feature): loss[d] = sum_t |x_d(t) - goal|^2 +
+    """Differentiable rollout of the step (smooth contacts when the env has the
+    "smooth" feature, else the contacts as the step runs them, differentiated
+    along the branch each contact decision took): loss[d] = sum_t |x_d(t) - goal|^2 +
     1e-3 |f^_d(t)|^2 for commands actions [T][D][4] from initial states
     x0 [D][30]. The forward pass stores a checkpoint every `ckpt_every` steps
     in a workspace it allocates from torch; backward recomputes each segment

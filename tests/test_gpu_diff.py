@@ -142,10 +142,10 @@ def test_rollout_fn_autograd():
     assert np.allclose(x0.grad.cpu().numpy(), 2.0 * gx, rtol=0, atol=0)
 
 
-def test_diff_requires_smooth_handle():
+def test_diff_rejects_bad_horizons():
     env, _ = pair([1] * 4, 0, ("floor",), seed=1)
     with pytest.raises(qs.QSError):
-        qs.qs_diff_forward(env.h, 4, 2, torch.zeros(4, 30, device=DEV), torch.zeros(4, 4, 4, device=DEV),
+        qs.qs_diff_forward(env.h, 0, 2, torch.zeros(4, 30, device=DEV), torch.zeros(1, 4, 4, device=DEV),
                            torch.zeros(4, device=DEV), torch.zeros(1 << 16, dtype=torch.uint8, device=DEV))
 
 
@@ -156,3 +156,94 @@ def test_diff_rejects_downwash():
         qs.qs_diff_forward(env.h, 4, 2, torch.zeros(8, 30, device=DEV), torch.zeros(4, 8, 4, device=DEV),
                            torch.zeros(8, device=DEV), torch.zeros(1 << 16, dtype=torch.uint8, device=DEV))
     assert e.value.status == qs.QS_ERR_UNSUPPORTED
+
+
+# ----------------------------------------------------------------------------- discrete contacts
+DISCRETE = ("floor", "walls", "collisions", "motor_noise")
+
+
+def discrete_case(seed):
+    """1 env x 3 drones whose 12 steps take every contact branch: drone 0 falls
+    onto the floor (hit, then resting with friction), drone 1 flies into the
+    +x wall, drone 2 catches up with drone 1 and collides with it."""
+    env, o = pair([3], 0, DISCRETE, seed=seed)
+    st = W.random_states(seed, 3, rate=0.5)
+    st[0, 0:6] = [0.0, 0.0, 0.02, 0.3, -0.2, -1.5]
+    st[1, 0:6] = [4.965, 1.0, 5.0, 1.0, 0.0, 0.0]
+    st[2, 0:6] = [4.852, 1.0, 5.0, 2.6, 0.0, 0.0]
+    prm = W.random_params(seed, 1, nominal(env))
+    goals = np.array([[1.0, -1.0, 3.0]], np.float32)
+    z = np.zeros(1, np.int32)
+    env.set_state(params=torch.from_numpy(prm).to(DEV), goals=torch.from_numpy(goals).to(DEV),
+                  ep_step=torch.from_numpy(z).to(DEV), tick=torch.from_numpy(z).to(DEV))
+    acts = W.actions(seed, 12, 3, lo=0.2, hi=0.8)
+    return env, o, st, prm, goals, acts
+
+
+def test_discrete_case_takes_every_branch():
+    """The oracle run of the case hits the floor, rests on it, hits a wall and
+    collides, with every decision well away from its threshold."""
+    env, o, st, prm, goals, acts = discrete_case(5)
+    o.set_state(st.astype(np.float64), prm.astype(np.float64), goals.astype(np.float64), np.zeros(1, np.int32),
+                np.zeros(1, np.uint32))
+    seen = 0
+    for t in range(acts.shape[0]):
+        o.step(acts[t].astype(np.float64), want_obs=False)
+        ev, _, _ = o.get_events()
+        seen |= int(np.bitwise_or.reduce(ev))
+    for bit in (O.EV_HIT_FLOOR, O.EV_ON_FLOOR, O.EV_HIT_WALL, O.EV_HIT_QUAD):
+        assert seen & bit, bit
+    margin, _ = o.margins()
+    assert margin.min() > 1e-4
+
+
+def test_discrete_forward_loss_matches_oracle():
+    env, o, st, prm, goals, acts = discrete_case(5)
+    loss, _, _ = gpu_grads(env, st, acts, 4)
+    want = oracle_total(o, st.astype(np.float64), prm.astype(np.float64), goals.astype(np.float64),
+                        acts.astype(np.float64))
+    assert np.allclose(loss, want, rtol=1e-4, atol=1e-4)
+
+
+def test_discrete_adjoint_matches_oracle_finite_differences():
+    """Every command and every initial-state entry of the discrete-contact case
+    against central differences of the FP64 oracle (h = 1e-6; a coordinate
+    whose differences at h and 2h disagree, i.e. whose perturbation flips a
+    contact decision, is left out; at most 5% may be): 1e-3 relative or 1e-4
+    of the largest entry."""
+    T, C = 12, 4
+    env, o, st, prm, goals, acts = discrete_case(5)
+    _, ga, gx = gpu_grads(env, st, acts, C)
+    st64, prm64, g64, a64 = (v.astype(np.float64) for v in (st, prm, goals, acts))
+
+    def fd(perturb, h):
+        p_, m_ = perturb(h), perturb(-h)
+        return (oracle_total(o, *p_).sum() - oracle_total(o, *m_).sum()) / (2 * h)
+
+    got, ref, ok = [], [], []
+    for t in range(T):
+        for d in range(3):
+            for r in range(4):
+                def pa(h, t=t, d=d, r=r):
+                    a2 = a64.copy()
+                    a2[t, d, r] += h
+                    return st64, prm64, g64, a2
+                f1, f2 = fd(pa, 1e-6), fd(pa, 2e-6)
+                got.append(ga[t, d, r]), ref.append(f1), ok.append(abs(f1 - f2) <= 1e-4 * (1 + abs(f1)))
+    for d in range(3):
+        for k in range(26):
+            def px(h, d=d, k=k):
+                s2 = st64.copy()
+                s2[d, k] += h
+                return s2, prm64, g64, a64
+            f1, f2 = fd(px, 1e-6), fd(px, 2e-6)
+            got.append(gx[d, k]), ref.append(f1), ok.append(abs(f1 - f2) <= 1e-4 * (1 + abs(f1)))
+    got, ref, ok = np.array(got), np.array(ref), np.array(ok)
+    assert ok.mean() >= 0.95
+    scale = np.abs(ref[ok]).max()
+    err = np.abs(got[ok] - ref[ok])
+    assert np.all(err <= 1e-3 * np.abs(ref[ok]) + 1e-4 * scale), err.max() / scale
+    assert np.all(gx[:, 26:] == 0)
+    # the gradient through the floor-hit reset: the fallen drone's initial
+    # height and vertical speed no longer reach its later positions
+    assert np.abs(ref).max() > 0
