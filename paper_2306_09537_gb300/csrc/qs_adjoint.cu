@@ -166,7 +166,7 @@ __device__ __forceinline__ void rotation_vjp(const float R[9], const float w1[3]
     // Q(w1) = I + qa W + qb W^2: lambda_w1 from Q
     //  <G, [dw]x> = dw . vex(G),  vex(G) = (G21 - G12, G02 - G20, G10 - G01)
     //  <G, [dw]x W + W [dw]x> = dw . vex(-(G W) - (W G))   (W^T = -W)
-    float GW[9], WG[9];
+    float GW[9];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
             float a1 = 0.f, a2 = 0.f;
@@ -175,9 +175,7 @@ __device__ __forceinline__ void rotation_vjp(const float R[9], const float w1[3]
                 a2 += Wm[3 * i + k] * GQ[3 * k + j];
             }
             GW[3 * i + j] = -(a1 + a2);
-            WG[3 * i + j] = 0.f;
         }
-    (void)WG;
     const float vG[3] = {GQ[7] - GQ[5], GQ[2] - GQ[6], GQ[3] - GQ[1]};
     const float vGW[3] = {GW[7] - GW[5], GW[2] - GW[6], GW[3] - GW[1]};
     float gA = 0.f, gB = 0.f;
@@ -199,7 +197,7 @@ __device__ __forceinline__ void rotation_vjp(const float R[9], const float w1[3]
 // (x v R w uf eps); la: lambda of the acceleration (for the pair exchange);
 // lu: accumulated lambda of the rotor-speed command u.
 __device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const Consts& c, const float u[4],
-                                            const float pacc[3], uint32_t tick, int d, int sub, float lx[3], float lv[3],
+                                            uint32_t tick, int d, int sub, float lx[3], float lv[3],
                                             float lR[9], float lw[3], float luf[4], float leps[4], float la[3],
                                             float lu[4]) {
     const float dt = c.dt;
@@ -281,8 +279,6 @@ __device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const 
         luf[r] = (1.f - p.alag) * luf1;
         lu[r] += p.alag * luf1;
     }
-    (void)pacc;
-    (void)wacc;
 }
 
 // ---------------------------------------------------------------- workspace
@@ -485,10 +481,9 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
                     sx[2 * nt + threadIdx.x] = si.x[2];
                 }
                 __syncthreads();
-                float pa[3] = {0.f, 0.f, 0.f}, la[3] = {0.f, 0.f, 0.f};
+                float la[3] = {0.f, 0.f, 0.f};
                 if (act) {
-                    pair_acc(c, si.x, sx, nt, sbase, lane, N, p.arm, pa);
-                    substep_vjp(si, p, c, u, pa, tick0 + t, d, sub, lx, lv, lR, lw, luf, leps, la, lu);
+                    substep_vjp(si, p, c, u, tick0 + t, d, sub, lx, lv, lR, lw, luf, leps, la, lu);
                     sla[threadIdx.x] = la[0];
                     sla[nt + threadIdx.x] = la[1];
                     sla[2 * nt + threadIdx.x] = la[2];
