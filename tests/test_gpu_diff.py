@@ -247,3 +247,19 @@ def test_discrete_adjoint_matches_oracle_finite_differences():
     # the gradient through the floor-hit reset: the fallen drone's initial
     # height and vertical speed no longer reach its later positions
     assert np.abs(ref).max() > 0
+
+
+def test_rollout_fn_discrete_contacts():
+    """RolloutFn on a handle with the discrete contacts: torch.autograd
+    gradients equal the library's forward/backward entry points."""
+    from paper_2306_09537_gb300.env import RolloutFn
+    env, o, st, prm, goals, acts = discrete_case(5)
+    T = acts.shape[0]
+    a = torch.from_numpy(acts).to(DEV).requires_grad_(True)
+    x0 = torch.from_numpy(st).to(DEV).requires_grad_(True)
+    loss = RolloutFn.apply(a, x0, env, 4)
+    loss.sum().backward()
+    l_ref, ga, gx = gpu_grads(env, st, acts, 4)
+    assert np.allclose(loss.detach().cpu().numpy(), l_ref, rtol=0, atol=0)
+    assert np.array_equal(a.grad.cpu().numpy().astype(np.float64), ga)
+    assert np.array_equal(x0.grad.cpu().numpy().astype(np.float64), gx)
