@@ -28,6 +28,11 @@
  *    QS_ERR_CUDA. Errors detected on the device (a non-finite state) set a
  *    status word that qs_sync() reports. qs_last_error() gives a message.
  *  - Floating point is binary32 throughout the device path.
+ *  - A handle is used by one host thread at a time; distinct handles are
+ *    independent (apart from qs_diff_grad_static's shared array).
+ *  - Results do not depend on launch shapes (qs_set_block,
+ *    qs_set_rollout_shape): the same state, parameters and commands give the
+ *    same bits through qs_step, qs_step_host and qs_rollout.
  *
  * Layouts (row-major, contiguous):
  *  actions  [D][4]            per-rotor normalised commands (16-byte aligned)
