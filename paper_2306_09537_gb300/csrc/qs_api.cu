@@ -59,7 +59,8 @@ struct qs_env {
     // device staging of qs_step_host (one allocation, made on first use)
     char* stage = nullptr;
     size_t st_obs = 0, st_rew = 0, st_done = 0;
-    int32_t* status_h = nullptr;  // pinned host copy of the device status word (qs_sync)
+    int32_t* status_h = nullptr;  // host view of the status word (qs_sync)
+    bool status_mapped = false;   // the device status word is page-locked host memory
     std::string err;
 };
 
@@ -470,6 +471,25 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
     h->dv.ev = (uint32_t*)(base + o_ev);
     h->dv.knn = rec ? (int16_t*)(base + o_knn) : nullptr;
     h->dv.status = (int32_t*)(base + o_status);
+    {
+        // where the device can update page-locked host memory atomically (a
+        // coherent host link), the status word lives there: kernels set it in
+        // place and qs_sync reads it after its wait, with no copy
+        int native = 0;
+        void* dptr = nullptr;
+        if (cudaDeviceGetAttribute(&native, cudaDevAttrHostNativeAtomicSupported, h->device) == cudaSuccess && native &&
+            cudaHostAlloc((void**)&h->status_h, sizeof(int32_t), cudaHostAllocMapped) == cudaSuccess) {
+            if (cudaHostGetDevicePointer(&dptr, h->status_h, 0) == cudaSuccess && dptr) {
+                *h->status_h = 0;
+                h->dv.status = (int32_t*)dptr;
+                h->status_mapped = true;
+            } else {
+                cudaFreeHost(h->status_h);
+                h->status_h = nullptr;
+            }
+        }
+        cudaGetLastError();
+    }
     h->dv.scn = (float*)(base + o_scn);
     h->dv.scn_sel = (uint8_t*)(base + o_sel);
     h->dv.D = h->D;
@@ -481,24 +501,26 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
                   cudaSuccess &&
               cudaMemcpy((void*)h->dv.env_of, env_of.data(), sizeof(int32_t) * D, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(h->d_perm, perm.data(), sizeof(int) * E, cudaMemcpyHostToDevice) == cudaSuccess;
-    if (!ok) {
+    auto release = [&]() {
+        cudaFree(h->d_tiles);
         cudaFree(h->arena);
+        if (h->status_h) cudaFreeHost(h->status_h);
         delete h;
+    };
+    if (!ok) {
+        release();
         return fail(nullptr, QS_ERR_CUDA, "qs_create: initial upload failed");
     }
     h->perm_h = perm;
     qs_status s = upload_tiles(h);
     if (s != QS_OK) {
         std::string m = h->err;
-        cudaFree(h->arena);
-        delete h;
+        release();
         return fail(nullptr, s, m);
     }
     ce = launch_reset(h->c, h->dv, h->c.key0, h->c.key1, nullptr, h->stream);
     if (ce != cudaSuccess) {
-        cudaFree(h->d_tiles);
-        cudaFree(h->arena);
-        delete h;
+        release();
         return fail(nullptr, QS_ERR_CUDA, std::string("qs_create: reset launch: ") + cudaGetErrorString(ce));
     }
     *out = h;
@@ -851,12 +873,15 @@ qs_status qs_sync(qs_env* h) {
         h->status_h = nullptr;
         return fail(h, QS_ERR_OOM, "qs_sync: pinned status word");
     }
-    // the status word follows the stream's work, so one wait covers both
-    cudaError_t e = cudaMemcpyAsync(h->status_h, h->dv.status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "qs_sync status copy");
+    cudaError_t e = cudaSuccess;
+    if (!h->status_mapped) {
+        // the status word follows the stream's work, so one wait covers both
+        e = cudaMemcpyAsync(h->status_h, h->dv.status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "qs_sync status copy");
+    }
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "qs_sync");
-    if (*h->status_h & 1) return fail(h, QS_ERR_STATE_NONFINITE, "a drone state became non-finite");
+    if (*(volatile int32_t*)h->status_h & 1) return fail(h, QS_ERR_STATE_NONFINITE, "a drone state became non-finite");
     return QS_OK;
 }
 
