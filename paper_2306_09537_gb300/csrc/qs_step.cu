@@ -100,7 +100,7 @@ __device__ __forceinline__ void apply_downwash(const Consts& c, Drone& s, uint32
 
 // S13 reward of one drone (Sec. III-E): weighted state terms, event indicators
 // and the proximity term over its neighbours (keys = squared distances).
-__device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s, const EnvRegs& er, const float g[3],
+__device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s, float prox, const float g[3],
                                                 const float fh[4], uint32_t ev, const uint64_t best[QS_MAX_K], int keff) {
     const float dgx = s.x[0] - g[0], dgy = s.x[1] - g[1], dgz = s.x[2] - g[2];
     float r = c.w[QS_W_POS] * sqrtf(dgx * dgx + dgy * dgy + dgz * dgz);
@@ -119,7 +119,7 @@ __device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s,
     r += (ev & EV_HIT_QUAD) ? c.w[QS_W_HIT_QUAD] : 0.0f;
     if (keff > 0 && c.w[QS_W_NEAR] != 0.0f) {
         float near = 0.0f;
-        const float inv_prox = __frcp_rn(er.p.prox);
+        const float inv_prox = __frcp_rn(prox);
 #pragma unroll
         for (int k = 0; k < QS_MAX_K; ++k) {
             if (k < keff) {
@@ -300,7 +300,7 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
     ev_out = ev;
 
     // ---- S13 reward and done
-    if (rew) rew[d] = compute_reward(c, s, er, gl, fh, ev, best, W > 1 ? keff : 0);
+    if (rew) rew[d] = compute_reward(c, s, er.p.prox, gl, fh, ev, best, W > 1 ? keff : 0);
     end_step<EXT>(c, dv, s, er, fh, lane, e, d, done);
     if (scn && er.ep == 0) gc.until = -1;  // an auto-reset drew a new record
 }
@@ -422,13 +422,16 @@ constexpr int WS_OBS_MAX = 18 + 6 * QS_MAX_K;
 template <int P>
 struct WsShared {
     float nrm[2][WS_SUB][4][32 * P];  // motor-noise normals [buffer][substep][rotor][drone lane]
-    float st[18][32 * P];             // x v R w of each drone lane after the step (post-collision)
+    // the published end of a step, [buffer] by step parity:
+    float st[2][18][32 * P];          // x v R w of each drone lane after the step (post-collision)
+    float g[2][3][32 * P];            // goal of each lane's drone
+    int nb[2][QS_MAX_K][32 * P];      // CTA drone lane of each neighbour
+    int keff[2][32 * P];
+    float rin[2][9][32 * P];          // reward inputs: command f^ (4), previous command (4), proximity radius
+    uint32_t ev[2][32 * P];           // event bits
     float sx[3][32 * P];              // pair-pass staging: positions
     float sv[3][32 * P];              //                    velocities
-    float g[3][32 * P];               // goal of each lane's drone
     uint32_t key[32 * P];             // swap keys
-    int nb[QS_MAX_K][32 * P];         // CTA drone lane of each neighbour
-    int keff[32 * P];
     float rows[32 * P * WS_OBS_MAX];
 };
 
@@ -489,31 +492,32 @@ __device__ __forceinline__ void ws_motor_normals(const Consts& c, WsShared<P>& s
 // written with 16-byte stores.
 template <int P>
 __device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, const Tile& tile,
-                                             const int* __restrict__ perm, WsShared<P>& sh, const WsMap& m,
+                                             const int* __restrict__ perm, WsShared<P>& sh, const WsMap& m, int b,
                                              float* __restrict__ obs, const float ex[3], const float evv[3],
                                              const float ew[3]) {
     const int od = c.obs_dim, K = c.K, L = m.L;
+    const float(&st)[18][32 * P] = sh.st[b];
     const bool contig = tile.pad != 0;
     const int d_first = dv.env_off[perm[tile.first]];
     const int ridx = contig ? m.d - d_first : L;
     if (m.act) {
         float* row = sh.rows + ridx * od;
-        row[0] = sh.st[0][L] - sh.g[0][L] + ex[0];
-        row[1] = sh.st[1][L] - sh.g[1][L] + ex[1];
-        row[2] = sh.st[2][L] - sh.g[2][L] + ex[2];
-        row[3] = sh.st[3][L] + evv[0];
-        row[4] = sh.st[4][L] + evv[1];
-        row[5] = sh.st[5][L] + evv[2];
-        for (int k = 6; k < 15; ++k) row[k] = sh.st[k][L];
-        row[15] = sh.st[15][L] + ew[0];
-        row[16] = sh.st[16][L] + ew[1];
-        row[17] = sh.st[17][L] + ew[2];
-        const int ke = sh.keff[L];
+        row[0] = st[0][L] - sh.g[b][0][L] + ex[0];
+        row[1] = st[1][L] - sh.g[b][1][L] + ex[1];
+        row[2] = st[2][L] - sh.g[b][2][L] + ex[2];
+        row[3] = st[3][L] + evv[0];
+        row[4] = st[4][L] + evv[1];
+        row[5] = st[5][L] + evv[2];
+        for (int k = 6; k < 15; ++k) row[k] = st[k][L];
+        row[15] = st[15][L] + ew[0];
+        row[16] = st[16][L] + ew[1];
+        row[17] = st[17][L] + ew[2];
+        const int ke = sh.keff[b][L];
         for (int k = 0; k < K; ++k) {
             float* on = row + 18 + 6 * k;
             if (k < ke) {
-                const int j = sh.nb[k][L];
-                for (int q = 0; q < 6; ++q) on[q] = sh.st[q][j] - sh.st[q][L];
+                const int j = sh.nb[b][k][L];
+                for (int q = 0; q < 6; ++q) on[q] = st[q][j] - st[q][L];
             } else {
                 for (int q = 0; q < 6; ++q) on[q] = 0.f;
             }
@@ -548,10 +552,11 @@ __device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, con
 // and B2 (post-step state, goal and neighbours published for the observation
 // rows), then writes the knn record, reward and done and ends the step. Every
 // thread of the dynamics warps calls it.
-template <bool EXT, int P>
+template <bool EXT, int P, bool DEFER>
 __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv, WsShared<P>& sh, const WsMap& m,
                                                  Drone& s, EnvRegs& er, uint32_t& ev_out, const float4 a, const int nb,
                                                  float* __restrict__ rew, uint8_t* __restrict__ done, GoalCache& gc) {
+    const int b = nb;  // the step's buffers: its motor normals and its published end
     const int W = m.W, L = m.L, lane = m.lane, N = m.N, e = m.e, d = m.d, sbase = m.sbase;
     const bool act = m.act;
     const int K = c.K;
@@ -638,14 +643,23 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
         const float v18[18] = {s.x[0], s.x[1], s.x[2], s.v[0], s.v[1], s.v[2], s.R[0], s.R[1], s.R[2],
                                s.R[3], s.R[4], s.R[5], s.R[6], s.R[7], s.R[8], s.w[0], s.w[1], s.w[2]};
 #pragma unroll
-        for (int k = 0; k < 18; ++k) sh.st[k][L] = v18[k];
-        sh.g[0][L] = gl[0];
-        sh.g[1][L] = gl[1];
-        sh.g[2][L] = gl[2];
-        sh.keff[L] = W > 1 ? keff : 0;
+        for (int k = 0; k < 18; ++k) sh.st[b][k][L] = v18[k];
+        sh.g[b][0][L] = gl[0];
+        sh.g[b][1][L] = gl[1];
+        sh.g[b][2][L] = gl[2];
+        sh.keff[b][L] = W > 1 ? keff : 0;
 #pragma unroll
         for (int k = 0; k < QS_MAX_K; ++k)
-            if (k < keff) sh.nb[k][L] = sbase + (int)(best[k] & 0xffffffffu);
+            if (k < keff) sh.nb[b][k][L] = sbase + (int)(best[k] & 0xffffffffu);
+        if (DEFER) {  // the noise side computes the reward from these
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                sh.rin[b][r][L] = fh[r];
+                sh.rin[b][4 + r][L] = s.fp[r];
+            }
+            sh.rin[b][8][L] = er.p.prox;
+            sh.ev[b][L] = ev;
+        }
     }
     __syncthreads();  // B2
     if (!act) return;
@@ -654,10 +668,46 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
         for (int k = 0; k < QS_MAX_K; ++k)
             if (k < K) dv.knn[(size_t)k * dv.D + d] = (W > 1 && k < keff) ? (int16_t)(best[k] & 0xffffu) : (int16_t)-1;
     }
-    if (rew) rew[d] = compute_reward(c, s, er, gl, fh, ev, best, W > 1 ? keff : 0);
+    if (!DEFER && rew) rew[d] = compute_reward(c, s, er.p.prox, gl, fh, ev, best, W > 1 ? keff : 0);
     end_step<EXT>(c, dv, s, er, fh, lane, e, d, done);
     if (EXT && er.ep == 0) gc.until = -1;  // an auto-reset drew a new record
     ev_out = ev;
+}
+
+// Noise side: the reward of the step published in buffer b (the same
+// compute_reward as the dynamics side, on the published post-step state; the
+// neighbour keys recomputed with the canonical pair key on the same positions).
+template <int P>
+__device__ __forceinline__ void ws_reward(const Consts& c, WsShared<P>& sh, const WsMap& m, int b,
+                                          float* __restrict__ rew) {
+    if (!m.act) return;
+    const int L = m.L;
+    Drone s;
+    for (int k = 0; k < 3; ++k) {
+        s.x[k] = sh.st[b][k][L];
+        s.v[k] = sh.st[b][3 + k][L];
+        s.w[k] = sh.st[b][15 + k][L];
+    }
+    for (int k = 0; k < 9; ++k) s.R[k] = sh.st[b][6 + k][L];
+    float fh[4];
+    for (int r = 0; r < 4; ++r) {
+        fh[r] = sh.rin[b][r][L];
+        s.fp[r] = sh.rin[b][4 + r][L];
+    }
+    const float g[3] = {sh.g[b][0][L], sh.g[b][1][L], sh.g[b][2][L]};
+    const int keff = sh.keff[b][L];
+    uint64_t best[QS_MAX_K];
+#pragma unroll
+    for (int k = 0; k < QS_MAX_K; ++k) {
+        best[k] = ~0ull;
+        if (k < keff) {
+            const int j = sh.nb[b][k][L];
+            float dx, dy, dz;
+            const float key = pair_key(s.x[0], s.x[1], s.x[2], sh.st[b][0][j], sh.st[b][1][j], sh.st[b][2][j], dx, dy, dz);
+            best[k] = (uint64_t)__float_as_uint(key) << 32;
+        }
+    }
+    rew[m.d] = compute_reward(c, s, sh.rin[b][8][L], g, fh, sh.ev[b][L], best, keff);
 }
 
 template <bool EXT>
@@ -674,7 +724,7 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
         float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
         if (m.act && io.obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, m.d, 0u, ex, evv, ew);
         __syncthreads();  // B2
-        if (io.obs) ws_store_obs<1>(c, dv, tile, perm, sh, m, io.obs, ex, evv, ew);
+        if (io.obs) ws_store_obs<1>(c, dv, tile, perm, sh, m, 0, io.obs, ex, evv, ew);
         return;
     }
     // ---------------- dynamics warp
@@ -688,7 +738,7 @@ __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, co
         a = __ldg(reinterpret_cast<const float4*>(io.act) + m.d);
     }
     GoalCache gc{{0.f, 0.f, 0.f}, 0, -1};
-    ws_dynamics_step<EXT, 1>(c, dv, sh, m, s, er, ev, a, 0, io.rew, io.done, gc);
+    ws_dynamics_step<EXT, 1, false>(c, dv, sh, m, s, er, ev, a, 0, io.rew, io.done, gc);
     if (!m.act) return;
     dv.ev[m.d] = ev;
     store_drone(s, dv.st, dv.D, m.d);
@@ -711,18 +761,36 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_rollout_ws(const C
     const size_t D = dv.D, E = dv.E;
     if (threadIdx.x >= 32 * P) {
         // ---------------- noise side; the env's Philox counter advances by one per step
+        // Step t's observation rows and reward are finished during step t + 1's
+        // dynamics, from the end of step t published in buffer t & 1.
         const uint32_t tick0 = m.act ? dv.tick[m.e] : 0u;  // the dynamics side writes it after the last step
         ws_motor_normals<P>(c, sh, m, tick0, 0);
+        float px[3] = {0.f, 0.f, 0.f}, pv[3] = {0.f, 0.f, 0.f}, pw[3] = {0.f, 0.f, 0.f};  // step t-1's sensor noise
         for (int t = 0; t < nsteps; ++t) {
             const uint32_t tick = tick0 + (uint32_t)t;
-            float* obs = io.obs ? io.obs + (size_t)(t0 + t) * D * c.obs_dim : nullptr;
             __syncthreads();  // B1 of step t: buffer t & 1 holds step t's normals
             float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
-            if (m.act && obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, m.d, 0u, ex, evv, ew);
+            if (m.act && io.obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, m.d, 0u, ex, evv, ew);
             // the other buffer was last read by the dynamics side before B2 of step t - 1
             if (t + 1 < nsteps) ws_motor_normals<P>(c, sh, m, tick + 1, (t + 1) & 1);
+            if (t > 0) {
+                const int pb = (t - 1) & 1;
+                if (io.obs) ws_store_obs<P>(c, dv, tile, perm, sh, m, pb, io.obs + (size_t)(t0 + t - 1) * D * c.obs_dim,
+                                            px, pv, pw);
+                if (io.rew) ws_reward<P>(c, sh, m, pb, io.rew + (size_t)(t0 + t - 1) * D);
+            }
+            for (int k = 0; k < 3; ++k) {
+                px[k] = ex[k];
+                pv[k] = evv[k];
+                pw[k] = ew[k];
+            }
             __syncthreads();  // B2 of step t
-            if (obs) ws_store_obs<P>(c, dv, tile, perm, sh, m, obs, ex, evv, ew);
+        }
+        if (nsteps > 0) {  // the last step, after its B2
+            const int pb = (nsteps - 1) & 1;
+            if (io.obs)
+                ws_store_obs<P>(c, dv, tile, perm, sh, m, pb, io.obs + (size_t)(t0 + nsteps - 1) * D * c.obs_dim, px, pv, pw);
+            if (io.rew) ws_reward<P>(c, sh, m, pb, io.rew + (size_t)(t0 + nsteps - 1) * D);
         }
         return;
     }
@@ -740,7 +808,7 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_rollout_ws(const C
     for (int t = 0; t < nsteps; ++t) {
         const float4 a = a_next;
         if (m.act && t + 1 < nsteps) a_next = __ldg(act4 + (size_t)(t0 + t + 1) * D);
-        ws_dynamics_step<EXT, P>(c, dv, sh, m, s, er, ev, a, t & 1,
+        ws_dynamics_step<EXT, P, true>(c, dv, sh, m, s, er, ev, a, t & 1,
                                  io.rew ? io.rew + (size_t)(t0 + t) * D : nullptr,
                                  io.done ? io.done + (size_t)(t0 + t) * E : nullptr, gc);
     }
