@@ -372,12 +372,12 @@ __device__ __forceinline__ void command4(const Consts& c, const float* act, size
 __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_fwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                             const int* __restrict__ perm, const DiffArgs a) {
     extern __shared__ float sm[];
-    const Tile tile = tiles[blockIdx.x];
+    const Tile tile = tile_at(dv, tiles, blockIdx.x, blockDim.x);
     const int W = tile.W, nt = blockDim.x;
     const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
     const bool ok = slot < tile.count;
-    const int e = ok ? perm[tile.first + slot] : 0;
-    const int d0 = ok ? dv.env_off[e] : 0, N = ok ? dv.env_off[e + 1] - d0 : 0;
+    const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
+    const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
     const bool act = lane < N;
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;
@@ -419,12 +419,12 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_fwd(const Consts c, cons
 __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                             const int* __restrict__ perm, const DiffArgs a) {
     extern __shared__ float sm[];
-    const Tile tile = tiles[blockIdx.x];
+    const Tile tile = tile_at(dv, tiles, blockIdx.x, blockDim.x);
     const int W = tile.W, nt = blockDim.x;
     const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
     const bool ok = slot < tile.count;
-    const int e = ok ? perm[tile.first + slot] : 0;
-    const int d0 = ok ? dv.env_off[e] : 0, N = ok ? dv.env_off[e + 1] - d0 : 0;
+    const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
+    const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
     const bool act = lane < N;
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;
@@ -791,12 +791,12 @@ __device__ __forceinline__ void collision_vjp(const Consts& c, const float xs[3]
 __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                              const int* __restrict__ perm, const DiffArgs a) {
     extern __shared__ float sm[];
-    const Tile tile = tiles[blockIdx.x];
+    const Tile tile = tile_at(dv, tiles, blockIdx.x, blockDim.x);
     const int W = tile.W, nt = blockDim.x;
     const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
     const bool ok = slot < tile.count;
-    const int e = ok ? perm[tile.first + slot] : 0;
-    const int d0 = ok ? dv.env_off[e] : 0, N = ok ? dv.env_off[e + 1] - d0 : 0;
+    const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
+    const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
     const bool act = lane < N;
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;
@@ -842,12 +842,12 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, con
 __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                              const int* __restrict__ perm, const DiffArgs a) {
     extern __shared__ float sm[];
-    const Tile tile = tiles[blockIdx.x];
+    const Tile tile = tile_at(dv, tiles, blockIdx.x, blockDim.x);
     const int W = tile.W, nt = blockDim.x;
     const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
     const bool ok = slot < tile.count;
-    const int e = ok ? perm[tile.first + slot] : 0;
-    const int d0 = ok ? dv.env_off[e] : 0, N = ok ? dv.env_off[e + 1] - d0 : 0;
+    const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
+    const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
     const bool act = lane < N;
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;

@@ -229,6 +229,43 @@ int default_block(int W, int slots, int n_sm) {
 
 bool rollout_is_ws(const qs_env* h) { return h->rollout_block == QS_BLOCK_WARP_SPECIALISED; }
 
+// Whether a tile table of `lanes` lanes per tile cuts E envs of width W into
+// consecutive runs of lanes / W slots from slot 0 (the rule tile_at computes).
+bool follows_uniform_rule(const Tile* t, size_t n, int E, int W, int lanes) {
+    const int per = lanes / W;
+    if (per < 1 || per * W != lanes || (long)n * per < E) return false;
+    for (size_t i = 0; i < n; ++i) {
+        const int first = (int)i * per;
+        if (t[i].first != first || t[i].count != std::min(per, E - first) || t[i].W != W) return false;
+    }
+    return true;
+}
+
+// Uniform geometry: one width class, every env the same size, envs in slot
+// order, and every tile table the kernels read following the computed rule
+// for the block it is launched with.
+void set_uniform(qs_env* h, const std::vector<Tile>& tiles, const std::vector<Tile>& rtiles, int rblock,
+                 const std::vector<Tile>& dtiles, const std::vector<Tile>& wtiles) {
+    h->dv.uni_n = 0;
+    h->dv.uni_wlog = 0;
+    if (h->plan.size() != 1 || h->E < 1) return;
+    const int N = h->env_off_h[1], W = h->plan[0].W;
+    for (int e = 0; e <= h->E; ++e)
+        if (h->env_off_h[e] != e * N) return;
+    for (int e = 0; e < h->E; ++e)
+        if (h->perm_h[e] != e) return;
+    const ClassPlan& cp = h->plan[0];
+    if (!follows_uniform_rule(tiles.data() + cp.tile_off, cp.n_tiles, h->E, W, cp.block) ||
+        !follows_uniform_rule(rtiles.data(), rtiles.size(), h->E, W, rblock) ||
+        !follows_uniform_rule(dtiles.data(), dtiles.size(), h->E, W, h->diff_block) ||
+        (!wtiles.empty() && !follows_uniform_rule(wtiles.data(), wtiles.size(), h->E, W, 32 * h->ws_p)))
+        return;
+    int wlog = 0;
+    while ((1 << wlog) < W) ++wlog;
+    h->dv.uni_n = N;
+    h->dv.uni_wlog = wlog;
+}
+
 qs_status upload_tiles(qs_env* h) {
     std::vector<Tile> tiles, rtiles, dtiles, wtiles;
     build_tiles(h, tiles);
@@ -239,6 +276,7 @@ qs_status upload_tiles(qs_env* h) {
     for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
     h->diff_block = std::max(32, maxW);  // many small CTAs: the adjoint is latency-bound
     build_rollout_tiles(h, dtiles, h->diff_block);
+    set_uniform(h, tiles, rtiles, rblock, dtiles, wtiles);
     drop_graph(h);
     if (h->d_tiles) cudaFree(h->d_tiles);
     h->d_tiles = nullptr;

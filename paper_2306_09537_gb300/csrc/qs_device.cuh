@@ -188,6 +188,30 @@ __device__ __forceinline__ void pack(const Drone& s, float4 q[NPLANE]) {
     f[35] = 0.0f;
 }
 
+// ---------------------------------------------------------------- slot geometry
+// A tile of `lanes` drone lanes holds lanes / W consecutive slots of the
+// permutation. With uniform geometry (dv.uni_n > 0: every env has uni_n
+// drones, one width class W, envs in slot order) tile i is slots
+// [i per, i per + per) and env e starts at drone e uni_n, so a kernel derives
+// both from its tile index instead of reading the tile table, the permutation
+// and the env offsets: three dependent loads before the first state load. The
+// host turns it on only after checking every tile table against this rule.
+__device__ __forceinline__ Tile tile_at(const Dev& dv, const Tile* __restrict__ tiles, int i, int lanes) {
+    if (dv.uni_n) {
+        const int per = lanes >> dv.uni_wlog, first = i * per;
+        return Tile{first, min(per, dv.E - first), 1 << dv.uni_wlog, 1};
+    }
+    return tiles[i];
+}
+
+// The env in slot j of the permutation.
+__device__ __forceinline__ int slot_env(const Dev& dv, const int* __restrict__ perm, int j) {
+    return dv.uni_n ? j : perm[j];
+}
+
+// The first drone of env e (e = E: the drone count).
+__device__ __forceinline__ int env_first(const Dev& dv, int e) { return dv.uni_n ? e * dv.uni_n : dv.env_off[e]; }
+
 // hi + lo <- hi + lo + delta, keeping the rounding error of the sum in lo.
 __device__ __forceinline__ void comp_add(float& hi, float& lo, float delta) {
     const float y = delta + lo;

@@ -76,6 +76,10 @@ struct Dev {
     float* scn;              // [2][QS_NSCN][E] scenario records, double-buffered (null: single goal only)
     uint8_t* scn_sel;        // [E] active buffer of each env's record
     int D, E;
+    // uniform geometry (every env uni_n drones, width class 1 << uni_wlog, slots
+    // in env order): tiles, envs and first drones follow from the tile index
+    // (tile_at); 0 when the swarm sizes differ
+    int uni_n = 0, uni_wlog = 0;
 };
 
 // A launch covers "tiles": consecutive slots (envs of one width class W) of

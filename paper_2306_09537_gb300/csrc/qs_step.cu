@@ -315,9 +315,9 @@ __device__ __forceinline__ SlotMap map_slot(const Dev& dv, const Tile& tile, con
     m.slot = threadIdx.x / W;
     m.lane = threadIdx.x - m.slot * W;
     const bool ok = m.slot < tile.count;
-    m.e = ok ? perm[tile.first + m.slot] : 0;
-    m.d0 = ok ? dv.env_off[m.e] : 0;
-    m.N = ok ? dv.env_off[m.e + 1] - m.d0 : 0;
+    m.e = ok ? slot_env(dv, perm, tile.first + m.slot) : 0;
+    m.d0 = ok ? env_first(dv, m.e) : 0;
+    m.N = ok ? env_first(dv, m.e + 1) - m.d0 : 0;
     m.act = m.lane < m.N;
     m.d = m.d0 + m.lane;
     m.sbase = m.slot * W;
@@ -331,7 +331,7 @@ template <int W, bool EXT>
 __global__ void __launch_bounds__(MAX_BLOCK, (W == 1 ? 3 : 1)) k_step(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                     const int* __restrict__ perm, const StepIO io, const int observe_only) {
     extern __shared__ float sm[];
-    const SlotMap m = map_slot(dv, tiles[blockIdx.x], perm, W);
+    const SlotMap m = map_slot(dv, tile_at(dv, tiles, blockIdx.x, blockDim.x), perm, W);
     Drone s;
     EnvRegs er;
     uint32_t ev = 0;
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 2) k_rollout(const Consts c, const 
         const int ti = s_next;
         __syncthreads();  // everyone has read s_next before thread 0 overwrites it
         if (ti >= n_tiles) return;
-        rollout_tile<EXT>(c, dv, tiles[ti], perm, sm, io, t0, nsteps);
+        rollout_tile<EXT>(c, dv, tile_at(dv, tiles, ti, blockDim.x), perm, sm, io, t0, nsteps);
     }
 }
 
@@ -460,9 +460,9 @@ __device__ __forceinline__ WsMap ws_map(const Dev& dv, const Tile& tile, const i
     m.slot = m.L / m.W;
     m.lane = m.L - m.slot * m.W;
     const bool ok = m.slot < tile.count;
-    m.e = ok ? perm[tile.first + m.slot] : 0;
-    m.d0 = ok ? dv.env_off[m.e] : 0;
-    m.N = ok ? dv.env_off[m.e + 1] - m.d0 : 0;
+    m.e = ok ? slot_env(dv, perm, tile.first + m.slot) : 0;
+    m.d0 = ok ? env_first(dv, m.e) : 0;
+    m.N = ok ? env_first(dv, m.e + 1) - m.d0 : 0;
     m.act = m.lane < m.N;
     m.d = m.d0 + m.lane;
     m.sbase = m.slot * m.W;
@@ -498,7 +498,7 @@ __device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, con
     const int od = c.obs_dim, K = c.K, L = m.L;
     const float(&st)[18][32 * P] = sh.st[b];
     const bool contig = tile.pad != 0;
-    const int d_first = dv.env_off[perm[tile.first]];
+    const int d_first = env_first(dv, slot_env(dv, perm, tile.first));
     const int ridx = contig ? m.d - d_first : L;
     if (m.act) {
         float* row = sh.rows + ridx * od;
@@ -525,8 +525,8 @@ __device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, con
     }
     side_sync<P>(2);
     if (contig) {
-        const int e_last = perm[tile.first + tile.count - 1];
-        const int n_floats = (dv.env_off[e_last + 1] - d_first) * od;
+        const int e_last = slot_env(dv, perm, tile.first + tile.count - 1);
+        const int n_floats = (env_first(dv, e_last + 1) - d_first) * od;
         float* dst = obs + (size_t)d_first * od;
         if (((uintptr_t)dst & 15u) == 0) {
             const int n4 = n_floats >> 2;
@@ -714,7 +714,7 @@ template <bool EXT>
 __global__ void __launch_bounds__(64) k_step_ws(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                 const int* __restrict__ perm, const StepIO io) {
     __shared__ WsShared<1> sh;
-    const Tile tile = tiles[blockIdx.x];
+    const Tile tile = tile_at(dv, tiles, blockIdx.x, 32);
     const WsMap m = ws_map<1>(dv, tile, perm);
     if (threadIdx.x >= 32) {
         // ---------------- noise warp
@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_rollout_ws(const C
                                                        const int* __restrict__ perm, const RolloutIO io, const int t0,
                                                        const int nsteps) {
     __shared__ WsShared<P> sh;
-    const Tile tile = tiles[blockIdx.x];
+    const Tile tile = tile_at(dv, tiles, blockIdx.x, 32 * P);
     const WsMap m = ws_map<P>(dv, tile, perm);
     const size_t D = dv.D, E = dv.E;
     if (threadIdx.x >= 32 * P) {

@@ -472,6 +472,69 @@ def test_launch_shape_does_not_change_results():
             assert all(torch.equal(a, b) for a, b in zip(ref, cur))
 
 
+@pytest.mark.parametrize("n,K", [(1, 0), (8, 6), (48, 6)])
+def test_uniform_geometry_matches_tile_tables(n, K):
+    """With equal swarm sizes the kernels compute each tile, its envs and their
+    first drones from the tile index; a handle whose last env differs in size
+    reads them from the tile table, the permutation and the env offsets. The
+    envs the two handles share give the same bits through every launch form:
+    per-call (warp-specialised and general kernels) and rollouts
+    (warp-specialised and persistent), across auto-resets."""
+    from paper_2306_09537_gb300 import qs
+    from paper_2306_09537_gb300.env import QuadSwarmEnv
+    E = 3000 if n == 1 else 240
+    last = 2 if n == 1 else n - 1
+    feats = FULL + ("auto_reset",)
+    sizes_b = np.array([n] * (E - 1) + [last], dtype=np.int32)
+    Ds = (E - 1) * n
+    st = W.random_states(9, E * n + 2)
+    st[:Ds, 0:3] = W.clustered_positions(9, [n] * (E - 1), spread=0.12) if n > 1 else st[:Ds, 0:3]
+    prm, goals = None, W.random_goals(9, E)
+    envs = []
+    for sizes in (n, sizes_b):
+        env = QuadSwarmEnv(E, sizes, K, feats, seed=9, weights=ALL_WEIGHTS, device=DEV, episode_steps=4)
+        if prm is None:
+            prm = W.random_params(9, E, nominal(env))
+        env.set_state(torch.from_numpy(np.ascontiguousarray(st[:env.D], np.float32)).to(DEV),
+                      torch.from_numpy(prm.astype(np.float32)).to(DEV),
+                      torch.from_numpy(goals.astype(np.float32)).to(DEV),
+                      torch.zeros(E, dtype=torch.int32, device=DEV), torch.full((E,), 5, dtype=torch.int32, device=DEV))
+        envs.append(env)
+    a, b = envs
+    wcls = 1 if n == 1 else int(2 ** np.ceil(np.log2(n)))
+
+    def shared(env, obs, rew, done):
+        return obs[..., :Ds, :], rew[..., :Ds], (None if done is None else done[..., :E - 1]), env.get_state()["state"][:Ds]
+
+    T = 6
+    acts = torch.from_numpy(W.actions(9, 4 * T, a.D + 2)).to(DEV)
+    t = 0
+    for block in (None, max(64, wcls)):  # per-call: default plan, then the general kernel
+        if block:
+            for env in envs:
+                for w in ({1, 2} if env is b else {1}) if n == 1 else {wcls}:
+                    qs.qs_set_block(env.h, w, block)
+        for _ in range(T):
+            ra = shared(a, *a.step(acts[t, :a.D].contiguous()))
+            rb = shared(b, *b.step(acts[t, :b.D].contiguous()))
+            assert all(torch.equal(x, y) for x, y in zip(ra, rb)), (block, t)
+            t += 1
+    shapes = ([(qs.QS_BLOCK_WARP_SPECIALISED, 0, False)] if wcls <= 64 else []) + [(max(128, wcls), 0, False)]
+    for shape in shapes:
+        outs = []
+        for env in envs:
+            qs.qs_set_rollout_shape(env.h, *shape)
+            obs = torch.empty(T, env.D, env.obs_dim, device=DEV)
+            rew = torch.empty(T, env.D, device=DEV)
+            done = torch.empty(T, E, dtype=torch.uint8, device=DEV)
+            env.rollout(acts[t:t + T, :env.D].contiguous(), obs, rew, done)
+            outs.append(shared(env, obs, rew, done))
+        assert all(torch.equal(x, y) for x, y in zip(*outs)), shape
+        t += T
+    for env in envs:
+        env.close()
+
+
 def test_auto_reset_matches_oracle():
     sizes = [4] * 50
     feats = FULL + ("auto_reset",)
