@@ -35,7 +35,7 @@ METRIC = "quadrotor-steps/sec on 1 GB300 (plain vs batched vs fwd+adjoint), % of
 # from an ncu capture of this command's headline kernel (L2 flushed before the
 # launch; the outputs stay in L2 during the launch, so the write count is 0).
 # Valid while k_step_ws<false> is unchanged.
-K_STEP_WS_DRAM_BYTES = None  # re-captured after each change of the kernel
+K_STEP_WS_DRAM_BYTES = 2075136 + 0
 K_STEP_WS_DRAM_SOURCE = "profiles/k_step_ws_plain_8192x1.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
 UNIT = "quadrotor-steps/s"
 WL = W.PLAIN
