@@ -32,7 +32,7 @@
  *    independent (apart from qs_diff_grad_static's shared array).
  *  - Results do not depend on launch shapes (qs_set_block,
  *    qs_set_rollout_shape): the same state, parameters and commands give the
- *    same bits through qs_step, qs_step_host and qs_rollout.
+ *    same bits through qs_step, qs_step_host, qs_serve_step and qs_rollout.
  *
  * Layouts (row-major, contiguous):
  *  actions  [D][4]            per-rotor normalised commands (16-byte aligned)
@@ -234,6 +234,44 @@ qs_status qs_step(qs_env* h, const float* actions_dev, float* obs_dev, float* re
  * buffer and one asynchronous copy. */
 qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, float* reward_host,
                        uint8_t* done_host);
+
+/* Resident stepping for synchronous host loops (the Gym wrapper of Sec. III:
+ * post commands, wait, read the observations). qs_serve_begin starts one
+ * cooperative launch that keeps every drone in registers and runs a control
+ * step (the same computation and bits as qs_step) each time qs_serve_step is
+ * called; the launch and completion round trip of a per-call step is replaced
+ * by two words of page-locked host memory, one the host advances and one the
+ * last CTA of a step advances.
+ *
+ *  actions_host [D][4] in, obs_host [D][obs_dim], reward_host [D], done_host
+ *  [E] out (outputs nullable): page-locked host memory the device can map
+ *  (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory; actions 16-byte,
+ *  obs 8-byte aligned), owned by the caller, read and written in place by the
+ *  server until qs_serve_end. Write a step's commands, call qs_serve_step, read
+ *  its outputs.
+ *  idle_ms: when no step is posted for about this long the server retires
+ *  (the drones return to the handle's memory and the launch ends);
+ *  qs_serve_step then starts it again, with no effect on the results.
+ *
+ * Requires every swarm to have at most 64 drones, a handle created on a
+ * non-blocking stream (cudaStreamNonBlocking, as torch.cuda.Stream() makes;
+ * the legacy default stream and streams that synchronise with it would wait
+ * behind the resident launch), a device with native atomics on host memory
+ * (a coherent host link such as NVLink-C2C) and room for all of the handle's
+ * CTAs at once; QS_ERR_UNSUPPORTED otherwise. While serving, a device-wide
+ * synchronisation (or a call that implies one, such as cudaFree) waits until
+ * the server retires. Misaligned or unmapped buffers:
+ * QS_ERR_ARG. While serving, every call that uses the handle's stream or
+ * state returns QS_ERR_ARG; qs_serve_end (or qs_destroy) ends serving and
+ * writes the drones back, after which they continue with qs_step or
+ * qs_rollout exactly as if every step had been a qs_step. qs_serve_step
+ * returns after the step's outputs are in host memory; a non-finite drone
+ * state is reported as by qs_sync; a step that does not complete within 10 s
+ * returns QS_ERR_TIMEOUT. */
+qs_status qs_serve_begin(qs_env* h, const float* actions_host, float* obs_host, float* reward_host,
+                         uint8_t* done_host, int32_t idle_ms);
+qs_status qs_serve_step(qs_env* h);
+qs_status qs_serve_end(qs_env* h);
 
 /* T control steps (T >= 1) of every env, batched: actions_dev [T][D][4],
  * obs_dev [T][D][obs_dim], reward_dev [T][D], done_dev [T][E] (outputs

@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <mutex>
 #include <new>
@@ -61,6 +63,12 @@ struct qs_env {
     size_t st_obs = 0, st_rew = 0, st_done = 0;
     int32_t* status_h = nullptr;  // host view of the status word (qs_sync)
     bool status_mapped = false;   // the device status word is page-locked host memory
+    // resident step server (qs_serve_*): while it runs its launch occupies the stream
+    bool serving = false;
+    int* serve_words = nullptr;               // page-locked, mapped: [0] go, [1] fin
+    unsigned long long* serve_dev = nullptr;  // device: [0] CTAs finished since the launch began, [1] relay word
+    ServeIO serve_io{};
+    int serve_k = 0;                             // steps completed since qs_serve_begin
     std::string err;
 };
 
@@ -81,6 +89,12 @@ qs_status fail(qs_env* h, qs_status s, const std::string& msg) {
     if (h) h->err = msg;
     else g_create_error = msg;
     return s;
+}
+
+// Calls that use the handle's stream or state are refused while a resident
+// server occupies the stream.
+qs_status busy(qs_env* h, const char* who) {
+    return fail(h, QS_ERR_ARG, std::string(who) + ": the handle is serving (call qs_serve_end first)");
 }
 
 qs_status cuda_fail(qs_env* h, cudaError_t e, const char* where) {
@@ -322,6 +336,22 @@ qs_status do_step(qs_env* h, const float* act, float* obs, float* rew, uint8_t* 
         cudaError_t e = launch_step(h->c, h->dv, cp, h->d_tiles, h->d_perm, io, 0, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     }
+    return QS_OK;
+}
+
+// (Re)starts the resident server at step serve_k: go = fin = serve_k, the CTA
+// counter zeroed and the relay word at serve_k before the cooperative launch.
+qs_status serve_launch(qs_env* h) {
+    volatile int* w = h->serve_words;
+    w[0] = h->serve_k;
+    w[1] = h->serve_k;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    const unsigned long long init[2] = {0ull, (unsigned long long)(unsigned int)h->serve_k};
+    cudaError_t e = cudaMemcpy(h->serve_dev, init, sizeof init, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_serve(h->c, h->dv, h->d_wtiles, h->n_wtiles, h->ws_p, h->d_perm, h->serve_io, h->serve_k, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "resident server launch");
+    h->serving = true;
     return QS_OK;
 }
 
@@ -569,12 +599,15 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
 qs_status qs_destroy(qs_env* h) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_destroy: NULL handle");
     DeviceGuard g(h->device);
+    if (h->serving) qs_serve_end(h);
     cudaStreamSynchronize(h->stream);
     drop_graph(h);
     cudaFree(h->d_tiles);
     cudaFree(h->arena);
     cudaFree(h->stage);
     if (h->status_h) cudaFreeHost(h->status_h);
+    if (h->serve_words) cudaFreeHost(h->serve_words);
+    cudaFree(h->serve_dev);
     delete h;
     return QS_OK;
 }
@@ -589,6 +622,7 @@ qs_status qs_get_dims(const qs_env* h, int32_t* n_drones, int32_t* n_envs, int32
 
 qs_status qs_reset(qs_env* h, uint64_t seed, const uint8_t* env_mask_dev, float* obs_dev) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_reset: NULL handle");
+    if (h->serving) return busy(h, "qs_reset");
     if (obs_dev && !aligned(obs_dev, 8)) return fail(h, QS_ERR_ARG, "qs_reset: obs_dev must be 8-byte aligned");
     DeviceGuard g(h->device);
     const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
@@ -613,6 +647,7 @@ qs_status qs_reset(qs_env* h, uint64_t seed, const uint8_t* env_mask_dev, float*
 
 qs_status qs_step(qs_env* h, const float* actions_dev, float* obs_dev, float* reward_dev, uint8_t* done_dev) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_step: NULL handle");
+    if (h->serving) return busy(h, "qs_step");
     if (!actions_dev) return fail(h, QS_ERR_ARG, "qs_step: actions_dev is NULL");
     if (!aligned(actions_dev, 16)) return fail(h, QS_ERR_ARG, "qs_step: actions_dev must be 16-byte aligned");
     if (obs_dev && !aligned(obs_dev, 8)) return fail(h, QS_ERR_ARG, "qs_step: obs_dev must be 8-byte aligned");
@@ -634,6 +669,7 @@ void* mapped_host(const void* p, size_t align) {
 
 qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, float* reward_host, uint8_t* done_host) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_step_host: NULL handle");
+    if (h->serving) return busy(h, "qs_step_host");
     if (!actions_host) return fail(h, QS_ERR_ARG, "qs_step_host: actions_host is NULL");
     DeviceGuard g(h->device);
     const size_t D = h->D, E = h->E;
@@ -681,6 +717,7 @@ qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, fl
 qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_dev, float* reward_dev,
                      uint8_t* done_dev) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_rollout: NULL handle");
+    if (h->serving) return busy(h, "qs_rollout");
     if (T < 1) return fail(h, QS_ERR_ARG, "qs_rollout: T must be >= 1");
     if (!actions_dev || !aligned(actions_dev, 16)) return fail(h, QS_ERR_ARG, "qs_rollout: actions_dev NULL or misaligned");
     if (obs_dev && !aligned(obs_dev, 8)) return fail(h, QS_ERR_ARG, "qs_rollout: obs_dev must be 8-byte aligned");
@@ -720,6 +757,7 @@ qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_
 
 qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t use_graph) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_set_rollout_shape: NULL handle");
+    if (h->serving) return busy(h, "qs_set_rollout_shape");
     int maxW = 1;
     for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
     const bool ws = block == QS_BLOCK_WARP_SPECIALISED && maxW <= 64;
@@ -738,6 +776,7 @@ qs_status qs_set_rollout_shape(qs_env* h, int32_t block, int32_t fuse, int32_t u
 
 static qs_status diff_check(qs_env* h, const char* who, int32_t T, int32_t C) {
     if (!h) return fail(nullptr, QS_ERR_ARG, std::string(who) + ": NULL handle");
+    if (h->serving) return busy(h, who);
     if (h->cfg.flags & QS_F_DOWNWASH)
         return fail(h, QS_ERR_UNSUPPORTED, std::string(who) + ": the differentiable rollout has no downwash term");
     if (h->c.scn_mask & ~1u)
@@ -858,6 +897,7 @@ qs_status qs_get_rollout_shape(const qs_env* h, int32_t* block, int32_t* fuse, i
 qs_status qs_get_state(qs_env* h, float* state_dev, float* params_dev, float* goals_dev, int32_t* ep_step_dev,
                        uint32_t* tick_dev) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_get_state: NULL handle");
+    if (h->serving) return busy(h, "qs_get_state");
     DeviceGuard g(h->device);
     cudaError_t e = launch_get_state(h->dv, state_dev, params_dev, goals_dev, ep_step_dev, tick_dev, h->stream);
     return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_get_state");
@@ -866,6 +906,7 @@ qs_status qs_get_state(qs_env* h, float* state_dev, float* params_dev, float* go
 qs_status qs_set_state(qs_env* h, const float* state_dev, const float* params_dev, const float* goals_dev,
                        const int32_t* ep_step_dev, const uint32_t* tick_dev) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_set_state: NULL handle");
+    if (h->serving) return busy(h, "qs_set_state");
     DeviceGuard g(h->device);
     cudaError_t e = launch_set_state(h->c, h->dv, state_dev, params_dev, goals_dev, ep_step_dev, tick_dev, h->stream);
     return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_set_state");
@@ -873,6 +914,7 @@ qs_status qs_set_state(qs_env* h, const float* state_dev, const float* params_de
 
 qs_status qs_get_events(qs_env* h, uint32_t* events_dev, int16_t* knn_dev) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_get_events: NULL handle");
+    if (h->serving) return busy(h, "qs_get_events");
     if (knn_dev && !h->dv.knn && h->K > 0)
         return fail(h, QS_ERR_ARG, "qs_get_events: neighbour lists need QS_F_RECORD_KNN at creation");
     if (!events_dev && !knn_dev) return QS_OK;
@@ -883,6 +925,7 @@ qs_status qs_get_events(qs_env* h, uint32_t* events_dev, int16_t* knn_dev) {
 
 qs_status qs_get_scenario(qs_env* h, float* records_dev) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_get_scenario: NULL handle");
+    if (h->serving) return busy(h, "qs_get_scenario");
     if (!records_dev) return fail(h, QS_ERR_ARG, "qs_get_scenario: records_dev is NULL");
     DeviceGuard g(h->device);
     cudaError_t e = launch_scenario_io(h->dv, records_dev, nullptr, h->stream);
@@ -891,6 +934,7 @@ qs_status qs_get_scenario(qs_env* h, float* records_dev) {
 
 qs_status qs_set_scenario(qs_env* h, const float* records_dev) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_set_scenario: NULL handle");
+    if (h->serving) return busy(h, "qs_set_scenario");
     if (!records_dev) return fail(h, QS_ERR_ARG, "qs_set_scenario: records_dev is NULL");
     DeviceGuard g(h->device);
     cudaError_t e = launch_scenario_io(h->dv, nullptr, records_dev, h->stream);
@@ -899,6 +943,7 @@ qs_status qs_set_scenario(qs_env* h, const float* records_dev) {
 
 qs_status qs_get_goals(qs_env* h, float* goals_dev) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_get_goals: NULL handle");
+    if (h->serving) return busy(h, "qs_get_goals");
     if (!goals_dev) return fail(h, QS_ERR_ARG, "qs_get_goals: goals_dev is NULL");
     DeviceGuard g(h->device);
     cudaError_t e = launch_goals(h->c, h->dv, goals_dev, h->stream);
@@ -907,6 +952,7 @@ qs_status qs_get_goals(qs_env* h, float* goals_dev) {
 
 qs_status qs_sync(qs_env* h) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_sync: NULL handle");
+    if (h->serving) return busy(h, "qs_sync");
     DeviceGuard g(h->device);
     if (!h->status_h && cudaHostAlloc((void**)&h->status_h, sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) {
         h->status_h = nullptr;
@@ -926,6 +972,7 @@ qs_status qs_sync(qs_env* h) {
 
 qs_status qs_set_block(qs_env* h, int32_t width, int32_t block) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_set_block: NULL handle");
+    if (h->serving) return busy(h, "qs_set_block");
     const bool ws = block == QS_BLOCK_WARP_SPECIALISED;
     if (ws ? width > 32 : (block < 32 || block > 256 || block % 32 != 0 || block % width != 0))
         return fail(h, QS_ERR_ARG, "qs_set_block: block must be 32..256, a multiple of 32 and of width, or "
@@ -947,6 +994,124 @@ qs_status qs_get_block(const qs_env* h, int32_t width, int32_t* block) {
     *block = 0;
     for (const ClassPlan& cp : h->plan)
         if (cp.W == width) *block = cp.ws ? QS_BLOCK_WARP_SPECIALISED : cp.block;
+    return QS_OK;
+}
+
+qs_status qs_serve_begin(qs_env* h, const float* actions_host, float* obs_host, float* reward_host, uint8_t* done_host,
+                         int32_t idle_ms) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_serve_begin: NULL handle");
+    if (h->serving) return fail(h, QS_ERR_ARG, "qs_serve_begin: the handle is already serving");
+    if (!actions_host) return fail(h, QS_ERR_ARG, "qs_serve_begin: actions_host is NULL");
+    if (idle_ms < 1) return fail(h, QS_ERR_ARG, "qs_serve_begin: idle_ms must be >= 1");
+    if (!h->ws_p || h->n_wtiles < 1)
+        return fail(h, QS_ERR_UNSUPPORTED, "qs_serve_begin: every swarm must have at most 64 drones");
+    DeviceGuard g(h->device);
+    unsigned int sflags = 0;
+    if (!h->stream || cudaStreamGetFlags(h->stream, &sflags) != cudaSuccess || !(sflags & cudaStreamNonBlocking)) {
+        cudaGetLastError();
+        return fail(h, QS_ERR_UNSUPPORTED, "qs_serve_begin: the handle's stream must be a non-blocking stream (the "
+                                           "legacy default stream would wait behind the resident launch)");
+    }
+    int native = 0;
+    if (cudaDeviceGetAttribute(&native, cudaDevAttrHostNativeAtomicSupported, h->device) != cudaSuccess || !native) {
+        cudaGetLastError();
+        return fail(h, QS_ERR_UNSUPPORTED, "qs_serve_begin: the device has no native atomics on host memory");
+    }
+    const float* a = (const float*)mapped_host(actions_host, 16);
+    float* o = obs_host ? (float*)mapped_host(obs_host, 8) : nullptr;
+    float* r = reward_host ? (float*)mapped_host(reward_host, 4) : nullptr;
+    uint8_t* dn = done_host ? (uint8_t*)mapped_host(done_host, 1) : nullptr;
+    if (!a || (obs_host && !o) || (reward_host && !r) || (done_host && !dn))
+        return fail(h, QS_ERR_ARG, "qs_serve_begin: buffers must be page-locked host memory the device can map "
+                                   "(actions 16-byte, observations 8-byte aligned)");
+    if (serve_resident_ctas(h->c, h->ws_p) < h->n_wtiles)
+        return fail(h, QS_ERR_UNSUPPORTED, "qs_serve_begin: the handle's CTAs do not fit on the device at once");
+    if (!h->serve_words) {
+        void* dp = nullptr;
+        if (cudaHostAlloc((void**)&h->serve_words, 2 * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(&dp, h->serve_words, 0) != cudaSuccess || !dp) {
+            if (h->serve_words) cudaFreeHost(h->serve_words);
+            h->serve_words = nullptr;
+            cudaGetLastError();
+            return fail(h, QS_ERR_OOM, "qs_serve_begin: handshake words");
+        }
+        h->serve_io.go = (int*)dp;
+        h->serve_io.fin = (int*)dp + 1;
+    }
+    if (!h->serve_dev && cudaMalloc(&h->serve_dev, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        h->serve_dev = nullptr;
+        return fail(h, QS_ERR_OOM, "qs_serve_begin: CTA counter");
+    }
+    // drain the stream: the server must not queue behind earlier work it cannot see
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qs_serve_begin");
+    h->serve_io.act = a;
+    h->serve_io.obs = o;
+    h->serve_io.rew = r;
+    h->serve_io.done = dn;
+    h->serve_io.count = h->serve_dev;
+    h->serve_io.relay = (int*)(h->serve_dev + 1);  // low word of [1] (the device is little-endian)
+    h->serve_io.idle_ns = (long long)idle_ms * 1000000;
+    h->serve_k = 0;
+    return serve_launch(h);
+}
+
+qs_status qs_serve_step(qs_env* h) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_serve_step: NULL handle");
+    if (!h->serving) return fail(h, QS_ERR_ARG, "qs_serve_step: the handle is not serving (qs_serve_begin)");
+    const int k = h->serve_k;
+    int* go = h->serve_words;
+    // the caller's command writes happen before the post (release)
+    for (int attempt = 0;; ++attempt) {
+        int expected = k;
+        if (__atomic_compare_exchange_n(go, &expected, k + 1, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) break;
+        if (expected != SERVE_IDLE || attempt > 0) {
+            h->serving = false;
+            return fail(h, QS_ERR_CUDA, "qs_serve_step: the server's handshake word holds an unexpected value");
+        }
+        // the server retired while the host was idle; its launch ends by itself
+        DeviceGuard g(h->device);
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        h->serving = false;
+        if (e != cudaSuccess) return cuda_fail(h, e, "qs_serve_step");
+        qs_status st = serve_launch(h);
+        if (st != QS_OK) return st;
+    }
+    volatile int* fin = h->serve_words + 1;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (unsigned long i = 1; *fin != k + 1; ++i) {
+        if ((i & 4095) == 0) {
+            DeviceGuard g(h->device);
+            const cudaError_t q = cudaStreamQuery(h->stream);
+            if (q != cudaErrorNotReady) {
+                if (*fin == k + 1) break;
+                h->serving = false;
+                if (q == cudaSuccess) return fail(h, QS_ERR_CUDA, "qs_serve_step: the server ended before the step completed");
+                return cuda_fail(h, q, "qs_serve_step");
+            }
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(10))
+                return fail(h, QS_ERR_TIMEOUT, "qs_serve_step: the step did not complete within 10 s");
+        }
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    h->serve_k = k + 1;
+    if (h->status_mapped && (*(volatile int32_t*)h->status_h & 1))
+        return fail(h, QS_ERR_STATE_NONFINITE, "a drone state became non-finite");
+    return QS_OK;
+}
+
+qs_status qs_serve_end(qs_env* h) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_serve_end: NULL handle");
+    if (!h->serving) return QS_OK;
+    int expected = h->serve_k;
+    // fails only when the server already retired (SERVE_IDLE): its launch is ending
+    __atomic_compare_exchange_n(h->serve_words, &expected, SERVE_STOP, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST);
+    DeviceGuard g(h->device);
+    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    h->serving = false;
+    if (e != cudaSuccess) return cuda_fail(h, e, "qs_serve_end");
+    if (h->status_mapped && (*(volatile int32_t*)h->status_h & 1))
+        return fail(h, QS_ERR_STATE_NONFINITE, "a drone state became non-finite");
     return QS_OK;
 }
 

@@ -127,6 +127,27 @@ cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, in
 // lanes, P = 1 (every class at most 32 wide) or 2 (at most 64 wide).
 cudaError_t launch_rollout_ws(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int P, const int* perm,
                               const RolloutIO& io, int t0, int nsteps, cudaStream_t s);
+// Resident step server (k_serve): commands, outputs and the handshake words
+// live in page-locked host memory mapped into the device. Codes of the go
+// word besides a step count: the host ends the launch; the server retired.
+constexpr int SERVE_STOP = -1, SERVE_IDLE = -2;
+struct ServeIO {
+    const float* act;            // [D][4]
+    float* obs;                  // [D][obs_dim] or null
+    float* rew;                  // [D] or null
+    uint8_t* done;               // [E] or null
+    int* go;                     // steps posted by the host (or a stop code)
+    int* fin;                    // steps completed
+    unsigned long long* count;   // device: CTAs finished since the launch began
+    int* relay;                  // device: the value of go CTA 0 last acted on
+    long long idle_ns;           // the server retires after this long without a posted step
+};
+// One cooperative launch of n_tiles warp-specialised CTAs (64P threads) that
+// runs global steps k0, k0 + 1, ... as the host posts them.
+cudaError_t launch_serve(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int P, const int* perm,
+                         const ServeIO& io, int k0, cudaStream_t s);
+// CTAs of the server the device keeps resident at once.
+int serve_resident_ctas(const Consts& c, int P);
 // CTAs of `block` threads the device keeps resident at once for k_rollout
 // (the instance with or without scenarios and downwash).
 int rollout_grid(int block, bool extended);

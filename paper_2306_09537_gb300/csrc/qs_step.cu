@@ -818,6 +818,178 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_rollout_ws(const C
     if (m.lane == 0) store_env<EXT>(er, dv, m.e);
 }
 
+// ---------------------------------------------------------------- resident step server
+// A synchronous host loop (post commands, wait, read the outputs) pays a
+// launch and a completion round trip per step on the per-call path. The
+// server is one cooperative launch of the warp-specialised CTAs that keeps the
+// drones in the dynamics warps' registers and steps them each time the host
+// posts a step, with commands read from and outputs written to page-locked
+// host memory in place. Handshake words in page-locked host memory: `go`
+// counts the steps the host has posted (SERVE_STOP: end the launch;
+// SERVE_IDLE: the server retired after waiting too long); `fin` counts the
+// steps completed, written by the last CTA to finish each step (found with a
+// counter in device memory). Only CTA 0 polls `go` over the host link; it
+// relays what it reads through a word in device memory that the other CTAs
+// poll (one reader of the host's line instead of one per CTA). Measured on
+// GB300 at 8192 single-drone envs: one system-scope fence per CTA instead of
+// one per thread, and the relay instead of every CTA polling the host, took a
+// posted step from 15.8 to 11.1 us; a completion byte per CTA polled by the
+// host instead of the counter and fin was slower (11.7 us: 64 CTAs write each
+// line the host re-reads).
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_acquire_sys(const int* p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_sys(int* p, int v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 of CTAs other than 0: the relayed value once it leaves `posted`.
+// CTA 0 relays every value it acts on, so this wait ends once CTA 0's does;
+// its bound (4 idle_ns + 1 s, well past CTA 0's) only guards against a CTA 0
+// that stopped answering, after which the CTA stops as if the server had
+// retired.
+__device__ __forceinline__ int serve_follow(const int* relay, int posted, long long idle_ns) {
+    const unsigned long long t0 = global_ns(), limit = 4ull * (unsigned long long)idle_ns + 1000000000ull;
+    for (;;) {
+        const int v = ld_acquire_gpu(relay);
+        if (v != posted) return v;
+        if (global_ns() - t0 > limit) return SERVE_IDLE;
+        __nanosleep(64);
+    }
+}
+
+// Thread 0 of CTA 0: the value of `go` once it leaves `posted` (the steps
+// already run). After idle_ns without an answer the server retires by
+// swapping go from `posted` to SERVE_IDLE; the swap fails only when the host
+// posted a step (or stopped) first, so every CTA of the launch sees one
+// outcome.
+__device__ __forceinline__ int serve_wait(int* go, int posted, long long idle_ns) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        const int v = ld_acquire_sys(go);
+        if (v != posted) return v;
+        if (global_ns() - t0 > (unsigned long long)idle_ns) {
+            const int old = atomicCAS_system(go, posted, SERVE_IDLE);
+            __threadfence_system();
+            return old == posted ? SERVE_IDLE : old;
+        }
+        __nanosleep(32);
+    }
+}
+
+// Step k of the launch (global step k0 + k): B0 (the host posted it; the
+// noise side has drawn its motor normals into buffer k & 1), the per-call
+// warp-specialised step (B1, B2) with the observation rows of step k stored
+// by the noise side after B2 and the next step's normals drawn after them,
+// then B3, after which thread 0 fences the CTA's host writes at system scope
+// and counts the CTA done; the last CTA publishes fin = k0 + k + 1.
+template <bool EXT, int P>
+__global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_serve(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
+                                                                  const int* __restrict__ perm, const ServeIO io, const int k0) {
+    __shared__ WsShared<P> sh;
+    __shared__ int s_go;
+    const Tile tile = tile_at(dv, tiles, blockIdx.x, 32 * P);
+    const WsMap m = ws_map<P>(dv, tile, perm);
+    const bool noise = threadIdx.x >= 32 * P;
+    const uint32_t tick0 = (noise && m.act) ? dv.tick[m.e] : 0u;  // the dynamics side writes it back at the end
+    Drone s;
+    EnvRegs er;
+    uint32_t ev = 0;
+    GoalCache gc{{0.f, 0.f, 0.f}, 0, -1};
+    if (!noise && m.act) {
+        load_drone(s, dv.st, dv.D, m.d);
+        load_env<EXT>(er, c, dv, m.e);
+    }
+    if (noise) ws_motor_normals<P>(c, sh, m, tick0, 0);
+    const float4* act4 = reinterpret_cast<const float4*>(io.act) + m.d;
+    for (int k = 0;; ++k) {
+        if (threadIdx.x == 0) {
+            if (blockIdx.x == 0) {
+                s_go = serve_wait(io.go, k0 + k, io.idle_ns);
+                st_release_gpu(io.relay, s_go);
+            } else {
+                s_go = serve_follow(io.relay, k0 + k, io.idle_ns);
+            }
+        }
+        __syncthreads();  // B0
+        if (s_go != k0 + k + 1) break;  // SERVE_STOP or SERVE_IDLE
+        const int b = k & 1;
+        if (noise) {
+            const uint32_t tick = tick0 + (uint32_t)k;
+            __syncthreads();  // B1
+            float ex[3] = {0.f, 0.f, 0.f}, evv[3] = {0.f, 0.f, 0.f}, ew[3] = {0.f, 0.f, 0.f};
+            if (m.act && io.obs && (c.flags & QS_F_OBS_NOISE)) obs_noise(c, tick, m.d, 0u, ex, evv, ew);
+            __syncthreads();  // B2
+            if (io.obs) ws_store_obs<P>(c, dv, tile, perm, sh, m, b, io.obs, ex, evv, ew);
+            ws_motor_normals<P>(c, sh, m, tick + 1, b ^ 1);
+        } else {
+            // the host's commands of this step: fetched again, never from a cached line
+            const float4 a = m.act ? __ldcv(act4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            ws_dynamics_step<EXT, P, false>(c, dv, sh, m, s, er, ev, a, b, io.rew, io.done, gc);
+        }
+        __syncthreads();  // B3
+        if (threadIdx.x == 0) {
+            // the CTA's host writes of the step (ordered before it by B3) before its count
+            __threadfence_system();
+            const unsigned long long n = atomicAdd(io.count, 1ull) + 1ull;
+            if (n == (unsigned long long)gridDim.x * (unsigned long long)(k + 1)) {
+                __threadfence_system();
+                st_release_sys(io.fin, k0 + k + 1);
+            }
+        }
+    }
+    if (noise || !m.act) return;
+    dv.ev[m.d] = ev;
+    store_drone(s, dv.st, dv.D, m.d);
+    if (m.lane == 0) store_env<EXT>(er, dv, m.e);
+}
+
+cudaError_t launch_serve(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int P, const int* perm,
+                         const ServeIO& io, int k0, cudaStream_t st) {
+    const bool ext = extended(c);
+    const void* fn = P == 1 ? (ext ? (const void*)k_serve<true, 1> : (const void*)k_serve<false, 1>)
+                            : (ext ? (const void*)k_serve<true, 2> : (const void*)k_serve<false, 2>);
+    if (P != 1 && P != 2) return cudaErrorInvalidValue;
+    Consts cc = c;
+    Dev dd = dv;
+    ServeIO ii = io;
+    const Tile* tt = tiles;
+    const int* pp = perm;
+    int kk = k0;
+    void* args[] = {&cc, &dd, &tt, &pp, &ii, &kk};
+    return cudaLaunchCooperativeKernel(fn, dim3(n_tiles), dim3(64 * P), args, 0, st);
+}
+
+int serve_resident_ctas(const Consts& c, int P) {
+    int dev = 0, n_sm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const bool ext = extended(c);
+    const void* fn = P == 1 ? (ext ? (const void*)k_serve<true, 1> : (const void*)k_serve<false, 1>)
+                            : (ext ? (const void*)k_serve<true, 2> : (const void*)k_serve<false, 2>);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 64 * P, 0) != cudaSuccess) return 0;
+    return occ * n_sm;
+}
+
 template <bool EXT>
 cudaError_t launch_k_step(const Consts& c, const Dev& dv, const ClassPlan& cp, const Tile* t, const int* perm,
                           const StepIO& io, int observe_only, size_t smem, cudaStream_t st) {

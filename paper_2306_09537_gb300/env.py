@@ -97,6 +97,44 @@ class QuadSwarmEnv:
     def sync(self):
         qs.qs_sync(self.h)
 
+    def serve(self, idle_ms: int = 1000) -> "Server":
+        """Resident stepping with page-locked host buffers (see qs_serve_begin):
+
+            with env.serve() as srv:
+                srv.actions[:] = a          # host tensor [D][4]
+                srv.step()                  # returns when obs / reward / done are in host memory
+                use(srv.obs, srv.reward, srv.done)
+        """
+        return Server(self, idle_ms)
+
+
+class Server:
+    """Page-locked host buffers and a resident step server of one env handle."""
+
+    def __init__(self, env: QuadSwarmEnv, idle_ms: int = 1000):
+        self.env = env
+        self.actions = torch.zeros(env.D, 4).pin_memory()
+        self.obs = torch.zeros(env.D, env.obs_dim).pin_memory()
+        self.reward = torch.zeros(env.D).pin_memory()
+        self.done = torch.zeros(env.E, dtype=torch.uint8).pin_memory()
+        qs.qs_serve_begin(env.h, self.actions, self.obs, self.reward, self.done, idle_ms)
+        self.active = True
+
+    def step(self):
+        qs.qs_serve_step(self.env.h)
+        return self.obs, self.reward, self.done
+
+    def close(self):
+        if self.active:
+            self.active = False
+            qs.qs_serve_end(self.env.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
 
 class RolloutFn(torch.autograd.Function):
     """Differentiable rollout of the step (smooth contacts when the env has the

@@ -33,7 +33,7 @@ EXPORTS = ["qs_config_default", "qs_create", "qs_destroy", "qs_get_dims", "qs_re
            "qs_rollout", "qs_set_rollout_shape", "qs_get_rollout_shape", "qs_diff_workspace_size",
            "qs_diff_forward", "qs_diff_backward", "qs_diff_grad_static", "qs_get_state", "qs_set_state",
            "qs_get_events", "qs_get_scenario", "qs_set_scenario", "qs_get_goals", "qs_sync", "qs_set_block",
-           "qs_get_block", "qs_last_error"]
+           "qs_get_block", "qs_serve_begin", "qs_serve_step", "qs_serve_end", "qs_last_error"]
 # training scenarios (Sec. III-D) and goal formations, in the order of QS_SCN_* / QS_FORM_*
 SCENARIOS = ["single", "static", "dynamic", "swap", "shrink_expand", "swarm_vs_swarm", "pursuit_lissajous",
              "pursuit_bezier"]
@@ -106,6 +106,9 @@ def _load():
     L.qs_set_scenario.argtypes = [V, V]
     L.qs_get_goals.argtypes = [V, V]
     L.qs_sync.argtypes = [V]
+    L.qs_serve_begin.argtypes = [V, V, V, V, V, C.c_int32]
+    L.qs_serve_step.argtypes = [V]
+    L.qs_serve_end.argtypes = [V]
     L.qs_set_block.argtypes = [V, C.c_int32, C.c_int32]
     L.qs_get_block.argtypes = [V, C.c_int32, P(C.c_int32)]
     L.qs_last_error.argtypes = [V]
@@ -254,6 +257,18 @@ def qs_get_goals(h, goals):
 
 def qs_sync(h):
     return _check(_L.qs_sync(h), h)
+
+
+def qs_serve_begin(h, actions, obs=None, reward=None, done=None, idle_ms: int = 1000):
+    return _check(_L.qs_serve_begin(h, _p(actions), _p(obs), _p(reward), _p(done), int(idle_ms)), h)
+
+
+def qs_serve_step(h):
+    return _check(_L.qs_serve_step(h), h)
+
+
+def qs_serve_end(h):
+    return _check(_L.qs_serve_end(h), h)
 
 
 def qs_set_block(h, width: int, block: int):
