@@ -416,6 +416,21 @@ def run_forms(dev, stream, seed):
         env.close()
         del acts
 
+        # swarm size sweep at 32,768 drones, K = 6 (up to the paper's largest team,
+        # N = 128): the O(N^2) pair pass per env; default launch shapes
+        import dataclasses
+        sweep = []
+        for N in (8, 16, 32, 64, 128):
+            env = make(dataclasses.replace(W.SWARM, n_envs=32768 // N, swarm=N))
+            acts = torch.from_numpy(W.actions(seed, 200, env.D)).to(dev)
+            ms_call = per_call(env, acts, 100)
+            ms_roll = rollout(env, acts, 200)
+            sweep.append({"swarm": N, "n_envs": env.E, "call": env.D / ms_call * 1e3, "rollout": env.D / ms_roll * 1e3,
+                          "rollout_shape": list(qs.qs_get_rollout_shape(env.h))})
+            env.close()
+            del acts
+        forms["swarm_size_sweep"] = sweep
+
         # differentiable rollout: 1024 x 8, T = 128, checkpoints every 16, smooth
         # contacts; and the same with the step's own (discrete) contacts
         wl = W.DIFF
