@@ -243,33 +243,34 @@ def run_gpu(args, world, rank, local):
         # step (qs_step_host).
         ring = W.actions(seed + 1, 64, env.D)
         e2e_steps = min(steps, 500)
-        srv = env.serve()
-        a_np, r_np = srv.actions.numpy(), srv.reward.numpy()
-        for t in range(3):
-            np.copyto(a_np, ring[t % 64])
-            qs.qs_serve_step(env.h)
-        barrier(world)
-        t0 = time.perf_counter()
-        check = 0.0
-        for t in range(e2e_steps):
-            np.copyto(a_np, ring[t % 64])
-            qs.qs_serve_step(env.h)
-            check += float(r_np[0])
-        e2e_local = time.perf_counter() - t0
-        srv.close()
-        e2e_s = max_over_ranks(e2e_local, world)
-        a_host = torch.from_numpy(ring).pin_memory()
-        obs_h = torch.empty(env.D, env.obs_dim).pin_memory()
-        rew_h = torch.empty(env.D).pin_memory()
-        done_h = torch.empty(env.E, dtype=torch.uint8).pin_memory()
-        for t in range(3):
-            qs.qs_step_host(env.h, a_host[t % 64], obs_h, rew_h, done_h)
-        barrier(world)
-        t0 = time.perf_counter()
-        for t in range(e2e_steps):
-            qs.qs_step_host(env.h, a_host[t % 64], obs_h, rew_h, done_h)
-            check += float(rew_h[0])
-        e2e_host_s = max_over_ranks(time.perf_counter() - t0, world)
+        if not args.no_e2e:
+            srv = env.serve()
+            a_np, r_np = srv.actions.numpy(), srv.reward.numpy()
+            for t in range(3):
+                np.copyto(a_np, ring[t % 64])
+                qs.qs_serve_step(env.h)
+            barrier(world)
+            t0 = time.perf_counter()
+            check = 0.0
+            for t in range(e2e_steps):
+                np.copyto(a_np, ring[t % 64])
+                qs.qs_serve_step(env.h)
+                check += float(r_np[0])
+            e2e_local = time.perf_counter() - t0
+            srv.close()
+            e2e_s = max_over_ranks(e2e_local, world)
+            a_host = torch.from_numpy(ring).pin_memory()
+            obs_h = torch.empty(env.D, env.obs_dim).pin_memory()
+            rew_h = torch.empty(env.D).pin_memory()
+            done_h = torch.empty(env.E, dtype=torch.uint8).pin_memory()
+            for t in range(3):
+                qs.qs_step_host(env.h, a_host[t % 64], obs_h, rew_h, done_h)
+            barrier(world)
+            t0 = time.perf_counter()
+            for t in range(e2e_steps):
+                qs.qs_step_host(env.h, a_host[t % 64], obs_h, rew_h, done_h)
+                check += float(rew_h[0])
+            e2e_host_s = max_over_ranks(time.perf_counter() - t0, world)
 
     D, E, od = env.D, env.E, env.obs_dim
     value = world * D * steps / (total_ms * 1e-3)
@@ -297,11 +298,12 @@ def run_gpu(args, world, rank, local):
             "config": {"workload": WL.name, "n_envs": WL.n_envs, "swarm": 1, "k_neighbors": WL.k_neighbors,
                        "features": list(BENCH_FEATURES), "form": "per-call qs_step, state in HBM",
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-            "e2e": {"value": world * D * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": D * 16,
-                    "d2h_bytes_per_step": D * od * 4 + D * 4 + E, "api": "qs_serve_step (resident server)",
-                    "us_per_step": e2e_s / e2e_steps * 1e6,
-                    "qs_step_host": {"value": world * D * e2e_steps / e2e_host_s,
-                                     "us_per_step": e2e_host_s / e2e_steps * 1e6}},
+            "e2e": None if args.no_e2e else {
+                "value": world * D * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": D * 16,
+                "d2h_bytes_per_step": D * od * 4 + D * 4 + E, "api": "qs_serve_step (resident server)",
+                "us_per_step": e2e_s / e2e_steps * 1e6,
+                "qs_step_host": {"value": world * D * e2e_steps / e2e_host_s,
+                                 "us_per_step": e2e_host_s / e2e_steps * 1e6}},
             "gpu_launches": steps * n_classes, "roofline": roof,
             "clocks": clk.summary(), "wall_s_timed": t_wall}
     env.close()
@@ -573,6 +575,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end loops (for profiler runs: a profiler that completes each launch before "
+                         "returning would hold the resident server's launch until it retires, every step)")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / swarm / uneven / sweep forms")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
