@@ -267,7 +267,8 @@ qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, fl
  * qs_rollout exactly as if every step had been a qs_step. qs_serve_step
  * returns after the step's outputs are in host memory; a non-finite drone
  * state is reported as by qs_sync; a step that does not complete within 10 s
- * returns QS_ERR_TIMEOUT. */
+ * returns QS_ERR_TIMEOUT, after which qs_serve_step keeps waiting for that
+ * same step and qs_serve_end stops the server once the step is done. */
 qs_status qs_serve_begin(qs_env* h, const float* actions_host, float* obs_host, float* reward_host,
                          uint8_t* done_host, int32_t idle_ms);
 qs_status qs_serve_step(qs_env* h);

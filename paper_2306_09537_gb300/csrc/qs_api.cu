@@ -1065,6 +1065,7 @@ qs_status qs_serve_step(qs_env* h) {
     for (int attempt = 0;; ++attempt) {
         int expected = k;
         if (__atomic_compare_exchange_n(go, &expected, k + 1, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) break;
+        if (expected == k + 1) break;  // posted by a call that returned QS_ERR_TIMEOUT: keep waiting for it
         if (expected != SERVE_IDLE || attempt > 0) {
             h->serving = false;
             return fail(h, QS_ERR_CUDA, "qs_serve_step: the server's handshake word holds an unexpected value");
@@ -1103,9 +1104,12 @@ qs_status qs_serve_step(qs_env* h) {
 qs_status qs_serve_end(qs_env* h) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_serve_end: NULL handle");
     if (!h->serving) return QS_OK;
-    int expected = h->serve_k;
-    // fails only when the server already retired (SERVE_IDLE): its launch is ending
-    __atomic_compare_exchange_n(h->serve_words, &expected, SERVE_STOP, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST);
+    // from whatever step go holds (serve_k, or serve_k + 1 after a timed-out
+    // post); a retired server (SERVE_IDLE) is ending its launch already
+    int expected = __atomic_load_n(h->serve_words, __ATOMIC_SEQ_CST);
+    while (expected >= 0 &&
+           !__atomic_compare_exchange_n(h->serve_words, &expected, SERVE_STOP, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {
+    }
     DeviceGuard g(h->device);
     const cudaError_t e = cudaStreamSynchronize(h->stream);
     h->serving = false;
