@@ -236,25 +236,25 @@ def run_gpu(args, world, rank, local):
         total_ms = max_over_ranks(float(per.sum()), world)
         env.sync()
 
-        # end to end, synchronous host loop: each step's commands copied into
-        # page-locked host memory, the step posted, its observation, reward and
-        # done read back from page-locked host memory. Through the resident
-        # server (qs_serve_step) and, for comparison, the per-call host-buffer
-        # step (qs_step_host).
+        # end to end, synchronous host loop: each step's commands read by the
+        # GPU from page-locked host memory (a ring of 64 command slots), the
+        # step posted, its observation, reward and done written to page-locked
+        # host memory and read there. Through the resident server
+        # (qs_serve_step) and, for comparison, the per-call host-buffer step
+        # (qs_step_host) on the same ring.
         ring = W.actions(seed + 1, 64, env.D)
         e2e_steps = min(steps, 500)
         if not args.no_e2e:
-            srv = env.serve()
-            a_np, r_np = srv.actions.numpy(), srv.reward.numpy()
+            srv = env.serve(slots=64)
+            srv.slots.copy_(torch.from_numpy(ring))
+            r_np = srv.reward.numpy()
             for t in range(3):
-                np.copyto(a_np, ring[t % 64])
-                qs.qs_serve_step(env.h)
+                qs.qs_serve_step(env.h, t % 64)
             barrier(world)
             t0 = time.perf_counter()
             check = 0.0
             for t in range(e2e_steps):
-                np.copyto(a_np, ring[t % 64])
-                qs.qs_serve_step(env.h)
+                qs.qs_serve_step(env.h, t % 64)
                 check += float(r_np[0])
             e2e_local = time.perf_counter() - t0
             srv.close()

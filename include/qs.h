@@ -243,12 +243,15 @@ qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, fl
  * by two words of page-locked host memory, one the host advances and one the
  * last CTA of a step advances.
  *
- *  actions_host [D][4] in, obs_host [D][obs_dim], reward_host [D], done_host
- *  [E] out (outputs nullable): page-locked host memory the device can map
- *  (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory; actions 16-byte,
- *  obs 8-byte aligned), owned by the caller, read and written in place by the
- *  server until qs_serve_end. Write a step's commands, call qs_serve_step, read
- *  its outputs.
+ *  actions_host [n_slots][D][4] in (n_slots >= 1 command slots; a step reads
+ *  the slot qs_serve_step names, so commands can be written ahead), obs_host
+ *  [D][obs_dim], reward_host [D], done_host [E] out (outputs nullable):
+ *  page-locked host memory the device can map (cudaHostAlloc /
+ *  cudaHostRegister, e.g. torch pin_memory; actions 16-byte, obs 8-byte
+ *  aligned), owned by the caller, read and written in place by the server
+ *  until qs_serve_end. Write a step's commands into a slot, call
+ *  qs_serve_step(h, slot), read its outputs; a slot out of range returns
+ *  QS_ERR_ARG.
  *  idle_ms: when no step is posted for about this long the server retires
  *  (the drones return to the handle's memory and the launch ends);
  *  qs_serve_step then starts it again, with no effect on the results.
@@ -269,9 +272,9 @@ qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, fl
  * state is reported as by qs_sync; a step that does not complete within 10 s
  * returns QS_ERR_TIMEOUT, after which qs_serve_step keeps waiting for that
  * same step and qs_serve_end stops the server once the step is done. */
-qs_status qs_serve_begin(qs_env* h, const float* actions_host, float* obs_host, float* reward_host,
+qs_status qs_serve_begin(qs_env* h, const float* actions_host, int32_t n_slots, float* obs_host, float* reward_host,
                          uint8_t* done_host, int32_t idle_ms);
-qs_status qs_serve_step(qs_env* h);
+qs_status qs_serve_step(qs_env* h, int32_t slot);
 qs_status qs_serve_end(qs_env* h);
 
 /* T control steps (T >= 1) of every env, batched: actions_dev [T][D][4],

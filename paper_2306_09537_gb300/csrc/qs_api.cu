@@ -65,8 +65,8 @@ struct qs_env {
     bool status_mapped = false;   // the device status word is page-locked host memory
     // resident step server (qs_serve_*): while it runs its launch occupies the stream
     bool serving = false;
-    int* serve_words = nullptr;               // page-locked, mapped: [0] go, [1] fin
-    unsigned long long* serve_dev = nullptr;  // device: [0] CTAs finished since the launch began, [1] relay word
+    unsigned long long* serve_words = nullptr;  // page-locked, mapped: [0] go (slot << 32 | steps), [1] fin (low half)
+    unsigned long long* serve_dev = nullptr;    // device: [0] CTAs finished since the launch began, [1] relay word
     ServeIO serve_io{};
     int serve_k = 0;                             // steps completed since qs_serve_begin
     std::string err;
@@ -342,11 +342,11 @@ qs_status do_step(qs_env* h, const float* act, float* obs, float* rew, uint8_t* 
 // (Re)starts the resident server at step serve_k: go = fin = serve_k, the CTA
 // counter zeroed and the relay word at serve_k before the cooperative launch.
 qs_status serve_launch(qs_env* h) {
-    volatile int* w = h->serve_words;
-    w[0] = h->serve_k;
-    w[1] = h->serve_k;
+    const unsigned long long go = (unsigned long long)(unsigned int)h->serve_k;  // slot 0
+    __atomic_store_n(h->serve_words, go, __ATOMIC_SEQ_CST);
+    *(volatile int*)(h->serve_words + 1) = h->serve_k;
     std::atomic_thread_fence(std::memory_order_seq_cst);
-    const unsigned long long init[2] = {0ull, (unsigned long long)(unsigned int)h->serve_k};
+    const unsigned long long init[2] = {0ull, go};
     cudaError_t e = cudaMemcpy(h->serve_dev, init, sizeof init, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = launch_serve(h->c, h->dv, h->d_wtiles, h->n_wtiles, h->ws_p, h->d_perm, h->serve_io, h->serve_k, h->stream);
@@ -997,12 +997,13 @@ qs_status qs_get_block(const qs_env* h, int32_t width, int32_t* block) {
     return QS_OK;
 }
 
-qs_status qs_serve_begin(qs_env* h, const float* actions_host, float* obs_host, float* reward_host, uint8_t* done_host,
-                         int32_t idle_ms) {
+qs_status qs_serve_begin(qs_env* h, const float* actions_host, int32_t n_slots, float* obs_host, float* reward_host,
+                         uint8_t* done_host, int32_t idle_ms) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_serve_begin: NULL handle");
     if (h->serving) return fail(h, QS_ERR_ARG, "qs_serve_begin: the handle is already serving");
     if (!actions_host) return fail(h, QS_ERR_ARG, "qs_serve_begin: actions_host is NULL");
     if (idle_ms < 1) return fail(h, QS_ERR_ARG, "qs_serve_begin: idle_ms must be >= 1");
+    if (n_slots < 1) return fail(h, QS_ERR_ARG, "qs_serve_begin: n_slots must be >= 1");
     if (!h->ws_p || h->n_wtiles < 1)
         return fail(h, QS_ERR_UNSUPPORTED, "qs_serve_begin: every swarm must have at most 64 drones");
     DeviceGuard g(h->device);
@@ -1028,15 +1029,15 @@ qs_status qs_serve_begin(qs_env* h, const float* actions_host, float* obs_host, 
         return fail(h, QS_ERR_UNSUPPORTED, "qs_serve_begin: the handle's CTAs do not fit on the device at once");
     if (!h->serve_words) {
         void* dp = nullptr;
-        if (cudaHostAlloc((void**)&h->serve_words, 2 * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        if (cudaHostAlloc((void**)&h->serve_words, 2 * sizeof(unsigned long long), cudaHostAllocMapped) != cudaSuccess ||
             cudaHostGetDevicePointer(&dp, h->serve_words, 0) != cudaSuccess || !dp) {
             if (h->serve_words) cudaFreeHost(h->serve_words);
             h->serve_words = nullptr;
             cudaGetLastError();
             return fail(h, QS_ERR_OOM, "qs_serve_begin: handshake words");
         }
-        h->serve_io.go = (int*)dp;
-        h->serve_io.fin = (int*)dp + 1;
+        h->serve_io.go = (unsigned long long*)dp;
+        h->serve_io.fin = (int*)((unsigned long long*)dp + 1);
     }
     if (!h->serve_dev && cudaMalloc(&h->serve_dev, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         h->serve_dev = nullptr;
@@ -1050,23 +1051,30 @@ qs_status qs_serve_begin(qs_env* h, const float* actions_host, float* obs_host, 
     h->serve_io.rew = r;
     h->serve_io.done = dn;
     h->serve_io.count = h->serve_dev;
-    h->serve_io.relay = (int*)(h->serve_dev + 1);  // low word of [1] (the device is little-endian)
+    h->serve_io.relay = h->serve_dev + 1;
+    h->serve_io.n_slots = n_slots;
     h->serve_io.idle_ns = (long long)idle_ms * 1000000;
     h->serve_k = 0;
     return serve_launch(h);
 }
 
-qs_status qs_serve_step(qs_env* h) {
+qs_status qs_serve_step(qs_env* h, int32_t slot) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_serve_step: NULL handle");
     if (!h->serving) return fail(h, QS_ERR_ARG, "qs_serve_step: the handle is not serving (qs_serve_begin)");
+    if (slot < 0 || slot >= h->serve_io.n_slots) return fail(h, QS_ERR_ARG, "qs_serve_step: slot out of range");
     const int k = h->serve_k;
-    int* go = h->serve_words;
-    // the caller's command writes happen before the post (release)
-    for (int attempt = 0;; ++attempt) {
-        int expected = k;
-        if (__atomic_compare_exchange_n(go, &expected, k + 1, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) break;
-        if (expected == k + 1) break;  // posted by a call that returned QS_ERR_TIMEOUT: keep waiting for it
-        if (expected != SERVE_IDLE || attempt > 0) {
+    unsigned long long* go = h->serve_words;
+    // the caller's command writes happen before the post (sequentially consistent swap)
+    for (int relaunches = 0;;) {
+        unsigned long long cur = __atomic_load_n(go, __ATOMIC_SEQ_CST);
+        const int steps = (int)(unsigned int)(cur & 0xffffffffull);
+        if (steps == k) {
+            const unsigned long long want = ((unsigned long long)(unsigned int)slot << 32) | (unsigned int)(k + 1);
+            if (__atomic_compare_exchange_n(go, &cur, want, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) break;
+            continue;  // the server retired meanwhile
+        }
+        if (steps == k + 1) break;  // posted by a call that returned QS_ERR_TIMEOUT: keep waiting for it
+        if (steps != SERVE_IDLE || relaunches++ > 0) {
             h->serving = false;
             return fail(h, QS_ERR_CUDA, "qs_serve_step: the server's handshake word holds an unexpected value");
         }
@@ -1078,7 +1086,7 @@ qs_status qs_serve_step(qs_env* h) {
         qs_status st = serve_launch(h);
         if (st != QS_OK) return st;
     }
-    volatile int* fin = h->serve_words + 1;
+    volatile int* fin = (volatile int*)(h->serve_words + 1);
     const auto t0 = std::chrono::steady_clock::now();
     for (unsigned long i = 1; *fin != k + 1; ++i) {
         if ((i & 4095) == 0) {
@@ -1106,9 +1114,10 @@ qs_status qs_serve_end(qs_env* h) {
     if (!h->serving) return QS_OK;
     // from whatever step go holds (serve_k, or serve_k + 1 after a timed-out
     // post); a retired server (SERVE_IDLE) is ending its launch already
-    int expected = __atomic_load_n(h->serve_words, __ATOMIC_SEQ_CST);
-    while (expected >= 0 &&
-           !__atomic_compare_exchange_n(h->serve_words, &expected, SERVE_STOP, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) {
+    unsigned long long cur = __atomic_load_n(h->serve_words, __ATOMIC_SEQ_CST);
+    while ((int)(unsigned int)(cur & 0xffffffffull) >= 0) {
+        const unsigned long long stop = (cur & ~0xffffffffull) | (unsigned long long)(unsigned int)SERVE_STOP;
+        if (__atomic_compare_exchange_n(h->serve_words, &cur, stop, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST)) break;
     }
     DeviceGuard g(h->device);
     const cudaError_t e = cudaStreamSynchronize(h->stream);

@@ -132,14 +132,15 @@ cudaError_t launch_rollout_ws(const Consts& c, const Dev& dv, const Tile* tiles,
 // word besides a step count: the host ends the launch; the server retired.
 constexpr int SERVE_STOP = -1, SERVE_IDLE = -2;
 struct ServeIO {
-    const float* act;            // [D][4]
+    const float* act;            // [n_slots][D][4]
     float* obs;                  // [D][obs_dim] or null
     float* rew;                  // [D] or null
     uint8_t* done;               // [E] or null
-    int* go;                     // steps posted by the host (or a stop code)
+    unsigned long long* go;      // low half: steps posted by the host (or a stop code); high half: command slot
     int* fin;                    // steps completed
     unsigned long long* count;   // device: CTAs finished since the launch began
-    int* relay;                  // device: the value of go CTA 0 last acted on
+    unsigned long long* relay;   // device: the value of go CTA 0 last acted on
+    int n_slots;
     long long idle_ns;           // the server retires after this long without a posted step
 };
 // One cooperative launch of n_tiles warp-specialised CTAs (64P threads) that

@@ -825,8 +825,9 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_rollout_ws(const C
 // drones in the dynamics warps' registers and steps them each time the host
 // posts a step, with commands read from and outputs written to page-locked
 // host memory in place. Handshake words in page-locked host memory: `go`
-// counts the steps the host has posted (SERVE_STOP: end the launch;
-// SERVE_IDLE: the server retired after waiting too long); `fin` counts the
+// holds in its low half the steps the host has posted (SERVE_STOP: end the
+// launch; SERVE_IDLE: the server retired after waiting too long) and in its
+// high half the command slot of the last posted step; `fin` counts the
 // steps completed, written by the last CTA to finish each step (found with a
 // counter in device memory). Only CTA 0 polls `go` over the host link; it
 // relays what it reads through a word in device memory that the other CTAs
@@ -842,9 +843,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ __forceinline__ int ld_acquire_sys(const int* p) {
-    int v;
-    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -852,45 +853,50 @@ __device__ __forceinline__ void st_release_sys(int* p, int v) {
     asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_release_gpu(int* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_release_gpu(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+
+// The step count (or stop code) and the command slot of a go word.
+__device__ __forceinline__ int go_steps(unsigned long long v) { return (int)(unsigned int)(v & 0xffffffffull); }
+__device__ __forceinline__ int go_slot(unsigned long long v) { return (int)(unsigned int)(v >> 32); }
 
 // Thread 0 of CTAs other than 0: the relayed value once it leaves `posted`.
 // CTA 0 relays every value it acts on, so this wait ends once CTA 0's does;
 // its bound (4 idle_ns + 1 s, well past CTA 0's) only guards against a CTA 0
 // that stopped answering, after which the CTA stops as if the server had
 // retired.
-__device__ __forceinline__ int serve_follow(const int* relay, int posted, long long idle_ns) {
+__device__ __forceinline__ unsigned long long serve_follow(const unsigned long long* relay, int posted, long long idle_ns) {
     const unsigned long long t0 = global_ns(), limit = 4ull * (unsigned long long)idle_ns + 1000000000ull;
     for (;;) {
-        const int v = ld_acquire_gpu(relay);
-        if (v != posted) return v;
-        if (global_ns() - t0 > limit) return SERVE_IDLE;
+        const unsigned long long v = ld_acquire_gpu(relay);
+        if (go_steps(v) != posted) return v;
+        if (global_ns() - t0 > limit) return (unsigned long long)(unsigned int)SERVE_IDLE;
         __nanosleep(64);
     }
 }
 
-// Thread 0 of CTA 0: the value of `go` once it leaves `posted` (the steps
-// already run). After idle_ns without an answer the server retires by
-// swapping go from `posted` to SERVE_IDLE; the swap fails only when the host
-// posted a step (or stopped) first, so every CTA of the launch sees one
-// outcome.
-__device__ __forceinline__ int serve_wait(int* go, int posted, long long idle_ns) {
+// Thread 0 of CTA 0: the value of `go` once its step count leaves `posted`
+// (the steps already run). After idle_ns without an answer the server retires
+// by swapping go from the value it last read to SERVE_IDLE; the swap fails
+// only when the host posted a step (or stopped) first, so every CTA of the
+// launch sees one outcome.
+__device__ __forceinline__ unsigned long long serve_wait(unsigned long long* go, int posted, long long idle_ns) {
     const unsigned long long t0 = global_ns();
     for (;;) {
-        const int v = ld_acquire_sys(go);
-        if (v != posted) return v;
+        const unsigned long long v = ld_acquire_sys(go);
+        if (go_steps(v) != posted) return v;
         if (global_ns() - t0 > (unsigned long long)idle_ns) {
-            const int old = atomicCAS_system(go, posted, SERVE_IDLE);
+            const unsigned long long idle = (v & ~0xffffffffull) | (unsigned long long)(unsigned int)SERVE_IDLE;
+            const unsigned long long old = atomicCAS_system(go, v, idle);
             __threadfence_system();
-            return old == posted ? SERVE_IDLE : old;
+            return old == v ? idle : old;
         }
         __nanosleep(32);
     }
@@ -906,7 +912,7 @@ template <bool EXT, int P>
 __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_serve(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                                   const int* __restrict__ perm, const ServeIO io, const int k0) {
     __shared__ WsShared<P> sh;
-    __shared__ int s_go;
+    __shared__ unsigned long long s_go;
     const Tile tile = tile_at(dv, tiles, blockIdx.x, 32 * P);
     const WsMap m = ws_map<P>(dv, tile, perm);
     const bool noise = threadIdx.x >= 32 * P;
@@ -920,7 +926,6 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_serve(const Consts
         load_env<EXT>(er, c, dv, m.e);
     }
     if (noise) ws_motor_normals<P>(c, sh, m, tick0, 0);
-    const float4* act4 = reinterpret_cast<const float4*>(io.act) + m.d;
     for (int k = 0;; ++k) {
         if (threadIdx.x == 0) {
             if (blockIdx.x == 0) {
@@ -931,7 +936,9 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_serve(const Consts
             }
         }
         __syncthreads();  // B0
-        if (s_go != k0 + k + 1) break;  // SERVE_STOP or SERVE_IDLE
+        const unsigned long long g = s_go;
+        // SERVE_STOP, SERVE_IDLE, or a slot the host never checked
+        if (go_steps(g) != k0 + k + 1 || go_slot(g) >= io.n_slots) break;
         const int b = k & 1;
         if (noise) {
             const uint32_t tick = tick0 + (uint32_t)k;
@@ -943,6 +950,7 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_serve(const Consts
             ws_motor_normals<P>(c, sh, m, tick + 1, b ^ 1);
         } else {
             // the host's commands of this step: fetched again, never from a cached line
+            const float4* act4 = reinterpret_cast<const float4*>(io.act + (size_t)go_slot(g) * 4 * dv.D) + m.d;
             const float4 a = m.act ? __ldcv(act4) : make_float4(0.f, 0.f, 0.f, 0.f);
             ws_dynamics_step<EXT, P, false>(c, dv, sh, m, s, er, ev, a, b, io.rew, io.done, gc);
         }

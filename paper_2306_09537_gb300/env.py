@@ -97,31 +97,34 @@ class QuadSwarmEnv:
     def sync(self):
         qs.qs_sync(self.h)
 
-    def serve(self, idle_ms: int = 1000) -> "Server":
+    def serve(self, idle_ms: int = 1000, slots: int = 1) -> "Server":
         """Resident stepping with page-locked host buffers (see qs_serve_begin):
 
             with env.serve() as srv:
-                srv.actions[:] = a          # host tensor [D][4]
+                srv.actions[:] = a          # host tensor [D][4] (command slot 0)
                 srv.step()                  # returns when obs / reward / done are in host memory
                 use(srv.obs, srv.reward, srv.done)
-        """
-        return Server(self, idle_ms)
+
+        With slots > 1, srv.slots [slots][D][4] holds commands written ahead and
+        srv.step(slot) steps with slot `slot`."""
+        return Server(self, idle_ms, slots)
 
 
 class Server:
     """Page-locked host buffers and a resident step server of one env handle."""
 
-    def __init__(self, env: QuadSwarmEnv, idle_ms: int = 1000):
+    def __init__(self, env: QuadSwarmEnv, idle_ms: int = 1000, slots: int = 1):
         self.env = env
-        self.actions = torch.zeros(env.D, 4).pin_memory()
+        self.slots = torch.zeros(slots, env.D, 4).pin_memory()
+        self.actions = self.slots[0]
         self.obs = torch.zeros(env.D, env.obs_dim).pin_memory()
         self.reward = torch.zeros(env.D).pin_memory()
         self.done = torch.zeros(env.E, dtype=torch.uint8).pin_memory()
-        qs.qs_serve_begin(env.h, self.actions, self.obs, self.reward, self.done, idle_ms)
+        qs.qs_serve_begin(env.h, self.slots, self.obs, self.reward, self.done, idle_ms, slots)
         self.active = True
 
-    def step(self):
-        qs.qs_serve_step(self.env.h)
+    def step(self, slot: int = 0):
+        qs.qs_serve_step(self.env.h, slot)
         return self.obs, self.reward, self.done
 
     def close(self):

@@ -106,8 +106,8 @@ def _load():
     L.qs_set_scenario.argtypes = [V, V]
     L.qs_get_goals.argtypes = [V, V]
     L.qs_sync.argtypes = [V]
-    L.qs_serve_begin.argtypes = [V, V, V, V, V, C.c_int32]
-    L.qs_serve_step.argtypes = [V]
+    L.qs_serve_begin.argtypes = [V, V, C.c_int32, V, V, V, C.c_int32]
+    L.qs_serve_step.argtypes = [V, C.c_int32]
     L.qs_serve_end.argtypes = [V]
     L.qs_set_block.argtypes = [V, C.c_int32, C.c_int32]
     L.qs_get_block.argtypes = [V, C.c_int32, P(C.c_int32)]
@@ -259,12 +259,12 @@ def qs_sync(h):
     return _check(_L.qs_sync(h), h)
 
 
-def qs_serve_begin(h, actions, obs=None, reward=None, done=None, idle_ms: int = 1000):
-    return _check(_L.qs_serve_begin(h, _p(actions), _p(obs), _p(reward), _p(done), int(idle_ms)), h)
+def qs_serve_begin(h, actions, obs=None, reward=None, done=None, idle_ms: int = 1000, n_slots: int = 1):
+    return _check(_L.qs_serve_begin(h, _p(actions), int(n_slots), _p(obs), _p(reward), _p(done), int(idle_ms)), h)
 
 
-def qs_serve_step(h):
-    return _check(_L.qs_serve_step(h), h)
+def qs_serve_step(h, slot: int = 0):
+    return _check(_L.qs_serve_step(h, int(slot)), h)
 
 
 def qs_serve_end(h):

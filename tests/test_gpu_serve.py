@@ -84,6 +84,26 @@ def test_serve_equals_steps_uneven_with_scenarios_and_downwash():
                    feats=FEATS + ("downwash",))
 
 
+def test_serve_command_slots():
+    """Commands written ahead into slots, stepped in a shuffled slot order."""
+    a, b = twins([8] * 128, 6)
+    S, T = 5, 12
+    acts = W.actions(13, T, a.D)
+    order = np.random.default_rng(1).integers(0, S, T)
+    with a.serve(slots=S) as srv:
+        for t in range(T):
+            srv.slots[order[t]].copy_(torch.from_numpy(acts[t]))
+            o1, r1, d1 = srv.step(int(order[t]))
+            o2, r2, d2 = b.step(torch.from_numpy(acts[t]).to(DEV))
+            assert torch.equal(o1, o2.cpu()) and torch.equal(r1, r2.cpu()) and torch.equal(d1, d2.cpu()), t
+        for bad in (-1, S):
+            with pytest.raises(qs.QSError):
+                srv.step(bad)
+        srv.step(0)  # still serving after the refusals
+    with pytest.raises(qs.QSError):
+        qs.qs_serve_begin(a.h, srv.slots, n_slots=0)
+
+
 def test_serve_retires_when_idle_and_restarts():
     serve_vs_steps([8] * 64, 6, 8, pause_at=4, idle_ms=20)
 
