@@ -82,4 +82,7 @@ def test_null_handle_calls_fail_cleanly(qs):
     assert L.qs_sync(None) == qs.QS_ERR_ARG
     assert L.qs_rollout(None, 1, None, None, None, None) == qs.QS_ERR_ARG
     assert L.qs_get_dims(None, None, None, None) == qs.QS_ERR_ARG
+    assert L.qs_serve_begin(None, None, 1, None, None, None, 1000) == qs.QS_ERR_ARG
+    assert L.qs_serve_step(None, 0) == qs.QS_ERR_ARG
+    assert L.qs_serve_end(None) == qs.QS_ERR_ARG
     assert "NULL" in qs.qs_last_error(None)
