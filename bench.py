@@ -245,12 +245,14 @@ def run_gpu(args, world, rank, local):
         ring = W.actions(seed + 1, 64, env.D)
         e2e_steps = min(steps, 500)
         if not args.no_e2e:
+            # ranks align before serving: a collective enqueued behind the
+            # resident launch would wait until the server retires
+            barrier(world)
             srv = env.serve(slots=64)
             srv.slots.copy_(torch.from_numpy(ring))
             r_np = srv.reward.numpy()
             for t in range(3):
                 qs.qs_serve_step(env.h, t % 64)
-            barrier(world)
             t0 = time.perf_counter()
             check = 0.0
             for t in range(e2e_steps):
