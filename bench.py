@@ -591,7 +591,7 @@ def main():
         run_reference(args, world, rank)
         return
     line = run_gpu(args, world, rank, local)
-    if rank == 0 and not args.no_forms:
+    if world == 1 and not args.no_forms:  # the extra forms run on a single GPU only
         import torch
         dev = torch.device("cuda", local)
         line["forms"] = run_forms(dev, torch.cuda.Stream(device=dev), WL.seed)
@@ -601,7 +601,7 @@ def main():
                                     ("plain_rollout", "swarm_call", "swarm_rollout", "uneven_batched", "fwd_adjoint",
                                      "fwd_adjoint_discrete")}
     if rank == 0:
-        if not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline:  # the oracle's CPU baseline: rank 0 at N = 1 only
             v, cores, sample = oracle_run(200)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
         print(json.dumps(line), flush=True)
