@@ -14,6 +14,23 @@ from paper_2306_09537_gb300.env import QuadSwarmEnv
 
 pytestmark = pytest.mark.gpu
 
+
+@pytest.fixture(autouse=True, scope="module")
+def _host_link_supports_serving():
+    """The server needs native atomics on page-locked host memory (a coherent
+    host link such as NVLink-C2C); elsewhere qs_serve_begin refuses with
+    QS_ERR_UNSUPPORTED and these tests do not apply."""
+    env = QuadSwarmEnv(4, 1, 0, ("floor",), seed=1, device=DEV, stream=torch.cuda.Stream())
+    try:
+        qs.qs_serve_begin(env.h, torch.zeros(env.D, 4).pin_memory())
+        qs.qs_serve_end(env.h)
+    except qs.QSError as ex:
+        if ex.status == qs.QS_ERR_UNSUPPORTED and "native atomics" in str(ex):
+            pytest.skip("no native atomics on host memory")
+        raise
+    finally:
+        env.close()
+
 FEATS = ("floor", "walls", "motor_noise", "obs_noise", "dr", "collisions", "auto_reset")
 
 
