@@ -130,7 +130,14 @@ class Server:
     def close(self):
         if self.active:
             self.active = False
-            qs.qs_serve_end(self.env.h)
+            if self.env.h:  # a destroyed handle ended its server already
+                qs.qs_serve_end(self.env.h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
     def __enter__(self):
         return self
