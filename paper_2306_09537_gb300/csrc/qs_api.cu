@@ -497,8 +497,8 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
     // neither scenarios nor downwash lengthen the dynamics warp's step (then
     // its noise warp would idle at the barriers); else the persistent kernel,
     // whose work counter also balances uneven swarm sizes. Measured on GB300
-    // (warp-specialised vs persistent): plain 8192 x 1 3.3e9 vs 2.6e9, swarm
-    // 2048 x 8 3.4e9 vs 2.8e9; with every scenario type 1.9e9 vs 2.1e9;
+    // (warp-specialised vs persistent): plain 8192 x 1 3.2e9 vs 2.4e9, swarm
+    // 2048 x 8 3.6e9 vs 2.8e9; with every scenario type 1.9e9 vs 2.0e9;
     // uneven sizes up to 64 (two-warp pairs per CTA) 1.86e9 vs 1.80e9, close
     // enough to leave to the autotuner.
     {
