@@ -415,18 +415,39 @@ def run_forms(dev, stream, seed):
             env.close()
             del acts
 
-        # uneven swarms, 4096 envs, sizes {1..64}: one persistent launch vs per-size launches
+        # uneven swarms, 4096 envs, sizes {1..64}: the batched rollout, the per-call
+        # step (one launch for every width class), and the baseline of per-size
+        # launches: the same envs in one handle per width class, one launch each
         env = make(W.UNEVEN)
         tuned = autotune.tune(env, horizon=256)
         acts = torch.from_numpy(W.actions(seed, 256, env.D)).to(dev)
         ms_roll = rollout(env, acts, 256)
         ms_call = per_call(env, acts, 256)
-        n_classes = len(tuned["step_blocks"])
+        sizes = W.UNEVEN.sizes()
+        wcls = np.array([1 if n == 1 else 1 << int(np.ceil(np.log2(n))) for n in sizes])
+        parts = []
+        for w in sorted(set(wcls.tolist())):
+            sel = sizes[wcls == w]
+            e = QuadSwarmEnv(len(sel), sel, W.UNEVEN.k_neighbors, W.UNEVEN.features + ("auto_reset",), seed=seed,
+                             weights=W.UNEVEN.weights, device=dev, stream=stream)
+            e.reset(seed)
+            parts.append((e, torch.from_numpy(W.actions(seed, 1, e.D)).to(dev)[0]))
+
+        def per_size():
+            for e, a in parts:
+                e.step(a)
+        for _ in range(3):
+            per_size()
+        ms_ps = float(np.mean([_events_ms(per_size, stream, reps=1, flush=flush) for _ in range(100)]))
+        for e, _ in parts:
+            e.close()
         forms["uneven_batched"] = {"value": env.D / ms_roll * 1e3, "ms_per_step": ms_roll, "T": 256,
                                    "drones": env.D, "shape": list(tuned["rollout"])}
-        forms["uneven_per_size_launches"] = {"value": env.D / ms_call * 1e3, "ms_per_step": ms_call,
-                                             "launches_per_step": n_classes}
-        forms["uneven_speedup_vs_per_size"] = ms_call / ms_roll
+        forms["uneven_call"] = {"value": env.D / ms_call * 1e3, "ms_per_step": ms_call, "launches_per_step": 1}
+        forms["uneven_per_size_launches"] = {"value": env.D / ms_ps * 1e3, "ms_per_step": ms_ps,
+                                             "launches_per_step": len(parts)}
+        forms["uneven_speedup_vs_per_size"] = ms_ps / ms_roll
+        forms["uneven_call_speedup_vs_per_size"] = ms_ps / ms_call
         env.close()
         del acts
 
@@ -608,8 +629,8 @@ def main():
         f = line["forms"]
         # throughput of each form relative to the plain per-call GPU step (same binary32 accuracy)
         f["ratio_vs_plain_call"] = {k: f[k]["value"] / line["value"] for k in
-                                    ("plain_rollout", "swarm_call", "swarm_rollout", "uneven_batched", "fwd_adjoint",
-                                     "fwd_adjoint_discrete")}
+                                    ("plain_rollout", "swarm_call", "swarm_rollout", "uneven_batched", "uneven_call",
+                                     "fwd_adjoint", "fwd_adjoint_discrete")}
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:  # the oracle's CPU baseline: rank 0 at N = 1 only
             v, cores, sample = oracle_run(200)

@@ -222,7 +222,9 @@ qs_status qs_reset(qs_env* h, uint64_t seed, const uint8_t* env_mask_dev, float*
 /* One control step of every env (Sec. III-A .. III-E): actions_dev [D][4] in,
  * obs_dev [D][obs_dim], reward_dev [D], done_dev [E] out. obs_dev, reward_dev
  * and done_dev may be NULL (not written). A non-finite drone state found on
- * the device is reported by the next qs_sync() or qs_step_host(). */
+ * the device is reported by the next qs_sync() or qs_step_host(). One launch:
+ * the per-call kernel of the handle's width class, or, when the swarm sizes
+ * span several classes, one step of the rollout kernel (qs_rollout, T = 1). */
 qs_status qs_step(qs_env* h, const float* actions_dev, float* obs_dev, float* reward_dev, uint8_t* done_dev);
 
 /* qs_step for callers whose buffers live in host memory: actions_host [D][4]
@@ -393,8 +395,11 @@ qs_status qs_sync(qs_env* h);
  * multiple of 32 and of `width`, at most 256; or QS_BLOCK_WARP_SPECIALISED
  * (widths <= 32, the default there): CTAs of two warps per 32 drones, one
  * integrating the dynamics while the other draws the motor and sensor noise
- * and writes the observation rows. Used by the autotuner; results do not
- * depend on it. QS_ERR_ARG for an invalid shape or a class the handle lacks. */
+ * and writes the observation rows. It shapes the steps of a handle whose envs
+ * all fall in one class, and the reset observation; a handle with several
+ * classes steps them all in one launch shaped by qs_set_rollout_shape. Used
+ * by the autotuner; results do not depend on it. QS_ERR_ARG for an invalid
+ * shape or a class the handle lacks. */
 #define QS_BLOCK_WARP_SPECIALISED 1
 qs_status qs_set_block(qs_env* h, int32_t width, int32_t block);
 

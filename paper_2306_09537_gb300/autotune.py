@@ -34,7 +34,9 @@ def _time(fn, stream, reps):
 
 
 def tune(env, steps: int = 32, horizon: int = 64, reps: int = 3, apply: bool = True) -> dict:
-    """Returns {"step_blocks": {W: block}, "rollout": (block, fuse, graph), "timings": {...}}."""
+    """Returns {"step_blocks": {W: block}, "rollout": (block, fuse, graph), "timings": {...}}
+    (step_blocks is empty for a handle with several width classes: its per-call
+    step is the rollout launch, and the rollout shape covers it)."""
     from .env import QuadSwarmEnv
     key = _signature(env)
     if key in _CACHE:
@@ -50,7 +52,10 @@ def tune(env, steps: int = 32, horizon: int = 64, reps: int = 3, apply: bool = T
         timings = {"step": {}, "rollout": {}}
         step_blocks = {}
         with torch.cuda.stream(stream):
-            for w in classes:
+            # a handle with several width classes steps them all in one launch of
+            # the rollout kernels, shaped below; only a single class has a
+            # per-call kernel to shape
+            for w in (classes if len(classes) == 1 else []):
                 best = None
                 for b in (qs.QS_BLOCK_WARP_SPECIALISED, 32, 64, 128, 256):
                     if b == qs.QS_BLOCK_WARP_SPECIALISED:

@@ -330,7 +330,13 @@ qs_status enqueue_rollout(qs_env* h, int T, const RolloutIO& io) {
     return QS_OK;
 }
 
+
+// One control step of every env. A handle with several width classes steps
+// them all in one launch of the rollout kernels with T = 1 (the same bits as
+// the per-class kernels; measured on GB300 with sizes 1..64: 4096 envs 90.8
+// -> 35.5 us, 65,536 envs 271 -> 207 us); one class keeps its per-call kernel.
 qs_status do_step(qs_env* h, const float* act, float* obs, float* rew, uint8_t* done) {
+    if (h->plan.size() > 1) return enqueue_rollout(h, 1, RolloutIO{act, obs, rew, done});
     StepIO io{act, obs, rew, done};
     for (const ClassPlan& cp : h->plan) {
         cudaError_t e = launch_step(h->c, h->dv, cp, h->d_tiles, h->d_perm, io, 0, h->stream);

@@ -452,16 +452,23 @@ def test_rollout_graph_replay():
     assert torch.equal(env.get_state()["state"], env2.get_state()["state"])
 
 
-def test_launch_shape_does_not_change_results():
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 20, 33, 64, 100])
+def test_launch_shape_does_not_change_results(n):
+    """The per-call kernel of a handle whose envs share one width class gives
+    the same bits in every CTA shape (and warp-specialised where the class
+    allows it)."""
     from paper_2306_09537_gb300 import qs
-    sizes = [1] * 100 + [8] * 40 + [64] * 4 + [3, 5, 2] * 7
+    WS = qs.QS_BLOCK_WARP_SPECIALISED
+    wcls = 1 if n == 1 else int(2 ** np.ceil(np.log2(n)))
+    sizes = [n] * max(4, 1536 // n)
+    blocks = [b for b in (None, 32, 64, 128, 256, WS)
+              if b is None or (b == WS and wcls <= 32) or (b != WS and b >= wcls and b % wcls == 0)]
     ref = None
-    for block in (None, 64, 128, 256, qs.QS_BLOCK_WARP_SPECIALISED):
+    for block in blocks:
         env, _ = pair(sizes, 6, FULL, seed=8)
         if block:
-            for wcls in (1, 2, 4, 8, 64):
-                qs.qs_set_block(env.h, wcls, block if (wcls <= 32 or block != qs.QS_BLOCK_WARP_SPECIALISED) else 128)
-            assert qs.qs_get_block(env.h, 8) == block
+            qs.qs_set_block(env.h, wcls, block)
+            assert qs.qs_get_block(env.h, wcls) == block
         acts = torch.from_numpy(W.actions(8, 3, env.D)).to(DEV)
         for t in range(3):
             obs, rew, _ = env.step(acts[t])
@@ -469,7 +476,31 @@ def test_launch_shape_does_not_change_results():
         if ref is None:
             ref = cur
         else:
-            assert all(torch.equal(a, b) for a, b in zip(ref, cur))
+            assert all(torch.equal(a, b) for a, b in zip(ref, cur)), block
+
+
+@pytest.mark.parametrize("sizes", [[1] * 100 + [8] * 40 + [3, 5, 2, 17, 32] * 7,
+                                   [1] * 100 + [8] * 40 + [64] * 4 + [3, 5, 2] * 7 + [100, 128]])
+def test_mixed_class_step_is_one_launch_in_any_rollout_shape(sizes):
+    """A handle whose swarm sizes span several width classes steps them all in
+    one launch of the rollout kernels (T = 1): the same bits through the
+    persistent kernel in several CTA sizes and, where every class allows it,
+    the warp-specialised one."""
+    from paper_2306_09537_gb300 import qs
+    WS = qs.QS_BLOCK_WARP_SPECIALISED
+    shapes = [(128, 0, False), (256, 0, True)] + ([(WS, 0, False)] if max(sizes) <= 64 else [])
+    ref = None
+    for shape in shapes:
+        env, _ = pair(sizes, 6, FULL + ("auto_reset",), seed=9, episode_steps=2)
+        qs.qs_set_rollout_shape(env.h, *shape)
+        acts = torch.from_numpy(W.actions(9, 4, env.D)).to(DEV)
+        for t in range(4):  # across an auto-reset
+            obs, rew, done = env.step(acts[t])
+        cur = (obs.clone(), rew.clone(), done.clone(), env.get_state()["state"])
+        if ref is None:
+            ref = cur
+        else:
+            assert all(torch.equal(a, b) for a, b in zip(ref, cur)), shape
 
 
 @pytest.mark.parametrize("n,K", [(1, 0), (8, 6), (48, 6)])
