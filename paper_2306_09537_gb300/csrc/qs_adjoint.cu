@@ -288,7 +288,8 @@ __device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const 
 size_t diff_workspace_bytes(int D, int T, int C, int substeps) {
     const int nck = (T + C - 1) / C;
     const size_t ck = (size_t)nck * NPLANE * D * sizeof(float4);
-    const size_t sc = (size_t)C * (substeps + 1) * NSUB * D * sizeof(float);
+    // two scratch buffers: the backward pass recomputes one segment while it reverses the next
+    const size_t sc = 2 * (size_t)C * (substeps + 1) * NSUB * D * sizeof(float);
     return ck + sc + 256;
 }
 
@@ -328,19 +329,35 @@ __device__ __forceinline__ void read_x0(Drone& s, const float* __restrict__ x0, 
     s.wlo[0] = s.wlo[1] = s.wlo[2] = 0.f;
 }
 
+// Barrier of the threads that share the staged positions: the whole CTA (id
+// 0), or one group of n threads of the pipelined adjoint (named barrier id; a
+// group of one warp only needs its lanes converged).
+__device__ __forceinline__ void group_sync(int id, int n) {
+    if (id == 0)
+        __syncthreads();
+    else if (n == 32)
+        __syncwarp();
+    else if (id == 1)
+        asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+    else
+        asm volatile("bar.sync 2, %0;" ::"r"(n) : "memory");
+}
+
 // One smooth substep of the slot's drones (pair force from the positions at
-// the substep start, staged in shared memory).
+// the substep start, staged in shared memory at the thread's group-local
+// index lt; bid, bn: the barrier of the threads sharing them).
 __device__ __forceinline__ void smooth_substep(const Consts& c, Drone& s, const Prm& p, const float u[4], uint32_t tick,
-                                               int d, int sub, bool act, float* sx, int nt, int sbase, int lane, int N) {
+                                               int d, int sub, bool act, float* sx, int nt, int sbase, int lane, int N,
+                                               int lt, int bid, int bn) {
     if (act) {
-        sx[threadIdx.x] = s.x[0];
-        sx[nt + threadIdx.x] = s.x[1];
-        sx[2 * nt + threadIdx.x] = s.x[2];
+        sx[lt] = s.x[0];
+        sx[nt + lt] = s.x[1];
+        sx[2 * nt + lt] = s.x[2];
     }
-    __syncthreads();
+    group_sync(bid, bn);
     float pa[3] = {0.f, 0.f, 0.f};
     if (act) pair_acc(c, s.x, sx, nt, sbase, lane, N, p.arm, pa);
-    __syncthreads();
+    group_sync(bid, bn);
     if (act) substep(s, p, c, u, tick, d, sub, pa);
 }
 
@@ -404,7 +421,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_fwd(const Consts c, cons
         float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4];
         if (act) command4(c, a.act, D, t, d, fh, u, msk);
         for (int sub = 0; sub < c.substeps; ++sub)
-            smooth_substep(c, s, p, u, tick0 + t, d, sub, act, sm, nt, sbase, lane, N);
+            smooth_substep(c, s, p, u, tick0 + t, d, sub, act, sm, nt, sbase, lane, N, threadIdx.x, 0, nt);
         if (act) {
             const float dx = s.x[0] - g[0], dy = s.x[1] - g[1], dz = s.x[2] - g[2];
             L += dx * dx + dy * dy + dz * dz + 1e-3f * (fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
@@ -416,20 +433,31 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_fwd(const Consts c, cons
     }
 }
 
+// Adjoint of the smooth rollout, pipelined over checkpoint segments. The CTA
+// holds two groups of nb threads over the same drones: while group 1 runs the
+// reverse of segment s from its saved substep states, group 0 recomputes
+// segment s - 1 from its checkpoint into the other scratch buffer and leaves
+// the segment's final positions in shared memory; one CTA barrier per segment
+// hands a buffer from group 0 to group 1. Each group synchronises its staged
+// positions with its own barrier.
 __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                             const int* __restrict__ perm, const DiffArgs a) {
     extern __shared__ float sm[];
-    const Tile tile = tile_at(dv, tiles, blockIdx.x, blockDim.x);
-    const int W = tile.W, nt = blockDim.x;
-    const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
+    const int nb = blockDim.x >> 1, grp = threadIdx.x >= nb ? 1 : 0, lt = threadIdx.x - grp * nb, bid = 1 + grp;
+    const Tile tile = tile_at(dv, tiles, blockIdx.x, nb);
+    const int W = tile.W, nt = nb;
+    const int slot = lt / W, lane = lt - slot * W;
     const bool ok = slot < tile.count;
     const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
     const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
     const bool act = lane < N;
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;
-    float* sx = sm;            // [3][nt] positions
-    float* sla = sm + 3 * nt;  // [3][nt] lambda of the acceleration
+    float* sx = sm + grp * 3 * nb;  // [3][nb] positions of the group
+    float* sla = sm + 6 * nb;       // [3][nb] lambda of the acceleration (group 1)
+    float* xfin = sm + 9 * nb;      // [2][3][nb] positions at the end of a recomputed segment
+    const int S = c.substeps;
+    const size_t sbuf = (size_t)a.C * (S + 1) * NSUB * D;  // floats of one scratch buffer
     Prm p;
     float g[3] = {0.f, 0.f, 0.f};
     uint32_t tick0 = 0;
@@ -444,71 +472,89 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
     }
     float lx[3] = {0.f, 0.f, 0.f}, lv[3] = {0.f, 0.f, 0.f}, lR[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float lw[3] = {0.f, 0.f, 0.f}, luf[4] = {0.f, 0.f, 0.f, 0.f}, leps[4] = {0.f, 0.f, 0.f, 0.f};
-    const int S = c.substeps;
     const int nseg = (a.T + a.C - 1) / a.C;
-    for (int seg = nseg - 1; seg >= 0; --seg) {
-        const int tb = seg * a.C, te = min(a.T, tb + a.C);
-        // recompute the segment, saving every substep input
-        Drone s;
-        if (act) {
-            float4 q[NPLANE];
-            const float4* ck = a.ckpt + (size_t)seg * NPLANE * D;
-            for (int pl = 0; pl < NPLANE; ++pl) q[pl] = ck[(size_t)pl * D + d];
-            unpack(s, q);
-        }
-        for (int t = tb; t < te; ++t) {
-            float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4];
-            if (act) command4(c, a.act, D, t, d, fh, u, msk);
-            for (int sub = 0; sub < S; ++sub) {
-                if (act) save_sub(a.scratch, D, (t - tb) * S + sub, d, s);
-                smooth_substep(c, s, p, u, tick0 + t, d, sub, act, sx, nt, sbase, lane, N);
+    for (int it = 0; it <= nseg; ++it) {
+        if (grp == 0 && it < nseg) {
+            // recompute segment nseg - 1 - it, saving every substep input
+            const int seg = nseg - 1 - it, tb = seg * a.C, te = min(a.T, tb + a.C);
+            float* scr = a.scratch + (size_t)(it & 1) * sbuf;
+            Drone s;
+            if (act) {
+                float4 q[NPLANE];
+                const float4* ck = a.ckpt + (size_t)seg * NPLANE * D;
+                for (int pl = 0; pl < NPLANE; ++pl) q[pl] = ck[(size_t)pl * D + d];
+                unpack(s, q);
             }
-        }
-        // reverse through the segment; s holds the state after step te - 1
-        float xpost[3] = {s.x[0], s.x[1], s.x[2]};
-        for (int t = te - 1; t >= tb; --t) {
-            float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4] = {0.f, 0.f, 0.f, 0.f};
-            if (act) command4(c, a.act, D, t, d, fh, u, msk);
-            // loss of step t: |x(t) - g|^2 + 1e-3 |f^|^2
-            for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (xpost[k] - g[k]);
-            float lu[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int sub = S - 1; sub >= 0; --sub) {
-                Drone si;
-                if (act) load_sub(a.scratch, D, (t - tb) * S + sub, d, si);
-                if (act) {
-                    sx[threadIdx.x] = si.x[0];
-                    sx[nt + threadIdx.x] = si.x[1];
-                    sx[2 * nt + threadIdx.x] = si.x[2];
-                }
-                __syncthreads();
-                float la[3] = {0.f, 0.f, 0.f};
-                if (act) {
-                    substep_vjp(si, p, c, u, tick0 + t, d, sub, lx, lv, lR, lw, luf, leps, la, lu);
-                    sla[threadIdx.x] = la[0];
-                    sla[nt + threadIdx.x] = la[1];
-                    sla[2 * nt + threadIdx.x] = la[2];
-                }
-                __syncthreads();
-                if (act) pair_vjp(c, si.x, la, sx, sla, nt, sbase, lane, N, p.arm, lx);
-                __syncthreads();
-                if (sub == 0) {
-                    xpost[0] = si.x[0];
-                    xpost[1] = si.x[1];
-                    xpost[2] = si.x[2];
+            for (int t = tb; t < te; ++t) {
+                float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4];
+                if (act) command4(c, a.act, D, t, d, fh, u, msk);
+                for (int sub = 0; sub < S; ++sub) {
+                    if (act) save_sub(scr, D, (t - tb) * S + sub, d, s);
+                    smooth_substep(c, s, p, u, tick0 + t, d, sub, act, sx, nt, sbase, lane, N, lt, bid, nb);
                 }
             }
             if (act) {
-                float ga[4];
-                for (int r = 0; r < 4; ++r) {
-                    // u = sqrt(f^): du/df^ = 1 / (2u)
-                    const float du = u[r] > 0.f ? 0.5f / u[r] : 0.f;
-                    ga[r] = msk[r] * (lu[r] * du + dl * 2e-3f * fh[r]);
+                float* xf = xfin + (it & 1) * 3 * nb;
+                xf[lt] = s.x[0];
+                xf[nb + lt] = s.x[1];
+                xf[2 * nb + lt] = s.x[2];
+            }
+        } else if (grp == 1 && it >= 1) {
+            // reverse through segment nseg - it, recomputed in the previous round
+            const int seg = nseg - it, tb = seg * a.C, te = min(a.T, tb + a.C);
+            const float* scr = a.scratch + (size_t)((it - 1) & 1) * sbuf;
+            const float* xf = xfin + ((it - 1) & 1) * 3 * nb;
+            float xpost[3] = {0.f, 0.f, 0.f};  // the state after step t
+            if (act) {
+                xpost[0] = xf[lt];
+                xpost[1] = xf[nb + lt];
+                xpost[2] = xf[2 * nb + lt];
+            }
+            for (int t = te - 1; t >= tb; --t) {
+                float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4] = {0.f, 0.f, 0.f, 0.f};
+                if (act) command4(c, a.act, D, t, d, fh, u, msk);
+                // loss of step t: |x(t) - g|^2 + 1e-3 |f^|^2
+                for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (xpost[k] - g[k]);
+                float lu[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int sub = S - 1; sub >= 0; --sub) {
+                    Drone si;
+                    if (act) load_sub(scr, D, (t - tb) * S + sub, d, si);
+                    if (act) {
+                        sx[lt] = si.x[0];
+                        sx[nt + lt] = si.x[1];
+                        sx[2 * nt + lt] = si.x[2];
+                    }
+                    group_sync(bid, nb);
+                    float la[3] = {0.f, 0.f, 0.f};
+                    if (act) {
+                        substep_vjp(si, p, c, u, tick0 + t, d, sub, lx, lv, lR, lw, luf, leps, la, lu);
+                        sla[lt] = la[0];
+                        sla[nt + lt] = la[1];
+                        sla[2 * nt + lt] = la[2];
+                    }
+                    group_sync(bid, nb);
+                    if (act) pair_vjp(c, si.x, la, sx, sla, nt, sbase, lane, N, p.arm, lx);
+                    group_sync(bid, nb);
+                    if (sub == 0) {
+                        xpost[0] = si.x[0];
+                        xpost[1] = si.x[1];
+                        xpost[2] = si.x[2];
+                    }
                 }
-                reinterpret_cast<float4*>(a.grad_act + (size_t)t * D * 4)[d] = make_float4(ga[0], ga[1], ga[2], ga[3]);
+                if (act) {
+                    float ga[4];
+                    for (int r = 0; r < 4; ++r) {
+                        // u = sqrt(f^): du/df^ = 1 / (2u)
+                        const float du = u[r] > 0.f ? 0.5f / u[r] : 0.f;
+                        ga[r] = msk[r] * (lu[r] * du + dl * 2e-3f * fh[r]);
+                    }
+                    reinterpret_cast<float4*>(a.grad_act + (size_t)t * D * 4)[d] = make_float4(ga[0], ga[1], ga[2], ga[3]);
+                }
             }
         }
+        __syncthreads();  // hand over: buffer it & 1 recomputed; buffer (it - 1) & 1 free again
     }
-    if (act) {
+    if (grp == 1 && act) {
         float* gx = a.grad_x0 + (size_t)d * QS_STATE_DIM;
         for (int k = 0; k < 3; ++k) gx[k] = lx[k];
         for (int k = 0; k < 3; ++k) gx[3 + k] = lv[k];
@@ -714,16 +760,17 @@ __device__ __forceinline__ void discrete_substep_vjp(const Drone& s, const Prm& 
 // positions and pre-collision velocities staged in shared memory (sx, sv:
 // [3][nt]). Every thread of the CTA calls it.
 __device__ __forceinline__ void discrete_collisions(const Consts& c, Drone& s, const Prm& p, uint32_t tick, int d,
-                                                    bool act, float* sx, float* sv, int nt, int sbase, int lane, int N) {
+                                                    bool act, float* sx, float* sv, int nt, int sbase, int lane, int N,
+                                                    int lt, int bid, int bn) {
     if (act) {
-        sx[threadIdx.x] = s.x[0];
-        sx[nt + threadIdx.x] = s.x[1];
-        sx[2 * nt + threadIdx.x] = s.x[2];
-        sv[threadIdx.x] = s.v[0];
-        sv[nt + threadIdx.x] = s.v[1];
-        sv[2 * nt + threadIdx.x] = s.v[2];
+        sx[lt] = s.x[0];
+        sx[nt + lt] = s.x[1];
+        sx[2 * nt + lt] = s.x[2];
+        sv[lt] = s.v[0];
+        sv[nt + lt] = s.v[1];
+        sv[2 * nt + lt] = s.v[2];
     }
-    __syncthreads();
+    group_sync(bid, bn);
     float dvs[3] = {0.f, 0.f, 0.f};
     bool responded = false;
     if (act && N > 1) {
@@ -733,7 +780,7 @@ __device__ __forceinline__ void discrete_collisions(const Consts& c, Drone& s, c
         bool dwh = false;
         responded = pair_scan(c, s, p.thr, lane, N, sbase, sx, sv, nt, 0, true, true, ev, best, dvs, false, az, dwh);
     }
-    __syncthreads();
+    group_sync(bid, bn);
     if (responded) apply_response(c, s, tick, d, dvs);
 }
 
@@ -827,7 +874,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, con
             command4(c, a.act, D, t, d, fh, u, msk);
             for (int sub = 0; sub < c.substeps; ++sub) substep(s, p, c, u, tick0 + t, d, sub, zero3);
         }
-        if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sm, sm + 3 * nt, nt, sbase, lane, N);
+        if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sm, sm + 3 * nt, nt, sbase, lane, N, threadIdx.x, 0, nt);
         if (act) {
             const float dx = s.x[0] - g[0], dy = s.x[1] - g[1], dz = s.x[2] - g[2];
             L += dx * dx + dy * dy + dz * dz + 1e-3f * (fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
@@ -839,12 +886,17 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, con
     }
 }
 
+// Adjoint of the discrete-contact rollout, pipelined over checkpoint segments
+// like k_diff_bwd: group 0 recomputes segment s - 1 (every substep input and
+// each step's pre-collision state) into one scratch buffer while group 1
+// reverses segment s from the other.
 __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                              const int* __restrict__ perm, const DiffArgs a) {
     extern __shared__ float sm[];
-    const Tile tile = tile_at(dv, tiles, blockIdx.x, blockDim.x);
-    const int W = tile.W, nt = blockDim.x;
-    const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
+    const int nb = blockDim.x >> 1, grp = threadIdx.x >= nb ? 1 : 0, lt = threadIdx.x - grp * nb, bid = 1 + grp;
+    const Tile tile = tile_at(dv, tiles, blockIdx.x, nb);
+    const int W = tile.W, nt = nb;
+    const int slot = lt / W, lane = lt - slot * W;
     const bool ok = slot < tile.count;
     const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
     const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
@@ -852,9 +904,11 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;
     const bool coll = (c.flags & QS_F_COLLISIONS) != 0;
-    float* sx = sm;            // [3][nt] positions
-    float* sv = sm + 3 * nt;   // [3][nt] velocities
-    float* sl = sm + 6 * nt;   // [3][nt] lambda of the post-collision velocity
+    float* sx = sm + grp * 6 * nb;       // [3][nb] positions of the group
+    float* sv = sx + 3 * nb;             // [3][nb] velocities of the group
+    float* sl = sm + 12 * nb;            // [3][nb] lambda of the post-collision velocity (group 1)
+    const int S = c.substeps, S1 = c.substeps + 1;  // saved states per step: each substep's input, then the pre-collision state
+    const size_t sbuf = (size_t)a.C * S1 * NSUB * D;  // floats of one scratch buffer
     Prm p;
     float g[3] = {0.f, 0.f, 0.f};
     uint32_t tick0 = 0;
@@ -869,74 +923,80 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
     }
     float lx[3] = {0.f, 0.f, 0.f}, lv[3] = {0.f, 0.f, 0.f}, lR[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float lw[3] = {0.f, 0.f, 0.f}, luf[4] = {0.f, 0.f, 0.f, 0.f}, leps[4] = {0.f, 0.f, 0.f, 0.f};
-    const int S = c.substeps, S1 = c.substeps + 1;  // saved states per step: each substep's input, then the pre-collision state
     const float zero3[3] = {0.f, 0.f, 0.f};
     const int nseg = (a.T + a.C - 1) / a.C;
-    for (int seg = nseg - 1; seg >= 0; --seg) {
-        const int tb = seg * a.C, te = min(a.T, tb + a.C);
-        // recompute the segment, saving every substep input and each step's pre-collision state
-        Drone s;
-        if (act) {
-            float4 q[NPLANE];
-            const float4* ck = a.ckpt + (size_t)seg * NPLANE * D;
-            for (int pl = 0; pl < NPLANE; ++pl) q[pl] = ck[(size_t)pl * D + d];
-            unpack(s, q);
-        }
-        for (int t = tb; t < te; ++t) {
-            float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4];
+    for (int it = 0; it <= nseg; ++it) {
+        if (grp == 0 && it < nseg) {
+            // recompute segment nseg - 1 - it
+            const int seg = nseg - 1 - it, tb = seg * a.C, te = min(a.T, tb + a.C);
+            float* scr = a.scratch + (size_t)(it & 1) * sbuf;
+            Drone s;
             if (act) {
-                command4(c, a.act, D, t, d, fh, u, msk);
-                for (int sub = 0; sub < S; ++sub) {
-                    save_sub(a.scratch, D, (t - tb) * S1 + sub, d, s);
-                    substep(s, p, c, u, tick0 + t, d, sub, zero3);
-                }
-                save_sub(a.scratch, D, (t - tb) * S1 + S, d, s);
+                float4 q[NPLANE];
+                const float4* ck = a.ckpt + (size_t)seg * NPLANE * D;
+                for (int pl = 0; pl < NPLANE; ++pl) q[pl] = ck[(size_t)pl * D + d];
+                unpack(s, q);
             }
-            if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sx, sv, nt, sbase, lane, N);
-        }
-        // reverse through the segment
-        for (int t = te - 1; t >= tb; --t) {
-            float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4] = {0.f, 0.f, 0.f, 0.f};
-            Drone sc;
-            if (act) {
-                command4(c, a.act, D, t, d, fh, u, msk);
-                load_sub(a.scratch, D, (t - tb) * S1 + S, d, sc);
-                // loss of step t: |x(t) - g|^2 + 1e-3 |f^|^2 (the collision pass leaves x unchanged)
-                for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (sc.x[k] - g[k]);
-            }
-            if (coll) {
+            for (int t = tb; t < te; ++t) {
+                float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4];
                 if (act) {
-                    sx[threadIdx.x] = sc.x[0];
-                    sx[nt + threadIdx.x] = sc.x[1];
-                    sx[2 * nt + threadIdx.x] = sc.x[2];
-                    sv[threadIdx.x] = sc.v[0];
-                    sv[nt + threadIdx.x] = sc.v[1];
-                    sv[2 * nt + threadIdx.x] = sc.v[2];
-                    sl[threadIdx.x] = lv[0];
-                    sl[nt + threadIdx.x] = lv[1];
-                    sl[2 * nt + threadIdx.x] = lv[2];
+                    command4(c, a.act, D, t, d, fh, u, msk);
+                    for (int sub = 0; sub < S; ++sub) {
+                        save_sub(scr, D, (t - tb) * S1 + sub, d, s);
+                        substep(s, p, c, u, tick0 + t, d, sub, zero3);
+                    }
+                    save_sub(scr, D, (t - tb) * S1 + S, d, s);
                 }
-                __syncthreads();
-                if (act && N > 1) collision_vjp(c, sc.x, sc.v, p.thr, sx, sv, sl, nt, sbase, lane, N, lx, lv);
-                __syncthreads();
+                if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sx, sv, nt, sbase, lane, N, lt, bid, nb);
             }
-            float lu[4] = {0.f, 0.f, 0.f, 0.f};
-            if (act) {
-                for (int sub = S - 1; sub >= 0; --sub) {
-                    Drone si;
-                    load_sub(a.scratch, D, (t - tb) * S1 + sub, d, si);
-                    discrete_substep_vjp(si, p, c, u, tick0 + t, d, sub, lx, lv, lR, lw, luf, leps, lu);
+        } else if (grp == 1 && it >= 1) {
+            // reverse through segment nseg - it, recomputed in the previous round
+            const int seg = nseg - it, tb = seg * a.C, te = min(a.T, tb + a.C);
+            const float* scr = a.scratch + (size_t)((it - 1) & 1) * sbuf;
+            for (int t = te - 1; t >= tb; --t) {
+                float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4] = {0.f, 0.f, 0.f, 0.f};
+                Drone sc;
+                if (act) {
+                    command4(c, a.act, D, t, d, fh, u, msk);
+                    load_sub(scr, D, (t - tb) * S1 + S, d, sc);
+                    // loss of step t: |x(t) - g|^2 + 1e-3 |f^|^2 (the collision pass leaves x unchanged)
+                    for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (sc.x[k] - g[k]);
                 }
-                float ga[4];
-                for (int r = 0; r < 4; ++r) {
-                    const float du = u[r] > 0.f ? 0.5f / u[r] : 0.f;
-                    ga[r] = msk[r] * (lu[r] * du + dl * 2e-3f * fh[r]);
+                if (coll) {
+                    if (act) {
+                        sx[lt] = sc.x[0];
+                        sx[nt + lt] = sc.x[1];
+                        sx[2 * nt + lt] = sc.x[2];
+                        sv[lt] = sc.v[0];
+                        sv[nt + lt] = sc.v[1];
+                        sv[2 * nt + lt] = sc.v[2];
+                        sl[lt] = lv[0];
+                        sl[nt + lt] = lv[1];
+                        sl[2 * nt + lt] = lv[2];
+                    }
+                    group_sync(bid, nb);
+                    if (act && N > 1) collision_vjp(c, sc.x, sc.v, p.thr, sx, sv, sl, nt, sbase, lane, N, lx, lv);
+                    group_sync(bid, nb);
                 }
-                reinterpret_cast<float4*>(a.grad_act + (size_t)t * D * 4)[d] = make_float4(ga[0], ga[1], ga[2], ga[3]);
+                float lu[4] = {0.f, 0.f, 0.f, 0.f};
+                if (act) {
+                    for (int sub = S - 1; sub >= 0; --sub) {
+                        Drone si;
+                        load_sub(scr, D, (t - tb) * S1 + sub, d, si);
+                        discrete_substep_vjp(si, p, c, u, tick0 + t, d, sub, lx, lv, lR, lw, luf, leps, lu);
+                    }
+                    float ga[4];
+                    for (int r = 0; r < 4; ++r) {
+                        const float du = u[r] > 0.f ? 0.5f / u[r] : 0.f;
+                        ga[r] = msk[r] * (lu[r] * du + dl * 2e-3f * fh[r]);
+                    }
+                    reinterpret_cast<float4*>(a.grad_act + (size_t)t * D * 4)[d] = make_float4(ga[0], ga[1], ga[2], ga[3]);
+                }
             }
         }
+        __syncthreads();  // hand over: buffer it & 1 recomputed; buffer (it - 1) & 1 free again
     }
-    if (act) {
+    if (grp == 1 && act) {
         float* gx = a.grad_x0 + (size_t)d * QS_STATE_DIM;
         for (int k = 0; k < 3; ++k) gx[k] = lx[k];
         for (int k = 0; k < 3; ++k) gx[3 + k] = lv[k];
@@ -963,12 +1023,15 @@ cudaError_t launch_diff(int backward, const Consts& c, const Dev& dv, const Tile
     const int nck = (T + C - 1) / C;
     a.ckpt = reinterpret_cast<float4*>(workspace);
     a.scratch = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + (size_t)nck * NPLANE * dv.D * sizeof(float4));
-    const size_t smem = sizeof(float) * 9 * block;
+    // forward: one group of `block` threads; backward: two (recompute, reverse)
+    // with 15 planes of `block` floats between them
+    const size_t smem = sizeof(float) * 9 * block, smem2 = sizeof(float) * 15 * block;
+    if (2 * block > ADJ_BLOCK_MAX) return cudaErrorInvalidValue;
     if (c.flags & QS_F_SMOOTH) {
-        if (backward) k_diff_bwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
+        if (backward) k_diff_bwd<<<n_tiles, 2 * block, smem2, st>>>(c, dv, tiles, perm, a);
         else k_diff_fwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
     } else {
-        if (backward) k_diffd_bwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
+        if (backward) k_diffd_bwd<<<n_tiles, 2 * block, smem2, st>>>(c, dv, tiles, perm, a);
         else k_diffd_fwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
     }
     return cudaGetLastError();
