@@ -197,23 +197,16 @@ __device__ __forceinline__ void rotation_vjp(const float R[9], const float w1[3]
 // (x v R w uf eps); la: lambda of the acceleration (for the pair exchange);
 // lu: accumulated lambda of the rotor-speed command u.
 __device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const Consts& c, const float u[4],
-                                            uint32_t tick, int d, int sub, float lx[3], float lv[3],
+                                            const float eps1s[4], float lx[3], float lv[3],
                                             float lR[9], float lw[3], float luf[4], float leps[4], float la[3],
                                             float lu[4]) {
     const float dt = c.dt;
     // ---- recompute the forward intermediates
     float uf1[4], eps1[4], f[4];
     for (int r = 0; r < 4; ++r) uf1[r] = fmaf(p.alag, u[r] - s.uf[r], s.uf[r]);
-    float nrm[4] = {0.f, 0.f, 0.f, 0.f};
-    if (c.flags & QS_F_MOTOR_NOISE) {
-        const uint4 q = philox_rk(tick, (uint32_t)d, ctr_word(TAG_MOTOR, (uint32_t)sub, 0), c.rk);
-        const float2 n01 = box_muller(u01(q.x), u01(q.y));
-        const float2 n23 = box_muller(u01(q.z), u01(q.w));
-        nrm[0] = n01.x; nrm[1] = n01.y; nrm[2] = n23.x; nrm[3] = n23.y;
-        for (int r = 0; r < 4; ++r) eps1[r] = fmaf(c.alpha_nd, s.eps[r], p.ans * nrm[r]);
-    } else {
-        for (int r = 0; r < 4; ++r) eps1[r] = s.eps[r];
-    }
+    // the motor noise after the update, as the forward left it (saved with the
+    // next substep's input): the draw itself is additive and drops out
+    for (int r = 0; r < 4; ++r) eps1[r] = eps1s[r];
     for (int r = 0; r < 4; ++r) f[r] = fmaf(p.fmax * uf1[r], uf1[r], eps1[r]);
     const float T = (f[0] + f[1]) + (f[2] + f[3]);
     const float sa = p.arm * 0.70710678118654752f;
@@ -315,6 +308,18 @@ __device__ __forceinline__ void load_sub(const float* sc, size_t D, int idx, int
     for (int q = 0; q < 3; ++q) s.wlo[q] = b[(k++) * D];
     for (int q = 0; q < 4; ++q) s.uf[q] = b[(k++) * D];
     for (int q = 0; q < 4; ++q) s.eps[q] = b[(k++) * D];
+}
+
+// The motor-noise state (eps) of saved entry idx.
+__device__ __forceinline__ void load_eps(const float* sc, size_t D, int idx, int d, float e[4]) {
+    const float* b = sc + (size_t)idx * NSUB * D + d + (size_t)25 * D;  // x v R w wlo uf: 25 floats first
+    for (int q = 0; q < 4; ++q) e[q] = b[q * D];
+}
+
+// The position of saved entry idx.
+__device__ __forceinline__ void load_x(const float* sc, size_t D, int idx, int d, float x[3]) {
+    const float* b = sc + (size_t)idx * NSUB * D + d;
+    for (int q = 0; q < 3; ++q) x[q] = b[q * D];
 }
 
 __device__ __forceinline__ void read_x0(Drone& s, const float* __restrict__ x0, int d) {
@@ -435,11 +440,13 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_fwd(const Consts c, cons
 
 // Adjoint of the smooth rollout, pipelined over checkpoint segments. The CTA
 // holds two groups of nb threads over the same drones: while group 1 runs the
-// reverse of segment s from its saved substep states, group 0 recomputes
+// reverse of segment s from its saved substep inputs, group 0 recomputes
 // segment s - 1 from its checkpoint into the other scratch buffer and leaves
-// the segment's final positions in shared memory; one CTA barrier per segment
-// hands a buffer from group 0 to group 1. Each group synchronises its staged
-// positions with its own barrier.
+// the segment's final position and motor noise in shared memory; one CTA
+// barrier per segment hands a buffer from group 0 to group 1. Each group
+// synchronises its staged positions with its own barrier. The reverse takes
+// each substep's updated motor noise (and each step's end position) from the
+// next saved input instead of drawing it again.
 __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                             const int* __restrict__ perm, const DiffArgs a) {
     extern __shared__ float sm[];
@@ -455,9 +462,9 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
     const size_t D = dv.D;
     float* sx = sm + grp * 3 * nb;  // [3][nb] positions of the group
     float* sla = sm + 6 * nb;       // [3][nb] lambda of the acceleration (group 1)
-    float* xfin = sm + 9 * nb;      // [2][3][nb] positions at the end of a recomputed segment
+    float* fin = sm + 9 * nb;       // [2][7][nb] position and motor noise at the end of a recomputed segment
     const int S = c.substeps;
-    const size_t sbuf = (size_t)a.C * (S + 1) * NSUB * D;  // floats of one scratch buffer
+    const size_t sbuf = (size_t)a.C * (S + 1) * NSUB * D;  // floats of one scratch buffer (each substep's input)
     Prm p;
     float g[3] = {0.f, 0.f, 0.f};
     uint32_t tick0 = 0;
@@ -494,31 +501,42 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
                 }
             }
             if (act) {
-                float* xf = xfin + (it & 1) * 3 * nb;
-                xf[lt] = s.x[0];
-                xf[nb + lt] = s.x[1];
-                xf[2 * nb + lt] = s.x[2];
+                float* f = fin + (it & 1) * 7 * nb;
+                for (int k = 0; k < 3; ++k) f[k * nb + lt] = s.x[k];
+                for (int r = 0; r < 4; ++r) f[(3 + r) * nb + lt] = s.eps[r];
             }
         } else if (grp == 1 && it >= 1) {
             // reverse through segment nseg - it, recomputed in the previous round
             const int seg = nseg - it, tb = seg * a.C, te = min(a.T, tb + a.C);
             const float* scr = a.scratch + (size_t)((it - 1) & 1) * sbuf;
-            const float* xf = xfin + ((it - 1) & 1) * 3 * nb;
-            float xpost[3] = {0.f, 0.f, 0.f};  // the state after step t
-            if (act) {
-                xpost[0] = xf[lt];
-                xpost[1] = xf[nb + lt];
-                xpost[2] = xf[2 * nb + lt];
-            }
+            const float* f = fin + ((it - 1) & 1) * 7 * nb;
             for (int t = te - 1; t >= tb; --t) {
                 float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4] = {0.f, 0.f, 0.f, 0.f};
-                if (act) command4(c, a.act, D, t, d, fh, u, msk);
+                // the state after step t: the next step's first input, or the segment's end
+                float xpost[3] = {0.f, 0.f, 0.f}, eps_end[4] = {0.f, 0.f, 0.f, 0.f};
+                if (act) {
+                    command4(c, a.act, D, t, d, fh, u, msk);
+                    if (t + 1 < te) {
+                        load_x(scr, D, (t + 1 - tb) * S, d, xpost);
+                        load_eps(scr, D, (t + 1 - tb) * S, d, eps_end);
+                    } else {
+                        for (int k = 0; k < 3; ++k) xpost[k] = f[k * nb + lt];
+                        for (int r = 0; r < 4; ++r) eps_end[r] = f[(3 + r) * nb + lt];
+                    }
+                }
                 // loss of step t: |x(t) - g|^2 + 1e-3 |f^|^2
                 for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (xpost[k] - g[k]);
                 float lu[4] = {0.f, 0.f, 0.f, 0.f};
                 for (int sub = S - 1; sub >= 0; --sub) {
                     Drone si;
-                    if (act) load_sub(scr, D, (t - tb) * S + sub, d, si);
+                    float eps1[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (act) {
+                        load_sub(scr, D, (t - tb) * S + sub, d, si);
+                        if (sub + 1 < S)
+                            load_eps(scr, D, (t - tb) * S + sub + 1, d, eps1);
+                        else
+                            for (int r = 0; r < 4; ++r) eps1[r] = eps_end[r];
+                    }
                     if (act) {
                         sx[lt] = si.x[0];
                         sx[nt + lt] = si.x[1];
@@ -527,7 +545,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
                     group_sync(bid, nb);
                     float la[3] = {0.f, 0.f, 0.f};
                     if (act) {
-                        substep_vjp(si, p, c, u, tick0 + t, d, sub, lx, lv, lR, lw, luf, leps, la, lu);
+                        substep_vjp(si, p, c, u, eps1, lx, lv, lR, lw, luf, leps, la, lu);
                         sla[lt] = la[0];
                         sla[nt + lt] = la[1];
                         sla[2 * nt + lt] = la[2];
@@ -535,11 +553,6 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
                     group_sync(bid, nb);
                     if (act) pair_vjp(c, si.x, la, sx, sla, nt, sbase, lane, N, p.arm, lx);
                     group_sync(bid, nb);
-                    if (sub == 0) {
-                        xpost[0] = si.x[0];
-                        xpost[1] = si.x[1];
-                        xpost[2] = si.x[2];
-                    }
                 }
                 if (act) {
                     float ga[4];
@@ -580,20 +593,16 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
 // Adjoint of one discrete substep. s: substep input; the lambdas hold the
 // output's on entry and the input's on return; lu accumulates lambda of u.
 __device__ __forceinline__ void discrete_substep_vjp(const Drone& s, const Prm& p, const Consts& c, const float u[4],
-                                                     uint32_t tick, int d, int sub, float lx[3], float lv[3],
+                                                     const float eps1s[4], float lx[3], float lv[3],
                                                      float lR[9], float lw[3], float luf[4], float leps[4],
                                                      float lu[4]) {
     const float dt = c.dt, g = c.g;
     // ---- the forward substep again, with its decisions (as in substep())
     float uf1[4], eps1[4], f[4];
     for (int r = 0; r < 4; ++r) uf1[r] = fmaf(p.alag, u[r] - s.uf[r], s.uf[r]);
-    if (c.flags & QS_F_MOTOR_NOISE) {
-        float n[4];
-        motor_normals(c, tick, d, sub, n);
-        for (int r = 0; r < 4; ++r) eps1[r] = fmaf(c.alpha_nd, s.eps[r], p.ans * n[r]);
-    } else {
-        for (int r = 0; r < 4; ++r) eps1[r] = s.eps[r];
-    }
+    // the motor noise after the update, as the forward left it (saved with the
+    // next substep's input or the step's pre-collision state)
+    for (int r = 0; r < 4; ++r) eps1[r] = eps1s[r];
     for (int r = 0; r < 4; ++r) f[r] = fmaf(p.fmax * uf1[r], uf1[r], eps1[r]);
     const float T = (f[0] + f[1]) + (f[2] + f[3]);
     const float sa = p.arm * 0.70710678118654752f;
@@ -982,8 +991,10 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
                 if (act) {
                     for (int sub = S - 1; sub >= 0; --sub) {
                         Drone si;
+                        float eps1[4];
                         load_sub(scr, D, (t - tb) * S1 + sub, d, si);
-                        discrete_substep_vjp(si, p, c, u, tick0 + t, d, sub, lx, lv, lR, lw, luf, leps, lu);
+                        load_eps(scr, D, (t - tb) * S1 + sub + 1, d, eps1);
+                        discrete_substep_vjp(si, p, c, u, eps1, lx, lv, lR, lw, luf, leps, lu);
                     }
                     float ga[4];
                     for (int r = 0; r < 4; ++r) {
@@ -1024,8 +1035,8 @@ cudaError_t launch_diff(int backward, const Consts& c, const Dev& dv, const Tile
     a.ckpt = reinterpret_cast<float4*>(workspace);
     a.scratch = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + (size_t)nck * NPLANE * dv.D * sizeof(float4));
     // forward: one group of `block` threads; backward: two (recompute, reverse)
-    // with 15 planes of `block` floats between them
-    const size_t smem = sizeof(float) * 9 * block, smem2 = sizeof(float) * 15 * block;
+    // with up to 23 planes of `block` floats between them
+    const size_t smem = sizeof(float) * 9 * block, smem2 = sizeof(float) * 23 * block;
     if (2 * block > ADJ_BLOCK_MAX) return cudaErrorInvalidValue;
     if (c.flags & QS_F_SMOOTH) {
         if (backward) k_diff_bwd<<<n_tiles, 2 * block, smem2, st>>>(c, dv, tiles, perm, a);
