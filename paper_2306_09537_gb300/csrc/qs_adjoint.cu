@@ -353,7 +353,7 @@ __device__ __forceinline__ void group_sync(int id, int n) {
 // index lt; bid, bn: the barrier of the threads sharing them).
 __device__ __forceinline__ void smooth_substep(const Consts& c, Drone& s, const Prm& p, const float u[4], uint32_t tick,
                                                int d, int sub, bool act, float* sx, int nt, int sbase, int lane, int N,
-                                               int lt, int bid, int bn) {
+                                               int lt, int bid, int bn, const float* nrm = nullptr) {
     if (act) {
         sx[lt] = s.x[0];
         sx[nt + lt] = s.x[1];
@@ -363,7 +363,36 @@ __device__ __forceinline__ void smooth_substep(const Consts& c, Drone& s, const 
     float pa[3] = {0.f, 0.f, 0.f};
     if (act) pair_acc(c, s.x, sx, nt, sbase, lane, N, p.arm, pa);
     group_sync(bid, bn);
-    if (act) substep(s, p, c, u, tick, d, sub, pa);
+    if (act) substep(s, p, c, u, tick, d, sub, pa, nrm);
+}
+
+// The forward kernels run two groups of nb threads over the same drones: group
+// 0 integrates, group 1 draws the motor-noise normals of the next control
+// step (up to FWD_SUB substeps) into shared memory, double-buffered by step
+// parity, so that the Philox and Box-Muller work is off the integration chain.
+constexpr int FWD_SUB = 4;
+
+__device__ __forceinline__ float* fwd_normals(float* base, int nb, int b, int sub, int r, int lt) {
+    return base + ((b * FWD_SUB + sub) * 4 + r) * nb + lt;
+}
+
+// Group 1 of a forward kernel: step t's normals are ready at the t-th CTA
+// barrier of the loop; the next step's are drawn while group 0 integrates.
+__device__ __forceinline__ void fwd_noise_group(const Consts& c, float* nbase, int nb, int lt, bool act, bool ahead,
+                                                uint32_t tick0, int d, int T) {
+    const int S = c.substeps;
+    auto draw = [&](int t) {
+        for (int sub = 0; sub < S; ++sub) {
+            float n[4];
+            motor_normals(c, tick0 + (uint32_t)t, d, sub, n);
+            for (int r = 0; r < 4; ++r) *fwd_normals(nbase, nb, t & 1, sub, r, lt) = n[r];
+        }
+    };
+    if (ahead && act && T > 0) draw(0);
+    for (int t = 0; t < T; ++t) {
+        __syncthreads();  // buffer t & 1 holds step t's normals; buffer (t + 1) & 1 is free
+        if (ahead && act && t + 1 < T) draw(t + 1);
+    }
 }
 
 struct DiffArgs {
@@ -394,29 +423,36 @@ __device__ __forceinline__ void command4(const Consts& c, const float* act, size
 __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_fwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                             const int* __restrict__ perm, const DiffArgs a) {
     extern __shared__ float sm[];
-    const Tile tile = tile_at(dv, tiles, blockIdx.x, blockDim.x);
-    const int W = tile.W, nt = blockDim.x;
-    const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
+    const int nb = blockDim.x >> 1, grp = threadIdx.x >= nb ? 1 : 0, lt = threadIdx.x - grp * nb;
+    const Tile tile = tile_at(dv, tiles, blockIdx.x, nb);
+    const int W = tile.W, nt = nb;
+    const int slot = lt / W, lane = lt - slot * W;
     const bool ok = slot < tile.count;
     const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
     const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
     const bool act = lane < N;
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;
+    const bool ahead = (c.flags & QS_F_MOTOR_NOISE) && c.substeps <= FWD_SUB;
+    float* nbase = sm + 9 * nb;  // [2][FWD_SUB][4][nb] motor normals
+    const uint32_t tick0 = act ? dv.tick[e] : 0u;
+    if (grp == 1) {
+        fwd_noise_group(c, nbase, nb, lt, act, ahead, tick0, d, a.T);
+        return;
+    }
     Drone s;
     Prm p;
     float g[3] = {0.f, 0.f, 0.f};
-    uint32_t tick0 = 0;
     if (act) {
         read_x0(s, a.x0, d);
         p = load_prm(dv.prm, dv.E, e);
         g[0] = dv.goal[e];
         g[1] = dv.goal[dv.E + e];
         g[2] = dv.goal[2 * dv.E + e];
-        tick0 = dv.tick[e];
     }
     float L = 0.f;
     for (int t = 0; t < a.T; ++t) {
+        __syncthreads();  // step t's motor normals ready (group 1)
         if (act && t % a.C == 0) {
             float4 q[NPLANE];
             pack(s, q);
@@ -425,8 +461,12 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_fwd(const Consts c, cons
         }
         float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4];
         if (act) command4(c, a.act, D, t, d, fh, u, msk);
-        for (int sub = 0; sub < c.substeps; ++sub)
-            smooth_substep(c, s, p, u, tick0 + t, d, sub, act, sm, nt, sbase, lane, N, threadIdx.x, 0, nt);
+        for (int sub = 0; sub < c.substeps; ++sub) {
+            float n[4];
+            if (ahead)
+                for (int r = 0; r < 4; ++r) n[r] = *fwd_normals(nbase, nb, t & 1, sub, r, lt);
+            smooth_substep(c, s, p, u, tick0 + t, d, sub, act, sm, nt, sbase, lane, N, lt, 1, nb, ahead ? n : nullptr);
+        }
         if (act) {
             const float dx = s.x[0] - g[0], dy = s.x[1] - g[1], dz = s.x[2] - g[2];
             L += dx * dx + dy * dy + dz * dz + 1e-3f * (fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
@@ -847,9 +887,10 @@ __device__ __forceinline__ void collision_vjp(const Consts& c, const float xs[3]
 __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                              const int* __restrict__ perm, const DiffArgs a) {
     extern __shared__ float sm[];
-    const Tile tile = tile_at(dv, tiles, blockIdx.x, blockDim.x);
-    const int W = tile.W, nt = blockDim.x;
-    const int slot = threadIdx.x / W, lane = threadIdx.x - slot * W;
+    const int nb = blockDim.x >> 1, grp = threadIdx.x >= nb ? 1 : 0, lt = threadIdx.x - grp * nb;
+    const Tile tile = tile_at(dv, tiles, blockIdx.x, nb);
+    const int W = tile.W, nt = nb;
+    const int slot = lt / W, lane = lt - slot * W;
     const bool ok = slot < tile.count;
     const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
     const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
@@ -857,21 +898,27 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, con
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;
     const bool coll = (c.flags & QS_F_COLLISIONS) != 0;
+    const bool ahead = (c.flags & QS_F_MOTOR_NOISE) && c.substeps <= FWD_SUB;
+    float* nbase = sm + 9 * nb;  // [2][FWD_SUB][4][nb] motor normals
+    const uint32_t tick0 = act ? dv.tick[e] : 0u;
+    if (grp == 1) {
+        fwd_noise_group(c, nbase, nb, lt, act, ahead, tick0, d, a.T);
+        return;
+    }
     Drone s;
     Prm p;
     float g[3] = {0.f, 0.f, 0.f};
-    uint32_t tick0 = 0;
     if (act) {
         read_x0(s, a.x0, d);
         p = load_prm(dv.prm, dv.E, e);
         g[0] = dv.goal[e];
         g[1] = dv.goal[dv.E + e];
         g[2] = dv.goal[2 * dv.E + e];
-        tick0 = dv.tick[e];
     }
     const float zero3[3] = {0.f, 0.f, 0.f};
     float L = 0.f;
     for (int t = 0; t < a.T; ++t) {
+        __syncthreads();  // step t's motor normals ready (group 1)
         if (act && t % a.C == 0) {
             float4 q[NPLANE];
             pack(s, q);
@@ -881,9 +928,14 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, con
         float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4];
         if (act) {
             command4(c, a.act, D, t, d, fh, u, msk);
-            for (int sub = 0; sub < c.substeps; ++sub) substep(s, p, c, u, tick0 + t, d, sub, zero3);
+            for (int sub = 0; sub < c.substeps; ++sub) {
+                float n[4];
+                if (ahead)
+                    for (int r = 0; r < 4; ++r) n[r] = *fwd_normals(nbase, nb, t & 1, sub, r, lt);
+                substep(s, p, c, u, tick0 + t, d, sub, zero3, ahead ? n : nullptr);
+            }
         }
-        if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sm, sm + 3 * nt, nt, sbase, lane, N, threadIdx.x, 0, nt);
+        if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sm, sm + 3 * nt, nt, sbase, lane, N, lt, 1, nb);
         if (act) {
             const float dx = s.x[0] - g[0], dy = s.x[1] - g[1], dz = s.x[2] - g[2];
             L += dx * dx + dy * dy + dz * dz + 1e-3f * (fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
@@ -1034,16 +1086,16 @@ cudaError_t launch_diff(int backward, const Consts& c, const Dev& dv, const Tile
     const int nck = (T + C - 1) / C;
     a.ckpt = reinterpret_cast<float4*>(workspace);
     a.scratch = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + (size_t)nck * NPLANE * dv.D * sizeof(float4));
-    // forward: one group of `block` threads; backward: two (recompute, reverse)
-    // with up to 23 planes of `block` floats between them
-    const size_t smem = sizeof(float) * 9 * block, smem2 = sizeof(float) * 23 * block;
+    // forward: two groups of `block` threads (integration, motor normals ahead);
+    // backward: two (recompute, reverse) with up to 23 planes of `block` floats
+    const size_t smem = sizeof(float) * (9 + 2 * FWD_SUB * 4) * block, smem2 = sizeof(float) * 23 * block;
     if (2 * block > ADJ_BLOCK_MAX) return cudaErrorInvalidValue;
     if (c.flags & QS_F_SMOOTH) {
         if (backward) k_diff_bwd<<<n_tiles, 2 * block, smem2, st>>>(c, dv, tiles, perm, a);
-        else k_diff_fwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
+        else k_diff_fwd<<<n_tiles, 2 * block, smem, st>>>(c, dv, tiles, perm, a);
     } else {
         if (backward) k_diffd_bwd<<<n_tiles, 2 * block, smem2, st>>>(c, dv, tiles, perm, a);
-        else k_diffd_fwd<<<n_tiles, block, smem, st>>>(c, dv, tiles, perm, a);
+        else k_diffd_fwd<<<n_tiles, 2 * block, smem, st>>>(c, dv, tiles, perm, a);
     }
     return cudaGetLastError();
 }
