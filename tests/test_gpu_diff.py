@@ -117,6 +117,38 @@ def test_adjoint_matches_torch_autograd_reference():
         assert np.all(err <= 1e-3 * np.abs(ref) + 1e-4 * scale), err.max() / scale
 
 
+@pytest.mark.parametrize("features", [("smooth",), ("floor", "walls", "collisions")])
+def test_wide_swarms_adjoint(features):
+    """Swarms of 128 and 64 drones (the adjoint's two warp groups then span
+    several warps each and meet at named barriers) next to a small one:
+    forward loss against the FP64 oracle, gradients independent of the
+    checkpoint interval (one segment, or several pipelined), and, for the
+    smooth contacts, against torch.autograd through the FP64 reference."""
+    sizes = [128, 64, 3]
+    T = 12
+    env, o, st, prm, goals, acts = setup(sizes, T, 31, features=features, spread=0.3)
+    loss, ga, gx = gpu_grads(env, st, acts, 3)
+    want = oracle_total(o, st.astype(np.float64), prm.astype(np.float64), goals.astype(np.float64),
+                        acts.astype(np.float64))
+    assert np.allclose(loss, want, rtol=1e-4, atol=1e-4)
+    _, ga1, gx1 = gpu_grads(env, st, acts, T)
+    assert np.array_equal(ga, ga1) and np.array_equal(gx, gx1)
+    if "smooth" in features:
+        p = env.cfg.params
+        cfg = {"dt": env.cfg.dt, "gravity": p.gravity, "alpha_ns_frac": p.alpha_ns_frac, "alpha_nd": p.alpha_nd,
+               "smooth_kc": p.smooth_kc, "smooth_beta": p.smooth_beta, "kappa": p.kappa, "room_hx": p.room_hx,
+               "room_hy": p.room_hy, "room_h": p.room_h, "omega_max": p.omega_max, "substeps": env.cfg.substeps}
+        cfg = {k: float(v) if k != "substeps" else int(v) for k, v in cfg.items()}
+        x0 = torch.tensor(st.astype(np.float64), requires_grad=True)
+        a = torch.tensor(acts.astype(np.float64), requires_grad=True)
+        L = smooth_rollout_loss(x0, a, torch.tensor(prm.astype(np.float64)), torch.tensor(goals.astype(np.float64)),
+                                sizes, cfg).sum()
+        L.backward()
+        for g, ref in ((ga, a.grad.numpy()), (gx[:, :26], x0.grad.numpy()[:, :26])):
+            scale = np.abs(ref).max()
+            assert np.all(np.abs(g - ref) <= 1e-3 * np.abs(ref) + 1e-4 * scale), np.abs(g - ref).max() / scale
+
+
 def test_checkpoint_interval_does_not_change_gradients():
     sizes = [8] * 16 + [3] * 8
     T = 24
