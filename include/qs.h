@@ -390,6 +390,20 @@ qs_status qs_get_events(qs_env* h, uint32_t* events_dev, int16_t* knn_dev);
  * (QS_ERR_STATE_NONFINITE stays reported until the next full qs_reset). */
 qs_status qs_sync(qs_env* h);
 
+/* The library's Philox4x32-10 counter-based generator (Salmon et al., SC'11),
+ * which every random draw of the step, the resets and the scenarios uses,
+ * exposed for checking it against other implementations:
+ * out_dev[i][0..3] = Philox4x32-10(counter (ctr_dev[i][0], ctr_dev[i][1],
+ * ctr_dev[i][2], 0), key (key0, key1)) for i < n, computed on the current
+ * device and enqueued on cuda_stream (NULL: the legacy default stream).
+ * ctr_dev [n][3] and out_dev [n][4] (16-byte aligned) are uint32 device
+ * buffers owned by the caller. variant 0 uses the round keys precomputed on
+ * the host (the form the step's draws use), 1 the inline key schedule (the
+ * form of the reset draws). QS_ERR_ARG for NULL or misaligned buffers,
+ * n < 0 or another variant. Needs no handle. */
+qs_status qs_philox4x32_10(const uint32_t* ctr_dev, uint32_t key0, uint32_t key1, int32_t variant, uint32_t* out_dev,
+                           int64_t n, void* cuda_stream);
+
 /* Launch shape of qs_step for one swarm-width class (the envs whose swarm size
  * rounds up to the power of two `width`, 1..128): `block` threads per CTA, a
  * multiple of 32 and of `width`, at most 256; or QS_BLOCK_WARP_SPECIALISED

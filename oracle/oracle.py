@@ -93,6 +93,7 @@ def lib():
             L = C.CDLL(_LIB_PATH)
             P = C.POINTER
             L.or_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
+            L.or_philox4x32_10_n.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32), C.c_size_t]
             L.or_uniform.argtypes = [C.c_uint32]
             L.or_uniform.restype = C.c_double
             L.or_polar.argtypes = [P(C.c_double), P(C.c_double)]
@@ -136,6 +137,15 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     k = np.ascontiguousarray(key, dtype=np.uint32)
     out = np.zeros(4, dtype=np.uint32)
     lib().or_philox4x32_10(_ptr(c, C.c_uint32), _ptr(k, C.c_uint32), _ptr(out, C.c_uint32))
+    return out
+
+
+def philox4x32_10_batch(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of every row of ctr [n][4] under key [2]: [n][4] uint32."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros_like(c)
+    lib().or_philox4x32_10_n(_ptr(c, C.c_uint32), _ptr(k, C.c_uint32), _ptr(out, C.c_uint32), c.shape[0])
     return out
 
 

@@ -71,6 +71,11 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
+/* n blocks: out[4 i .. 4 i + 3] = or_philox4x32_10(ctr[4 i .. 4 i + 3], key). */
+void or_philox4x32_10_n(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, size_t n) {
+    for (size_t i = 0; i < n; ++i) or_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
 /* u = (2k+1) / 2^24 with k = the top 23 bits of r: strictly inside (0,1) and
  * exactly representable in binary32 and binary64 alike. */
 double or_uniform(uint32_t r) { return ((double)(r >> 9) + 0.5) * (1.0 / 8388608.0); }

@@ -133,6 +133,7 @@ typedef struct {
 } or_env;
 
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void or_philox4x32_10_n(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, size_t n);
 double or_uniform(uint32_t r);
 void or_polar(const double m[9], double r[9]);
 float or_pair_key(const float xi[3], const float xj[3]);

@@ -1134,6 +1134,14 @@ qs_status qs_serve_end(qs_env* h) {
     return QS_OK;
 }
 
+qs_status qs_philox4x32_10(const uint32_t* ctr_dev, uint32_t key0, uint32_t key1, int32_t variant, uint32_t* out_dev,
+                           int64_t n, void* cuda_stream) {
+    if (n < 0 || (n > 0 && (!ctr_dev || !out_dev)) || (variant != 0 && variant != 1) || (out_dev && !aligned(out_dev, 16)))
+        return fail(nullptr, QS_ERR_ARG, "qs_philox4x32_10: NULL or misaligned buffer, n < 0 or variant not 0 / 1");
+    const cudaError_t e = launch_philox(ctr_dev, key0, key1, variant, out_dev, (long long)n, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? QS_OK : fail(nullptr, QS_ERR_CUDA, std::string("qs_philox4x32_10: ") + cudaGetErrorString(e));
+}
+
 const char* qs_last_error(const qs_env* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 }  // extern "C"

@@ -160,6 +160,10 @@ cudaError_t launch_diff(int backward, const Consts& c, const Dev& dv, const Tile
                         float* grad_act, float* grad_x0, void* workspace, int T, int C, cudaStream_t s);
 
 // kernels (qs_kernels.cu)
+// out [n][4] = Philox4x32-10 of ctr [n][3] (word 3 zero) under (key0, key1);
+// variant 0: precomputed round keys, 1: inline key schedule.
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int variant, uint32_t* out, long long n,
+                          cudaStream_t s);
 cudaError_t launch_reset(const Consts& c, const Dev& dv, uint32_t key0, uint32_t key1, const uint8_t* mask,
                          cudaStream_t s);
 cudaError_t launch_get_state(const Dev& dv, float* state, float* params, float* goals, int32_t* ep,

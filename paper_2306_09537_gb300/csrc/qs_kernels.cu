@@ -174,4 +174,35 @@ cudaError_t launch_get_events(const Dev& dv, int K, uint32_t* events, int16_t* k
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- Philox check
+// out[i] = Philox4x32-10(ctr[i][0..2], 0; key) through the same device
+// functions the step and the resets draw with: the precomputed round keys
+// (variant 0) or the inline key schedule (variant 1).
+struct RoundKeys {
+    uint32_t rk[20];
+};
+
+__global__ void k_philox(const uint32_t* __restrict__ ctr, RoundKeys rk, uint32_t key0, uint32_t key1, int variant,
+                         uint4* __restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t c0 = ctr[3 * i], c1 = ctr[3 * i + 1], c2 = ctr[3 * i + 2];
+        out[i] = variant == 0 ? philox_rk(c0, c1, c2, rk.rk) : philox(c0, c1, c2, key0, key1);
+    }
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int variant, uint32_t* out, long long n,
+                          cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    Consts c{};
+    c.key0 = key0;
+    c.key1 = key1;
+    set_round_keys(c);
+    RoundKeys rk;
+    for (int k = 0; k < 20; ++k) rk.rk[k] = c.rk[k];
+    const long long want = (n + 255) / 256;
+    const int grid = (int)(want < 4096 ? want : 4096);
+    k_philox<<<grid, 256, 0, st>>>(ctr, rk, key0, key1, variant, reinterpret_cast<uint4*>(out), n);
+    return cudaGetLastError();
+}
+
 }  // namespace qsk

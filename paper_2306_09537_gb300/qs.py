@@ -33,7 +33,7 @@ EXPORTS = ["qs_config_default", "qs_create", "qs_destroy", "qs_get_dims", "qs_re
            "qs_rollout", "qs_set_rollout_shape", "qs_get_rollout_shape", "qs_diff_workspace_size",
            "qs_diff_forward", "qs_diff_backward", "qs_diff_grad_static", "qs_get_state", "qs_set_state",
            "qs_get_events", "qs_get_scenario", "qs_set_scenario", "qs_get_goals", "qs_sync", "qs_set_block",
-           "qs_get_block", "qs_serve_begin", "qs_serve_step", "qs_serve_end", "qs_last_error"]
+           "qs_get_block", "qs_serve_begin", "qs_serve_step", "qs_serve_end", "qs_philox4x32_10", "qs_last_error"]
 # training scenarios (Sec. III-D) and goal formations, in the order of QS_SCN_* / QS_FORM_*
 SCENARIOS = ["single", "static", "dynamic", "swap", "shrink_expand", "swarm_vs_swarm", "pursuit_lissajous",
              "pursuit_bezier"]
@@ -109,6 +109,7 @@ def _load():
     L.qs_serve_begin.argtypes = [V, V, C.c_int32, V, V, V, C.c_int32]
     L.qs_serve_step.argtypes = [V, C.c_int32]
     L.qs_serve_end.argtypes = [V]
+    L.qs_philox4x32_10.argtypes = [V, C.c_uint32, C.c_uint32, C.c_int32, V, C.c_int64, V]
     L.qs_set_block.argtypes = [V, C.c_int32, C.c_int32]
     L.qs_get_block.argtypes = [V, C.c_int32, P(C.c_int32)]
     L.qs_last_error.argtypes = [V]
@@ -269,6 +270,13 @@ def qs_serve_step(h, slot: int = 0):
 
 def qs_serve_end(h):
     return _check(_L.qs_serve_end(h), h)
+
+
+def qs_philox4x32_10(ctr, key0: int, key1: int, out, variant: int = 0, stream=None):
+    """out [n][4] = the library's Philox4x32-10 of ctr [n][3] (uint32 tensors on the device)."""
+    n = ctr.shape[0]
+    return _check(_L.qs_philox4x32_10(_p(ctr), C.c_uint32(int(key0)), C.c_uint32(int(key1)), int(variant), _p(out),
+                                      int(n), stream))
 
 
 def qs_set_block(h, width: int, block: int):

@@ -24,7 +24,7 @@ def qs():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "qs.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(qs_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(qs_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(qs):
