@@ -1,0 +1,80 @@
+"""Closed forms checked on the CUDA path directly (the oracle is pinned to the
+same ones in test_oracle_pins.py): hover equilibrium and the discrete free
+fall of semi-implicit Euler, through the per-call step and the rollout."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import DEV, nominal
+from paper_2306_09537_gb300.env import QuadSwarmEnv
+
+pytestmark = pytest.mark.gpu
+
+E = 256
+
+
+def _env(z0):
+    """Drones at rest, upright, nominal parameters (t2w = 2: hover command 1/2),
+    motors at hover speed sqrt(1/2), no noise, floor or walls."""
+    env = QuadSwarmEnv(E, 1, 0, (), seed=1, device=DEV)
+    st = np.zeros((E, 30), np.float32)
+    st[:, 0] = np.linspace(-3, 3, E)
+    st[:, 1] = np.linspace(2, -2, E)
+    st[:, 2] = z0
+    st[:, 6:15] = np.eye(3, dtype=np.float32).ravel()
+    prm = np.tile(np.array(nominal(env), np.float32), (E, 1))
+    assert prm[0, 4] == 2.0  # t2w
+    return env, st, prm
+
+
+def _set(env, st, prm):
+    env.set_state(torch.from_numpy(st).to(DEV), torch.from_numpy(prm).to(DEV), torch.zeros(E, 3, device=DEV),
+                  torch.zeros(E, dtype=torch.int32, device=DEV), torch.zeros(E, dtype=torch.int32, device=DEV))
+
+
+@pytest.mark.parametrize("form", ["step", "rollout"])
+def test_hover_equilibrium(form):
+    """Thrust m g on every rotor set: no torque, so the rotation stays exactly
+    the identity and the body rates exactly zero; the position drifts only by
+    the binary32 rounding of the thrust balance (|T / m - g| ~ 1e-6 m/s^2,
+    under 1e-5 m over 10 s)."""
+    env, st, prm = _env(5.0)
+    st[:, 18:22] = np.sqrt(np.float32(0.5))  # u_f at hover
+    st[:, 26:30] = 0.5                       # previous command
+    _set(env, st, prm)
+    T = 1000
+    acts = torch.full((T, env.D, 4), 0.5, device=DEV)
+    if form == "step":
+        for t in range(T):
+            env.step(acts[t])
+    else:
+        env.rollout(acts, torch.empty(T, env.D, env.obs_dim, device=DEV), None, None)
+    s = env.get_state()["state"].cpu().numpy()
+    assert np.array_equal(s[:, 6:15], st[:, 6:15])       # R = I
+    assert np.all(s[:, 15:18] == 0)                      # body rates
+    assert np.abs(s[:, 0:3] - st[:, 0:3]).max() <= 1e-5  # position
+    assert np.abs(s[:, 3:6]).max() <= 1e-5               # velocity
+
+
+@pytest.mark.parametrize("form", ["step", "rollout"])
+def test_free_fall_semi_implicit_euler(form):
+    """Motors off: a = g exactly each substep, so after n substeps of dt
+    v_n = -g n dt and z_n = z_0 - g dt^2 n (n + 1) / 2 (semi-implicit Euler;
+    explicit Euler would give n (n - 1) / 2, 2.5 cm apart after 1 s), within
+    binary32 accumulation; x and y stay exactly put."""
+    env, st, prm = _env(9.0)
+    _set(env, st, prm)
+    T = 100
+    acts = torch.zeros(T, env.D, 4, device=DEV)
+    if form == "step":
+        for t in range(T):
+            env.step(acts[t])
+    else:
+        env.rollout(acts, torch.empty(T, env.D, env.obs_dim, device=DEV), None, None)
+    s = env.get_state()["state"].cpu().numpy()
+    dt, g, n = float(env.cfg.dt), float(env.cfg.params.gravity), T * int(env.cfg.substeps)
+    z = 9.0 - g * dt * dt * n * (n + 1) / 2
+    assert np.abs(s[:, 2] - z).max() <= 2e-4
+    assert np.abs(s[:, 5] - (-g * n * dt)).max() <= 2e-5
+    assert np.array_equal(s[:, 0:2], st[:, 0:2]) and np.all(s[:, 3:5] == 0)
+    assert abs(z - (9.0 - g * dt * dt * n * (n - 1) / 2)) > 0.02  # the two integrators are told apart
