@@ -78,3 +78,30 @@ def test_free_fall_semi_implicit_euler(form):
     assert np.abs(s[:, 5] - (-g * n * dt)).max() <= 2e-5
     assert np.array_equal(s[:, 0:2], st[:, 0:2]) and np.all(s[:, 3:5] == 0)
     assert abs(z - (9.0 - g * dt * dt * n * (n - 1) / 2)) > 0.02  # the two integrators are told apart
+
+
+def test_head_on_collision_swaps_normal_velocities():
+    """Two equal drones closing head-on along x, alpha_c = 1 and no
+    perturbation: after the step's collision pass their x velocities are
+    swapped (so momentum and kinetic energy are conserved), both are flagged,
+    and the tangential components are untouched."""
+    env = QuadSwarmEnv(1, 2, 1, ("collisions",), seed=1, device=DEV, alpha_c=1.0, coll_sigma_v=0.0, coll_sigma_w=0.0)
+    st = np.zeros((2, 30), np.float32)
+    st[:, 2] = 5.0
+    st[0, 0], st[1, 0] = -0.03, 0.03          # 6 cm apart: inside 2 x arm (9.2 cm)
+    st[0, 3], st[1, 3] = 1.0, -0.5            # closing at 1.5 m/s
+    st[:, 4] = 0.25                           # a common tangential velocity
+    st[:, 6:15] = np.eye(3, dtype=np.float32).ravel()
+    st[:, 18:22] = np.sqrt(np.float32(0.5))
+    st[:, 26:30] = 0.5
+    prm = np.tile(np.array(nominal(env), np.float32), (1, 1))
+    env.set_state(torch.from_numpy(st).to(DEV), torch.from_numpy(prm).to(DEV), torch.zeros(1, 3, device=DEV),
+                  torch.zeros(1, dtype=torch.int32, device=DEV), torch.zeros(1, dtype=torch.int32, device=DEV))
+    env.step(torch.full((2, 4), 0.5, device=DEV))
+    s = env.get_state()["state"].cpu().numpy()
+    ev, _ = env.get_events()
+    assert abs(s[0, 3] - (-0.5)) <= 1e-5 and abs(s[1, 3] - 1.0) <= 1e-5
+    assert abs((s[0, 3] + s[1, 3]) - 0.5) <= 1e-5                              # momentum
+    assert abs((s[0, 3] ** 2 + s[1, 3] ** 2) - (1.0 + 0.25)) <= 2e-5            # kinetic energy along x
+    assert np.allclose(s[:, 4], 0.25, atol=1e-6) and np.abs(s[:, 5]).max() <= 1e-5
+    assert np.all((ev.cpu().numpy() & 16) != 0)                                 # hit_quad on both
