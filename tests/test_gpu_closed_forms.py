@@ -105,3 +105,40 @@ def test_head_on_collision_swaps_normal_velocities():
     assert abs((s[0, 3] ** 2 + s[1, 3] ** 2) - (1.0 + 0.25)) <= 2e-5            # kinetic energy along x
     assert np.allclose(s[:, 4], 0.25, atol=1e-6) and np.abs(s[:, 5]).max() <= 1e-5
     assert np.all((ev.cpu().numpy() & 16) != 0)                                 # hit_quad on both
+
+
+def test_motor_lag_step_response():
+    """From rest, command 1 on every rotor: the normalised rotor speed after n
+    substeps is 1 - (1 - alpha)^n with alpha = 1 - exp(-dt / tau_m), reaching
+    98% after ceil(ln 50 / -ln(1 - alpha)) substeps (2% settling, tau_m ln 50)."""
+    env, st, prm = _env(5.0)
+    _set(env, st, prm)
+    dt, tau = float(env.cfg.dt), float(prm[0, 5])
+    alpha = 1.0 - np.exp(-dt / tau)
+    n98 = int(np.ceil(np.log(50.0) / -np.log(1.0 - alpha)))
+    S = int(env.cfg.substeps)
+    for t in range(1, (n98 + S - 1) // S + 2):
+        env.step(torch.ones(env.D, 4, device=DEV))
+        uf = env.get_state()["state"][:, 18:22].cpu().numpy()
+        n = t * S
+        assert np.abs(uf - (1.0 - (1.0 - alpha) ** n)).max() <= 2e-6, t
+        assert (uf.min() >= 0.98) == (n >= n98), t
+
+
+def test_torque_free_spin_about_a_principal_axis():
+    """Motors off and a body rate about the z axis: w x (I w) vanishes, so the
+    body rate stays exactly constant, and the rotation advances by
+    atan(dt w_z) per substep about z (the polar factor of I + dt [w]x)."""
+    env, st, prm = _env(9.0)
+    wz = 3.0
+    st[:, 17] = wz
+    _set(env, st, prm)
+    T = 50
+    for t in range(T):
+        env.step(torch.zeros(env.D, 4, device=DEV))
+    s = env.get_state()["state"].cpu().numpy()
+    dt, n = float(env.cfg.dt), T * int(env.cfg.substeps)
+    psi = n * np.arctan(dt * wz)
+    Rz = np.array([[np.cos(psi), -np.sin(psi), 0.0], [np.sin(psi), np.cos(psi), 0.0], [0.0, 0.0, 1.0]])
+    assert np.all(s[:, 15] == 0) and np.all(s[:, 16] == 0) and np.all(s[:, 17] == np.float32(wz))
+    assert np.abs(s[:, 6:15] - Rz.ravel()).max() <= 2e-5
