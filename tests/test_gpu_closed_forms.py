@@ -142,3 +142,50 @@ def test_torque_free_spin_about_a_principal_axis():
     Rz = np.array([[np.cos(psi), -np.sin(psi), 0.0], [np.sin(psi), np.cos(psi), 0.0], [0.0, 0.0, 1.0]])
     assert np.all(s[:, 15] == 0) and np.all(s[:, 16] == 0) and np.all(s[:, 17] == np.float32(wz))
     assert np.abs(s[:, 6:15] - Rz.ravel()).max() <= 2e-5
+
+
+def test_wall_removes_the_normal_velocity():
+    """A drone past the x wall and moving outward (alpha_c = 1, no
+    perturbation): put back on the wall, its normal velocity removed, the
+    tangential one kept; flagged hit_wall."""
+    env = QuadSwarmEnv(E, 1, 0, ("walls",), seed=1, device=DEV, alpha_c=1.0, coll_sigma_v=0.0, coll_sigma_w=0.0)
+    _, st, prm = _env(5.0)
+    hx = float(env.cfg.params.room_hx)
+    st[:, 0] = hx - 0.001
+    st[:, 3] = 2.0                 # outward: crosses the wall within the step
+    st[:, 4] = np.linspace(-1, 1, E)
+    st[:, 18:22] = np.sqrt(np.float32(0.5))
+    st[:, 26:30] = 0.5
+    _set(env, st, prm)
+    env.step(torch.full((E, 4), 0.5, device=DEV))
+    s = env.get_state()["state"].cpu().numpy()
+    ev, _ = env.get_events()
+    assert np.all(s[:, 0] == np.float32(hx)) and np.all(s[:, 3] == 0)
+    assert np.abs(s[:, 4] - st[:, 4]).max() <= 1e-6
+    assert np.all((ev.cpu().numpy() & 4) != 0)  # hit_wall
+
+
+def test_floor_hit_rests_upright_keeping_the_heading():
+    """A tilted, rolling drone falling through the floor: height, velocity and
+    body rates zero, the rotation upright about z with the heading of the body
+    x axis kept; flagged hit_floor."""
+    env = QuadSwarmEnv(E, 1, 0, ("floor",), seed=1, device=DEV)
+    _, st, prm = _env(0.005)
+    yaw = np.linspace(-3.0, 3.0, E)
+    tilt = 0.3
+    for i, psi in enumerate(yaw):
+        Rz = np.array([[np.cos(psi), -np.sin(psi), 0], [np.sin(psi), np.cos(psi), 0], [0, 0, 1.0]])
+        Rx = np.array([[1.0, 0, 0], [0, np.cos(tilt), -np.sin(tilt)], [0, np.sin(tilt), np.cos(tilt)]])
+        st[i, 6:15] = (Rz @ Rx).ravel()
+    st[:, 5] = -2.0
+    st[:, 15:18] = (1.0, 0.0, 0.0)  # a roll rate: turns about the body x axis, whose heading is kept
+    _set(env, st, prm)
+    env.step(torch.zeros(E, 4, device=DEV))
+    s = env.get_state()["state"].cpu().numpy()
+    ev, _ = env.get_events()
+    assert np.all(s[:, 2] == 0) and np.all(s[:, 3:6] == 0) and np.all(s[:, 15:18] == 0)
+    R = s[:, 6:15].reshape(E, 3, 3)
+    assert np.abs(R[:, 2, :] - [0, 0, 1]).max() == 0 and np.abs(R[:, :, 2] - [0, 0, 1]).max() == 0
+    heading = np.arctan2(R[:, 1, 0], R[:, 0, 0])
+    assert np.abs(np.angle(np.exp(1j * (heading - yaw)))).max() <= 1e-5
+    assert np.all((ev.cpu().numpy() & 1) != 0)  # hit_floor
