@@ -499,19 +499,28 @@ qs_status qs_create(const qs_config* cfg, void* cuda_stream, qs_env** out) {
         }
     }
     // default rollout shape: warp-specialised while every class is at most 32
-    // wide, the handle fits about one wave of its CTAs (latency-bound) and
+    // wide, its CTAs (one per 32 drone lanes) fit one wave on the device
+    // (latency-bound; a second wave would run the whole horizon again) and
     // neither scenarios nor downwash lengthen the dynamics warp's step (then
     // its noise warp would idle at the barriers); else the persistent kernel,
     // whose work counter also balances uneven swarm sizes. Measured on GB300
-    // (warp-specialised vs persistent): plain 8192 x 1 3.2e9 vs 2.4e9, swarm
-    // 2048 x 8 3.6e9 vs 2.8e9; with every scenario type 1.9e9 vs 2.0e9;
+    // (warp-specialised vs persistent, us per step): plain 8192 x 1 2.66 vs
+    // 3.47, 28,672 x 1 3.75 vs 3.90, 30,720 x 1 (past the 29,184 lanes of
+    // one wave) 5.89 vs 3.90; swarm 2048 x 8 4.81 vs 6.67, 4096 x 8 9.46 vs
+    // 7.81; with every scenario type 1.9e9 vs 2.0e9 quadrotor-steps/s;
     // uneven sizes up to 64 (two-warp pairs per CTA) 1.86e9 vs 1.80e9, close
     // enough to leave to the autotuner.
     {
         int maxW = 1;
-        for (const ClassPlan& cp : h->plan) maxW = std::max(maxW, cp.W);
+        long ws_ctas = 0;
+        for (size_t ci = 0; ci < h->plan.size(); ++ci) {
+            maxW = std::max(maxW, h->plan[ci].W);
+            const int per = std::max(1, 32 / h->plan[ci].W);
+            ws_ctas += (h->class_slots[ci] + per - 1) / per;
+        }
         const bool ext = (h->c.scn_mask & ~1u) != 0 || (h->c.flags & QS_F_DOWNWASH) != 0;
-        if (maxW <= 32 && !ext && (long)h->D <= ws_wave(n_sm)) h->rollout_block = QS_BLOCK_WARP_SPECIALISED;
+        if (maxW <= 32 && !ext && ws_ctas <= rollout_ws_resident_ctas(h->c, 1))
+            h->rollout_block = QS_BLOCK_WARP_SPECIALISED;
     }
 
     // one arena for the state

@@ -149,6 +149,9 @@ cudaError_t launch_serve(const Consts& c, const Dev& dv, const Tile* tiles, int 
                          const ServeIO& io, int k0, cudaStream_t s);
 // CTAs of the server the device keeps resident at once.
 int serve_resident_ctas(const Consts& c, int P);
+// CTAs of the warp-specialised rollout (64P threads) the device keeps
+// resident at once.
+int rollout_ws_resident_ctas(const Consts& c, int P);
 // CTAs of `block` threads the device keeps resident at once for k_rollout
 // (the instance with or without scenarios and downwash).
 int rollout_grid(int block, bool extended);

@@ -1008,6 +1008,17 @@ int serve_resident_ctas(const Consts& c, int P) {
     return occ * n_sm;
 }
 
+int rollout_ws_resident_ctas(const Consts& c, int P) {
+    int dev = 0, n_sm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const bool ext = extended(c);
+    const void* fn = P == 1 ? (ext ? (const void*)k_rollout_ws<true, 1> : (const void*)k_rollout_ws<false, 1>)
+                            : (ext ? (const void*)k_rollout_ws<true, 2> : (const void*)k_rollout_ws<false, 2>);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 64 * P, 0) != cudaSuccess) return 0;
+    return occ * n_sm;
+}
+
 template <bool EXT>
 cudaError_t launch_k_step(const Consts& c, const Dev& dv, const ClassPlan& cp, const Tile* t, const int* perm,
                           const StepIO& io, int observe_only, size_t smem, cudaStream_t st) {

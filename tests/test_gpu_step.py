@@ -415,6 +415,19 @@ def test_ws_rollout_equals_steps(shape, extended, widest):
         assert torch.equal(env.get_scenario(), env2.get_scenario())
 
 
+def test_ws_rollout_default_only_within_one_wave():
+    """The warp-specialised rollout is the default only while its CTAs (one per
+    32 drone lanes) fit one wave: a second wave would run the whole horizon
+    again. 155,680 drones need 4,865 CTAs, more than 152 SMs x 32 resident
+    CTAs could hold at any occupancy."""
+    from paper_2306_09537_gb300 import qs
+    from paper_2306_09537_gb300.env import QuadSwarmEnv
+    for E, ws in ((4096, True), (152 * 32 * 32 + 32, False)):
+        env = QuadSwarmEnv(E, 1, 0, ("floor", "walls", "motor_noise", "obs_noise", "dr"), seed=1, device=DEV)
+        assert (qs.qs_get_rollout_shape(env.h)[0] == qs.QS_BLOCK_WARP_SPECIALISED) == ws, E
+        env.close()
+
+
 def test_ws_rollout_needs_narrow_classes():
     from paper_2306_09537_gb300 import qs
     env, _ = pair([4, 65], 2, FULL, seed=1)
