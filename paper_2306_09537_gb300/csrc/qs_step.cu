@@ -844,9 +844,13 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_rollout_ws(const C
 // poll (one reader of the host's line instead of one per CTA). Measured on
 // GB300 at 8192 single-drone envs: one system-scope fence per CTA instead of
 // one per thread, and the relay instead of every CTA polling the host, took a
-// posted step from 15.8 to 11.1 us; a completion byte per CTA polled by the
-// host instead of the counter and fin was slower (11.7 us: 64 CTAs write each
-// line the host re-reads).
+// posted step from 15.8 to 11.1 us, and an acquire-release count instead of
+// a second system-scope fence in the last CTA to 10.6 us; a completion byte
+// per CTA polled by the host instead of the counter and fin was slower (11.7
+// us: 64 CTAs write each line the host re-reads), and so were several reads
+// of go (or of the relay) kept in flight at once instead of one (7.2 -> 11.2
+// us for a one-CTA server: the reads keep taking the line from the host
+// while it posts).
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -867,6 +871,12 @@ __device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_gpu(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
 }
 
 __device__ __forceinline__ void st_release_gpu(unsigned long long* p, unsigned long long v) {
@@ -966,13 +976,12 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_serve(const Consts
         }
         __syncthreads();  // B3
         if (threadIdx.x == 0) {
-            // the CTA's host writes of the step (ordered before it by B3) before its count
+            // the CTA's host writes of the step (ordered before it by B3) performed
+            // at system scope before its count; the count's acquire side orders
+            // every CTA's count before the last one's release of fin
             __threadfence_system();
-            const unsigned long long n = atomicAdd(io.count, 1ull) + 1ull;
-            if (n == (unsigned long long)gridDim.x * (unsigned long long)(k + 1)) {
-                __threadfence_system();
-                st_release_sys(io.fin, k0 + k + 1);
-            }
+            const unsigned long long n = atom_add_acq_rel_gpu(io.count, 1ull) + 1ull;
+            if (n == (unsigned long long)gridDim.x * (unsigned long long)(k + 1)) st_release_sys(io.fin, k0 + k + 1);
         }
     }
     if (noise || !m.act) return;

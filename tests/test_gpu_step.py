@@ -655,6 +655,7 @@ def _one_step_through(env, o, acts, path):
 @pytest.mark.parametrize("wl_name,path", [
     ("swarm_2048x8_k6", "call"), ("swarm_2048x8_k6", (1, 0, False)), ("swarm_2048x8_k6", (64, 0, True)),
     ("uneven_4096", "call"), ("uneven_4096", (64, 0, True)), ("uneven_4096", (128, 0, False)),
+    ("uneven_4096", (1, 0, True)),  # warp-specialised rollout with two-warp pairs (swarms up to 64)
 ])
 def test_full_size_one_step_parity(wl_name, path):
     """The swarm (2048 x 8, K = 6) and uneven (4096 envs, 40,408 drones)
