@@ -845,7 +845,8 @@ __global__ void __launch_bounds__(64 * P, (P == 1 ? 6 : 1)) k_rollout_ws(const C
 // GB300 at 8192 single-drone envs: one system-scope fence per CTA instead of
 // one per thread, and the relay instead of every CTA polling the host, took a
 // posted step from 15.8 to 11.1 us, and an acquire-release count instead of
-// a second system-scope fence in the last CTA to 10.6 us; a completion byte
+// a second system-scope fence in the last CTA a synchronous host loop from
+// 11.5 to 11.0 us per step; a completion byte
 // per CTA polled by the host instead of the counter and fin was slower (11.7
 // us: 64 CTAs write each line the host re-reads), and so were several reads
 // of go (or of the relay) kept in flight at once instead of one (7.2 -> 11.2
