@@ -295,8 +295,8 @@ qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_
 /* Launch shape of qs_rollout: `block` threads per CTA of the persistent
  * kernel (32..256, a multiple of 32, at least the widest swarm class), or
  * QS_BLOCK_WARP_SPECIALISED (every class at most 64 wide; the default when
- * every class is at most 32 wide, the handle has at most about one wave of
- * such CTAs and neither scenarios nor downwash are on): per 32 drones
+ * every class is at most 32 wide, all of the handle's such CTAs are
+ * resident at once and neither scenarios nor downwash are on): per 32 drones
  * (64 when a class is wider than 32) one CTA whose dynamics warps integrate
  * while as many noise warps draw the noise and store the observation rows,
  * every step; `fuse` control steps per
