@@ -225,8 +225,17 @@ void drop_graph(qs_env* h) {
 long ws_wave(int n_sm) { return (long)n_sm * 8 * 32; }
 
 // The warp-specialised step wins while a class is latency-bound: up to about
-// one wave of its CTAs.
-bool use_ws(int W, int slots, int n_sm) { return W <= 32 && (long)slots * W <= ws_wave(n_sm); }
+// one wave of its CTAs. Swarms of 17..32 keep it only up to two CTAs per SM:
+// their dynamics warps' pair pass (31 partners a drone) is heavy in issue
+// slots, and once more CTAs share an SM the noise warps' work competes for
+// those slots instead of filling idle ones (measured on GB300 at K = 6,
+// warp-specialised vs one env per 32-thread CTA: 8,192 drones 16.99 vs 17.13
+// us, 16,384 18.77 vs 17.83, 32,768 25.04 vs 21.26; swarms of 16 stay level
+// or ahead up to 32,768).
+bool use_ws(int W, int slots, int n_sm) {
+    const long threads = (long)slots * W;
+    return W <= 32 && threads <= (W > 16 ? (long)n_sm * 64 : ws_wave(n_sm));
+}
 
 // Default launch shape of the general per-call kernel: 64 threads per CTA (or
 // W) for classes beyond a wave (small CTAs interleave their load, compute and
@@ -236,6 +245,7 @@ bool use_ws(int W, int slots, int n_sm) { return W <= 32 && (long)slots * W <= w
 int default_block(int W, int slots, int n_sm) {
     const long threads = (long)slots * W;
     if (threads > ws_wave(n_sm)) return std::max(64, W);
+    if (W >= 32) return W;  // one env per CTA (32-wide: 21.3 vs 22.7 us for 64-thread CTAs at 32,768 drones)
     int b = 256;
     while (b > 32 && b > W && threads / b < 2 * n_sm) b >>= 1;
     return std::max(b, std::max(W, 32));
