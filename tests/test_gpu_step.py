@@ -428,6 +428,19 @@ def test_ws_rollout_default_only_within_one_wave():
         env.close()
 
 
+def test_per_call_default_shapes():
+    """Per-call defaults: the warp-specialised step for narrow swarms while
+    latency-bound; swarms of 17..32 only up to two CTAs per SM (here 4,096
+    drones), beyond that one env per 32-thread CTA (32,768 drones); swarms of
+    16 keep it at 32,768 drones."""
+    from paper_2306_09537_gb300 import qs
+    from paper_2306_09537_gb300.env import QuadSwarmEnv
+    for E, N, expect in ((128, 32, qs.QS_BLOCK_WARP_SPECIALISED), (1024, 32, 32), (2048, 16, qs.QS_BLOCK_WARP_SPECIALISED)):
+        env = QuadSwarmEnv(E, N, 6, ("floor", "walls", "collisions"), seed=1, device=DEV)
+        assert qs.qs_get_block(env.h, N) == expect, (E, N)
+        env.close()
+
+
 def test_ws_rollout_needs_narrow_classes():
     from paper_2306_09537_gb300 import qs
     env, _ = pair([4, 65], 2, FULL, seed=1)
