@@ -86,11 +86,14 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The loaded oracle library. ``QS_ORACLE_LIB`` names another build of the
+    same source to load instead: the mutation test points it at copies with a
+    planted mistake, to check that the pins reject each one."""
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_LIB_PATH)
+            path = os.environ.get("QS_ORACLE_LIB") or build()
+            L = C.CDLL(path)
             P = C.POINTER
             L.or_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
             L.or_philox4x32_10_n.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32), C.c_size_t]

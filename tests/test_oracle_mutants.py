@@ -1,0 +1,110 @@
+"""The oracle's pins reject plausible mistakes: each case below plants one
+mistake in a copy of the oracle's source (a wrong sign, a dropped term, a
+transposed operand, a wrong index), builds it, and runs the pin suite
+(tests/test_oracle_pins.py) against that build; some pin must fail. A mistake
+no pin catches would pass straight into the GPU parity bars."""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+OUT = os.path.join(ORACLE, "_build", "mutants")
+
+# name: [(text in qs_oracle.c, replacement)], each text present exactly once
+MUTANTS = {
+    # S3 wrench
+    "yaw spin signs flipped": [("const double spin[4] = {-1.0, 1.0, -1.0, 1.0};",
+                                "const double spin[4] = {1.0, -1.0, 1.0, -1.0};")],
+    "pitch torque sign": [("tau[1] += -px * f[r];", "tau[1] += px * f[r];")],
+    "roll torque sign": [("tau[0] += py * f[r];", "tau[0] += -py * f[r];")],
+    # S1 motor lag
+    "lag coefficient exp(-dt/tau) instead of 1 - exp(-dt/tau)": [
+        ("const double alpha_lag = 1.0 - exp(-dt / tau_m);", "const double alpha_lag = exp(-dt / tau_m);")],
+    # S4 linear dynamics
+    "gravity sign": [("F[2] / m - g}", "F[2] / m + g}")],
+    "thrust along a row of R instead of its third column": [
+        ("double F[3] = {R[2] * T, R[5] * T, R[8] * T};", "double F[3] = {R[6] * T, R[7] * T, R[8] * T};")],
+    # S5 angular dynamics
+    "gyroscopic term dropped": [
+        ("double wdot[3] = {(tau[0] - gyro[0]) / ixx, (tau[1] - gyro[1]) / iyy, (tau[2] - gyro[2]) / izz};",
+         "double wdot[3] = {tau[0] / ixx, tau[1] / iyy, tau[2] / izz};")],
+    "gyroscopic term sign": [("(tau[0] - gyro[0]) / ixx, (tau[1] - gyro[1]) / iyy, (tau[2] - gyro[2]) / izz",
+                              "(tau[0] + gyro[0]) / ixx, (tau[1] + gyro[1]) / iyy, (tau[2] + gyro[2]) / izz")],
+    # S6 integration
+    "explicit instead of semi-implicit Euler": [
+        ("for (int k = 0; k < 3; ++k) x[k] += v[k] * dt;",
+         "for (int k = 0; k < 3; ++k) x[k] += (v[k] - acc[k] * dt) * dt;")],
+    "rotation advanced the wrong way": [("M[3 * i + 0] = r0 + dt *", "M[3 * i + 0] = r0 - dt *"),
+                                        ("M[3 * i + 1] = r1 + dt *", "M[3 * i + 1] = r1 - dt *"),
+                                        ("M[3 * i + 2] = r2 + dt *", "M[3 * i + 2] = r2 - dt *")],
+    # S7, S8 contacts
+    "floor hit heading sign": [("if (hyp >= 1e-6) { cs = R[0] / hyp; sn = R[3] / hyp; }",
+                                "if (hyp >= 1e-6) { cs = R[0] / hyp; sn = -R[3] / hyp; }")],
+    "wall reflects instead of removing the normal velocity": [
+        ("if (v[k] > 0.0) { v[k] = 0.0; hit_wall = 1; }", "if (v[k] > 0.0) { v[k] = -v[k]; hit_wall = 1; }")],
+    # S10 collision response
+    "collision response sign": [
+        ("(vj[0] - vi[0]) * n[0] + (vj[1] - vi[1]) * n[1] + (vj[2] - vi[2]) * n[2]",
+         "(vi[0] - vj[0]) * n[0] + (vi[1] - vj[1]) * n[1] + (vi[2] - vj[2]) * n[2]")],
+    # S11 neighbours
+    "neighbour ties to the higher index": [("return x->j < y->j ? -1 : (x->j > y->j ? 1 : 0);",
+                                            "return x->j > y->j ? -1 : (x->j < y->j ? 1 : 0);")],
+    # S12 observation
+    "goal-relative position sign": [("o[k] = x[k] - goal[k] + ex[k];", "o[k] = goal[k] - x[k] + ex[k];")],
+    "neighbour-relative position sign": [("on[q] = sj[OR_S_X + q] - x[q];", "on[q] = x[q] - sj[OR_S_X + q];")],
+    "rotation observed transposed": [("for (int k = 0; k < 9; ++k) o[6 + k] = R[k];",
+                                      "for (int k = 0; k < 9; ++k) o[6 + k] = R[3 * (k % 3) + k / 3];")],
+    "position noise U(0, s) instead of U(-s, s)": [("ex[0] = (2.0 * u0[0] - 1.0) * c->obs_sigma_x;",
+                                                    "ex[0] = u0[0] * c->obs_sigma_x;")],
+    # S13 reward
+    "spin norm missing a component": [("r += W[OR_W_SPIN] * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);",
+                                       "r += W[OR_W_SPIN] * sqrt(w[0] * w[0] + w[1] * w[1]);")],
+    "orientation term on the wrong entry of R": [("r += W[OR_W_ORI] * R[8];", "r += W[OR_W_ORI] * R[4];")],
+    "command change with swapped rotors": [("fh[0] - fprev[0], fh[1] - fprev[1]", "fh[0] - fprev[1], fh[1] - fprev[0]")],
+    "proximity term on the squared distance": [("near += fmax(1.0 - dd / alpha_prox, 0.0);",
+                                                "near += fmax(1.0 - dd * dd / alpha_prox, 0.0);")],
+    # S0 randomisation and the random streams
+    "randomisation range halved": [("c->dr_lo + (c->dr_hi - c->dr_lo) * u[k]",
+                                    "c->dr_lo + (c->dr_hi - c->dr_lo) * 0.5 * u[k]")],
+    "uniform from the wrong bits": [("((double)(r >> 9) + 0.5) * (1.0 / 8388608.0)",
+                                     "((double)(r >> 8) + 0.5) * (1.0 / 16777216.0)")],
+    "Box-Muller angle pi u instead of 2 pi u": [("double ang = 2.0 * M_PI * u1;", "double ang = M_PI * u1;")],
+}
+
+
+def _build(name, edits, src):
+    for old, new in edits:
+        assert src.count(old) == 1, (name, old)
+        src = src.replace(old, new)
+    stem = "".join(ch if ch.isalnum() else "_" for ch in name)
+    cpath, so = os.path.join(OUT, stem + ".c"), os.path.join(OUT, stem + ".so")
+    with open(cpath, "w") as f:
+        f.write(src)
+    subprocess.run(["gcc", "-std=c11", "-D_GNU_SOURCE", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+                    "-fno-fast-math", "-pthread", "-I", ORACLE, "-o", so, cpath, "-lm"], check=True)
+    return so
+
+
+def _caught(name, edits, src):
+    so = _build(name, edits, src)
+    env = dict(os.environ, QS_ORACLE_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x", "-q",
+                        "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True)
+    return r.returncode != 0
+
+
+def test_pins_reject_every_planted_mistake():
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc is needed to build the mutated oracles")
+    os.makedirs(OUT, exist_ok=True)
+    with open(os.path.join(ORACLE, "qs_oracle.c")) as f:
+        src = f.read()
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        futs = {name: ex.submit(_caught, name, edits, src) for name, edits in MUTANTS.items()}
+        survivors = [name for name, fut in futs.items() if not fut.result()]
+    assert not survivors, f"mistakes no pin catches: {survivors}"

@@ -165,6 +165,50 @@ def test_p3_pure_yaw_response():
     assert abs(wz) > 1.0  # the test exercised a real rotation
 
 
+def ry(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+@pytest.mark.parametrize("axis", ["roll", "pitch"])
+def test_p3_roll_and_pitch_from_the_rotor_layout(axis):
+    """Sec. III-A: the thrust torque is the sum of p_r x (0, 0, f_r) over rotors
+    at p_r = l (cos t_r, sin t_r, 0), t_r = 45 + 90 r degrees (X layout). Commands
+    (a, a, b, b) give a pure roll torque, (a, b, b, a) a pure pitch torque (the
+    other thrust torque and the yaw torque cancel); with the motors at their lag
+    fixed point the torque is constant, the rotation stays about one principal
+    axis (no gyroscopic term), so after n substeps w = n dt tau / I exactly and
+    the attitude is the rotation about that axis by the sum of atan(dt w)."""
+    c, o = make(flags=0)
+    a, b = 0.55, 0.45
+    f_hat = np.array([a, a, b, b]) if axis == "roll" else np.array([a, b, b, a])
+    st = base_state()
+    st[0, 18:22] = np.sqrt(f_hat)   # u_f = sqrt(f^): the lag leaves it unchanged
+    st[0, 26:30] = f_hat
+    o.set_state(st, nominal(c)[None], np.zeros((1, 3)), np.zeros(1, np.int32), 0)
+    fmax = 0.25 * c.mass * c.gravity * c.t2w
+    f = fmax * f_hat
+    tau = np.zeros(3)
+    for r in range(4):
+        t = math.radians(45.0 + 90.0 * r)
+        tau += np.cross(c.arm * np.array([math.cos(t), math.sin(t), 0.0]), np.array([0.0, 0.0, f[r]]))
+    k, inertia, rot = (0, c.ixx, rx) if axis == "roll" else (1, c.iyy, ry)
+    assert abs(tau[1 - k]) < 1e-18 and tau[2] == 0.0 and abs(tau[k]) > 1e-4
+    # rotors at +y (roll) or +x (pitch) push harder: roll rate positive, pitch rate negative
+    assert (tau[k] > 0) == (axis == "roll")
+    dt, w, ang = c.dt, 0.0, 0.0
+    for t in range(1, 11):
+        o.step(f_hat[None])
+        for sub in range(2):
+            w += dt * tau[k] / inertia
+            ang += math.atan(dt * w)
+        s = o.get_state()["state"][0]
+        assert abs(s[15 + k] - w) < 1e-9 * max(1.0, abs(w)), t
+        assert abs(s[15 + (1 - k)]) < 1e-12 and abs(s[17]) < 1e-12
+        assert np.abs(s[6:15].reshape(3, 3) - rot(ang)).max() < 1e-9, t
+    assert abs(w) > 1.0
+
+
 # --------------------------------------------------------------------------- P4 motor lag
 def test_p4_motor_lag_settling():
     """Sec. III-A: first-order lag whose 2% settling time is tau_m ln 50."""
@@ -556,6 +600,55 @@ def test_reward_special_case_identity_pose():
     o.set_state(st, nominal(c)[None], np.array([[1.0, 2.0, 3.0]]), np.zeros(1, np.int32), 0)
     _, r, _ = o.step(np.full((1, 4), 0.5))
     assert abs(r[0] - (0.7 + 0.13 + 0.19 + 0.23)) < 1e-9
+
+
+@pytest.mark.parametrize("term", ["pos", "vel", "ori", "spin", "act", "dact", "rot", "yaw"])
+def test_reward_terms_one_at_a_time(term):
+    """Sec. III-E, one weight at a time on a generic state: each state term is
+    its weight times the quantity the paper names (unsquared norms; the
+    command terms on f^ and f^ - f^_prev), evaluated on the state after the
+    step and checked against numpy's norms of that state."""
+    weights = {n: 0.0 for n in O.W_NAMES}
+    weights[term] = -1.7
+    c, o = make(flags=0, weights=weights)
+    st = base_state(x=(1.0, -2.0, 4.0))
+    st[0, 3:6] = (0.3, -0.8, 0.5)
+    st[0, 6:15] = (rz(0.4) @ rx(0.3)).ravel()
+    st[0, 15:18] = (1.5, -2.0, 3.0)
+    f_prev = np.array([0.4, 0.9, 0.5, 0.7])
+    st[0, 26:30] = f_prev
+    goal = np.array([[0.5, 0.5, 3.0]])
+    o.set_state(st, nominal(c)[None], goal, np.zeros(1, np.int32), 0)
+    f_hat = np.array([0.1, 0.5, 0.5, 0.7])
+    _, r, _ = o.step(f_hat[None])
+    s = o.get_state()["state"][0]
+    x, v, R, w = s[0:3], s[3:6], s[6:15].reshape(3, 3), s[15:18]
+    q = {"pos": np.linalg.norm(x - goal[0]), "vel": np.linalg.norm(v), "ori": R[2, 2], "spin": np.linalg.norm(w),
+         "act": np.linalg.norm(f_hat), "dact": np.linalg.norm(f_hat - f_prev), "rot": 0.5 * (np.trace(R) - 1.0),
+         "yaw": R[0, 0]}[term]
+    assert np.abs(s[6:15]).min() > 1e-3 or term not in ("ori", "rot", "yaw")
+    assert abs(r[0] - (-1.7) * q) < 1e-12 * max(1.0, abs(q)), (term, r[0], q)
+
+
+def test_reward_proximity_term():
+    """Sec. III-E proximity term: each neighbour within alpha_prox = 4 l adds
+    max(1 - d / alpha_prox, 0) (linear in the distance d). Two identical drones
+    0.1 m apart at hover keep their separation over the step, so each one's
+    reward is w_near (1 - 0.1 / alpha_prox); at 0.3 m (beyond alpha_prox) it is 0."""
+    weights = {n: 0.0 for n in O.W_NAMES}
+    weights["near"] = -2.0
+    for sep in (0.1, 0.3):
+        c, o = make(n_envs=1, sizes=[2], K=1, flags=0, weights=weights)
+        st = base_state(n=2)
+        st[1, 0] = sep
+        o.set_state(st, nominal(c)[None], np.array([[0.0, 0.0, 5.0]]), np.zeros(1, np.int32), 0)
+        _, r, _ = o.step(np.full((2, 4), 0.5))
+        s = o.get_state()["state"]
+        assert abs((s[1, 0] - s[0, 0]) - sep) < 1e-12
+        alpha_prox = 4.0 * c.arm
+        expect = -2.0 * max(1.0 - sep / alpha_prox, 0.0)
+        assert np.abs(r - expect).max() < 1e-12, (sep, r, expect)
+    assert 0.1 < 4.0 * c.arm < 0.3
 
 
 def test_done_and_auto_reset():
