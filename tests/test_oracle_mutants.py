@@ -74,6 +74,33 @@ MUTANTS = {
     "uniform from the wrong bits": [("((double)(r >> 9) + 0.5) * (1.0 / 8388608.0)",
                                      "((double)(r >> 8) + 0.5) * (1.0 / 16777216.0)")],
     "Box-Muller angle pi u instead of 2 pi u": [("double ang = 2.0 * M_PI * u1;", "double ang = M_PI * u1;")],
+    "initial velocity range [0, 2] instead of [-1, 1]": [("s[OR_S_V + 1] = -1.0 + 2.0 * u[4];",
+                                                          "s[OR_S_V + 1] = 2.0 * u[4];")],
+    "initial rotation from a wrong quaternion formula": [("R[1] = 2.0 * (qx * qy - qz * qw);",
+                                                          "R[1] = 2.0 * (qx * qy + qz * qw);")],
+    # S1, S2 motors
+    "thrust linear in the rotor speed": [("f[r] = fmax * uf[r] * uf[r] + eps[r];", "f[r] = fmax * uf[r] + eps[r];")],
+    "motor noise without its AR(1) memory": [("eps[r] = c->alpha_nd * eps[r] + alpha_ns * n[r];",
+                                              "eps[r] = alpha_ns * n[r];")],
+    # S6, S7, S8 again
+    "no re-orthonormalisation": [("double nx = 0.5 * (x[k] + it[k]);", "double nx = x[k];")],
+    "friction on m g instead of m g - F_z": [("double ffric = c->mu * (m * g - F[2]);",
+                                              "double ffric = c->mu * m * g;")],
+    "ceiling reflects": [("if (v[2] > 0.0) { v[2] = 0.0; hit_ceil = 1; }",
+                          "if (v[2] > 0.0) { v[2] = -v[2]; hit_ceil = 1; }")],
+    "wall body-rate perturbation dropped": [("w[k] = w[k] + c->coll_sigma_w * n[3 + k];", "w[k] = w[k];")],
+    "smooth floor pulls down": [("acc[2] += kc * softplus_b(-x[2], beta);", "acc[2] -= kc * softplus_b(-x[2], beta);")],
+    # S9, S10 again
+    "collision radius l instead of 2 l": [("volatile float r = li + lj;", "volatile float r = li;")],
+    "collision body-rate perturbation dropped": [("wi[k] = wi[k] + c->coll_sigma_w * nn[3 + k];", "wi[k] = wi[k];")],
+    # S10b downwash
+    "downwash pushes up": [("az[i] -= c->dw_k1 * (c->dw_k2 * dz + c->dw_b1);",
+                            "az[i] += c->dw_k1 * (c->dw_k2 * dz + c->dw_b1);")],
+    "downwash from the drone below": [("if (rxy2 < r * r && dz > 0.0 && dz < c->dw_height) {",
+                                       "if (rxy2 < r * r && dz < 0.0 && -dz < c->dw_height) {")],
+    # S13 done
+    "episode ends a step late": [("int is_done = h->ep_t[e] >= c->episode_steps;",
+                                  "int is_done = h->ep_t[e] > c->episode_steps;")],
 }
 
 

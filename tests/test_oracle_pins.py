@@ -343,6 +343,52 @@ def test_p8_head_on_collision_swaps_normal_velocity():
             assert np.abs((va[i] - (va[i] @ nn) * nn) - (vb[i] - (vb[i] @ nn) * nn)).max() < 1e-12
 
 
+def _gaussian(x, sigma):
+    """Sample x of N(0, sigma^2): mean, variance and kurtosis within 4 standard
+    errors."""
+    n = x.size
+    m, v = x.mean(), x.var()
+    kurt = ((x - m) ** 4).mean() / v ** 2
+    return abs(m) < 4 * sigma / math.sqrt(n) and abs(v / sigma ** 2 - 1) < 4 * math.sqrt(2 / n) \
+        and abs(kurt - 3) < 4 * math.sqrt(24 / n)
+
+
+@pytest.mark.parametrize("contact", ["quad", "wall"])
+def test_contact_perturbations_are_gaussian(contact):
+    """Sec. III-B: a responding drone gets v <- alpha (v + v~ + eps_v) and
+    w <- w + eps_w with Gaussian eps. With alpha = 1 and the contact the last
+    event of the step (the pair response follows both substeps; the wall is
+    crossed in the second substep), the difference to the same step without
+    perturbation is eps itself: each component N(0, sigma^2), uncorrelated."""
+    n_env, sv, sw = 4000, 0.2, 0.5
+    runs = []
+    for sig_v, sig_w in ((sv, sw), (0.0, 0.0)):
+        if contact == "quad":
+            c, o = make(n_envs=n_env, sizes=[2] * n_env, flags=O.F_COLLISIONS, alpha_c=1.0, coll_sigma_v=sig_v,
+                        coll_sigma_w=sig_w)
+            st = base_state(2 * n_env)
+            st[1::2, 0] = 0.05
+            st[0::2, 3], st[1::2, 3] = 1.0, -1.0
+            goals = np.zeros((n_env, 3))
+        else:
+            c, o = make(n_envs=n_env, flags=O.F_WALLS, alpha_c=1.0, coll_sigma_v=sig_v, coll_sigma_w=sig_w)
+            st = base_state(n_env, x=(5.0 - 1.5 * c.dt, 0.0, 5.0))
+            st[:, 3:6] = (1.0, 0.5, 0.0)
+            goals = np.zeros((n_env, 3))
+        o.set_state(st, np.tile(nominal(c), (n_env, 1)), goals, np.zeros(n_env, np.int32), 0)
+        o.step(np.full((st.shape[0], 4), 0.5))
+        ev, _, _ = o.get_events()
+        assert (ev & (O.EV_HIT_QUAD if contact == "quad" else O.EV_HIT_WALL)).all()
+        runs.append(o.get_state()["state"])
+    dv = runs[0][:, 3:6] - runs[1][:, 3:6]
+    dw = runs[0][:, 15:18] - runs[1][:, 15:18]
+    for k in range(3):
+        assert _gaussian(dv[:, k], sv), ("v", k, dv[:, k].mean(), dv[:, k].std())
+        assert _gaussian(dw[:, k], sw), ("w", k, dw[:, k].mean(), dw[:, k].std())
+    corr = np.corrcoef(np.hstack([dv, dw]).T)
+    assert np.abs(corr - np.eye(6)).max() < 4 / math.sqrt(dv.shape[0])
+
+
 def test_separating_pair_only_flags():
     """Overlapping but separating drones are flagged and keep their velocities."""
     c, o = make(n_envs=1, sizes=[2], flags=O.F_COLLISIONS, alpha_c=0.5)
