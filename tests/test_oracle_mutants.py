@@ -101,6 +101,25 @@ MUTANTS = {
     # S13 done
     "episode ends a step late": [("int is_done = h->ep_t[e] >= c->episode_steps;",
                                   "int is_done = h->ep_t[e] > c->episode_steps;")],
+    "body rates unbounded above": [("if (w[k] > c->omega_max) w[k] = c->omega_max;", "if (0) w[k] = c->omega_max;")],
+    "velocity noise U(0, s) instead of U(-s, s)": [("evv[1] = (2.0 * u1[0] - 1.0) * c->obs_sigma_v;",
+                                                    "evv[1] = u1[0] * c->obs_sigma_v;")],
+    "body-rate noise missing on one axis": [
+        ("ew[0] = n0 * c->obs_sigma_w; ew[1] = n1 * c->obs_sigma_w; ew[2] = n2 * c->obs_sigma_w;",
+         "ew[0] = n0 * c->obs_sigma_w; ew[1] = n1 * c->obs_sigma_w; ew[2] = 0.0;")],
+    # Sec. III-D scenario goals
+    "circle radius s n / pi": [("double r = fmin(s * n / (2.0 * M_PI), rmax), th = 2.0 * M_PI * k / n;",
+                                "double r = fmin(s * n / M_PI, rmax), th = 2.0 * M_PI * k / n;")],
+    "grid not centred": [("out[0] = s * ((k % m) - 0.5 * (m - 1));\n        out[1] = s * ((k / m) - 0.5 * (rows - 1));",
+                          "out[0] = s * (k % m);\n        out[1] = s * ((k / m) - 0.5 * (rows - 1));")],
+    "sphere heights off by half a step": [("double z = 1.0 - (2.0 * k + 1.0) / n, rho = sqrt(1.0 - z * z);",
+                                           "double z = 1.0 - (2.0 * k) / n, rho = sqrt(1.0 - z * z);")],
+    "cylinder rings not centred": [("out[2] = s * ((k / m) - 0.5 * (used - 1));", "out[2] = s * (k / m);")],
+    "cube layers twice as far apart": [("out[2] = s * ((k / (m * m)) - 0.5 * (layers - 1));",
+                                        "out[2] = 2.0 * s * ((k / (m * m)) - 0.5 * (layers - 1));")],
+    "golden angle replaced by its complement": [
+        ("return (uint32_t)floor(4294967296.0 * (3.0 - sqrt(5.0)) / 2.0);",
+         "return (uint32_t)floor(4294967296.0 * (sqrt(5.0) - 1.0) / 4.0);")],
 }
 
 
