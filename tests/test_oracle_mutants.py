@@ -117,6 +117,23 @@ MUTANTS = {
     "cylinder rings not centred": [("out[2] = s * ((k / m) - 0.5 * (used - 1));", "out[2] = s * (k / m);")],
     "cube layers twice as far apart": [("out[2] = s * ((k / (m * m)) - 0.5 * (layers - 1));",
                                         "out[2] = 2.0 * s * ((k / (m * m)) - 0.5 * (layers - 1));")],
+    # smooth contacts and the loss of the differentiable rollout
+    "softplus without the 1/beta": [("return (fmax(z, 0.0) + log1p(exp(-fabs(z)))) / beta;",
+                                     "return (fmax(z, 0.0) + log1p(exp(-fabs(z))));")],
+    "smooth pair pulls together": [
+        ("out[0] += mag * dx / dist; out[1] += mag * dy / dist; out[2] += mag * dz / dist;",
+         "out[0] -= mag * dx / dist; out[1] -= mag * dy / dist; out[2] -= mag * dz / dist;")],
+    "smooth pair radius l instead of 2 l": [
+        ("double mag = kc * softplus_b(2.0 * p[OR_P_ARM] - dist, c->smooth_beta);",
+         "double mag = kc * softplus_b(p[OR_P_ARM] - dist, c->smooth_beta);")],
+    "smooth ceiling pulls out": [("acc[2] -= kc * softplus_b(x[2] - c->room_h, beta);",
+                                  "acc[2] += kc * softplus_b(x[2] - c->room_h, beta);")],
+    "smooth wall pulls out": [("acc[0] -= kc * softplus_b(x[0] - c->room_hx, beta);",
+                               "acc[0] += kc * softplus_b(x[0] - c->room_hx, beta);")],
+    "loss command weight 1e-2": [("for (int r = 0; r < 4; ++r) l += 1e-3 * fh[r] * fh[r];",
+                                  "for (int r = 0; r < 4; ++r) l += 1e-2 * fh[r] * fh[r];")],
+    "loss on unsquared distances": [("for (int k = 0; k < 3; ++k) l += (x[k] - goal[k]) * (x[k] - goal[k]);",
+                                     "for (int k = 0; k < 3; ++k) l += fabs(x[k] - goal[k]);")],
     "golden angle replaced by its complement": [
         ("return (uint32_t)floor(4294967296.0 * (3.0 - sqrt(5.0)) / 2.0);",
          "return (uint32_t)floor(4294967296.0 * (sqrt(5.0) - 1.0) / 4.0);")],

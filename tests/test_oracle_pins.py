@@ -740,6 +740,81 @@ def test_smooth_pair_forces_cancel():
     assert np.abs(s[:, 3:6] - st[:, 3:6]).max() > 0.1  # the penalty acted
 
 
+def _sp(u, beta):
+    """softplus_beta(u) = log(1 + exp(beta u)) / beta"""
+    return np.logaddexp(0.0, beta * u) / beta
+
+
+@pytest.mark.parametrize("face", ["ceiling", "+x", "-x", "+y", "-y"])
+def test_smooth_boundaries_push_inward(face):
+    """Smooth contacts (the differentiable form): a boundary pushes with
+    k_c sp_beta(u) / m = smooth_kc g sp_beta(u) along its inward normal, u the
+    penetration, in every substep. A hovering drone 2 mm past the face: after
+    the control step its outward velocity is -dt k (sp(u0) + sp(u1)) with u1
+    the penetration after the first (semi-implicit) substep; the other
+    components stay 0."""
+    c, o = make(flags=O.F_SMOOTH)
+    H, hx, hy = c.room_h, c.room_hx, c.room_hy
+    axis, sign, lim = {"ceiling": (2, 1, H), "+x": (0, 1, hx), "-x": (0, -1, hx), "+y": (1, 1, hy),
+                       "-y": (1, -1, hy)}[face]
+    x0 = np.array([0.0, 0.0, 5.0])
+    x0[axis] = sign * (lim + 0.002)
+    o.set_state(base_state(x=tuple(x0)), nominal(c)[None], np.zeros((1, 3)), np.zeros(1, np.int32), 0)
+    o.step(np.full((1, 4), 0.5))
+    s = o.get_state()["state"][0]
+    k, dt, beta = c.smooth_kc * c.gravity, c.dt, c.smooth_beta
+    u0 = 0.002
+    v1 = -dt * k * _sp(u0, beta)                 # outward component after substep 1
+    u1 = u0 + v1 * dt
+    v2 = v1 - dt * k * _sp(u1, beta)
+    v = s[3:6]
+    assert abs(sign * v[axis] - v2) < 1e-12 * max(1.0, abs(v2)), (v, v2)
+    assert np.abs(np.delete(v, axis)).max() < 1e-12
+    assert v2 < -0.005  # pushed inward
+
+
+def test_smooth_pair_repels_along_the_line_of_centres():
+    """Smooth pair term: k_c sp_beta(2 l - d) / m along n_ij = (x_i - x_j) / d,
+    evaluated in every substep on the positions at its start: two hovering
+    drones 1.5 l apart along a skew direction move apart along it, each by
+    dt k (sp(2 l - d0) + sp(2 l - d1)) with d1 = d0 + 2 v1 dt after the first
+    (semi-implicit) substep."""
+    c, o = make(n_envs=1, sizes=[2], flags=O.F_SMOOTH)
+    n = np.array([0.6, -0.48, 0.64])
+    n /= np.linalg.norm(n)
+    d = 1.5 * c.arm
+    st = base_state(2)
+    st[1, 0:3] = st[0, 0:3] + d * n
+    o.set_state(st, nominal(c)[None], np.zeros((1, 3)), np.zeros(1, np.int32), 0)
+    o.step(np.full((2, 4), 0.5))
+    v = o.get_state()["state"][:, 3:6]
+    k, dt = c.smooth_kc * c.gravity, c.dt
+    v1 = dt * k * _sp(2 * c.arm - d, c.smooth_beta)
+    d1 = d + 2 * v1 * dt
+    gain = v1 + dt * k * _sp(2 * c.arm - d1, c.smooth_beta)
+    assert np.abs(v[0] - (-gain * n)).max() < 1e-12 and np.abs(v[1] - gain * n).max() < 1e-12
+    assert gain > 0.01
+
+
+def test_diff_loss_definition():
+    """The differentiable rollout's loss: per drone and step ||x - g||^2 on the
+    position after the step plus 1e-3 ||f^||^2, summed over the steps."""
+    c, o = make(n_envs=1, sizes=[3], flags=O.F_SMOOTH)
+    st = base_state(3)
+    st[:, 0:3] = [[0.0, 0.0, 5.0], [1.0, -1.0, 4.0], [-2.0, 0.5, 6.0]]
+    goal = np.array([[0.5, 0.25, 5.5]])
+    o.set_state(st, nominal(c)[None], goal, np.zeros(1, np.int32), 0)
+    acts = [np.array([[0.2, 0.4, 0.6, 0.8]] * 3), np.array([[0.9, 0.1, 0.3, 0.7]] * 3)]
+    total = np.zeros(3)
+    expect = np.zeros(3)
+    for a in acts:
+        _, _, _, l = o.step(a, want_loss=True)
+        total += l
+        x = o.get_state()["state"][:, 0:3]
+        expect += ((x - goal[0]) ** 2).sum(1) + 1e-3 * (a ** 2).sum(1)
+    assert np.abs(total - expect).max() < 1e-12
+
+
 def test_body_rate_bound():
     """Body rates saturate at omega_max per axis (reading; the paper is silent)."""
     c, o = make(flags=0)
