@@ -134,6 +134,22 @@ MUTANTS = {
                                   "for (int r = 0; r < 4; ++r) l += 1e-2 * fh[r] * fh[r];")],
     "loss on unsquared distances": [("for (int k = 0; k < 3; ++k) l += (x[k] - goal[k]) * (x[k] - goal[k]);",
                                      "for (int k = 0; k < 3; ++k) l += fabs(x[k] - goal[k]);")],
+    "switch one step late": [("const int sw = tau >= (int)rec[OR_R_TSW];", "const int sw = tau > (int)rec[OR_R_TSW];")],
+    "shrink factor starting contracted": [
+        ("lam = 1.0 - (1.0 - c->se_min) * 0.5 * (1.0 - cos(2.0 * M_PI * tau / c->se_period));",
+         "lam = 1.0 - (1.0 - c->se_min) * 0.5 * (1.0 + cos(2.0 * M_PI * tau / c->se_period));")],
+    "dynamic goals keep the first centre": [
+        ("for (int k = 0; k < 3; ++k) g[k] = (sw ? c1[k] : c0[k]) + off[k];",
+         "for (int k = 0; k < 3; ++k) g[k] = c0[k] + off[k];")],
+    "swarm vs swarm groups never exchange": [("const double* cc = (grp ^ sw) ? c1 : c0;",
+                                              "const double* cc = grp ? c1 : c0;")],
+    "swap never swaps": [("const int slot = sw ? swap_slot(h, rec_seed(rec), i, N) : i;", "const int slot = i;")],
+    "Lissajous cosine": [("g[k] = c0[k] + c1[k] * sin(2.0 * M_PI * (p - floor(p)));",
+                          "g[k] = c0[k] + c1[k] * cos(2.0 * M_PI * (p - floor(p)));")],
+    "Lissajous time in substeps": [("const double T = c->substeps * c->dt;", "const double T = c->dt;")],
+    "Bezier control point off the Catmull-Rom tangent": [("double p1 = w0[k] + (w1[k] - wm[k]) / 6.0,",
+                                                          "double p1 = w0[k] + (w1[k] - wm[k]) / 3.0,")],
+    "downwash body-rate noise dropped": [("wi[k] += Tc * c->dw_sigma_w * nn[3 + k];", "wi[k] += 0.0;")],
     "golden angle replaced by its complement": [
         ("return (uint32_t)floor(4294967296.0 * (3.0 - sqrt(5.0)) / 2.0);",
          "return (uint32_t)floor(4294967296.0 * (sqrt(5.0) - 1.0) / 4.0);")],
