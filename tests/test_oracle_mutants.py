@@ -150,6 +150,12 @@ MUTANTS = {
     "Bezier control point off the Catmull-Rom tangent": [("double p1 = w0[k] + (w1[k] - wm[k]) / 6.0,",
                                                           "double p1 = w0[k] + (w1[k] - wm[k]) / 3.0,")],
     "downwash body-rate noise dropped": [("wi[k] += Tc * c->dw_sigma_w * nn[3 + k];", "wi[k] += 0.0;")],
+    "reset rotor speed at the hover command instead of its root": [("s[OR_S_UF + r] = sqrt(hov);",
+                                                                     "s[OR_S_UF + r] = hov;")],
+    "symmetric action map without the half": [("fh = 0.5 * (a + 1.0);", "fh = a + 1.0;")],
+    "commands clipped at 0.9": [("fh = a_in[r] < 0.0 ? 0.0 : (a_in[r] > 1.0 ? 1.0 : a_in[r]);",
+                                 "fh = a_in[r] < 0.0 ? 0.0 : (a_in[r] > 0.9 ? 0.9 : a_in[r]);")],
+    "lag toward the command instead of its root": [("double u = sqrt(fh);", "double u = fh;")],
     "golden angle replaced by its complement": [
         ("return (uint32_t)floor(4294967296.0 * (3.0 - sqrt(5.0)) / 2.0);",
          "return (uint32_t)floor(4294967296.0 * (sqrt(5.0) - 1.0) / 4.0);")],

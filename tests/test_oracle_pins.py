@@ -697,6 +697,26 @@ def test_reward_proximity_term():
     assert 0.1 < 4.0 * c.arm < 0.3
 
 
+def test_symmetric_action_map():
+    """Sec. III-A as printed: f^ = (clip(a, -1, 1) + 1) / 2. Commands (-1, 0, 1, 3)
+    give f^ = (0, 1/2, 1, 1), |f^| = 3/2 (read through the command-norm reward
+    term alone); commands 0 give the hover command 1/2 (t2w = 2), so a hovering
+    drone stays exactly where it is."""
+    weights = {n: 0.0 for n in O.W_NAMES}
+    weights["act"] = 1.0
+    c, o = make(flags=O.F_ACTION_SYMMETRIC, weights=weights)
+    o.set_state(base_state(), nominal(c)[None], np.zeros((1, 3)), np.zeros(1, np.int32), 0)
+    _, r, _ = o.step(np.array([[-1.0, 0.0, 1.0, 3.0]]))
+    assert abs(r[0] - 1.5) < 1e-15
+    c, o = make(flags=O.F_ACTION_SYMMETRIC)
+    st = base_state()
+    o.set_state(st, nominal(c)[None], np.zeros((1, 3)), np.zeros(1, np.int32), 0)
+    for _ in range(10):
+        o.step(np.zeros((1, 4)))
+    s = o.get_state()["state"][0]
+    assert np.abs(s[0:6] - st[0, 0:6]).max() < 1e-12 and np.abs(s[15:18]).max() < 1e-12
+
+
 def test_done_and_auto_reset():
     """Episodes end after episode_steps control steps (15 s at 100 Hz, Sec. IV)."""
     c, o = make(n_envs=2, flags=O.F_AUTO_RESET, episode_steps=5)
