@@ -256,7 +256,10 @@ qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, fl
  *  QS_ERR_ARG.
  *  idle_ms: when no step is posted for about this long the server retires
  *  (the drones return to the handle's memory and the launch ends);
- *  qs_serve_step then starts it again, with no effect on the results.
+ *  qs_serve_step then starts it again, with no effect on the results. At
+ *  most QS_SERVE_IDLE_MS_MAX (60 s): a resident launch holds every SM it
+ *  occupies while it waits, so a longer wait on a shared GPU is refused
+ *  (QS_ERR_ARG), as is idle_ms < 1.
  *
  * Requires every swarm to have at most 64 drones, a handle created on a
  * non-blocking stream (cudaStreamNonBlocking, as torch.cuda.Stream() makes;
@@ -274,6 +277,7 @@ qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, fl
  * state is reported as by qs_sync; a step that does not complete within 10 s
  * returns QS_ERR_TIMEOUT, after which qs_serve_step keeps waiting for that
  * same step and qs_serve_end stops the server once the step is done. */
+#define QS_SERVE_IDLE_MS_MAX 60000
 qs_status qs_serve_begin(qs_env* h, const float* actions_host, int32_t n_slots, float* obs_host, float* reward_host,
                          uint8_t* done_host, int32_t idle_ms);
 qs_status qs_serve_step(qs_env* h, int32_t slot);
@@ -343,14 +347,18 @@ qs_status qs_diff_backward(qs_env* h, int32_t T, int32_t ckpt_every, const float
  * owns the memory budget. It needs no workspace argument: the checkpoints and
  * recomputed substep states live in a fixed array of QS_DIFF_STATIC_BYTES
  * (64 MiB) inside the library's device image, held on every GPU that loads
- * the library until the process exits. The call allocates nothing; the
+ * the library until the process exits (a device reset or a released
+ * primary context ends the array's life with the context; the next call made
+ * outside a stream capture finds it again). The call allocates nothing; the
  * caller still passes every input and output: x0_dev [D][30], actions_dev
  * [T][D][4], dloss_dev [D] in; loss_dev [D], grad_actions_dev [T][D][4],
  * grad_x0_dev [D][30] out (same meaning as qs_diff_forward/_backward).
  * A rollout whose workspace (qs_diff_workspace_size) exceeds the array returns
- * QS_ERR_UNSUPPORTED and enqueues nothing. The first call on a device looks
- * the array's device address up (cudaGetSymbolAddress); make that first call
- * before any stream capture. All calls share the one array: calls whose work
+ * QS_ERR_UNSUPPORTED and enqueues nothing. Each call made while the
+ * handle's stream is not capturing looks the array's device address up
+ * (cudaGetSymbolAddress); a call made during a capture reuses the address of
+ * the last such call on that device, so make the first call on a device
+ * before any stream capture (otherwise QS_ERR_UNSUPPORTED). All calls share the one array: calls whose work
  * overlaps on the GPU (other streams, other handles) race and must be
  * serialised by the caller. The array keeps the last call's contents; no call
  * depends on them. */

@@ -24,6 +24,7 @@ _lib = None
 F_DR, F_MOTOR_NOISE, F_OBS_NOISE, F_COLLISIONS = 1 << 0, 1 << 1, 1 << 2, 1 << 3
 F_FLOOR, F_WALLS, F_AUTO_RESET, F_SMOOTH = 1 << 4, 1 << 5, 1 << 6, 1 << 7
 F_ACTION_SYMMETRIC, F_RECORD_KNN, F_DOWNWASH = 1 << 8, 1 << 9, 1 << 10
+F_ROUND32, F_ROUND32_SR = 1 << 11, 1 << 12  # conditioning instruments (see qs_oracle.h)
 EV_HIT_FLOOR, EV_ON_FLOOR, EV_HIT_WALL, EV_HIT_CEIL, EV_HIT_QUAD = 1, 2, 4, 8, 16
 NST, NPRM = 30, 7
 W_NAMES = ["pos", "vel", "ori", "spin", "act", "dact", "rot", "yaw", "hit_floor", "on_floor",
@@ -66,6 +67,7 @@ class OrConfig(C.Structure):
         ("form_spacing", C.c_double), ("form_rmax", C.c_double), ("scn_margin", C.c_double),
         ("se_min", C.c_double), ("se_period", C.c_double), ("liss_f", C.c_double), ("bez_seg", C.c_double),
         ("w", C.c_double * 14),
+        ("round_salt", C.c_uint64),
     ]
 
 

@@ -952,6 +952,33 @@ static void obs_row(or_env* h, int e, int i, const int32_t* nbr, int keff, uint3
     }
 }
 
+/* Conditioning instrument: one drone's state rounded to binary32 (see
+ * OR_F_ROUND32), to nearest or stochastically. The stochastic choice hashes
+ * (seed, salt, drone, tick, substep, component) with SplitMix64's finaliser. */
+static uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static void round_state_f32(const or_env* h, double* s, int d, uint32_t tick, int sub) {
+    const int sr = (h->cfg.flags & OR_F_ROUND32_SR) != 0;
+    for (int k = 0; k < OR_NST; ++k) {
+        float f = (float)s[k];
+        if (sr && (double)f != s[k]) {
+            float lo = (double)f < s[k] ? f : nextafterf(f, -INFINITY);
+            float hi = (double)f < s[k] ? nextafterf(f, INFINITY) : f;
+            double p = (s[k] - (double)lo) / ((double)hi - (double)lo);
+            uint64_t z = mix64(h->cfg.seed ^ mix64(h->cfg.round_salt) ^
+                               mix64(((uint64_t)(uint32_t)d << 32) ^ ((uint64_t)tick << 12) ^
+                                     ((uint64_t)sub << 6) ^ (uint64_t)k));
+            double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+            f = u < p ? hi : lo;
+        }
+        s[k] = (double)f;
+    }
+}
+
 static void step_env(or_env* h, int e, const double* actions, double* obs, double* rew, uint8_t* done,
                      double* loss) {
     const or_config* c = &h->cfg;
@@ -969,9 +996,11 @@ static void step_env(or_env* h, int e, const double* actions, double* obs, doubl
     /* substeps S1 .. S8 (drones of one env are coupled only through the smooth pair force) */
     for (int sub = 0; sub < c->substeps; ++sub) {
         if (smooth) for (int d = d0; d < d1; ++d) smooth_pair_acc(h, e, d, pacc + 3 * (d - d0));
-        for (int d = d0; d < d1; ++d)
+        for (int d = d0; d < d1; ++d) {
             substep_drone(h, e, d, sub, actions + 4 * (size_t)d, smooth ? pacc + 3 * (d - d0) : NULL,
                           fhat + 4 * (d - d0));
+            if (c->flags & OR_F_ROUND32) round_state_f32(h, h->st + (size_t)d * OR_NST, d, h->tick[e], sub);
+        }
     }
 
     /* binary32 positions and arm length for the canonical keys */

@@ -19,6 +19,14 @@
 #define OR_F_ACTION_SYMMETRIC (1u << 8)
 #define OR_F_RECORD_KNN       (1u << 9)
 #define OR_F_DOWNWASH         (1u << 10)
+/* Conditioning instruments (off in every run of the model itself): after each
+ * substep the drone state is rounded to binary32, to nearest (ROUND32) or
+ * stochastically (ROUND32 | ROUND32_SR: up or down with probability given by
+ * the distance to the two neighbours, from a hash of the seed, round_salt,
+ * drone, tick, substep and component). Comparing such a run with a plain one
+ * measures how much a trajectory amplifies perturbations of binary32 size. */
+#define OR_F_ROUND32          (1u << 11)
+#define OR_F_ROUND32_SR       (1u << 12)
 
 /* per-drone event bits of the last control step */
 #define OR_EV_HIT_FLOOR (1u << 0)
@@ -112,6 +120,7 @@ typedef struct {
      * Bezier segment */
     double form_spacing, form_rmax, scn_margin, se_min, se_period, liss_f, bez_seg;
     double w[OR_NW];
+    uint64_t round_salt; /* extra hash input of OR_F_ROUND32_SR */
 } or_config;
 
 typedef struct {

@@ -861,20 +861,30 @@ namespace {
 std::mutex g_static_mu;
 void* g_static_addr[256] = {};  // device address of g_diff_static, per device ordinal
 
-// Device address of the array on the current device (looked up once per
-// device; in host code g_diff_static names a host-side stand-in, not memory
-// the GPU can use).
+// Device address of the array on the current device. In host code
+// g_diff_static names a host-side stand-in, not memory the GPU can use, so
+// the address comes from cudaGetSymbolAddress. It is looked up again on every
+// call made while the handle's stream is not capturing (a device reset or a
+// released primary context moves the array); while capturing, the address
+// found by the last such call on this device is used, so the first call on a
+// device has to come before any capture.
 qs_status static_workspace(qs_env* h, void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(h, e, "qs_diff_grad_static: cudaGetDevice");
     if (dev < 0 || dev >= 256) return fail(h, QS_ERR_UNSUPPORTED, "qs_diff_grad_static: device ordinal >= 256");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(h->stream, &cs);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qs_diff_grad_static: cudaStreamIsCapturing");
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_diff_static);
         if (e != cudaSuccess || !p) return cuda_fail(h, e, "qs_diff_grad_static: cudaGetSymbolAddress");
         g_static_addr[dev] = p;
+    } else if (!g_static_addr[dev]) {
+        return fail(h, QS_ERR_UNSUPPORTED,
+                    "qs_diff_grad_static: the first call on a device must come before any stream capture");
     }
     *out = g_static_addr[dev];
     return QS_OK;
@@ -1027,7 +1037,8 @@ qs_status qs_serve_begin(qs_env* h, const float* actions_host, int32_t n_slots, 
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_serve_begin: NULL handle");
     if (h->serving) return fail(h, QS_ERR_ARG, "qs_serve_begin: the handle is already serving");
     if (!actions_host) return fail(h, QS_ERR_ARG, "qs_serve_begin: actions_host is NULL");
-    if (idle_ms < 1) return fail(h, QS_ERR_ARG, "qs_serve_begin: idle_ms must be >= 1");
+    if (idle_ms < 1 || idle_ms > QS_SERVE_IDLE_MS_MAX)
+        return fail(h, QS_ERR_ARG, "qs_serve_begin: idle_ms must be in [1, " + std::to_string(QS_SERVE_IDLE_MS_MAX) + "]");
     if (n_slots < 1) return fail(h, QS_ERR_ARG, "qs_serve_begin: n_slots must be >= 1");
     if (!h->ws_p || h->n_wtiles < 1)
         return fail(h, QS_ERR_UNSUPPORTED, "qs_serve_begin: every swarm must have at most 64 drones");

@@ -48,6 +48,7 @@ def scenario_mask(names) -> int:
         m |= 1 << SCENARIOS.index(n)
     return m
 QS_DIFF_STATIC_BYTES = 64 << 20
+QS_SERVE_IDLE_MS_MAX = 60000  # longest idle wait of the resident server
 
 
 class qs_params(C.Structure):

@@ -171,8 +171,10 @@ def test_serve_rejects_unsupported_handles_and_buffers():
         qs.qs_serve_begin(env.h, torch.zeros(env.D, 4, device=DEV))  # device memory
     with pytest.raises(qs.QSError):
         qs.qs_serve_begin(env.h, torch.zeros(env.D, 4))  # pageable host memory
-    with pytest.raises(qs.QSError):
-        qs.qs_serve_begin(env.h, torch.zeros(env.D, 4).pin_memory(), idle_ms=0)
+    for idle in (0, 60001):  # a resident launch may not wait longer than a minute on a shared GPU
+        with pytest.raises(qs.QSError) as ex:
+            qs.qs_serve_begin(env.h, torch.zeros(env.D, 4).pin_memory(), idle_ms=idle)
+        assert ex.value.status == qs.QS_ERR_ARG
     with pytest.raises(qs.QSError):
         qs.qs_serve_step(env.h)  # not serving
     qs.qs_serve_end(env.h)  # not serving: nothing to end

@@ -1,7 +1,8 @@
 """The oracle's pins reject plausible mistakes: each case below plants one
 mistake in a copy of the oracle's source (a wrong sign, a dropped term, a
 transposed operand, a wrong index), builds it, and runs the pin suite
-(tests/test_oracle_pins.py) against that build; some pin must fail. A mistake
+(tests/test_oracle_pins.py and the principal-axis pins of
+tests/test_oracle_conditioning.py) against that build; some pin must fail. A mistake
 no pin catches would pass straight into the GPU parity bars."""
 import concurrent.futures as cf
 import os
@@ -33,6 +34,8 @@ MUTANTS = {
     "gyroscopic term dropped": [
         ("double wdot[3] = {(tau[0] - gyro[0]) / ixx, (tau[1] - gyro[1]) / iyy, (tau[2] - gyro[2]) / izz};",
          "double wdot[3] = {tau[0] / ixx, tau[1] / iyy, tau[2] / izz};")],
+    "gyroscopic term with the x and y inertias swapped": [
+        ("double Iw[3] = {ixx * w[0], iyy * w[1], izz * w[2]};", "double Iw[3] = {iyy * w[0], ixx * w[1], izz * w[2]};")],
     "gyroscopic term sign": [("(tau[0] - gyro[0]) / ixx, (tau[1] - gyro[1]) / iyy, (tau[2] - gyro[2]) / izz",
                               "(tau[0] + gyro[0]) / ixx, (tau[1] + gyro[1]) / iyy, (tau[2] + gyro[2]) / izz")],
     # S6 integration
@@ -175,12 +178,25 @@ def _build(name, edits, src):
     return so
 
 
+PIN_TESTS = [os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+             os.path.join(ROOT, "tests", "test_oracle_conditioning.py") + "::test_intermediate_axis_instability_rate",
+             os.path.join(ROOT, "tests", "test_oracle_conditioning.py") + "::test_major_and_minor_axis_spin_is_stable"]
+
+
 def _caught(name, edits, src):
+    """True when a pin fails on the mutant (pytest exit code 1 with a failed
+    test); any other outcome of the run (a collection or usage error, a crash)
+    is a fault of the harness and raises."""
     so = _build(name, edits, src)
     env = dict(os.environ, QS_ORACLE_LIB=so)
-    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x", "-q",
-                        "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True)
-    return r.returncode != 0
+    r = subprocess.run([sys.executable, "-m", "pytest", *PIN_TESTS, "-x", "-q", "-p", "no:cacheprovider",
+                        "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True)
+    if r.returncode == 0:
+        return False
+    if r.returncode == 1 and " failed" in r.stdout:
+        return True
+    raise RuntimeError(f"mutant {name!r}: pytest exited {r.returncode} without a failed pin:\n"
+                       f"{r.stdout[-2000:]}\n{r.stderr[-2000:]}")
 
 
 def test_pins_reject_every_planted_mistake():
