@@ -31,16 +31,56 @@ sys.path.insert(0, ROOT)
 from paper_2306_09537_gb300 import workloads as W  # noqa: E402
 
 METRIC = "quadrotor-steps/sec on 1 GB300 (plain vs batched vs fwd+adjoint), % of roofline"
-# DRAM bytes (read + write) of one k_step_ws<false> launch of the plain 8192 x 1 step,
-# from an ncu capture of this command's headline kernel (L2 flushed before the
-# launch; the outputs stay in L2 during the launch, so the write count is 0).
-# Valid while k_step_ws<false> is unchanged.
-K_STEP_WS_DRAM_BYTES = 2075136 + 0
-K_STEP_WS_DRAM_SOURCE = "profiles/k_step_ws_plain_8192x1.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+# DRAM bytes (read + write) of one launch of the headline kernel on the plain
+# 8192 x 1 step, from an ncu capture of this command (L2 flushed before the
+# launch), and the SHA-256 of the library sources that capture was taken on:
+# once the kernel sources change, the figure no longer describes the kernel
+# and the roofline's traffic is reported as null until it is captured again.
+HEADLINE_DRAM = {"bytes_per_launch": 2075136, "sources_sha256": None,
+                 "source": "profiles/k_step_ws_plain_8192x1.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
 UNIT = "quadrotor-steps/s"
 WL = W.PLAIN
 BENCH_FEATURES = WL.features + ("auto_reset",)
 L2_FLUSH_BYTES = 256 << 20
+
+
+def library_sources_sha256() -> str:
+    """SHA-256 over the CUDA sources and the public header of the library."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2306_09537_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)) + ["../../include/qs.h"]:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def headline_traffic():
+    """(bytes per launch or None, note) for the roofline's traffic field."""
+    cur = library_sources_sha256()
+    if HEADLINE_DRAM["sources_sha256"] == cur:
+        return HEADLINE_DRAM["bytes_per_launch"], HEADLINE_DRAM["source"]
+    return None, f"kernel sources changed since the ncu capture ({HEADLINE_DRAM['source']}); sources sha256 {cur[:16]}"
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def peaks():
@@ -178,6 +218,17 @@ def oracle_run(steps, n_envs=None, threads=None, seed=None):
     return o.D * steps / dt, cores, f"{E} envs x {steps} control steps of the plain workload, binary64, {cores} threads"
 
 
+def cpu_baseline_legs():
+    """The oracle on all host cores (the whole 1000-step plain workload) and on
+    one core (its first 200 steps), about 10-20 s of CPU work together, with
+    the host's core count and CPU model."""
+    v, cores, sample = oracle_run(1000)
+    v1, _, sample1 = oracle_run(200, threads=1)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": sample1},
+            "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -190,7 +241,8 @@ def run_reference(args, world, rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WL.name, "n_envs": WL.n_envs, "swarm": 1, "k_neighbors": WL.k_neighbors,
                        "features": list(BENCH_FEATURES)},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -214,8 +266,16 @@ def run_gpu(args, world, rank, local):
         acts = torch.from_numpy(W.actions(seed, period, env.D)).to(dev)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
         n_classes = 1
-        for t in range(warm):
-            env.step(acts[t % period])
+        # warm-up: the timed loop itself (flush, step) for at least W steps and
+        # at least 0.5 s, so that clocks, caches of the host path and the GPU's
+        # front end are in their steady state when timing starts
+        t_warm, n_warm = time.perf_counter() + 0.5, 0
+        while n_warm < warm or time.perf_counter() < t_warm:
+            flush.zero_()
+            env.step(acts[n_warm % period])
+            n_warm += 1
+            if n_warm % 64 == 0:
+                stream.synchronize()
         stream.synchronize()
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -223,10 +283,16 @@ def run_gpu(args, world, rank, local):
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
             t_wall = time.perf_counter()
+            # a short device-side pause ahead of the first timed step lets the
+            # host enqueue the timed steps before the GPU reaches them: each
+            # event pair then times the GPU's step, never a GPU idling on the
+            # host's launch of the next call
+            if hasattr(torch.cuda, "_sleep"):
+                torch.cuda._sleep(4_000_000)
             for t in range(steps):
                 flush.zero_()
                 ev0[t].record(stream)
-                env.step(acts[(warm + t) % period])
+                env.step(acts[(n_warm + t) % period])
                 ev1[t].record(stream)
             stream.synchronize()
             t_wall = time.perf_counter() - t_wall
@@ -290,7 +356,8 @@ def run_gpu(args, world, rank, local):
     ab = algorithmic_bytes(D, E, od)
     ach_gbs = ab / launch_s / 1e9
     ops = OPS_PER_QUAD_STEP_N1 * D
-    alu_peak = 152 * 128 * sm_max * 1e6 / 1e9  # G lane-ops/s
+    n_sm = torch.cuda.get_device_properties(torch.device("cuda", local)).multi_processor_count
+    alu_peak = n_sm * 128 * sm_max * 1e6 / 1e9  # G lane-ops/s
     ach_gops = ops / launch_s / 1e9
     t_hbm, t_alu = ab / (hbm * 1e9), ops / (alu_peak * 1e9)
     if t_hbm >= t_alu:
@@ -298,13 +365,16 @@ def run_gpu(args, world, rank, local):
                 "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs" if src == "measured" else "fallback 6.8 TB/s"}
     else:
         roof = {"bound": "alu", "achieved": ach_gops, "peak": alu_peak, "unit": "Gop/s", "frac": ach_gops / alu_peak,
-                "peak_source": "152 SMs x 128 FP32/INT32 lanes x max SM clock"}
-    roof.update({"kernel": "qsk::k_step_ws<false>", "traffic": K_STEP_WS_DRAM_BYTES, "traffic_source": K_STEP_WS_DRAM_SOURCE,
+                "peak_source": f"{n_sm} SMs x 128 FP32/INT32 lanes x max SM clock"}
+    traffic, traffic_src = headline_traffic()
+    roof.update({"kernel": "qsk::k_step_ws<false>", "traffic": traffic, "traffic_source": traffic_src,
                  "algorithmic_bytes_per_launch": ab,
                  "algorithmic_ops_per_launch": ops,
                  "alt": {"hbm_frac": ach_gbs / hbm, "alu_frac": ach_gops / alu_peak}})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warm,
-            "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": total_ms / steps, "ms_per_step_median": float(np.median(per)),
+            "ms_per_step_p90": float(np.quantile(per, 0.9)), "warmup_steps_run": n_warm,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": WL.name, "n_envs": WL.n_envs, "swarm": 1, "k_neighbors": WL.k_neighbors,
                        "features": list(BENCH_FEATURES), "form": "per-call qs_step, state in HBM",
@@ -349,7 +419,7 @@ def run_forms(dev, stream, seed):
     from paper_2306_09537_gb300 import autotune, qs
     from paper_2306_09537_gb300.env import QuadSwarmEnv
     hbm, sm_max, _ = peaks()
-    alu_peak = 152 * 128 * sm_max * 1e6
+    alu_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * sm_max * 1e6
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     forms = {}
     with torch.cuda.stream(stream):
@@ -634,8 +704,7 @@ def main():
                                      "fwd_adjoint", "fwd_adjoint_discrete")}
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:  # the oracle's CPU baseline: rank 0 at N = 1 only
-            v, cores, sample = oracle_run(200)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+            line["cpu_baseline"] = cpu_baseline_legs()
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
