@@ -129,6 +129,14 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_samples(self, n, timeout=5.0):
+        """Blocks until n more samples have arrived (or the timeout)."""
+        if not self.proc:
+            return
+        target, t_end = len(self.lines) + n, time.perf_counter() + timeout
+        while len(self.lines) < target and time.perf_counter() < t_end:
+            time.sleep(0.01)
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -266,22 +274,26 @@ def run_gpu(args, world, rank, local):
         acts = torch.from_numpy(W.actions(seed, period, env.D)).to(dev)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
         n_classes = 1
-        # warm-up: the timed loop itself (flush, step) for at least W steps and
-        # at least 0.5 s, so that clocks, caches of the host path and the GPU's
-        # front end are in their steady state when timing starts
-        t_warm, n_warm = time.perf_counter() + 0.5, 0
-        while n_warm < warm or time.perf_counter() < t_warm:
-            flush.zero_()
-            env.step(acts[n_warm % period])
-            n_warm += 1
-            if n_warm % 64 == 0:
-                stream.synchronize()
-        stream.synchronize()
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        barrier(world)
-        torch.cuda.synchronize()
+        # the clock samples (every 100 ms) span the warm-up, the timed region
+        # and one sample after it, since a short timed region may fall between
+        # two samples
         with ClockSampler(local) as clk:
+            clk.wait_samples(1)
+            # warm-up: the timed loop itself (flush, step) for at least W steps
+            # and at least 0.5 s, so that clocks, the host path and the GPU's
+            # front end are in their steady state when timing starts
+            t_warm, n_warm = time.perf_counter() + 0.5, 0
+            while n_warm < warm or time.perf_counter() < t_warm:
+                flush.zero_()
+                env.step(acts[n_warm % period])
+                n_warm += 1
+                if n_warm % 64 == 0:
+                    stream.synchronize()
+            stream.synchronize()
+            barrier(world)
+            torch.cuda.synchronize()
             t_wall = time.perf_counter()
             # a short device-side pause ahead of the first timed step lets the
             # host enqueue the timed steps before the GPU reaches them: each
@@ -296,8 +308,9 @@ def run_gpu(args, world, rank, local):
                 ev1[t].record(stream)
             stream.synchronize()
             t_wall = time.perf_counter() - t_wall
-        barrier(world)
-        torch.cuda.synchronize()
+            barrier(world)
+            torch.cuda.synchronize()
+            clk.wait_samples(1)
         per = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])  # ms
         total_ms = max_over_ranks(float(per.sum()), world)
         env.sync()

@@ -166,3 +166,35 @@ def stacked_positions(seed: int, sizes, per_column: int = 3, offset: float = 0.0
             p[i, 0:2] = base[0:2] + rng.uniform(-offset, offset, 2)
         out.append(p)
     return np.concatenate(out, axis=0).astype(np.float32)
+
+
+def contact_swarm_states(seed: int, n_envs: int, n: int, spread: float = 0.08) -> np.ndarray:
+    """Binary32 drone states [n_envs * n][30] of swarms placed to meet every
+    contact within a few dozen steps: env e % 4 == 0 a cluster in mid-air
+    (pairs collide), 1 a cluster just above the floor falling at 1.5 m/s,
+    2 a cluster at the +x wall moving outward with the thrust axis pointing
+    back into the room, 3 a cluster under the ceiling climbing with the thrust
+    axis pointing down (so that drones leave the wall or ceiling after the hit
+    instead of pressing on it); velocities and body rates otherwise as in
+    random_states."""
+    s = random_states(seed, n_envs * n, rate=0.5).astype(np.float64)
+    rng = np.random.Generator(np.random.Philox(key=np.uint64(0xC0A7_0000 + seed)))
+    for e in range(n_envs):
+        sl = slice(e * n, (e + 1) * n)
+        p = rng.uniform(-spread, spread, (n, 3))
+        kind = e % 4
+        if kind == 0:
+            c = np.array([rng.uniform(-3.0, 3.0), rng.uniform(-3.0, 3.0), rng.uniform(3.0, 7.0)])
+        elif kind == 1:
+            c = np.array([rng.uniform(-3.0, 3.0), rng.uniform(-3.0, 3.0), spread + 0.03])
+            s[sl, 5] = -1.5
+        elif kind == 2:
+            c = np.array([5.0 - spread - 0.03, rng.uniform(-3.0, 3.0), rng.uniform(3.0, 7.0)])
+            s[sl, 3] = 1.5
+            s[sl, 6:15] = np.array([0.0, 0.0, -1.0, 0.0, 1.0, 0.0, 1.0, 0.0, 0.0])  # body z along -x
+        else:
+            c = np.array([rng.uniform(-3.0, 3.0), rng.uniform(-3.0, 3.0), 10.0 - spread - 0.03])
+            s[sl, 5] = 1.5
+            s[sl, 6:15] = np.array([1.0, 0.0, 0.0, 0.0, -1.0, 0.0, 0.0, 0.0, -1.0])  # body z down
+        s[sl, 0:3] = c[None, :] + p
+    return s.astype(np.float32)

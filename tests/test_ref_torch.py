@@ -68,3 +68,100 @@ def test_reference_gradient_equals_oracle_finite_differences():
             g = a.grad[p].reshape(-1)[q].item()
         fd = (oracle_loss(c, sp, prm, goals, ap).sum() - oracle_loss(c, sm_, prm, goals, am).sum()) / (2 * h)
         assert abs(g - fd) <= 1e-5 * max(1.0, abs(fd)), (kind, p, q, g, fd)
+
+
+# ----------------------------------------------------------------------------- discrete contacts
+DSIZES = [3, 4]
+DT = 12
+
+
+def discrete_case(seed=28):
+    """Env 0: one drone falls onto the floor (hit, then resting with
+    friction), one flies into the +x wall, one catches up with it and
+    collides; env 1: four drones packed closely enough to collide."""
+    from oracle.ref_step_torch import discrete_rollout_loss  # noqa: F401
+    E, D = len(DSIZES), sum(DSIZES)
+    c = O.default_config(n_envs=E, k_neighbors=0, flags=O.F_FLOOR | O.F_WALLS | O.F_COLLISIONS, seed=seed)
+    O.set_config(c, coll_sigma_v=0.0, coll_sigma_w=0.0)
+    nominal = [c.mass, c.ixx, c.iyy, c.izz, c.t2w, c.tau_m, c.arm]
+    st = W.random_states(seed, D, rate=0.5).astype(np.float64)
+    st[0, 0:6] = [0.0, 0.0, 0.02, 0.3, -0.2, -1.5]
+    st[1, 0:6] = [4.965, 1.0, 5.0, 1.0, 0.0, 0.0]
+    st[2, 0:6] = [4.852, 1.0, 5.0, 2.6, 0.0, 0.0]
+    st[3:7, 0:3] = W.clustered_positions(seed, [4], spread=0.05).astype(np.float64) + [0.0, 0.0, 3.0]
+    prm = W.random_params(seed, E, nominal).astype(np.float64)
+    goals = W.random_goals(seed, E).astype(np.float64)
+    acts = W.actions(seed, DT, D, lo=0.2, hi=0.8).astype(np.float64)
+    cfg = {k: getattr(c, k) for k in ("dt", "gravity", "kappa", "room_hx", "room_hy", "room_h", "omega_max",
+                                      "substeps", "mu", "alpha_c")}
+    cfg.update(floor=True, walls=True, collisions=True)
+    return c, st, prm, goals, acts, cfg
+
+
+def oracle_run_discrete(c, st, prm, goals, acts):
+    o = O.Oracle(c, DSIZES)
+    o.set_state(st, prm, goals, np.zeros(len(DSIZES), np.int32), np.zeros(len(DSIZES), np.uint32))
+    loss = np.zeros(o.D)
+    evs, margin = [], np.inf
+    for t in range(acts.shape[0]):
+        o.step(acts[t], want_obs=False, want_loss=True, loss=loss)
+        ev, _, mg = o.get_events()
+        evs.append(ev.copy())
+        margin = min(margin, mg.min())
+        o.clear_margin()
+    return loss, np.array(evs), margin
+
+
+def test_discrete_reference_forward_and_events_equal_oracle():
+    from oracle.ref_step_torch import discrete_rollout_loss
+    c, st, prm, goals, acts, cfg = discrete_case()
+    want, oev, margin = oracle_run_discrete(c, st, prm, goals, acts)
+    evs = []
+    got = discrete_rollout_loss(torch.tensor(st), torch.tensor(acts), torch.tensor(prm), torch.tensor(goals),
+                                DSIZES, cfg, events=evs).numpy()
+    assert margin > 1e-6  # no decision within binary64 rounding of its threshold
+    assert np.array_equal(np.array(evs).astype(np.uint32), oev)
+    seen = int(np.bitwise_or.reduce(oev.ravel()))
+    for bit in (O.EV_HIT_FLOOR, O.EV_ON_FLOOR, O.EV_HIT_WALL, O.EV_HIT_QUAD):
+        assert seen & bit, bit
+    assert np.allclose(got, want, rtol=1e-11, atol=1e-12)
+
+
+def test_discrete_reference_gradient_equals_oracle_finite_differences():
+    """Every command and initial-state entry: autograd of the reference
+    against central differences of the C oracle (h = 1e-6), where the
+    differences at h and 2h agree (a perturbation that flips a contact
+    decision makes the loss jump; such coordinates are left out)."""
+    from oracle.ref_step_torch import discrete_rollout_loss
+    c, st, prm, goals, acts, cfg = discrete_case()
+    x0 = torch.tensor(st, requires_grad=True)
+    a = torch.tensor(acts, requires_grad=True)
+    discrete_rollout_loss(x0, a, torch.tensor(prm), torch.tensor(goals), DSIZES, cfg).sum().backward()
+
+    def fd(sp, ap, h):
+        def L(s_, a_):
+            return oracle_run_discrete(c, s_, prm, goals, a_)[0].sum()
+        return (L(*sp(h)) - L(*sp(-h))) / (2 * h) if ap is None else (L(*ap(h)) - L(*ap(-h))) / (2 * h)
+
+    got, ref, ok = [], [], []
+    for d in range(sum(DSIZES)):
+        for k in range(26):
+            def sp(h, d=d, k=k):
+                s2 = st.copy()
+                s2[d, k] += h
+                return s2, acts
+            f1, f2 = fd(sp, None, 1e-6), fd(sp, None, 2e-6)
+            got.append(x0.grad[d, k].item()), ref.append(f1), ok.append(abs(f1 - f2) <= 1e-4 * (1 + abs(f1)))
+    rng = np.random.default_rng(1)
+    for t, d, r in zip(rng.integers(0, DT, 40), rng.integers(0, sum(DSIZES), 40), rng.integers(0, 4, 40)):
+        def ap(h, t=t, d=d, r=r):
+            a2 = acts.copy()
+            a2[t, d, r] += h
+            return st, a2
+        f1, f2 = fd(None, ap, 1e-6), fd(None, ap, 2e-6)
+        got.append(a.grad[t, d, r].item()), ref.append(f1), ok.append(abs(f1 - f2) <= 1e-4 * (1 + abs(f1)))
+    got, ref, ok = np.array(got), np.array(ref), np.array(ok)
+    assert ok.mean() >= 0.95
+    scale = np.abs(ref[ok]).max()
+    assert np.all(np.abs(got[ok] - ref[ok]) <= 1e-5 * np.abs(ref[ok]) + 1e-7 * scale), \
+        np.abs(got[ok] - ref[ok]).max() / scale
