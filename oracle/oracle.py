@@ -25,6 +25,7 @@ F_DR, F_MOTOR_NOISE, F_OBS_NOISE, F_COLLISIONS = 1 << 0, 1 << 1, 1 << 2, 1 << 3
 F_FLOOR, F_WALLS, F_AUTO_RESET, F_SMOOTH = 1 << 4, 1 << 5, 1 << 6, 1 << 7
 F_ACTION_SYMMETRIC, F_RECORD_KNN, F_DOWNWASH = 1 << 8, 1 << 9, 1 << 10
 F_ROUND32, F_ROUND32_SR = 1 << 11, 1 << 12  # conditioning instruments (see qs_oracle.h)
+F_EVENT_TIME = 1 << 13  # contacts resolved at their crossing time (see qs_oracle.h)
 EV_HIT_FLOOR, EV_ON_FLOOR, EV_HIT_WALL, EV_HIT_CEIL, EV_HIT_QUAD = 1, 2, 4, 8, 16
 NST, NPRM = 30, 7
 W_NAMES = ["pos", "vel", "ori", "spin", "act", "dact", "rot", "yaw", "hit_floor", "on_floor",

@@ -762,6 +762,7 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
     /* S6: semi-implicit Euler: velocities first, then positions with the new
      * velocities; dR/dt = R [w]x with body-frame w; polar re-orthonormalisation. */
     double vold[2] = {v[0], v[1]};
+    const double x0[3] = {x[0], x[1], x[2]}; /* substep start (event-time contacts) */
     for (int k = 0; k < 3; ++k) v[k] += acc[k] * dt;
     if (on_floor && moving) {
         /* friction never reverses the sliding direction within one substep */
@@ -802,6 +803,15 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
         if (x[2] <= 0.0) note_cmp(h, d, v[2] - acc[2] * dt, -acc[2] * dt); /* v+ = v + a dt vs 0 */
         if (x[2] <= 0.0 && v[2] < 0.0) {
             h->ev[d] |= OR_EV_HIT_FLOOR;
+            if (c->flags & OR_F_EVENT_TIME) {
+                /* the floor was crossed at time tau = -z0 / v_z of the substep's
+                 * straight path x0 + v s; the drone is at rest from then on, so
+                 * it travels horizontally only for tau */
+                double tau = -x0[2] / v[2];
+                tau = tau < 0.0 ? 0.0 : (tau > dt ? dt : tau);
+                x[0] = x0[0] + v[0] * tau;
+                x[1] = x0[1] + v[1] * tau;
+            }
             x[2] = 0.0;
             for (int k = 0; k < 3; ++k) { v[k] = 0.0; w[k] = 0.0; }
             double cs, sn, hyp = sqrt(R[0] * R[0] + R[3] * R[3]);
@@ -821,23 +831,28 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
      * reflected), then v <- alpha_c (v + eps_v), w <- w + eps_w. (A drone whose
      * velocity the floor rule just zeroed is clamped without a response.) */
     if (c->flags & OR_F_WALLS) {
-        int hit_wall = 0, hit_ceil = 0;
+        int hit_wall = 0, hit_ceil = 0, clamped[3] = {0, 0, 0};
+        double tau = dt;                                     /* earliest crossing (event-time contacts) */
+        const double v1[3] = {v[0], v[1], v[2]};
         const double lim[2] = {c->room_hx, c->room_hy};
         for (int k = 0; k < 2; ++k) {
             note_cmp(h, d, x[k], lim[k]);
             note_cmp(h, d, x[k], -lim[k]);
             if (x[k] > lim[k]) {
-                if (v[k] > 0.0) { v[k] = 0.0; hit_wall = 1; }
+                if (v[k] > 0.0) { v[k] = 0.0; hit_wall = 1; tau = fmin(tau, (lim[k] - x0[k]) / v1[k]); }
                 x[k] = lim[k];
+                clamped[k] = 1;
             } else if (x[k] < -lim[k]) {
-                if (v[k] < 0.0) { v[k] = 0.0; hit_wall = 1; }
+                if (v[k] < 0.0) { v[k] = 0.0; hit_wall = 1; tau = fmin(tau, (-lim[k] - x0[k]) / v1[k]); }
                 x[k] = -lim[k];
+                clamped[k] = 1;
             }
         }
         note_cmp(h, d, x[2], c->room_h);
         if (x[2] > c->room_h) {
-            if (v[2] > 0.0) { v[2] = 0.0; hit_ceil = 1; }
+            if (v[2] > 0.0) { v[2] = 0.0; hit_ceil = 1; tau = fmin(tau, (c->room_h - x0[2]) / v1[2]); }
             x[2] = c->room_h;
+            clamped[2] = 1;
         }
         if (hit_wall || hit_ceil) {
             double n[6];
@@ -845,6 +860,15 @@ static void substep_drone(or_env* h, int e, int d, int sub, const double a_in[4]
             for (int k = 0; k < 3; ++k) {
                 v[k] = c->alpha_c * (v[k] + c->coll_sigma_v * n[k]);
                 w[k] = w[k] + c->coll_sigma_w * n[3 + k];
+            }
+            if (c->flags & OR_F_EVENT_TIME) {
+                /* the first boundary was crossed at tau on the straight path
+                 * x0 + v1 s; the coordinates the boundaries do not hold move with
+                 * the pre-contact velocity until tau and the post-contact one
+                 * for the rest of the substep */
+                tau = tau < 0.0 ? 0.0 : tau;
+                for (int k = 0; k < 3; ++k)
+                    if (!clamped[k]) x[k] = x0[k] + v1[k] * tau + v[k] * (dt - tau);
             }
             if (hit_wall) h->ev[d] |= OR_EV_HIT_WALL;
             if (hit_ceil) h->ev[d] |= OR_EV_HIT_CEIL;
@@ -1029,7 +1053,11 @@ static void step_env(or_env* h, int e, const double* actions, double* obs, doubl
      * then once per responding drone v <- alpha_c (v + sum + eps_v), w <- w + eps_w. */
     if (!smooth && (c->flags & OR_F_COLLISIONS) && N >= 2) {
         double* dv = (double*)calloc((size_t)3 * N, sizeof(double));
+        double* dx_et = (double*)calloc((size_t)3 * N, sizeof(double)); /* sum_j v~_ij sigma_ij */
+        double* smax = (double*)calloc((size_t)N, sizeof(double));      /* earliest contact of i */
         uint8_t* resp = (uint8_t*)calloc((size_t)N, 1);
+        const int et = (c->flags & OR_F_EVENT_TIME) != 0;
+        const double Tc = c->substeps * c->dt;
         for (int i = 0; i < N; ++i)
             for (int j = 0; j < N; ++j) {
                 if (i == j || !coll[i * N + j]) continue;
@@ -1050,6 +1078,23 @@ static void step_env(or_env* h, int e, const double* actions, double* obs, doubl
                 double vn = (vj[0] - vi[0]) * n[0] + (vj[1] - vi[1]) * n[1] + (vj[2] - vi[2]) * n[2];
                 for (int k = 0; k < 3; ++k) dv[3 * i + k] += vn * n[k];
                 resp[i] = 1;
+                if (et) {
+                    /* contact time: run the pair's relative motion back from the
+                     * end of the control step, r(s) = dx - dvv s; the separation
+                     * reached the contact distance rho = l_i + l_j at
+                     * sigma = -c0 / (sqrt(b^2 - a c0) - b), a = |dvv|^2,
+                     * b = dx . dvv (< 0: approaching), c0 = |dx|^2 - rho^2 (< 0:
+                     * overlapping); at most the control step's duration */
+                    double rho = 2.0 * p[OR_P_ARM];
+                    double a = dvv[0] * dvv[0] + dvv[1] * dvv[1] + dvv[2] * dvv[2];
+                    double b = app;
+                    double c0 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2] - rho * rho;
+                    double sig = -c0 / (sqrt(b * b - a * c0) - b);
+                    if (sig > Tc) sig = Tc;
+                    if (sig < 0.0) sig = 0.0;
+                    for (int k = 0; k < 3; ++k) dx_et[3 * i + k] += vn * n[k] * sig;
+                    if (sig > smax[i]) smax[i] = sig;  /* ties keep the lower partner index */
+                }
             }
         for (int i = 0; i < N; ++i) {
             if (!resp[i]) continue;
@@ -1057,12 +1102,20 @@ static void step_env(or_env* h, int e, const double* actions, double* obs, doubl
             draw_six_normals(h, h->tick[e], (uint32_t)(d0 + i), OR_TAG_COLL, 0, nn);
             double* vi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_V;
             double* wi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_W;
+            double* xi = h->st + (size_t)(d0 + i) * OR_NST + OR_S_X;
             for (int k = 0; k < 3; ++k) {
+                double vold_k = vi[k];
                 vi[k] = c->alpha_c * (vi[k] + dv[3 * i + k] + c->coll_sigma_v * nn[k]);
                 wi[k] = wi[k] + c->coll_sigma_w * nn[3 + k];
+                if (et) {
+                    /* each exchange acts from its own contact time, the decay and
+                     * the perturbation from the drone's earliest contact */
+                    double Dk = vi[k] - vold_k - c->alpha_c * dv[3 * i + k];
+                    xi[k] += c->alpha_c * dx_et[3 * i + k] + Dk * smax[i];
+                }
             }
         }
-        free(dv); free(resp);
+        free(dv); free(dx_et); free(smax); free(resp);
     }
 
     /* S10b: downwash (Sec. III-B "Downwash"). A drone j above drone i that

@@ -25,6 +25,12 @@
  * the distance to the two neighbours, from a hash of the seed, round_salt,
  * drone, tick, substep and component). Comparing such a run with a plain one
  * measures how much a trajectory amplifies perturbations of binary32 size. */
+/* Event-time contacts (a variant of the model for gradients, beyond the
+ * paper): a contact detected at the end of a substep (floor, walls,
+ * ceiling) or control step (quad-quad) is resolved at its crossing time on
+ * the straight path that led there, and the drone flies the rest of the
+ * interval with its post-contact velocity. */
+#define OR_F_EVENT_TIME       (1u << 13)
 #define OR_F_ROUND32          (1u << 11)
 #define OR_F_ROUND32_SR       (1u << 12)
 

@@ -16,6 +16,9 @@ tensor ops over all drones at once:
   derivative of the piecewise-smooth map along the branches of the run.
   Contact perturbations and motor noise are left out (their draws are
   additive and drop out of the gradient; the comparisons set them to zero).
+  With cfg["event_time"] the contacts are resolved at their crossing time
+  (qs_oracle.h, OR_F_EVENT_TIME); autograd then differentiates through the
+  crossing times too.
 
 The polar factor of the integrated rotation is Newton's iteration
 X <- (X + X^-T)/2 with a fixed number of steps (converged in binary64 for the
@@ -159,8 +162,14 @@ def discrete_rollout_loss(x0, actions, params, goals, sizes, cfg, events=None):
     no motor noise and no contact perturbations. Same arguments as
     smooth_rollout_loss plus cfg["mu"], cfg["alpha_c"]; ``events``, if a
     list, receives each step's event bits (hit floor 1, on floor 2, wall 4,
-    ceiling 8, quad 16) per drone."""
+    ceiling 8, quad 16) per drone. cfg["event_time"] (default False): the
+    contacts at their crossing times (floor: tau = -z0 / v_z; walls and
+    ceiling: the earliest boundary crossing of the substep's straight path;
+    pairs: the contact distance on the pair's relative motion run back from
+    the end of the step, at most the step's duration)."""
     dt, g = cfg["dt"], cfg["gravity"]
+    et = bool(cfg.get("event_time", False))
+    Tc = cfg["substeps"] * dt
     sizes = [int(n) for n in sizes]
     env_of = torch.repeat_interleave(torch.arange(len(sizes)), torch.tensor(sizes))
     P = params[env_of]
@@ -216,6 +225,7 @@ def discrete_rollout_loss(x0, actions, params, goals, sizes, cfg, events=None):
             # S5: Euler's equation; S6: semi-implicit Euler and the polar factor
             wdot = (tau - torch.cross(w, I * w, dim=-1)) / I
             vold = v[:, 0:2]
+            xs0 = x  # substep start (event-time contacts)
             v = v + acc * dt
             if cfg["floor"]:
                 stop = moving & ((v[:, 0:2] * vold).sum(-1) < 0.0)
@@ -232,6 +242,11 @@ def discrete_rollout_loss(x0, actions, params, goals, sizes, cfg, events=None):
                 Rz = torch.stack([torch.stack([cs, -sn, z], -1), torch.stack([sn, cs, z], -1),
                                   torch.stack([z, z, o], -1)], -2)
                 R = torch.where(hit[:, None, None], Rz, R)
+                if et:
+                    vz = torch.where(hit, v[:, 2], -torch.ones_like(zero))
+                    tau = torch.clamp(-xs0[:, 2] / vz, 0.0, dt)
+                    xy = xs0[:, 0:2] + v[:, 0:2] * tau[:, None]
+                    x = torch.where(hit[:, None], torch.cat([xy, x[:, 2:3]], -1), x)
                 x = torch.where(hit[:, None], torch.cat([x[:, 0:2], zero[:, None]], -1), x)
                 v = torch.where(hit[:, None], torch.zeros_like(v), v)
                 w = torch.where(hit[:, None], torch.zeros_like(w), w)
@@ -239,22 +254,38 @@ def discrete_rollout_loss(x0, actions, params, goals, sizes, cfg, events=None):
             # S8: walls and ceiling: back onto the boundary; an outward normal
             # velocity is removed, then the decay alpha_c
             if cfg["walls"]:
-                xs, vs = [], []
+                xs, vs, clamped = [], [], []
+                v1 = v
+                tau = torch.full_like(zero, dt)
                 hit_wall = torch.zeros(D, dtype=torch.bool)
                 for k in range(2):
                     over, under = x[:, k] > lim[k], x[:, k] < -lim[k]
                     out = (over & (v[:, k] > 0.0)) | (under & (v[:, k] < 0.0))
                     hit_wall = hit_wall | out
+                    if et:
+                        bound = torch.where(over, lim[k] + 0.0 * x[:, k], -lim[k] + 0.0 * x[:, k])
+                        vk = torch.where(out, v[:, k], torch.ones_like(zero))
+                        tau = torch.where(out, torch.minimum(tau, (bound - xs0[:, k]) / vk), tau)
                     xs.append(torch.where(over, lim[k] + 0.0 * x[:, k], torch.where(under, -lim[k] + 0.0 * x[:, k],
                                                                                      x[:, k])))
                     vs.append(torch.where(out, zero, v[:, k]))
+                    clamped.append(over | under)
                 over = x[:, 2] > cfg["room_h"]
                 hit_ceil = over & (v[:, 2] > 0.0)
+                if et:
+                    vk = torch.where(hit_ceil, v[:, 2], torch.ones_like(zero))
+                    tau = torch.where(hit_ceil, torch.minimum(tau, (cfg["room_h"] - xs0[:, 2]) / vk), tau)
                 xs.append(torch.where(over, cfg["room_h"] + 0.0 * x[:, 2], x[:, 2]))
                 vs.append(torch.where(hit_ceil, zero, v[:, 2]))
+                clamped.append(over)
                 x, v = torch.stack(xs, -1), torch.stack(vs, -1)
                 resp = hit_wall | hit_ceil
                 v = torch.where(resp[:, None], ac * v, v)
+                if et:
+                    tau = torch.clamp(tau, min=0.0)
+                    xe = xs0 + v1 * tau[:, None] + v * (dt - tau)[:, None]
+                    free = resp[:, None] & ~torch.stack(clamped, -1)
+                    x = torch.where(free, xe, x)
                 ev = ev | torch.where(hit_wall, 4, 0) | torch.where(hit_ceil, 8, 0)
         # S9, S10: the pair set on the positions after the substeps and the
         # Jacobi response from the pre-collision velocities
@@ -273,7 +304,21 @@ def discrete_rollout_loss(x0, actions, params, goals, sizes, cfg, events=None):
             contrib = torch.where(sel[:, None], vn[:, None] * n, torch.zeros_like(n))
             dv = torch.zeros_like(v).index_add(0, ii, contrib)
             responded = torch.zeros(D, dtype=torch.bool).index_fill(0, ii[sel], True)
+            vpre = v
             v = torch.where(responded[:, None], ac * (v + dv), v)
+            if et:
+                # contact time sigma of each pair: |r - (v_i - v_j) sigma| = 2 l
+                rho2 = (2.0 * arm[ii]) ** 2
+                a_ = (dvv * dvv).sum(-1)
+                c0 = (r * r).sum(-1) - rho2
+                disc = torch.where(sel, app * app - a_ * c0, torch.ones_like(app))
+                den = torch.where(sel, torch.sqrt(disc) - app, torch.ones_like(app))
+                sig = torch.clamp(torch.where(sel, -c0 / den, torch.zeros_like(app)), 0.0, Tc)
+                dx_et = torch.zeros_like(x).index_add(0, ii, contrib * sig[:, None])
+                smax = torch.zeros_like(zero).scatter_reduce(0, ii, torch.where(sel, sig, torch.zeros_like(sig)),
+                                                             reduce="amax", include_self=True)
+                Dv = v - vpre - ac * dv
+                x = torch.where(responded[:, None], x + ac * dx_et + Dv * smax[:, None], x)
         if events is not None:
             events.append(ev.numpy().copy())
         loss = loss + ((x - G) ** 2).sum(-1) + 1e-3 * (fh * fh).sum(-1)

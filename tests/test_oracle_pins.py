@@ -450,6 +450,71 @@ def test_p9_floor_hit_resets_momenta_keeps_heading():
     assert np.abs(R - rz(psi)).max() < 1e-14
 
 
+def test_event_time_floor_and_wall_crossing_closed_form():
+    """Event-time contacts (beyond the paper; the differentiable model's
+    variant): motors off, upright, one substep. Floor: the drone crosses
+    z = 0 at tau = -z0 / v1_z on the straight path x0 + v1 s (v1 = v0 + g dt,
+    semi-implicit Euler) and stops there, so x_xy = x0_xy + v1_xy tau
+    instead of x0_xy + v1_xy dt. Wall: the first crossing of x = 5 at
+    tau = (5 - x0) / v1_x; after it the tangential coordinates move with
+    alpha_c v1 (no perturbation), the normal one stays on the wall."""
+    dt = 0.005
+    c, o = make(flags=O.F_FLOOR | O.F_EVENT_TIME, substeps=1, dt=dt)
+    st = base_state(x=(0.3, 0.1, 0.004), uf=0.0, fprev=0.0)
+    st[0, 3:6] = (1.0, 0.5, -1.0)
+    o.set_state(st, nominal(c)[None], np.zeros((1, 3)), np.zeros(1, np.int32), 0)
+    o.step(np.zeros((1, 4)))
+    s = o.get_state()["state"][0]
+    v1z = -1.0 - c.gravity * dt
+    tau = -0.004 / v1z
+    assert s[2] == 0.0 and np.all(s[3:6] == 0.0)
+    assert abs(s[0] - (0.3 + 1.0 * tau)) < 1e-15 and abs(s[1] - (0.1 + 0.5 * tau)) < 1e-15
+    assert tau < dt and abs(s[0] - (0.3 + 1.0 * dt)) > 1e-4  # the sampled reset would have gone the whole dt
+
+    c, o = make(flags=O.F_WALLS | O.F_EVENT_TIME, substeps=1, dt=dt, coll_sigma_v=0.0, coll_sigma_w=0.0)
+    st = base_state(x=(4.995, 1.0, 5.0), uf=0.0, fprev=0.0)
+    st[0, 3:6] = (2.0, 0.4, 0.3)
+    o.set_state(st, nominal(c)[None], np.zeros((1, 3)), np.zeros(1, np.int32), 0)
+    o.step(np.zeros((1, 4)))
+    s = o.get_state()["state"][0]
+    ev, _, _ = o.get_events()
+    assert ev[0] & O.EV_HIT_WALL
+    v1 = np.array([2.0, 0.4, 0.3 - c.gravity * dt])
+    tau = (5.0 - 4.995) / v1[0]
+    ac = c.alpha_c
+    assert s[0] == 5.0 and s[3] == 0.0
+    assert abs(s[1] - (1.0 + v1[1] * tau + ac * v1[1] * (dt - tau))) < 1e-15
+    assert abs(s[2] - (5.0 + v1[2] * tau + ac * v1[2] * (dt - tau))) < 1e-15
+    assert abs(s[4] - ac * v1[1]) < 1e-15 and abs(s[5] - ac * v1[2]) < 1e-15
+
+
+def test_event_time_pair_contact_time_closed_form():
+    """Event-time pair contact: two drones on a line, approaching head-on
+    with closing speed u, overlapping by delta at the end of the step: the
+    contact happened sigma = delta / u before the end (within the step), and
+    with alpha_c = 1 and no perturbation each drone flies its exchanged
+    velocity for sigma, so the positions move by (v_i' - v_i) sigma."""
+    dt = 0.005
+    c, o = make(n_envs=1, sizes=[2], flags=O.F_COLLISIONS | O.F_EVENT_TIME, substeps=1, dt=dt, alpha_c=1.0,
+                coll_sigma_v=0.0, coll_sigma_w=0.0)
+    arm = c.arm
+    st = base_state(n=2, x=(0.0, 0.0, 5.0), uf=0.0, fprev=0.0)
+    u = 3.0
+    delta = 0.004
+    # positions at the end of the substep are x0 + v1 dt (free flight, x and y unaffected by gravity)
+    gap = 2.0 * arm - delta
+    st[0, 0], st[1, 0] = -gap / 2 - 1.5 * dt, gap / 2 + 1.5 * dt
+    st[0, 3], st[1, 3] = 1.5, -1.5
+    o.set_state(st, np.tile(nominal(c), (1, 1)), np.zeros((1, 3)), np.zeros(1, np.int32), 0)
+    o.step(np.zeros((2, 4)))
+    s = o.get_state()["state"]
+    sigma = delta / u
+    # exchanged velocities: -1.5 and +1.5; displacement (v' - v) sigma = -3 sigma and +3 sigma
+    assert abs(s[0, 3] + 1.5) < 1e-12 and abs(s[1, 3] - 1.5) < 1e-12
+    assert abs(s[0, 0] - (-gap / 2 - 3.0 * sigma)) < 1e-12
+    assert abs(s[1, 0] - (gap / 2 + 3.0 * sigma)) < 1e-12
+
+
 def test_p9_static_and_sliding_friction():
     """Sec. III-B ground: at rest with |F_xy| <= mu (m g - F_z) nothing moves;
     otherwise the drone accelerates by (|F_xy| - mu (m g - F_z)) / m."""

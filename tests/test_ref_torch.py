@@ -75,13 +75,14 @@ DSIZES = [3, 4]
 DT = 12
 
 
-def discrete_case(seed=28):
+def discrete_case(seed=28, event_time=False):
     """Env 0: one drone falls onto the floor (hit, then resting with
     friction), one flies into the +x wall, one catches up with it and
     collides; env 1: four drones packed closely enough to collide."""
     from oracle.ref_step_torch import discrete_rollout_loss  # noqa: F401
     E, D = len(DSIZES), sum(DSIZES)
-    c = O.default_config(n_envs=E, k_neighbors=0, flags=O.F_FLOOR | O.F_WALLS | O.F_COLLISIONS, seed=seed)
+    flags = O.F_FLOOR | O.F_WALLS | O.F_COLLISIONS | (O.F_EVENT_TIME if event_time else 0)
+    c = O.default_config(n_envs=E, k_neighbors=0, flags=flags, seed=seed)
     O.set_config(c, coll_sigma_v=0.0, coll_sigma_w=0.0)
     nominal = [c.mass, c.ixx, c.iyy, c.izz, c.t2w, c.tau_m, c.arm]
     st = W.random_states(seed, D, rate=0.5).astype(np.float64)
@@ -94,7 +95,7 @@ def discrete_case(seed=28):
     acts = W.actions(seed, DT, D, lo=0.2, hi=0.8).astype(np.float64)
     cfg = {k: getattr(c, k) for k in ("dt", "gravity", "kappa", "room_hx", "room_hy", "room_h", "omega_max",
                                       "substeps", "mu", "alpha_c")}
-    cfg.update(floor=True, walls=True, collisions=True)
+    cfg.update(floor=True, walls=True, collisions=True, event_time=event_time)
     return c, st, prm, goals, acts, cfg
 
 
@@ -112,9 +113,10 @@ def oracle_run_discrete(c, st, prm, goals, acts):
     return loss, np.array(evs), margin
 
 
-def test_discrete_reference_forward_and_events_equal_oracle():
+@pytest.mark.parametrize("event_time", [False, True])
+def test_discrete_reference_forward_and_events_equal_oracle(event_time):
     from oracle.ref_step_torch import discrete_rollout_loss
-    c, st, prm, goals, acts, cfg = discrete_case()
+    c, st, prm, goals, acts, cfg = discrete_case(event_time=event_time)
     want, oev, margin = oracle_run_discrete(c, st, prm, goals, acts)
     evs = []
     got = discrete_rollout_loss(torch.tensor(st), torch.tensor(acts), torch.tensor(prm), torch.tensor(goals),
@@ -127,13 +129,14 @@ def test_discrete_reference_forward_and_events_equal_oracle():
     assert np.allclose(got, want, rtol=1e-11, atol=1e-12)
 
 
-def test_discrete_reference_gradient_equals_oracle_finite_differences():
+@pytest.mark.parametrize("event_time", [False, True])
+def test_discrete_reference_gradient_equals_oracle_finite_differences(event_time):
     """Every command and initial-state entry: autograd of the reference
     against central differences of the C oracle (h = 1e-6), where the
     differences at h and 2h agree (a perturbation that flips a contact
     decision makes the loss jump; such coordinates are left out)."""
     from oracle.ref_step_torch import discrete_rollout_loss
-    c, st, prm, goals, acts, cfg = discrete_case()
+    c, st, prm, goals, acts, cfg = discrete_case(event_time=event_time)
     x0 = torch.tensor(st, requires_grad=True)
     a = torch.tensor(acts, requires_grad=True)
     discrete_rollout_loss(x0, a, torch.tensor(prm), torch.tensor(goals), DSIZES, cfg).sum().backward()
@@ -165,3 +168,25 @@ def test_discrete_reference_gradient_equals_oracle_finite_differences():
     scale = np.abs(ref[ok]).max()
     assert np.all(np.abs(got[ok] - ref[ok]) <= 1e-5 * np.abs(ref[ok]) + 1e-7 * scale), \
         np.abs(got[ok] - ref[ok]).max() / scale
+
+
+def test_event_time_contacts_move_the_map():
+    """The event-time contacts change the step where a contact happens: the
+    falling drone's horizontal position after its floor hit and the
+    wall-hitting and colliding drones' positions differ from the sampled
+    contacts, and the gradients of the loss with respect to the falling
+    drone's initial height and vertical speed gain the crossing-time term
+    (the sampled floor reset passes nothing through it)."""
+    from oracle.ref_step_torch import discrete_rollout_loss
+    out = {}
+    for et in (False, True):
+        c, st, prm, goals, acts, cfg = discrete_case(event_time=et)
+        x0 = torch.tensor(st, requires_grad=True)
+        L = discrete_rollout_loss(x0, torch.tensor(acts), torch.tensor(prm), torch.tensor(goals), DSIZES, cfg)
+        L.sum().backward()
+        out[et] = (L.detach().numpy(), x0.grad.numpy().copy())
+    dl = np.abs(out[True][0] - out[False][0])
+    assert (dl[:3] > 1e-6).all()             # every contact of env 0 moved the trajectory
+    g0, g1 = out[False][1], out[True][1]
+    for k in (2, 5):  # z0 and v_z0 of the drone that lands
+        assert abs(g1[0, k] - g0[0, k]) > 1e-2 * max(abs(g0[0, k]), 1e-3), (k, g0[0, k], g1[0, k])
