@@ -49,7 +49,7 @@ MUTANTS = {
     "floor hit heading sign": [("if (hyp >= 1e-6) { cs = R[0] / hyp; sn = R[3] / hyp; }",
                                 "if (hyp >= 1e-6) { cs = R[0] / hyp; sn = -R[3] / hyp; }")],
     "wall reflects instead of removing the normal velocity": [
-        ("if (v[k] > 0.0) { v[k] = 0.0; hit_wall = 1; }", "if (v[k] > 0.0) { v[k] = -v[k]; hit_wall = 1; }")],
+        ("if (v[k] > 0.0) { v[k] = 0.0; hit_wall = 1;", "if (v[k] > 0.0) { v[k] = -v[k]; hit_wall = 1;")],
     # S10 collision response
     "collision response sign": [
         ("(vj[0] - vi[0]) * n[0] + (vj[1] - vi[1]) * n[1] + (vj[2] - vi[2]) * n[2]",
@@ -89,8 +89,8 @@ MUTANTS = {
     "no re-orthonormalisation": [("double nx = 0.5 * (x[k] + it[k]);", "double nx = x[k];")],
     "friction on m g instead of m g - F_z": [("double ffric = c->mu * (m * g - F[2]);",
                                               "double ffric = c->mu * m * g;")],
-    "ceiling reflects": [("if (v[2] > 0.0) { v[2] = 0.0; hit_ceil = 1; }",
-                          "if (v[2] > 0.0) { v[2] = -v[2]; hit_ceil = 1; }")],
+    "ceiling reflects": [("if (v[2] > 0.0) { v[2] = 0.0; hit_ceil = 1;",
+                          "if (v[2] > 0.0) { v[2] = -v[2]; hit_ceil = 1;")],
     "wall body-rate perturbation dropped": [("w[k] = w[k] + c->coll_sigma_w * n[3 + k];", "w[k] = w[k];")],
     "smooth floor pulls down": [("acc[2] += kc * softplus_b(-x[2], beta);", "acc[2] -= kc * softplus_b(-x[2], beta);")],
     # S9, S10 again
