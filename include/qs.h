@@ -86,6 +86,7 @@ typedef enum {
 #define QS_F_ACTION_SYMMETRIC (1u << 8) /* f^ = (clip(a,-1,1)+1)/2 instead of clip(a,0,1) */
 #define QS_F_RECORD_KNN       (1u << 9) /* keep neighbour indices for qs_get_events */
 #define QS_F_DOWNWASH         (1u << 10) /* downwash from drones overlapping above (Sec. III-B) */
+#define QS_F_EVENT_TIME       (1u << 11) /* differentiable rollout only: contacts at their crossing time */
 
 /* Training scenarios (Sec. III-D). qs_config.scenarios is a mask of
  * (1u << QS_SCN_*); at every reset each env draws its scenario uniformly from
@@ -330,9 +331,26 @@ qs_status qs_get_rollout_shape(const qs_env* h, int32_t* block, int32_t* fuse, i
  *    walls and ceiling, collisions with their perturbations); the gradient is
  *    the derivative of the contact branch each decision took (the map is
  *    piecewise smooth; resets that set a state component to a constant pass
- *    no gradient through it).
+ *    no gradient through it);
+ *  - with QS_F_EVENT_TIME (a variant of the model for gradients, beyond the
+ *    paper's Sec. III-B), each contact detected at the end of a substep
+ *    (floor, walls, ceiling) or control step (quad-quad) is resolved at its
+ *    crossing time on the straight path that led there: a drone that hits the
+ *    floor moves horizontally only until it crosses z = 0 (tau = -z0 / v_z),
+ *    a wall or ceiling contact moves the coordinates the boundaries do not
+ *    hold with the pre-contact velocity until the first crossing and with the
+ *    post-contact velocity after it, and a colliding pair touched sigma =
+ *    -c0 / (sqrt(b^2 - a c0) - b) before the end of the step (a = |v_i -
+ *    v_j|^2, b = (v_i - v_j).(x_i - x_j), c0 = |x_i - x_j|^2 - (l_i + l_j)^2,
+ *    at most the step's duration), each exchange acting on the position from
+ *    its contact time and the decay and perturbation from the drone's
+ *    earliest contact. The gradient then includes the terms through the
+ *    crossing times (the saltation of the hybrid dynamics).
  * A handle created with QS_F_DOWNWASH or with scenarios other than the single
- * goal returns QS_ERR_UNSUPPORTED. */
+ * goal, or with QS_F_EVENT_TIME together with QS_F_SMOOTH, returns
+ * QS_ERR_UNSUPPORTED. QS_F_EVENT_TIME changes only these entry points:
+ * qs_step, qs_step_host, qs_rollout and qs_serve_begin return
+ * QS_ERR_UNSUPPORTED for a handle created with it. */
 qs_status qs_diff_workspace_size(const qs_env* h, int32_t T, int32_t ckpt_every, size_t* bytes);
 qs_status qs_diff_forward(qs_env* h, int32_t T, int32_t ckpt_every, const float* x0_dev, const float* actions_dev,
                           float* loss_dev, void* workspace_dev);

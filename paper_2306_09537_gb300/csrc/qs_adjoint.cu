@@ -316,6 +316,12 @@ __device__ __forceinline__ void load_eps(const float* sc, size_t D, int idx, int
     for (int q = 0; q < 4; ++q) e[q] = b[q * D];
 }
 
+// The velocity of saved entry idx.
+__device__ __forceinline__ void load_v(const float* sc, size_t D, int idx, int d, float v[3]) {
+    const float* b = sc + (size_t)idx * NSUB * D + d + (size_t)3 * D;
+    for (int q = 0; q < 3; ++q) v[q] = b[q * D];
+}
+
 // The position of saved entry idx.
 __device__ __forceinline__ void load_x(const float* sc, size_t D, int idx, int d, float x[3]) {
     const float* b = sc + (size_t)idx * NSUB * D + d;
@@ -632,8 +638,14 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
 
 // Adjoint of one discrete substep. s: substep input; the lambdas hold the
 // output's on entry and the input's on return; lu accumulates lambda of u.
+// ET: the event-time contacts (QS_F_EVENT_TIME): the floor hit moves the
+// drone horizontally only up to the crossing time tau = -z0 / v1_z, a wall or
+// ceiling contact moves the coordinates the boundaries do not hold with v1
+// up to the first crossing tau = (L - x0_k) / v1_k and with the post-contact
+// velocity v' after it; the reverse adds the terms through tau.
+template <bool ET>
 __device__ __forceinline__ void discrete_substep_vjp(const Drone& s, const Prm& p, const Consts& c, const float u[4],
-                                                     const float eps1s[4], float lx[3], float lv[3],
+                                                     const float eps1s[4], const float vo[3], float lx[3], float lv[3],
                                                      float lR[9], float lw[3], float luf[4], float leps[4],
                                                      float lu[4]) {
     const float dt = c.dt, g = c.g;
@@ -693,26 +705,66 @@ __device__ __forceinline__ void discrete_substep_vjp(const Drone& s, const Prm& 
     for (int k = 0; k < 9; ++k) R1[k] = s.R[k];
     rotate_polar(R1, w1, dt);
     const bool hit = (c.flags & QS_F_FLOOR) && x1[2] <= 0.0f && v1[2] < 0.0f;
+    // event-time floor: crossing time and the velocity that led there
+    float tf = dt, vz_hit = 0.f;
+    bool tf_free = false;
+    if (ET && hit) {
+        vz_hit = v1[2];
+        const float t_raw = -s.x[2] / v1[2];
+        tf_free = t_raw > 0.0f && t_raw < dt;
+        tf = fminf(fmaxf(t_raw, 0.0f), dt);
+        x1[0] = fmaf(v1[0], tf, s.x[0]);
+        x1[1] = fmaf(v1[1], tf, s.x[1]);
+    }
+    const float vh1[2] = {v1[0], v1[1]};  // horizontal velocity before the floor reset
     if (hit) {
         x1[2] = 0.0f;
         v1[0] = v1[1] = v1[2] = 0.0f;
     }
     bool clamp_x[3] = {false, false, false}, zero_v[3] = {false, false, false}, bump = false;
+    float tw = dt;  // event-time walls: earliest crossing and the axis that set it
+    int kw = -1;
     if (c.flags & QS_F_WALLS) {
         const float lim[3] = {c.room_hx, c.room_hy, c.room_h};
         for (int k = 0; k < 3; ++k) {
+            float bound = 0.f;
             if (x1[k] > lim[k]) {
                 clamp_x[k] = true;
                 zero_v[k] = v1[k] > 0.0f;
+                bound = lim[k];
             } else if (k < 2 && x1[k] < -lim[k]) {
                 clamp_x[k] = true;
                 zero_v[k] = v1[k] < 0.0f;
+                bound = -lim[k];
+            }
+            if (ET && zero_v[k]) {
+                const float tk = (bound - s.x[k]) / v1[k];
+                if (tk < tw) {
+                    tw = tk;
+                    kw = k;
+                }
             }
             bump |= zero_v[k];
         }
     }
+    const bool tw_free = ET && bump && kw >= 0 && tw > 0.0f;
+    if (ET && bump) tw = fmaxf(tw, 0.0f);
+    // the post-contact velocity of the event-time walls, alpha_c (v1 + sigma_v n)
+    // with the outward parts removed: the substep's output velocity (saved)
+    const float* vpost = vo;
 
     // ---- reverse
+    // event-time walls: x_j = x0_j + v1_j tau + v'_j (dt - tau) for the coordinates
+    // the boundaries do not hold; lambda of tau, and v' receives (dt - tau) lambda x_j
+    float ltw = 0.f, twf[3] = {dt, dt, dt};
+    if (ET && bump) {
+        for (int k = 0; k < 3; ++k) {
+            if (clamp_x[k]) continue;
+            ltw += lx[k] * (v1[k] - vpost[k]);
+            lv[k] = fmaf(dt - tw, lx[k], lv[k]);
+            twf[k] = tw;
+        }
+    }
     // walls: v <- alpha_c (v + eps) after the outward components are removed; x held on the boundary
     if (bump)
         for (int k = 0; k < 3; ++k) lv[k] *= c.alpha_c;
@@ -750,7 +802,21 @@ __device__ __forceinline__ void discrete_substep_vjp(const Drone& s, const Prm& 
     }
     // x1 = x + v1 dt; the stop rule; v1 = v + a dt (v_z first set to 0 on the floor)
     float lv1[3];
-    for (int k = 0; k < 3; ++k) lv1[k] = lv[k] + dt * lx[k];
+    for (int k = 0; k < 3; ++k) lv1[k] = lv[k] + (ET ? twf[k] : dt) * lx[k];
+    if (ET && hit) {
+        // event-time floor: x_xy = x0_xy + v1_xy tau, tau = -z0 / v1_z
+        const float ltf = lx[0] * vh1[0] + lx[1] * vh1[1];
+        lv1[0] = lv[0] + tf * lx[0];
+        lv1[1] = lv[1] + tf * lx[1];
+        if (tf_free) {
+            lx[2] -= ltf / vz_hit;
+            lv1[2] -= ltf * tf / vz_hit;
+        }
+    }
+    if (tw_free) {  // tau = (L - x0_k) / v1_k of the axis that crossed first
+        lx[kw] -= ltw / v1[kw];
+        lv1[kw] -= ltw * tw / v1[kw];
+    }
     if (stop) lv1[0] = lv1[1] = 0.0f;
     float la[3];
     for (int k = 0; k < 3; ++k) {
@@ -833,6 +899,91 @@ __device__ __forceinline__ void discrete_collisions(const Consts& c, Drone& s, c
     if (responded) apply_response(c, s, tick, d, dvs);
 }
 
+// ---------------------------------------------------------------- event-time pair contacts
+// With QS_F_EVENT_TIME a colliding, approaching pair (i, j) is taken to have
+// touched sigma_ij before the end of the control step: running the pair's
+// relative motion back, r(s) = r - u s with r = x_i - x_j, u = v_i - v_j, the
+// separation equals the contact distance (key = thr) at
+//   sigma = -c0 / (sqrt(b^2 - a c0) - b),  a = |u|^2, b = u . r (< 0), c0 = key - thr (< 0),
+// at most the step's duration. The exchange with j acts on drone i's
+// position from then on, the decay and the perturbation from its earliest
+// contact sigma* = max_j sigma_ij:
+//   x_i' = x_i + alpha_c sum_j v~_ij sigma_ij + D_i sigma*,  D_i = v_i' - v_i - alpha_c sum_j v~_ij.
+// Derivatives of sigma (implicit function, p = r - u sigma the separation at
+// contact): d sigma / d r = -p / (a sigma - b), d sigma / d u = sigma p / (a sigma - b).
+struct PairEt {
+    float n[3], w[3], vn, inv, sig, p[3], den;
+    bool free;
+};
+
+__device__ __forceinline__ PairEt pair_et(const float dx[3], float key, float thr, const float rv[3], float app,
+                                          float Tc) {
+    PairEt q;
+    q.inv = key > 0.0f ? rsqrtf(key) : 0.0f;
+    q.n[0] = key > 0.0f ? -dx[0] * q.inv : 0.0f;
+    q.n[1] = key > 0.0f ? -dx[1] * q.inv : 0.0f;
+    q.n[2] = key > 0.0f ? -dx[2] * q.inv : 1.0f;
+    for (int k = 0; k < 3; ++k) q.w[k] = -rv[k];  // v_j - v_i
+    q.vn = q.w[0] * q.n[0] + q.w[1] * q.n[1] + q.w[2] * q.n[2];
+    const float a = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+    const float c0 = key - thr;
+    const float raw = -c0 / (sqrtf(fmaxf(app * app - a * c0, 0.0f)) - app);
+    q.free = raw > 0.0f && raw < Tc;
+    q.sig = fminf(fmaxf(raw, 0.0f), Tc);
+    for (int k = 0; k < 3; ++k) q.p[k] = -dx[k] - rv[k] * q.sig;  // r - u sigma
+    q.den = a * q.sig - app;
+    return q;
+}
+
+// The event-time collision pass of a control step (forward).
+__device__ __forceinline__ void discrete_collisions_et(const Consts& c, Drone& s, const Prm& p, uint32_t tick, int d,
+                                                       bool act, float* sx, float* sv, int nt, int sbase, int lane,
+                                                       int N, int lt, int bid, int bn) {
+    if (act) {
+        sx[lt] = s.x[0];
+        sx[nt + lt] = s.x[1];
+        sx[2 * nt + lt] = s.x[2];
+        sv[lt] = s.v[0];
+        sv[nt + lt] = s.v[1];
+        sv[2 * nt + lt] = s.v[2];
+    }
+    group_sync(bid, bn);
+    float dvs[3] = {0.f, 0.f, 0.f}, dxs[3] = {0.f, 0.f, 0.f}, smax = 0.f;
+    bool responded = false;
+    if (act && N > 1) {
+        const float Tc = c.substeps * c.dt;
+        for (int j = 0; j < N; ++j) {
+            if (j == lane) continue;
+            const int tj = sbase + j;
+            float dx[3];
+            const float key = pair_key(s.x[0], s.x[1], s.x[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx[0], dx[1], dx[2]);
+            if (!(key < p.thr)) continue;
+            const float rv[3] = {s.v[0] - sv[tj], s.v[1] - sv[nt + tj], s.v[2] - sv[2 * nt + tj]};
+            const float app = -(rv[0] * dx[0] + rv[1] * dx[1] + rv[2] * dx[2]);
+            if (!(app < 0.0f)) continue;
+            const PairEt q = pair_et(dx, key, p.thr, rv, app, Tc);
+            for (int k = 0; k < 3; ++k) {
+                dvs[k] = fmaf(q.vn, q.n[k], dvs[k]);
+                dxs[k] = fmaf(q.vn * q.sig, q.n[k], dxs[k]);
+            }
+            smax = fmaxf(smax, q.sig);
+            responded = true;
+        }
+    }
+    group_sync(bid, bn);
+    if (responded) {
+        float n[6];
+        six_normals(c, tick, (uint32_t)d, TAG_COLL, 0, n);
+        for (int k = 0; k < 3; ++k) {
+            const float v0 = s.v[k];
+            s.v[k] = c.alpha_c * (s.v[k] + dvs[k] + c.sig_cv * n[k]);
+            comp_add(s.w[k], s.wlo[k], c.sig_cw * n[3 + k]);
+            const float Dk = s.v[k] - v0 - c.alpha_c * dvs[k];
+            s.x[k] = fmaf(Dk, smax, fmaf(c.alpha_c, dxs[k], s.x[k]));
+        }
+    }
+}
+
 // Adjoint of the collision pass: xs, vs the pre-collision position and
 // velocity of the thread's drone (as staged: sx, sv), sl the lambda of every
 // drone's post-collision velocity. For a responding drone i,
@@ -884,6 +1035,128 @@ __device__ __forceinline__ void collision_vjp(const Consts& c, const float xs[3]
     }
 }
 
+// Adjoint of the event-time collision pass together with step t's loss term,
+// which the pass's position correction feeds: on entry lx, lv hold lambda of
+// the post-collision x and v without that term, on return lambda of the
+// pre-collision x and v. sc: the pre-collision state. Every thread of the
+// group calls it. For a responding drone i (notation of discrete_collisions_et):
+//  - the exchange terms alpha_c v~_ij . (lambda v'_i - lambda v'_j) as in
+//    collision_vjp, and alpha_c sigma_ij v~_ij . (lambda x'_i - lambda x'_j);
+//  - the decay: lambda v_i += (alpha_c - 1) sigma* lambda x'_i;
+//  - through sigma_ij: lambda (x_i, v_i) += W_ij (d sigma / d r, d sigma / d u) with
+//    W_ij = alpha_c vn (n . (lambda x'_i - lambda x'_j)) + [j is i's earliest]
+//    lambda x'_i . D_i + [i is j's earliest] lambda x'_j . D_j.
+// The partners' lambdas, lambda x' . D and earliest partners are exchanged
+// through shared memory (sl, slx, sq, sarg: [3][nt], [3][nt], [nt], [nt]).
+__device__ __forceinline__ void collision_vjp_et(const Consts& c, const Drone& sc, const Prm& p, uint32_t tick, int d,
+                                                 bool act, float* sx, float* sv, float* sl, float* slx, float* sq,
+                                                 int* sarg, int nt, int sbase, int lane, int N, int lt, int bid, int bn,
+                                                 float dl, const float g[3], float lx[3], float lv[3]) {
+    const float Tc = c.substeps * c.dt, ac = c.alpha_c;
+    if (act) {
+        sx[lt] = sc.x[0];
+        sx[nt + lt] = sc.x[1];
+        sx[2 * nt + lt] = sc.x[2];
+        sv[lt] = sc.v[0];
+        sv[nt + lt] = sc.v[1];
+        sv[2 * nt + lt] = sc.v[2];
+    }
+    group_sync(bid, bn);
+    float dvs[3] = {0.f, 0.f, 0.f}, dxs[3] = {0.f, 0.f, 0.f}, smax = 0.f, Dv[3] = {0.f, 0.f, 0.f};
+    int m = -1;
+    bool responded = false;
+    if (act && N > 1) {
+        for (int j = 0; j < N; ++j) {
+            if (j == lane) continue;
+            const int tj = sbase + j;
+            float dx[3];
+            const float key = pair_key(sc.x[0], sc.x[1], sc.x[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx[0], dx[1],
+                                       dx[2]);
+            if (!(key < p.thr)) continue;
+            const float rv[3] = {sc.v[0] - sv[tj], sc.v[1] - sv[nt + tj], sc.v[2] - sv[2 * nt + tj]};
+            const float app = -(rv[0] * dx[0] + rv[1] * dx[1] + rv[2] * dx[2]);
+            if (!(app < 0.0f)) continue;
+            const PairEt q = pair_et(dx, key, p.thr, rv, app, Tc);
+            for (int k = 0; k < 3; ++k) {
+                dvs[k] = fmaf(q.vn, q.n[k], dvs[k]);
+                dxs[k] = fmaf(q.vn * q.sig, q.n[k], dxs[k]);
+            }
+            if (q.sig > smax || m < 0) {
+                if (q.sig > smax) smax = q.sig;
+                if (q.sig >= smax) m = j;
+            }
+            responded = true;
+        }
+    }
+    float xp[3] = {sc.x[0], sc.x[1], sc.x[2]}, qd = 0.f;
+    if (responded) {
+        float n[6];
+        six_normals(c, tick, (uint32_t)d, TAG_COLL, 0, n);
+        for (int k = 0; k < 3; ++k) {
+            const float v1 = ac * (sc.v[k] + dvs[k] + c.sig_cv * n[k]);
+            Dv[k] = v1 - sc.v[k] - ac * dvs[k];
+            xp[k] = fmaf(Dv[k], smax, fmaf(ac, dxs[k], sc.x[k]));
+        }
+    }
+    if (act) {
+        // loss of step t at the post-collision position
+        for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (xp[k] - g[k]);
+        if (responded) qd = lx[0] * Dv[0] + lx[1] * Dv[1] + lx[2] * Dv[2];
+        sl[lt] = lv[0];
+        sl[nt + lt] = lv[1];
+        sl[2 * nt + lt] = lv[2];
+        slx[lt] = lx[0];
+        slx[nt + lt] = lx[1];
+        slx[2 * nt + lt] = lx[2];
+        sq[lt] = qd;
+        sarg[lt] = responded ? m : -1;
+    }
+    group_sync(bid, bn);
+    if (responded) {
+        const float l0[3] = {lv[0], lv[1], lv[2]}, x0[3] = {lx[0], lx[1], lx[2]};
+        float acc_v[3] = {0.f, 0.f, 0.f}, acc_x[3] = {0.f, 0.f, 0.f}, gx[3] = {0.f, 0.f, 0.f}, gv[3] = {0.f, 0.f, 0.f};
+        for (int j = 0; j < N; ++j) {
+            if (j == lane) continue;
+            const int tj = sbase + j;
+            float dx[3];
+            const float key = pair_key(sc.x[0], sc.x[1], sc.x[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx[0], dx[1],
+                                       dx[2]);
+            if (!(key < p.thr)) continue;
+            const float rv[3] = {sc.v[0] - sv[tj], sc.v[1] - sv[nt + tj], sc.v[2] - sv[2 * nt + tj]};
+            const float app = -(rv[0] * dx[0] + rv[1] * dx[1] + rv[2] * dx[2]);
+            if (!(app < 0.0f)) continue;
+            const PairEt q = pair_et(dx, key, p.thr, rv, app, Tc);
+            const float qv[3] = {l0[0] - sl[tj], l0[1] - sl[nt + tj], l0[2] - sl[2 * nt + tj]};
+            const float qx[3] = {x0[0] - slx[tj], x0[1] - slx[nt + tj], x0[2] - slx[2 * nt + tj]};
+            const float nq = q.n[0] * qv[0] + q.n[1] * qv[1] + q.n[2] * qv[2];
+            const float nQ = q.n[0] * qx[0] + q.n[1] * qx[1] + q.n[2] * qx[2];
+            for (int k = 0; k < 3; ++k) acc_v[k] -= q.n[k] * (nq + q.sig * nQ);
+            if (key > 0.0f) {
+                float y[3];
+                for (int k = 0; k < 3; ++k) y[k] = (nq + q.sig * nQ) * q.w[k] + q.vn * (qv[k] + q.sig * qx[k]);
+                const float ny = q.n[0] * y[0] + q.n[1] * y[1] + q.n[2] * y[2];
+                for (int k = 0; k < 3; ++k) acc_x[k] += (y[k] - ny * q.n[k]) * q.inv;
+            }
+            if (q.free) {
+                float W = ac * q.vn * nQ;
+                if (m == j) W += qd;
+                if (sarg[tj] == lane) W += sq[tj];
+                const float f = W / q.den;
+                for (int k = 0; k < 3; ++k) {
+                    gx[k] -= f * q.p[k];
+                    gv[k] += f * q.sig * q.p[k];
+                }
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            lv[k] = ac * (l0[k] + acc_v[k]) + (ac - 1.f) * smax * x0[k] + gv[k];
+            lx[k] = x0[k] + ac * acc_x[k] + gx[k];
+        }
+    }
+    group_sync(bid, bn);
+}
+
+template <bool ET>
 __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                              const int* __restrict__ perm, const DiffArgs a) {
     extern __shared__ float sm[];
@@ -932,10 +1205,11 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, con
                 float n[4];
                 if (ahead)
                     for (int r = 0; r < 4; ++r) n[r] = *fwd_normals(nbase, nb, t & 1, sub, r, lt);
-                substep(s, p, c, u, tick0 + t, d, sub, zero3, ahead ? n : nullptr);
+                substep<ET>(s, p, c, u, tick0 + t, d, sub, zero3, ahead ? n : nullptr);
             }
         }
-        if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sm, sm + 3 * nt, nt, sbase, lane, N, lt, 1, nb);
+        if (coll && ET) discrete_collisions_et(c, s, p, tick0 + t, d, act, sm, sm + 3 * nt, nt, sbase, lane, N, lt, 1, nb);
+        else if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sm, sm + 3 * nt, nt, sbase, lane, N, lt, 1, nb);
         if (act) {
             const float dx = s.x[0] - g[0], dy = s.x[1] - g[1], dz = s.x[2] - g[2];
             L += dx * dx + dy * dy + dz * dz + 1e-3f * (fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
@@ -951,6 +1225,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, con
 // like k_diff_bwd: group 0 recomputes segment s - 1 (every substep input and
 // each step's pre-collision state) into one scratch buffer while group 1
 // reverses segment s from the other.
+template <bool ET>
 __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                              const int* __restrict__ perm, const DiffArgs a) {
     extern __shared__ float sm[];
@@ -968,6 +1243,9 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
     float* sx = sm + grp * 6 * nb;       // [3][nb] positions of the group
     float* sv = sx + 3 * nb;             // [3][nb] velocities of the group
     float* sl = sm + 12 * nb;            // [3][nb] lambda of the post-collision velocity (group 1)
+    float* slx = sm + 15 * nb;           // event time: [3][nb] lambda of the post-collision position,
+    float* sq = sm + 18 * nb;            //   [nb] lambda x' . D, [nb] earliest partner (group 1)
+    int* sarg = reinterpret_cast<int*>(sm + 19 * nb);
     const int S = c.substeps, S1 = c.substeps + 1;  // saved states per step: each substep's input, then the pre-collision state
     const size_t sbuf = (size_t)a.C * S1 * NSUB * D;  // floats of one scratch buffer
     Prm p;
@@ -1004,11 +1282,12 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
                     command4(c, a.act, D, t, d, fh, u, msk);
                     for (int sub = 0; sub < S; ++sub) {
                         save_sub(scr, D, (t - tb) * S1 + sub, d, s);
-                        substep(s, p, c, u, tick0 + t, d, sub, zero3);
+                        substep<ET>(s, p, c, u, tick0 + t, d, sub, zero3);
                     }
                     save_sub(scr, D, (t - tb) * S1 + S, d, s);
                 }
-                if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sx, sv, nt, sbase, lane, N, lt, bid, nb);
+                if (coll && ET) discrete_collisions_et(c, s, p, tick0 + t, d, act, sx, sv, nt, sbase, lane, N, lt, bid, nb);
+                else if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sx, sv, nt, sbase, lane, N, lt, bid, nb);
             }
         } else if (grp == 1 && it >= 1) {
             // reverse through segment nseg - it, recomputed in the previous round
@@ -1020,10 +1299,15 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
                 if (act) {
                     command4(c, a.act, D, t, d, fh, u, msk);
                     load_sub(scr, D, (t - tb) * S1 + S, d, sc);
-                    // loss of step t: |x(t) - g|^2 + 1e-3 |f^|^2 (the collision pass leaves x unchanged)
-                    for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (sc.x[k] - g[k]);
+                    // loss of step t: |x(t) - g|^2 + 1e-3 |f^|^2 (the collision pass leaves x
+                    // unchanged; the event-time pass moves it and adds the term itself)
+                    if (!(ET && coll))
+                        for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (sc.x[k] - g[k]);
                 }
-                if (coll) {
+                if (coll && ET) {
+                    collision_vjp_et(c, sc, p, tick0 + t, d, act, sx, sv, sl, slx, sq, sarg, nt, sbase, lane, N, lt, bid,
+                                     nb, dl, g, lx, lv);
+                } else if (coll) {
                     if (act) {
                         sx[lt] = sc.x[0];
                         sx[nt + lt] = sc.x[1];
@@ -1043,10 +1327,11 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
                 if (act) {
                     for (int sub = S - 1; sub >= 0; --sub) {
                         Drone si;
-                        float eps1[4];
+                        float eps1[4], vo[3];
                         load_sub(scr, D, (t - tb) * S1 + sub, d, si);
                         load_eps(scr, D, (t - tb) * S1 + sub + 1, d, eps1);
-                        discrete_substep_vjp(si, p, c, u, eps1, lx, lv, lR, lw, luf, leps, lu);
+                        if (ET) load_v(scr, D, (t - tb) * S1 + sub + 1, d, vo);
+                        discrete_substep_vjp<ET>(si, p, c, u, eps1, vo, lx, lv, lR, lw, luf, leps, lu);
                     }
                     float ga[4];
                     for (int r = 0; r < 4; ++r) {
@@ -1088,14 +1373,20 @@ cudaError_t launch_diff(int backward, const Consts& c, const Dev& dv, const Tile
     a.scratch = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + (size_t)nck * NPLANE * dv.D * sizeof(float4));
     // forward: two groups of `block` threads (integration, motor normals ahead);
     // backward: two (recompute, reverse) with up to 23 planes of `block` floats
+    // (positions and velocities of both groups, the reverse's lambdas of the
+    // post-collision velocity and, with event-time contacts, position, its
+    // lambda x' . D and earliest partner: 20 planes)
     const size_t smem = sizeof(float) * (9 + 2 * FWD_SUB * 4) * block, smem2 = sizeof(float) * 23 * block;
     if (2 * block > ADJ_BLOCK_MAX) return cudaErrorInvalidValue;
     if (c.flags & QS_F_SMOOTH) {
         if (backward) k_diff_bwd<<<n_tiles, 2 * block, smem2, st>>>(c, dv, tiles, perm, a);
         else k_diff_fwd<<<n_tiles, 2 * block, smem, st>>>(c, dv, tiles, perm, a);
+    } else if (c.flags & QS_F_EVENT_TIME) {
+        if (backward) k_diffd_bwd<true><<<n_tiles, 2 * block, smem2, st>>>(c, dv, tiles, perm, a);
+        else k_diffd_fwd<true><<<n_tiles, 2 * block, smem, st>>>(c, dv, tiles, perm, a);
     } else {
-        if (backward) k_diffd_bwd<<<n_tiles, 2 * block, smem2, st>>>(c, dv, tiles, perm, a);
-        else k_diffd_fwd<<<n_tiles, 2 * block, smem, st>>>(c, dv, tiles, perm, a);
+        if (backward) k_diffd_bwd<false><<<n_tiles, 2 * block, smem2, st>>>(c, dv, tiles, perm, a);
+        else k_diffd_fwd<false><<<n_tiles, 2 * block, smem, st>>>(c, dv, tiles, perm, a);
     }
     return cudaGetLastError();
 }

@@ -670,9 +670,17 @@ qs_status qs_reset(qs_env* h, uint64_t seed, const uint8_t* env_mask_dev, float*
     return QS_OK;
 }
 
+// Event-time contacts are a model of the differentiable rollout only.
+static qs_status no_event_time(qs_env* h, const char* who) {
+    if (!(h->cfg.flags & QS_F_EVENT_TIME)) return QS_OK;
+    return fail(h, QS_ERR_UNSUPPORTED,
+                std::string(who) + ": a handle with QS_F_EVENT_TIME runs the differentiable rollout only");
+}
+
 qs_status qs_step(qs_env* h, const float* actions_dev, float* obs_dev, float* reward_dev, uint8_t* done_dev) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_step: NULL handle");
     if (h->serving) return busy(h, "qs_step");
+    if (no_event_time(h, "qs_step") != QS_OK) return QS_ERR_UNSUPPORTED;
     if (!actions_dev) return fail(h, QS_ERR_ARG, "qs_step: actions_dev is NULL");
     if (!aligned(actions_dev, 16)) return fail(h, QS_ERR_ARG, "qs_step: actions_dev must be 16-byte aligned");
     if (obs_dev && !aligned(obs_dev, 8)) return fail(h, QS_ERR_ARG, "qs_step: obs_dev must be 8-byte aligned");
@@ -695,6 +703,7 @@ void* mapped_host(const void* p, size_t align) {
 qs_status qs_step_host(qs_env* h, const float* actions_host, float* obs_host, float* reward_host, uint8_t* done_host) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_step_host: NULL handle");
     if (h->serving) return busy(h, "qs_step_host");
+    if (no_event_time(h, "qs_step_host") != QS_OK) return QS_ERR_UNSUPPORTED;
     if (!actions_host) return fail(h, QS_ERR_ARG, "qs_step_host: actions_host is NULL");
     DeviceGuard g(h->device);
     const size_t D = h->D, E = h->E;
@@ -743,6 +752,7 @@ qs_status qs_rollout(qs_env* h, int32_t T, const float* actions_dev, float* obs_
                      uint8_t* done_dev) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_rollout: NULL handle");
     if (h->serving) return busy(h, "qs_rollout");
+    if (no_event_time(h, "qs_rollout") != QS_OK) return QS_ERR_UNSUPPORTED;
     if (T < 1) return fail(h, QS_ERR_ARG, "qs_rollout: T must be >= 1");
     if (!actions_dev || !aligned(actions_dev, 16)) return fail(h, QS_ERR_ARG, "qs_rollout: actions_dev NULL or misaligned");
     if (obs_dev && !aligned(obs_dev, 8)) return fail(h, QS_ERR_ARG, "qs_rollout: obs_dev must be 8-byte aligned");
@@ -806,6 +816,8 @@ static qs_status diff_check(qs_env* h, const char* who, int32_t T, int32_t C) {
         return fail(h, QS_ERR_UNSUPPORTED, std::string(who) + ": the differentiable rollout has no downwash term");
     if (h->c.scn_mask & ~1u)
         return fail(h, QS_ERR_UNSUPPORTED, std::string(who) + ": the differentiable rollout uses the single goal only");
+    if ((h->cfg.flags & QS_F_EVENT_TIME) && (h->cfg.flags & QS_F_SMOOTH))
+        return fail(h, QS_ERR_UNSUPPORTED, std::string(who) + ": event-time contacts apply to the discrete contacts only");
     if (T < 1 || C < 1) return fail(h, QS_ERR_ARG, std::string(who) + ": T and ckpt_every must be >= 1");
     return QS_OK;
 }
@@ -1036,6 +1048,7 @@ qs_status qs_serve_begin(qs_env* h, const float* actions_host, int32_t n_slots, 
                          uint8_t* done_host, int32_t idle_ms) {
     if (!h) return fail(nullptr, QS_ERR_ARG, "qs_serve_begin: NULL handle");
     if (h->serving) return fail(h, QS_ERR_ARG, "qs_serve_begin: the handle is already serving");
+    if (no_event_time(h, "qs_serve_begin") != QS_OK) return QS_ERR_UNSUPPORTED;
     if (!actions_host) return fail(h, QS_ERR_ARG, "qs_serve_begin: actions_host is NULL");
     if (idle_ms < 1 || idle_ms > QS_SERVE_IDLE_MS_MAX)
         return fail(h, QS_ERR_ARG, "qs_serve_begin: idle_ms must be in [1, " + std::to_string(QS_SERVE_IDLE_MS_MAX) + "]");

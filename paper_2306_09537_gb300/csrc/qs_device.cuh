@@ -351,7 +351,10 @@ __device__ __forceinline__ void motor_normals(const Consts& c, uint32_t tick, in
 }
 
 // nrm: this substep's four motor-noise normals when already drawn elsewhere
-// (nullptr: draw them here).
+// (nullptr: draw them here). ET: event-time contacts (QS_F_EVENT_TIME, the
+// differentiable rollout's variant): a floor, wall or ceiling contact is
+// resolved at its crossing time on the substep's straight path x0 + v1 s.
+template <bool ET = false>
 __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts& c, const float u[4], uint32_t tick,
                                             int d, int sub, const float pacc[3], const float* nrm = nullptr) {
     uint32_t ev = 0;
@@ -427,6 +430,7 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     const float wd2 = (tz - (s.w[0] * Iw1 - s.w[1] * Iw0)) * p.inv_izz;
     // S6 semi-implicit Euler, body rates bounded by omega_max
     const float vx0 = s.v[0], vy0 = s.v[1];
+    const float x0[3] = {s.x[0], s.x[1], s.x[2]};  // substep start (event-time contacts)
     s.v[0] = fmaf(a0, dt, s.v[0]);
     s.v[1] = fmaf(a1, dt, s.v[1]);
     s.v[2] = fmaf(a2, dt, s.v[2]);
@@ -457,6 +461,11 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     // S7 floor hit: momenta to zero, upright attitude keeping the heading
     if ((c.flags & QS_F_FLOOR) && s.x[2] <= 0.0f && s.v[2] < 0.0f) {
         ev |= EV_HIT_FLOOR;
+        if (ET) {  // crossing at tau = -z0 / v_z; at rest from then on
+            const float tau = fminf(fmaxf(-x0[2] / s.v[2], 0.0f), dt);
+            s.x[0] = fmaf(s.v[0], tau, x0[0]);
+            s.x[1] = fmaf(s.v[1], tau, x0[1]);
+        }
         s.x[2] = 0.0f;
         for (int k = 0; k < 3; ++k) {
             s.v[k] = 0.0f;
@@ -482,24 +491,31 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     // was moving outward its normal velocity is removed and
     // v <- alpha_c (v + eps_v), w <- w + eps_w
     if (c.flags & QS_F_WALLS) {
-        bool wall = false, ceil = false;
+        bool wall = false, ceil = false, held[3] = {false, false, false};
+        const float v1[3] = {s.v[0], s.v[1], s.v[2]};
+        float tau = dt;  // earliest boundary crossing (event-time contacts)
         if (s.x[0] > c.room_hx) {
-            if (s.v[0] > 0.0f) { s.v[0] = 0.0f; wall = true; }
+            if (s.v[0] > 0.0f) { s.v[0] = 0.0f; wall = true; if (ET) tau = fminf(tau, (c.room_hx - x0[0]) / v1[0]); }
             s.x[0] = c.room_hx;
+            held[0] = true;
         } else if (s.x[0] < -c.room_hx) {
-            if (s.v[0] < 0.0f) { s.v[0] = 0.0f; wall = true; }
+            if (s.v[0] < 0.0f) { s.v[0] = 0.0f; wall = true; if (ET) tau = fminf(tau, (-c.room_hx - x0[0]) / v1[0]); }
             s.x[0] = -c.room_hx;
+            held[0] = true;
         }
         if (s.x[1] > c.room_hy) {
-            if (s.v[1] > 0.0f) { s.v[1] = 0.0f; wall = true; }
+            if (s.v[1] > 0.0f) { s.v[1] = 0.0f; wall = true; if (ET) tau = fminf(tau, (c.room_hy - x0[1]) / v1[1]); }
             s.x[1] = c.room_hy;
+            held[1] = true;
         } else if (s.x[1] < -c.room_hy) {
-            if (s.v[1] < 0.0f) { s.v[1] = 0.0f; wall = true; }
+            if (s.v[1] < 0.0f) { s.v[1] = 0.0f; wall = true; if (ET) tau = fminf(tau, (-c.room_hy - x0[1]) / v1[1]); }
             s.x[1] = -c.room_hy;
+            held[1] = true;
         }
         if (s.x[2] > c.room_h) {
-            if (s.v[2] > 0.0f) { s.v[2] = 0.0f; ceil = true; }
+            if (s.v[2] > 0.0f) { s.v[2] = 0.0f; ceil = true; if (ET) tau = fminf(tau, (c.room_h - x0[2]) / v1[2]); }
             s.x[2] = c.room_h;
+            held[2] = true;
         }
         if (wall || ceil) {
             float n[6];
@@ -507,6 +523,11 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
             for (int k = 0; k < 3; ++k) {
                 s.v[k] = c.alpha_c * fmaf(c.sig_cv, n[k], s.v[k]);
                 comp_add(s.w[k], s.wlo[k], c.sig_cw * n[3 + k]);
+            }
+            if (ET) {  // pre-contact velocity until tau, post-contact for the rest
+                tau = fmaxf(tau, 0.0f);
+                for (int k = 0; k < 3; ++k)
+                    if (!held[k]) s.x[k] = fmaf(s.v[k], dt - tau, fmaf(v1[k], tau, x0[k]));
             }
             ev |= (wall ? EV_HIT_WALL : 0u) | (ceil ? EV_HIT_CEIL : 0u);
         }

@@ -21,10 +21,11 @@ QS_BLOCK_WARP_SPECIALISED = 1
 
 F_DR, F_MOTOR_NOISE, F_OBS_NOISE, F_COLLISIONS = 1 << 0, 1 << 1, 1 << 2, 1 << 3
 F_FLOOR, F_WALLS, F_AUTO_RESET, F_SMOOTH = 1 << 4, 1 << 5, 1 << 6, 1 << 7
-F_ACTION_SYMMETRIC, F_RECORD_KNN, F_DOWNWASH = 1 << 8, 1 << 9, 1 << 10
+F_ACTION_SYMMETRIC, F_RECORD_KNN, F_DOWNWASH, F_EVENT_TIME = 1 << 8, 1 << 9, 1 << 10, 1 << 11
 FEATURE_FLAGS = {"dr": F_DR, "motor_noise": F_MOTOR_NOISE, "obs_noise": F_OBS_NOISE, "collisions": F_COLLISIONS,
                  "floor": F_FLOOR, "walls": F_WALLS, "auto_reset": F_AUTO_RESET, "smooth": F_SMOOTH,
-                 "action_symmetric": F_ACTION_SYMMETRIC, "record_knn": F_RECORD_KNN, "downwash": F_DOWNWASH}
+                 "action_symmetric": F_ACTION_SYMMETRIC, "record_knn": F_RECORD_KNN, "downwash": F_DOWNWASH,
+                 "event_time": F_EVENT_TIME}
 EV_HIT_FLOOR, EV_ON_FLOOR, EV_HIT_WALL, EV_HIT_CEIL, EV_HIT_QUAD = 1, 2, 4, 8, 16
 W_NAMES = ["pos", "vel", "ori", "spin", "act", "dact", "rot", "yaw", "hit_floor", "on_floor", "hit_wall", "hit_ceil",
            "hit_quad", "near"]

@@ -21,7 +21,7 @@ import numpy as np
 
 # Named feature switches; each side maps them onto its own flag bits.
 FEATURES = ("dr", "motor_noise", "obs_noise", "collisions", "floor", "walls", "auto_reset",
-            "smooth", "action_symmetric", "record_knn")
+            "smooth", "action_symmetric", "record_knn", "downwash", "event_time")
 
 UNEVEN_SIZES = (1, 2, 4, 8, 16, 32, 64)
 

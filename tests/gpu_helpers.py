@@ -9,7 +9,7 @@ from paper_2306_09537_gb300 import workloads as W
 OR_FLAGS = {"dr": O.F_DR, "motor_noise": O.F_MOTOR_NOISE, "obs_noise": O.F_OBS_NOISE, "collisions": O.F_COLLISIONS,
             "floor": O.F_FLOOR, "walls": O.F_WALLS, "auto_reset": O.F_AUTO_RESET, "smooth": O.F_SMOOTH,
             "action_symmetric": O.F_ACTION_SYMMETRIC, "record_knn": O.F_RECORD_KNN,
-            "downwash": O.F_DOWNWASH}
+            "downwash": O.F_DOWNWASH, "event_time": O.F_EVENT_TIME}
 ALL_WEIGHTS = {n: 0.1 * (i + 1) * (-1) ** i for i, n in enumerate(O.W_NAMES)}
 DEV = torch.device("cuda:0")
 
