@@ -553,7 +553,9 @@ def run_forms(dev, stream, seed):
         # contacts; and the same with the step's own (discrete) contacts
         wl = W.DIFF
         for name, feats in (("fwd_adjoint", wl.features),
-                            ("fwd_adjoint_discrete", ("dr", "motor_noise", "floor", "walls", "collisions"))):
+                            ("fwd_adjoint_discrete", ("dr", "motor_noise", "floor", "walls", "collisions")),
+                            ("fwd_adjoint_event_time",
+                             ("dr", "motor_noise", "floor", "walls", "collisions", "event_time"))):
             env = QuadSwarmEnv(wl.n_envs, wl.swarm, wl.k_neighbors, feats, seed=seed, weights=wl.weights,
                                device=dev, stream=stream)
             env.reset(seed)
@@ -714,7 +716,7 @@ def main():
         # throughput of each form relative to the plain per-call GPU step (same binary32 accuracy)
         f["ratio_vs_plain_call"] = {k: f[k]["value"] / line["value"] for k in
                                     ("plain_rollout", "swarm_call", "swarm_rollout", "uneven_batched", "uneven_call",
-                                     "fwd_adjoint", "fwd_adjoint_discrete")}
+                                     "fwd_adjoint", "fwd_adjoint_discrete", "fwd_adjoint_event_time")}
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:  # the oracle's CPU baseline: rank 0 at N = 1 only
             line["cpu_baseline"] = cpu_baseline_legs()
