@@ -36,7 +36,8 @@ METRIC = "quadrotor-steps/sec on 1 GB300 (plain vs batched vs fwd+adjoint), % of
 # launch), and the SHA-256 of the library sources that capture was taken on:
 # once the kernel sources change, the figure no longer describes the kernel
 # and the roofline's traffic is reported as null until it is captured again.
-HEADLINE_DRAM = {"bytes_per_launch": 2075136, "sources_sha256": None,
+HEADLINE_DRAM = {"bytes_per_launch": 2074880,
+                 "sources_sha256": "54df55dac685951505c9dc02f09a95b06cf70d540c7c8d2c3710a5744c73ae55",
                  "source": "profiles/k_step_ws_plain_8192x1.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
 UNIT = "quadrotor-steps/s"
 WL = W.PLAIN
@@ -282,9 +283,10 @@ def run_gpu(args, world, rank, local):
         with ClockSampler(local) as clk:
             clk.wait_samples(1)
             # warm-up: the timed loop itself (flush, step) for at least W steps
-            # and at least 0.5 s, so that clocks, the host path and the GPU's
-            # front end are in their steady state when timing starts
-            t_warm, n_warm = time.perf_counter() + 0.5, 0
+            # and at least --warmup-seconds (0.5 s), so that clocks, the host
+            # path and the GPU's front end are in their steady state when
+            # timing starts
+            t_warm, n_warm = time.perf_counter() + args.warmup_seconds, 0
             while n_warm < warm or time.perf_counter() < t_warm:
                 flush.zero_()
                 env.step(acts[n_warm % period])
@@ -692,6 +694,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--warmup-seconds", type=float, default=0.5,
+                    help="least wall time of the headline's warm-up loop (0 for profiler runs: exactly W steps)")
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true",
