@@ -71,7 +71,8 @@ typedef enum {
     QS_ERR_OOM = 3,             /* device allocation failed */
     QS_ERR_STATE_NONFINITE = 4, /* the device found a non-finite drone state */
     QS_ERR_TIMEOUT = 5,         /* reserved: a bounded device wait gave up */
-    QS_ERR_UNSUPPORTED = 6      /* e.g. a swarm larger than QS_MAX_SWARM */
+    QS_ERR_UNSUPPORTED = 6,     /* e.g. a swarm larger than QS_MAX_SWARM */
+    QS_ERR_INDEX = 7            /* debug build only: a device index check failed (qs_build_flags) */
 } qs_status;
 
 /* qs_config.flags */
@@ -429,6 +430,25 @@ qs_status qs_sync(qs_env* h);
  * n < 0 or another variant. Needs no handle. */
 qs_status qs_philox4x32_10(const uint32_t* ctr_dev, uint32_t key0, uint32_t key1, int32_t variant, uint32_t* out_dev,
                            int64_t n, void* cuda_stream);
+
+/* Build of the loaded library. Bit QS_BUILD_DEBUG_CHECKS: the debug build
+ * (libquadswarm_gpu_debug.so, compiled with -DQS_DEBUG_CHECKS; the paper has
+ * no counterpart). In it the kernels check the indices they derive from
+ * their launch geometry (each slot's env, first drone and size, the slot's
+ * lanes within the CTA, a drone's env, a contiguous observation block) against
+ * the buffers they address; a failed check sets a bit of the handle's status
+ * word and the thread skips the work that would use the index (no access out
+ * of range, no trap, no skipped barrier), and the next qs_sync returns
+ * QS_ERR_INDEX. Results are otherwise those of the release build. */
+#define QS_BUILD_DEBUG_CHECKS 1
+int32_t qs_build_flags(void);
+
+/* Debug build only: runs one check of the device index `index` against the
+ * handle's drone count on its stream (a kernel that reads and rewrites the
+ * event word of drone `index` when the check passes), so that a test can see
+ * a failed check reported by qs_sync without any access out of range.
+ * QS_ERR_UNSUPPORTED in the release build, which would not check. */
+qs_status qs_debug_check_selftest(qs_env* h, int32_t index);
 
 /* Launch shape of qs_step for one swarm-width class (the envs whose swarm size
  * rounds up to the power of two `width`, 1..128): `block` threads per CTA, a

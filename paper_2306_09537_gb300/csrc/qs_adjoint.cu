@@ -433,9 +433,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_fwd(const Consts c, cons
     const Tile tile = tile_at(dv, tiles, blockIdx.x, nb);
     const int W = tile.W, nt = nb;
     const int slot = lt / W, lane = lt - slot * W;
-    const bool ok = slot < tile.count;
-    const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
-    const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
+    const SlotGeo geo = slot_geometry(dv, perm, tile, slot, W, nt);
+    const int e = geo.e, d0 = geo.d0, N = geo.N;
     const bool act = lane < N;
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;
@@ -500,9 +499,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
     const Tile tile = tile_at(dv, tiles, blockIdx.x, nb);
     const int W = tile.W, nt = nb;
     const int slot = lt / W, lane = lt - slot * W;
-    const bool ok = slot < tile.count;
-    const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
-    const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
+    const SlotGeo geo = slot_geometry(dv, perm, tile, slot, W, nt);
+    const int e = geo.e, d0 = geo.d0, N = geo.N;
     const bool act = lane < N;
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;
@@ -1164,9 +1162,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, con
     const Tile tile = tile_at(dv, tiles, blockIdx.x, nb);
     const int W = tile.W, nt = nb;
     const int slot = lt / W, lane = lt - slot * W;
-    const bool ok = slot < tile.count;
-    const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
-    const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
+    const SlotGeo geo = slot_geometry(dv, perm, tile, slot, W, nt);
+    const int e = geo.e, d0 = geo.d0, N = geo.N;
     const bool act = lane < N;
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;
@@ -1233,9 +1230,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
     const Tile tile = tile_at(dv, tiles, blockIdx.x, nb);
     const int W = tile.W, nt = nb;
     const int slot = lt / W, lane = lt - slot * W;
-    const bool ok = slot < tile.count;
-    const int e = ok ? slot_env(dv, perm, tile.first + slot) : 0;
-    const int d0 = ok ? env_first(dv, e) : 0, N = ok ? env_first(dv, e + 1) - d0 : 0;
+    const SlotGeo geo = slot_geometry(dv, perm, tile, slot, W, nt);
+    const int e = geo.e, d0 = geo.d0, N = geo.N;
     const bool act = lane < N;
     const int d = d0 + lane, sbase = slot * W;
     const size_t D = dv.D;

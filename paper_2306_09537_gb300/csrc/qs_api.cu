@@ -1013,8 +1013,28 @@ qs_status qs_sync(qs_env* h) {
     }
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "qs_sync");
-    if (*(volatile int32_t*)h->status_h & 1) return fail(h, QS_ERR_STATE_NONFINITE, "a drone state became non-finite");
+    const int32_t st = *(volatile int32_t*)h->status_h;
+    if (st & 1) return fail(h, QS_ERR_STATE_NONFINITE, "a drone state became non-finite");
+    if (st & 2) return fail(h, QS_ERR_INDEX, "a device index check of the debug build failed");
     return QS_OK;
+}
+
+int32_t qs_build_flags(void) {
+#ifdef QS_DEBUG_CHECKS
+    return QS_BUILD_DEBUG_CHECKS;
+#else
+    return 0;
+#endif
+}
+
+qs_status qs_debug_check_selftest(qs_env* h, int32_t index) {
+    if (!h) return fail(nullptr, QS_ERR_ARG, "qs_debug_check_selftest: NULL handle");
+    if (h->serving) return busy(h, "qs_debug_check_selftest");
+    if (!(qs_build_flags() & QS_BUILD_DEBUG_CHECKS))
+        return fail(h, QS_ERR_UNSUPPORTED, "qs_debug_check_selftest: the release build has no device index checks");
+    DeviceGuard g(h->device);
+    cudaError_t e = launch_check_selftest(h->dv, index, h->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(h, e, "qs_debug_check_selftest");
 }
 
 qs_status qs_set_block(qs_env* h, int32_t width, int32_t block) {

@@ -188,6 +188,24 @@ __device__ __forceinline__ void pack(const Drone& s, float4 q[NPLANE]) {
     f[35] = 0.0f;
 }
 
+// ---------------------------------------------------------------- debug index checks
+// The debug build (-DQS_DEBUG_CHECKS, libquadswarm_gpu_debug.so) checks the
+// indices a kernel derives from its launch geometry (the env of a slot, its
+// first drone and size, the slot's lanes, saved-state entries, the env of a
+// drone) against the buffers they address. A failed check sets bit 1 of the
+// status word (QS_ERR_INDEX at the next qs_sync) and the thread drops the work
+// that would use the index, so nothing is accessed out of range and no
+// barrier is skipped. The release build compiles the checks out.
+constexpr int32_t STATUS_NONFINITE = 1, STATUS_INDEX = 2;
+#ifdef QS_DEBUG_CHECKS
+__device__ __forceinline__ bool qs_check(int32_t* status, bool ok) {
+    if (!ok) atomicOr(status, STATUS_INDEX);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool qs_check(int32_t*, bool) { return true; }
+#endif
+
 // ---------------------------------------------------------------- slot geometry
 // A tile of `lanes` drone lanes holds lanes / W consecutive slots of the
 // permutation. With uniform geometry (dv.uni_n > 0: every env has uni_n
@@ -211,6 +229,33 @@ __device__ __forceinline__ int slot_env(const Dev& dv, const int* __restrict__ p
 
 // The first drone of env e (e = E: the drone count).
 __device__ __forceinline__ int env_first(const Dev& dv, int e) { return dv.uni_n ? e * dv.uni_n : dv.env_off[e]; }
+
+// Slot `slot` of a tile: its env, first drone and size; ok when the slot
+// exists (and, in the debug build, when the slot lies in the permutation, its
+// env in [0, E), the env's drones in [0, D) and within the slot's W lanes,
+// and the slot's lanes within the nt threads of the group).
+struct SlotGeo {
+    int e, d0, N;
+    bool ok;
+};
+
+__device__ __forceinline__ SlotGeo slot_geometry(const Dev& dv, const int* __restrict__ perm, const Tile& tile, int slot,
+                                                 int W, int nt) {
+    SlotGeo g{0, 0, 0, slot < tile.count};
+    if (g.ok) g.ok = qs_check(dv.status, tile.first + slot >= 0 && tile.first + slot < dv.E);
+    if (g.ok) {
+        g.e = slot_env(dv, perm, tile.first + slot);
+        g.ok = qs_check(dv.status, g.e >= 0 && g.e < dv.E);
+    }
+    if (g.ok) {
+        g.d0 = env_first(dv, g.e);
+        g.N = env_first(dv, g.e + 1) - g.d0;
+        g.ok = qs_check(dv.status,
+                        g.d0 >= 0 && g.N >= 1 && g.N <= W && g.d0 + g.N <= dv.D && (slot + 1) * W <= nt);
+        if (!g.ok) g.d0 = g.N = 0;
+    }
+    return g;
+}
 
 // hi + lo <- hi + lo + delta, keeping the rounding error of the sum in lo.
 __device__ __forceinline__ void comp_add(float& hi, float& lo, float delta) {

@@ -72,7 +72,7 @@ struct Dev {
     const int32_t* env_of;   // [D]
     uint32_t* ev;            // [D] event bits of the last step
     int16_t* knn;            // [K][D] neighbour local indices (QS_F_RECORD_KNN)
-    int32_t* status;         // device error word (bit 0: non-finite state)
+    int32_t* status;         // device error word (bit 0: non-finite state; bit 1: a debug-build index check failed)
     float* scn;              // [2][QS_NSCN][E] scenario records, double-buffered (null: single goal only)
     uint8_t* scn_sel;        // [E] active buffer of each env's record
     int D, E;
@@ -176,5 +176,8 @@ cudaError_t launch_set_state(const Consts& c, const Dev& dv, const float* state,
 cudaError_t launch_get_events(const Dev& dv, int K, uint32_t* events, int16_t* knn, cudaStream_t s);
 cudaError_t launch_scenario_io(const Dev& dv, float* out, const float* in, cudaStream_t s);
 cudaError_t launch_goals(const Consts& c, const Dev& dv, float* goals, cudaStream_t s);
+// Debug build: one index check of `index` against the drone count (see
+// qs_debug_check_selftest).
+cudaError_t launch_check_selftest(const Dev& dv, int index, cudaStream_t s);
 
 }  // namespace qsk

@@ -34,6 +34,7 @@ __global__ void k_reset_drone(const Consts c, const Dev dv, uint32_t k0, uint32_
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= dv.D) return;
     const int e = dv.env_of[d];
+    if (!qs_check(dv.status, e >= 0 && e < dv.E)) return;
     if (mask && !mask[e]) return;
     const uint32_t tick = dv.tick[e];  // 0 after a full reset (set by k_reset_env)
     Drone s;
@@ -115,6 +116,7 @@ cudaError_t launch_set_state(const Consts& c, const Dev& dv, const float* state,
 __global__ void k_scenario_io(const Dev dv, float* __restrict__ out, const float* __restrict__ in) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= dv.E) return;
+    if (!qs_check(dv.status, dv.scn_sel[e] == 0 || dv.scn_sel[e] == 1)) return;
     float* base = dv.scn + (size_t)dv.scn_sel[e] * QS_NSCN * dv.E + e;
     for (int k = 0; k < QS_NSCN; ++k) {
         if (out)
@@ -135,7 +137,10 @@ cudaError_t launch_scenario_io(const Dev& dv, float* out, const float* in, cudaS
 __global__ void k_goals(const Consts c, const Dev dv, float* __restrict__ goals) {
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= dv.D) return;
-    const int e = dv.env_of[d], d0 = dv.env_off[e], N = dv.env_off[e + 1] - d0, i = d - d0;
+    const int e = dv.env_of[d];
+    if (!qs_check(dv.status, e >= 0 && e < dv.E)) return;
+    const int d0 = dv.env_off[e], N = dv.env_off[e + 1] - d0, i = d - d0;
+    if (!qs_check(dv.status, i >= 0 && i < N)) return;
     const int tau = dv.ep[e], sel = dv.scn_sel[e];
     const float genv[3] = {dv.goal[e], dv.goal[dv.E + e], dv.goal[2 * dv.E + e]};
     float g[3] = {genv[0], genv[1], genv[2]};
@@ -188,6 +193,26 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, RoundKeys rk, uint32_
         const uint32_t c0 = ctr[3 * i], c1 = ctr[3 * i + 1], c2 = ctr[3 * i + 2];
         out[i] = variant == 0 ? philox_rk(c0, c1, c2, rk.rk) : philox(c0, c1, c2, key0, key1);
     }
+}
+
+#ifdef QS_DEBUG_CHECKS
+// One index check (debug build): the event word of drone `index` is read and
+// written back only when the check passes.
+__global__ void k_check_selftest(const Dev dv, int index) {
+    if (qs_check(dv.status, index >= 0 && index < dv.D)) dv.ev[index] = dv.ev[index];
+}
+#endif
+
+cudaError_t launch_check_selftest(const Dev& dv, int index, cudaStream_t st) {
+#ifdef QS_DEBUG_CHECKS
+    k_check_selftest<<<1, 1, 0, st>>>(dv, index);
+    return cudaGetLastError();
+#else
+    (void)dv;
+    (void)index;
+    (void)st;
+    return cudaErrorNotSupported;  // the release build has no checks: never launched
+#endif
 }
 
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int variant, uint32_t* out, long long n,

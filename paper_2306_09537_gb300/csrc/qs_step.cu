@@ -314,10 +314,10 @@ __device__ __forceinline__ SlotMap map_slot(const Dev& dv, const Tile& tile, con
     SlotMap m;
     m.slot = threadIdx.x / W;
     m.lane = threadIdx.x - m.slot * W;
-    const bool ok = m.slot < tile.count;
-    m.e = ok ? slot_env(dv, perm, tile.first + m.slot) : 0;
-    m.d0 = ok ? env_first(dv, m.e) : 0;
-    m.N = ok ? env_first(dv, m.e + 1) - m.d0 : 0;
+    const SlotGeo g = slot_geometry(dv, perm, tile, m.slot, W, blockDim.x);
+    m.e = g.e;
+    m.d0 = g.d0;
+    m.N = g.N;
     m.act = m.lane < m.N;
     m.d = m.d0 + m.lane;
     m.sbase = m.slot * W;
@@ -459,10 +459,10 @@ __device__ __forceinline__ WsMap ws_map(const Dev& dv, const Tile& tile, const i
     m.L = threadIdx.x & (32 * P - 1);
     m.slot = m.L / m.W;
     m.lane = m.L - m.slot * m.W;
-    const bool ok = m.slot < tile.count;
-    m.e = ok ? slot_env(dv, perm, tile.first + m.slot) : 0;
-    m.d0 = ok ? env_first(dv, m.e) : 0;
-    m.N = ok ? env_first(dv, m.e + 1) - m.d0 : 0;
+    const SlotGeo g = slot_geometry(dv, perm, tile, m.slot, m.W, 32 * P);
+    m.e = g.e;
+    m.d0 = g.d0;
+    m.N = g.N;
     m.act = m.lane < m.N;
     m.d = m.d0 + m.lane;
     m.sbase = m.slot * m.W;
@@ -497,8 +497,9 @@ __device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, con
                                              const float ew[3]) {
     const int od = c.obs_dim, K = c.K, L = m.L;
     const float(&st)[18][32 * P] = sh.st[b];
-    const bool contig = tile.pad != 0;
-    const int d_first = env_first(dv, slot_env(dv, perm, tile.first));
+    const bool contig = tile.pad != 0 &&
+                        qs_check(dv.status, tile.first >= 0 && tile.count >= 1 && tile.first + tile.count <= dv.E);
+    const int d_first = contig ? env_first(dv, slot_env(dv, perm, tile.first)) : 0;
     const int ridx = contig ? m.d - d_first : L;
     if (m.act) {
         float* row = sh.rows + ridx * od;
@@ -524,9 +525,10 @@ __device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, con
         }
     }
     side_sync<P>(2);
-    if (contig) {
-        const int e_last = slot_env(dv, perm, tile.first + tile.count - 1);
-        const int n_floats = (env_first(dv, e_last + 1) - d_first) * od;
+    const int e_last = contig ? slot_env(dv, perm, tile.first + tile.count - 1) : 0;
+    const int d_end = contig ? env_first(dv, e_last + 1) : 0;
+    if (contig && qs_check(dv.status, d_first >= 0 && d_end <= dv.D && d_end - d_first <= 32 * P)) {
+        const int n_floats = (d_end - d_first) * od;
         float* dst = obs + (size_t)d_first * od;
         if (((uintptr_t)dst & 15u) == 0) {
             const int n4 = n_floats >> 2;
@@ -540,7 +542,7 @@ __device__ __forceinline__ void ws_store_obs(const Consts& c, const Dev& dv, con
             float2* dst2 = reinterpret_cast<float2*>(dst);
             for (int i = L; i < n2; i += 32 * P) dst2[i] = src2[i];
         }
-    } else if (m.act) {
+    } else if (m.act && !contig) {
         const float2* src2 = reinterpret_cast<const float2*>(sh.rows + ridx * od);
         float2* dst2 = reinterpret_cast<float2*>(obs + (size_t)m.d * od);
         for (int i = 0; i < od / 2; ++i) dst2[i] = src2[i];

@@ -13,9 +13,11 @@ import os
 
 from . import build as _build
 
-QS_OK, QS_ERR_ARG, QS_ERR_CUDA, QS_ERR_OOM, QS_ERR_STATE_NONFINITE, QS_ERR_TIMEOUT, QS_ERR_UNSUPPORTED = range(7)
+(QS_OK, QS_ERR_ARG, QS_ERR_CUDA, QS_ERR_OOM, QS_ERR_STATE_NONFINITE, QS_ERR_TIMEOUT, QS_ERR_UNSUPPORTED,
+ QS_ERR_INDEX) = range(8)
 STATUS_NAMES = ["QS_OK", "QS_ERR_ARG", "QS_ERR_CUDA", "QS_ERR_OOM", "QS_ERR_STATE_NONFINITE", "QS_ERR_TIMEOUT",
-                "QS_ERR_UNSUPPORTED"]
+                "QS_ERR_UNSUPPORTED", "QS_ERR_INDEX"]
+QS_BUILD_DEBUG_CHECKS = 1
 QS_MAX_SWARM, QS_MAX_K, QS_STATE_DIM, QS_PARAM_DIM = 128, 8, 30, 7
 QS_BLOCK_WARP_SPECIALISED = 1
 
@@ -34,7 +36,8 @@ EXPORTS = ["qs_config_default", "qs_create", "qs_destroy", "qs_get_dims", "qs_re
            "qs_rollout", "qs_set_rollout_shape", "qs_get_rollout_shape", "qs_diff_workspace_size",
            "qs_diff_forward", "qs_diff_backward", "qs_diff_grad_static", "qs_get_state", "qs_set_state",
            "qs_get_events", "qs_get_scenario", "qs_set_scenario", "qs_get_goals", "qs_sync", "qs_set_block",
-           "qs_get_block", "qs_serve_begin", "qs_serve_step", "qs_serve_end", "qs_philox4x32_10", "qs_last_error"]
+           "qs_get_block", "qs_serve_begin", "qs_serve_step", "qs_serve_end", "qs_philox4x32_10", "qs_last_error",
+           "qs_build_flags", "qs_debug_check_selftest"]
 # training scenarios (Sec. III-D) and goal formations, in the order of QS_SCN_* / QS_FORM_*
 SCENARIOS = ["single", "static", "dynamic", "swap", "shrink_expand", "swarm_vs_swarm", "pursuit_lissajous",
              "pursuit_bezier"]
@@ -76,11 +79,13 @@ class QSError(RuntimeError):
 
 
 def library_path() -> str:
-    return _build.LIB
+    return os.environ.get("QS_LIBRARY") or _build.LIB
 
 
 def _load():
-    path = _build.LIB
+    # QS_LIBRARY names another build of the same sources to load (the debug
+    # build with device index checks, _build.LIB_DEBUG)
+    path = library_path()
     if not os.path.exists(path):
         raise ImportError(f"libquadswarm_gpu.so is not built ({path}); run __graft_entry__.build() or "
                           "python -m paper_2306_09537_gb300.build")
@@ -116,6 +121,8 @@ def _load():
     L.qs_get_block.argtypes = [V, C.c_int32, P(C.c_int32)]
     L.qs_last_error.argtypes = [V]
     L.qs_last_error.restype = C.c_char_p
+    L.qs_build_flags.argtypes = []
+    L.qs_debug_check_selftest.argtypes = [V, C.c_int32]
     for n in EXPORTS:
         if n not in ("qs_config_default", "qs_last_error"):
             getattr(L, n).restype = C.c_int
@@ -279,6 +286,15 @@ def qs_philox4x32_10(ctr, key0: int, key1: int, out, variant: int = 0, stream=No
     n = ctr.shape[0]
     return _check(_L.qs_philox4x32_10(_p(ctr), C.c_uint32(int(key0)), C.c_uint32(int(key1)), int(variant), _p(out),
                                       int(n), stream))
+
+
+def qs_build_flags() -> int:
+    """Bits of the loaded build (QS_BUILD_DEBUG_CHECKS: device index checks)."""
+    return int(_L.qs_build_flags())
+
+
+def qs_debug_check_selftest(h, index: int):
+    return _check(_L.qs_debug_check_selftest(h, int(index)), h)
 
 
 def qs_set_block(h, width: int, block: int):

@@ -86,3 +86,15 @@ def test_null_handle_calls_fail_cleanly(qs):
     assert L.qs_serve_step(None, 0) == qs.QS_ERR_ARG
     assert L.qs_serve_end(None) == qs.QS_ERR_ARG
     assert "NULL" in qs.qs_last_error(None)
+
+
+def test_debug_build_loads_with_every_symbol_and_its_flag(qs):
+    """The debug build (device index checks) exports the same ABI and says so;
+    the release build reports no checks."""
+    from paper_2306_09537_gb300 import build as b
+    dbg = C.CDLL(b.LIB_DEBUG)
+    for n in declared_functions():
+        assert hasattr(dbg, n), f"{n} missing from the debug build"
+    dbg.qs_build_flags.restype = C.c_int32
+    assert dbg.qs_build_flags() == qs.QS_BUILD_DEBUG_CHECKS
+    assert qs.qs_build_flags() == 0
