@@ -666,9 +666,10 @@ def profile_case(name, local):
             acts = torch.from_numpy(W.actions(3, 20, env.D)).to(dev)
             for t in range(20):
                 env.step(acts[t])
-        elif name in ("adjoint", "adjoint_discrete"):  # 1024 envs x 8, 32 steps, checkpoints every 16
+        elif name in ("adjoint", "adjoint_discrete", "adjoint_event_time"):  # 1024 envs x 8, 32 steps, ckpt 16
             wl = W.DIFF
-            feats = wl.features if name == "adjoint" else ("dr", "motor_noise", "floor", "walls", "collisions")
+            feats = {"adjoint": wl.features, "adjoint_discrete": ("dr", "motor_noise", "floor", "walls", "collisions"),
+                     "adjoint_event_time": ("dr", "motor_noise", "floor", "walls", "collisions", "event_time")}[name]
             env = QuadSwarmEnv(wl.n_envs, wl.swarm, 0, feats, seed=5, device=dev, stream=stream)
             env.reset(5)
             T, C = 32, 16
@@ -689,7 +690,7 @@ def profile_case(name, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-case", choices=["rollout", "rollout_ws", "scenario_rollout", "call_large", "swarm_call",
-                                               "adjoint", "adjoint_discrete"], default=None,
+                                               "adjoint", "adjoint_discrete", "adjoint_event_time"], default=None,
                     help="run one small case of a form (for ncu captures) and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
