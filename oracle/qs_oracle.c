@@ -32,6 +32,13 @@
  * neighbour indices and collision sets are well defined decisions. Build with
  * -ffp-contract=off and without -ffast-math.
  *
+ * Two options go beyond the paper: OR_F_EVENT_TIME resolves each detected
+ * contact at its crossing time within the substep or step (a variant of the
+ * model whose gradients carry the crossing-time terms), and OR_F_ROUND32 /
+ * OR_F_ROUND32_SR round the state to binary32 after every substep, an
+ * instrument the tests use to measure how strongly a trajectory amplifies
+ * perturbations of binary32 size. Neither is on by default.
+ *
  * Parity unpinned (no closed form or printed value constrains them): the
  * reward weights' semantics, the friction constant mu, the collision constants
  * and the sensor-noise reading; the tests only check them for self-consistency
