@@ -31,22 +31,29 @@ namespace qsk {
 constexpr int ADJ_BLOCK_MAX = 256;
 constexpr int NSUB = 29;  // floats of a saved substep input: x v R w wlo uf eps
 
-__device__ __forceinline__ float sigmoidf_(float z) { return __frcp_rn(1.0f + __expf(-z)); }
+// Logistic function 1 / (1 + exp(-z)) from e = exp(-|z|) in (0, 1]: the
+// reciprocal of 1 + e in [1, 2] never meets an infinite or denormal operand
+// (1 + exp(-z) overflows for a drone far from a wall, z ~ -1000, and sends the
+// reciprocal down its slow special-value path).
+__device__ __forceinline__ float sigmoidf_(float z) {
+    const float e = __expf(-fabsf(z));
+    const float s = __frcp_rn(1.0f + e);
+    return z >= 0.0f ? s : e * s;
+}
 
 // Pairs farther apart than 2 l + 88 / beta have softplus_beta(2 l - d) below
 // exp(-88) / beta: their penalty and its derivatives vanish in binary32
-// sums of order-g accelerations, so they are skipped.
-__device__ __forceinline__ bool pair_far(float d2, float arm, float beta) {
+// sums of order-g accelerations, so they are skipped. The squared distance
+// beyond which a pair is skipped (formed once per drone, outside the pair loop):
+__device__ __forceinline__ float pair_far_d2(float arm, float beta) {
     const float r = 2.f * arm + 88.f / beta;
-    return d2 > r * r;
+    return r * r;
 }
 
-// Wall / floor / ceiling penalty acceleration and its diagonal derivative.
-__device__ __forceinline__ void wall_acc(const Consts& c, const float x[3], float acc[3], float dacc[3]) {
+// Diagonal derivative of the wall / floor / ceiling penalty acceleration
+// (the acceleration itself is the substep's).
+__device__ __forceinline__ void wall_dacc(const Consts& c, const float x[3], float dacc[3]) {
     const float kcg = c.kc * c.g, b = c.beta;
-    acc[0] = kcg * (softplus_b(-c.room_hx - x[0], b) - softplus_b(x[0] - c.room_hx, b));
-    acc[1] = kcg * (softplus_b(-c.room_hy - x[1], b) - softplus_b(x[1] - c.room_hy, b));
-    acc[2] = kcg * (softplus_b(-x[2], b) - softplus_b(x[2] - c.room_h, b));
     dacc[0] = -kcg * (sigmoidf_(b * (-c.room_hx - x[0])) + sigmoidf_(b * (x[0] - c.room_hx)));
     dacc[1] = -kcg * (sigmoidf_(b * (-c.room_hy - x[1])) + sigmoidf_(b * (x[1] - c.room_hy)));
     dacc[2] = -kcg * (sigmoidf_(-b * x[2]) + sigmoidf_(b * (x[2] - c.room_h)));
@@ -57,15 +64,15 @@ __device__ __forceinline__ void wall_acc(const Consts& c, const float x[3], floa
 __device__ __forceinline__ void pair_acc(const Consts& c, const float x[3], const float* sx, int nt, int sbase, int lane,
                                          int N, float arm, float out[3]) {
     out[0] = out[1] = out[2] = 0.f;
-    const float kcg = c.kc * c.g;
+    const float kcg = c.kc * c.g, far2 = pair_far_d2(arm, c.beta);
     for (int j = 0; j < N; ++j) {
         if (j == lane) continue;
         const int tj = sbase + j;
         const float r0 = x[0] - sx[tj], r1 = x[1] - sx[nt + tj], r2 = x[2] - sx[2 * nt + tj];
         const float d2 = r0 * r0 + r1 * r1 + r2 * r2;
-        if (d2 == 0.f || pair_far(d2, arm, c.beta)) continue;
+        if (d2 == 0.f || d2 > far2) continue;
         const float d = sqrtf(d2);
-        const float psi = kcg * softplus_b(2.f * arm - d, c.beta) * __frcp_rn(d);
+        const float psi = kcg * softplus_b(2.f * arm - d, c.beta, c.inv_beta) * __frcp_rn(d);
         out[0] = fmaf(psi, r0, out[0]);
         out[1] = fmaf(psi, r1, out[1]);
         out[2] = fmaf(psi, r2, out[2]);
@@ -75,16 +82,16 @@ __device__ __forceinline__ void pair_acc(const Consts& c, const float x[3], cons
 // lambda_x += sum_j J_ij (lam_a_i - lam_a_j)
 __device__ __forceinline__ void pair_vjp(const Consts& c, const float x[3], const float la[3], const float* sx,
                                          const float* sla, int nt, int sbase, int lane, int N, float arm, float lx[3]) {
-    const float kcg = c.kc * c.g, b = c.beta;
+    const float kcg = c.kc * c.g, b = c.beta, far2 = pair_far_d2(arm, c.beta);
     for (int j = 0; j < N; ++j) {
         if (j == lane) continue;
         const int tj = sbase + j;
         const float r0 = x[0] - sx[tj], r1 = x[1] - sx[nt + tj], r2 = x[2] - sx[2 * nt + tj];
         const float d2 = r0 * r0 + r1 * r1 + r2 * r2;
-        if (d2 == 0.f || pair_far(d2, arm, c.beta)) continue;
+        if (d2 == 0.f || d2 > far2) continue;
         const float d = sqrtf(d2), id = __frcp_rn(d);
         const float pen = 2.f * arm - d;
-        const float sp = softplus_b(pen, b), sg = sigmoidf_(b * pen);
+        const float sp = softplus_b(pen, b, c.inv_beta), sg = sigmoidf_(b * pen);
         const float psi = kcg * sp * id;
         const float dpsi = kcg * (-sg * id - sp * id * id);  // d psi / d d
         const float q0 = la[0] - sla[tj], q1 = la[1] - sla[nt + tj], q2 = la[2] - sla[2 * nt + tj];
@@ -102,8 +109,9 @@ __device__ __forceinline__ void rotation_vjp(const float R[9], const float w1[3]
     // M = R Q(w1)
     const float n2 = w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2];
     const float cc = __frsqrt_rn(fmaf(dt * dt, n2, 1.0f));
+    const float inv1c = __frcp_rn(1.0f + cc);  // 1 + c in (1, 2]: one reciprocal for both quotients below
     const float qa = dt * cc;
-    const float qb = dt * dt * cc * cc / (1.0f + cc);
+    const float qb = dt * dt * cc * cc * inv1c;
     // W = [w1]x, W2 = W W
     const float Wm[9] = {0.f, -w1[2], w1[1], w1[2], 0.f, -w1[0], -w1[1], w1[0], 0.f};
     float W2[9], Q[9], M[9];
@@ -186,7 +194,7 @@ __device__ __forceinline__ void rotation_vjp(const float R[9], const float w1[3]
     // a = dt c, b = dt^2 c^2 / (1 + c), c = (1 + dt^2 |w|^2)^(-1/2):
     // dc/dw = -dt^2 c^3 w, da/dw = dt dc/dw, db/dw = dt^2 c (2 + c) / (1 + c)^2 dc/dw
     const float dcs = -dt * dt * cc * cc * cc;
-    const float dadc = dt, dbdc = dt * dt * cc * (2.f + cc) / ((1.f + cc) * (1.f + cc));
+    const float dadc = dt, dbdc = dt * dt * cc * (2.f + cc) * inv1c * inv1c;
     for (int k = 0; k < 3; ++k)
         lw1[k] += qa * vG[k] + qb * vGW[k] + (gA * dadc + gB * dbdc) * dcs * w1[k];
     for (int k = 0; k < 9; ++k) lR[k] = lRin[k];
@@ -252,8 +260,8 @@ __device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const 
     lw[1] -= c1[1] + p.iyy * c2[1];
     lw[2] -= c1[2] + p.izz * c2[2];
     // a = T R e_z / m + g + wall(x) + pair: walls on the diagonal, thrust
-    float wacc[3], dwall[3];
-    wall_acc(c, s.x, wacc, dwall);
+    float dwall[3];
+    wall_dacc(c, s.x, dwall);
     for (int k = 0; k < 3; ++k) lx[k] += dwall[k] * la[k];
     const float b3[3] = {s.R[2], s.R[5], s.R[8]};
     const float lT = (la[0] * b3[0] + la[1] * b3[1] + la[2] * b3[2]) * p.inv_m;
@@ -602,7 +610,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
                     float ga[4];
                     for (int r = 0; r < 4; ++r) {
                         // u = sqrt(f^): du/df^ = 1 / (2u)
-                        const float du = u[r] > 0.f ? 0.5f / u[r] : 0.f;
+                        const float du = u[r] > 0.f ? 0.5f * __frcp_rn(u[r]) : 0.f;  // = 0.5 / u exactly
                         ga[r] = msk[r] * (lu[r] * du + dl * 2e-3f * fh[r]);
                     }
                     reinterpret_cast<float4*>(a.grad_act + (size_t)t * D * 4)[d] = make_float4(ga[0], ga[1], ga[2], ga[3]);
@@ -1331,7 +1339,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
                     }
                     float ga[4];
                     for (int r = 0; r < 4; ++r) {
-                        const float du = u[r] > 0.f ? 0.5f / u[r] : 0.f;
+                        const float du = u[r] > 0.f ? 0.5f * __frcp_rn(u[r]) : 0.f;  // = 0.5 / u exactly
                         ga[r] = msk[r] * (lu[r] * du + dl * 2e-3f * fh[r]);
                     }
                     reinterpret_cast<float4*>(a.grad_act + (size_t)t * D * 4)[d] = make_float4(ga[0], ga[1], ga[2], ga[3]);

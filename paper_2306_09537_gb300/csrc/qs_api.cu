@@ -128,6 +128,7 @@ void build_consts(qs_env* h) {
     c.room_hy = p.room_hy;
     c.room_h = p.room_h;
     c.beta = p.smooth_beta;
+    c.inv_beta = 1.0f / p.smooth_beta;
     c.kc = p.smooth_kc;
     c.omega_max = p.omega_max;
     c.ans_frac = p.alpha_ns_frac;

@@ -335,9 +335,9 @@ __device__ __forceinline__ float command(const Consts& c, float a) {
 // equals exp(z) / beta to binary32 precision (log1p(x) = x - x^2/2 + ...,
 // x < 1.2e-7), which the hardware exponential gives in a few instructions;
 // contact penalties far from any contact take that path.
-__device__ __forceinline__ float softplus_b(float u, float beta) {
+// ib = 1 / beta (Consts::inv_beta).
+__device__ __forceinline__ float softplus_b(float u, float beta, float ib) {
     const float z = beta * u;
-    const float ib = __frcp_rn(beta);
     if (z < -16.0f) return __expf(z) * ib;
     return (fmaxf(z, 0.0f) + log1pf(__expf(-fabsf(z)))) * ib;
 }
@@ -437,9 +437,10 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     bool on_floor = false, moving = false;
     if (c.flags & QS_F_SMOOTH) {
         const float kcg = c.kc * g;
-        a2 += kcg * (softplus_b(-s.x[2], c.beta) - softplus_b(s.x[2] - c.room_h, c.beta));
-        a0 += kcg * (softplus_b(-c.room_hx - s.x[0], c.beta) - softplus_b(s.x[0] - c.room_hx, c.beta));
-        a1 += kcg * (softplus_b(-c.room_hy - s.x[1], c.beta) - softplus_b(s.x[1] - c.room_hy, c.beta));
+        const float b = c.beta, ib = c.inv_beta;
+        a2 += kcg * (softplus_b(-s.x[2], b, ib) - softplus_b(s.x[2] - c.room_h, b, ib));
+        a0 += kcg * (softplus_b(-c.room_hx - s.x[0], b, ib) - softplus_b(s.x[0] - c.room_hx, b, ib));
+        a1 += kcg * (softplus_b(-c.room_hy - s.x[1], b, ib) - softplus_b(s.x[1] - c.room_hy, b, ib));
         a0 += pacc[0];
         a1 += pacc[1];
         a2 += pacc[2];

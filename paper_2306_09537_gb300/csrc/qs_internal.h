@@ -35,6 +35,7 @@ struct Consts {
     float obs_sx, obs_sv, obs_sw;
     float room_hx, room_hy, room_h;
     float beta, kc, omega_max, ans_frac, prox_factor, dr_lo, dr_hi;
+    float inv_beta;  // 1 / beta, rounded once on the host
     float dw_k1, dw_k2, dw_b1, dw_h, dw_sa, dw_sw;  // downwash
     // scenarios: enabled mask, goal spacing, circle radius cap, clearance,
     // shrink/expand minimum and period, Lissajous base frequency, Bezier
