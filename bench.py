@@ -36,8 +36,8 @@ METRIC = "quadrotor-steps/sec on 1 GB300 (plain vs batched vs fwd+adjoint), % of
 # launch), and the SHA-256 of the library sources that capture was taken on:
 # once the kernel sources change, the figure no longer describes the kernel
 # and the roofline's traffic is reported as null until it is captured again.
-HEADLINE_DRAM = {"bytes_per_launch": 2074795,
-                 "sources_sha256": "4c59cdd5a74a046577147f168d26bdca68fc68e524ba5a4a555b94042c626023",
+HEADLINE_DRAM = {"bytes_per_launch": 2075307,
+                 "sources_sha256": "acedc392046b2c18da616bdd0da579c376bc0256591b5cbcfb69bd061241e6e2",
                  "source": "profiles/k_step_ws_plain_8192x1.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
 UNIT = "quadrotor-steps/s"
 WL = W.PLAIN
@@ -584,6 +584,33 @@ def run_forms(dev, stream, seed):
                            "workspace_bytes": int(ws.numel()), "features": list(feats)}
             env.close()
             del acts, ws
+
+        # drone-count sweep of the smooth fwd + adjoint (swarms of 8, T = 128,
+        # checkpoints every 16): from latency-bound at 8,192 drones to full waves
+        sweep = []
+        for E in (1024, 8192, 32768):
+            env = QuadSwarmEnv(E, wl.swarm, wl.k_neighbors, wl.features, seed=seed, weights=wl.weights,
+                               device=dev, stream=stream)
+            env.reset(seed)
+            T, C = wl.horizon, wl.ckpt_every
+            x0 = env.get_state()["state"].contiguous()
+            acts = torch.from_numpy(W.actions(seed, T, env.D, lo=0.05, hi=0.95)).to(dev)
+            ws = torch.empty(qs.qs_diff_workspace_size(env.h, T, C), dtype=torch.uint8, device=dev)
+            loss = torch.empty(env.D, device=dev)
+            dl = torch.ones(env.D, device=dev)
+            ga = torch.empty_like(acts)
+            gx = torch.empty(env.D, 30, device=dev)
+
+            def fwd_bwd():
+                qs.qs_diff_forward(env.h, T, C, x0, acts, loss, ws)
+                qs.qs_diff_backward(env.h, T, C, acts, dl, ws, ga, gx)
+            fwd_bwd()
+            ms_fb = _events_ms(fwd_bwd, stream, reps=3, flush=flush)
+            sweep.append({"drones": env.D, "value": env.D * T / ms_fb * 1e3, "ms_per_rollout": ms_fb,
+                          "workspace_bytes": int(ws.numel())})
+            env.close()
+            del acts, ws, ga, gx
+        forms["fwd_adjoint_sweep"] = sweep
 
         # env-count sweep of the batched plain form (1 drone per env)
         sweep = []
