@@ -59,13 +59,26 @@ __device__ __forceinline__ uint32_t ctr_word(uint32_t tag, uint32_t sub, uint32_
 // (2k+1)/2^24 with k the top 23 bits: inside (0,1), exact in binary32.
 __device__ __forceinline__ float u01(uint32_t r) { return (float)(r >> 9) * (1.0f / 8388608.0f) + (1.0f / 16777216.0f); }
 
+// Square root by the hardware approximation (PTX sqrt.approx.f32): a couple
+// of instructions where the correctly rounded sqrtf takes a longer sequence
+// with a special-case branch. Its relative error (measured on GB300 over the
+// command range by tests/test_gpu_closed_forms.py) is a few units in the last
+// place at most, far inside every tolerance of the values it feeds: the
+// Box-Muller radius, the rotor-speed command sqrt(f^) and the reward's norms.
+// The differentiable rollout keeps sqrtf (its adjoint differentiates it).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Box-Muller: two N(0,1) from two uniforms, (rho cos 2 pi u1, rho sin 2 pi u1),
 // rho = sqrt(-2 ln u0). The angle is evaluated as 2 pi (u1 - 1/2) + pi, i.e.
 // cos(2 pi u1) = -cos(theta), sin(2 pi u1) = -sin(theta) with theta in (-pi, pi),
 // where the hardware sine/cosine is accurate to ~4e-7 absolute; the radius
 // keeps the accurate logarithm (u0 near 1 makes ln u0 tiny).
 __device__ __forceinline__ float2 box_muller(float u0, float u1) {
-    const float rho = sqrtf(-2.0f * logf(u0));
+    const float rho = sqrt_approx(-2.0f * logf(u0));
     float s, c;
     __sincosf(6.28318530717958648f * (u1 - 0.5f), &s, &c);
     return make_float2(-rho * c, -rho * s);

@@ -103,13 +103,13 @@ __device__ __forceinline__ void apply_downwash(const Consts& c, Drone& s, uint32
 __device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s, float prox, const float g[3],
                                                 const float fh[4], uint32_t ev, const uint64_t best[QS_MAX_K], int keff) {
     const float dgx = s.x[0] - g[0], dgy = s.x[1] - g[1], dgz = s.x[2] - g[2];
-    float r = c.w[QS_W_POS] * sqrtf(dgx * dgx + dgy * dgy + dgz * dgz);
-    r += c.w[QS_W_VEL] * sqrtf(s.v[0] * s.v[0] + s.v[1] * s.v[1] + s.v[2] * s.v[2]);
+    float r = c.w[QS_W_POS] * sqrt_approx(dgx * dgx + dgy * dgy + dgz * dgz);
+    r += c.w[QS_W_VEL] * sqrt_approx(s.v[0] * s.v[0] + s.v[1] * s.v[1] + s.v[2] * s.v[2]);
     r += c.w[QS_W_ORI] * s.R[8];
-    r += c.w[QS_W_SPIN] * sqrtf(s.w[0] * s.w[0] + s.w[1] * s.w[1] + s.w[2] * s.w[2]);
-    r += c.w[QS_W_ACT] * sqrtf(fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
+    r += c.w[QS_W_SPIN] * sqrt_approx(s.w[0] * s.w[0] + s.w[1] * s.w[1] + s.w[2] * s.w[2]);
+    r += c.w[QS_W_ACT] * sqrt_approx(fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
     const float q0 = fh[0] - s.fp[0], q1 = fh[1] - s.fp[1], q2 = fh[2] - s.fp[2], q3 = fh[3] - s.fp[3];
-    r += c.w[QS_W_DACT] * sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    r += c.w[QS_W_DACT] * sqrt_approx(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
     r += c.w[QS_W_ROT] * 0.5f * (s.R[0] + s.R[4] + s.R[8] - 1.0f);
     r += c.w[QS_W_YAW] * s.R[0];
     r += (ev & EV_HIT_FLOOR) ? c.w[QS_W_HIT_FLOOR] : 0.0f;
@@ -124,7 +124,7 @@ __device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s,
         for (int k = 0; k < QS_MAX_K; ++k) {
             if (k < keff) {
                 const float key = __uint_as_float((uint32_t)(best[k] >> 32));
-                near += fmaxf(1.0f - sqrtf(key) * inv_prox, 0.0f);
+                near += fmaxf(1.0f - sqrt_approx(key) * inv_prox, 0.0f);
             }
         }
         r += c.w[QS_W_NEAR] * near;
@@ -201,7 +201,7 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
         fh[1] = command(c, a.y);
         fh[2] = command(c, a.z);
         fh[3] = command(c, a.w);
-        const float u[4] = {sqrtf(fh[0]), sqrtf(fh[1]), sqrtf(fh[2]), sqrtf(fh[3])};
+        const float u[4] = {sqrt_approx(fh[0]), sqrt_approx(fh[1]), sqrt_approx(fh[2]), sqrt_approx(fh[3])};
         const float zero3[3] = {0.f, 0.f, 0.f};
         for (int sub = 0; sub < c.substeps; ++sub) ev |= substep(s, er.p, c, u, tick, d, sub, zero3);
     }
@@ -573,10 +573,10 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
         fh[1] = command(c, a.y);
         fh[2] = command(c, a.z);
         fh[3] = command(c, a.w);
-        u[0] = sqrtf(fh[0]);
-        u[1] = sqrtf(fh[1]);
-        u[2] = sqrtf(fh[2]);
-        u[3] = sqrtf(fh[3]);
+        u[0] = sqrt_approx(fh[0]);
+        u[1] = sqrt_approx(fh[1]);
+        u[2] = sqrt_approx(fh[2]);
+        u[3] = sqrt_approx(fh[3]);
     }
     if (b1) __syncthreads();  // B1: motor normals ready (the rollout's later steps: drawn before the last B2)
     if (act) {

@@ -189,3 +189,36 @@ def test_floor_hit_rests_upright_keeping_the_heading():
     heading = np.arctan2(R[:, 1, 0], R[:, 0, 0])
     assert np.abs(np.angle(np.exp(1j * (heading - yaw)))).max() <= 1e-5
     assert np.all((ev.cpu().numpy() & 1) != 0)  # hit_floor
+
+
+@pytest.mark.parametrize("form", ["step", "rollout"])
+def test_reward_action_term_square_root_error(form):
+    """With only the action weight set, the reward is the norm of the
+    normalised command (Sec. III-E); with one non-zero rotor command f per
+    drone that is sqrt(fl32(f^2)), which the step evaluates with the hardware
+    square-root approximation (as it does the rotor-speed command sqrt(f) and
+    the Box-Muller radius). Against the binary64 root of the same binary32
+    input its relative error stays within two units in the last place
+    (2^-22) over the command range, and the root of zero is zero."""
+    n = 65536
+    env = QuadSwarmEnv(n, 1, 0, (), seed=4, weights={"act": 1.0}, device=DEV)
+    env.reset(4)
+    rng = np.random.default_rng(4)
+    f = rng.uniform(0.0, 1.0, n).astype(np.float32)
+    f[:8] = [0.0, 1.0, 0.5, 0.25, 1e-6, 2.0 ** -20, 0.75, np.nextafter(np.float32(1), np.float32(0))]
+    acts = np.zeros((n, 4), np.float32)
+    acts[:, 0] = f
+    a = torch.from_numpy(acts).to(DEV)
+    if form == "step":
+        env.step(a)
+        r = env.reward.cpu().numpy().astype(np.float64)
+    else:
+        rew = torch.empty(1, n, device=DEV)
+        env.rollout(a[None], None, rew, None)
+        r = rew[0].cpu().numpy().astype(np.float64)
+    x = (f * f).astype(np.float64)  # fl32(f^2), correctly rounded by numpy
+    want = np.sqrt(x)
+    assert r[0] == 0.0
+    rel = np.abs(r[1:] - want[1:]) / want[1:]
+    print(f"max relative error {rel.max():.3e} = 2^{np.log2(rel.max()):.2f}")
+    assert rel.max() <= 2.0 ** -22
