@@ -377,7 +377,7 @@ __device__ __forceinline__ void smooth_substep(const Consts& c, Drone& s, const 
     float pa[3] = {0.f, 0.f, 0.f};
     if (act) pair_acc(c, s.x, sx, nt, sbase, lane, N, p.arm, pa);
     group_sync(bid, bn);
-    if (act) substep(s, p, c, u, tick, d, sub, pa, nrm);
+    if (act) substep<false, 1>(s, p, c, u, tick, d, sub, pa, nrm);
 }
 
 // The forward kernels run two groups of nb threads over the same drones: group
@@ -1210,7 +1210,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, con
                 float n[4];
                 if (ahead)
                     for (int r = 0; r < 4; ++r) n[r] = *fwd_normals(nbase, nb, t & 1, sub, r, lt);
-                substep<ET>(s, p, c, u, tick0 + t, d, sub, zero3, ahead ? n : nullptr);
+                substep<ET, 0>(s, p, c, u, tick0 + t, d, sub, zero3, ahead ? n : nullptr);
             }
         }
         if (coll && ET) discrete_collisions_et(c, s, p, tick0 + t, d, act, sm, sm + 3 * nt, nt, sbase, lane, N, lt, 1, nb);
@@ -1286,7 +1286,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
                     command4(c, a.act, D, t, d, fh, u, msk);
                     for (int sub = 0; sub < S; ++sub) {
                         save_sub(scr, D, (t - tb) * S1 + sub, d, s);
-                        substep<ET>(s, p, c, u, tick0 + t, d, sub, zero3);
+                        substep<ET, 0>(s, p, c, u, tick0 + t, d, sub, zero3);
                     }
                     save_sub(scr, D, (t - tb) * S1 + S, d, s);
                 }

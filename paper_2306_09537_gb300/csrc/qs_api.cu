@@ -49,6 +49,7 @@ struct qs_env {
     int ws_p = 0;  // 1 or 2 dynamics warps per CTA; 0: a class is wider than 64
     int diff_block = 32;
     int rollout_block = 128;  // or QS_BLOCK_WARP_SPECIALISED
+    bool single_drone = false;  // every env holds one drone (the single-drone rollout instance)
     int rollout_fuse = 0;   // control steps per launch (0: all T in one launch)
     int rollout_grid = 0;   // resident CTAs for rollout_block
     int use_graph = 1;
@@ -322,7 +323,8 @@ qs_status upload_tiles(qs_env* h) {
     h->n_dtiles = (int)n2;
     h->d_wtiles = h->d_tiles + n0 + n1 + n2;
     h->n_wtiles = (int)wtiles.size();
-    h->rollout_grid = rollout_grid(rblock, (h->c.scn_mask & ~1u) != 0 || (h->c.flags & QS_F_DOWNWASH) != 0);
+    h->single_drone = maxW == 1;
+    h->rollout_grid = rollout_grid(rblock, extended_instance(h->c), h->single_drone);
     return QS_OK;
 }
 
@@ -335,7 +337,7 @@ qs_status enqueue_rollout(qs_env* h, int T, const RolloutIO& io) {
                             ? launch_rollout_ws(h->c, h->dv, h->d_wtiles, h->n_wtiles, h->ws_p, h->d_perm, io, t0, n,
                                                 h->stream)
                             : launch_rollout(h->c, h->dv, h->d_rtiles, h->n_rtiles, h->rollout_block, h->d_perm,
-                                             h->d_counter, io, t0, n, h->rollout_grid, h->stream);
+                                             h->d_counter, io, t0, n, h->rollout_grid, h->single_drone, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "rollout launch");
     }
     return QS_OK;

@@ -412,9 +412,12 @@ __device__ __forceinline__ void motor_normals(const Consts& c, uint32_t tick, in
 // (nullptr: draw them here). ET: event-time contacts (QS_F_EVENT_TIME, the
 // differentiable rollout's variant): a floor, wall or ceiling contact is
 // resolved at its crossing time on the substep's straight path x0 + v1 s.
-template <bool ET = false>
+// SMC: the contact form, 0 discrete, 1 smooth (QS_F_SMOOTH) or -1 read from
+// the flags; a kernel that knows it compiles only that branch.
+template <bool ET = false, int SMC = -1>
 __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts& c, const float u[4], uint32_t tick,
                                             int d, int sub, const float pacc[3], const float* nrm = nullptr) {
+    const bool smooth = SMC < 0 ? (c.flags & QS_F_SMOOTH) != 0 : SMC > 0;
     uint32_t ev = 0;
     const float dt = c.dt, g = c.g;
     // S1 first-order motor lag on the normalised rotor speed
@@ -448,7 +451,7 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     const float F0 = s.R[2] * T, F1 = s.R[5] * T, F2 = s.R[8] * T;
     float a0 = F0 * p.inv_m, a1 = F1 * p.inv_m, a2 = fmaf(F2, p.inv_m, -g);
     bool on_floor = false, moving = false;
-    if (c.flags & QS_F_SMOOTH) {
+    if (smooth) {
         const float kcg = c.kc * g;
         const float b = c.beta, ib = c.inv_beta;
         a2 += kcg * (softplus_b(-s.x[2], b, ib) - softplus_b(s.x[2] - c.room_h, b, ib));
@@ -511,7 +514,7 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     }
     rotate_polar(s.R, s.w, dt);
 
-    if (c.flags & QS_F_SMOOTH) {
+    if (smooth) {
         if (s.x[2] < 0.0f) ev |= EV_HIT_FLOOR;
         if (s.x[2] > c.room_h) ev |= EV_HIT_CEIL;
         if (fabsf(s.x[0]) > c.room_hx || fabsf(s.x[1]) > c.room_hy) ev |= EV_HIT_WALL;

@@ -51,6 +51,13 @@ struct Consts {
     int substeps, K, episode_steps, obs_dim;
 };
 
+// Whether a handle runs the general instance of the step kernels (scenario
+// goals, downwash or smooth contacts, each decided at run time) rather than
+// the common one that compiles them out.
+inline bool extended_instance(const Consts& c) {
+    return (c.scn_mask & ~1u) != 0 || (c.flags & (QS_F_DOWNWASH | QS_F_SMOOTH)) != 0;
+}
+
 // Fills c.rk from c.key0 / c.key1 (Weyl increments 0x9E3779B9, 0xBB67AE85).
 inline void set_round_keys(Consts& c) {
     uint32_t k0 = c.key0, k1 = c.key1;
@@ -122,8 +129,10 @@ cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, con
                         const StepIO& io, int observe_only, cudaStream_t s);
 // Persistent launch over n_tiles tiles (any classes) of `block` threads;
 // steps t0 .. t0+nsteps-1 of the io buffers. grid <= 0: one CTA per tile.
+// single: every env of the handle holds one drone (the single-drone instance).
 cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int block, const int* perm,
-                           int* counter, const RolloutIO& io, int t0, int nsteps, int grid, cudaStream_t s);
+                           int* counter, const RolloutIO& io, int t0, int nsteps, int grid, bool single,
+                           cudaStream_t s);
 // Warp-specialised rollout: one CTA of 64P threads per tile of 32P drone
 // lanes, P = 1 (every class at most 32 wide) or 2 (at most 64 wide).
 cudaError_t launch_rollout_ws(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int P, const int* perm,
@@ -153,9 +162,10 @@ int serve_resident_ctas(const Consts& c, int P);
 // CTAs of the warp-specialised rollout (64P threads) the device keeps
 // resident at once.
 int rollout_ws_resident_ctas(const Consts& c, int P);
-// CTAs of `block` threads the device keeps resident at once for k_rollout
-// (the instance with or without scenarios and downwash).
-int rollout_grid(int block, bool extended);
+// CTAs of `block` threads the device keeps resident at once for the k_rollout
+// instance launch_rollout picks (extended: extended_instance(); single: one
+// drone per env).
+int rollout_grid(int block, bool extended, bool single);
 
 // differentiable rollout (qs_adjoint.cu)
 size_t diff_workspace_bytes(int D, int T, int C, int substeps);

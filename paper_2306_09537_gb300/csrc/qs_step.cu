@@ -29,9 +29,12 @@ constexpr int MAX_BLOCK = 256;
 constexpr int SMEM_PLANES = 7;
 
 // The step kernels come in two instances: EXT = true carries the training
-// scenarios (per-drone goals) and the downwash term, EXT = false neither, so
-// the common configuration keeps the smaller code and register budget.
-inline bool extended(const Consts& c) { return (c.scn_mask & ~1u) != 0 || (c.flags & QS_F_DOWNWASH) != 0; }
+// scenarios (per-drone goals), the downwash term and the smooth contacts,
+// deciding each at run time; EXT = false is the common configuration (one
+// goal, no downwash, the paper's discrete contacts) with these decided at
+// compile time, so it keeps the smaller code and register budget, and the
+// substep's contact branch is straight-line code (extended_instance()).
+inline bool extended(const Consts& c) { return extended_instance(c); }
 
 // Per-env values a thread keeps in registers.
 struct EnvRegs {
@@ -203,7 +206,7 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
         fh[3] = command(c, a.w);
         const float u[4] = {sqrt_approx(fh[0]), sqrt_approx(fh[1]), sqrt_approx(fh[2]), sqrt_approx(fh[3])};
         const float zero3[3] = {0.f, 0.f, 0.f};
-        for (int sub = 0; sub < c.substeps; ++sub) ev |= substep(s, er.p, c, u, tick, d, sub, zero3);
+        for (int sub = 0; sub < c.substeps; ++sub) ev |= substep<false, EXT ? -1 : 0>(s, er.p, c, u, tick, d, sub, zero3);
     }
 
     // ---- pair pass: collisions (S9, S10) and K nearest neighbours (S11)
@@ -224,7 +227,7 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
         bool responded = false, dw_hit = false;
         float dw_az = 0.f;
         if (act && N > 1) {
-            const bool coll = (c.flags & QS_F_COLLISIONS) && !(c.flags & QS_F_SMOOTH) && !observe_only;
+            const bool coll = (c.flags & QS_F_COLLISIONS) && !(EXT && (c.flags & QS_F_SMOOTH)) && !observe_only;
             const bool flag_coll = (c.flags & QS_F_COLLISIONS) && !observe_only;
             responded = pair_scan(c, s, er.p.thr, lane, N, sbase, sx, sv, nt, keff, coll, flag_coll, ev, best, dvs,
                                   dw && !observe_only, dw_az, dw_hit);
@@ -350,11 +353,13 @@ __global__ void __launch_bounds__(MAX_BLOCK, (W == 1 ? 3 : 1)) k_step(const Cons
     if (m.lane == 0) store_env<EXT>(er, dv, m.e);
 }
 
-// T steps of one tile with the state in registers.
-template <bool EXT>
+// T steps of one tile with the state in registers. W1: every tile of the
+// launch holds single-drone slots (a compile-time width of 1: no pair pass,
+// neighbour or staging code).
+template <bool EXT, bool W1>
 __device__ __forceinline__ void rollout_tile(const Consts& c, const Dev& dv, const Tile& tile, const int* __restrict__ perm,
                                              float* sm, const RolloutIO& io, int t0, int nsteps) {
-    const int W = tile.W;
+    const int W = W1 ? 1 : tile.W;
     const SlotMap m = map_slot(dv, tile, perm, W);
     Drone s;
     EnvRegs er;
@@ -384,8 +389,13 @@ __device__ __forceinline__ void rollout_tile(const Consts& c, const Dev& dv, con
 }
 
 // Persistent rollout: CTAs take tiles from *counter (zeroed before the launch)
-// until none is left. Tiles are ordered costliest first.
-template <bool EXT>
+// until none is left. Tiles are ordered costliest first. The W1 instance
+// (EXT = false only) serves handles whose envs all hold one drone: 107
+// registers instead of 121 and no untaken swarm code in the step loop (with
+// the smooth contacts compiled out of the EXT = false instances, batched
+// 1,048,576 single-drone envs went from 1.75e10 to 1.90e10 quadrotor-steps/s,
+// each change about half of it).
+template <bool EXT, bool W1>
 __global__ void __launch_bounds__(MAX_BLOCK, 2) k_rollout(const Consts c, const Dev dv, const Tile* __restrict__ tiles,
                                                        const int n_tiles, const int* __restrict__ perm,
                                                        int* __restrict__ counter, const RolloutIO io, const int t0,
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 2) k_rollout(const Consts c, const 
         const int ti = s_next;
         __syncthreads();  // everyone has read s_next before thread 0 overwrites it
         if (ti >= n_tiles) return;
-        rollout_tile<EXT>(c, dv, tile_at(dv, tiles, ti, blockDim.x), perm, sm, io, t0, nsteps);
+        rollout_tile<EXT, W1>(c, dv, tile_at(dv, tiles, ti, blockDim.x), perm, sm, io, t0, nsteps);
     }
 }
 
@@ -585,9 +595,9 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
             if (mnoise && sub < nahead) {
                 const float n[4] = {sh.nrm[nb][sub][0][L], sh.nrm[nb][sub][1][L], sh.nrm[nb][sub][2][L],
                                     sh.nrm[nb][sub][3][L]};
-                ev |= substep(s, er.p, c, u, er.tick, d, sub, zero3, n);
+                ev |= substep<false, EXT ? -1 : 0>(s, er.p, c, u, er.tick, d, sub, zero3, n);
             } else {
-                ev |= substep(s, er.p, c, u, er.tick, d, sub, zero3);
+                ev |= substep<false, EXT ? -1 : 0>(s, er.p, c, u, er.tick, d, sub, zero3);
             }
         }
     }
@@ -609,7 +619,7 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
         bool responded = false, dw_hit = false;
         float dw_az = 0.f;
         if (act && N > 1) {
-            const bool coll = (c.flags & QS_F_COLLISIONS) && !(c.flags & QS_F_SMOOTH);
+            const bool coll = (c.flags & QS_F_COLLISIONS) && !(EXT && (c.flags & QS_F_SMOOTH));
             const bool flag_coll = (c.flags & QS_F_COLLISIONS) != 0;
             responded = pair_scan(c, s, er.p.thr, lane, N, sbase, &sh.sx[0][0], &sh.sv[0][0], 32 * P, keff, coll,
                                   flag_coll, ev, best, dvs, dw, dw_az, dw_hit);
@@ -1065,14 +1075,19 @@ cudaError_t launch_step(const Consts& c, const Dev& dv, const ClassPlan& cp, con
                : launch_k_step<false>(c, dv, cp, t, perm, io, observe_only, smem, st);
 }
 
-int rollout_grid(int block, bool ext) {
+// The k_rollout instance for a handle: the general one, or without scenarios,
+// downwash and smooth contacts, and of those the single-drone one.
+const void* rollout_kernel(bool ext, bool single) {
+    if (ext) return (const void*)k_rollout<true, false>;
+    return single ? (const void*)k_rollout<false, true> : (const void*)k_rollout<false, false>;
+}
+
+int rollout_grid(int block, bool ext, bool single) {
     int dev = 0, n_sm = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (ext)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rollout<true>, block, sizeof(float) * SMEM_PLANES * block);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rollout<false>, block, sizeof(float) * SMEM_PLANES * block);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rollout_kernel(ext, single), block,
+                                                  sizeof(float) * SMEM_PLANES * block);
     return (occ > 0 ? occ : 1) * n_sm;
 }
 
@@ -1097,16 +1112,19 @@ cudaError_t launch_rollout_ws(const Consts& c, const Dev& dv, const Tile* tiles,
 }
 
 cudaError_t launch_rollout(const Consts& c, const Dev& dv, const Tile* tiles, int n_tiles, int block, const int* perm,
-                           int* counter, const RolloutIO& io, int t0, int nsteps, int grid, cudaStream_t st) {
+                           int* counter, const RolloutIO& io, int t0, int nsteps, int grid, bool single,
+                           cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(float) * SMEM_PLANES * block;
     const int g = grid > 0 ? grid : n_tiles;
     const int grid_n = g < n_tiles ? g : n_tiles;
     if (extended(c))
-        k_rollout<true><<<grid_n, block, smem, st>>>(c, dv, tiles, n_tiles, perm, counter, io, t0, nsteps);
+        k_rollout<true, false><<<grid_n, block, smem, st>>>(c, dv, tiles, n_tiles, perm, counter, io, t0, nsteps);
+    else if (single)
+        k_rollout<false, true><<<grid_n, block, smem, st>>>(c, dv, tiles, n_tiles, perm, counter, io, t0, nsteps);
     else
-        k_rollout<false><<<grid_n, block, smem, st>>>(c, dv, tiles, n_tiles, perm, counter, io, t0, nsteps);
+        k_rollout<false, false><<<grid_n, block, smem, st>>>(c, dv, tiles, n_tiles, perm, counter, io, t0, nsteps);
     return cudaGetLastError();
 }
 
