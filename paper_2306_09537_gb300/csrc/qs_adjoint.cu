@@ -31,13 +31,22 @@ namespace qsk {
 constexpr int ADJ_BLOCK_MAX = 256;
 constexpr int NSUB = 29;  // floats of a saved substep input: x v R w wlo uf eps
 
+// Reciprocal by the hardware approximation (PTX rcp.approx.f32, about one
+// unit in the last place): used only for quantities of the reverse pass,
+// whose tolerance is far above it; the forward keeps the correctly rounded
+// reciprocal, so the saved and recomputed states are unchanged.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Logistic function 1 / (1 + exp(-z)) from e = exp(-|z|) in (0, 1]: the
 // reciprocal of 1 + e in [1, 2] never meets an infinite or denormal operand
-// (1 + exp(-z) overflows for a drone far from a wall, z ~ -1000, and sends the
-// reciprocal down its slow special-value path).
+// (1 + exp(-z) overflows for a drone far from a wall, z ~ -1000).
 __device__ __forceinline__ float sigmoidf_(float z) {
     const float e = __expf(-fabsf(z));
-    const float s = __frcp_rn(1.0f + e);
+    const float s = rcp_approx(1.0f + e);
     return z >= 0.0f ? s : e * s;
 }
 
@@ -45,8 +54,8 @@ __device__ __forceinline__ float sigmoidf_(float z) {
 // exp(-88) / beta: their penalty and its derivatives vanish in binary32
 // sums of order-g accelerations, so they are skipped. The squared distance
 // beyond which a pair is skipped (formed once per drone, outside the pair loop):
-__device__ __forceinline__ float pair_far_d2(float arm, float beta) {
-    const float r = 2.f * arm + 88.f / beta;
+__device__ __forceinline__ float pair_far_d2(float arm, float inv_beta) {
+    const float r = 2.f * arm + 88.f * inv_beta;
     return r * r;
 }
 
@@ -64,7 +73,7 @@ __device__ __forceinline__ void wall_dacc(const Consts& c, const float x[3], flo
 __device__ __forceinline__ void pair_acc(const Consts& c, const float x[3], const float* sx, int nt, int sbase, int lane,
                                          int N, float arm, float out[3]) {
     out[0] = out[1] = out[2] = 0.f;
-    const float kcg = c.kc * c.g, far2 = pair_far_d2(arm, c.beta);
+    const float kcg = c.kc * c.g, far2 = pair_far_d2(arm, c.inv_beta);
     for (int j = 0; j < N; ++j) {
         if (j == lane) continue;
         const int tj = sbase + j;
@@ -82,14 +91,14 @@ __device__ __forceinline__ void pair_acc(const Consts& c, const float x[3], cons
 // lambda_x += sum_j J_ij (lam_a_i - lam_a_j)
 __device__ __forceinline__ void pair_vjp(const Consts& c, const float x[3], const float la[3], const float* sx,
                                          const float* sla, int nt, int sbase, int lane, int N, float arm, float lx[3]) {
-    const float kcg = c.kc * c.g, b = c.beta, far2 = pair_far_d2(arm, c.beta);
+    const float kcg = c.kc * c.g, b = c.beta, far2 = pair_far_d2(arm, c.inv_beta);
     for (int j = 0; j < N; ++j) {
         if (j == lane) continue;
         const int tj = sbase + j;
         const float r0 = x[0] - sx[tj], r1 = x[1] - sx[nt + tj], r2 = x[2] - sx[2 * nt + tj];
         const float d2 = r0 * r0 + r1 * r1 + r2 * r2;
         if (d2 == 0.f || d2 > far2) continue;
-        const float d = sqrtf(d2), id = __frcp_rn(d);
+        const float d = sqrtf(d2), id = rcp_approx(d);
         const float pen = 2.f * arm - d;
         const float sp = softplus_b(pen, b, c.inv_beta), sg = sigmoidf_(b * pen);
         const float psi = kcg * sp * id;
@@ -104,100 +113,91 @@ __device__ __forceinline__ void pair_vjp(const Consts& c, const float x[3], cons
 
 // Adjoint of R' = B(R Q(w1)) (Q the polar factor of I + dt [w1]x, B one
 // Bjorck step): lR holds lambda of R' on entry and lambda of R on return;
-// lw1 receives lambda of w1 (added to its entry value).
+// lw1 receives lambda of w1 (added to its entry value). The products are
+// written out with the identities of a skew matrix W = [w]x:
+// W^2 = w w^T - |w|^2 I, <G, W> = w . vex(G), <G, W^2> = w^T G w - |w|^2 tr G,
+// vex(-(G W + W G)) = (G + G^T) w - 2 tr(G) w, with
+// vex(X) = (X21 - X12, X02 - X20, X10 - X01); and for the Bjorck step
+// M L^T M + M M^T L = M (X + X^T), X = L^T M.
 __device__ __forceinline__ void rotation_vjp(const float R[9], const float w1[3], float dt, float lR[9], float lw1[3]) {
-    // M = R Q(w1)
-    const float n2 = w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2];
-    const float cc = __frsqrt_rn(fmaf(dt * dt, n2, 1.0f));
-    const float inv1c = __frcp_rn(1.0f + cc);  // 1 + c in (1, 2]: one reciprocal for both quotients below
+    const float w0 = w1[0], wy = w1[1], w2 = w1[2];
+    const float n2 = w0 * w0 + wy * wy + w2 * w2;
+    const float cc = rsqrtf(fmaf(dt * dt, n2, 1.0f));
+    const float inv1c = rcp_approx(1.0f + cc);  // 1 + c in (1, 2]: one reciprocal for both quotients below
     const float qa = dt * cc;
     const float qb = dt * dt * cc * cc * inv1c;
-    // W = [w1]x, W2 = W W
-    const float Wm[9] = {0.f, -w1[2], w1[1], w1[2], 0.f, -w1[0], -w1[1], w1[0], 0.f};
-    float W2[9], Q[9], M[9];
+    // Q = I + qa W + qb W^2
+    const float p01 = w0 * wy, p02 = w0 * w2, p12 = wy * w2;
+    const float Q[9] = {1.f + qb * (w0 * w0 - n2), qb * p01 - qa * w2,         qb * p02 + qa * wy,
+                        qb * p01 + qa * w2,         1.f + qb * (wy * wy - n2), qb * p12 - qa * w0,
+                        qb * p02 - qa * wy,         qb * p12 + qa * w0,         1.f + qb * (w2 * w2 - n2)};
+    // M = R Q
+    float M[9];
+#pragma unroll
     for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            float acc = 0.f;
-            for (int k = 0; k < 3; ++k) acc += Wm[3 * i + k] * Wm[3 * k + j];
-            W2[3 * i + j] = acc;
-            Q[3 * i + j] = (i == j ? 1.f : 0.f) + qa * Wm[3 * i + j] + qb * acc;
-        }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            float acc = 0.f;
-            for (int k = 0; k < 3; ++k) acc += R[3 * i + k] * Q[3 * k + j];
-            M[3 * i + j] = acc;
-        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i] * Q[j] + R[3 * i + 1] * Q[3 + j] + R[3 * i + 2] * Q[6 + j];
 
     // ---- reverse
-    // R' = B(M): G_M = 1.5 L - 0.5 (L S + M L^T M + M M^T L), S = M^T M
-    float S[9], MMt[9], GM[9];
+    // R' = B(M) = M (1.5 I - 0.5 S), S = M^T M:
+    // G_M = 1.5 L - 0.5 (L S + M (X + X^T)), X = L^T M
+    float S[9], Y[9];
+#pragma unroll
     for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            float a1 = 0.f, a2 = 0.f;
-            for (int k = 0; k < 3; ++k) {
-                a1 += M[3 * k + i] * M[3 * k + j];
-                a2 += M[3 * i + k] * M[3 * j + k];
-            }
-            S[3 * i + j] = a1;
-            MMt[3 * i + j] = a2;
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            S[3 * i + j] = M[i] * M[j] + M[3 + i] * M[3 + j] + M[6 + i] * M[6 + j];
+            S[3 * j + i] = S[3 * i + j];
         }
-    float LtM[9];  // L^T M
+    float X[9];
+#pragma unroll
     for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            float acc = 0.f;
-            for (int k = 0; k < 3; ++k) acc += lR[3 * k + i] * M[3 * k + j];
-            LtM[3 * i + j] = acc;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) X[3 * i + j] = lR[i] * M[j] + lR[3 + i] * M[3 + j] + lR[6 + i] * M[6 + j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            Y[3 * i + j] = X[3 * i + j] + X[3 * j + i];
+            Y[3 * j + i] = Y[3 * i + j];
         }
+    float GM[9];
+#pragma unroll
     for (int i = 0; i < 3; ++i)
+#pragma unroll
         for (int j = 0; j < 3; ++j) {
-            float t1 = 0.f, t2 = 0.f, t3 = 0.f;
-            for (int k = 0; k < 3; ++k) {
-                t1 += lR[3 * i + k] * S[3 * k + j];
-                t2 += M[3 * i + k] * LtM[3 * k + j];
-                t3 += MMt[3 * i + k] * lR[3 * k + j];
-            }
-            GM[3 * i + j] = 1.5f * lR[3 * i + j] - 0.5f * (t1 + t2 + t3);
+            float t = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) t += lR[3 * i + k] * S[3 * k + j] + M[3 * i + k] * Y[3 * k + j];
+            GM[3 * i + j] = 1.5f * lR[3 * i + j] - 0.5f * t;
         }
     // M = R Q: lambda_R = G_M Q^T, G_Q = R^T G_M
-    float GQ[9], lRin[9];
+    float GQ[9];
+#pragma unroll
     for (int i = 0; i < 3; ++i)
+#pragma unroll
         for (int j = 0; j < 3; ++j) {
-            float a1 = 0.f, a2 = 0.f;
-            for (int k = 0; k < 3; ++k) {
-                a1 += GM[3 * i + k] * Q[3 * j + k];
-                a2 += R[3 * k + i] * GM[3 * k + j];
-            }
-            lRin[3 * i + j] = a1;
-            GQ[3 * i + j] = a2;
+            lR[3 * i + j] = GM[3 * i] * Q[3 * j] + GM[3 * i + 1] * Q[3 * j + 1] + GM[3 * i + 2] * Q[3 * j + 2];
+            GQ[3 * i + j] = R[i] * GM[j] + R[3 + i] * GM[3 + j] + R[6 + i] * GM[6 + j];
         }
-    // Q(w1) = I + qa W + qb W^2: lambda_w1 from Q
-    //  <G, [dw]x> = dw . vex(G),  vex(G) = (G21 - G12, G02 - G20, G10 - G01)
-    //  <G, [dw]x W + W [dw]x> = dw . vex(-(G W) - (W G))   (W^T = -W)
-    float GW[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            float a1 = 0.f, a2 = 0.f;
-            for (int k = 0; k < 3; ++k) {
-                a1 += GQ[3 * i + k] * Wm[3 * k + j];
-                a2 += Wm[3 * i + k] * GQ[3 * k + j];
-            }
-            GW[3 * i + j] = -(a1 + a2);
-        }
+    // Q(w1) = I + qa W + qb W^2: lambda_w1 = qa vex(G_Q) + qb vex(-(G_Q W + W G_Q))
+    //   + (<G_Q, W> da/dc + <G_Q, W^2> db/dc) dc/dw
     const float vG[3] = {GQ[7] - GQ[5], GQ[2] - GQ[6], GQ[3] - GQ[1]};
-    const float vGW[3] = {GW[7] - GW[5], GW[2] - GW[6], GW[3] - GW[1]};
-    float gA = 0.f, gB = 0.f;
-    for (int k = 0; k < 9; ++k) {
-        gA += GQ[k] * Wm[k];
-        gB += GQ[k] * W2[k];
-    }
+    const float tr = GQ[0] + GQ[4] + GQ[8];
+    const float Gw[3] = {GQ[0] * w0 + GQ[1] * wy + GQ[2] * w2, GQ[3] * w0 + GQ[4] * wy + GQ[5] * w2,
+                         GQ[6] * w0 + GQ[7] * wy + GQ[8] * w2};
+    const float Gtw[3] = {GQ[0] * w0 + GQ[3] * wy + GQ[6] * w2, GQ[1] * w0 + GQ[4] * wy + GQ[7] * w2,
+                          GQ[2] * w0 + GQ[5] * wy + GQ[8] * w2};
+    const float gA = w0 * vG[0] + wy * vG[1] + w2 * vG[2];
+    const float gB = (w0 * Gw[0] + wy * Gw[1] + w2 * Gw[2]) - n2 * tr;
     // a = dt c, b = dt^2 c^2 / (1 + c), c = (1 + dt^2 |w|^2)^(-1/2):
     // dc/dw = -dt^2 c^3 w, da/dw = dt dc/dw, db/dw = dt^2 c (2 + c) / (1 + c)^2 dc/dw
     const float dcs = -dt * dt * cc * cc * cc;
     const float dadc = dt, dbdc = dt * dt * cc * (2.f + cc) * inv1c * inv1c;
+    const float gc = (gA * dadc + gB * dbdc) * dcs;
+#pragma unroll
     for (int k = 0; k < 3; ++k)
-        lw1[k] += qa * vG[k] + qb * vGW[k] + (gA * dadc + gB * dbdc) * dcs * w1[k];
-    for (int k = 0; k < 9; ++k) lR[k] = lRin[k];
+        lw1[k] += qa * vG[k] + qb * ((Gw[k] + Gtw[k]) - 2.f * tr * w1[k]) + gc * w1[k];
 }
 
 // Adjoint of the substep map of the smooth form. s: substep input (as saved);
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
                     float ga[4];
                     for (int r = 0; r < 4; ++r) {
                         // u = sqrt(f^): du/df^ = 1 / (2u)
-                        const float du = u[r] > 0.f ? 0.5f * __frcp_rn(u[r]) : 0.f;  // = 0.5 / u exactly
+                        const float du = u[r] > 0.f ? 0.5f * rcp_approx(u[r]) : 0.f;
                         ga[r] = msk[r] * (lu[r] * du + dl * 2e-3f * fh[r]);
                     }
                     reinterpret_cast<float4*>(a.grad_act + (size_t)t * D * 4)[d] = make_float4(ga[0], ga[1], ga[2], ga[3]);
@@ -1339,7 +1339,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
                     }
                     float ga[4];
                     for (int r = 0; r < 4; ++r) {
-                        const float du = u[r] > 0.f ? 0.5f * __frcp_rn(u[r]) : 0.f;  // = 0.5 / u exactly
+                        const float du = u[r] > 0.f ? 0.5f * rcp_approx(u[r]) : 0.f;
                         ga[r] = msk[r] * (lu[r] * du + dl * 2e-3f * fh[r]);
                     }
                     reinterpret_cast<float4*>(a.grad_act + (size_t)t * D * 4)[d] = make_float4(ga[0], ga[1], ga[2], ga[3]);
