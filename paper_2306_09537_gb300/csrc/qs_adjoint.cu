@@ -31,16 +31,6 @@ namespace qsk {
 constexpr int ADJ_BLOCK_MAX = 256;
 constexpr int NSUB = 29;  // floats of a saved substep input: x v R w wlo uf eps
 
-// Reciprocal by the hardware approximation (PTX rcp.approx.f32, about one
-// unit in the last place): used only for quantities of the reverse pass,
-// whose tolerance is far above it; the forward keeps the correctly rounded
-// reciprocal, so the saved and recomputed states are unchanged.
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // Logistic function 1 / (1 + exp(-z)) from e = exp(-|z|) in (0, 1]: the
 // reciprocal of 1 + e in [1, 2] never meets an infinite or denormal operand
 // (1 + exp(-z) overflows for a drone far from a wall, z ~ -1000).
@@ -427,7 +417,7 @@ __device__ __forceinline__ void command4(const Consts& c, const float* act, size
     const float av[4] = {a.x, a.y, a.z, a.w};
     for (int r = 0; r < 4; ++r) {
         fh[r] = command(c, av[r]);
-        u[r] = sqrtf(fh[r]);
+        u[r] = sqrt_approx(fh[r]);  // as the step computes it
         // d f^ / d a: 1 inside the clip range (1/2 for the symmetric map), 0 outside
         const bool in = (c.flags & QS_F_ACTION_SYMMETRIC) ? (av[r] > -1.f && av[r] < 1.f) : (av[r] > 0.f && av[r] < 1.f);
         msk[r] = in ? ((c.flags & QS_F_ACTION_SYMMETRIC) ? 0.5f : 1.f) : 0.f;

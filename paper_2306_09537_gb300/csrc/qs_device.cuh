@@ -65,10 +65,18 @@ __device__ __forceinline__ float u01(uint32_t r) { return (float)(r >> 9) * (1.0
 // command range by tests/test_gpu_closed_forms.py) is a few units in the last
 // place at most, far inside every tolerance of the values it feeds: the
 // Box-Muller radius, the rotor-speed command sqrt(f^) and the reward's norms.
-// The differentiable rollout keeps sqrtf (its adjoint differentiates it).
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
     asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Reciprocal by the hardware approximation (PTX rcp.approx.f32, about one
+// unit in the last place), where the correctly rounded __frcp_rn carries a
+// longer sequence with a special-case branch.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 
@@ -366,7 +374,7 @@ __device__ __forceinline__ void rotate_polar(float R[9], const float w[3], float
     float cc = rsqrtf(q);
     cc = cc * fmaf(-0.5f * q * cc, cc, 1.5f);  // one Newton step: ~1 ulp, no drift of the angle
     const float a = dt * cc;
-    const float b = dt * dt * cc * cc * __frcp_rn(1.0f + cc);
+    const float b = dt * dt * cc * cc * rcp_approx(1.0f + cc);  // 1 + c in (1, 2]
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
