@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_fwd(const Consts c, cons
     float g[3] = {0.f, 0.f, 0.f};
     if (act) {
         read_x0(s, a.x0, d);
-        p = load_prm(dv.prm, dv.E, e);
+        p = load_prm(c, dv.prm, dv.E, e);
         g[0] = dv.goal[e];
         g[1] = dv.goal[dv.E + e];
         g[2] = dv.goal[2 * dv.E + e];
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diff_bwd(const Consts c, cons
     uint32_t tick0 = 0;
     float dl = 0.f;
     if (act) {
-        p = load_prm(dv.prm, dv.E, e);
+        p = load_prm(c, dv.prm, dv.E, e);
         g[0] = dv.goal[e];
         g[1] = dv.goal[dv.E + e];
         g[2] = dv.goal[2 * dv.E + e];
@@ -1178,7 +1178,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_fwd(const Consts c, con
     float g[3] = {0.f, 0.f, 0.f};
     if (act) {
         read_x0(s, a.x0, d);
-        p = load_prm(dv.prm, dv.E, e);
+        p = load_prm(c, dv.prm, dv.E, e);
         g[0] = dv.goal[e];
         g[1] = dv.goal[dv.E + e];
         g[2] = dv.goal[2 * dv.E + e];
@@ -1247,7 +1247,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
     uint32_t tick0 = 0;
     float dl = 0.f;
     if (act) {
-        p = load_prm(dv.prm, dv.E, e);
+        p = load_prm(c, dv.prm, dv.E, e);
         g[0] = dv.goal[e];
         g[1] = dv.goal[dv.E + e];
         g[2] = dv.goal[2 * dv.E + e];

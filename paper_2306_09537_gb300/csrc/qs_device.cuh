@@ -108,43 +108,61 @@ struct Prm {
     float m, ixx, iyy, izz, t2w, tau, arm, fmax, alag, ans, inv_m, inv_ixx, inv_iyy, inv_izz, thr, prox;
 };
 
-// Derived constants of the randomised values: f_max = m g t2w / 4 (max thrust
-// per rotor), alpha_lag = 1 - exp(-dt / tau_m) (first-order lag whose 2%
-// settling time is tau_m ln 50), motor-noise scale, inverses, collision
-// threshold fl32((l + l)^2) and proximity radius prox_factor * l.
-__device__ __forceinline__ void derive(const Consts& c, const float p7[QS_PARAM_DIM], float out[NPRM_DEV]) {
-    for (int k = 0; k < QS_PARAM_DIM; ++k) out[k] = p7[k];
-    const float m = p7[P_M], arm = p7[P_ARM];
-    out[P_FMAX] = 0.25f * m * c.g * p7[P_T2W];
-    out[P_ALAG] = -expm1f(-c.dt / p7[P_TAU]);
-    out[P_ANS] = c.ans_frac * m * c.g * 0.25f;
-    out[P_INVM] = 1.0f / m;
-    out[P_INVIXX] = 1.0f / p7[P_IXX];
-    out[P_INVIYY] = 1.0f / p7[P_IYY];
-    out[P_INVIZZ] = 1.0f / p7[P_IZZ];
-    const float r = __fadd_rn(arm, arm);
-    out[P_THR] = __fmul_rn(r, r);
-    out[P_PROX] = c.prox_factor * arm;
+// The per-env constants a kernel forms from the randomised values as it loads
+// them: motor-noise scale a_ns = ans_frac m g / 4, the inverses of m and the
+// inertia diagonal (hardware reciprocals, about one unit in the last place),
+// the collision threshold fl32((l + l)^2) and the proximity radius
+// prox_factor * l. derive() stores the same values, so a kernel that loads
+// them and one that forms them agree bit for bit.
+__device__ __forceinline__ void complete_prm(const Consts& c, Prm& p) {
+    p.ans = c.ans_frac * p.m * c.g * 0.25f;
+    p.inv_m = rcp_approx(p.m);
+    p.inv_ixx = rcp_approx(p.ixx);
+    p.inv_iyy = rcp_approx(p.iyy);
+    p.inv_izz = rcp_approx(p.izz);
+    const float r = __fadd_rn(p.arm, p.arm);
+    p.thr = __fmul_rn(r, r);
+    p.prox = c.prox_factor * p.arm;
 }
 
-__device__ __forceinline__ Prm load_prm(const float* __restrict__ prm, int E, int e) {
+// Derived constants of the randomised values: f_max = m g t2w / 4 (max thrust
+// per rotor), alpha_lag = 1 - exp(-dt / tau_m) (first-order lag whose 2%
+// settling time is tau_m ln 50), and complete_prm()'s.
+__device__ __forceinline__ void derive(const Consts& c, const float p7[QS_PARAM_DIM], float out[NPRM_DEV]) {
+    for (int k = 0; k < QS_PARAM_DIM; ++k) out[k] = p7[k];
+    Prm q;
+    q.m = p7[P_M];
+    q.ixx = p7[P_IXX];
+    q.iyy = p7[P_IYY];
+    q.izz = p7[P_IZZ];
+    q.arm = p7[P_ARM];
+    complete_prm(c, q);
+    out[P_FMAX] = 0.25f * q.m * c.g * p7[P_T2W];
+    out[P_ALAG] = -expm1f(-c.dt / p7[P_TAU]);
+    out[P_ANS] = q.ans;
+    out[P_INVM] = q.inv_m;
+    out[P_INVIXX] = q.inv_ixx;
+    out[P_INVIYY] = q.inv_iyy;
+    out[P_INVIZZ] = q.inv_izz;
+    out[P_THR] = q.thr;
+    out[P_PROX] = q.prox;
+}
+
+// The 7 planes a step reads (m, inertia diagonal, arm, f_max, alpha_lag: 28 B
+// per env); the rest is formed by complete_prm(). t2w and tau_m enter only
+// through f_max and alpha_lag and are not loaded.
+__device__ __forceinline__ Prm load_prm(const Consts& c, const float* __restrict__ prm, int E, int e) {
     Prm p;
     p.m = __ldg(prm + P_M * E + e);
     p.ixx = __ldg(prm + P_IXX * E + e);
     p.iyy = __ldg(prm + P_IYY * E + e);
     p.izz = __ldg(prm + P_IZZ * E + e);
-    p.t2w = __ldg(prm + P_T2W * E + e);
-    p.tau = __ldg(prm + P_TAU * E + e);
     p.arm = __ldg(prm + P_ARM * E + e);
     p.fmax = __ldg(prm + P_FMAX * E + e);
     p.alag = __ldg(prm + P_ALAG * E + e);
-    p.ans = __ldg(prm + P_ANS * E + e);
-    p.inv_m = __ldg(prm + P_INVM * E + e);
-    p.inv_ixx = __ldg(prm + P_INVIXX * E + e);
-    p.inv_iyy = __ldg(prm + P_INVIYY * E + e);
-    p.inv_izz = __ldg(prm + P_INVIZZ * E + e);
-    p.thr = __ldg(prm + P_THR * E + e);
-    p.prox = __ldg(prm + P_PROX * E + e);
+    p.t2w = 0.f;
+    p.tau = 0.f;
+    complete_prm(c, p);
     return p;
 }
 

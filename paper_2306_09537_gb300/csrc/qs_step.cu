@@ -48,7 +48,7 @@ struct EnvRegs {
 
 template <bool EXT>
 __device__ __forceinline__ void load_env(EnvRegs& er, const Consts& c, const Dev& dv, int e) {
-    er.p = load_prm(dv.prm, dv.E, e);
+    er.p = load_prm(c, dv.prm, dv.E, e);
     er.g0 = dv.goal[e];
     er.g1 = dv.goal[dv.E + e];
     er.g2 = dv.goal[2 * dv.E + e];
