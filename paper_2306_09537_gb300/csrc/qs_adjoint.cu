@@ -40,15 +40,6 @@ __device__ __forceinline__ float sigmoidf_(float z) {
     return z >= 0.0f ? s : e * s;
 }
 
-// Pairs farther apart than 2 l + 88 / beta have softplus_beta(2 l - d) below
-// exp(-88) / beta: their penalty and its derivatives vanish in binary32
-// sums of order-g accelerations, so they are skipped. The squared distance
-// beyond which a pair is skipped (formed once per drone, outside the pair loop):
-__device__ __forceinline__ float pair_far_d2(float arm, float inv_beta) {
-    const float r = 2.f * arm + 88.f * inv_beta;
-    return r * r;
-}
-
 // Diagonal derivative of the wall / floor / ceiling penalty acceleration
 // (the acceleration itself is the substep's).
 __device__ __forceinline__ void wall_dacc(const Consts& c, const float x[3], float dacc[3]) {
@@ -56,26 +47,6 @@ __device__ __forceinline__ void wall_dacc(const Consts& c, const float x[3], flo
     dacc[0] = -kcg * (sigmoidf_(b * (-c.room_hx - x[0])) + sigmoidf_(b * (x[0] - c.room_hx)));
     dacc[1] = -kcg * (sigmoidf_(b * (-c.room_hy - x[1])) + sigmoidf_(b * (x[1] - c.room_hy)));
     dacc[2] = -kcg * (sigmoidf_(-b * x[2]) + sigmoidf_(b * (x[2] - c.room_h)));
-}
-
-// Smooth pair acceleration of the thread's drone from the slot's positions in
-// shared memory (sx[3][nt]); j == lane and coincident drones contribute 0.
-__device__ __forceinline__ void pair_acc(const Consts& c, const float x[3], const float* sx, int nt, int sbase, int lane,
-                                         int N, float arm, float out[3]) {
-    out[0] = out[1] = out[2] = 0.f;
-    const float kcg = c.kc * c.g, far2 = pair_far_d2(arm, c.inv_beta);
-    for (int j = 0; j < N; ++j) {
-        if (j == lane) continue;
-        const int tj = sbase + j;
-        const float r0 = x[0] - sx[tj], r1 = x[1] - sx[nt + tj], r2 = x[2] - sx[2 * nt + tj];
-        const float d2 = r0 * r0 + r1 * r1 + r2 * r2;
-        if (d2 == 0.f || d2 > far2) continue;
-        const float d = sqrtf(d2);
-        const float psi = kcg * softplus_b(2.f * arm - d, c.beta, c.inv_beta) * __frcp_rn(d);
-        out[0] = fmaf(psi, r0, out[0]);
-        out[1] = fmaf(psi, r1, out[1]);
-        out[2] = fmaf(psi, r2, out[2]);
-    }
 }
 
 // lambda_x += sum_j J_ij (lam_a_i - lam_a_j)

@@ -381,6 +381,35 @@ __device__ __forceinline__ float softplus_b(float u, float beta, float ib) {
     return (fmaxf(z, 0.0f) + log1pf(__expf(-fabsf(z)))) * ib;
 }
 
+// Pairs farther apart than 2 l + 88 / beta have softplus_beta(2 l - d) below
+// exp(-88) / beta: their penalty and its derivatives vanish in binary32
+// sums of order-g accelerations, so they are skipped. The squared distance
+// beyond which a pair is skipped (formed once per drone, outside the pair loop):
+__device__ __forceinline__ float pair_far_d2(float arm, float inv_beta) {
+    const float r = 2.f * arm + 88.f * inv_beta;
+    return r * r;
+}
+
+// Smooth pair acceleration of the thread's drone from the slot's positions in
+// shared memory (sx[3][nt]); j == lane and coincident drones contribute 0.
+__device__ __forceinline__ void pair_acc(const Consts& c, const float x[3], const float* sx, int nt, int sbase, int lane,
+                                         int N, float arm, float out[3]) {
+    out[0] = out[1] = out[2] = 0.f;
+    const float kcg = c.kc * c.g, far2 = pair_far_d2(arm, c.inv_beta);
+    for (int j = 0; j < N; ++j) {
+        if (j == lane) continue;
+        const int tj = sbase + j;
+        const float r0 = x[0] - sx[tj], r1 = x[1] - sx[nt + tj], r2 = x[2] - sx[2 * nt + tj];
+        const float d2 = r0 * r0 + r1 * r1 + r2 * r2;
+        if (d2 == 0.f || d2 > far2) continue;
+        const float d = sqrtf(d2);
+        const float psi = kcg * softplus_b(2.f * arm - d, c.beta, c.inv_beta) * __frcp_rn(d);
+        out[0] = fmaf(psi, r0, out[0]);
+        out[1] = fmaf(psi, r1, out[1]);
+        out[2] = fmaf(psi, r2, out[2]);
+    }
+}
+
 // R <- polar(R + dt R [w]x) for a rotation R. In closed form the polar factor
 // of I + dt [w]x is the rotation about w by atan(dt |w|), i.e.
 // Q = I + a [w]x + b [w]x^2 with c = 1/sqrt(1 + dt^2 |w|^2), a = dt c,

@@ -199,7 +199,31 @@ __device__ __forceinline__ void step_body(const int W, const Consts& c, const De
     uint32_t myk = 0;
     float fh[4] = {0.f, 0.f, 0.f, 0.f};
     uint32_t ev = 0;
-    if (act && !observe_only) {
+    // smooth contacts of a swarm (general instance): the pair penalty from the
+    // positions at each substep's start, staged like the pair pass (uniform
+    // over the CTA: every thread meets the barriers)
+    const bool spair = EXT && (c.flags & QS_F_SMOOTH) && W > 1 && !observe_only;
+    if (spair) {
+        if (act) {
+            fh[0] = command(c, a.x);
+            fh[1] = command(c, a.y);
+            fh[2] = command(c, a.z);
+            fh[3] = command(c, a.w);
+        }
+        const float u[4] = {sqrt_approx(fh[0]), sqrt_approx(fh[1]), sqrt_approx(fh[2]), sqrt_approx(fh[3])};
+        for (int sub = 0; sub < c.substeps; ++sub) {
+            float pacc[3] = {0.f, 0.f, 0.f};
+            if (act) {
+                sx[threadIdx.x] = s.x[0];
+                sx[nt + threadIdx.x] = s.x[1];
+                sx[2 * nt + threadIdx.x] = s.x[2];
+            }
+            __syncthreads();
+            if (act && N > 1) pair_acc(c, s.x, sx, nt, sbase, lane, N, er.p.arm, pacc);
+            __syncthreads();
+            if (act) ev |= substep<false, EXT ? -1 : 0>(s, er.p, c, u, tick, d, sub, pacc);
+        }
+    } else if (act && !observe_only) {
         fh[0] = command(c, a.x);
         fh[1] = command(c, a.y);
         fh[2] = command(c, a.z);
@@ -589,7 +613,31 @@ __device__ __forceinline__ void ws_dynamics_step(const Consts& c, const Dev& dv,
         u[3] = sqrt_approx(fh[3]);
     }
     if (b1) __syncthreads();  // B1: motor normals ready (the rollout's later steps: drawn before the last B2)
-    if (act) {
+    // smooth contacts of a swarm (general instance): the pair penalty from the
+    // positions at each substep's start, staged like the pair pass
+    const bool spair = EXT && (c.flags & QS_F_SMOOTH) && W > 1;
+    if (spair) {
+        for (int sub = 0; sub < c.substeps; ++sub) {
+            float pacc[3] = {0.f, 0.f, 0.f};
+            if (act) {
+                sh.sx[0][L] = s.x[0];
+                sh.sx[1][L] = s.x[1];
+                sh.sx[2][L] = s.x[2];
+            }
+            side_sync<P>(1);
+            if (act && N > 1) pair_acc(c, s.x, &sh.sx[0][0], 32 * P, sbase, lane, N, er.p.arm, pacc);
+            side_sync<P>(1);
+            if (act) {
+                if (mnoise && sub < nahead) {
+                    const float n[4] = {sh.nrm[nb][sub][0][L], sh.nrm[nb][sub][1][L], sh.nrm[nb][sub][2][L],
+                                        sh.nrm[nb][sub][3][L]};
+                    ev |= substep<false, EXT ? -1 : 0>(s, er.p, c, u, er.tick, d, sub, pacc, n);
+                } else {
+                    ev |= substep<false, EXT ? -1 : 0>(s, er.p, c, u, er.tick, d, sub, pacc);
+                }
+            }
+        }
+    } else if (act) {
         const float zero3[3] = {0.f, 0.f, 0.f};
         for (int sub = 0; sub < c.substeps; ++sub) {
             if (mnoise && sub < nahead) {

@@ -121,6 +121,11 @@ def test_reset_matches_oracle(sizes, K):
     ("k_gt_n", [2, 3, 4] * 40, 8, FULL),
     ("symmetric_actions", [4] * 100, 3, FULL + ("action_symmetric",)),
     ("no_noise_no_dr", [8] * 100, 6, ("floor", "walls", "collisions", "record_knn")),
+    # smooth contacts (the differentiable form) stepped by the general instance:
+    # wall and floor penalties, and the pair penalty of swarms in every substep
+    ("smooth_single", [1] * 300, 0, ("smooth", "dr", "motor_noise", "obs_noise")),
+    ("smooth_swarm8", [8] * 200, 6, ("smooth", "dr", "motor_noise", "obs_noise", "collisions", "record_knn")),
+    ("smooth_uneven", [1, 2, 3, 8, 17, 33, 64] * 4, 6, ("smooth", "dr", "motor_noise", "collisions", "record_knn")),
 ])
 def test_single_step_parity(name, sizes, K, features):
     # 100+ drones packed into 0.24 m would all touch; spread large swarms wider
@@ -375,6 +380,20 @@ def test_rollout_equals_steps():
     size, auto-reset crossing episode boundaries) reproduces T per-call steps."""
     sizes = [1, 2, 8, 64, 3, 33, 16, 5, 128] * 6
     _, _, ro, ref, (s1, s2), (ev1, ev2) = _rollout_vs_steps(sizes, 6, 12)
+    for a, b in zip(ro, ref):
+        assert torch.equal(a, b)
+    for k in ("state", "params", "goals", "ep_step", "tick"):
+        assert torch.equal(s1[k], s2[k]), k
+    assert torch.equal(ev1, ev2)
+
+
+@pytest.mark.parametrize("sizes", [[8] * 64, [1, 2, 8, 33, 64, 5] * 6])
+def test_smooth_rollout_equals_steps(sizes):
+    """A smooth-contact handle (the general instance, with the pair penalty
+    staged in every substep) gives the same bits in the rollout and in
+    per-call steps, through the warp-specialised and the persistent kernels."""
+    feats = ("smooth", "dr", "motor_noise", "obs_noise", "collisions", "auto_reset")
+    _, acts, ro, ref, (s1, s2), (ev1, ev2) = _rollout_vs_steps(sizes, 6, 10, feats=feats, seed=9)
     for a, b in zip(ro, ref):
         assert torch.equal(a, b)
     for k in ("state", "params", "goals", "ep_step", "tick"):
