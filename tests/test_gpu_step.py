@@ -126,6 +126,12 @@ def test_reset_matches_oracle(sizes, K):
     ("smooth_single", [1] * 300, 0, ("smooth", "dr", "motor_noise", "obs_noise")),
     ("smooth_swarm8", [8] * 200, 6, ("smooth", "dr", "motor_noise", "obs_noise", "collisions", "record_knn")),
     ("smooth_uneven", [1, 2, 3, 8, 17, 33, 64] * 4, 6, ("smooth", "dr", "motor_noise", "collisions", "record_knn")),
+    # further feature combinations: each contact rule alone, neighbours without
+    # collisions, and the smooth contacts with downwash (general instance)
+    ("floor_only", [1] * 300, 0, ("floor", "dr", "motor_noise")),
+    ("walls_only", [4] * 100, 3, ("walls", "dr", "collisions", "record_knn")),
+    ("knn_without_collisions", [8] * 100, 6, ("floor", "walls", "obs_noise", "record_knn")),
+    ("smooth_downwash", [8] * 100, 6, ("smooth", "dr", "motor_noise", "downwash", "collisions", "record_knn")),
 ])
 def test_single_step_parity(name, sizes, K, features):
     # 100+ drones packed into 0.24 m would all touch; spread large swarms wider
