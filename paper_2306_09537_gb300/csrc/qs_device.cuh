@@ -185,10 +185,11 @@ __device__ __forceinline__ void draw_env(const Consts& c, uint32_t k0, uint32_t 
     const float u[10] = {u01(a.x), u01(a.y), u01(a.z), u01(a.w), u01(b.x), u01(b.y), u01(b.z), u01(b.w),
                          u01(d.x), u01(d.y)};
     const bool dr = (c.flags & QS_F_DR) != 0;
-    for (int k = 0; k < QS_PARAM_DIM; ++k) p7[k] = dr ? c.nominal[k] * (c.dr_lo + (c.dr_hi - c.dr_lo) * u[k]) : c.nominal[k];
-    goal[0] = -c.room_hx + 2.0f * c.room_hx * u[7];
-    goal[1] = -c.room_hy + 2.0f * c.room_hy * u[8];
-    goal[2] = c.room_h * u[9];
+    for (int k = 0; k < QS_PARAM_DIM; ++k)
+        p7[k] = dr ? __fmul_rn(c.nominal[k], __fmaf_rn(__fsub_rn(c.dr_hi, c.dr_lo), u[k], c.dr_lo)) : c.nominal[k];
+    goal[0] = __fmaf_rn(__fmul_rn(2.0f, c.room_hx), u[7], -c.room_hx);
+    goal[1] = __fmaf_rn(__fmul_rn(2.0f, c.room_hy), u[8], -c.room_hy);
+    goal[2] = __fmul_rn(c.room_h, u[9]);
 }
 
 // ---------------------------------------------------------------- drone state
@@ -296,11 +297,35 @@ __device__ __forceinline__ SlotGeo slot_geometry(const Dev& dv, const int* __res
     return g;
 }
 
+// The step's arithmetic is written with explicit roundings (__fmul_rn,
+// __fadd_rn, __fmaf_rn): the compiler fuses a multiply and an add into one
+// rounding only inside a basic block, so with implicit contraction the same
+// source could round differently in the per-call, rollout, warp-specialised
+// and server kernels that inline it; with explicit roundings every kernel
+// gives the same bits by construction.
+// a0 b0 + a1 b1 + a2 b2 as fma(a2, b2, fma(a1, b1, a0 b0)).
+__device__ __forceinline__ float dot3(float a0, float a1, float a2, float b0, float b1, float b2) {
+    return __fmaf_rn(a2, b2, __fmaf_rn(a1, b1, __fmul_rn(a0, b0)));
+}
+// a b - c d as fma(-c, d, a b).
+__device__ __forceinline__ float cross_c(float a, float b, float c, float d) {
+    return __fmaf_rn(-c, d, __fmul_rn(a, b));
+}
+
 // hi + lo <- hi + lo + delta, keeping the rounding error of the sum in lo.
 __device__ __forceinline__ void comp_add(float& hi, float& lo, float delta) {
-    const float y = delta + lo;
-    const float t = hi + y;
-    lo = y - (t - hi);
+    const float y = __fadd_rn(delta, lo);
+    const float t = __fadd_rn(hi, y);
+    lo = __fsub_rn(y, __fsub_rn(t, hi));
+    hi = t;
+}
+
+// hi + lo <- hi + lo + a b, the product entering with the low word in one
+// rounding.
+__device__ __forceinline__ void comp_add_prod(float& hi, float& lo, float a, float b) {
+    const float y = __fmaf_rn(a, b, lo);
+    const float t = __fadd_rn(hi, y);
+    lo = __fsub_rn(y, __fsub_rn(t, hi));
     hi = t;
 }
 
@@ -326,27 +351,27 @@ __device__ __forceinline__ void draw_drone(const Consts& c, uint32_t k0, uint32_
     const uint4 a = philox(tick, (uint32_t)d, ctr_word(tag, 0, 0), k0, k1);
     const uint4 b = philox(tick, (uint32_t)d, ctr_word(tag, 0, 1), k0, k1);
     const uint4 q = philox(tick, (uint32_t)d, ctr_word(tag, 0, 2), k0, k1);
-    s.x[0] = -c.room_hx + 2.0f * c.room_hx * u01(a.x);
-    s.x[1] = -c.room_hy + 2.0f * c.room_hy * u01(a.y);
-    s.x[2] = c.room_h * u01(a.z);
-    s.v[0] = -1.0f + 2.0f * u01(a.w);
-    s.v[1] = -1.0f + 2.0f * u01(b.x);
-    s.v[2] = -1.0f + 2.0f * u01(b.y);
+    s.x[0] = __fmaf_rn(__fmul_rn(2.0f, c.room_hx), u01(a.x), -c.room_hx);
+    s.x[1] = __fmaf_rn(__fmul_rn(2.0f, c.room_hy), u01(a.y), -c.room_hy);
+    s.x[2] = __fmul_rn(c.room_h, u01(a.z));
+    s.v[0] = __fmaf_rn(2.0f, u01(a.w), -1.0f);
+    s.v[1] = __fmaf_rn(2.0f, u01(b.x), -1.0f);
+    s.v[2] = __fmaf_rn(2.0f, u01(b.y), -1.0f);
     const float u6 = u01(b.z), u7 = u01(b.w), u8 = u01(q.x);
     const float ra = sqrtf(1.0f - u6), rb = sqrtf(u6);
     float s7, c7, s8, c8;
     sincospif(2.0f * u7, &s7, &c7);
     sincospif(2.0f * u8, &s8, &c8);
     const float qx = ra * s7, qy = ra * c7, qz = rb * s8, qw = rb * c8;
-    s.R[0] = 1.0f - 2.0f * (qy * qy + qz * qz);
-    s.R[1] = 2.0f * (qx * qy - qz * qw);
-    s.R[2] = 2.0f * (qx * qz + qy * qw);
-    s.R[3] = 2.0f * (qx * qy + qz * qw);
-    s.R[4] = 1.0f - 2.0f * (qx * qx + qz * qz);
-    s.R[5] = 2.0f * (qy * qz - qx * qw);
-    s.R[6] = 2.0f * (qx * qz - qy * qw);
-    s.R[7] = 2.0f * (qy * qz + qx * qw);
-    s.R[8] = 1.0f - 2.0f * (qx * qx + qy * qy);
+    s.R[0] = __fmaf_rn(-2.0f, __fmaf_rn(qz, qz, __fmul_rn(qy, qy)), 1.0f);
+    s.R[1] = __fmul_rn(2.0f, cross_c(qx, qy, qz, qw));
+    s.R[2] = __fmul_rn(2.0f, __fmaf_rn(qy, qw, __fmul_rn(qx, qz)));
+    s.R[3] = __fmul_rn(2.0f, __fmaf_rn(qz, qw, __fmul_rn(qx, qy)));
+    s.R[4] = __fmaf_rn(-2.0f, __fmaf_rn(qz, qz, __fmul_rn(qx, qx)), 1.0f);
+    s.R[5] = __fmul_rn(2.0f, cross_c(qy, qz, qx, qw));
+    s.R[6] = __fmul_rn(2.0f, cross_c(qx, qz, qy, qw));
+    s.R[7] = __fmul_rn(2.0f, __fmaf_rn(qx, qw, __fmul_rn(qy, qz)));
+    s.R[8] = __fmaf_rn(-2.0f, __fmaf_rn(qy, qy, __fmul_rn(qx, qx)), 1.0f);
     s.w[0] = -1.0f + 2.0f * u01(q.y);
     s.w[1] = -1.0f + 2.0f * u01(q.z);
     s.w[2] = -1.0f + 2.0f * u01(q.w);
@@ -374,11 +399,14 @@ __device__ __forceinline__ float command(const Consts& c, float a) {
 // equals exp(z) / beta to binary32 precision (log1p(x) = x - x^2/2 + ...,
 // x < 1.2e-7), which the hardware exponential gives in a few instructions;
 // contact penalties far from any contact take that path.
-// ib = 1 / beta (Consts::inv_beta).
+// ib = 1 / beta (Consts::inv_beta). The smooth-contact arithmetic is written
+// with explicit roundings (__fmul_rn, __fadd_rn, __fmaf_rn) so that no kernel's
+// compiler fuses it differently: every kernel that steps the smooth form
+// gives the same bits.
 __device__ __forceinline__ float softplus_b(float u, float beta, float ib) {
-    const float z = beta * u;
-    if (z < -16.0f) return __expf(z) * ib;
-    return (fmaxf(z, 0.0f) + log1pf(__expf(-fabsf(z)))) * ib;
+    const float z = __fmul_rn(beta, u);
+    if (z < -16.0f) return __fmul_rn(__expf(z), ib);
+    return __fmul_rn(__fadd_rn(fmaxf(z, 0.0f), log1pf(__expf(-fabsf(z)))), ib);
 }
 
 // Pairs farther apart than 2 l + 88 / beta have softplus_beta(2 l - d) below
@@ -395,15 +423,15 @@ __device__ __forceinline__ float pair_far_d2(float arm, float inv_beta) {
 __device__ __forceinline__ void pair_acc(const Consts& c, const float x[3], const float* sx, int nt, int sbase, int lane,
                                          int N, float arm, float out[3]) {
     out[0] = out[1] = out[2] = 0.f;
-    const float kcg = c.kc * c.g, far2 = pair_far_d2(arm, c.inv_beta);
+    const float kcg = __fmul_rn(c.kc, c.g), far2 = pair_far_d2(arm, c.inv_beta);
     for (int j = 0; j < N; ++j) {
         if (j == lane) continue;
         const int tj = sbase + j;
         const float r0 = x[0] - sx[tj], r1 = x[1] - sx[nt + tj], r2 = x[2] - sx[2 * nt + tj];
-        const float d2 = r0 * r0 + r1 * r1 + r2 * r2;
+        const float d2 = __fmaf_rn(r2, r2, __fmaf_rn(r1, r1, __fmul_rn(r0, r0)));
         if (d2 == 0.f || d2 > far2) continue;
         const float d = sqrtf(d2);
-        const float psi = kcg * softplus_b(2.f * arm - d, c.beta, c.inv_beta) * __frcp_rn(d);
+        const float psi = __fmul_rn(__fmul_rn(kcg, softplus_b(__fsub_rn(2.f * arm, d), c.beta, c.inv_beta)), __frcp_rn(d));
         out[0] = fmaf(psi, r0, out[0]);
         out[1] = fmaf(psi, r1, out[1]);
         out[2] = fmaf(psi, r2, out[2]);
@@ -416,37 +444,37 @@ __device__ __forceinline__ void pair_acc(const Consts& c, const float x[3], cons
 // b = dt^2 c^2 / (1 + c); row_i(R [w]x) = row_i(R) x w. One Bjorck step
 // R <- R (3I - R^T R) / 2 then removes the binary32 drift of R itself.
 __device__ __forceinline__ void rotate_polar(float R[9], const float w[3], float dt) {
-    const float n2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    const float q = fmaf(dt * dt, n2, 1.0f);
+    const float n2 = dot3(w[0], w[1], w[2], w[0], w[1], w[2]);
+    const float q = __fmaf_rn(__fmul_rn(dt, dt), n2, 1.0f);
     float cc = rsqrtf(q);
-    cc = cc * fmaf(-0.5f * q * cc, cc, 1.5f);  // one Newton step: ~1 ulp, no drift of the angle
-    const float a = dt * cc;
-    const float b = dt * dt * cc * cc * rcp_approx(1.0f + cc);  // 1 + c in (1, 2]
+    cc = __fmul_rn(cc, __fmaf_rn(__fmul_rn(__fmul_rn(-0.5f, q), cc), cc, 1.5f));  // one Newton step: ~1 ulp
+    const float a = __fmul_rn(dt, cc);
+    const float b = __fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(dt, dt), cc), cc), rcp_approx(__fadd_rn(1.0f, cc)));
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
-        const float t0 = r1 * w[2] - r2 * w[1], t1 = r2 * w[0] - r0 * w[2], t2 = r0 * w[1] - r1 * w[0];
-        const float q0 = t1 * w[2] - t2 * w[1], q1 = t2 * w[0] - t0 * w[2], q2 = t0 * w[1] - t1 * w[0];
-        R[3 * i] = fmaf(b, q0, fmaf(a, t0, r0));
-        R[3 * i + 1] = fmaf(b, q1, fmaf(a, t1, r1));
-        R[3 * i + 2] = fmaf(b, q2, fmaf(a, t2, r2));
+        const float t0 = cross_c(r1, w[2], r2, w[1]), t1 = cross_c(r2, w[0], r0, w[2]), t2 = cross_c(r0, w[1], r1, w[0]);
+        const float q0 = cross_c(t1, w[2], t2, w[1]), q1 = cross_c(t2, w[0], t0, w[2]), q2 = cross_c(t0, w[1], t1, w[0]);
+        R[3 * i] = __fmaf_rn(b, q0, __fmaf_rn(a, t0, r0));
+        R[3 * i + 1] = __fmaf_rn(b, q1, __fmaf_rn(a, t1, r1));
+        R[3 * i + 2] = __fmaf_rn(b, q2, __fmaf_rn(a, t2, r2));
     }
     // one Bjorck step: S = R^T R; R <- R (1.5 I - 0.5 S)
     float S[6];  // 00 01 02 11 12 22
-    S[0] = R[0] * R[0] + R[3] * R[3] + R[6] * R[6];
-    S[1] = R[0] * R[1] + R[3] * R[4] + R[6] * R[7];
-    S[2] = R[0] * R[2] + R[3] * R[5] + R[6] * R[8];
-    S[3] = R[1] * R[1] + R[4] * R[4] + R[7] * R[7];
-    S[4] = R[1] * R[2] + R[4] * R[5] + R[7] * R[8];
-    S[5] = R[2] * R[2] + R[5] * R[5] + R[8] * R[8];
-    const float A00 = 1.5f - 0.5f * S[0], A11 = 1.5f - 0.5f * S[3], A22 = 1.5f - 0.5f * S[5];
-    const float A01 = -0.5f * S[1], A02 = -0.5f * S[2], A12 = -0.5f * S[4];
+    S[0] = dot3(R[0], R[3], R[6], R[0], R[3], R[6]);
+    S[1] = dot3(R[0], R[3], R[6], R[1], R[4], R[7]);
+    S[2] = dot3(R[0], R[3], R[6], R[2], R[5], R[8]);
+    S[3] = dot3(R[1], R[4], R[7], R[1], R[4], R[7]);
+    S[4] = dot3(R[1], R[4], R[7], R[2], R[5], R[8]);
+    S[5] = dot3(R[2], R[5], R[8], R[2], R[5], R[8]);
+    const float A00 = __fmaf_rn(-0.5f, S[0], 1.5f), A11 = __fmaf_rn(-0.5f, S[3], 1.5f), A22 = __fmaf_rn(-0.5f, S[5], 1.5f);
+    const float A01 = __fmul_rn(-0.5f, S[1]), A02 = __fmul_rn(-0.5f, S[2]), A12 = __fmul_rn(-0.5f, S[4]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
-        R[3 * i] = r0 * A00 + r1 * A01 + r2 * A02;
-        R[3 * i + 1] = r0 * A01 + r1 * A11 + r2 * A12;
-        R[3 * i + 2] = r0 * A02 + r1 * A12 + r2 * A22;
+        R[3 * i] = dot3(r0, r1, r2, A00, A01, A02);
+        R[3 * i + 1] = dot3(r0, r1, r2, A01, A11, A12);
+        R[3 * i + 2] = dot3(r0, r1, r2, A02, A12, A22);
     }
 }
 
@@ -506,52 +534,54 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     const float F0 = s.R[2] * T, F1 = s.R[5] * T, F2 = s.R[8] * T;
     float a0 = F0 * p.inv_m, a1 = F1 * p.inv_m, a2 = fmaf(F2, p.inv_m, -g);
     bool on_floor = false, moving = false;
-    if (smooth) {
-        const float kcg = c.kc * g;
+    if (smooth) {  // explicit roundings (see softplus_b)
+        const float kcg = __fmul_rn(c.kc, g);
         const float b = c.beta, ib = c.inv_beta;
-        a2 += kcg * (softplus_b(-s.x[2], b, ib) - softplus_b(s.x[2] - c.room_h, b, ib));
-        a0 += kcg * (softplus_b(-c.room_hx - s.x[0], b, ib) - softplus_b(s.x[0] - c.room_hx, b, ib));
-        a1 += kcg * (softplus_b(-c.room_hy - s.x[1], b, ib) - softplus_b(s.x[1] - c.room_hy, b, ib));
-        a0 += pacc[0];
-        a1 += pacc[1];
-        a2 += pacc[2];
+        const float pz = __fsub_rn(softplus_b(-s.x[2], b, ib), softplus_b(__fsub_rn(s.x[2], c.room_h), b, ib));
+        const float px = __fsub_rn(softplus_b(__fsub_rn(-c.room_hx, s.x[0]), b, ib),
+                                   softplus_b(__fsub_rn(s.x[0], c.room_hx), b, ib));
+        const float py = __fsub_rn(softplus_b(__fsub_rn(-c.room_hy, s.x[1]), b, ib),
+                                   softplus_b(__fsub_rn(s.x[1], c.room_hy), b, ib));
+        a2 = __fadd_rn(__fmaf_rn(kcg, pz, a2), pacc[2]);
+        a0 = __fadd_rn(__fmaf_rn(kcg, px, a0), pacc[0]);
+        a1 = __fadd_rn(__fmaf_rn(kcg, py, a1), pacc[1]);
     } else if ((c.flags & QS_F_FLOOR) && s.x[2] <= 0.0f) {
-        const float mg = p.m * g;
+        const float mg = __fmul_rn(p.m, g);
         if (F2 < mg) {
             // resting on the floor: friction mu (m g - F_z) against the motion
             on_floor = true;
             ev |= EV_ON_FLOOR;
-            const float ffric = c.mu * (mg - F2);
+            const float ffric = __fmul_rn(c.mu, __fsub_rn(mg, F2));
             float fx = F0, fy = F1;
             if (s.v[0] == 0.0f && s.v[1] == 0.0f) {
-                const float nf = sqrtf(fx * fx + fy * fy);
-                const float keep = nf > ffric ? (nf - ffric) * __frcp_rn(nf) : 0.0f;
-                fx *= keep;
-                fy *= keep;
+                const float nf = sqrtf(__fmaf_rn(fy, fy, __fmul_rn(fx, fx)));
+                const float keep = nf > ffric ? __fmul_rn(__fsub_rn(nf, ffric), __frcp_rn(nf)) : 0.0f;
+                fx = __fmul_rn(fx, keep);
+                fy = __fmul_rn(fy, keep);
             } else {
-                const float inv_nv = rsqrtf(s.v[0] * s.v[0] + s.v[1] * s.v[1]);
-                fx -= ffric * s.v[0] * inv_nv;
-                fy -= ffric * s.v[1] * inv_nv;
+                const float inv_nv = rsqrtf(__fmaf_rn(s.v[1], s.v[1], __fmul_rn(s.v[0], s.v[0])));
+                fx = __fmaf_rn(-__fmul_rn(ffric, s.v[0]), inv_nv, fx);
+                fy = __fmaf_rn(-__fmul_rn(ffric, s.v[1]), inv_nv, fy);
                 moving = true;
             }
-            a0 = fx * p.inv_m;
-            a1 = fy * p.inv_m;
+            a0 = __fmul_rn(fx, p.inv_m);
+            a1 = __fmul_rn(fy, p.inv_m);
             a2 = 0.0f;
             s.v[2] = 0.0f;
         }
     }
     // S5 Euler's equation, diagonal inertia
-    const float Iw0 = p.ixx * s.w[0], Iw1 = p.iyy * s.w[1], Iw2 = p.izz * s.w[2];
-    const float wd0 = (tx - (s.w[1] * Iw2 - s.w[2] * Iw1)) * p.inv_ixx;
-    const float wd1 = (ty - (s.w[2] * Iw0 - s.w[0] * Iw2)) * p.inv_iyy;
-    const float wd2 = (tz - (s.w[0] * Iw1 - s.w[1] * Iw0)) * p.inv_izz;
+    const float Iw0 = __fmul_rn(p.ixx, s.w[0]), Iw1 = __fmul_rn(p.iyy, s.w[1]), Iw2 = __fmul_rn(p.izz, s.w[2]);
+    const float wd0 = __fmul_rn(__fsub_rn(tx, cross_c(s.w[1], Iw2, s.w[2], Iw1)), p.inv_ixx);
+    const float wd1 = __fmul_rn(__fsub_rn(ty, cross_c(s.w[2], Iw0, s.w[0], Iw2)), p.inv_iyy);
+    const float wd2 = __fmul_rn(__fsub_rn(tz, cross_c(s.w[0], Iw1, s.w[1], Iw0)), p.inv_izz);
     // S6 semi-implicit Euler, body rates bounded by omega_max
     const float vx0 = s.v[0], vy0 = s.v[1];
     const float x0[3] = {s.x[0], s.x[1], s.x[2]};  // substep start (event-time contacts)
     s.v[0] = fmaf(a0, dt, s.v[0]);
     s.v[1] = fmaf(a1, dt, s.v[1]);
     s.v[2] = fmaf(a2, dt, s.v[2]);
-    if (on_floor && moving && (s.v[0] * vx0 + s.v[1] * vy0) < 0.0f) {
+    if (on_floor && moving && __fmaf_rn(s.v[1], vy0, __fmul_rn(s.v[0], vx0)) < 0.0f) {
         s.v[0] = 0.0f;
         s.v[1] = 0.0f;
     }
@@ -561,7 +591,7 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     const float wd[3] = {wd0, wd1, wd2};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        comp_add(s.w[k], s.wlo[k], wd[k] * dt);
+        comp_add_prod(s.w[k], s.wlo[k], wd[k], dt);
         if (fabsf(s.w[k]) > c.omega_max) {
             s.w[k] = copysignf(c.omega_max, s.w[k]);
             s.wlo[k] = 0.0f;
@@ -590,13 +620,13 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
             s.wlo[k] = 0.0f;
         }
         float cs, sn;
-        const float h2 = s.R[0] * s.R[0] + s.R[3] * s.R[3];
+        const float h2 = __fmaf_rn(s.R[3], s.R[3], __fmul_rn(s.R[0], s.R[0]));
         if (h2 >= 1e-12f) {
             const float ih = rsqrtf(h2);
             cs = s.R[0] * ih;
             sn = s.R[3] * ih;
         } else {
-            const float ih = rsqrtf(s.R[1] * s.R[1] + s.R[4] * s.R[4]);
+            const float ih = rsqrtf(__fmaf_rn(s.R[4], s.R[4], __fmul_rn(s.R[1], s.R[1])));
             cs = s.R[4] * ih;
             sn = -s.R[1] * ih;
         }
@@ -639,7 +669,7 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
             six_normals(c, tick, (uint32_t)d, TAG_WALL, (uint32_t)sub, n);
             for (int k = 0; k < 3; ++k) {
                 s.v[k] = c.alpha_c * fmaf(c.sig_cv, n[k], s.v[k]);
-                comp_add(s.w[k], s.wlo[k], c.sig_cw * n[3 + k]);
+                comp_add_prod(s.w[k], s.wlo[k], c.sig_cw, n[3 + k]);
             }
             if (ET) {  // pre-contact velocity until tau, post-contact for the rest
                 tau = fmaxf(tau, 0.0f);
@@ -692,7 +722,7 @@ __device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float
         // downwash: j overlaps this drone from above (horizontal distance below
         // l_i + l_j, height difference in (0, dw_h))
         if (dw && __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) < thr && dz > 0.0f && dz < c.dw_h) {
-            dw_az -= c.dw_k1 * fmaf(c.dw_k2, dz, c.dw_b1);
+            dw_az = __fmaf_rn(-c.dw_k1, __fmaf_rn(c.dw_k2, dz, c.dw_b1), dw_az);
             dw_hit = true;
         }
         if (flag_coll && key < thr) {
@@ -700,7 +730,7 @@ __device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float
             if (coll) {
                 // approaching iff (v_i - v_j) . (x_i - x_j) < 0
                 const float rv0 = s.v[0] - sv[tj], rv1 = s.v[1] - sv[nt + tj], rv2 = s.v[2] - sv[2 * nt + tj];
-                const float app = -(rv0 * dx + rv1 * dy + rv2 * dz);
+                const float app = -dot3(rv0, rv1, rv2, dx, dy, dz);
                 if (app < 0.0f) {
                     float n0 = 0.f, n1 = 0.f, n2 = 1.f;
                     if (key > 0.0f) {
@@ -709,7 +739,7 @@ __device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float
                         n1 = -dy * inv;
                         n2 = -dz * inv;
                     }
-                    const float vn = -(rv0 * n0 + rv1 * n1 + rv2 * n2);  // (v_j - v_i) . n
+                    const float vn = -dot3(rv0, rv1, rv2, n0, n1, n2);  // (v_j - v_i) . n
                     dvs[0] = fmaf(vn, n0, dvs[0]);
                     dvs[1] = fmaf(vn, n1, dvs[1]);
                     dvs[2] = fmaf(vn, n2, dvs[2]);
@@ -726,12 +756,12 @@ __device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float
 __device__ __forceinline__ void apply_response(const Consts& c, Drone& s, uint32_t tick, int d, const float dvs[3]) {
     float n[6];
     six_normals(c, tick, (uint32_t)d, TAG_COLL, 0, n);
-    s.v[0] = c.alpha_c * (s.v[0] + dvs[0] + c.sig_cv * n[0]);
-    s.v[1] = c.alpha_c * (s.v[1] + dvs[1] + c.sig_cv * n[1]);
-    s.v[2] = c.alpha_c * (s.v[2] + dvs[2] + c.sig_cv * n[2]);
-    comp_add(s.w[0], s.wlo[0], c.sig_cw * n[3]);
-    comp_add(s.w[1], s.wlo[1], c.sig_cw * n[4]);
-    comp_add(s.w[2], s.wlo[2], c.sig_cw * n[5]);
+    s.v[0] = __fmul_rn(c.alpha_c, __fmaf_rn(c.sig_cv, n[0], __fadd_rn(s.v[0], dvs[0])));
+    s.v[1] = __fmul_rn(c.alpha_c, __fmaf_rn(c.sig_cv, n[1], __fadd_rn(s.v[1], dvs[1])));
+    s.v[2] = __fmul_rn(c.alpha_c, __fmaf_rn(c.sig_cv, n[2], __fadd_rn(s.v[2], dvs[2])));
+    comp_add_prod(s.w[0], s.wlo[0], c.sig_cw, n[3]);
+    comp_add_prod(s.w[1], s.wlo[1], c.sig_cw, n[4]);
+    comp_add_prod(s.w[2], s.wlo[2], c.sig_cw, n[5]);
 }
 
 // Sensor noise of the observation (Sec. III-C): U(-s,s) on x and v, N(0,s^2)

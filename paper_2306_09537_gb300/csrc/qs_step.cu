@@ -93,33 +93,38 @@ __device__ __forceinline__ void apply_downwash(const Consts& c, Drone& s, uint32
     float n[6];
     six_normals(c, tick, (uint32_t)d, TAG_DOWNWASH, 0, n);
     const float Tc = c.dt * (float)c.substeps;
-    s.v[0] = fmaf(Tc, c.dw_sa * n[0], s.v[0]);
-    s.v[1] = fmaf(Tc, c.dw_sa * n[1], s.v[1]);
+    s.v[0] = __fmaf_rn(Tc, __fmul_rn(c.dw_sa, n[0]), s.v[0]);
+    s.v[1] = __fmaf_rn(Tc, __fmul_rn(c.dw_sa, n[1]), s.v[1]);
     s.v[2] = fmaf(Tc, fmaf(c.dw_sa, n[2], az), s.v[2]);
-    comp_add(s.w[0], s.wlo[0], Tc * c.dw_sw * n[3]);
-    comp_add(s.w[1], s.wlo[1], Tc * c.dw_sw * n[4]);
-    comp_add(s.w[2], s.wlo[2], Tc * c.dw_sw * n[5]);
+    const float tsw = __fmul_rn(Tc, c.dw_sw);
+    comp_add_prod(s.w[0], s.wlo[0], tsw, n[3]);
+    comp_add_prod(s.w[1], s.wlo[1], tsw, n[4]);
+    comp_add_prod(s.w[2], s.wlo[2], tsw, n[5]);
 }
 
 // S13 reward of one drone (Sec. III-E): weighted state terms, event indicators
 // and the proximity term over its neighbours (keys = squared distances).
 __device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s, float prox, const float g[3],
                                                 const float fh[4], uint32_t ev, const uint64_t best[QS_MAX_K], int keff) {
-    const float dgx = s.x[0] - g[0], dgy = s.x[1] - g[1], dgz = s.x[2] - g[2];
-    float r = c.w[QS_W_POS] * sqrt_approx(dgx * dgx + dgy * dgy + dgz * dgz);
-    r += c.w[QS_W_VEL] * sqrt_approx(s.v[0] * s.v[0] + s.v[1] * s.v[1] + s.v[2] * s.v[2]);
-    r += c.w[QS_W_ORI] * s.R[8];
-    r += c.w[QS_W_SPIN] * sqrt_approx(s.w[0] * s.w[0] + s.w[1] * s.w[1] + s.w[2] * s.w[2]);
-    r += c.w[QS_W_ACT] * sqrt_approx(fh[0] * fh[0] + fh[1] * fh[1] + fh[2] * fh[2] + fh[3] * fh[3]);
-    const float q0 = fh[0] - s.fp[0], q1 = fh[1] - s.fp[1], q2 = fh[2] - s.fp[2], q3 = fh[3] - s.fp[3];
-    r += c.w[QS_W_DACT] * sqrt_approx(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
-    r += c.w[QS_W_ROT] * 0.5f * (s.R[0] + s.R[4] + s.R[8] - 1.0f);
-    r += c.w[QS_W_YAW] * s.R[0];
-    r += (ev & EV_HIT_FLOOR) ? c.w[QS_W_HIT_FLOOR] : 0.0f;
-    r += (ev & EV_ON_FLOOR) ? c.w[QS_W_ON_FLOOR] : 0.0f;
-    r += (ev & EV_HIT_WALL) ? c.w[QS_W_HIT_WALL] : 0.0f;
-    r += (ev & EV_HIT_CEIL) ? c.w[QS_W_HIT_CEIL] : 0.0f;
-    r += (ev & EV_HIT_QUAD) ? c.w[QS_W_HIT_QUAD] : 0.0f;
+    // explicit roundings: the same bits from every kernel that computes it
+    const float dgx = __fsub_rn(s.x[0], g[0]), dgy = __fsub_rn(s.x[1], g[1]), dgz = __fsub_rn(s.x[2], g[2]);
+    float r = __fmul_rn(c.w[QS_W_POS], sqrt_approx(dot3(dgx, dgy, dgz, dgx, dgy, dgz)));
+    r = __fmaf_rn(c.w[QS_W_VEL], sqrt_approx(dot3(s.v[0], s.v[1], s.v[2], s.v[0], s.v[1], s.v[2])), r);
+    r = __fmaf_rn(c.w[QS_W_ORI], s.R[8], r);
+    r = __fmaf_rn(c.w[QS_W_SPIN], sqrt_approx(dot3(s.w[0], s.w[1], s.w[2], s.w[0], s.w[1], s.w[2])), r);
+    const float na = __fmaf_rn(fh[3], fh[3], dot3(fh[0], fh[1], fh[2], fh[0], fh[1], fh[2]));
+    r = __fmaf_rn(c.w[QS_W_ACT], sqrt_approx(na), r);
+    const float q0 = __fsub_rn(fh[0], s.fp[0]), q1 = __fsub_rn(fh[1], s.fp[1]), q2 = __fsub_rn(fh[2], s.fp[2]),
+                q3 = __fsub_rn(fh[3], s.fp[3]);
+    r = __fmaf_rn(c.w[QS_W_DACT], sqrt_approx(__fmaf_rn(q3, q3, dot3(q0, q1, q2, q0, q1, q2))), r);
+    const float tr = __fsub_rn(__fadd_rn(__fadd_rn(s.R[0], s.R[4]), s.R[8]), 1.0f);
+    r = __fmaf_rn(__fmul_rn(c.w[QS_W_ROT], 0.5f), tr, r);
+    r = __fmaf_rn(c.w[QS_W_YAW], s.R[0], r);
+    r = __fadd_rn(r, (ev & EV_HIT_FLOOR) ? c.w[QS_W_HIT_FLOOR] : 0.0f);
+    r = __fadd_rn(r, (ev & EV_ON_FLOOR) ? c.w[QS_W_ON_FLOOR] : 0.0f);
+    r = __fadd_rn(r, (ev & EV_HIT_WALL) ? c.w[QS_W_HIT_WALL] : 0.0f);
+    r = __fadd_rn(r, (ev & EV_HIT_CEIL) ? c.w[QS_W_HIT_CEIL] : 0.0f);
+    r = __fadd_rn(r, (ev & EV_HIT_QUAD) ? c.w[QS_W_HIT_QUAD] : 0.0f);
     if (keff > 0 && c.w[QS_W_NEAR] != 0.0f) {
         float near = 0.0f;
         const float inv_prox = __frcp_rn(prox);
@@ -127,10 +132,10 @@ __device__ __forceinline__ float compute_reward(const Consts& c, const Drone& s,
         for (int k = 0; k < QS_MAX_K; ++k) {
             if (k < keff) {
                 const float key = __uint_as_float((uint32_t)(best[k] >> 32));
-                near += fmaxf(1.0f - sqrt_approx(key) * inv_prox, 0.0f);
+                near = __fadd_rn(near, fmaxf(__fmaf_rn(-sqrt_approx(key), inv_prox, 1.0f), 0.0f));
             }
         }
-        r += c.w[QS_W_NEAR] * near;
+        r = __fmaf_rn(c.w[QS_W_NEAR], near, r);
     }
     return r;
 }

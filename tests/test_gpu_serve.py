@@ -101,6 +101,13 @@ def test_serve_equals_steps_uneven_with_scenarios_and_downwash():
                    feats=FEATS + ("downwash",))
 
 
+def test_serve_equals_steps_smooth_swarms():
+    """Smooth contacts (the general instance, the pair penalty staged before
+    every substep by one or two dynamics warps)."""
+    serve_vs_steps([8, 33, 64, 2, 17] * 8, 6, 10, feats=("smooth", "motor_noise", "obs_noise", "dr", "collisions",
+                                                        "auto_reset"))
+
+
 def test_serve_command_slots():
     """Commands written ahead into slots, stepped in a shuffled slot order."""
     a, b = twins([8] * 128, 6)

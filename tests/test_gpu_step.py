@@ -393,13 +393,17 @@ def test_rollout_equals_steps():
     assert torch.equal(ev1, ev2)
 
 
-@pytest.mark.parametrize("sizes", [[8] * 64, [1, 2, 8, 33, 64, 5] * 6])
-def test_smooth_rollout_equals_steps(sizes):
+@pytest.mark.parametrize("sizes,ws", [([8] * 64, False), ([1, 2, 8, 33, 64, 5] * 6, False),
+                                      ([1, 2, 8, 33, 64, 5] * 6, True)])
+def test_smooth_rollout_equals_steps(sizes, ws):
     """A smooth-contact handle (the general instance, with the pair penalty
     staged in every substep) gives the same bits in the rollout and in
-    per-call steps, through the warp-specialised and the persistent kernels."""
+    per-call steps, through the warp-specialised kernels (one or two dynamics
+    warps per CTA) and the persistent one."""
+    from paper_2306_09537_gb300 import qs
     feats = ("smooth", "dr", "motor_noise", "obs_noise", "collisions", "auto_reset")
-    _, acts, ro, ref, (s1, s2), (ev1, ev2) = _rollout_vs_steps(sizes, 6, 10, feats=feats, seed=9)
+    shape = (qs.QS_BLOCK_WARP_SPECIALISED, 0, 1) if ws else None
+    _, acts, ro, ref, (s1, s2), (ev1, ev2) = _rollout_vs_steps(sizes, 6, 10, shape=shape, feats=feats, seed=9)
     for a, b in zip(ro, ref):
         assert torch.equal(a, b)
     for k in ("state", "params", "goals", "ep_step", "tick"):
