@@ -89,6 +89,16 @@ __device__ __forceinline__ void formation_offset(const Consts& c, int form, int 
     }
 }
 
+// A coordinate uniform in [-h + m, h - m] (a room half-width h, clearance m)
+// and a height uniform in [m, h - m], with explicit roundings so that every
+// kernel that draws a record gives the same bits.
+__device__ __forceinline__ float in_box(float h, float m, float u) {
+    return __fmaf_rn(__fmul_rn(2.0f, __fsub_rn(h, m)), u, __fadd_rn(-h, m));
+}
+__device__ __forceinline__ float in_height(float h, float m, float u) {
+    return __fmaf_rn(__fsub_rn(h, __fmul_rn(2.0f, m)), u, m);
+}
+
 // Scenario record of env e after a reset: five Philox blocks at (tick, e,
 // tag << 16 | block) under key (k0, k1). Type uniform over the enabled ones;
 // formations uniform over the five; switch step uniform in [T/4, 3T/4] (T the
@@ -142,12 +152,12 @@ __device__ __forceinline__ void draw_scenario(const Consts& c, uint32_t k0, uint
         rec[QS_R_PHASE + 1] = u01(b4.y);
         rec[QS_R_PHASE + 2] = u01(b4.z);
     } else {
-        rec[QS_R_C0 + 0] = -hx + m + 2.0f * (hx - m) * u01(b1.x);
-        rec[QS_R_C0 + 1] = -hy + m + 2.0f * (hy - m) * u01(b1.y);
-        rec[QS_R_C0 + 2] = m + (hz - 2.0f * m) * u01(b1.z);
-        rec[QS_R_C1 + 0] = -hx + m + 2.0f * (hx - m) * u01(b2.x);
-        rec[QS_R_C1 + 1] = -hy + m + 2.0f * (hy - m) * u01(b2.y);
-        rec[QS_R_C1 + 2] = m + (hz - 2.0f * m) * u01(b2.z);
+        rec[QS_R_C0 + 0] = in_box(hx, m, u01(b1.x));
+        rec[QS_R_C0 + 1] = in_box(hy, m, u01(b1.y));
+        rec[QS_R_C0 + 2] = in_height(hz, m, u01(b1.z));
+        rec[QS_R_C1 + 0] = in_box(hx, m, u01(b2.x));
+        rec[QS_R_C1 + 1] = in_box(hy, m, u01(b2.y));
+        rec[QS_R_C1 + 2] = in_height(hz, m, u01(b2.z));
     }
 }
 
@@ -177,9 +187,9 @@ __device__ __forceinline__ uint32_t swap_key(const Consts& c, uint32_t seed, int
 __device__ __forceinline__ void waypoint(const Consts& c, uint32_t seed, int j, float w[3]) {
     const uint4 r = philox_rk(seed, (uint32_t)(j + 1), TAG_WAYPOINT << 16, c.rk);
     const float m = c.scn_m;
-    w[0] = -c.room_hx + m + 2.0f * (c.room_hx - m) * u01(r.x);
-    w[1] = -c.room_hy + m + 2.0f * (c.room_hy - m) * u01(r.y);
-    w[2] = m + (c.room_h - 2.0f * m) * u01(r.z);
+    w[0] = in_box(c.room_hx, m, u01(r.x));
+    w[1] = in_box(c.room_hy, m, u01(r.y));
+    w[2] = in_height(c.room_h, m, u01(r.z));
 }
 
 // True when env e's drones need the swap permutation at step tau.
@@ -232,12 +242,13 @@ __device__ __forceinline__ void scenario_goal(const Consts& c, const Dev& dv, in
         waypoint(c, seed, q, w0);
         waypoint(c, seed, q + 1, w1);
         waypoint(c, seed, q + 2, w2);
-        const float b0 = v * v * v, b1 = 3.0f * v * v * u, b2 = 3.0f * v * u * u, b3 = u * u * u;
+        const float b0 = __fmul_rn(__fmul_rn(v, v), v), b1 = __fmul_rn(__fmul_rn(__fmul_rn(3.0f, v), v), u),
+                    b2 = __fmul_rn(__fmul_rn(__fmul_rn(3.0f, v), u), u), b3 = __fmul_rn(__fmul_rn(u, u), u);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float p1 = w0[k] + (w1[k] - wm[k]) * (1.0f / 6.0f);
-            const float p2 = w1[k] - (w2[k] - w0[k]) * (1.0f / 6.0f);
-            g[k] = b0 * w0[k] + b1 * p1 + b2 * p2 + b3 * w1[k];
+            const float p1 = __fmaf_rn(__fsub_rn(w1[k], wm[k]), 1.0f / 6.0f, w0[k]);
+            const float p2 = __fmaf_rn(-__fsub_rn(w2[k], w0[k]), 1.0f / 6.0f, w1[k]);
+            g[k] = __fmaf_rn(b3, w1[k], __fmaf_rn(b2, p2, __fmaf_rn(b1, p1, __fmul_rn(b0, w0[k]))));
         }
         return;
     }
@@ -250,7 +261,8 @@ __device__ __forceinline__ void scenario_goal(const Consts& c, const Dev& dv, in
     } else if (type == QS_SCN_SWAP && sw) {
         k = slot;
     } else if (type == QS_SCN_SHRINK_EXPAND) {
-        lam = 1.0f - (1.0f - c.se_min) * 0.5f * (1.0f - cospif(2.0f * (float)tau / c.se_period));
+        lam = __fmaf_rn(-__fmul_rn(__fsub_rn(1.0f, c.se_min), 0.5f), __fsub_rn(1.0f, cospif(2.0f * (float)tau / c.se_period)),
+                        1.0f);
     } else if (type == QS_SCN_SWARM_VS_SWARM) {
         const int n0 = (N + 1) >> 1, grp = i >= n0 ? 1 : 0;
         k = i - grp * n0;
