@@ -29,6 +29,9 @@ def main(out_path):
             ("swarm_ws", [8] * 300, 6, FULL, ()),
             ("swarm64", [64, 40, 33] * 8, 6, FULL + ("downwash",), ()),
             ("scenarios", [8, 5, 16, 1] * 40, 6, FULL, tuple(qs.SCENARIOS)),
+            # smooth contacts stepped by the general instance (pair penalty staged per substep)
+            ("smooth_step", [1, 2, 8, 33, 64] * 8, 6, ("smooth", "motor_noise", "obs_noise", "dr", "collisions",
+                                                     "record_knn", "auto_reset"), ()),
         ]
         for name, sizes, K, feats, scn in cases:
             env = QuadSwarmEnv(len(sizes), np.asarray(sizes, np.int32), K, feats, seed=11, device=DEV,
