@@ -139,6 +139,38 @@ def test_single_step_parity(name, sizes, K, features):
     check_step(r, sizes)
 
 
+@pytest.mark.parametrize("substeps", [1, 3, 5])
+@pytest.mark.parametrize("sizes,K", [([1] * 300, 0), ([8] * 100, 6), ([8] * 60, 0)])
+def test_single_step_parity_substeps(substeps, sizes, K):
+    """Physics substeps per control step other than the paper's two (the
+    warp-specialised kernels draw the motor normals of up to four substeps
+    ahead and the rest inline), and swarms without neighbour observations."""
+    r = one_step(sizes, K, FULL, seed=40 + substeps, substeps=substeps)
+    check_step(r, sizes)
+
+
+@pytest.mark.parametrize("substeps", [1, 5])
+def test_rollout_equals_steps_substeps(substeps):
+    """Rollouts (warp-specialised and persistent) against per-call steps with
+    1 and 5 physics substeps per control step."""
+    from paper_2306_09537_gb300 import qs
+    for sizes, shape in (([8] * 64, None), ([1, 2, 8, 33, 64, 5] * 6, None), ([1, 2, 8, 33, 64, 5] * 6,
+                                                                              (qs.QS_BLOCK_WARP_SPECIALISED, 0, 1))):
+        env, _ = pair(sizes, 6, FULL + ("auto_reset",), seed=14, episode_steps=7, substeps=substeps)
+        env2, _ = pair(sizes, 6, FULL + ("auto_reset",), seed=14, episode_steps=7, substeps=substeps)
+        if shape is not None:
+            qs.qs_set_rollout_shape(env.h, *shape)
+        T = 9
+        acts = torch.from_numpy(W.actions(14, T, env.D)).to(DEV)
+        obs = torch.empty(T, env.D, env.obs_dim, device=DEV)
+        rew = torch.empty(T, env.D, device=DEV)
+        env.rollout(acts, obs, rew, None)
+        for t in range(T):
+            o2, r2, _ = env2.step(acts[t])
+            assert torch.equal(obs[t], o2) and torch.equal(rew[t], r2), (sizes[:3], shape, t)
+        assert torch.equal(env.get_state()["state"], env2.get_state()["state"])
+
+
 def test_single_step_contacts_exercised():
     """A room-contact-heavy state: many drones start at the floor, walls or
     ceiling, moving outward, so every contact branch is taken."""
