@@ -179,18 +179,18 @@ __device__ __forceinline__ void substep_vjp(const Drone& s, const Prm& p, const 
     for (int r = 0; r < 4; ++r) f[r] = fmaf(p.fmax * uf1[r], uf1[r], eps1[r]);
     const float T = (f[0] + f[1]) + (f[2] + f[3]);
     const float sa = p.arm * 0.70710678118654752f;
-    const float Iw[3] = {p.ixx * s.w[0], p.iyy * s.w[1], p.izz * s.w[2]};
+    const float Iw[3] = {__fmul_rn(p.ixx, s.w[0]), __fmul_rn(p.iyy, s.w[1]), __fmul_rn(p.izz, s.w[2])};
     const float tx = sa * ((f[0] + f[1]) - (f[2] + f[3]));
     const float ty = sa * ((f[1] + f[2]) - (f[0] + f[3]));
     const float tz = c.kappa * ((f[1] + f[3]) - (f[0] + f[2]));
-    const float wd[3] = {(tx - (s.w[1] * Iw[2] - s.w[2] * Iw[1])) * p.inv_ixx,
-                         (ty - (s.w[2] * Iw[0] - s.w[0] * Iw[2])) * p.inv_iyy,
-                         (tz - (s.w[0] * Iw[1] - s.w[1] * Iw[0])) * p.inv_izz};
+    const float wd[3] = {__fmul_rn(__fsub_rn(tx, cross_c(s.w[1], Iw[2], s.w[2], Iw[1])), p.inv_ixx),
+                         __fmul_rn(__fsub_rn(ty, cross_c(s.w[2], Iw[0], s.w[0], Iw[2])), p.inv_iyy),
+                         __fmul_rn(__fsub_rn(tz, cross_c(s.w[0], Iw[1], s.w[1], Iw[0])), p.inv_izz)};
     // w' exactly as the forward computed it (compensated), and the clamp mask
     float w1[3], pass[3];
     for (int k = 0; k < 3; ++k) {
         float hi = s.w[k], lo = s.wlo[k];
-        comp_add(hi, lo, wd[k] * dt);
+        comp_add_prod(hi, lo, wd[k], dt);
         pass[k] = fabsf(hi) > c.omega_max ? 0.f : 1.f;
         w1[k] = fabsf(hi) > c.omega_max ? copysignf(c.omega_max, hi) : hi;
     }
@@ -630,41 +630,41 @@ __device__ __forceinline__ void discrete_substep_vjp(const Drone& s, const Prm& 
     const float tz = c.kappa * ((f[1] + f[3]) - (f[0] + f[2]));
     const float F0 = s.R[2] * T, F1 = s.R[5] * T, F2 = s.R[8] * T;
     float a[3] = {F0 * p.inv_m, F1 * p.inv_m, fmaf(F2, p.inv_m, -g)};
-    const float mg = p.m * g;
+    const float mg = __fmul_rn(p.m, g);
     const bool on_floor = (c.flags & QS_F_FLOOR) && s.x[2] <= 0.0f && F2 < mg;
     const bool still = on_floor && s.v[0] == 0.0f && s.v[1] == 0.0f;
-    const float ffric = on_floor ? c.mu * (mg - F2) : 0.0f;
+    const float ffric = on_floor ? __fmul_rn(c.mu, __fsub_rn(mg, F2)) : 0.0f;
     float nf = 0.f, keep = 0.f, vh[2] = {0.f, 0.f}, inv_nv = 0.f;
     if (on_floor) {
         float fx = F0, fy = F1;
         if (still) {
-            nf = sqrtf(fx * fx + fy * fy);
-            keep = nf > ffric ? (nf - ffric) * __frcp_rn(nf) : 0.0f;
-            fx *= keep;
-            fy *= keep;
+            nf = sqrtf(__fmaf_rn(fy, fy, __fmul_rn(fx, fx)));
+            keep = nf > ffric ? __fmul_rn(__fsub_rn(nf, ffric), __frcp_rn(nf)) : 0.0f;
+            fx = __fmul_rn(fx, keep);
+            fy = __fmul_rn(fy, keep);
         } else {
-            inv_nv = rsqrtf(s.v[0] * s.v[0] + s.v[1] * s.v[1]);
+            inv_nv = rsqrtf(__fmaf_rn(s.v[1], s.v[1], __fmul_rn(s.v[0], s.v[0])));
             vh[0] = s.v[0] * inv_nv;
             vh[1] = s.v[1] * inv_nv;
-            fx -= ffric * s.v[0] * inv_nv;
-            fy -= ffric * s.v[1] * inv_nv;
+            fx = __fmaf_rn(-__fmul_rn(ffric, s.v[0]), inv_nv, fx);
+            fy = __fmaf_rn(-__fmul_rn(ffric, s.v[1]), inv_nv, fy);
         }
-        a[0] = fx * p.inv_m;
-        a[1] = fy * p.inv_m;
+        a[0] = __fmul_rn(fx, p.inv_m);
+        a[1] = __fmul_rn(fy, p.inv_m);
         a[2] = 0.0f;
     }
-    const float Iw[3] = {p.ixx * s.w[0], p.iyy * s.w[1], p.izz * s.w[2]};
-    const float wd[3] = {(tx - (s.w[1] * Iw[2] - s.w[2] * Iw[1])) * p.inv_ixx,
-                         (ty - (s.w[2] * Iw[0] - s.w[0] * Iw[2])) * p.inv_iyy,
-                         (tz - (s.w[0] * Iw[1] - s.w[1] * Iw[0])) * p.inv_izz};
+    const float Iw[3] = {__fmul_rn(p.ixx, s.w[0]), __fmul_rn(p.iyy, s.w[1]), __fmul_rn(p.izz, s.w[2])};
+    const float wd[3] = {__fmul_rn(__fsub_rn(tx, cross_c(s.w[1], Iw[2], s.w[2], Iw[1])), p.inv_ixx),
+                         __fmul_rn(__fsub_rn(ty, cross_c(s.w[2], Iw[0], s.w[0], Iw[2])), p.inv_iyy),
+                         __fmul_rn(__fsub_rn(tz, cross_c(s.w[0], Iw[1], s.w[1], Iw[0])), p.inv_izz)};
     float v1[3] = {fmaf(a[0], dt, s.v[0]), fmaf(a[1], dt, s.v[1]), fmaf(a[2], dt, on_floor ? 0.0f : s.v[2])};
-    const bool stop = on_floor && !still && (v1[0] * s.v[0] + v1[1] * s.v[1]) < 0.0f;
+    const bool stop = on_floor && !still && __fmaf_rn(v1[1], s.v[1], __fmul_rn(v1[0], s.v[0])) < 0.0f;
     if (stop) v1[0] = v1[1] = 0.0f;
     float x1[3] = {fmaf(v1[0], dt, s.x[0]), fmaf(v1[1], dt, s.x[1]), fmaf(v1[2], dt, s.x[2])};
     float w1[3], pass[3];
     for (int k = 0; k < 3; ++k) {
         float hi = s.w[k], lo = s.wlo[k];
-        comp_add(hi, lo, wd[k] * dt);
+        comp_add_prod(hi, lo, wd[k], dt);
         pass[k] = fabsf(hi) > c.omega_max ? 0.f : 1.f;
         w1[k] = fabsf(hi) > c.omega_max ? copysignf(c.omega_max, hi) : hi;
     }
@@ -943,9 +943,9 @@ __device__ __forceinline__ void discrete_collisions_et(const Consts& c, Drone& s
         six_normals(c, tick, (uint32_t)d, TAG_COLL, 0, n);
         for (int k = 0; k < 3; ++k) {
             const float v0 = s.v[k];
-            s.v[k] = c.alpha_c * (s.v[k] + dvs[k] + c.sig_cv * n[k]);
-            comp_add(s.w[k], s.wlo[k], c.sig_cw * n[3 + k]);
-            const float Dk = s.v[k] - v0 - c.alpha_c * dvs[k];
+            s.v[k] = __fmul_rn(c.alpha_c, __fmaf_rn(c.sig_cv, n[k], __fadd_rn(s.v[k], dvs[k])));
+            comp_add_prod(s.w[k], s.wlo[k], c.sig_cw, n[3 + k]);
+            const float Dk = __fmaf_rn(-c.alpha_c, dvs[k], __fsub_rn(s.v[k], v0));
             s.x[k] = fmaf(Dk, smax, fmaf(c.alpha_c, dxs[k], s.x[k]));
         }
     }

@@ -312,16 +312,8 @@ __device__ __forceinline__ float cross_c(float a, float b, float c, float d) {
     return __fmaf_rn(-c, d, __fmul_rn(a, b));
 }
 
-// hi + lo <- hi + lo + delta, keeping the rounding error of the sum in lo.
-__device__ __forceinline__ void comp_add(float& hi, float& lo, float delta) {
-    const float y = __fadd_rn(delta, lo);
-    const float t = __fadd_rn(hi, y);
-    lo = __fsub_rn(y, __fsub_rn(t, hi));
-    hi = t;
-}
-
-// hi + lo <- hi + lo + a b, the product entering with the low word in one
-// rounding.
+// hi + lo <- hi + lo + a b, keeping the rounding error of the sum in lo
+// (Kahan); the product enters with the low word in one rounding.
 __device__ __forceinline__ void comp_add_prod(float& hi, float& lo, float a, float b) {
     const float y = __fmaf_rn(a, b, lo);
     const float t = __fadd_rn(hi, y);
