@@ -161,6 +161,35 @@ def test_wide_swarms_adjoint(features):
             assert ok, worst
 
 
+@pytest.mark.parametrize("features", [("smooth", "motor_noise", "dr"),
+                                      ("floor", "walls", "collisions", "motor_noise", "dr")])
+def test_diff_forward_runs_the_steps_dynamics(features):
+    """The differentiable forward steps the step's own dynamics: its state
+    checkpoint after C control steps equals, bit for bit, the state a rollout
+    reaches from the same initial state, parameters, goals and commands
+    (position, velocity, attitude, body rates, motor speeds, motor noise; the
+    previous-command entries, which only the step's reward reads, excluded)."""
+    from paper_2306_09537_gb300 import qs as Q
+    sizes = [8] * 16 + [3, 1, 17, 32]
+    T, C = 8, 4
+    env, _, st, prm, goals, acts = setup(sizes, T, 31, features=features)
+    x0 = torch.from_numpy(st).to(DEV)
+    a = torch.from_numpy(acts).to(DEV)
+    ws = torch.empty(Q.qs_diff_workspace_size(env.h, T, C), dtype=torch.uint8, device=DEV)
+    loss = torch.empty(env.D, device=DEV)
+    Q.qs_diff_forward(env.h, T, C, x0, a, loss, ws)
+    env.sync()
+    nplane, D = 9, env.D  # checkpoints lead the workspace: [T / C][9 float4 planes][D]
+    ck = ws.view(torch.float32)[: (T // C) * nplane * D * 4].reshape(T // C, nplane, D, 4)
+    ck1 = ck[1].permute(1, 0, 2).reshape(D, nplane * 4).cpu().numpy()
+    env2, _ = pair(sizes, 0, features, seed=31)
+    z = torch.zeros(env2.E, dtype=torch.int32, device=DEV)
+    env2.set_state(x0, torch.from_numpy(prm).to(DEV), torch.from_numpy(goals).to(DEV), z, z)
+    env2.rollout(a[:C].contiguous(), None, None, None)
+    s2 = env2.get_state()["state"].cpu().numpy()
+    assert np.array_equal(ck1[:, 0:26], s2[:, 0:26])
+
+
 def test_checkpoint_interval_does_not_change_gradients():
     sizes = [8] * 16 + [3] * 8
     T = 24
