@@ -24,11 +24,11 @@ FULL = ("floor", "walls", "motor_noise", "obs_noise", "dr", "collisions", "recor
 MARGIN_1STEP = 1e-6  # ~17 binary32 ulps: one step from identical inputs cannot flip a wider decision
 
 
-def one_step(sizes, K, features, seed, weights=ALL_WEIGHTS, spread=0.12, **kw):
+def one_step(sizes, K, features, seed, weights=ALL_WEIGHTS, spread=0.12, act_range=(0.0, 1.0), **kw):
     env, o = pair(sizes, K, features, seed=seed, weights=weights, **kw)
     st, prm, goals = seeded_inputs(env, seed, sizes, spread=spread if max(sizes) > 1 else None)
     set_both(env, o, st, prm, goals, ep=3, tick=11)
-    acts = W.actions(seed, 1, env.D)[0]
+    acts = W.actions(seed, 1, env.D, lo=act_range[0], hi=act_range[1])[0]
     obs, rew, done = env.step(torch.from_numpy(acts).to(DEV))
     ev, knn = env.get_events(knn="record_knn" in features and K > 0)
     g = gpu_state(env)
@@ -137,6 +137,16 @@ def test_single_step_parity(name, sizes, K, features):
     # 100+ drones packed into 0.24 m would all touch; spread large swarms wider
     r = one_step(sizes, K, features, seed=sum(map(ord, name)) % 1000, spread=1.0 if max(sizes) > 64 else 0.12)
     check_step(r, sizes)
+
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_single_step_parity_commands_out_of_range(symmetric):
+    """Commands beyond the action map's range (Sec. III-A: clip to [0, 1], or
+    the paper's (clip(a, -1, 1) + 1) / 2) are clipped the same way on both
+    sides; the reward's action terms see the clipped commands."""
+    feats = FULL + (("action_symmetric",) if symmetric else ())
+    r = one_step([8] * 100, 6, feats, seed=77, act_range=(-1.5, 1.5))
+    check_step(r, [8] * 100)
 
 
 @pytest.mark.parametrize("substeps", [1, 3, 5])
