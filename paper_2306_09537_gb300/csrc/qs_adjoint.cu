@@ -29,7 +29,9 @@
 namespace qsk {
 
 constexpr int ADJ_BLOCK_MAX = 256;
-constexpr int NSUB = 29;  // floats of a saved substep input: x v R w wlo uf eps
+constexpr int NSUB = 29;
+// steps of a checkpoint segment whose collision responses the backward records
+constexpr int RFLAG_WORDS = 32, RFLAG_BITS = 32 * RFLAG_WORDS;  // floats of a saved substep input: x v R w wlo uf eps
 
 // Logistic function 1 / (1 + exp(-z)) from e = exp(-|z|) in (0, 1]: the
 // reciprocal of 1 + e in [1, 2] never meets an infinite or denormal operand
@@ -321,6 +323,16 @@ __device__ __forceinline__ void group_sync(int id, int n) {
         asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
     else
         asm volatile("bar.sync 2, %0;" ::"r"(n) : "memory");
+}
+
+// group_sync that also returns whether v holds for any thread of the group.
+__device__ __forceinline__ bool group_sync_or(int id, int n, bool v) {
+    if (id == 0) return __syncthreads_or(v) != 0;
+    if (n == 32) return __any_sync(0xffffffffu, v);
+    uint32_t r;
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+                 : "=r"(r) : "r"((uint32_t)v), "r"(id), "r"(n) : "memory");
+    return r != 0;
 }
 
 // One smooth substep of the slot's drones (pair force from the positions at
@@ -841,7 +853,9 @@ __device__ __forceinline__ void discrete_substep_vjp(const Drone& s, const Prm& 
 // The collision pass of a control step (S9, S10) as the step kernels run it:
 // positions and pre-collision velocities staged in shared memory (sx, sv:
 // [3][nt]). Every thread of the CTA calls it.
-__device__ __forceinline__ void discrete_collisions(const Consts& c, Drone& s, const Prm& p, uint32_t tick, int d,
+// Returns whether any drone of the group responded (the same value in every
+// thread of the group).
+__device__ __forceinline__ bool discrete_collisions(const Consts& c, Drone& s, const Prm& p, uint32_t tick, int d,
                                                     bool act, float* sx, float* sv, int nt, int sbase, int lane, int N,
                                                     int lt, int bid, int bn) {
     if (act) {
@@ -862,8 +876,9 @@ __device__ __forceinline__ void discrete_collisions(const Consts& c, Drone& s, c
         bool dwh = false;
         responded = pair_scan(c, s, p.thr, lane, N, sbase, sx, sv, nt, 0, true, true, ev, best, dvs, false, az, dwh);
     }
-    group_sync(bid, bn);
+    const bool any = group_sync_or(bid, bn, responded);
     if (responded) apply_response(c, s, tick, d, dvs);
+    return any;
 }
 
 // ---------------------------------------------------------------- event-time pair contacts
@@ -891,19 +906,20 @@ __device__ __forceinline__ PairEt pair_et(const float dx[3], float key, float th
     q.n[1] = key > 0.0f ? -dx[1] * q.inv : 0.0f;
     q.n[2] = key > 0.0f ? -dx[2] * q.inv : 1.0f;
     for (int k = 0; k < 3; ++k) q.w[k] = -rv[k];  // v_j - v_i
-    q.vn = q.w[0] * q.n[0] + q.w[1] * q.n[1] + q.w[2] * q.n[2];
-    const float a = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
-    const float c0 = key - thr;
-    const float raw = -c0 / (sqrtf(fmaxf(app * app - a * c0, 0.0f)) - app);
+    q.vn = dot3(q.w[0], q.w[1], q.w[2], q.n[0], q.n[1], q.n[2]);
+    const float a = dot3(rv[0], rv[1], rv[2], rv[0], rv[1], rv[2]);
+    const float c0 = __fsub_rn(key, thr);
+    const float raw = -c0 / __fsub_rn(sqrtf(fmaxf(cross_c(app, app, a, c0), 0.0f)), app);
     q.free = raw > 0.0f && raw < Tc;
     q.sig = fminf(fmaxf(raw, 0.0f), Tc);
-    for (int k = 0; k < 3; ++k) q.p[k] = -dx[k] - rv[k] * q.sig;  // r - u sigma
-    q.den = a * q.sig - app;
+    for (int k = 0; k < 3; ++k) q.p[k] = __fmaf_rn(-rv[k], q.sig, -dx[k]);  // r - u sigma
+    q.den = __fmaf_rn(a, q.sig, -app);
     return q;
 }
 
-// The event-time collision pass of a control step (forward).
-__device__ __forceinline__ void discrete_collisions_et(const Consts& c, Drone& s, const Prm& p, uint32_t tick, int d,
+// The event-time collision pass of a control step (forward); returns whether
+// any drone of the group responded (the same value in every thread of it).
+__device__ __forceinline__ bool discrete_collisions_et(const Consts& c, Drone& s, const Prm& p, uint32_t tick, int d,
                                                        bool act, float* sx, float* sv, int nt, int sbase, int lane,
                                                        int N, int lt, int bid, int bn) {
     if (act) {
@@ -926,7 +942,7 @@ __device__ __forceinline__ void discrete_collisions_et(const Consts& c, Drone& s
             const float key = pair_key(s.x[0], s.x[1], s.x[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx[0], dx[1], dx[2]);
             if (!(key < p.thr)) continue;
             const float rv[3] = {s.v[0] - sv[tj], s.v[1] - sv[nt + tj], s.v[2] - sv[2 * nt + tj]};
-            const float app = -(rv[0] * dx[0] + rv[1] * dx[1] + rv[2] * dx[2]);
+            const float app = -dot3(rv[0], rv[1], rv[2], dx[0], dx[1], dx[2]);
             if (!(app < 0.0f)) continue;
             const PairEt q = pair_et(dx, key, p.thr, rv, app, Tc);
             for (int k = 0; k < 3; ++k) {
@@ -937,7 +953,7 @@ __device__ __forceinline__ void discrete_collisions_et(const Consts& c, Drone& s
             responded = true;
         }
     }
-    group_sync(bid, bn);
+    const bool any = group_sync_or(bid, bn, responded);
     if (responded) {
         float n[6];
         six_normals(c, tick, (uint32_t)d, TAG_COLL, 0, n);
@@ -949,6 +965,7 @@ __device__ __forceinline__ void discrete_collisions_et(const Consts& c, Drone& s
             s.x[k] = fmaf(Dk, smax, fmaf(c.alpha_c, dxs[k], s.x[k]));
         }
     }
+    return any;
 }
 
 // Adjoint of the collision pass: xs, vs the pre-collision position and
@@ -973,7 +990,7 @@ __device__ __forceinline__ void collision_vjp(const Consts& c, const float xs[3]
         const float key = pair_key(xs[0], xs[1], xs[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx, dy, dz);
         if (!(key < thr)) continue;
         const float rv0 = vs[0] - sv[tj], rv1 = vs[1] - sv[nt + tj], rv2 = vs[2] - sv[2 * nt + tj];
-        if (!(-(rv0 * dx + rv1 * dy + rv2 * dz) < 0.0f)) continue;  // approaching
+        if (!(-dot3(rv0, rv1, rv2, dx, dy, dz) < 0.0f)) continue;  // approaching
         responded = true;
         float n[3] = {0.f, 0.f, 1.f}, inv = 0.f;
         if (key > 0.0f) {
@@ -1000,6 +1017,13 @@ __device__ __forceinline__ void collision_vjp(const Consts& c, const float xs[3]
             lx[k] += c.alpha_c * acc_x[k];
         }
     }
+}
+
+// lambda x += d loss / d x of step t's term |x - g|^2 (scaled by dl), with
+// explicit roundings: the same bits whether or not the collision reverse runs.
+__device__ __forceinline__ void loss_term(float dl, const float x[3], const float g[3], float lx[3]) {
+    const float s2 = __fmul_rn(dl, 2.f);
+    for (int k = 0; k < 3; ++k) lx[k] = __fmaf_rn(s2, __fsub_rn(x[k], g[k]), lx[k]);
 }
 
 // Adjoint of the event-time collision pass together with step t's loss term,
@@ -1041,7 +1065,7 @@ __device__ __forceinline__ void collision_vjp_et(const Consts& c, const Drone& s
                                        dx[2]);
             if (!(key < p.thr)) continue;
             const float rv[3] = {sc.v[0] - sv[tj], sc.v[1] - sv[nt + tj], sc.v[2] - sv[2 * nt + tj]};
-            const float app = -(rv[0] * dx[0] + rv[1] * dx[1] + rv[2] * dx[2]);
+            const float app = -dot3(rv[0], rv[1], rv[2], dx[0], dx[1], dx[2]);
             if (!(app < 0.0f)) continue;
             const PairEt q = pair_et(dx, key, p.thr, rv, app, Tc);
             for (int k = 0; k < 3; ++k) {
@@ -1060,14 +1084,13 @@ __device__ __forceinline__ void collision_vjp_et(const Consts& c, const Drone& s
         float n[6];
         six_normals(c, tick, (uint32_t)d, TAG_COLL, 0, n);
         for (int k = 0; k < 3; ++k) {
-            const float v1 = ac * (sc.v[k] + dvs[k] + c.sig_cv * n[k]);
-            Dv[k] = v1 - sc.v[k] - ac * dvs[k];
+            const float v1 = __fmul_rn(ac, __fmaf_rn(c.sig_cv, n[k], __fadd_rn(sc.v[k], dvs[k])));
+            Dv[k] = __fmaf_rn(-ac, dvs[k], __fsub_rn(v1, sc.v[k]));
             xp[k] = fmaf(Dv[k], smax, fmaf(ac, dxs[k], sc.x[k]));
         }
     }
+    if (act) loss_term(dl, xp, g, lx);  // loss of step t at the post-collision position
     if (act) {
-        // loss of step t at the post-collision position
-        for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (xp[k] - g[k]);
         if (responded) qd = lx[0] * Dv[0] + lx[1] * Dv[1] + lx[2] * Dv[2];
         sl[lt] = lv[0];
         sl[nt + lt] = lv[1];
@@ -1090,7 +1113,7 @@ __device__ __forceinline__ void collision_vjp_et(const Consts& c, const Drone& s
                                        dx[2]);
             if (!(key < p.thr)) continue;
             const float rv[3] = {sc.v[0] - sv[tj], sc.v[1] - sv[nt + tj], sc.v[2] - sv[2 * nt + tj]};
-            const float app = -(rv[0] * dx[0] + rv[1] * dx[1] + rv[2] * dx[2]);
+            const float app = -dot3(rv[0], rv[1], rv[2], dx[0], dx[1], dx[2]);
             if (!(app < 0.0f)) continue;
             const PairEt q = pair_et(dx, key, p.thr, rv, app, Tc);
             const float qv[3] = {l0[0] - sl[tj], l0[1] - sl[nt + tj], l0[2] - sl[2 * nt + tj]};
@@ -1211,6 +1234,11 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
     float* slx = sm + 15 * nb;           // event time: [3][nb] lambda of the post-collision position,
     float* sq = sm + 18 * nb;            //   [nb] lambda x' . D, [nb] earliest partner (group 1)
     int* sarg = reinterpret_cast<int*>(sm + 19 * nb);
+    // [2][RFLAG_WORDS] bit q: some drone of the group responded to a collision
+    // in step tb + q of the segment recomputed into that buffer (steps beyond
+    // RFLAG_BITS are taken as responding); the reverse skips the collision
+    // adjoint of a step without responses, which is then the identity
+    uint32_t* rflag = reinterpret_cast<uint32_t*>(sm + 23 * nb);
     const int S = c.substeps, S1 = c.substeps + 1;  // saved states per step: each substep's input, then the pre-collision state
     const size_t sbuf = (size_t)a.C * S1 * NSUB * D;  // floats of one scratch buffer
     Prm p;
@@ -1234,6 +1262,9 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
             // recompute segment nseg - 1 - it
             const int seg = nseg - 1 - it, tb = seg * a.C, te = min(a.T, tb + a.C);
             float* scr = a.scratch + (size_t)(it & 1) * sbuf;
+            uint32_t* fl = rflag + (it & 1) * RFLAG_WORDS;
+            if (lt == 0)
+                for (int w = 0; w < RFLAG_WORDS; ++w) fl[w] = 0u;
             Drone s;
             if (act) {
                 float4 q[NPLANE];
@@ -1251,14 +1282,21 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
                     }
                     save_sub(scr, D, (t - tb) * S1 + S, d, s);
                 }
-                if (coll && ET) discrete_collisions_et(c, s, p, tick0 + t, d, act, sx, sv, nt, sbase, lane, N, lt, bid, nb);
-                else if (coll) discrete_collisions(c, s, p, tick0 + t, d, act, sx, sv, nt, sbase, lane, N, lt, bid, nb);
+                bool any = false;
+                if (coll && ET)
+                    any = discrete_collisions_et(c, s, p, tick0 + t, d, act, sx, sv, nt, sbase, lane, N, lt, bid, nb);
+                else if (coll)
+                    any = discrete_collisions(c, s, p, tick0 + t, d, act, sx, sv, nt, sbase, lane, N, lt, bid, nb);
+                if (lt == 0 && any && t - tb < RFLAG_BITS) fl[(t - tb) >> 5] |= 1u << ((t - tb) & 31);
             }
         } else if (grp == 1 && it >= 1) {
             // reverse through segment nseg - it, recomputed in the previous round
             const int seg = nseg - it, tb = seg * a.C, te = min(a.T, tb + a.C);
             const float* scr = a.scratch + (size_t)((it - 1) & 1) * sbuf;
+            const uint32_t* fl = rflag + ((it - 1) & 1) * RFLAG_WORDS;
             for (int t = te - 1; t >= tb; --t) {
+                const int q = t - tb;  // the same in every thread of the group
+                const bool any = q >= RFLAG_BITS || ((fl[q >> 5] >> (q & 31)) & 1u);
                 float fh[4] = {0.f, 0.f, 0.f, 0.f}, u[4] = {0.f, 0.f, 0.f, 0.f}, msk[4] = {0.f, 0.f, 0.f, 0.f};
                 Drone sc;
                 if (act) {
@@ -1266,13 +1304,12 @@ __global__ void __launch_bounds__(ADJ_BLOCK_MAX) k_diffd_bwd(const Consts c, con
                     load_sub(scr, D, (t - tb) * S1 + S, d, sc);
                     // loss of step t: |x(t) - g|^2 + 1e-3 |f^|^2 (the collision pass leaves x
                     // unchanged; the event-time pass moves it and adds the term itself)
-                    if (!(ET && coll))
-                        for (int k = 0; k < 3; ++k) lx[k] += dl * 2.f * (sc.x[k] - g[k]);
+                    if (!(ET && coll && any)) loss_term(dl, sc.x, g, lx);
                 }
-                if (coll && ET) {
+                if (coll && ET && any) {
                     collision_vjp_et(c, sc, p, tick0 + t, d, act, sx, sv, sl, slx, sq, sarg, nt, sbase, lane, N, lt, bid,
                                      nb, dl, g, lx, lv);
-                } else if (coll) {
+                } else if (coll && any) {
                     if (act) {
                         sx[lt] = sc.x[0];
                         sx[nt + lt] = sc.x[1];
@@ -1341,7 +1378,8 @@ cudaError_t launch_diff(int backward, const Consts& c, const Dev& dv, const Tile
     // (positions and velocities of both groups, the reverse's lambdas of the
     // post-collision velocity and, with event-time contacts, position, its
     // lambda x' . D and earliest partner: 20 planes)
-    const size_t smem = sizeof(float) * (9 + 2 * FWD_SUB * 4) * block, smem2 = sizeof(float) * 23 * block;
+    const size_t smem = sizeof(float) * (9 + 2 * FWD_SUB * 4) * block,
+                 smem2 = sizeof(float) * 23 * block + sizeof(uint32_t) * 2 * RFLAG_WORDS;
     if (2 * block > ADJ_BLOCK_MAX) return cudaErrorInvalidValue;
     if (c.flags & QS_F_SMOOTH) {
         if (backward) k_diff_bwd<<<n_tiles, 2 * block, smem2, st>>>(c, dv, tiles, perm, a);
