@@ -582,11 +582,15 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     s.x[2] = fmaf(s.v[2], dt, s.x[2]);
     const float wd[3] = {wd0, wd1, wd2};
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        comp_add_prod(s.w[k], s.wlo[k], wd[k], dt);
-        if (fabsf(s.w[k]) > c.omega_max) {
-            s.w[k] = copysignf(c.omega_max, s.w[k]);
-            s.wlo[k] = 0.0f;
+    for (int k = 0; k < 3; ++k) comp_add_prod(s.w[k], s.wlo[k], wd[k], dt);
+    // body rates past omega_max are rare: one test on the largest first
+    if (fmaxf(fmaxf(fabsf(s.w[0]), fabsf(s.w[1])), fabsf(s.w[2])) > c.omega_max) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (fabsf(s.w[k]) > c.omega_max) {
+                s.w[k] = copysignf(c.omega_max, s.w[k]);
+                s.wlo[k] = 0.0f;
+            }
         }
     }
     rotate_polar(s.R, s.w, dt);
@@ -629,7 +633,9 @@ __device__ __forceinline__ uint32_t substep(Drone& s, const Prm& p, const Consts
     // S8 walls and ceiling: a drone past a boundary is put back onto it; if it
     // was moving outward its normal velocity is removed and
     // v <- alpha_c (v + eps_v), w <- w + eps_w
-    if (c.flags & QS_F_WALLS) {
+    // (a drone inside the room, the common case, passes one test)
+    if ((c.flags & QS_F_WALLS) &&
+        (fabsf(s.x[0]) > c.room_hx || fabsf(s.x[1]) > c.room_hy || s.x[2] > c.room_h)) {
         bool wall = false, ceil = false, held[3] = {false, false, false};
         const float v1[3] = {s.v[0], s.v[1], s.v[2]};
         float tau = dt;  // earliest boundary crossing (event-time contacts)
