@@ -222,3 +222,64 @@ def test_reward_action_term_square_root_error(form):
     rel = np.abs(r[1:] - want[1:]) / want[1:]
     print(f"max relative error {rel.max():.3e} = 2^{np.log2(rel.max()):.2f}")
     assert rel.max() <= 2.0 ** -22
+
+
+def test_normals_within_the_binary32_transform_bound():
+    """The body-rate sensor noise is sigma_w times Box-Muller normals (R18).
+    Drones hovering with zero body rates and equal rotor commands feel no
+    torque and keep their body rates exactly zero through a step, so the
+    observed body rates are the noise alone. Each of the 3 x 8192 normals is
+    compared with the exact transform of the same two uniforms, formed here in
+    binary64 from the oracle's Philox stream (first checked against the
+    oracle's own step, which pins this test's reading of the stream layout),
+    within the error of the binary32 transform: with y = -2 ln u0 the radius
+    rho = sqrt(y) and dy = 2 x 2^-21.41 max(1, y / 2) the error of a
+    logarithm that is good to 2^-21.41 absolute on [0.5, 2] and 3 units in the
+    last place elsewhere, |n - n_exact| <= min(dy / (2 rho), sqrt(dy)) +
+    1e-6 (rho + 1) (the sine and cosine to 2^-21.41 absolute, the square root
+    and the products to a few units in the last place)."""
+    from gpu_helpers import pair, set_both
+    from oracle import oracle as O
+    E, seed, tick = 8192, 11, 3
+    env, o = pair(np.ones(E, np.int32), 0, ("obs_noise",), seed=seed)
+    st = np.zeros((E, 30), np.float32)
+    st[:, 0] = np.linspace(-3, 3, E)
+    st[:, 1] = np.linspace(2, -2, E)
+    st[:, 2] = 5.0
+    st[:, 6:15] = np.eye(3, dtype=np.float32).ravel()
+    st[:, 18:22] = np.sqrt(np.float32(0.5))
+    st[:, 26:30] = 0.5
+    prm = np.tile(np.array(nominal(env), np.float32), (E, 1))
+    set_both(env, o, st, prm, np.zeros((E, 3), np.float32), tick=tick)
+    env.step(torch.full((E, 4), 0.5, device=DEV))
+    obs = env.obs.cpu().numpy().astype(np.float64)
+    o_obs = o.step(np.full((E, 4), 0.5))[0]
+    s = env.get_state()["state"].cpu().numpy()
+    assert np.all(s[:, 15:18] == 0)  # the body rates stayed exactly zero
+    n_gpu = obs[:, 15:18] / float(np.float32(env.cfg.params.obs_sigma_w))
+    n_or = o_obs[:, 15:18] / float(o.cfg.obs_sigma_w)
+
+    # the transform of the stream's uniforms: blocks 1 and 2 of the OBS tag
+    # (4), substream 0, at counter (tick, drone); words z, w of block 1 feed
+    # the first pair, words x, y of block 2 the third normal
+    key = np.array([seed & 0xffffffff, seed >> 32], np.uint32)
+    d = np.arange(E, dtype=np.uint32)
+
+    def block(blk):
+        ctr = np.stack([np.full(E, tick, np.uint32), d, np.full(E, (4 << 16) | blk, np.uint32),
+                        np.zeros(E, np.uint32)], axis=1)
+        return O.philox4x32_10_batch(ctr, key)
+
+    def u(r):
+        return ((r.astype(np.float64) // 512) + 0.5) / 8388608.0
+    b1, b2 = block(1), block(2)
+    y01, y2 = -2.0 * np.log(u(b1[:, 2])), -2.0 * np.log(u(b2[:, 0]))
+    th01, th2 = 2.0 * np.pi * u(b1[:, 3]), 2.0 * np.pi * u(b2[:, 1])
+    exact = np.stack([np.sqrt(y01) * np.cos(th01), np.sqrt(y01) * np.sin(th01), np.sqrt(y2) * np.cos(th2)], axis=1)
+    y = np.stack([y01, y01, y2], axis=1)
+    assert np.abs(n_or - exact).max() <= 1e-9  # the oracle draws exactly these normals
+    rho = np.sqrt(y)
+    dy = 2.0 * 2.0 ** -21.41 * np.maximum(1.0, y / 2.0)
+    bound = np.minimum(dy / (2.0 * np.maximum(rho, 1e-30)), np.sqrt(dy)) + 1e-6 * (rho + 1.0)
+    err = np.abs(n_gpu - exact)
+    assert np.all(err <= bound), float((err / bound).max())
