@@ -85,7 +85,7 @@ __device__ __forceinline__ void pair_vjp(const Consts& c, const float x[3], cons
 __device__ __forceinline__ void rotation_vjp(const float R[9], const float w1[3], float dt, float lR[9], float lw1[3]) {
     const float w0 = w1[0], wy = w1[1], w2 = w1[2];
     const float n2 = w0 * w0 + wy * wy + w2 * w2;
-    const float cc = rsqrtf(fmaf(dt * dt, n2, 1.0f));
+    const float cc = rsqrt_approx_ge1(fmaf(dt * dt, n2, 1.0f));
     const float inv1c = rcp_approx(1.0f + cc);  // 1 + c in (1, 2]: one reciprocal for both quotients below
     const float qa = dt * cc;
     const float qb = dt * dt * cc * cc * inv1c;

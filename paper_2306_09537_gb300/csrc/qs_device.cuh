@@ -56,8 +56,13 @@ __device__ __forceinline__ uint32_t ctr_word(uint32_t tag, uint32_t sub, uint32_
     return (tag << 16) | (sub << 8) | blk;
 }
 
-// (2k+1)/2^24 with k the top 23 bits: inside (0,1), exact in binary32.
-__device__ __forceinline__ float u01(uint32_t r) { return (float)(r >> 9) * (1.0f / 8388608.0f) + (1.0f / 16777216.0f); }
+// (2k+1)/2^24 with k the top 23 bits: inside (0,1), exact in binary32. Formed
+// from the bits of 1 + k 2^-23 (k as the mantissa) minus 1 - 2^-24, a
+// difference that is exact (the operands lie within a factor of two), so no
+// integer-to-float conversion is needed.
+__device__ __forceinline__ float u01(uint32_t r) {
+    return __fsub_rn(__uint_as_float(0x3F800000u | (r >> 9)), 0.99999994039535522f);
+}
 
 // Square root by the hardware approximation (PTX sqrt.approx.ftz.f32): a
 // couple of instructions where the correctly rounded sqrtf takes a longer
@@ -109,8 +114,10 @@ __device__ __forceinline__ float rsqrt_approx_ge1(float x) {
 // quadrotor-step).
 __device__ __forceinline__ float2 box_muller(float u0, float u1) {
     const float rho = sqrt_approx(fmaxf(-2.0f * __logf(u0), 0.0f));
-    float s, c;
-    __sincosf(6.28318530717958648f * (u1 - 0.5f), &s, &c);
+    float s, c;  // hardware sine and cosine (.ftz: the angle is never subnormal)
+    const float th = 6.28318530717958648f * (u1 - 0.5f);
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(th));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(th));
     return make_float2(-rho * c, -rho * s);
 }
 
