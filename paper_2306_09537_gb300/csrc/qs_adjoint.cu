@@ -37,7 +37,7 @@ constexpr int RFLAG_WORDS = 32, RFLAG_BITS = 32 * RFLAG_WORDS;  // floats of a s
 // reciprocal of 1 + e in [1, 2] never meets an infinite or denormal operand
 // (1 + exp(-z) overflows for a drone far from a wall, z ~ -1000).
 __device__ __forceinline__ float sigmoidf_(float z) {
-    const float e = __expf(-fabsf(z));
+    const float e = exp_approx(-fabsf(z));
     const float s = rcp_approx(1.0f + e);
     return z >= 0.0f ? s : e * s;
 }

@@ -91,6 +91,24 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// exp(x) = 2^(x log2 e) and ln(x) = log2(x) ln 2 on the hardware base-2
+// approximations (PTX ex2.approx.ftz.f32, lg2.approx.ftz.f32): a scaling and
+// one hardware operation, without the argument checks of the library forms.
+// A result or argument below 2^-126 is taken as zero. The logarithm's error
+// stays inside the bound the Box-Muller normals are tested against
+// (2^-21.41 absolute on [0.5, 2]); the exponential feeds the smooth contact
+// penalties, where the differentiable rollout's tests bound it.
+__device__ __forceinline__ float exp_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__fmul_rn(x, 1.44269504088896341f)));
+    return y;
+}
+__device__ __forceinline__ float log_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return __fmul_rn(y, 0.693147180559945309f);
+}
+
 // Reciprocal square root by the hardware approximation (PTX
 // rsqrt.approx.ftz.f32) for arguments known to be at least 1.
 __device__ __forceinline__ float rsqrt_approx_ge1(float x) {
@@ -103,9 +121,9 @@ __device__ __forceinline__ float rsqrt_approx_ge1(float x) {
 // rho = sqrt(-2 ln u0). The angle is evaluated as 2 pi (u1 - 1/2) + pi, i.e.
 // cos(2 pi u1) = -cos(theta), sin(2 pi u1) = -sin(theta) with theta in (-pi, pi),
 // where the hardware sine/cosine is accurate to ~4e-7 absolute. The radius
-// takes the hardware logarithm (__logf: 2^-21.41 absolute on [0.5, 2], 3 units
-// in the last place elsewhere), clamped at zero where a u0 just below 1 rounds
-// ln u0 up to a positive value. The error of a normal is then at most
+// takes the hardware logarithm (log_approx; within 2^-21.41 absolute on
+// [0.5, 2] and 3 units in the last place elsewhere, the bound of __logf),
+// clamped at zero where a u0 just below 1 rounds ln u0 up to a positive value. The error of a normal is then at most
 // dy / (2 rho) with dy = 2^-20.41 max(1, rho^2 / 2), and never above
 // sqrt(dy) ~ 8.5e-4 (radii near zero, whose normals are near zero too): below
 // 2e-6 for rho > 0.2, i.e. for 98% of the draws. Against the library logf
@@ -113,7 +131,7 @@ __device__ __forceinline__ float rsqrt_approx_ge1(float x) {
 // batched step at 1,048,576 envs runs 7% faster (six transforms per
 // quadrotor-step).
 __device__ __forceinline__ float2 box_muller(float u0, float u1) {
-    const float rho = sqrt_approx(fmaxf(-2.0f * __logf(u0), 0.0f));
+    const float rho = sqrt_approx(fmaxf(-2.0f * log_approx(u0), 0.0f));
     float s, c;  // hardware sine and cosine (.ftz: the angle is never subnormal)
     const float th = 6.28318530717958648f * (u1 - 0.5f);
     asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(th));
@@ -426,8 +444,8 @@ __device__ __forceinline__ float command(const Consts& c, float a) {
 // gives the same bits.
 __device__ __forceinline__ float softplus_b(float u, float beta, float ib) {
     const float z = __fmul_rn(beta, u);
-    if (z < -16.0f) return __fmul_rn(__expf(z), ib);
-    return __fmul_rn(__fadd_rn(fmaxf(z, 0.0f), log1pf(__expf(-fabsf(z)))), ib);
+    if (z < -16.0f) return __fmul_rn(exp_approx(z), ib);
+    return __fmul_rn(__fadd_rn(fmaxf(z, 0.0f), log1pf(exp_approx(-fabsf(z)))), ib);
 }
 
 // Pairs farther apart than 2 l + 88 / beta have softplus_beta(2 l - d) below
