@@ -123,13 +123,13 @@ __device__ __forceinline__ float rsqrt_approx_ge1(float x) {
 // where the hardware sine/cosine is accurate to ~4e-7 absolute. The radius
 // takes the hardware logarithm (log_approx; within 2^-21.41 absolute on
 // [0.5, 2] and 3 units in the last place elsewhere, the bound of __logf),
-// clamped at zero where a u0 just below 1 rounds ln u0 up to a positive value. The error of a normal is then at most
-// dy / (2 rho) with dy = 2^-20.41 max(1, rho^2 / 2), and never above
-// sqrt(dy) ~ 8.5e-4 (radii near zero, whose normals are near zero too): below
-// 2e-6 for rho > 0.2, i.e. for 98% of the draws. Against the library logf
-// (about one unit in the last place, with a longer instruction sequence) the
-// batched step at 1,048,576 envs runs 7% faster (six transforms per
-// quadrotor-step).
+// clamped at zero where a u0 just below 1 rounds ln u0 up to a positive
+// value. The error of a normal is then at most dy / (2 rho) with
+// dy = 2^-20.41 max(1, rho^2 / 2), and never above sqrt(dy) ~ 8.5e-4 (radii
+// near zero, whose normals are near zero too): below 2e-6 for rho > 0.2, i.e.
+// for 98% of the draws. Against the library logf (about one unit in the last
+// place, with a longer instruction sequence) the batched step at 1,048,576
+// envs runs 7% faster (six transforms per quadrotor-step).
 __device__ __forceinline__ float2 box_muller(float u0, float u1) {
     const float rho = sqrt_approx(fmaxf(-2.0f * log_approx(u0), 0.0f));
     float s, c;  // hardware sine and cosine (.ftz: the angle is never subnormal)
