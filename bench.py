@@ -37,7 +37,7 @@ METRIC = "quadrotor-steps/sec on 1 GB300 (plain vs batched vs fwd+adjoint), % of
 # once the kernel sources change, the figure no longer describes the kernel
 # and the roofline's traffic is reported as null until it is captured again.
 HEADLINE_DRAM = {"bytes_per_launch": 1769301,
-                 "sources_sha256": "aef248cac0202be653848bb094c02ad2c60c0579f4b0f76f302b10f18bf6df2d",
+                 "sources_sha256": "9329eb635a1b1fd2268fe5877937e3ee9861007b3bc69b9c6b8ab8ff1f1913bf",
                  "source": "profiles/k_step_ws_plain_8192x1.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
 UNIT = "quadrotor-steps/s"
 WL = W.PLAIN
