@@ -3,7 +3,13 @@ per-call step, and CTA size / control steps per launch / graph use of the
 batched rollout. Candidates are timed with CUDA events on a scratch twin of
 the environment (same configuration, same seed), so tuning never advances the
 caller's simulation; the best shapes are then applied to the caller's handle.
-Results depend only on the configuration and are cached per process."""
+Each timed repetition starts from a cold L2 (a 256 MiB write before it), as a
+step or rollout does when other work runs between calls, and a candidate is
+ranked by its median over the repetitions: the ranking of close candidates
+can differ between warm and cold timing (the uneven 4096-env rollout, one
+session: persistent 64-thread CTAs 20.7 us per step warm and 19.2 us cold
+against 20.3 and 20.4 us for the warp-specialised kernel). Results depend
+only on the configuration and are cached per process."""
 from __future__ import annotations
 
 import numpy as np
@@ -21,19 +27,23 @@ def _signature(env) -> tuple:
             if env.sizes is not None else int(c.n_per_env))
 
 
-def _time(fn, stream, reps):
-    best = float("inf")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _time(fn, stream, reps, flush):
+    ts = []
     for _ in range(reps):
+        flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         fn()
         b.record(stream)
         b.synchronize()
-        best = min(best, a.elapsed_time(b))
-    return best
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
 
 
-def tune(env, steps: int = 32, horizon: int = 64, reps: int = 3, apply: bool = True) -> dict:
+def tune(env, steps: int = 32, horizon: int = 64, reps: int = 5, apply: bool = True) -> dict:
     """Returns {"step_blocks": {W: block}, "rollout": (block, fuse, graph), "timings": {...}}
     (step_blocks is empty for a handle with several width classes: its per-call
     step is the rollout launch, and the rollout shape covers it)."""
@@ -52,6 +62,7 @@ def tune(env, steps: int = 32, horizon: int = 64, reps: int = 3, apply: bool = T
         timings = {"step": {}, "rollout": {}}
         step_blocks = {}
         with torch.cuda.stream(stream):
+            flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=twin.device)
             # a handle with several width classes steps them all in one launch of
             # the rollout kernels, shaped below; only a single class has a
             # per-call kernel to shape
@@ -69,7 +80,7 @@ def tune(env, steps: int = 32, horizon: int = 64, reps: int = 3, apply: bool = T
                         for t in range(steps):
                             twin.step(acts[t])
                     run()
-                    ms = _time(run, stream, reps) / steps
+                    ms = _time(run, stream, reps, flush) / steps
                     timings["step"][(w, b)] = ms
                     if best is None or ms < best[0]:
                         best = (ms, b)
@@ -92,10 +103,11 @@ def tune(env, steps: int = 32, horizon: int = 64, reps: int = 3, apply: bool = T
                         def run():
                             twin.rollout(acts[:horizon], obs, rew, None)
                         run()
-                        ms = _time(run, stream, reps) / horizon
+                        ms = _time(run, stream, reps, flush) / horizon
                         timings["rollout"][(b, fuse, graph)] = ms
                         if best is None or ms < best[0]:
                             best = (ms, (b, fuse, graph))
+            del flush
         twin.close()
         res = {"step_blocks": step_blocks, "rollout": best[1], "timings": timings}
         _CACHE[key] = res
