@@ -750,48 +750,101 @@ __device__ __forceinline__ void topk_insert(uint64_t best[QS_MAX_K], int K, uint
     }
 }
 
+// Compare-exchange of two (key, index) words: a <- min, b <- max.
+__device__ __forceinline__ void cmp_swap(uint64_t& a, uint64_t& b) {
+    const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+
+// Sorts k[0..8) ascending with Floyd's 19-comparator network for 8 inputs
+// (Knuth, The Art of Computer Programming vol. 3, Sec. 5.3.4), depth 6:
+// the words are distinct (the low half is the partner index), so the result
+// is the same order an insertion sort gives.
+static_assert(QS_MAX_K == 8, "the sorting network holds QS_MAX_K words");
+__device__ __forceinline__ void sort8(uint64_t k[8]) {
+    cmp_swap(k[0], k[2]); cmp_swap(k[1], k[3]); cmp_swap(k[4], k[6]); cmp_swap(k[5], k[7]);
+    cmp_swap(k[0], k[4]); cmp_swap(k[1], k[5]); cmp_swap(k[2], k[6]); cmp_swap(k[3], k[7]);
+    cmp_swap(k[0], k[1]); cmp_swap(k[2], k[3]); cmp_swap(k[4], k[5]); cmp_swap(k[6], k[7]);
+    cmp_swap(k[2], k[4]); cmp_swap(k[3], k[5]);
+    cmp_swap(k[1], k[4]); cmp_swap(k[3], k[6]);
+    cmp_swap(k[1], k[2]); cmp_swap(k[3], k[4]); cmp_swap(k[5], k[6]);
+}
+
+// One partner j of the pair pass: its canonical key |x_j - x_i|^2, the
+// collision flag and Jacobi term (S9, S10) and the downwash term (S10b).
+__device__ __forceinline__ float pair_partner(const Consts& c, const Drone& s, float thr, int tj, const float* sx,
+                                              const float* sv, int nt, bool coll, bool flag_coll, uint32_t& ev,
+                                              float dvs[3], const bool dw, float& dw_az, bool& dw_hit,
+                                              bool& responded) {
+    float dx, dy, dz;
+    const float key = pair_key(s.x[0], s.x[1], s.x[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx, dy, dz);
+    // downwash: j overlaps this drone from above (horizontal distance below
+    // l_i + l_j, height difference in (0, dw_h))
+    if (dw && __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) < thr && dz > 0.0f && dz < c.dw_h) {
+        dw_az = __fmaf_rn(-c.dw_k1, __fmaf_rn(c.dw_k2, dz, c.dw_b1), dw_az);
+        dw_hit = true;
+    }
+    if (flag_coll && key < thr) {
+        ev |= EV_HIT_QUAD;
+        if (coll) {
+            // approaching iff (v_i - v_j) . (x_i - x_j) < 0
+            const float rv0 = s.v[0] - sv[tj], rv1 = s.v[1] - sv[nt + tj], rv2 = s.v[2] - sv[2 * nt + tj];
+            const float app = -dot3(rv0, rv1, rv2, dx, dy, dz);
+            if (app < 0.0f) {
+                float n0 = 0.f, n1 = 0.f, n2 = 1.f;
+                if (key > 0.0f) {
+                    const float inv = rsqrtf(key);
+                    n0 = -dx * inv;
+                    n1 = -dy * inv;
+                    n2 = -dz * inv;
+                }
+                const float vn = -dot3(rv0, rv1, rv2, n0, n1, n2);  // (v_j - v_i) . n
+                dvs[0] = fmaf(vn, n0, dvs[0]);
+                dvs[1] = fmaf(vn, n1, dvs[1]);
+                dvs[2] = fmaf(vn, n2, dvs[2]);
+                responded = true;
+            }
+        }
+    }
+    return key;
+}
+
 // S9 + S11 for the thread's drone (slot-local index `lane`) against the slot's
 // staged positions / pre-collision velocities (planes of stride nt): collision
 // flag, the Jacobi sum of ((v_j - v_i).n) n over colliding approaching
-// partners (S10), and the sorted neighbour list.
+// partners (S10), and the sorted neighbour list. Swarms of at most 8 (width
+// classes up to 8, so the test is uniform over a tile) keep every partner's
+// (key, index) word in registers and sort them with a network of 19
+// compare-exchanges; larger swarms insert each partner into the list of the
+// K nearest so far.
 __device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float thr, int lane, int N, int sbase,
                                           const float* sx, const float* sv, int nt, int keff, bool coll, bool flag_coll,
                                           uint32_t& ev, uint64_t best[QS_MAX_K], float dvs[3], const bool dw,
                                           float& dw_az, bool& dw_hit) {
     bool responded = false;
-    for (int j = 0; j < N; ++j) {
-        if (j == lane) continue;
-        const int tj = sbase + j;
-        float dx, dy, dz;
-        const float key = pair_key(s.x[0], s.x[1], s.x[2], sx[tj], sx[nt + tj], sx[2 * nt + tj], dx, dy, dz);
-        // downwash: j overlaps this drone from above (horizontal distance below
-        // l_i + l_j, height difference in (0, dw_h))
-        if (dw && __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) < thr && dz > 0.0f && dz < c.dw_h) {
-            dw_az = __fmaf_rn(-c.dw_k1, __fmaf_rn(c.dw_k2, dz, c.dw_b1), dw_az);
-            dw_hit = true;
-        }
-        if (flag_coll && key < thr) {
-            ev |= EV_HIT_QUAD;
-            if (coll) {
-                // approaching iff (v_i - v_j) . (x_i - x_j) < 0
-                const float rv0 = s.v[0] - sv[tj], rv1 = s.v[1] - sv[nt + tj], rv2 = s.v[2] - sv[2 * nt + tj];
-                const float app = -dot3(rv0, rv1, rv2, dx, dy, dz);
-                if (app < 0.0f) {
-                    float n0 = 0.f, n1 = 0.f, n2 = 1.f;
-                    if (key > 0.0f) {
-                        const float inv = rsqrtf(key);
-                        n0 = -dx * inv;
-                        n1 = -dy * inv;
-                        n2 = -dz * inv;
-                    }
-                    const float vn = -dot3(rv0, rv1, rv2, n0, n1, n2);  // (v_j - v_i) . n
-                    dvs[0] = fmaf(vn, n0, dvs[0]);
-                    dvs[1] = fmaf(vn, n1, dvs[1]);
-                    dvs[2] = fmaf(vn, n2, dvs[2]);
-                    responded = true;
-                }
+    if (N <= 8) {
+        uint64_t kk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            kk[j] = ~0ull;
+            if (j < N && j != lane) {
+                const float key = pair_partner(c, s, thr, sbase + j, sx, sv, nt, coll, flag_coll, ev, dvs, dw, dw_az,
+                                               dw_hit, responded);
+                kk[j] = ((uint64_t)__float_as_uint(key) << 32) | (uint32_t)j;
             }
         }
+        if (keff > 0) {
+            sort8(kk);
+#pragma unroll
+            for (int k = 0; k < QS_MAX_K; ++k) best[k] = k < keff ? kk[k] : ~0ull;
+        }
+        return responded;
+    }
+    for (int j = 0; j < N; ++j) {
+        if (j == lane) continue;
+        const float key = pair_partner(c, s, thr, sbase + j, sx, sv, nt, coll, flag_coll, ev, dvs, dw, dw_az, dw_hit,
+                                       responded);
         if (keff > 0) topk_insert(best, keff, ((uint64_t)__float_as_uint(key) << 32) | (uint32_t)j);
     }
     return responded;
