@@ -750,6 +750,19 @@ __device__ __forceinline__ void topk_insert(uint64_t best[QS_MAX_K], int K, uint
     }
 }
 
+// The same with the list length KN fixed at compile time (no test of k < K).
+template <int KN>
+__device__ __forceinline__ void topk_insert_n(uint64_t best[QS_MAX_K], uint64_t cand) {
+#pragma unroll
+    for (int k = 0; k < KN; ++k) {
+        if (cand < best[k]) {
+            const uint64_t t = best[k];
+            best[k] = cand;
+            cand = t;
+        }
+    }
+}
+
 // Compare-exchange of two (key, index) words: a <- min, b <- max.
 __device__ __forceinline__ void cmp_swap(uint64_t& a, uint64_t& b) {
     const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
@@ -817,7 +830,7 @@ __device__ __forceinline__ float pair_partner(const Consts& c, const Drone& s, f
 // classes up to 8, so the test is uniform over a tile) keep every partner's
 // (key, index) word in registers and sort them with a network of 19
 // compare-exchanges; larger swarms insert each partner into the list of the
-// K nearest so far.
+// K nearest so far (with K = 6 a list of compile-time length).
 __device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float thr, int lane, int N, int sbase,
                                           const float* sx, const float* sv, int nt, int keff, bool coll, bool flag_coll,
                                           uint32_t& ev, uint64_t best[QS_MAX_K], float dvs[3], const bool dw,
@@ -838,6 +851,15 @@ __device__ __forceinline__ bool pair_scan(const Consts& c, const Drone& s, float
             sort8(kk);
 #pragma unroll
             for (int k = 0; k < QS_MAX_K; ++k) best[k] = k < keff ? kk[k] : ~0ull;
+        }
+        return responded;
+    }
+    if (keff == 6) {  // the paper's K (N > 8 here, so keff = K): the list length fixed
+        for (int j = 0; j < N; ++j) {
+            if (j == lane) continue;
+            const float key = pair_partner(c, s, thr, sbase + j, sx, sv, nt, coll, flag_coll, ev, dvs, dw, dw_az,
+                                           dw_hit, responded);
+            topk_insert_n<6>(best, ((uint64_t)__float_as_uint(key) << 32) | (uint32_t)j);
         }
         return responded;
     }
